@@ -1,0 +1,653 @@
+/*
+ * Plain, sequential CPU oracle for the FF-SRL batched XPBD step
+ * (Dall'Alba et al., "FF-SRL: High Performance GPU-Based Surgical Simulation
+ * For Robot Learning", arXiv 2503.18616).
+ *
+ * TEST INFRASTRUCTURE ONLY. The test suite, the package smoke check and the
+ * CPU-baseline leg of the benchmark are the only code allowed to load this
+ * library. The simulator library never links, loads or calls it, and the two
+ * share no source, header, table or helper. Everything here is written for a
+ * reader who checks it against the paper by eye: one environment at a time,
+ * one constraint at a time, in the order the method defines, no blocking,
+ * fusion or reordering.
+ *
+ * Precision: REAL is double (liboracle_f64). The same file compiled with
+ * -DREAL=float (liboracle_f32) exists only to measure the FP32 rounding floor.
+ *
+ * What each part follows (section numbers of the paper):
+ *   - simulation loop ............ Algorithm 1 (Sec. III-A), with the readings below
+ *   - edge-distance constraint ... Eq. 1, XPBD compliance form (MacklinXPBD2016,
+ *                                  the XPBD paper the method builds on, Sec. III-A)
+ *   - tet-volume constraint ...... Eqs. 2-3, with the corrected gradient assignment
+ *   - tool collision ............. Sec. III-A "Collisions", sphere proxy vs vertices
+ *   - reward / termination ....... Sec. IV (reward R = w_l l + w_d d + w_s s), Sec. III-B
+ *   - substepping ................ Sec. III-A (n substeps x 1 iteration)
+ *
+ * Readings where the paper is silent, garbled or departs from the workload
+ * (each is also listed in the design notes of the repository):
+ *   R1  Eq. 2 assigns the cross products to the wrong vertices and flips the
+ *       sign of the d term. Used here: g_b = x_ca x x_da / 6,
+ *       g_c = x_da x x_ba / 6, g_d = x_ba x x_ca / 6, g_a = -(g_b+g_c+g_d),
+ *       the exact gradient of C = (x_ba x x_ca).x_da / 6 - V0.
+ *   R2  Stiffness k in [0,1] is replaced by XPBD compliance: alpha~ = alpha/h^2,
+ *       dlambda = (-C - alpha~ lambda) / (sum_i w_i |g_i|^2 + alpha~),
+ *       dx_i = w_i dlambda g_i; lambda reset to 0 at the start of every substep.
+ *   R3  Eq. 3's denominator gains the inverse masses w_i (needed for pins).
+ *   R4  Constraints run as graph-coloured Gauss-Seidel: all distance colours,
+ *       then all volume colours; inside a colour no two constraints share a
+ *       vertex, so visiting order inside a colour does not change the result.
+ *       Colouring is greedy first-fit: edges in ascending (min,max) order,
+ *       tets in input order, the two families coloured separately.
+ *   R5  Collision runs once per substep, after the constraint iterations and
+ *       before the velocity update.
+ *   R6  Sphere test is strict (|d| < r); |d| = 0 pushes along +z; pinned
+ *       vertices (w = 0) never move; the tool is kinematic.
+ *   R7  The tool moves once per step, at its start, then stays put for the
+ *       substeps; it is clamped to a box around the rest bounding box.
+ *   R8  Degenerate constraints are skipped: zero denominator, or an edge
+ *       shorter than 1e-12 x extent. A tet with negative rest volume has its
+ *       last two vertices swapped at setup.
+ *   R9  Counter-based RNG: SplitMix64 (Steele, Lea, Flood, OOPSLA 2014).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef REAL
+#define REAL double
+#endif
+
+#define ORC_OK 0
+#define ORC_E_INVAL (-1)
+#define ORC_E_OOM (-3)
+#define ORC_E_DEGENERATE (-4)
+#define ORC_MAX_COLORS 256
+
+/* ------------------------------------------------------------------------ */
+/* Counter-based random numbers (R9).                                        */
+/* ------------------------------------------------------------------------ */
+
+static const uint64_t ORC_GOLDEN_GAMMA = 0x9E3779B97F4A7C15ULL;
+
+/* SplitMix64 output function applied to one state word. */
+uint64_t orc_mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* The n-th (0-based) output of SplitMix64 started from state `state`. */
+uint64_t orc_sm64(uint64_t state, uint64_t n) {
+    return orc_mix64(state + (n + 1) * ORC_GOLDEN_GAMMA);
+}
+
+/* Per-environment stream: domain 0 = actions, 1 = observation sample,
+ * 2 = target vertex. */
+uint64_t orc_stream(uint64_t seed, uint64_t env, uint32_t domain) {
+    return orc_sm64(seed, 4 * env + domain);
+}
+
+/* Top 24 bits of r as a uniform number in [-1, 1). */
+double orc_uniform_pm1(uint64_t r) {
+    double u = (double)(r >> 40) * (1.0 / 16777216.0);
+    return 2.0 * u - 1.0;
+}
+
+/* Action component `axis` of environment `env` at its step `t` since reset. */
+double orc_action(uint64_t seed, uint64_t env, uint64_t t, int axis) {
+    return orc_uniform_pm1(orc_sm64(orc_stream(seed, env, 0), 3 * t + (uint64_t)axis));
+}
+
+/* Floyd's sampling of k distinct indices from [0, n), sorted ascending. */
+int orc_sample_indices(uint64_t seed, uint64_t env, int n, int k, int* out) {
+    if (k < 0 || k > n) return ORC_E_INVAL;
+    uint64_t st = orc_stream(seed, env, 1);
+    int m = 0;
+    for (int j = n - k; j < n; ++j) {
+        uint64_t r = orc_sm64(st, (uint64_t)j);
+        int t = (int)(r % (uint64_t)(j + 1));
+        int taken = 0;
+        for (int q = 0; q < m; ++q)
+            if (out[q] == t) taken = 1;
+        out[m++] = taken ? j : t;
+    }
+    for (int a = 1; a < m; ++a) { /* insertion sort */
+        int key = out[a], b = a - 1;
+        while (b >= 0 && out[b] > key) { out[b + 1] = out[b]; --b; }
+        out[b + 1] = key;
+    }
+    return ORC_OK;
+}
+
+int orc_target_index(uint64_t seed, uint64_t env, int n) {
+    return (int)(orc_sm64(orc_stream(seed, env, 2), 0) % (uint64_t)n);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Small vector helpers.                                                     */
+/* ------------------------------------------------------------------------ */
+
+static void vsub(const REAL* a, const REAL* b, REAL* o) {
+    o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2];
+}
+static void vcross(const REAL* a, const REAL* b, REAL* o) {
+    REAL t0 = a[1] * b[2] - a[2] * b[1];
+    REAL t1 = a[2] * b[0] - a[0] * b[2];
+    REAL t2 = a[0] * b[1] - a[1] * b[0];
+    o[0] = t0; o[1] = t1; o[2] = t2;
+}
+static REAL vdot(const REAL* a, const REAL* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static REAL vnorm(const REAL* a) { return sqrt(vdot(a, a)); }
+
+/* Signed tet volume (x_ba x x_ca) . x_da / 6 (the C^v definition, Sec. III-A). */
+static REAL tet_volume(const REAL* xa, const REAL* xb, const REAL* xc, const REAL* xd) {
+    REAL ba[3], ca[3], da[3], n[3];
+    vsub(xb, xa, ba); vsub(xc, xa, ca); vsub(xd, xa, da);
+    vcross(ba, ca, n);
+    return vdot(n, da) / 6;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Mesh setup (Sec. III-A: vertices, edges, tets; rest distance and rest     */
+/* volume computed before the loop; R4 colouring, R8 orientation).           */
+/* ------------------------------------------------------------------------ */
+
+typedef struct orc_mesh {
+    int V, T, E;
+    REAL* rest;     /* [V][3] */
+    REAL* w;        /* [V] inverse mass, 0 = pinned */
+    int* tet;       /* [T][4] oriented */
+    int* flipped;   /* [T] 1 if vertices 2 and 3 were swapped */
+    REAL* V0;       /* [T] rest volume (> 0) */
+    int* edge;      /* [E][2], edge[0] < edge[1], ascending */
+    REAL* d;        /* [E] rest length */
+    int n_ecol, n_tcol;
+    int* ecolor;    /* [E] */
+    int* tcolor;    /* [T] */
+    int* eorder;    /* [E] colour-major order: position -> edge id */
+    int* torder;    /* [T] */
+    int* ecol_off;  /* [n_ecol + 1] */
+    int* tcol_off;  /* [n_tcol + 1] */
+    int n_top;
+    int* top;       /* ascending ids of vertices with z == max z */
+    REAL bbmin[3], bbmax[3];
+    REAL extent;    /* max side of the rest bounding box */
+} orc_mesh;
+
+void orc_mesh_destroy(orc_mesh* m) {
+    if (!m) return;
+    free(m->rest); free(m->w); free(m->tet); free(m->flipped); free(m->V0);
+    free(m->edge); free(m->d); free(m->ecolor); free(m->tcolor);
+    free(m->eorder); free(m->torder); free(m->ecol_off); free(m->tcol_off);
+    free(m->top); free(m);
+}
+
+static int cmp_pair(const void* pa, const void* pb) {
+    const int* a = (const int*)pa; const int* b = (const int*)pb;
+    if (a[0] != b[0]) return a[0] < b[0] ? -1 : 1;
+    if (a[1] != b[1]) return a[1] < b[1] ? -1 : 1;
+    return 0;
+}
+
+/* Greedy first-fit colouring: constraint i (visited in index order) takes the
+ * smallest colour used by no earlier constraint that shares a vertex with it.
+ * used[v][c] marks colour c as taken at vertex v. */
+static int color_first_fit(int n, int arity, const int* cons, int V, int* color, int* n_colors) {
+    unsigned char* used = (unsigned char*)calloc((size_t)V * ORC_MAX_COLORS, 1);
+    if (!used) return ORC_E_OOM;
+    int nc = 0;
+    for (int i = 0; i < n; ++i) {
+        int c = 0;
+        for (;;) {
+            int clash = 0;
+            for (int k = 0; k < arity; ++k)
+                if (used[(size_t)cons[i * arity + k] * ORC_MAX_COLORS + c]) clash = 1;
+            if (!clash) break;
+            ++c;
+            if (c >= ORC_MAX_COLORS) { free(used); return ORC_E_INVAL; }
+        }
+        color[i] = c;
+        for (int k = 0; k < arity; ++k) used[(size_t)cons[i * arity + k] * ORC_MAX_COLORS + c] = 1;
+        if (c + 1 > nc) nc = c + 1;
+    }
+    free(used);
+    *n_colors = nc;
+    return ORC_OK;
+}
+
+/* Stable colour-major order: constraints sorted by (colour, index). */
+static void color_major(int n, const int* color, int nc, int* order, int* off) {
+    int p = 0;
+    for (int c = 0; c < nc; ++c) {
+        off[c] = p;
+        for (int i = 0; i < n; ++i)
+            if (color[i] == c) order[p++] = i;
+    }
+    off[nc] = p;
+}
+
+/* Builds the mesh tables. If edges_in is given (n_edges_in pairs), it replaces
+ * the edge extraction from tets (used only by pins with a single constraint).
+ * Returns NULL and sets *err on failure. */
+orc_mesh* orc_mesh_create(int V, const double* rest, const double* w, int T, const int* tets,
+                          int n_edges_in, const int* edges_in, int* err) {
+    *err = ORC_E_INVAL;
+    if (V <= 0 || T < 0 || (T == 0 && !edges_in)) return NULL;
+    orc_mesh* m = (orc_mesh*)calloc(1, sizeof(orc_mesh));
+    if (!m) { *err = ORC_E_OOM; return NULL; }
+    m->V = V; m->T = T;
+    m->rest = (REAL*)malloc(sizeof(REAL) * 3 * V);
+    m->w = (REAL*)malloc(sizeof(REAL) * V);
+    m->tet = (int*)malloc(sizeof(int) * 4 * (T > 0 ? T : 1));
+    m->flipped = (int*)calloc(T > 0 ? T : 1, sizeof(int));
+    m->V0 = (REAL*)malloc(sizeof(REAL) * (T > 0 ? T : 1));
+    for (int i = 0; i < 3 * V; ++i) m->rest[i] = (REAL)rest[i];
+    for (int i = 0; i < V; ++i) {
+        m->w[i] = (REAL)w[i];
+        if (!(w[i] >= 0)) { orc_mesh_destroy(m); return NULL; }
+    }
+    /* bounding box and extent */
+    for (int k = 0; k < 3; ++k) { m->bbmin[k] = m->rest[k]; m->bbmax[k] = m->rest[k]; }
+    for (int i = 0; i < V; ++i)
+        for (int k = 0; k < 3; ++k) {
+            if (m->rest[3 * i + k] < m->bbmin[k]) m->bbmin[k] = m->rest[3 * i + k];
+            if (m->rest[3 * i + k] > m->bbmax[k]) m->bbmax[k] = m->rest[3 * i + k];
+        }
+    m->extent = 0;
+    for (int k = 0; k < 3; ++k)
+        if (m->bbmax[k] - m->bbmin[k] > m->extent) m->extent = m->bbmax[k] - m->bbmin[k];
+    /* tets: validate, orient (R8), rest volume */
+    for (int t = 0; t < T; ++t) {
+        int q[4];
+        for (int k = 0; k < 4; ++k) {
+            q[k] = tets[4 * t + k];
+            if (q[k] < 0 || q[k] >= V) { orc_mesh_destroy(m); return NULL; }
+        }
+        for (int a = 0; a < 4; ++a)
+            for (int b = a + 1; b < 4; ++b)
+                if (q[a] == q[b]) { orc_mesh_destroy(m); return NULL; }
+        REAL vol = tet_volume(&m->rest[3 * q[0]], &m->rest[3 * q[1]], &m->rest[3 * q[2]], &m->rest[3 * q[3]]);
+        if (vol < 0) {
+            int s = q[2]; q[2] = q[3]; q[3] = s;
+            m->flipped[t] = 1;
+            vol = tet_volume(&m->rest[3 * q[0]], &m->rest[3 * q[1]], &m->rest[3 * q[2]], &m->rest[3 * q[3]]);
+        }
+        REAL L3 = m->extent * m->extent * m->extent;
+        if (!(vol > 1e-12 * L3)) { orc_mesh_destroy(m); *err = ORC_E_DEGENERATE; return NULL; }
+        for (int k = 0; k < 4; ++k) m->tet[4 * t + k] = q[k];
+        m->V0[t] = vol;
+    }
+    /* edges: the six vertex pairs of every tet, as (min, max), sorted, unique */
+    int* pairs;
+    int np;
+    if (edges_in) {
+        np = n_edges_in;
+        pairs = (int*)malloc(sizeof(int) * 2 * (np > 0 ? np : 1));
+        for (int e = 0; e < np; ++e) {
+            int a = edges_in[2 * e], b = edges_in[2 * e + 1];
+            if (a < 0 || a >= V || b < 0 || b >= V || a == b) { free(pairs); orc_mesh_destroy(m); return NULL; }
+            pairs[2 * e] = a < b ? a : b;
+            pairs[2 * e + 1] = a < b ? b : a;
+        }
+    } else {
+        np = 6 * T;
+        pairs = (int*)malloc(sizeof(int) * 2 * (np > 0 ? np : 1));
+        static const int PA[6] = {0, 0, 0, 1, 1, 2}, PB[6] = {1, 2, 3, 2, 3, 3};
+        for (int t = 0; t < T; ++t)
+            for (int k = 0; k < 6; ++k) {
+                int a = m->tet[4 * t + PA[k]], b = m->tet[4 * t + PB[k]];
+                pairs[2 * (6 * t + k)] = a < b ? a : b;
+                pairs[2 * (6 * t + k) + 1] = a < b ? b : a;
+            }
+    }
+    qsort(pairs, (size_t)np, sizeof(int) * 2, cmp_pair);
+    int E = 0;
+    for (int p = 0; p < np; ++p)
+        if (E == 0 || cmp_pair(&pairs[2 * p], &pairs[2 * (E - 1)]) != 0) {
+            pairs[2 * E] = pairs[2 * p]; pairs[2 * E + 1] = pairs[2 * p + 1]; ++E;
+        }
+    m->E = E;
+    m->edge = (int*)malloc(sizeof(int) * 2 * (E > 0 ? E : 1));
+    m->d = (REAL*)malloc(sizeof(REAL) * (E > 0 ? E : 1));
+    memcpy(m->edge, pairs, sizeof(int) * 2 * E);
+    free(pairs);
+    for (int e = 0; e < E; ++e) {
+        REAL ab[3];
+        vsub(&m->rest[3 * m->edge[2 * e]], &m->rest[3 * m->edge[2 * e + 1]], ab);
+        m->d[e] = vnorm(ab);
+        if (!(m->d[e] > 0)) { orc_mesh_destroy(m); *err = ORC_E_DEGENERATE; return NULL; }
+    }
+    /* colouring (R4) */
+    m->ecolor = (int*)malloc(sizeof(int) * (E > 0 ? E : 1));
+    m->tcolor = (int*)malloc(sizeof(int) * (T > 0 ? T : 1));
+    m->eorder = (int*)malloc(sizeof(int) * (E > 0 ? E : 1));
+    m->torder = (int*)malloc(sizeof(int) * (T > 0 ? T : 1));
+    int rc = color_first_fit(E, 2, m->edge, V, m->ecolor, &m->n_ecol);
+    if (rc == ORC_OK) rc = color_first_fit(T, 4, m->tet, V, m->tcolor, &m->n_tcol);
+    if (rc != ORC_OK) { orc_mesh_destroy(m); *err = rc; return NULL; }
+    m->ecol_off = (int*)malloc(sizeof(int) * (m->n_ecol + 1));
+    m->tcol_off = (int*)malloc(sizeof(int) * (m->n_tcol + 1));
+    color_major(E, m->ecolor, m->n_ecol, m->eorder, m->ecol_off);
+    color_major(T, m->tcolor, m->n_tcol, m->torder, m->tcol_off);
+    /* top face: vertices whose z equals the largest z */
+    m->top = (int*)malloc(sizeof(int) * V);
+    m->n_top = 0;
+    for (int i = 0; i < V; ++i)
+        if (m->rest[3 * i + 2] == m->bbmax[2]) m->top[m->n_top++] = i;
+    *err = ORC_OK;
+    return m;
+}
+
+/* Read-only views for the test suite. which: 0 info, see below. */
+void orc_mesh_info(const orc_mesh* m, int* out /* 6 */) {
+    out[0] = m->V; out[1] = m->T; out[2] = m->E;
+    out[3] = m->n_ecol; out[4] = m->n_tcol; out[5] = m->n_top;
+}
+/* which: 0 tet[4T], 1 flipped[T], 2 edge[2E], 3 ecolor[E], 4 tcolor[T],
+ *        5 eorder[E], 6 torder[T], 7 ecol_off, 8 tcol_off, 9 top */
+int orc_mesh_get_int(const orc_mesh* m, int which, int* out) {
+    switch (which) {
+    case 0: memcpy(out, m->tet, sizeof(int) * 4 * m->T); break;
+    case 1: memcpy(out, m->flipped, sizeof(int) * m->T); break;
+    case 2: memcpy(out, m->edge, sizeof(int) * 2 * m->E); break;
+    case 3: memcpy(out, m->ecolor, sizeof(int) * m->E); break;
+    case 4: memcpy(out, m->tcolor, sizeof(int) * m->T); break;
+    case 5: memcpy(out, m->eorder, sizeof(int) * m->E); break;
+    case 6: memcpy(out, m->torder, sizeof(int) * m->T); break;
+    case 7: memcpy(out, m->ecol_off, sizeof(int) * (m->n_ecol + 1)); break;
+    case 8: memcpy(out, m->tcol_off, sizeof(int) * (m->n_tcol + 1)); break;
+    case 9: memcpy(out, m->top, sizeof(int) * m->n_top); break;
+    default: return ORC_E_INVAL;
+    }
+    return ORC_OK;
+}
+/* which: 0 d[E], 1 V0[T], 2 bbmin[3], 3 bbmax[3], 4 extent */
+int orc_mesh_get_real(const orc_mesh* m, int which, double* out) {
+    switch (which) {
+    case 0: for (int e = 0; e < m->E; ++e) out[e] = m->d[e]; break;
+    case 1: for (int t = 0; t < m->T; ++t) out[t] = m->V0[t]; break;
+    case 2: for (int k = 0; k < 3; ++k) out[k] = m->bbmin[k]; break;
+    case 3: for (int k = 0; k < 3; ++k) out[k] = m->bbmax[k]; break;
+    case 4: out[0] = m->extent; break;
+    default: return ORC_E_INVAL;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Constraint projections (Eq. 1, Eqs. 2-3, readings R1-R3, R8).             */
+/* ------------------------------------------------------------------------ */
+
+/* Distance constraint C = |x_a - x_b| - d. Gradient wrt x_a is n = x_ab/|x_ab|,
+ * wrt x_b is -n. Returns the constraint value before the update. */
+REAL orc_project_edge(REAL* xa, REAL* xb, REAL wa, REAL wb, REAL d, REAL alpha_t,
+                      REAL* lambda, REAL min_len) {
+    REAL ab[3];
+    vsub(xa, xb, ab);
+    REAL len = vnorm(ab);
+    REAL C = len - d;
+    REAL denom = wa + wb + alpha_t;
+    if (len < min_len || denom == 0) return C;
+    REAL n[3] = {ab[0] / len, ab[1] / len, ab[2] / len};
+    REAL dl = (-C - alpha_t * (*lambda)) / denom;
+    for (int k = 0; k < 3; ++k) {
+        xa[k] += wa * dl * n[k];
+        xb[k] -= wb * dl * n[k];
+    }
+    *lambda += dl;
+    return C;
+}
+
+/* Volume constraint C = (x_ba x x_ca).x_da / 6 - V0 with the gradients of R1. */
+REAL orc_project_tet(REAL* xa, REAL* xb, REAL* xc, REAL* xd, const REAL* w4, REAL V0,
+                     REAL alpha_t, REAL* lambda) {
+    REAL ba[3], ca[3], da[3], g[4][3];
+    vsub(xb, xa, ba); vsub(xc, xa, ca); vsub(xd, xa, da);
+    vcross(ca, da, g[1]);
+    vcross(da, ba, g[2]);
+    vcross(ba, ca, g[3]);
+    for (int k = 0; k < 3; ++k) {
+        g[1][k] /= 6; g[2][k] /= 6; g[3][k] /= 6;
+        g[0][k] = -(g[1][k] + g[2][k] + g[3][k]);
+    }
+    REAL C = tet_volume(xa, xb, xc, xd) - V0; /* C^v by its definition */
+    REAL denom = alpha_t;
+    for (int i = 0; i < 4; ++i) denom += w4[i] * vdot(g[i], g[i]);
+    if (denom == 0) return C;
+    REAL dl = (-C - alpha_t * (*lambda)) / denom;
+    REAL* x[4] = {xa, xb, xc, xd};
+    for (int i = 0; i < 4; ++i)
+        for (int k = 0; k < 3; ++k) x[i][k] += w4[i] * dl * g[i][k];
+    *lambda += dl;
+    return C;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Environment: parameters, state, reset and step.                           */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double dt;
+    int substeps, iterations;
+    double gravity[3];
+    double alpha_d, alpha_v;   /* compliance of distance / volume constraints */
+    double radius;             /* sphere tool radius */
+    double action_scale;       /* tool displacement per step for |a| = 1 */
+    double margin_xy, margin_below, margin_above; /* tool box (R7) */
+    double w_l, w_d, w_s, success_dist;           /* reward weights (Sec. IV) */
+    int n_obs, max_steps;
+} orc_params;
+
+typedef struct orc_env {
+    const orc_mesh* m;
+    int V;
+    REAL* x;      /* [V][3] */
+    REAL* v;      /* [V][3] */
+    REAL* xprev;  /* [V][3] */
+    REAL* lam_e;  /* [E] */
+    REAL* lam_t;  /* [T] */
+    REAL c[3];    /* tool centre */
+    REAL lo[3], hi[3];
+    REAL l_prev;
+    int t;        /* steps since reset */
+    uint64_t seed, env;
+    int* obs;     /* [n_obs] vertex ids */
+    int n_obs;
+    int target;
+    int n_contacts;
+    int* contacts; /* ascending ids touched by the tool in the last substep */
+} orc_env;
+
+void orc_env_destroy(orc_env* s) {
+    if (!s) return;
+    free(s->x); free(s->v); free(s->xprev); free(s->lam_e); free(s->lam_t);
+    free(s->obs); free(s->contacts); free(s);
+}
+
+orc_env* orc_env_create(const orc_mesh* m) {
+    orc_env* s = (orc_env*)calloc(1, sizeof(orc_env));
+    s->m = m; s->V = m->V;
+    s->x = (REAL*)calloc(3 * m->V, sizeof(REAL));
+    s->v = (REAL*)calloc(3 * m->V, sizeof(REAL));
+    s->xprev = (REAL*)calloc(3 * m->V, sizeof(REAL));
+    s->lam_e = (REAL*)calloc(m->E > 0 ? m->E : 1, sizeof(REAL));
+    s->lam_t = (REAL*)calloc(m->T > 0 ? m->T : 1, sizeof(REAL));
+    s->obs = (int*)calloc(m->V, sizeof(int));
+    s->contacts = (int*)calloc(m->V, sizeof(int));
+    return s;
+}
+
+static REAL dist3(const REAL* a, const REAL* b) {
+    REAL d[3];
+    vsub(a, b, d);
+    return vnorm(d);
+}
+
+/* Episode reset (Sec. III-B): rest positions, zero velocity, tool at its
+ * start above the centre of the top face, fresh observation sample and
+ * target vertex drawn from (seed, env). */
+int orc_env_reset(orc_env* s, const orc_params* p, uint64_t seed, uint64_t env) {
+    const orc_mesh* m = s->m;
+    if (p->n_obs < 0 || p->n_obs > m->n_top || m->n_top == 0) return ORC_E_INVAL;
+    for (int i = 0; i < 3 * m->V; ++i) { s->x[i] = m->rest[i]; s->v[i] = 0; }
+    for (int k = 0; k < 2; ++k) {
+        s->c[k] = (m->bbmin[k] + m->bbmax[k]) / 2;
+        s->lo[k] = m->bbmin[k] - (REAL)p->margin_xy;
+        s->hi[k] = m->bbmax[k] + (REAL)p->margin_xy;
+    }
+    s->c[2] = m->bbmax[2] + (REAL)p->radius;
+    s->lo[2] = m->bbmax[2] - (REAL)p->margin_below;
+    s->hi[2] = m->bbmax[2] + (REAL)p->margin_above;
+    s->t = 0; s->seed = seed; s->env = env;
+    s->n_obs = p->n_obs;
+    int* idx = (int*)malloc(sizeof(int) * (p->n_obs > 0 ? p->n_obs : 1));
+    orc_sample_indices(seed, env, m->n_top, p->n_obs, idx);
+    for (int k = 0; k < p->n_obs; ++k) s->obs[k] = m->top[idx[k]];
+    free(idx);
+    s->target = m->top[orc_target_index(seed, env, m->n_top)];
+    s->l_prev = dist3(s->c, &s->x[3 * s->target]);
+    s->n_contacts = 0;
+    return ORC_OK;
+}
+
+/* Tool-tissue collision against the sphere proxy (Sec. III-A "Collisions",
+ * readings R5, R6). Records contacts when `record` is set. */
+static void collide_sphere(orc_env* s, REAL r, int record) {
+    const orc_mesh* m = s->m;
+    if (record) s->n_contacts = 0;
+    for (int i = 0; i < m->V; ++i) {
+        if (m->w[i] == 0) continue;
+        REAL* x = &s->x[3 * i];
+        REAL d[3];
+        vsub(x, s->c, d);
+        REAL len = vnorm(d);
+        if (len < r) {
+            if (len > 0) {
+                REAL n[3] = {d[0] / len, d[1] / len, d[2] / len};
+                for (int k = 0; k < 3; ++k) x[k] = s->c[k] + r * n[k];
+            } else {
+                x[0] = s->c[0]; x[1] = s->c[1]; x[2] = s->c[2] + r;
+            }
+            if (record) s->contacts[s->n_contacts++] = i;
+        }
+    }
+}
+
+/* One substep (Algorithm 1's inner loop with readings R2, R4, R5). */
+static void substep(orc_env* s, const orc_params* p, REAL h, REAL alpha_d, int record) {
+    const orc_mesh* m = s->m;
+    const REAL min_len = (REAL)1e-12 * m->extent;
+    /* predict velocity and position */
+    for (int i = 0; i < m->V; ++i) {
+        for (int k = 0; k < 3; ++k) s->xprev[3 * i + k] = s->x[3 * i + k];
+        if (m->w[i] == 0) continue;
+        for (int k = 0; k < 3; ++k) {
+            s->v[3 * i + k] += h * (REAL)p->gravity[k];
+            s->x[3 * i + k] += h * s->v[3 * i + k];
+        }
+    }
+    /* constraint iterations: distance colours, then volume colours */
+    REAL at_d = alpha_d / (h * h);
+    REAL at_v = (REAL)p->alpha_v / (h * h);
+    for (int e = 0; e < m->E; ++e) s->lam_e[e] = 0;
+    for (int t = 0; t < m->T; ++t) s->lam_t[t] = 0;
+    for (int it = 0; it < p->iterations; ++it) {
+        for (int c = 0; c < m->n_ecol; ++c)
+            for (int q = m->ecol_off[c]; q < m->ecol_off[c + 1]; ++q) {
+                int e = m->eorder[q];
+                int a = m->edge[2 * e], b = m->edge[2 * e + 1];
+                orc_project_edge(&s->x[3 * a], &s->x[3 * b], m->w[a], m->w[b], m->d[e], at_d,
+                                 &s->lam_e[e], min_len);
+            }
+        for (int c = 0; c < m->n_tcol; ++c)
+            for (int q = m->tcol_off[c]; q < m->tcol_off[c + 1]; ++q) {
+                int t = m->torder[q];
+                const int* v4 = &m->tet[4 * t];
+                REAL w4[4] = {m->w[v4[0]], m->w[v4[1]], m->w[v4[2]], m->w[v4[3]]};
+                orc_project_tet(&s->x[3 * v4[0]], &s->x[3 * v4[1]], &s->x[3 * v4[2]], &s->x[3 * v4[3]],
+                                w4, m->V0[t], at_v, &s->lam_t[t]);
+            }
+    }
+    collide_sphere(s, (REAL)p->radius, record);
+    /* velocity update */
+    for (int i = 0; i < 3 * m->V; ++i) s->v[i] = (s->x[i] - s->xprev[i]) / h;
+}
+
+int orc_obs_dim(const orc_params* p) { return 3 + 3 * p->n_obs; }
+
+/* One simulation step: tool update (R7), `substeps` substeps, then
+ * observation, reward and termination (Sec. III-B, Sec. IV).
+ * action: 3 numbers in [-1, 1], or NULL to draw them from the counter-based
+ * stream of (seed, env, t). alpha_d < 0 selects p->alpha_d. */
+int orc_env_step(orc_env* s, const orc_params* p, const double* action, double alpha_d,
+                 double* obs, double* reward, unsigned char* done) {
+    const orc_mesh* m = s->m;
+    double a[3];
+    for (int k = 0; k < 3; ++k)
+        a[k] = action ? action[k] : orc_action(s->seed, s->env, (uint64_t)s->t, k);
+    for (int k = 0; k < 3; ++k) {
+        REAL c = s->c[k] + (REAL)(p->action_scale * a[k]);
+        if (c < s->lo[k]) c = s->lo[k];
+        if (c > s->hi[k]) c = s->hi[k];
+        s->c[k] = c;
+    }
+    REAL h = (REAL)(p->dt / p->substeps);
+    REAL ad = (REAL)(alpha_d >= 0 ? alpha_d : p->alpha_d);
+    for (int sub = 0; sub < p->substeps; ++sub) substep(s, p, h, ad, sub == p->substeps - 1);
+    /* observation: tool centre, then the sampled surface vertices */
+    if (obs) {
+        for (int k = 0; k < 3; ++k) obs[k] = (double)s->c[k];
+        for (int q = 0; q < s->n_obs; ++q)
+            for (int k = 0; k < 3; ++k) obs[3 + 3 * q + k] = (double)s->x[3 * s->obs[q] + k];
+    }
+    REAL l = dist3(s->c, &s->x[3 * s->target]);
+    int succ = l < (REAL)p->success_dist;
+    REAL R = (REAL)p->w_l * l + (REAL)p->w_d * (l - s->l_prev) + (REAL)p->w_s * (REAL)succ;
+    s->l_prev = l;
+    s->t += 1;
+    if (reward) *reward = (double)R;
+    if (done) *done = (unsigned char)(((p->max_steps > 0 && s->t >= p->max_steps) || succ) ? 1 : 0);
+    (void)m;
+    return ORC_OK;
+}
+
+/* n steps in a row; obs [n][obs_dim], reward [n], done [n] may be NULL.
+ * actions [n][3] or NULL for the counter-based stream. */
+int orc_env_run(orc_env* s, const orc_params* p, int n, const double* actions, double alpha_d,
+                double* obs, double* reward, unsigned char* done) {
+    int od = orc_obs_dim(p);
+    for (int i = 0; i < n; ++i) {
+        int rc = orc_env_step(s, p, actions ? &actions[3 * i] : NULL, alpha_d,
+                              obs ? &obs[(size_t)i * od] : NULL, reward ? &reward[i] : NULL,
+                              done ? &done[i] : NULL);
+        if (rc) return rc;
+    }
+    return ORC_OK;
+}
+
+/* State access for the test suite (all double arrays, [V][3] / [3]). */
+void orc_env_get(const orc_env* s, double* x, double* v, double* c) {
+    for (int i = 0; i < 3 * s->V; ++i) {
+        if (x) x[i] = (double)s->x[i];
+        if (v) v[i] = (double)s->v[i];
+    }
+    if (c) for (int k = 0; k < 3; ++k) c[k] = (double)s->c[k];
+}
+void orc_env_set(orc_env* s, const double* x, const double* v, const double* c) {
+    for (int i = 0; i < 3 * s->V; ++i) {
+        if (x) s->x[i] = (REAL)x[i];
+        if (v) s->v[i] = (REAL)v[i];
+    }
+    if (c) for (int k = 0; k < 3; ++k) s->c[k] = (REAL)c[k];
+}
+/* ints: [0] t, [1] target, [2] n_obs, [3] n_contacts, then obs ids, then contact ids */
+void orc_env_get_ints(const orc_env* s, int* out) {
+    out[0] = s->t; out[1] = s->target; out[2] = s->n_obs; out[3] = s->n_contacts;
+    for (int q = 0; q < s->n_obs; ++q) out[4 + q] = s->obs[q];
+    for (int q = 0; q < s->n_contacts; ++q) out[4 + s->n_obs + q] = s->contacts[q];
+}
+void orc_env_get_tool_box(const orc_env* s, double* lo, double* hi) {
+    for (int k = 0; k < 3; ++k) { lo[k] = (double)s->lo[k]; hi[k] = (double)s->hi[k]; }
+}
+int orc_real_size(void) { return (int)sizeof(REAL); }
