@@ -1,0 +1,378 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the batched XPBD step (FF-SRL method, arXiv 2503.18616).
+
+One benchmark step = one ffsrl_step over every environment of the workload:
+tool update, 10 substeps of predict / coloured constraint projection / sphere
+collision / velocity update, then observation, reward and done flags.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on host cores)
+
+Prints one JSON line on rank 0. The default workload is 4096 environments of
+the 17x17x9-vertex tissue block (2601 vertices, 10240 tets), device-drawn
+actions, positions and velocities resident in HBM (258 MB, larger than L2).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "env-steps/s at ≤1e-5·extent pos err vs FP64 oracle; learned warm-start vs plain"
+UNIT = "env-steps/s"
+POS_TOL = 1e-5
+
+# Algorithmic FP32 operations of the kernel's arithmetic (each add, mul, div,
+# sqrt counts one; an FMA counts two): per edge projection, tet projection and
+# vertex per substep.
+FLOP_EDGE, FLOP_TET, FLOP_VERT = 32, 115, 28
+# Algorithmic HBM bytes per env-step: x and v read and written once (48 B per
+# vertex), per-env scalars and the observation written.
+BYTES_VERT = 48
+
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
+N_SM, FP32_LANES = 152, 128
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return dict(FALLBACK_PEAKS), "fallback"
+
+
+def workload(name: str):
+    from paper_2503_18616_gb300 import inputs
+    w = inputs.WORKLOADS[name]
+    if "shape" not in w:
+        raise SystemExit(f"workload {name} is not a single-mesh batch")
+    mesh = inputs.grid_block(*w["shape"])
+    return w, mesh, inputs.default_params()
+
+
+def flops_per_env_step(V, E, T, params):
+    s, it = params["substeps"], params["iterations"]
+    return s * (it * (E * FLOP_EDGE + T * FLOP_TET) + V * FLOP_VERT)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("xpbd_step.cu", "xpbd_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2503_18616_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(profile: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", profile)
+    try:
+        kv = {}
+        with open(path) as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    kv[k.strip().lstrip("- ")] = v.strip()
+        if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+            return None
+        return float(kv["dram_bytes_per_full_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def oracle_rate(mesh, params, seconds: float, seed: int, envs=(0,), max_steps=None):
+    """FP64 oracle env-steps/s on one host thread over a bounded sample; also
+    returns the oracle states after the sampled steps for the accuracy check."""
+    import numpy as np  # noqa: F401
+    import oracle
+    om = oracle.Mesh(*mesh)
+    oes = []
+    for e in envs:
+        oe = oracle.Env(om, params)
+        oe.reset(seed, e)
+        oes.append(oe)
+    t0 = time.perf_counter()
+    oes[0].run(3, want_obs=False)
+    per_step = (time.perf_counter() - t0) / 3
+    n = max(5, int(seconds / (per_step * len(oes))))
+    if max_steps is not None:
+        n = min(n, max_steps)
+    for oe in oes:   # restart from reset so all envs run exactly n steps
+        oe.reset(seed, envs[oes.index(oe)])
+    t0 = time.perf_counter()
+    for oe in oes:
+        oe.run(n, want_obs=False)
+    dt = time.perf_counter() - t0
+    return len(oes) * n / dt, n, dt, oes, om
+
+
+def run_reference(args):
+    """The oracle as it stands, timed on host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    w, mesh, params = workload(args.workload)
+    om = oracle.Mesh(*mesh)
+    probe = oracle.Env(om, params)
+    probe.reset(args.seed, 0)
+    t0 = time.perf_counter()
+    probe.run(3, want_obs=False)
+    per_env_step = (time.perf_counter() - t0) / 3
+    budget = 120.0
+    n_sample = max(1, min(w["n_env"], int(budget / ((args.steps + args.warmup) * per_env_step))))
+    envs = []
+    for e in range(n_sample):
+        oe = oracle.Env(om, params)
+        oe.reset(args.seed, e)
+        envs.append(oe)
+    for _ in range(args.warmup):
+        for oe in envs:
+            oe.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for oe in envs:
+            oe.step()
+    dt = time.perf_counter() - t0
+    value = n_sample * args.steps / dt
+    sample = (f"{n_sample} of {w['n_env']} envs of the {om.V}-vertex block per step, "
+              f"FP64 oracle, 1 host thread")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload, "n_env": w["n_env"], "verts_per_env": om.V,
+                       "tets_per_env": om.T, "substeps": params["substeps"],
+                       "iterations": params["iterations"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    from paper_2503_18616_gb300 import ffsrl, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.gpus != world and world > 1:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world > 1:
+        __graft_entry__.build()
+
+    w, mesh, params = workload(args.workload)
+    n_env = w["n_env"]
+    sim = ffsrl.Sim([mesh], params, n_env)
+    seed = args.seed + 1000003 * rank          # each rank owns its own env shard
+    sim.reset(seed)
+    stream = sim.stream
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # Device-resident throughput: actions drawn on the device, outputs to HBM.
+    obs = torch.empty((n_env, sim.obs_dim), dtype=torch.float32, device="cuda")
+    rew = torch.empty(n_env, dtype=torch.float32, device="cuda")
+    done = torch.empty(n_env, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        sim.step_into(None, obs, rew, done)
+    torch.cuda.synchronize()
+    sim.sync()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            sim.step_into(None, obs, rew, done)
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    sim.sync()
+    if dist is not None:
+        t = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    value = world * n_env * args.steps / (t_ms / 1e3)
+
+    # End to end through the public host-buffer call: actions copied in,
+    # observation, reward and done copied out, every step.
+    acts = inputs.random_actions(1, n_env, 11 + rank)[0].astype(np.float32)
+    h_obs = np.empty((n_env, sim.obs_dim), np.float32)
+    h_rew = np.empty(n_env, np.float32)
+    h_done = np.empty(n_env, np.uint8)
+    sim.reset(seed)
+    for _ in range(args.warmup):
+        sim.step_host(acts, h_obs, h_rew, h_done)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.step_host(acts, h_obs, h_rew, h_done)
+    t_e2e = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    e2e = {"value": world * n_env * args.steps / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": int(acts.nbytes),
+           "d2h_bytes_per_step": int(h_obs.nbytes + h_rew.nbytes + h_done.nbytes)}
+
+    line = None
+    if rank == 0:
+        peaks, peak_src = load_peaks()
+        import oracle
+        om = oracle.Mesh(*mesh)
+        V, E, T = om.V, om.E, om.T
+        ms_kernel = t_ms / args.steps          # one step-kernel launch per step
+        flops = flops_per_env_step(V, E, T, params) * n_env
+        clock_mhz = float(peaks.get("sm_max_mhz", FALLBACK_PEAKS["sm_max_mhz"]))
+        alu_peak = 2 * FP32_LANES * N_SM * clock_mhz * 1e6 / 1e12
+        achieved = flops / (ms_kernel / 1e3) / 1e12
+        traffic = ncu_traffic("xpbd_step_block17x17x9_4096env.txt")
+        hbm_bytes = (BYTES_VERT * V + 4 * sim.obs_dim + 16) * n_env
+        roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": achieved / alu_peak, "traffic": traffic,
+                    "kernel": "xpbd_step_kernel<256,resident>",
+                    "peak_source": f"{N_SM} SMs x {FP32_LANES} FP32 lanes x 2 x {clock_mhz:.0f} MHz "
+                                   f"(max SM clock, {peak_src})",
+                    "algorithmic_flops_per_launch": flops,
+                    "hbm": {"achieved_gbs": hbm_bytes / (ms_kernel / 1e3) / 1e9,
+                            "peak_gbs": float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])),
+                            "algorithmic_bytes_per_launch": hbm_bytes, "peak_source": peak_src}}
+        roofline["hbm"]["frac"] = roofline["hbm"]["achieved_gbs"] / roofline["hbm"]["peak_gbs"]
+
+        # Accuracy and CPU baseline: the FP64 oracle advances two sampled envs
+        # for a bounded number of steps on one host thread; the GPU replays the
+        # same envs from the same reset and the positions are compared.
+        cpu = None
+        acc = None
+        if world == 1 and not args.no_cpu_baseline:
+            sample_envs = (0, n_env - 1)
+            rate, n_steps, dt, oes, om = oracle_rate(mesh, params, args.cpu_seconds, seed, envs=sample_envs,
+                                                     max_steps=max(args.steps, 50))
+            sim.reset(seed)
+            for _ in range(n_steps):
+                sim.step_into(None, None, None, None)
+            x, _, _ = sim.get_state()
+            x = x.cpu().numpy().astype(np.float64)
+            errs = []
+            for e, oe in zip(sample_envs, oes):
+                ox, _, _ = oe.state()
+                errs.append(float(np.max(np.abs(x[e * V:(e + 1) * V] - ox)) / om.extent))
+            acc = {"max_pos_err_over_extent": max(errs), "tolerance": POS_TOL, "envs": list(sample_envs),
+                   "steps": n_steps, "within_tolerance": max(errs) <= POS_TOL}
+            cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"envs {list(sample_envs)} x {n_steps} steps of the {V}-vertex block, "
+                             f"FP64 oracle, 1 host thread, {dt:.1f} s"}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": args.workload, "n_env_per_gpu": n_env, "verts_per_env": V,
+                           "edges_per_env": E, "tets_per_env": T, "substeps": params["substeps"],
+                           "iterations": params["iterations"], "actions": "device counter-based draws",
+                           "l2": f"state {2 * 12 * V * n_env / 1e6:.0f} MB > 129 MB L2, no flush",
+                           "parallelism": f"env-sharded x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu, "accuracy": acc, "e2e": e2e,
+                "gpu_launches": args.steps, "clocks": clk}   # one step-kernel launch per step
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="block17x17x9_4096env_1000steps")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+/*
+ * ffsrl.h - C ABI of the GB300-native batched XPBD tissue simulator.
+ *
+ * The simulator advances many independent surgical-tissue environments at
+ * once with the method of FF-SRL (Dall'Alba et al., arXiv 2503.18616):
+ * extended position-based dynamics with substepping (Sec. III-A, Algorithm 1),
+ * edge-distance constraints (Eq. 1) and tet-volume constraints (Eqs. 2-3) in
+ * their compliance (XPBD) form, a kinematic tool that pushes tissue out of its
+ * signed-distance volume (Sec. III-A "Collisions"), and the reinforcement-
+ * learning interface of Sec. III-B: actions applied once per step, then
+ * observations, reward (Sec. IV) and termination flags. Every variable of every
+ * environment lives in one device array (Sec. III-B, last paragraph).
+ *
+ * Conventions for every entry point:
+ *   - Return value: FFSRL_OK (0) on success, a negative FFSRL_E_* code
+ *     otherwise; ffsrl_last_error() then gives a message (thread-local).
+ *   - Pointers named *_dev are device pointers (for example the data of a
+ *     torch CUDA tensor); they are read and written in stream order on the
+ *     stream given to ffsrl_create, and the library never frees them. Pointers
+ *     named *_host are ordinary host memory; calls taking them synchronise.
+ *   - ffsrl_create deep-copies every host input. The library owns all of its
+ *     device memory and frees it in ffsrl_destroy.
+ *   - Kernels run asynchronously: a device-side error (non-finite positions)
+ *     is reported by the next ffsrl_sync (FFSRL_E_NAN).
+ *   - There is no CPU fallback: without a usable CUDA device every call that
+ *     needs one returns FFSRL_E_CUDA.
+ *   - Layouts: "packed" vertex arrays hold env 0's vertices, then env 1's, and
+ *     so on ([total_verts][3], float32, metres); per-env arrays are
+ *     [n_env][...] in env order.
+ */
+#ifndef FFSRL_H
+#define FFSRL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FFSRL_OK 0
+#define FFSRL_E_INVAL (-1)      /* bad argument or mesh */
+#define FFSRL_E_CUDA (-2)       /* CUDA runtime error or no device */
+#define FFSRL_E_OOM (-3)        /* device or host allocation failed */
+#define FFSRL_E_DEGENERATE (-4) /* zero-volume tet or zero-length edge */
+#define FFSRL_E_NAN (-5)        /* non-finite state detected on the device */
+#define FFSRL_E_TIMEOUT (-6)    /* a bounded device wait gave up */
+
+typedef struct ffsrl_sim ffsrl_sim; /* opaque */
+
+/* One tet mesh in its rest state (Sec. III-A: V vertices with masses, tets).
+ * Edges (distance constraints) are every tet edge; rest lengths and rest
+ * volumes are computed from rest_pos before the loop (Eq. 1, Eq. 2). */
+typedef struct {
+    int32_t n_verts;         /* V, 1 .. 65535 */
+    int32_t n_tets;          /* T, >= 1 */
+    const double* rest_pos;  /* host [V][3], metres (rounded to float32 inside) */
+    const double* inv_mass;  /* host [V], 1/m; 0 pins the vertex */
+    const int32_t* tets;     /* host [T][4] vertex ids; a tet with negative
+                                rest volume gets its last two ids swapped */
+} ffsrl_mesh;
+
+/* Method and task parameters. Lengths in metres, times in seconds. */
+typedef struct {
+    double dt;                /* simulation step Delta t (Algorithm 1) */
+    int32_t substeps;         /* n substeps per step, h = dt / substeps (Sec. III-A) */
+    int32_t iterations;       /* constraint iterations per substep (>= 0) */
+    double gravity[3];        /* g of Algorithm 1 */
+    double compliance_dist;   /* XPBD compliance alpha of edge constraints */
+    double compliance_vol;    /* XPBD compliance alpha of volume constraints */
+    double tool_radius;       /* radius of the sphere tool proxy */
+    double action_scale;      /* tool displacement per step for a unit action */
+    double tool_margin_xy;    /* tool box: rest bbox grown by this in x and y, */
+    double tool_margin_below; /*   z from (top - below) ...                   */
+    double tool_margin_above; /*   ... to (top + above)                       */
+    double w_l, w_d, w_s;     /* reward weights of R = w_l l + w_d d + w_s s (Sec. IV) */
+    double success_dist;      /* s = 1 when l < success_dist (3 mm in Sec. IV) */
+    int32_t n_obs_verts;      /* sampled top-surface vertices in the observation */
+    int32_t max_steps;        /* done when the step count reaches this (0 = never) */
+    int32_t block_threads;    /* CUDA threads per environment; 0 = autotuned */
+    int32_t reserved[5];      /* must be zero */
+} ffsrl_params;
+
+/* Sizes of a created simulator. */
+typedef struct {
+    int32_t n_env;
+    int32_t n_meshes;
+    int32_t obs_dim;          /* 3 + 3 * n_obs_verts */
+    int32_t max_verts;        /* largest V over the meshes */
+    int64_t total_verts;      /* sum over envs of their mesh's V (packed rows) */
+    int32_t block_threads;    /* threads per environment in use */
+    int32_t resident_envs;    /* envs whose state stays in shared memory */
+} ffsrl_info;
+
+/* Creates n_env environments; env e uses meshes[env_mesh[e]] (env_mesh NULL:
+ * all use mesh 0) and the edge compliance env_compliance_dist[e] (NULL: the
+ * params value). Builds every mesh's constraint tables (edges, rest values,
+ * greedy first-fit colouring, colour-major order), allocates the device state
+ * on cuda_stream (a cudaStream_t; NULL = the legacy default stream) and resets
+ * every env with seed 0. On failure *out is NULL. */
+int ffsrl_create(const ffsrl_mesh* meshes, int32_t n_meshes, const int32_t* env_mesh,
+                 const double* env_compliance_dist, int32_t n_env, const ffsrl_params* params,
+                 void* cuda_stream, ffsrl_sim** out);
+
+/* Episode reset (Sec. III-B): for every env whose env_mask_dev[e] is nonzero
+ * (env_mask_dev NULL: all envs) the positions return to rest, velocities to
+ * zero, the tool to its start above the top face, the step count to zero, and
+ * the observed vertices and target vertex are drawn from (seed, env). */
+int ffsrl_reset(ffsrl_sim* sim, const uint8_t* env_mask_dev, uint64_t seed);
+
+/* One simulation step of every env (Algorithm 1 with the substep loop):
+ * tool update from actions_dev [n_env][3] in [-1, 1] (NULL: counter-based
+ * device draws from each env's reset seed), then `substeps` substeps of
+ * predict, coloured constraint projection, tool collision and velocity
+ * update, then obs_dev [n_env][obs_dim], reward_dev [n_env] and done_dev
+ * [n_env] (any of the three may be NULL). Asynchronous. */
+int ffsrl_step(ffsrl_sim* sim, const float* actions_dev, float* obs_dev, float* reward_dev,
+               uint8_t* done_dev);
+
+/* ffsrl_step with host buffers: copies actions_host in, runs the step, copies
+ * the outputs back and waits for them (pinned staging buffers owned by sim). */
+int ffsrl_step_host(ffsrl_sim* sim, const float* actions_host, float* obs_host,
+                    float* reward_host, uint8_t* done_host);
+
+/* Waits for the sim's stream; returns FFSRL_E_NAN if any env produced a
+ * non-finite position since the last call (and clears the flag). */
+int ffsrl_sync(ffsrl_sim* sim);
+
+int ffsrl_destroy(ffsrl_sim* sim);
+
+int ffsrl_get_info(const ffsrl_sim* sim, ffsrl_info* out);
+
+/* Thread-local message of the last failed call on this thread. */
+const char* ffsrl_last_error(void);
+
+/* --- state access (checkpoint / resume, tests) ----------------------------- */
+
+/* Packed state: x_dev, v_dev [total_verts][3]; tool_dev [n_env][3] float64.
+ * Any pointer may be NULL. get writes them, set reads them. */
+int ffsrl_get_state(ffsrl_sim* sim, float* x_dev, float* v_dev, double* tool_dev);
+int ffsrl_set_state(ffsrl_sim* sim, const float* x_dev, const float* v_dev, const double* tool_dev);
+
+/* Constraint tables of mesh `mesh` as built by ffsrl_create, copied to host.
+ * which: 0 oriented tets [T][4], 1 flipped [T], 2 edges [E][2] (min,max),
+ * 3 edge colour [E], 4 tet colour [T], 5 edge colour-major order [E],
+ * 6 tet colour-major order [T], 7 edge colour offsets [n_ecol+1],
+ * 8 tet colour offsets [n_tcol+1], 9 top-face vertices [n_top].
+ * With out_host NULL only *count is written (number of int32 values). */
+int ffsrl_get_mesh_table(const ffsrl_sim* sim, int32_t mesh, int32_t which, int32_t* out_host,
+                         int64_t* count);
+
+/* Per-env integers copied to host (waits for the stream): step count,
+ * target vertex, observed vertex ids [n_obs_verts], number of tool contacts
+ * in the last substep and their vertex ids in ascending order.
+ * contacts_host has room for the env's V entries; any pointer may be NULL. */
+int ffsrl_get_env_ints(ffsrl_sim* sim, int32_t env, int32_t* step_count, int32_t* target,
+                       int32_t* obs_ids_host, int32_t* n_contacts, int32_t* contacts_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFSRL_H */

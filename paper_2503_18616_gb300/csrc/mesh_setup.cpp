@@ -1,0 +1,166 @@
+// Host-side constraint-table construction (see mesh_setup.h).
+#include "mesh_setup.h"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+
+#include "../../include/ffsrl.h"
+
+namespace ffsrl {
+namespace {
+
+constexpr int kColourWords = 4;  // up to 256 colours per constraint family
+
+// Signed volume of the tet (x_b - x_a) x (x_c - x_a) . (x_d - x_a) / 6
+// (the C^v of Sec. III-A at rest), evaluated in double from float positions.
+double signed_volume(const std::vector<float>& p, int a, int b, int c, int d) {
+    double ba[3], ca[3], da[3];
+    for (int k = 0; k < 3; ++k) {
+        ba[k] = double(p[3 * b + k]) - double(p[3 * a + k]);
+        ca[k] = double(p[3 * c + k]) - double(p[3 * a + k]);
+        da[k] = double(p[3 * d + k]) - double(p[3 * a + k]);
+    }
+    const double nx = ba[1] * ca[2] - ba[2] * ca[1];
+    const double ny = ba[2] * ca[0] - ba[0] * ca[2];
+    const double nz = ba[0] * ca[1] - ba[1] * ca[0];
+    return (nx * da[0] + ny * da[1] + nz * da[2]) / 6.0;
+}
+
+// Greedy first-fit colouring: constraints are visited in index order and each
+// takes the lowest colour that none of its vertices already carries. A
+// per-vertex bitset records the colours present at that vertex.
+template <int ARITY>
+int colour_first_fit(int n, const int32_t* verts, int V, std::vector<int32_t>& colour,
+                     int& n_colours) {
+    std::vector<std::array<uint64_t, kColourWords>> present(V);
+    for (auto& b : present) b.fill(0);
+    colour.assign(n, 0);
+    n_colours = 0;
+    for (int i = 0; i < n; ++i) {
+        std::array<uint64_t, kColourWords> taken{};
+        for (int k = 0; k < ARITY; ++k) {
+            const auto& b = present[verts[ARITY * i + k]];
+            for (int w = 0; w < kColourWords; ++w) taken[w] |= b[w];
+        }
+        int c = -1;
+        for (int w = 0; w < kColourWords && c < 0; ++w)
+            if (~taken[w]) c = 64 * w + __builtin_ctzll(~taken[w]);
+        if (c < 0) return FFSRL_E_INVAL;
+        colour[i] = c;
+        for (int k = 0; k < ARITY; ++k)
+            present[verts[ARITY * i + k]][c >> 6] |= (uint64_t(1) << (c & 63));
+        n_colours = std::max(n_colours, c + 1);
+    }
+    return FFSRL_OK;
+}
+
+// Stable counting sort of constraint ids by colour.
+void colour_major(const std::vector<int32_t>& colour, int n_colours, std::vector<int32_t>& order,
+                  std::vector<int32_t>& offsets) {
+    offsets.assign(n_colours + 1, 0);
+    for (int32_t c : colour) ++offsets[c + 1];
+    for (int c = 0; c < n_colours; ++c) offsets[c + 1] += offsets[c];
+    std::vector<int32_t> next(offsets.begin(), offsets.end() - 1);
+    order.assign(colour.size(), 0);
+    for (size_t i = 0; i < colour.size(); ++i) order[next[colour[i]]++] = int32_t(i);
+}
+
+}  // namespace
+
+int build_host_mesh(int V, int T, const double* rest, const double* inv_mass,
+                    const int32_t* tets, HostMesh& m, std::string& err) {
+    if (V < 1 || V > 65535) { err = "n_verts must be in [1, 65535]"; return FFSRL_E_INVAL; }
+    if (T < 1) { err = "n_tets must be >= 1"; return FFSRL_E_INVAL; }
+    if (!rest || !inv_mass || !tets) { err = "mesh arrays must be non-NULL"; return FFSRL_E_INVAL; }
+    m = HostMesh();
+    m.V = V;
+    m.T = T;
+    m.rest.resize(3 * size_t(V));
+    m.inv_mass.resize(V);
+    for (int i = 0; i < 3 * V; ++i) {
+        if (!std::isfinite(rest[i])) { err = "non-finite rest position"; return FFSRL_E_INVAL; }
+        m.rest[i] = float(rest[i]);
+    }
+    for (int i = 0; i < V; ++i) {
+        if (!(inv_mass[i] >= 0.0) || !std::isfinite(inv_mass[i])) {
+            err = "inverse mass must be finite and >= 0";
+            return FFSRL_E_INVAL;
+        }
+        m.inv_mass[i] = float(inv_mass[i]);
+    }
+    for (int k = 0; k < 3; ++k) m.bbmin[k] = m.bbmax[k] = m.rest[k];
+    for (int i = 0; i < V; ++i)
+        for (int k = 0; k < 3; ++k) {
+            m.bbmin[k] = std::min(m.bbmin[k], double(m.rest[3 * i + k]));
+            m.bbmax[k] = std::max(m.bbmax[k], double(m.rest[3 * i + k]));
+        }
+    m.extent = std::max({m.bbmax[0] - m.bbmin[0], m.bbmax[1] - m.bbmin[1], m.bbmax[2] - m.bbmin[2]});
+    const double min_vol = 1e-12 * m.extent * m.extent * m.extent;
+
+    // Orientation and rest volume (Eq. 2's V0).
+    m.tet.resize(4 * size_t(T));
+    m.flipped.assign(T, 0);
+    m.V0.resize(T);
+    for (int t = 0; t < T; ++t) {
+        int32_t q[4];
+        for (int k = 0; k < 4; ++k) {
+            q[k] = tets[4 * t + k];
+            if (q[k] < 0 || q[k] >= V) { err = "tet vertex id out of range"; return FFSRL_E_INVAL; }
+        }
+        for (int a = 0; a < 4; ++a)
+            for (int b = a + 1; b < 4; ++b)
+                if (q[a] == q[b]) { err = "tet with a repeated vertex"; return FFSRL_E_INVAL; }
+        double vol = signed_volume(m.rest, q[0], q[1], q[2], q[3]);
+        if (vol < 0) {
+            std::swap(q[2], q[3]);
+            m.flipped[t] = 1;
+            vol = signed_volume(m.rest, q[0], q[1], q[2], q[3]);
+        }
+        if (!(vol > min_vol)) { err = "degenerate (zero-volume) tet"; return FFSRL_E_DEGENERATE; }
+        for (int k = 0; k < 4; ++k) m.tet[4 * t + k] = q[k];
+        m.V0[t] = float(vol);
+    }
+
+    // Edges: the six vertex pairs of each tet as (min << 32 | max), sorted, unique.
+    std::vector<uint64_t> keys;
+    keys.reserve(6 * size_t(T));
+    for (int t = 0; t < T; ++t)
+        for (int a = 0; a < 4; ++a)
+            for (int b = a + 1; b < 4; ++b) {
+                uint64_t lo = uint64_t(std::min(m.tet[4 * t + a], m.tet[4 * t + b]));
+                uint64_t hi = uint64_t(std::max(m.tet[4 * t + a], m.tet[4 * t + b]));
+                keys.push_back((lo << 32) | hi);
+            }
+    std::sort(keys.begin(), keys.end());
+    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+    m.E = int(keys.size());
+    m.edge.resize(2 * size_t(m.E));
+    m.rest_len.resize(m.E);
+    for (int e = 0; e < m.E; ++e) {
+        const int a = int(keys[e] >> 32), b = int(keys[e] & 0xffffffffu);
+        m.edge[2 * e] = a;
+        m.edge[2 * e + 1] = b;
+        double s = 0;
+        for (int k = 0; k < 3; ++k) {
+            const double dk = double(m.rest[3 * a + k]) - double(m.rest[3 * b + k]);
+            s += dk * dk;
+        }
+        const double len = std::sqrt(s);
+        if (!(len > 0)) { err = "zero-length edge"; return FFSRL_E_DEGENERATE; }
+        m.rest_len[e] = float(len);
+    }
+
+    // Colouring: edges in ascending order, tets in input order, separately.
+    int rc = colour_first_fit<2>(m.E, m.edge.data(), V, m.ecolor, m.n_ecol);
+    if (rc == FFSRL_OK) rc = colour_first_fit<4>(m.T, m.tet.data(), V, m.tcolor, m.n_tcol);
+    if (rc != FFSRL_OK) { err = "more than 256 colours needed"; return rc; }
+    colour_major(m.ecolor, m.n_ecol, m.eorder, m.ecol_off);
+    colour_major(m.tcolor, m.n_tcol, m.torder, m.tcol_off);
+
+    for (int i = 0; i < V; ++i)
+        if (double(m.rest[3 * i + 2]) == m.bbmax[2]) m.top.push_back(i);
+    return FFSRL_OK;
+}
+
+}  // namespace ffsrl

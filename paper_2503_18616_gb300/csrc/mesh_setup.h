@@ -1,0 +1,38 @@
+// Host-side constraint-table construction for the XPBD simulator.
+//
+// Everything the paper computes "before the simulation loop" (FF-SRL,
+// arXiv 2503.18616, Sec. III-A): edge list and rest distances d_ab (Eq. 1),
+// oriented tets and rest volumes V0 (Eq. 2), plus the graph colouring that
+// lets constraints of one colour be projected in parallel, the colour-major
+// constraint order, and the top-face vertex list used for observations.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace ffsrl {
+
+struct HostMesh {
+    int V = 0, T = 0, E = 0;
+    std::vector<float> rest;        // [V*3], float32 rest positions
+    std::vector<float> inv_mass;    // [V]
+    std::vector<int32_t> tet;       // [T*4] oriented (positive rest volume)
+    std::vector<int32_t> flipped;   // [T]
+    std::vector<float> V0;          // [T]
+    std::vector<int32_t> edge;      // [E*2], (min, max), ascending
+    std::vector<float> rest_len;    // [E]
+    int n_ecol = 0, n_tcol = 0;
+    std::vector<int32_t> ecolor, tcolor;      // per constraint
+    std::vector<int32_t> eorder, torder;      // colour-major position -> constraint
+    std::vector<int32_t> ecol_off, tcol_off;  // [n_col + 1]
+    std::vector<int32_t> top;                 // ascending ids with z == max z
+    double bbmin[3] = {0, 0, 0}, bbmax[3] = {0, 0, 0};
+    double extent = 0;
+};
+
+// Returns 0 or a negative FFSRL_E_* code with a message in err.
+int build_host_mesh(int V, int T, const double* rest, const double* inv_mass,
+                    const int32_t* tets, HostMesh& out, std::string& err);
+
+}  // namespace ffsrl

@@ -1,0 +1,94 @@
+// Device-side data layout of the batched XPBD simulator (sm_103a).
+//
+// HBM layout (one allocation per array, all envs concatenated, Sec. III-B of
+// FF-SRL, arXiv 2503.18616):
+//   positions / velocities: structure of arrays, x[k * stride + voff_e + i] for
+//     component k, env e, vertex i; voff_e is a multiple of 32 vertices so every
+//     env starts on a 128-byte boundary.
+//   constraint tables: per distinct mesh, in colour-major order, vertex ids
+//     packed as 16-bit pairs (edges: a | b << 16; tets: (a | b << 16, c | d << 16)).
+//   per-env scalars: tool centre (float64), last distance, step count, seed,
+//     target vertex, observed vertex ids, contact list, error flags.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ffsrl {
+
+constexpr int kMaxColours = 256;
+
+struct MeshDev {
+    int V, Vp, E, T;
+    int n_ecol, n_tcol, n_top, pad0;
+    const uint32_t* edge_ab;  // [E] colour-major
+    const float* edge_d;      // [E] rest lengths
+    const uint2* tet_abcd;    // [T] colour-major
+    const float* tet_V0;      // [T] rest volumes
+    const int* ecol_off;      // [n_ecol + 1]
+    const int* tcol_off;      // [n_tcol + 1]
+    const float4* rest_w;     // [V] rest position and inverse mass
+    const int* top;           // [n_top] top-face vertex ids
+    double box_lo[3], box_hi[3], tool_start[3];
+    float min_len;            // edges shorter than this are skipped
+    int pad1;
+};
+
+struct EnvDev {
+    int mesh;       // index into the mesh table
+    int voff;       // first padded vertex row of this env
+    float alpha_d;  // edge compliance / h^2 (alpha tilde of XPBD)
+    int loff;       // first lambda slot of this env (iterations > 1)
+};
+
+struct SimDev {
+    const MeshDev* meshes;
+    const EnvDev* envs;
+    int n_env;
+    int obs_dim;
+    long long stride;         // padded vertex rows over all envs
+    float* x;                 // [3][stride]
+    float* v;                 // [3][stride]
+    double* tool;             // [n_env][3]
+    float* l_prev;            // [n_env]
+    int* t_step;              // [n_env]
+    unsigned long long* seed; // [n_env]
+    int* obs_ids;             // [n_env][n_obs]
+    int* target;              // [n_env]
+    int* n_contacts;          // [n_env]
+    int* contacts;            // [stride]: env e's list at voff_e
+    int* err;                 // [n_env] bit 0: non-finite position
+    float* lambda;            // multipliers carried across iterations (iterations > 1)
+    float4* xg;               // [stride] working positions of envs not resident in SMEM
+    float* pg;                // [3][stride] substep-start positions of those envs
+    float h, gx, gy, gz;
+    float alpha_v;            // volume compliance / h^2
+    float radius;
+    double action_scale;
+    int substeps, iterations, n_obs, max_steps;
+    double w_l, w_d, w_s, success_dist;
+};
+
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): the n-th output of the
+// generator started at `state` is the output mix of state + (n + 1) * gamma.
+__host__ __device__ __forceinline__ unsigned long long splitmix64_nth(unsigned long long state,
+                                                                      unsigned long long n) {
+    unsigned long long z = state + (n + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Stream of env `env` for draw family `family` (0 actions, 1 observed vertices, 2 target).
+__host__ __device__ __forceinline__ unsigned long long env_stream(unsigned long long seed,
+                                                                  unsigned long long env,
+                                                                  unsigned family) {
+    return splitmix64_nth(seed, 4ull * env + family);
+}
+
+// Top 24 bits as a number in [-1, 1): exact in float32 and float64.
+__host__ __device__ __forceinline__ double to_unit_pm1(unsigned long long r) {
+    return 2.0 * (double)(r >> 40) * (1.0 / 16777216.0) - 1.0;
+}
+
+}  // namespace ffsrl

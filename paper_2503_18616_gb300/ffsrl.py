@@ -1,0 +1,259 @@
+"""Thin Python binding of libffsrl.so (include/ffsrl.h).
+
+Argument marshalling only: every step of the simulation runs in the library's
+CUDA kernels. PyTorch provides device memory (the tensors whose data pointers
+are passed through the C ABI) and the CUDA stream. There is no fallback: if the
+compiled library is missing this module raises instead of computing anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libffsrl.so")
+_lib = None
+
+FFSRL_OK = 0
+ERRORS = {-1: "FFSRL_E_INVAL", -2: "FFSRL_E_CUDA", -3: "FFSRL_E_OOM", -4: "FFSRL_E_DEGENERATE",
+          -5: "FFSRL_E_NAN", -6: "FFSRL_E_TIMEOUT"}
+
+# ffsrl_get_mesh_table selectors
+TABLES = {"tets": 0, "flipped": 1, "edges": 2, "ecolor": 3, "tcolor": 4, "eorder": 5,
+          "torder": 6, "ecol_off": 7, "tcol_off": 8, "top": 9}
+
+# every symbol include/ffsrl.h declares
+EXPORTS = ["ffsrl_create", "ffsrl_reset", "ffsrl_step", "ffsrl_step_host", "ffsrl_sync",
+           "ffsrl_destroy", "ffsrl_get_info", "ffsrl_last_error", "ffsrl_get_state",
+           "ffsrl_set_state", "ffsrl_get_mesh_table", "ffsrl_get_env_ints"]
+
+
+class FfsrlError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class ffsrl_mesh(ctypes.Structure):
+    _fields_ = [("n_verts", ctypes.c_int32), ("n_tets", ctypes.c_int32),
+                ("rest_pos", ctypes.c_void_p), ("inv_mass", ctypes.c_void_p),
+                ("tets", ctypes.c_void_p)]
+
+
+class ffsrl_params(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("substeps", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("gravity", ctypes.c_double * 3), ("compliance_dist", ctypes.c_double),
+                ("compliance_vol", ctypes.c_double), ("tool_radius", ctypes.c_double),
+                ("action_scale", ctypes.c_double), ("tool_margin_xy", ctypes.c_double),
+                ("tool_margin_below", ctypes.c_double), ("tool_margin_above", ctypes.c_double),
+                ("w_l", ctypes.c_double), ("w_d", ctypes.c_double), ("w_s", ctypes.c_double),
+                ("success_dist", ctypes.c_double), ("n_obs_verts", ctypes.c_int32),
+                ("max_steps", ctypes.c_int32), ("block_threads", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class ffsrl_info(ctypes.Structure):
+    _fields_ = [("n_env", ctypes.c_int32), ("n_meshes", ctypes.c_int32), ("obs_dim", ctypes.c_int32),
+                ("max_verts", ctypes.c_int32), ("total_verts", ctypes.c_int64),
+                ("block_threads", ctypes.c_int32), ("resident_envs", ctypes.c_int32)]
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libffsrl.so and declares its signatures; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it first (python -m paper_2503_18616_gb300.build); "
+                           "there is no CPU fallback")
+    L = ctypes.CDLL(path)
+    P, I32, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64
+    L.ffsrl_create.restype = ctypes.c_int
+    L.ffsrl_create.argtypes = [P, I32, P, P, I32, P, P, ctypes.POINTER(P)]
+    L.ffsrl_reset.restype = ctypes.c_int
+    L.ffsrl_reset.argtypes = [P, P, U64]
+    L.ffsrl_step.restype = ctypes.c_int
+    L.ffsrl_step.argtypes = [P, P, P, P, P]
+    L.ffsrl_step_host.restype = ctypes.c_int
+    L.ffsrl_step_host.argtypes = [P, P, P, P, P]
+    L.ffsrl_sync.restype = ctypes.c_int
+    L.ffsrl_sync.argtypes = [P]
+    L.ffsrl_destroy.restype = ctypes.c_int
+    L.ffsrl_destroy.argtypes = [P]
+    L.ffsrl_get_info.restype = ctypes.c_int
+    L.ffsrl_get_info.argtypes = [P, P]
+    L.ffsrl_last_error.restype = ctypes.c_char_p
+    L.ffsrl_last_error.argtypes = []
+    L.ffsrl_get_state.restype = ctypes.c_int
+    L.ffsrl_get_state.argtypes = [P, P, P, P]
+    L.ffsrl_set_state.restype = ctypes.c_int
+    L.ffsrl_set_state.argtypes = [P, P, P, P]
+    L.ffsrl_get_mesh_table.restype = ctypes.c_int
+    L.ffsrl_get_mesh_table.argtypes = [P, I32, I32, P, ctypes.POINTER(ctypes.c_int64)]
+    L.ffsrl_get_env_ints.restype = ctypes.c_int
+    L.ffsrl_get_env_ints.argtypes = [P, I32, P, P, P, P, P]
+    _lib = L
+    return L
+
+
+def _check(rc: int) -> None:
+    if rc != FFSRL_OK:
+        raise FfsrlError(rc, load_library().ffsrl_last_error().decode())
+
+
+def _np_ptr(a: np.ndarray) -> ctypes.c_void_p:
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _dptr(t) -> ctypes.c_void_p | None:
+    """Device pointer of a contiguous CUDA tensor (None passes NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_params(d: dict, block_threads: int = 0) -> ffsrl_params:
+    p = ffsrl_params()
+    p.dt = d["dt"]
+    p.substeps = d["substeps"]
+    p.iterations = d["iterations"]
+    p.gravity[:] = [float(g) for g in d["gravity"]]
+    p.compliance_dist = d["alpha_d"]
+    p.compliance_vol = d["alpha_v"]
+    p.tool_radius = d["radius"]
+    p.action_scale = d["action_scale"]
+    p.tool_margin_xy = d["margin_xy"]
+    p.tool_margin_below = d["margin_below"]
+    p.tool_margin_above = d["margin_above"]
+    p.w_l, p.w_d, p.w_s = d["w_l"], d["w_d"], d["w_s"]
+    p.success_dist = d["success_dist"]
+    p.n_obs_verts = d["n_obs"]
+    p.max_steps = d["max_steps"]
+    p.block_threads = block_threads
+    return p
+
+
+class Sim:
+    """Batched simulator handle (one ffsrl_sim)."""
+
+    def __init__(self, meshes, params: dict, n_env: int, env_mesh=None, env_compliance=None,
+                 stream=None, block_threads: int = 0):
+        import torch
+
+        self._torch = torch
+        L = load_library()
+        self._L = L
+        self.params = dict(params)
+        self._keep = []
+        arr = (ffsrl_mesh * len(meshes))()
+        for i, (rest, inv_mass, tets) in enumerate(meshes):
+            r = np.ascontiguousarray(rest, dtype=np.float64).reshape(-1, 3)
+            w = np.ascontiguousarray(inv_mass, dtype=np.float64).reshape(-1)
+            t = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+            self._keep += [r, w, t]
+            arr[i].n_verts, arr[i].n_tets = len(r), len(t)
+            arr[i].rest_pos, arr[i].inv_mass, arr[i].tets = r.ctypes.data, w.ctypes.data, t.ctypes.data
+        em = None
+        if env_mesh is not None:
+            em = np.ascontiguousarray(env_mesh, dtype=np.int32)
+            self._keep.append(em)
+        ec = None
+        if env_compliance is not None:
+            ec = np.ascontiguousarray(env_compliance, dtype=np.float64)
+            self._keep.append(ec)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        p = make_params(params, block_threads)
+        h = ctypes.c_void_p()
+        _check(L.ffsrl_create(arr, len(meshes), _np_ptr(em) if em is not None else None,
+                              _np_ptr(ec) if ec is not None else None, n_env, ctypes.byref(p),
+                              ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self._h = h
+        info = ffsrl_info()
+        _check(L.ffsrl_get_info(self._h, ctypes.byref(info)))
+        self.n_env = info.n_env
+        self.obs_dim = info.obs_dim
+        self.total_verts = info.total_verts
+        self.block_threads = info.block_threads
+        self.resident_envs = info.resident_envs
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _check(self._L.ffsrl_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- hot path ----------------------------------------------------------
+    def reset(self, seed: int = 0, mask=None) -> None:
+        _check(self._L.ffsrl_reset(self._h, _dptr(mask), int(seed)))
+
+    def step(self, actions=None, obs=None, reward=None, done=None):
+        """One step; allocates missing outputs. Returns (obs, reward, done)."""
+        torch = self._torch
+        if obs is None:
+            obs = torch.empty((self.n_env, self.obs_dim), dtype=torch.float32, device=self.device)
+        if reward is None:
+            reward = torch.empty(self.n_env, dtype=torch.float32, device=self.device)
+        if done is None:
+            done = torch.empty(self.n_env, dtype=torch.uint8, device=self.device)
+        _check(self._L.ffsrl_step(self._h, _dptr(actions), _dptr(obs), _dptr(reward), _dptr(done)))
+        return obs, reward, done
+
+    def step_into(self, actions, obs, reward, done) -> None:
+        """ffsrl_step on preallocated tensors (any may be None)."""
+        _check(self._L.ffsrl_step(self._h, _dptr(actions), _dptr(obs), _dptr(reward), _dptr(done)))
+
+    def step_host(self, actions=None, obs=None, reward=None, done=None):
+        """ffsrl_step_host on numpy buffers (allocated when missing)."""
+        if obs is None:
+            obs = np.empty((self.n_env, self.obs_dim), dtype=np.float32)
+        if reward is None:
+            reward = np.empty(self.n_env, dtype=np.float32)
+        if done is None:
+            done = np.empty(self.n_env, dtype=np.uint8)
+        a = None
+        if actions is not None:
+            a = np.ascontiguousarray(actions, dtype=np.float32).reshape(self.n_env, 3)
+        _check(self._L.ffsrl_step_host(self._h, _np_ptr(a) if a is not None else None, _np_ptr(obs),
+                                       _np_ptr(reward), _np_ptr(done)))
+        return obs, reward, done
+
+    def sync(self) -> None:
+        _check(self._L.ffsrl_sync(self._h))
+
+    # -- state access ---------------------------------------------------------
+    def get_state(self):
+        torch = self._torch
+        x = torch.empty((self.total_verts, 3), dtype=torch.float32, device=self.device)
+        v = torch.empty_like(x)
+        tool = torch.empty((self.n_env, 3), dtype=torch.float64, device=self.device)
+        _check(self._L.ffsrl_get_state(self._h, _dptr(x), _dptr(v), _dptr(tool)))
+        return x, v, tool
+
+    def set_state(self, x=None, v=None, tool=None) -> None:
+        _check(self._L.ffsrl_set_state(self._h, _dptr(x), _dptr(v), _dptr(tool)))
+
+    def mesh_table(self, name: str, mesh: int = 0) -> np.ndarray:
+        n = ctypes.c_int64(0)
+        _check(self._L.ffsrl_get_mesh_table(self._h, mesh, TABLES[name], None, ctypes.byref(n)))
+        out = np.zeros(max(n.value, 1), dtype=np.int32)
+        _check(self._L.ffsrl_get_mesh_table(self._h, mesh, TABLES[name], _np_ptr(out), ctypes.byref(n)))
+        return out[:n.value].copy()
+
+    def env_ints(self, env: int, max_verts: int | None = None) -> dict:
+        t = np.zeros(1, np.int32); tgt = np.zeros(1, np.int32); nc = np.zeros(1, np.int32)
+        ids = np.zeros(max(self.params["n_obs"], 1), np.int32)
+        cont = np.zeros(max_verts or 65536, np.int32)
+        _check(self._L.ffsrl_get_env_ints(self._h, env, _np_ptr(t), _np_ptr(tgt), _np_ptr(ids),
+                                          _np_ptr(nc), _np_ptr(cont)))
+        return {"t": int(t[0]), "target": int(tgt[0]), "obs_ids": ids[:self.params["n_obs"]].copy(),
+                "contacts": cont[:int(nc[0])].copy()}
