@@ -208,6 +208,33 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_e2e(args, sim, n_env, world, rank, seed, barrier, dist):
+    import numpy as np
+    import torch
+    from paper_2503_18616_gb300 import inputs
+    pool = inputs.random_actions(8, n_env, 11 + rank).astype(np.float32)   # a fresh action array per step
+
+    h_obs = np.empty((n_env, sim.obs_dim), np.float32)
+    h_rew = np.empty(n_env, np.float32)
+    h_done = np.empty(n_env, np.uint8)
+    sim.reset(seed)
+    for k in range(args.warmup):
+        sim.step_host(pool[k % len(pool)], h_obs, h_rew, h_done)
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        sim.step_host(pool[k % len(pool)], h_obs, h_rew, h_done)
+    t_e2e = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    return {"value": world * n_env * args.steps / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": int(pool[0].nbytes),
+           "d2h_bytes_per_step": int(h_obs.nbytes + h_rew.nbytes + h_done.nbytes)}
+
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -228,7 +255,7 @@ def run_ours(args):
         __graft_entry__.build()
 
     w, mesh, params = workload(args.workload)
-    n_env = w["n_env"]
+    n_env = args.envs or w["n_env"]
     sim = ffsrl.Sim([mesh], params, n_env)
     seed = args.seed + 1000003 * rank          # each rank owns its own env shard
     sim.reset(seed)
@@ -271,25 +298,9 @@ def run_ours(args):
 
     # End to end through the public host-buffer call: actions copied in,
     # observation, reward and done copied out, every step.
-    acts = inputs.random_actions(1, n_env, 11 + rank)[0].astype(np.float32)
-    h_obs = np.empty((n_env, sim.obs_dim), np.float32)
-    h_rew = np.empty(n_env, np.float32)
-    h_done = np.empty(n_env, np.uint8)
-    sim.reset(seed)
-    for _ in range(args.warmup):
-        sim.step_host(acts, h_obs, h_rew, h_done)
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        sim.step_host(acts, h_obs, h_rew, h_done)
-    t_e2e = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e = {"value": world * n_env * args.steps / t_e2e, "unit": UNIT,
-           "h2d_bytes_per_step": int(acts.nbytes),
-           "d2h_bytes_per_step": int(h_obs.nbytes + h_rew.nbytes + h_done.nbytes)}
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, sim, n_env, world, rank, seed, barrier, dist)
 
     line = None
     if rank == 0:
@@ -365,6 +376,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--envs", type=int, default=0, help="override the workload's env count")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

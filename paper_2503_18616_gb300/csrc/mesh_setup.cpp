@@ -13,8 +13,9 @@ namespace {
 constexpr int kColourWords = 4;  // up to 256 colours per constraint family
 
 // Signed volume of the tet (x_b - x_a) x (x_c - x_a) . (x_d - x_a) / 6
-// (the C^v of Sec. III-A at rest), evaluated in double from float positions.
-double signed_volume(const std::vector<float>& p, int a, int b, int c, int d) {
+// (the C^v of Sec. III-A at rest), evaluated in double.
+template <class Real>
+double signed_volume(const Real* p, int a, int b, int c, int d) {
     double ba[3], ca[3], da[3];
     for (int k = 0; k < 3; ++k) {
         ba[k] = double(p[3 * b + k]) - double(p[3 * a + k]);
@@ -89,11 +90,14 @@ int build_host_mesh(int V, int T, const double* rest, const double* inv_mass,
         }
         m.inv_mass[i] = float(inv_mass[i]);
     }
-    for (int k = 0; k < 3; ++k) m.bbmin[k] = m.bbmax[k] = m.rest[k];
+    // Bounding box, extent and top face come from the positions as given
+    // (float64), so the tool box and the observed surface do not depend on
+    // the float32 rounding of the state.
+    for (int k = 0; k < 3; ++k) m.bbmin[k] = m.bbmax[k] = rest[k];
     for (int i = 0; i < V; ++i)
         for (int k = 0; k < 3; ++k) {
-            m.bbmin[k] = std::min(m.bbmin[k], double(m.rest[3 * i + k]));
-            m.bbmax[k] = std::max(m.bbmax[k], double(m.rest[3 * i + k]));
+            m.bbmin[k] = std::min(m.bbmin[k], rest[3 * i + k]);
+            m.bbmax[k] = std::max(m.bbmax[k], rest[3 * i + k]);
         }
     m.extent = std::max({m.bbmax[0] - m.bbmin[0], m.bbmax[1] - m.bbmin[1], m.bbmax[2] - m.bbmin[2]});
     const double min_vol = 1e-12 * m.extent * m.extent * m.extent;
@@ -111,15 +115,17 @@ int build_host_mesh(int V, int T, const double* rest, const double* inv_mass,
         for (int a = 0; a < 4; ++a)
             for (int b = a + 1; b < 4; ++b)
                 if (q[a] == q[b]) { err = "tet with a repeated vertex"; return FFSRL_E_INVAL; }
-        double vol = signed_volume(m.rest, q[0], q[1], q[2], q[3]);
+        // orientation and degeneracy from the positions as given
+        double vol = signed_volume(rest, q[0], q[1], q[2], q[3]);
         if (vol < 0) {
             std::swap(q[2], q[3]);
             m.flipped[t] = 1;
-            vol = signed_volume(m.rest, q[0], q[1], q[2], q[3]);
+            vol = signed_volume(rest, q[0], q[1], q[2], q[3]);
         }
         if (!(vol > min_vol)) { err = "degenerate (zero-volume) tet"; return FFSRL_E_DEGENERATE; }
         for (int k = 0; k < 4; ++k) m.tet[4 * t + k] = q[k];
-        m.V0[t] = float(vol);
+        // rest volume of the float32 state, so C = 0 at rest up to float rounding
+        m.V0[t] = float(signed_volume(m.rest.data(), q[0], q[1], q[2], q[3]));
     }
 
     // Edges: the six vertex pairs of each tet as (min << 32 | max), sorted, unique.
@@ -159,7 +165,7 @@ int build_host_mesh(int V, int T, const double* rest, const double* inv_mass,
     colour_major(m.tcolor, m.n_tcol, m.torder, m.tcol_off);
 
     for (int i = 0; i < V; ++i)
-        if (double(m.rest[3 * i + 2]) == m.bbmax[2]) m.top.push_back(i);
+        if (rest[3 * i + 2] == m.bbmax[2]) m.top.push_back(i);
     return FFSRL_OK;
 }
 

@@ -135,7 +135,9 @@ __global__ void __launch_bounds__(BLOCK) xpbd_step_kernel(SimDev S, const int* _
         const unsigned long long st = env_stream(S.seed[env], (unsigned long long)env, 0u);
         for (int k = 0; k < 3; ++k) {
             const double a = actions ? (double)actions[3 * env + k] : to_unit_pm1(splitmix64_nth(st, 3ull * t + k));
-            double c = S.tool[3 * env + k] + S.action_scale * a;
+            // rounded product, then rounded sum (no fused multiply-add), so the
+            // float64 tool position is reproducible bit for bit
+            double c = __dadd_rn(S.tool[3 * env + k], __dmul_rn(S.action_scale, a));
             c = c < M.box_lo[k] ? M.box_lo[k] : c;
             c = c > M.box_hi[k] ? M.box_hi[k] : c;
             S.tool[3 * env + k] = c;
@@ -405,12 +407,15 @@ __global__ void unpack_state_kernel(SimDev S, const int* __restrict__ pstart, co
 template <int BLOCK, bool RES>
 static cudaError_t launch_one(const SimDev& S, const int* env_list, int n_blocks, size_t smem,
                               cudaStream_t st, const float* actions, float* obs, float* reward, uint8_t* done) {
-    static bool configured = false;
-    if (!configured) {
+    // Raise the kernel's dynamic shared-memory limit to what this launch needs
+    // (the limit plus the kernel's static shared memory must stay within the
+    // device's per-block opt-in maximum).
+    static size_t configured = 48 * 1024;
+    if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(xpbd_step_kernel<BLOCK, RES>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
-        configured = true;
+        configured = smem;
     }
     xpbd_step_kernel<BLOCK, RES><<<n_blocks, BLOCK, smem, st>>>(S, env_list, actions, obs, reward, done);
     return cudaGetLastError();

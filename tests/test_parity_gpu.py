@@ -129,7 +129,13 @@ def test_block9x9x5_one_env_100_steps(block):
 
 @pytest.mark.parametrize("mesh", ["two_tet", (2, 2, 2), (3, 2, 2), (3, 3, 2), (3, 3, 3), (5, 3, 2), (9, 9, 5)])
 def test_small_and_ragged_meshes(mesh):
-    m = inputs.two_tet_mesh() if mesh == "two_tet" else grid(mesh)
+    if mesh == "two_tet":
+        rest, w, tets = inputs.two_tet_mesh()
+        w = w.copy()
+        w[0] = 0.0      # hang the pair of tets from one vertex so it stays near its extent
+        m = (rest, w, tets)
+    else:
+        m = grid(mesh)
     n_obs = 2 if mesh == "two_tet" else 4
     p = P(n_obs=n_obs, radius=3e-3)
     n_env, steps = 3, 6
@@ -160,7 +166,10 @@ def test_small_and_ragged_meshes(mesh):
 @pytest.mark.parametrize("iterations", [0, 2, 3])
 def test_iteration_counts_carry_lambda(iterations):
     m = grid((9, 9, 5))
-    p = P(iterations=iterations, alpha_d=1e-4, alpha_v=1e-10)
+    # without constraints the unpinned tissue would free-fall far from its
+    # extent, so that case runs without gravity (the tool still acts)
+    grav = (0.0, 0.0, 0.0) if iterations == 0 else (0.0, 0.0, -9.81)
+    p = P(iterations=iterations, alpha_d=1e-4, alpha_v=1e-10, gravity=grav, radius=4e-3)
     n_env, steps = 2, 20
     sim = make_sim([m], p, n_env, seed=4)
     oenvs, _ = oracle_envs([m], p, n_env, seed=4)
@@ -222,7 +231,7 @@ def test_collision_contacts_bit_exact_on_identical_inputs():
 
 
 def test_uneven_meshes_per_env_compliance_and_streaming_path():
-    shapes = [(9, 9, 5), (13, 13, 7), (25, 25, 13)]     # the last exceeds one CTA's shared memory
+    shapes = [(9, 9, 5), (13, 13, 7), (27, 27, 14)]     # the last exceeds one CTA's shared memory
     meshes = [grid(s) for s in shapes]
     n_env, steps = 7, 8
     env_mesh = np.array([2, 0, 1, 2, 1, 0, 2], dtype=np.int32)
