@@ -77,8 +77,15 @@ typedef struct {
     int32_t n_obs_verts;      /* sampled top-surface vertices in the observation */
     int32_t max_steps;        /* done when the step count reaches this (0 = never) */
     int32_t block_threads;    /* CUDA threads per environment; 0 = autotuned */
-    int32_t reserved[5];      /* must be zero */
+    int32_t schedule_flags;   /* 0 = autotuned; else FFSRL_SCHED_* bits forcing a schedule */
+    int32_t reserved[4];      /* must be zero */
 } ffsrl_params;
+
+/* schedule_flags bits (execution choices only: results do not depend on them
+ * beyond float32 rounding order, and not at all for the first three). */
+#define FFSRL_SCHED_FORCE 1       /* use the bits below instead of autotuning them */
+#define FFSRL_SCHED_NO_PERMUTE 2  /* keep vertex order in shared memory, colour order of records */
+#define FFSRL_SCHED_NO_RING 4     /* read constraint records from L2 instead of the TMA ring */
 
 /* Sizes of a created simulator. */
 typedef struct {
@@ -87,8 +94,10 @@ typedef struct {
     int32_t obs_dim;          /* 3 + 3 * n_obs_verts */
     int32_t max_verts;        /* largest V over the meshes */
     int64_t total_verts;      /* sum over envs of their mesh's V (packed rows) */
-    int32_t block_threads;    /* threads per environment in use */
+    int32_t block_threads;    /* threads per environment in use (largest group) */
     int32_t resident_envs;    /* envs whose state stays in shared memory */
+    int32_t n_groups;         /* step-kernel launches per step */
+    int32_t ring_envs;        /* envs whose constraint records stream through the TMA ring */
 } ffsrl_info;
 
 /* Creates n_env environments; env e uses meshes[env_mesh[e]] (env_mesh NULL:

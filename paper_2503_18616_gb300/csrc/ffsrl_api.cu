@@ -1,10 +1,13 @@
-// C ABI of the batched XPBD simulator: creation, reset, step, state access.
-// Declarations and contracts are in include/ffsrl.h.
+// C ABI of the batched XPBD simulator: creation, reset, step, state access,
+// plus the launch planner and autotuner. Contracts are in include/ffsrl.h.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -35,13 +38,34 @@ int fail(int code, const std::string& msg) {
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-// One launch group: envs of one mesh, resident in shared memory or not.
+// One step-kernel launch: the envs of one mesh with one execution schedule.
 struct LaunchGroup {
-    bool resident;
-    size_t smem;
-    int n;
-    int* d_list;
+    int mesh = 0;
+    int n = 0;
+    int* d_list = nullptr;
+    bool resident = false, ring = false, permute = true;
+    int block = 256;
+    size_t smem = 0;
 };
+
+// Autotuner choices, cached per mesh size class and batch size for the
+// lifetime of the process.
+struct TuneKey {
+    int V, E, T, n_env, substeps, iterations;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(V, E, T, n_env, substeps, iterations) <
+               std::tie(o.V, o.E, o.T, o.n_env, o.substeps, o.iterations);
+    }
+};
+struct TuneChoice {
+    int block;
+    bool ring, permute;
+    float ms;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tune_cache;
+
+const int kBlocks[] = {128, 256, 384, 512};
 
 }  // namespace
 
@@ -49,7 +73,8 @@ struct ffsrl_sim {
     int device = 0;
     cudaStream_t stream = nullptr;
     ffsrl_params params{};
-    int n_env = 0, obs_dim = 0, block = 256;
+    int n_env = 0, obs_dim = 0;
+    size_t max_smem = 0;
     std::vector<HostMesh> meshes;
     std::vector<int> env_mesh, voff, pstart;
     long long stride = 0, total_verts = 0;
@@ -57,9 +82,11 @@ struct ffsrl_sim {
     float* h_pinned = nullptr;  // staging for ffsrl_step_host
     float* d_stage = nullptr;
     SimDev S{};
+    MeshDev* d_meshes[2] = {nullptr, nullptr};  // [0] plain schedule, [1] permuted schedule
+    std::vector<MeshDev> h_meshes[2];
     int* d_pstart = nullptr;
     std::vector<LaunchGroup> groups;
-    int resident_envs = 0;
+    int resident_envs = 0, ring_envs = 0;
 
     template <class T>
     cudaError_t alloc(T** p, size_t count) {
@@ -97,8 +124,143 @@ int check_params(const ffsrl_params& p) {
     const int b = p.block_threads;
     if (b != 0 && b != 128 && b != 256 && b != 384 && b != 512 && b != 768 && b != 1024)
         return fail(FFSRL_E_INVAL, "block_threads must be 0, 128, 256, 384, 512, 768 or 1024");
-    for (int k = 0; k < 5; ++k)
+    if (p.schedule_flags & ~(FFSRL_SCHED_FORCE | FFSRL_SCHED_NO_PERMUTE | FFSRL_SCHED_NO_RING))
+        return fail(FFSRL_E_INVAL, "unknown schedule_flags bits");
+    for (int k = 0; k < 4; ++k)
         if (p.reserved[k] != 0) return fail(FFSRL_E_INVAL, "reserved params must be zero");
+    return FFSRL_OK;
+}
+
+// Upload one mesh's schedule variant and fill its device descriptor.
+int upload_mesh(ffsrl_sim* s, const HostMesh& m, bool permute, MeshDev& d) {
+    const ffsrl_params& p = s->params;
+    Schedule sc;
+    build_schedule(m, 0x5EEDull + uint64_t(m.V), permute, sc);
+    d = MeshDev{};
+    d.V = m.V;
+    d.Vp = round_up(m.V, 32);
+    d.E = m.E;
+    d.T = m.T;
+    d.n_ecol = m.n_ecol;
+    d.n_tcol = m.n_tcol;
+    d.n_top = int(m.top.size());
+    d.n_seg = m.n_ecol + m.n_tcol;
+    d.ring_bytes = sc.ring_bytes;
+    std::vector<float4> rw(m.V);
+    for (int i = 0; i < m.V; ++i)
+        rw[i] = make_float4(m.rest[3 * i], m.rest[3 * i + 1], m.rest[3 * i + 2], m.inv_mass[i]);
+    unsigned char* d_recs;
+    int4* d_segs;
+    uint16_t *d_slot, *d_vert;
+    float4* d_rw;
+    int* d_top;
+    FFSRL_CUDA(s->upload(&d_recs, sc.stream.data(), sc.stream.size()));
+    FFSRL_CUDA(s->upload(&d_segs, reinterpret_cast<const int4*>(sc.segs.data()), sc.segs.size() / 4));
+    FFSRL_CUDA(s->upload(&d_slot, sc.slot_of.data(), sc.slot_of.size()));
+    FFSRL_CUDA(s->upload(&d_vert, sc.vert_of.data(), sc.vert_of.size()));
+    FFSRL_CUDA(s->upload(&d_rw, rw.data(), rw.size()));
+    FFSRL_CUDA(s->upload(&d_top, m.top.data(), m.top.size()));
+    d.recs = d_recs;
+    d.segs = d_segs;
+    d.slot_of = d_slot;
+    d.vert_of = d_vert;
+    d.rest_w = d_rw;
+    d.top = d_top;
+    // Tool box around the rest bounding box and tool start above the top face.
+    for (int k = 0; k < 2; ++k) {
+        d.box_lo[k] = m.bbmin[k] - p.tool_margin_xy;
+        d.box_hi[k] = m.bbmax[k] + p.tool_margin_xy;
+        d.tool_start[k] = (m.bbmin[k] + m.bbmax[k]) / 2;
+    }
+    d.box_lo[2] = m.bbmax[2] - p.tool_margin_below;
+    d.box_hi[2] = m.bbmax[2] + p.tool_margin_above;
+    d.tool_start[2] = m.bbmax[2] + p.tool_radius;
+    const double min_len = 1e-12 * m.extent;
+    d.min_len2 = float(min_len * min_len);
+    return FFSRL_OK;
+}
+
+// Shared memory a group needs, or 0 if the configuration does not fit.
+size_t group_smem(const ffsrl_sim* s, const MeshDev& d, bool resident, bool ring) {
+    const size_t b = step_smem_bytes(d.Vp, resident, ring, d.ring_bytes, d.n_seg);
+    return b + 128 <= s->max_smem ? b : 0;  // 128 B left for the kernel's static shared memory
+}
+
+cudaError_t launch_group(ffsrl_sim* s, const LaunchGroup& g, const float* a, float* o, float* r, uint8_t* d) {
+    SimDev S = s->S;
+    S.meshes = s->d_meshes[g.permute ? 1 : 0];
+    return launch_step(S, g.resident, g.ring, g.block, g.d_list, g.n, g.smem, s->stream, a, o, r, d);
+}
+
+// Times candidate schedules of one group on its own envs (device-drawn
+// actions, no outputs) and keeps the fastest. The envs are reset afterwards.
+int autotune_group(ffsrl_sim* s, LaunchGroup& g) {
+    const ffsrl_params& p = s->params;
+    const HostMesh& m = s->meshes[g.mesh];
+    const TuneKey key{m.V, m.E, m.T, g.n, p.substeps, p.iterations};
+    const bool force_sched = (p.schedule_flags & FFSRL_SCHED_FORCE) != 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end() && !p.block_threads && !force_sched) {
+            g.block = it->second.block;
+            g.ring = it->second.ring && group_smem(s, s->h_meshes[1][g.mesh], g.resident, true);
+            g.permute = it->second.permute;
+            g.smem = group_smem(s, s->h_meshes[g.permute][g.mesh], g.resident, g.ring);
+            return FFSRL_OK;
+        }
+    }
+    std::vector<int> blocks;
+    if (p.block_threads) blocks.push_back(p.block_threads);
+    else blocks.assign(std::begin(kBlocks), std::end(kBlocks));
+    std::vector<std::pair<bool, bool>> scheds;  // (permute, ring)
+    if (force_sched) {
+        scheds.push_back({!(p.schedule_flags & FFSRL_SCHED_NO_PERMUTE), !(p.schedule_flags & FFSRL_SCHED_NO_RING)});
+    } else {
+        scheds = {{true, true}, {true, false}, {false, true}, {false, false}};
+    }
+    cudaEvent_t e0, e1;
+    FFSRL_CUDA(cudaEventCreate(&e0));
+    FFSRL_CUDA(cudaEventCreate(&e1));
+    TuneChoice best{0, false, false, 1e30f};
+    int tried = 0;
+    for (auto [perm, ring] : scheds) {
+        if (ring && !group_smem(s, s->h_meshes[perm][g.mesh], g.resident, true)) continue;
+        for (int b : blocks) {
+            LaunchGroup c = g;
+            c.block = b;
+            c.ring = ring;
+            c.permute = perm;
+            c.smem = group_smem(s, s->h_meshes[perm][g.mesh], g.resident, ring);
+            if (!c.smem) continue;
+            const int reps = (blocks.size() * scheds.size() == 1) ? 0 : 2;
+            if (reps == 0) {
+                best = {b, ring, perm, 0.f};
+                ++tried;
+                continue;
+            }
+            FFSRL_CUDA(launch_group(s, c, nullptr, nullptr, nullptr, nullptr));  // warm-up
+            FFSRL_CUDA(cudaEventRecord(e0, s->stream));
+            for (int i = 0; i < reps; ++i) FFSRL_CUDA(launch_group(s, c, nullptr, nullptr, nullptr, nullptr));
+            FFSRL_CUDA(cudaEventRecord(e1, s->stream));
+            FFSRL_CUDA(cudaEventSynchronize(e1));
+            float ms = 0;
+            FFSRL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            ++tried;
+            if (ms < best.ms) best = {b, ring, perm, ms};
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!tried) return fail(FFSRL_E_INVAL, "no step schedule fits this device");
+    g.block = best.block;
+    g.ring = best.ring;
+    g.permute = best.permute;
+    g.smem = group_smem(s, s->h_meshes[g.permute][g.mesh], g.resident, g.ring);
+    if (!p.block_threads && !force_sched) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
     return FFSRL_OK;
 }
 
@@ -107,60 +269,19 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
     const int n_env = s->n_env;
     const double h = p.dt / p.substeps;
 
-    // Per-mesh device tables in colour-major order.
-    std::vector<MeshDev> md(s->meshes.size());
-    for (size_t mi = 0; mi < s->meshes.size(); ++mi) {
-        const HostMesh& m = s->meshes[mi];
-        MeshDev& d = md[mi];
-        d.V = m.V;
-        d.Vp = round_up(m.V, 32);
-        d.E = m.E;
-        d.T = m.T;
-        d.n_ecol = m.n_ecol;
-        d.n_tcol = m.n_tcol;
-        d.n_top = int(m.top.size());
-        std::vector<uint32_t> eab(m.E);
-        std::vector<float> ed(m.E);
-        for (int q = 0; q < m.E; ++q) {
-            const int e = m.eorder[q];
-            eab[q] = uint32_t(m.edge[2 * e]) | (uint32_t(m.edge[2 * e + 1]) << 16);
-            ed[q] = m.rest_len[e];
+    int max_optin = 0;
+    FFSRL_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device));
+    s->max_smem = size_t(max_optin);
+
+    for (int v = 0; v < 2; ++v) {
+        s->h_meshes[v].resize(s->meshes.size());
+        for (size_t mi = 0; mi < s->meshes.size(); ++mi) {
+            int rc = upload_mesh(s, s->meshes[mi], v == 1, s->h_meshes[v][mi]);
+            if (rc) return rc;
         }
-        std::vector<uint2> tq(m.T);
-        std::vector<float> tv(m.T);
-        for (int q = 0; q < m.T; ++q) {
-            const int t = m.torder[q];
-            tq[q].x = uint32_t(m.tet[4 * t]) | (uint32_t(m.tet[4 * t + 1]) << 16);
-            tq[q].y = uint32_t(m.tet[4 * t + 2]) | (uint32_t(m.tet[4 * t + 3]) << 16);
-            tv[q] = m.V0[t];
-        }
-        std::vector<float4> rw(m.V);
-        for (int i = 0; i < m.V; ++i)
-            rw[i] = make_float4(m.rest[3 * i], m.rest[3 * i + 1], m.rest[3 * i + 2], m.inv_mass[i]);
-        uint32_t* d_eab; float* d_ed; uint2* d_tq; float* d_tv; int* d_eo; int* d_to; float4* d_rw; int* d_top;
-        FFSRL_CUDA(s->upload(&d_eab, eab.data(), eab.size()));
-        FFSRL_CUDA(s->upload(&d_ed, ed.data(), ed.size()));
-        FFSRL_CUDA(s->upload(&d_tq, tq.data(), tq.size()));
-        FFSRL_CUDA(s->upload(&d_tv, tv.data(), tv.size()));
-        FFSRL_CUDA(s->upload(&d_eo, m.ecol_off.data(), m.ecol_off.size()));
-        FFSRL_CUDA(s->upload(&d_to, m.tcol_off.data(), m.tcol_off.size()));
-        FFSRL_CUDA(s->upload(&d_rw, rw.data(), rw.size()));
-        FFSRL_CUDA(s->upload(&d_top, m.top.data(), m.top.size()));
-        d.edge_ab = d_eab; d.edge_d = d_ed; d.tet_abcd = d_tq; d.tet_V0 = d_tv;
-        d.ecol_off = d_eo; d.tcol_off = d_to; d.rest_w = d_rw; d.top = d_top;
-        // Tool box around the rest bounding box and tool start above the top face.
-        for (int k = 0; k < 2; ++k) {
-            d.box_lo[k] = m.bbmin[k] - p.tool_margin_xy;
-            d.box_hi[k] = m.bbmax[k] + p.tool_margin_xy;
-            d.tool_start[k] = (m.bbmin[k] + m.bbmax[k]) / 2;
-        }
-        d.box_lo[2] = m.bbmax[2] - p.tool_margin_below;
-        d.box_hi[2] = m.bbmax[2] + p.tool_margin_above;
-        d.tool_start[2] = m.bbmax[2] + p.tool_radius;
-        d.min_len = float(1e-12 * m.extent);
+        FFSRL_CUDA(s->upload(&s->d_meshes[v], s->h_meshes[v].data(), s->h_meshes[v].size()));
     }
-    MeshDev* d_md;
-    FFSRL_CUDA(s->upload(&d_md, md.data(), md.size()));
+    const std::vector<MeshDev>& md = s->h_meshes[1];
 
     // Per-env descriptors and packed/padded offsets.
     std::vector<EnvDev> ev(n_env);
@@ -189,7 +310,7 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
     FFSRL_CUDA(s->upload(&s->d_pstart, s->pstart.data(), s->pstart.size()));
 
     SimDev& S = s->S;
-    S.meshes = d_md;
+    S.meshes = s->d_meshes[1];
     S.envs = d_ev;
     S.n_env = n_env;
     S.obs_dim = s->obs_dim;
@@ -198,6 +319,7 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
     FFSRL_CUDA(s->alloc(&S.v, 3 * size_t(s->stride)));
     FFSRL_CUDA(cudaMemset(S.x, 0, 3 * size_t(s->stride) * sizeof(float)));
     FFSRL_CUDA(cudaMemset(S.v, 0, 3 * size_t(s->stride) * sizeof(float)));
+    FFSRL_CUDA(s->alloc(&S.pg, 3 * size_t(s->stride)));
     FFSRL_CUDA(s->alloc(&S.tool, 3 * size_t(n_env)));
     FFSRL_CUDA(s->alloc(&S.l_prev, n_env));
     FFSRL_CUDA(s->alloc(&S.t_step, n_env));
@@ -211,6 +333,7 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
     S.lambda = nullptr;
     if (p.iterations > 1) FFSRL_CUDA(s->alloc(&S.lambda, size_t(loff)));
     S.h = float(h);
+    S.inv_h = float(1.0 / h);
     S.gx = float(p.gravity[0]);
     S.gy = float(p.gravity[1]);
     S.gz = float(p.gravity[2]);
@@ -226,10 +349,7 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
     S.w_s = p.w_s;
     S.success_dist = p.success_dist;
 
-    // Launch groups: per mesh, resident in shared memory when it fits.
-    int max_optin = 0;
-    FFSRL_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device));
-    const size_t static_smem = 64;  // tool centre in the kernel's static shared memory
+    // Launch groups: one per mesh; resident in shared memory when it fits.
     bool any_streaming = false;
     for (size_t mi = 0; mi < md.size(); ++mi) {
         std::vector<int> list;
@@ -237,26 +357,35 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
             if (s->env_mesh[e] == int(mi)) list.push_back(e);
         if (list.empty()) continue;
         LaunchGroup g;
+        g.mesh = int(mi);
         g.n = int(list.size());
-        const size_t res = resident_smem_bytes(md[mi].Vp);
-        g.resident = res + static_smem <= size_t(max_optin);
-        g.smem = g.resident ? res : streaming_smem_bytes(md[mi].Vp);
+        g.resident = group_smem(s, md[mi], true, false) != 0;
         any_streaming |= !g.resident;
-        if (g.resident) s->resident_envs += g.n;
         FFSRL_CUDA(s->upload(&g.d_list, list.data(), list.size()));
         s->groups.push_back(g);
     }
     S.xg = nullptr;
-    S.pg = nullptr;
-    if (any_streaming) {
-        FFSRL_CUDA(s->alloc(&S.xg, size_t(s->stride)));
-        FFSRL_CUDA(s->alloc(&S.pg, 3 * size_t(s->stride)));
-    }
+    if (any_streaming) FFSRL_CUDA(s->alloc(&S.xg, size_t(s->stride)));
 
     // Pinned host staging and device staging for ffsrl_step_host.
     const size_t stage = size_t(n_env) * (3 + s->obs_dim + 1) + (size_t(n_env) + 3) / 4;
     FFSRL_CUDA(cudaMallocHost(&s->h_pinned, stage * sizeof(float)));
     FFSRL_CUDA(s->alloc(&s->d_stage, stage));
+
+    // Every env needs a valid state (tool, target, step count) before the
+    // autotuner runs steps on it.
+    FFSRL_CUDA(launch_reset(S, nullptr, 0ull, s->stream));
+    FFSRL_CUDA(cudaStreamSynchronize(s->stream));
+    // Execution schedule per group (autotuned unless forced), largest groups first.
+    std::sort(s->groups.begin(), s->groups.end(), [&](const LaunchGroup& a, const LaunchGroup& b) {
+        return size_t(a.n) * md[a.mesh].V > size_t(b.n) * md[b.mesh].V;
+    });
+    for (LaunchGroup& g : s->groups) {
+        int rc = autotune_group(s, g);
+        if (rc) return rc;
+        if (g.resident) s->resident_envs += g.n;
+        if (g.ring) s->ring_envs += g.n;
+    }
     return FFSRL_OK;
 }
 
@@ -284,7 +413,6 @@ int ffsrl_create(const ffsrl_mesh* meshes, int32_t n_meshes, const int32_t* env_
     s->obs_dim = 3 + 3 * params->n_obs_verts;
     s->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaGetDevice(&s->device);
-    s->block = params->block_threads ? params->block_threads : 256;
     s->meshes.resize(n_meshes);
     for (int i = 0; i < n_meshes; ++i) {
         std::string err;
@@ -313,7 +441,9 @@ int ffsrl_create(const ffsrl_mesh* meshes, int32_t n_meshes, const int32_t* env_
     }
     rc = build_device(s, env_compliance_dist);
     if (rc == FFSRL_OK) {
+        // Reset after autotuning, which advanced the envs it timed.
         cudaError_t e = launch_reset(s->S, nullptr, 0ull, s->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s->S.err, 0, n_env * sizeof(int), s->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
         if (e != cudaSuccess) rc = fail(FFSRL_E_CUDA, std::string("initial reset: ") + cudaGetErrorString(e));
     }
@@ -345,8 +475,7 @@ int ffsrl_step(ffsrl_sim* sim, const float* actions_dev, float* obs_dev, float* 
     if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
     FFSRL_CUDA(cudaSetDevice(sim->device));
     for (const LaunchGroup& g : sim->groups)
-        FFSRL_CUDA(launch_step(sim->S, g.resident, sim->block, g.d_list, g.n, g.smem, sim->stream,
-                               actions_dev, obs_dev, reward_dev, done_dev));
+        FFSRL_CUDA(launch_group(sim, g, actions_dev, obs_dev, reward_dev, done_dev));
     return FFSRL_OK;
 }
 
@@ -389,11 +518,16 @@ int ffsrl_sync(ffsrl_sim* sim) {
     FFSRL_CUDA(cudaStreamSynchronize(sim->stream));
     std::vector<int> err(sim->n_env);
     FFSRL_CUDA(cudaMemcpy(err.data(), sim->S.err, err.size() * sizeof(int), cudaMemcpyDeviceToHost));
-    int first = -1;
+    int first = -1, bits = 0;
     for (int e = 0; e < sim->n_env; ++e)
-        if (err[e] && first < 0) first = e;
+        if (err[e]) {
+            bits |= err[e];
+            if (first < 0) first = e;
+        }
     if (first >= 0) {
         FFSRL_CUDA(cudaMemset(sim->S.err, 0, err.size() * sizeof(int)));
+        if (bits & kErrTimeout)
+            return fail(FFSRL_E_TIMEOUT, "a constraint-record copy timed out in env " + std::to_string(first));
         return fail(FFSRL_E_NAN, "non-finite positions in env " + std::to_string(first));
     }
     return FFSRL_OK;
@@ -408,8 +542,10 @@ int ffsrl_get_info(const ffsrl_sim* sim, ffsrl_info* out) {
     for (const HostMesh& m : sim->meshes) mv = std::max(mv, m.V);
     out->max_verts = mv;
     out->total_verts = sim->total_verts;
-    out->block_threads = sim->block;
+    out->block_threads = sim->groups.empty() ? 0 : sim->groups.front().block;
     out->resident_envs = sim->resident_envs;
+    out->n_groups = int(sim->groups.size());
+    out->ring_envs = sim->ring_envs;
     return FFSRL_OK;
 }
 

@@ -4,6 +4,8 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstring>
+#include <random>
 
 #include "../../include/ffsrl.h"
 
@@ -167,6 +169,117 @@ int build_host_mesh(int V, int T, const double* rest, const double* inv_mass,
     for (int i = 0; i < V; ++i)
         if (rest[3 * i + 2] == m.bbmax[2]) m.top.push_back(i);
     return FFSRL_OK;
+}
+
+namespace {
+
+// Orders the records of one colour in groups of 8 whose slot residues mod 8
+// are pairwise distinct in every vertex position, scanning a bounded window
+// of the remaining records; a group that cannot be completed is filled with
+// the earliest remaining records.
+template <int ARITY>
+std::vector<int> group_by_banks(const std::vector<std::array<int, ARITY>>& recs) {
+    const int n = int(recs.size());
+    const int window = 512;   // untaken records considered per group
+    std::vector<int> order;
+    order.reserve(n);
+    std::vector<char> taken(n, 0);
+    int start = 0;            // first untaken record
+    while (int(order.size()) < n) {
+        while (taken[start]) ++start;
+        unsigned used[ARITY] = {};
+        int got = 0, seen = 0;
+        for (int j = start; j < n && got < 8 && seen < window; ++j) {
+            if (taken[j]) continue;
+            ++seen;
+            const auto& r = recs[j];
+            bool ok = true;
+            for (int k = 0; k < ARITY; ++k) ok &= !(used[k] & (1u << (r[k] & 7)));
+            if (!ok) continue;
+            for (int k = 0; k < ARITY; ++k) used[k] |= 1u << (r[k] & 7);
+            taken[j] = 1;
+            order.push_back(j);
+            ++got;
+        }
+        for (int j = start; j < n && got < 8; ++j)
+            if (!taken[j]) {
+                taken[j] = 1;
+                order.push_back(j);
+                ++got;
+            }
+    }
+    return order;
+}
+
+void append_segment(Schedule& out, const void* data, int bytes, int count, int first) {
+    const int off = int(out.stream.size());
+    const int padded = (bytes + 15) / 16 * 16;
+    out.stream.resize(off + padded, 0);
+    std::memcpy(out.stream.data() + off, data, bytes);
+    out.segs.insert(out.segs.end(), {off, padded, count, first});
+    out.ring_bytes = std::max(out.ring_bytes, padded);
+}
+
+}  // namespace
+
+void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& out) {
+    out = Schedule();
+    const int V = m.V;
+    out.slot_of.resize(V);
+    out.vert_of.resize(V);
+    std::mt19937_64 rng(seed);
+    for (int b = 0; b < V; b += 32) {
+        const int n = std::min(32, V - b);
+        std::vector<int> p(n);
+        for (int i = 0; i < n; ++i) p[i] = i;
+        if (permute) std::shuffle(p.begin(), p.end(), rng);
+        for (int i = 0; i < n; ++i) {
+            out.slot_of[b + i] = uint16_t(b + p[i]);
+            out.vert_of[b + p[i]] = uint16_t(b + i);
+        }
+    }
+    for (int c = 0; c < m.n_ecol; ++c) {
+        const int beg = m.ecol_off[c], end = m.ecol_off[c + 1];
+        std::vector<std::array<int, 2>> r(end - beg);
+        for (int q = beg; q < end; ++q) {
+            const int e = m.eorder[q];
+            r[q - beg] = {out.slot_of[m.edge[2 * e]], out.slot_of[m.edge[2 * e + 1]]};
+        }
+        const std::vector<int> ord = permute ? group_by_banks<2>(r) : std::vector<int>();
+        std::vector<uint32_t> buf(2 * size_t(end - beg));
+        for (int j = 0; j < end - beg; ++j) {
+            const int src = permute ? ord[j] : j;
+            const int e = m.eorder[beg + src];
+            float d = m.rest_len[e];
+            uint32_t dbits;
+            std::memcpy(&dbits, &d, 4);
+            buf[2 * j] = uint32_t(r[src][0]) | (uint32_t(r[src][1]) << 16);
+            buf[2 * j + 1] = dbits;
+        }
+        append_segment(out, buf.data(), int(buf.size() * 4), end - beg, beg);
+    }
+    for (int c = 0; c < m.n_tcol; ++c) {
+        const int beg = m.tcol_off[c], end = m.tcol_off[c + 1];
+        std::vector<std::array<int, 4>> r(end - beg);
+        for (int q = beg; q < end; ++q) {
+            const int t = m.torder[q];
+            for (int k = 0; k < 4; ++k) r[q - beg][k] = out.slot_of[m.tet[4 * t + k]];
+        }
+        const std::vector<int> ord = permute ? group_by_banks<4>(r) : std::vector<int>();
+        std::vector<uint32_t> buf(4 * size_t(end - beg));
+        for (int j = 0; j < end - beg; ++j) {
+            const int src = permute ? ord[j] : j;
+            const int t = m.torder[beg + src];
+            float v0 = m.V0[t];
+            uint32_t vbits;
+            std::memcpy(&vbits, &v0, 4);
+            buf[4 * j] = uint32_t(r[src][0]) | (uint32_t(r[src][1]) << 16);
+            buf[4 * j + 1] = uint32_t(r[src][2]) | (uint32_t(r[src][3]) << 16);
+            buf[4 * j + 2] = vbits;
+            buf[4 * j + 3] = 0;
+        }
+        append_segment(out, buf.data(), int(buf.size() * 4), end - beg, m.E + beg);
+    }
 }
 
 }  // namespace ffsrl

@@ -35,4 +35,22 @@ struct HostMesh {
 int build_host_mesh(int V, int T, const double* rest, const double* inv_mass,
                     const int32_t* tets, HostMesh& out, std::string& err);
 
+// Execution schedule of one mesh on the GPU: vertex -> shared-memory slot map
+// and the colour-major constraint stream (edge colours, then tet colours),
+// each colour a 16-byte aligned segment of records.
+struct Schedule {
+    std::vector<uint16_t> slot_of, vert_of;  // [V]
+    std::vector<unsigned char> stream;       // records
+    std::vector<int32_t> segs;               // [n_seg][4]: byte offset, bytes, count, first constraint
+    int ring_bytes = 0;                      // largest segment
+};
+
+// Builds the schedule. Slots are a fixed permutation inside each aligned
+// block of 32 vertices (seeded by `seed`); inside each colour the records are
+// grouped so that the 8 records of every aligned group of 8 use distinct
+// slot residues modulo 8 in each vertex position where possible (distinct
+// shared-memory bank groups for 16-byte accesses). Both choices leave the
+// result unchanged: a colour's constraints touch disjoint vertices.
+void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& out);
+
 }  // namespace ffsrl

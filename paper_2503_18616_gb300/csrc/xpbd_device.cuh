@@ -5,8 +5,15 @@
 //   positions / velocities: structure of arrays, x[k * stride + voff_e + i] for
 //     component k, env e, vertex i; voff_e is a multiple of 32 vertices so every
 //     env starts on a 128-byte boundary.
-//   constraint tables: per distinct mesh, in colour-major order, vertex ids
-//     packed as 16-bit pairs (edges: a | b << 16; tets: (a | b << 16, c | d << 16)).
+//   constraint stream: per distinct mesh, one byte stream holding every colour
+//     (edge colours, then tet colours) as a 16-byte aligned segment of records.
+//     Edge record (8 B): slot(a) | slot(b) << 16, rest length. Tet record (16 B):
+//     slot(a) | slot(b) << 16, slot(c) | slot(d) << 16, rest volume, unused.
+//     Vertex "slots" are the shared-memory rows of the vertices: a fixed
+//     permutation inside each aligned block of 32 vertices, chosen with the
+//     order of records inside each colour so that the 8 lanes of each
+//     shared-memory access phase hit distinct bank groups. Records of one
+//     colour touch disjoint vertices, so their order does not change results.
 //   per-env scalars: tool centre (float64), last distance, step count, seed,
 //     target vertex, observed vertex ids, contact list, error flags.
 #pragma once
@@ -16,21 +23,19 @@
 
 namespace ffsrl {
 
-constexpr int kMaxColours = 256;
-
 struct MeshDev {
     int V, Vp, E, T;
-    int n_ecol, n_tcol, n_top, pad0;
-    const uint32_t* edge_ab;  // [E] colour-major
-    const float* edge_d;      // [E] rest lengths
-    const uint2* tet_abcd;    // [T] colour-major
-    const float* tet_V0;      // [T] rest volumes
-    const int* ecol_off;      // [n_ecol + 1]
-    const int* tcol_off;      // [n_tcol + 1]
-    const float4* rest_w;     // [V] rest position and inverse mass
-    const int* top;           // [n_top] top-face vertex ids
+    int n_ecol, n_tcol, n_top, n_seg;  // n_seg = n_ecol + n_tcol
+    int ring_bytes;                   // largest segment in bytes (one ring stage)
+    int pad0;
+    const unsigned char* recs;        // constraint stream
+    const int4* segs;                 // [n_seg] {byte offset, bytes, count, first constraint}
+    const uint16_t* slot_of;          // [V] shared-memory slot of each vertex
+    const uint16_t* vert_of;          // [V] vertex of each slot
+    const float4* rest_w;             // [V] rest position and inverse mass (vertex order)
+    const int* top;                   // [n_top] top-face vertex ids
     double box_lo[3], box_hi[3], tool_start[3];
-    float min_len;            // edges shorter than this are skipped
+    float min_len2;                   // edges with |x_ab|^2 below this are skipped
     int pad1;
 };
 
@@ -41,13 +46,17 @@ struct EnvDev {
     int loff;       // first lambda slot of this env (iterations > 1)
 };
 
+// Error bits in SimDev::err.
+constexpr int kErrNonFinite = 1;
+constexpr int kErrTimeout = 2;
+
 struct SimDev {
     const MeshDev* meshes;
     const EnvDev* envs;
     int n_env;
     int obs_dim;
     long long stride;         // padded vertex rows over all envs
-    float* x;                 // [3][stride]
+    float* x;                 // [3][stride] vertex order
     float* v;                 // [3][stride]
     double* tool;             // [n_env][3]
     float* l_prev;            // [n_env]
@@ -57,11 +66,11 @@ struct SimDev {
     int* target;              // [n_env]
     int* n_contacts;          // [n_env]
     int* contacts;            // [stride]: env e's list at voff_e
-    int* err;                 // [n_env] bit 0: non-finite position
+    int* err;                 // [n_env] kErr* bits
     float* lambda;            // multipliers carried across iterations (iterations > 1)
-    float4* xg;               // [stride] working positions of envs not resident in SMEM
-    float* pg;                // [3][stride] substep-start positions of those envs
-    float h, gx, gy, gz;
+    float4* xg;               // [stride] working positions (slot order) of envs not resident in SMEM
+    float* pg;                // [3][stride] substep-start positions (slot order)
+    float h, inv_h, gx, gy, gz;
     float alpha_v;            // volume compliance / h^2
     float radius;
     double action_scale;

@@ -9,12 +9,12 @@
 
 namespace ffsrl {
 
-// Shared memory of one CTA for an env with Vp padded vertices.
-size_t resident_smem_bytes(int Vp);
-size_t streaming_smem_bytes(int Vp);
+// Dynamic shared memory of one step CTA: positions (resident only), the
+// two-stage constraint ring (ring only), the segment table and contact bits.
+size_t step_smem_bytes(int Vp, bool resident, bool ring, int ring_bytes, int n_seg);
 
 // Step kernel over n_blocks envs (env_list NULL: envs 0..n_blocks-1).
-cudaError_t launch_step(const SimDev& S, bool resident, int block, const int* env_list, int n_blocks,
+cudaError_t launch_step(const SimDev& S, bool resident, bool ring, int block, const int* env_list, int n_blocks,
                         size_t smem_bytes, cudaStream_t stream, const float* actions, float* obs,
                         float* reward, uint8_t* done);
 cudaError_t launch_reset(const SimDev& S, const uint8_t* mask, unsigned long long seed, cudaStream_t st);

@@ -7,18 +7,21 @@
 // collision -> velocity update, then observation, reward and termination
 // (Sec. III-B, Sec. IV).
 //
-// Resident variant (RES = true): the env's positions live in shared memory for
-// the whole step as float4 (x, y, z, inverse mass), so the 10 substeps x 55
-// colour phases never touch HBM; the only HBM traffic per env-step is reading
-// and writing x and v once (48 B per vertex) plus the observation. Constraint
-// tables are shared by all envs of a mesh and stay in L2.
-// Non-resident variant (RES = false): identical arithmetic on a float4 working
-// copy in global memory (L2-resident for the CTAs in flight), for meshes whose
-// state does not fit in one CTA's shared memory.
+// Resident variant (RES): the env's positions live in shared memory for the
+// whole step as float4 (x, y, z, inverse mass) in slot order, so the
+// substeps x colours phases never touch HBM; per env-step the HBM traffic is
+// x and v read and written once (48 B per vertex) plus the observation.
+// Non-resident variant: the same arithmetic on a float4 working copy in
+// global memory (L2-resident while its CTA runs), for meshes too large for one
+// CTA's shared memory.
+// Ring variant (RING): the records of the next colour are copied from the
+// L2-resident constraint stream into a shared-memory double buffer by the
+// Tensor Memory Accelerator (cp.async.bulk with an mbarrier) while the current
+// colour is projected, so no thread waits on L2 for constraint records.
 //
-// Within a colour no two constraints share a vertex, so threads of the CTA
-// project one colour in parallel and a __syncthreads() separates colours; the
-// result equals the sequential colour-by-colour Gauss-Seidel order.
+// Within a colour no two constraints share a vertex, so the CTA's threads
+// project one colour in parallel and a barrier separates colours; the result
+// equals the sequential colour-by-colour Gauss-Seidel order.
 #include <cstdint>
 
 #include "xpbd_device.cuh"
@@ -28,28 +31,67 @@ namespace ffsrl {
 
 namespace {
 
-__device__ __forceinline__ float3 sub3(float4 a, float4 b) {
-    return make_float3(a.x - b.x, a.y - b.y, a.z - b.z);
+// ---- mbarrier and bulk-copy helpers (PTX, sm_90+) ---------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return uint32_t(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
-    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
-__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+            smem_addr(bar)),
+        "r"(bytes)
+        : "memory");
+}
+// Bulk copy global -> this CTA's shared memory; completion counted on `bar`.
+// dst, src and bytes are multiples of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Waits for the phase of parity `parity` to complete, giving up after a fixed
+// number of polls (each poll may suspend the thread briefly).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (uint32_t i = 0; i < (1u << 22); ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// ---- constraint projections ------------------------------------------------
 
 // Edge-distance constraint C = |x_a - x_b| - d in XPBD form (Eq. 1 with
 // compliance): dlambda = (-C - at lambda) / (w_a + w_b + at), x_a += w_a dlambda n,
 // x_b -= w_b dlambda n, n = (x_a - x_b) / |x_a - x_b|.
-__device__ __forceinline__ void project_edge(float4* X, uint32_t ab, float d, float at,
-                                             float min_len, float& lam) {
-    const int a = int(ab & 0xffffu), b = int(ab >> 16);
+__device__ __forceinline__ void project_edge(float4* X, uint2 rec, float at, float min_len2, float& lam) {
+    const int a = int(rec.x & 0xffffu), b = int(rec.x >> 16);
+    const float d = __uint_as_float(rec.y);
     float4 xa = X[a], xb = X[b];
     const float dx = xa.x - xb.x, dy = xa.y - xb.y, dz = xa.z - xb.z;
-    const float len = sqrtf(dx * dx + dy * dy + dz * dz);
-    const float C = len - d;
+    const float l2 = dx * dx + dy * dy + dz * dz;
     const float denom = xa.w + xb.w + at;
-    if (len < min_len || denom == 0.f) return;
-    const float dl = (-C - at * lam) / denom;
-    const float s = dl / len;
+    if (l2 < min_len2 || denom == 0.f) return;
+    const float len = sqrtf(l2);
+    const float C = len - d;
+    const float dl = __fdividef(-C - at * lam, denom);
+    const float s = __fdividef(dl, len);
     const float sa = xa.w * s, sb = xb.w * s;
     xa.x += sa * dx; xa.y += sa * dy; xa.z += sa * dz;
     xb.x -= sb * dx; xb.y -= sb * dy; xb.z -= sb * dz;
@@ -58,14 +100,21 @@ __device__ __forceinline__ void project_edge(float4* X, uint32_t ab, float d, fl
     lam += dl;
 }
 
+__device__ __forceinline__ float3 sub3(float4 a, float4 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
 // Tet-volume constraint C = (x_ba x x_ca) . x_da / 6 - V0 with gradients
 // g_b = x_ca x x_da / 6, g_c = x_da x x_ba / 6, g_d = x_ba x x_ca / 6,
 // g_a = -(g_b + g_c + g_d) (the consistent reading of Eq. 2), scaled as in
 // Eq. 3 with inverse masses and compliance: dlambda = (-C - at lambda) /
 // (sum w_i |g_i|^2 + at), x_i += w_i dlambda g_i.
-__device__ __forceinline__ void project_tet(float4* X, uint2 q, float V0, float at, float& lam) {
-    const int a = int(q.x & 0xffffu), b = int(q.x >> 16);
-    const int c = int(q.y & 0xffffu), d = int(q.y >> 16);
+__device__ __forceinline__ void project_tet(float4* X, uint4 rec, float at, float& lam) {
+    const int a = int(rec.x & 0xffffu), b = int(rec.x >> 16);
+    const int c = int(rec.y & 0xffffu), d = int(rec.y >> 16);
+    const float V0 = __uint_as_float(rec.z);
     float4 xa = X[a], xb = X[b], xc = X[c], xd = X[d];
     const float3 ba = sub3(xb, xa), ca = sub3(xc, xa), da = sub3(xd, xa);
     const float3 g1 = cross3(ca, da), g2 = cross3(da, ba), g3 = cross3(ba, ca);  // 6 x gradient
@@ -74,7 +123,7 @@ __device__ __forceinline__ void project_tet(float4* X, uint2 q, float V0, float 
     const float sw = xa.w * dot3(g0, g0) + xb.w * dot3(g1, g1) + xc.w * dot3(g2, g2) + xd.w * dot3(g3, g3);
     const float denom = sw * (1.0f / 36.0f) + at;
     if (denom == 0.f) return;
-    const float dl = (-C - at * lam) / denom;
+    const float dl = __fdividef(-C - at * lam, denom);
     const float s = dl * (1.0f / 6.0f);
     const float sa = xa.w * s, sb = xb.w * s, sc = xc.w * s, sd = xd.w * s;
     xa.x += sa * g0.x; xa.y += sa * g0.y; xa.z += sa * g0.z;
@@ -88,55 +137,75 @@ __device__ __forceinline__ void project_tet(float4* X, uint2 q, float V0, float 
     lam += dl;
 }
 
+__host__ __device__ __forceinline__ size_t align128(size_t b) { return (b + 127) / 128 * 128; }
+
+// Dynamic shared-memory layout: [X (resident only)] [ring (2 stages)] [segment table] [contact bits]
+struct SmemLayout {
+    size_t x_off, ring_off, seg_off, bits_off, total;
+    __host__ __device__ SmemLayout(int Vp, bool res, bool ring, int ring_bytes, int n_seg) {
+        x_off = 0;
+        ring_off = align128(res ? size_t(Vp) * 16 : 0);
+        seg_off = align128(ring_off + (ring ? 2 * size_t(ring_bytes) : 0));
+        bits_off = align128(seg_off + size_t(n_seg) * 16);
+        total = bits_off + size_t(Vp / 32) * 4;
+    }
+};
+
 }  // namespace
 
-size_t resident_smem_bytes(int Vp) {
-    return size_t(Vp) * sizeof(float4) + 3 * size_t(Vp) * sizeof(float) + size_t(Vp / 32) * 4;
+size_t step_smem_bytes(int Vp, bool resident, bool ring, int ring_bytes, int n_seg) {
+    return SmemLayout(Vp, resident, ring, ring_bytes, n_seg).total;
 }
-size_t streaming_smem_bytes(int Vp) { return size_t(Vp / 32) * 4; }
 
-template <int BLOCK, bool RES>
-__global__ void __launch_bounds__(BLOCK) xpbd_step_kernel(SimDev S, const int* __restrict__ env_list,
+// CTAs per SM the register allocation targets for each block size (about 85
+// registers per thread at 768 threads per SM, 64 at 1024).
+constexpr int min_ctas_per_sm(int block) {
+    return block <= 128 ? 6 : block <= 256 ? 3 : block <= 512 ? 2 : 1;
+}
+
+template <int BLOCK, bool RES, bool RING>
+__global__ void __launch_bounds__(BLOCK, min_ctas_per_sm(BLOCK)) xpbd_step_kernel(SimDev S, const int* __restrict__ env_list,
                                                           const float* __restrict__ actions,
                                                           float* __restrict__ obs,
                                                           float* __restrict__ reward,
                                                           uint8_t* __restrict__ done) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ double s_tool[3];
+
     const int env = env_list ? env_list[blockIdx.x] : int(blockIdx.x);
     const int tid = threadIdx.x;
     const EnvDev ed = S.envs[env];
-    const MeshDev& M = S.meshes[ed.mesh];
-    const int V = M.V, Vp = M.Vp;
+    const MeshDev M = S.meshes[ed.mesh];
+    const int V = M.V, Vp = M.Vp, n_seg = M.n_seg, n_ecol = M.n_ecol;
     const long long stride = S.stride;
+    const SmemLayout L(Vp, RES, RING, M.ring_bytes, n_seg);
 
-    float4* X;
-    float *Px, *Py, *Pz;
-    unsigned* bits;
-    if constexpr (RES) {
-        X = reinterpret_cast<float4*>(smem_raw);
-        Px = reinterpret_cast<float*>(X + Vp);
-        Py = Px + Vp;
-        Pz = Py + Vp;
-        bits = reinterpret_cast<unsigned*>(Pz + Vp);
-    } else {
-        X = S.xg + ed.voff;
-        Px = S.pg + ed.voff;
-        Py = Px + stride;
-        Pz = Py + stride;
-        bits = reinterpret_cast<unsigned*>(smem_raw);
-    }
-    __shared__ double s_tool[3];
+    float4* X = RES ? reinterpret_cast<float4*>(smem_raw + L.x_off) : S.xg + ed.voff;
+    unsigned char* ring = smem_raw + L.ring_off;
+    int4* segs = reinterpret_cast<int4*>(smem_raw + L.seg_off);
+    unsigned* bits = reinterpret_cast<unsigned*>(smem_raw + L.bits_off);
+    float* Px = S.pg + ed.voff;
+    float* Py = Px + stride;
+    float* Pz = Py + stride;
 
-    // Tool update once per step (Algorithm 1, "evaluate instrument state"):
-    // c <- clamp(c + scale * a) with a from the caller or from the env's
-    // counter-based stream at its current step count.
+    const int K = S.substeps * S.iterations * n_seg;  // colour phases in this step
+    for (int c = tid; c < n_seg; c += BLOCK) segs[c] = M.segs[c];
+    for (int w = tid; w < Vp / 32; w += BLOCK) bits[w] = 0u;
     if (tid == 0) {
+        if (RING) {
+            mbar_init(&mbar[0], 1);
+            mbar_init(&mbar[1], 1);
+            fence_mbar_init();
+        }
+        // Tool update once per step (Algorithm 1, "evaluate instrument
+        // state"): c <- clamp(c + scale * a), a from the caller or from the
+        // env's counter-based stream at its step count. Rounded product then
+        // rounded sum, so the float64 tool position is reproducible.
         const unsigned long long t = (unsigned long long)S.t_step[env];
         const unsigned long long st = env_stream(S.seed[env], (unsigned long long)env, 0u);
         for (int k = 0; k < 3; ++k) {
             const double a = actions ? (double)actions[3 * env + k] : to_unit_pm1(splitmix64_nth(st, 3ull * t + k));
-            // rounded product, then rounded sum (no fused multiply-add), so the
-            // float64 tool position is reproducible bit for bit
             double c = __dadd_rn(S.tool[3 * env + k], __dmul_rn(S.action_scale, a));
             c = c < M.box_lo[k] ? M.box_lo[k] : c;
             c = c > M.box_hi[k] ? M.box_hi[k] : c;
@@ -144,122 +213,159 @@ __global__ void __launch_bounds__(BLOCK) xpbd_step_kernel(SimDev S, const int* _
             s_tool[k] = c;
         }
     }
-
-    const float h = S.h;
-    const float* gx_ = S.x + ed.voff;
-    const float* gy_ = gx_ + stride;
-    const float* gz_ = gy_ + stride;
-    const float* gvx = S.v + ed.voff;
-    const float* gvy = gvx + stride;
-    const float* gvz = gvy + stride;
-
-    // Load the state and predict for the first substep (Algorithm 1:
-    // v~ = v + h g, x~ = x + h v~ for free vertices).
-    for (int i = tid; i < V; i += BLOCK) {
-        float4 xi = make_float4(gx_[i], gy_[i], gz_[i], M.rest_w[i].w);
-        Px[i] = xi.x;
-        Py[i] = xi.y;
-        Pz[i] = xi.z;
-        if (xi.w > 0.f) {
-            const float vx = gvx[i] + h * S.gx, vy = gvy[i] + h * S.gy, vz = gvz[i] + h * S.gz;
-            xi.x += h * vx;
-            xi.y += h * vy;
-            xi.z += h * vz;
-        }
-        X[i] = xi;
-    }
-    for (int w = tid; w < Vp / 32; w += BLOCK) bits[w] = 0u;
     __syncthreads();
-    const float cx = float(s_tool[0]), cy = float(s_tool[1]), cz = float(s_tool[2]);
-    const float r = S.radius;
-    const float at_d = ed.alpha_d, at_v = S.alpha_v;
-    const int E = M.E;
-    float* lam_e = S.lambda ? S.lambda + ed.loff : nullptr;
-    float* lam_t = lam_e ? lam_e + E : nullptr;
+    // Prefetch the first colour while the state loads.
+    if (RING && tid == 0 && K > 0) {
+        const int4 sg = segs[0];
+        mbar_expect_tx(&mbar[0], uint32_t(sg.y));
+        bulk_copy_g2s(ring, M.recs + sg.x, uint32_t(sg.y), &mbar[0]);
+    }
 
-    for (int sub = 0; sub < S.substeps; ++sub) {
+    const float h = S.h, inv_h = S.inv_h;
+    const float hgx = h * S.gx, hgy = h * S.gy, hgz = h * S.gz;
+    {
+        // Load the state (vertex order, coalesced) into slot order and predict
+        // for the first substep (Algorithm 1: v~ = v + h g, x~ = x + h v~).
+        const float* gx = S.x + ed.voff;
+        const float* gv = S.v + ed.voff;
+        for (int i = tid; i < V; i += BLOCK) {
+            const int s = M.slot_of[i];
+            float4 xi = make_float4(gx[i], gx[stride + i], gx[2 * stride + i], M.rest_w[i].w);
+            Px[s] = xi.x;
+            Py[s] = xi.y;
+            Pz[s] = xi.z;
+            if (xi.w > 0.f) {
+                xi.x += h * (gv[i] + hgx);
+                xi.y += h * (gv[stride + i] + hgy);
+                xi.z += h * (gv[2 * stride + i] + hgz);
+            }
+            X[s] = xi;
+        }
+    }
+    __syncthreads();
+
+    const float cx = float(s_tool[0]), cy = float(s_tool[1]), cz = float(s_tool[2]);
+    const float r = S.radius, r2 = r * r;
+    const float at_d = ed.alpha_d, at_v = S.alpha_v;
+    float* lam = S.lambda ? S.lambda + ed.loff : nullptr;
+    int k = 0;
+    bool failed = false;
+
+    for (int sub = 0; sub < S.substeps && !failed; ++sub) {
         if (sub > 0) {
-            // velocity update of the previous substep, v = (x - x_prev) / h,
+            // Velocity update of the previous substep, v = (x - x_prev) / h,
             // fused with this substep's prediction.
-            for (int i = tid; i < V; i += BLOCK) {
-                float4 xi = X[i];
-                const float vx = (xi.x - Px[i]) / h, vy = (xi.y - Py[i]) / h, vz = (xi.z - Pz[i]) / h;
-                Px[i] = xi.x;
-                Py[i] = xi.y;
-                Pz[i] = xi.z;
+            for (int s = tid; s < V; s += BLOCK) {
+                float4 xi = X[s];
+                const float vx = (xi.x - Px[s]) * inv_h, vy = (xi.y - Py[s]) * inv_h, vz = (xi.z - Pz[s]) * inv_h;
+                Px[s] = xi.x;
+                Py[s] = xi.y;
+                Pz[s] = xi.z;
                 if (xi.w > 0.f) {
-                    xi.x += h * (vx + h * S.gx);
-                    xi.y += h * (vy + h * S.gy);
-                    xi.z += h * (vz + h * S.gz);
-                    X[i] = xi;
+                    xi.x += h * (vx + hgx);
+                    xi.y += h * (vy + hgy);
+                    xi.z += h * (vz + hgz);
+                    X[s] = xi;
                 }
             }
             __syncthreads();
         }
-        for (int it = 0; it < S.iterations; ++it) {
-            const bool carry = lam_e != nullptr;
-            for (int col = 0; col < M.n_ecol; ++col) {
-                const int beg = M.ecol_off[col], end = M.ecol_off[col + 1];
-                for (int q = beg + tid; q < end; q += BLOCK) {
-                    float lam = (carry && it > 0) ? lam_e[q] : 0.f;
-                    project_edge(X, __ldg(M.edge_ab + q), __ldg(M.edge_d + q), at_d, M.min_len, lam);
-                    if (carry) lam_e[q] = lam;
+        for (int it = 0; it < S.iterations && !failed; ++it) {
+            for (int c = 0; c < n_seg; ++c, ++k) {
+                const int4 sg = segs[c];
+                const unsigned char* base = M.recs + sg.x;
+                bool ok = true;
+                if (RING) {
+                    if (tid == 0 && k + 1 < K) {
+                        // The other stage was read during colour k-1, which
+                        // every thread finished before the last barrier.
+                        const int4 nx = segs[(c + 1 == n_seg) ? 0 : c + 1];
+                        uint64_t* b = &mbar[(k + 1) & 1];
+                        mbar_expect_tx(b, uint32_t(nx.y));
+                        bulk_copy_g2s(ring + ((k + 1) & 1) * M.ring_bytes, M.recs + nx.x, uint32_t(nx.y), b);
+                    }
+                    ok = mbar_wait_bounded(&mbar[k & 1], uint32_t((k >> 1) & 1));
+                    base = ring + (k & 1) * M.ring_bytes;
                 }
-                __syncthreads();
-            }
-            for (int col = 0; col < M.n_tcol; ++col) {
-                const int beg = M.tcol_off[col], end = M.tcol_off[col + 1];
-                for (int q = beg + tid; q < end; q += BLOCK) {
-                    float lam = (carry && it > 0) ? lam_t[q] : 0.f;
-                    project_tet(X, __ldg(M.tet_abcd + q), __ldg(M.tet_V0 + q), at_v, lam);
-                    if (carry) lam_t[q] = lam;
+                const bool carry = lam != nullptr;
+                if (ok) {
+                    if (c < n_ecol) {
+                        const uint2* rec = reinterpret_cast<const uint2*>(base);
+                        for (int q = tid; q < sg.z; q += BLOCK) {
+                            float l = (carry && it > 0) ? lam[sg.w + q] : 0.f;
+                            project_edge(X, rec[q], at_d, M.min_len2, l);
+                            if (carry) lam[sg.w + q] = l;
+                        }
+                    } else {
+                        const uint4* rec = reinterpret_cast<const uint4*>(base);
+                        for (int q = tid; q < sg.z; q += BLOCK) {
+                            float l = (carry && it > 0) ? lam[sg.w + q] : 0.f;
+                            project_tet(X, rec[q], at_v, l);
+                            if (carry) lam[sg.w + q] = l;
+                        }
+                    }
                 }
-                __syncthreads();
+                if (__syncthreads_or(!ok)) {
+                    failed = true;
+                    break;
+                }
             }
         }
+        if (failed) break;
         // Sphere-tool collision (Sec. III-A "Collisions"): a free vertex
-        // closer than r to the centre is moved onto the sphere along the
+        // closer than r to the centre moves onto the sphere along the
         // centre-to-vertex direction (straight up if it sits on the centre).
         const bool last = sub == S.substeps - 1;
-        for (int i = tid; i < V; i += BLOCK) {
-            float4 xi = X[i];
+        for (int s = tid; s < V; s += BLOCK) {
+            float4 xi = X[s];
             if (xi.w > 0.f) {
                 const float dx = xi.x - cx, dy = xi.y - cy, dz = xi.z - cz;
-                const float len = sqrtf(dx * dx + dy * dy + dz * dz);
-                if (len < r) {
+                const float l2 = dx * dx + dy * dy + dz * dz;
+                if (l2 < r2) {
+                    const float len = sqrtf(l2);
                     if (len > 0.f) {
-                        xi.x = cx + r * (dx / len);
-                        xi.y = cy + r * (dy / len);
-                        xi.z = cz + r * (dz / len);
+                        const float f = __fdividef(r, len);
+                        xi.x = cx + f * dx;
+                        xi.y = cy + f * dy;
+                        xi.z = cz + f * dz;
                     } else {
                         xi.x = cx;
                         xi.y = cy;
                         xi.z = cz + r;
                     }
-                    X[i] = xi;
-                    if (last) atomicOr(&bits[i >> 5], 1u << (i & 31));
+                    X[s] = xi;
+                    if (last) {
+                        const int i = M.vert_of[s];
+                        atomicOr(&bits[i >> 5], 1u << (i & 31));
+                    }
                 }
             }
         }
     }
+    if (failed) {
+        // A constraint copy did not arrive: drain the copy that may still be
+        // in flight (bounded), flag the env and leave the state untouched.
+        if (tid == 0) {
+            if (RING && k + 1 < K) mbar_wait_bounded(&mbar[(k + 1) & 1], uint32_t(((k + 1) >> 1) & 1));
+            S.err[env] |= kErrTimeout;
+        }
+        return;
+    }
     __syncthreads();
 
-    // Write back x and v = (x - x_prev) / h; flag non-finite positions.
+    // Write back x and v = (x - x_prev) / h in vertex order; flag non-finite positions.
     float* ox = S.x + ed.voff;
-    float* oy = ox + stride;
-    float* oz = oy + stride;
-    float* ovx = S.v + ed.voff;
-    float* ovy = ovx + stride;
-    float* ovz = ovy + stride;
+    float* ov = S.v + ed.voff;
     int bad = 0;
     for (int i = tid; i < V; i += BLOCK) {
-        const float4 xi = X[i];
+        const int s = M.slot_of[i];
+        const float4 xi = X[s];
         ox[i] = xi.x;
-        oy[i] = xi.y;
-        oz[i] = xi.z;
-        ovx[i] = (xi.x - Px[i]) / h;
-        ovy[i] = (xi.y - Py[i]) / h;
-        ovz[i] = (xi.z - Pz[i]) / h;
+        ox[stride + i] = xi.y;
+        ox[2 * stride + i] = xi.z;
+        ov[i] = (xi.x - Px[s]) * inv_h;
+        ov[stride + i] = (xi.y - Py[s]) * inv_h;
+        ov[2 * stride + i] = (xi.z - Pz[s]) * inv_h;
         bad |= !(isfinite(xi.x) && isfinite(xi.y) && isfinite(xi.z));
     }
     bad = __syncthreads_or(bad);
@@ -297,16 +403,16 @@ __global__ void __launch_bounds__(BLOCK) xpbd_step_kernel(SimDev S, const int* _
             if (j < 3) {
                 val = float(s_tool[j]);
             } else {
-                const int q = (j - 3) / 3, k = (j - 3) - 3 * q;
-                const float4 xv = X[ids[q]];
-                val = k == 0 ? xv.x : (k == 1 ? xv.y : xv.z);
+                const int q = (j - 3) / 3, kk = (j - 3) - 3 * q;
+                const float4 xv = X[M.slot_of[ids[q]]];
+                val = kk == 0 ? xv.x : (kk == 1 ? xv.y : xv.z);
             }
             o[j] = val;
         }
     }
     // Reward R = w_l l + w_d (l - l_prev) + w_s s and termination (Sec. IV, Sec. III-B).
     if (tid == 0) {
-        const float4 xt = X[S.target[env]];
+        const float4 xt = X[M.slot_of[S.target[env]]];
         const double dx = s_tool[0] - double(xt.x), dy = s_tool[1] - double(xt.y), dz = s_tool[2] - double(xt.z);
         const double l = sqrt(dx * dx + dy * dy + dz * dz);
         const int succ = l < S.success_dist;
@@ -316,7 +422,7 @@ __global__ void __launch_bounds__(BLOCK) xpbd_step_kernel(SimDev S, const int* _
         S.t_step[env] = t;
         if (reward) reward[env] = float(R);
         if (done) done[env] = uint8_t(((S.max_steps > 0 && t >= S.max_steps) || succ) ? 1 : 0);
-        if (bad) S.err[env] |= 1;
+        if (bad) S.err[env] |= kErrNonFinite;
     }
 }
 
@@ -404,7 +510,7 @@ __global__ void unpack_state_kernel(SimDev S, const int* __restrict__ pstart, co
 // Launchers
 // ---------------------------------------------------------------------------
 
-template <int BLOCK, bool RES>
+template <int BLOCK, bool RES, bool RING>
 static cudaError_t launch_one(const SimDev& S, const int* env_list, int n_blocks, size_t smem,
                               cudaStream_t st, const float* actions, float* obs, float* reward, uint8_t* done) {
     // Raise the kernel's dynamic shared-memory limit to what this launch needs
@@ -412,35 +518,40 @@ static cudaError_t launch_one(const SimDev& S, const int* env_list, int n_blocks
     // device's per-block opt-in maximum).
     static size_t configured = 48 * 1024;
     if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(xpbd_step_kernel<BLOCK, RES>,
+        cudaError_t e = cudaFuncSetAttribute(xpbd_step_kernel<BLOCK, RES, RING>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
         configured = smem;
     }
-    xpbd_step_kernel<BLOCK, RES><<<n_blocks, BLOCK, smem, st>>>(S, env_list, actions, obs, reward, done);
+    xpbd_step_kernel<BLOCK, RES, RING><<<n_blocks, BLOCK, smem, st>>>(S, env_list, actions, obs, reward, done);
     return cudaGetLastError();
 }
 
-template <bool RES>
+template <bool RES, bool RING>
 static cudaError_t launch_block(int block, const SimDev& S, const int* env_list, int n_blocks, size_t smem,
                                 cudaStream_t st, const float* a, float* o, float* r, uint8_t* d) {
     switch (block) {
-    case 128: return launch_one<128, RES>(S, env_list, n_blocks, smem, st, a, o, r, d);
-    case 256: return launch_one<256, RES>(S, env_list, n_blocks, smem, st, a, o, r, d);
-    case 384: return launch_one<384, RES>(S, env_list, n_blocks, smem, st, a, o, r, d);
-    case 512: return launch_one<512, RES>(S, env_list, n_blocks, smem, st, a, o, r, d);
-    case 768: return launch_one<768, RES>(S, env_list, n_blocks, smem, st, a, o, r, d);
-    case 1024: return launch_one<1024, RES>(S, env_list, n_blocks, smem, st, a, o, r, d);
+    case 128: return launch_one<128, RES, RING>(S, env_list, n_blocks, smem, st, a, o, r, d);
+    case 256: return launch_one<256, RES, RING>(S, env_list, n_blocks, smem, st, a, o, r, d);
+    case 384: return launch_one<384, RES, RING>(S, env_list, n_blocks, smem, st, a, o, r, d);
+    case 512: return launch_one<512, RES, RING>(S, env_list, n_blocks, smem, st, a, o, r, d);
+    case 768: return launch_one<768, RES, RING>(S, env_list, n_blocks, smem, st, a, o, r, d);
+    case 1024: return launch_one<1024, RES, RING>(S, env_list, n_blocks, smem, st, a, o, r, d);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_step(const SimDev& S, bool resident, int block, const int* env_list, int n_blocks,
+cudaError_t launch_step(const SimDev& S, bool resident, bool ring, int block, const int* env_list, int n_blocks,
                         size_t smem_bytes, cudaStream_t stream, const float* actions, float* obs,
                         float* reward, uint8_t* done) {
     if (n_blocks <= 0) return cudaSuccess;
-    return resident ? launch_block<true>(block, S, env_list, n_blocks, smem_bytes, stream, actions, obs, reward, done)
-                    : launch_block<false>(block, S, env_list, n_blocks, smem_bytes, stream, actions, obs, reward, done);
+    if (resident && ring)
+        return launch_block<true, true>(block, S, env_list, n_blocks, smem_bytes, stream, actions, obs, reward, done);
+    if (resident)
+        return launch_block<true, false>(block, S, env_list, n_blocks, smem_bytes, stream, actions, obs, reward, done);
+    if (ring)
+        return launch_block<false, true>(block, S, env_list, n_blocks, smem_bytes, stream, actions, obs, reward, done);
+    return launch_block<false, false>(block, S, env_list, n_blocks, smem_bytes, stream, actions, obs, reward, done);
 }
 
 cudaError_t launch_reset(const SimDev& S, const uint8_t* mask, unsigned long long seed, cudaStream_t st) {

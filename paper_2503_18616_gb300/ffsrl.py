@@ -51,13 +51,16 @@ class ffsrl_params(ctypes.Structure):
                 ("w_l", ctypes.c_double), ("w_d", ctypes.c_double), ("w_s", ctypes.c_double),
                 ("success_dist", ctypes.c_double), ("n_obs_verts", ctypes.c_int32),
                 ("max_steps", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("schedule_flags", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+SCHED_FORCE, SCHED_NO_PERMUTE, SCHED_NO_RING = 1, 2, 4
 
 
 class ffsrl_info(ctypes.Structure):
     _fields_ = [("n_env", ctypes.c_int32), ("n_meshes", ctypes.c_int32), ("obs_dim", ctypes.c_int32),
                 ("max_verts", ctypes.c_int32), ("total_verts", ctypes.c_int64),
-                ("block_threads", ctypes.c_int32), ("resident_envs", ctypes.c_int32)]
+                ("block_threads", ctypes.c_int32), ("resident_envs", ctypes.c_int32),
+                ("n_groups", ctypes.c_int32), ("ring_envs", ctypes.c_int32)]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -116,7 +119,7 @@ def _dptr(t) -> ctypes.c_void_p | None:
     return ctypes.c_void_p(t.data_ptr())
 
 
-def make_params(d: dict, block_threads: int = 0) -> ffsrl_params:
+def make_params(d: dict, block_threads: int = 0, schedule_flags: int = 0) -> ffsrl_params:
     p = ffsrl_params()
     p.dt = d["dt"]
     p.substeps = d["substeps"]
@@ -134,6 +137,7 @@ def make_params(d: dict, block_threads: int = 0) -> ffsrl_params:
     p.n_obs_verts = d["n_obs"]
     p.max_steps = d["max_steps"]
     p.block_threads = block_threads
+    p.schedule_flags = schedule_flags
     return p
 
 
@@ -141,7 +145,7 @@ class Sim:
     """Batched simulator handle (one ffsrl_sim)."""
 
     def __init__(self, meshes, params: dict, n_env: int, env_mesh=None, env_compliance=None,
-                 stream=None, block_threads: int = 0):
+                 stream=None, block_threads: int = 0, schedule_flags: int = 0):
         import torch
 
         self._torch = torch
@@ -166,7 +170,7 @@ class Sim:
             ec = np.ascontiguousarray(env_compliance, dtype=np.float64)
             self._keep.append(ec)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        p = make_params(params, block_threads)
+        p = make_params(params, block_threads, schedule_flags)
         h = ctypes.c_void_p()
         _check(L.ffsrl_create(arr, len(meshes), _np_ptr(em) if em is not None else None,
                               _np_ptr(ec) if ec is not None else None, n_env, ctypes.byref(p),
@@ -179,6 +183,8 @@ class Sim:
         self.total_verts = info.total_verts
         self.block_threads = info.block_threads
         self.resident_envs = info.resident_envs
+        self.n_groups = info.n_groups
+        self.ring_envs = info.ring_envs
         self.device = torch.device("cuda", torch.cuda.current_device())
 
     def close(self) -> None:

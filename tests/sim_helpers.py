@@ -10,11 +10,12 @@ from paper_2503_18616_gb300 import inputs
 POS_TOL = 1e-5          # max |x_gpu - x_oracle| / extent (FP32 path vs FP64 oracle)
 
 
-def make_sim(meshes, params, n_env, env_mesh=None, env_compliance=None, block_threads=0, seed=0):
+def make_sim(meshes, params, n_env, env_mesh=None, env_compliance=None, block_threads=0, seed=0,
+             schedule_flags=0):
     from paper_2503_18616_gb300 import build, ffsrl
     build.build()
     sim = ffsrl.Sim(meshes, params, n_env, env_mesh=env_mesh, env_compliance=env_compliance,
-                    block_threads=block_threads)
+                    block_threads=block_threads, schedule_flags=schedule_flags)
     sim.reset(seed)
     return sim
 

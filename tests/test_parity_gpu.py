@@ -327,3 +327,28 @@ def test_non_finite_state_is_reported_by_sync():
         sim.sync()
     assert ei.value.code == -5 and "env 1" in str(ei.value)
     sim.sync()   # flag cleared
+
+
+def test_every_schedule_gives_bit_identical_results():
+    """Slot permutation, record grouping, the TMA ring and the block size are
+    execution choices: constraints of one colour touch disjoint vertices, so
+    every schedule must give the same bits."""
+    from paper_2503_18616_gb300 import ffsrl
+    m = grid((9, 9, 5))
+    p = P(iterations=2, alpha_d=1e-4)
+    n_env, steps = 3, 12
+    ref = None
+    for flags in (0, ffsrl.SCHED_NO_PERMUTE, ffsrl.SCHED_NO_RING, ffsrl.SCHED_NO_PERMUTE | ffsrl.SCHED_NO_RING):
+        for block in (128, 256, 384, 512, 1024):
+            sim = make_sim([m], p, n_env, block_threads=block, schedule_flags=ffsrl.SCHED_FORCE | flags, seed=3)
+            assert sim.ring_envs == (0 if flags & ffsrl.SCHED_NO_RING else n_env)
+            for _ in range(steps):
+                obs, rew, done = sim.step()
+            x, v, _ = sim.get_state()
+            out = (x.cpu().numpy(), v.cpu().numpy(), obs.cpu().numpy(), rew.cpu().numpy())
+            if ref is None:
+                ref = out
+            else:
+                for a, b in zip(ref, out):
+                    assert np.array_equal(a, b), (flags, block)
+            sim.close()
