@@ -317,7 +317,8 @@ def run_ours(args):
         hbm_bytes = (BYTES_VERT * V + 4 * sim.obs_dim + 16) * n_env
         roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                     "frac": achieved / alu_peak, "traffic": traffic,
-                    "kernel": f"xpbd_step_kernel<{sim.block_threads},resident,{'ring' if sim.ring_envs else 'l2'}>",
+                    "kernel": f"xpbd_step_kernel<{sim.block_threads},{sim.envs_per_cta},resident,"
+                              f"{'ring' if sim.ring_envs else 'l2'}>",
                     "peak_source": f"{N_SM} SMs x {FP32_LANES} FP32 lanes x 2 x {clock_mhz:.0f} MHz "
                                    f"(max SM clock, {peak_src})",
                     "algorithmic_flops_per_launch": flops,
@@ -357,7 +358,8 @@ def run_ours(args):
                            "iterations": params["iterations"], "actions": "device counter-based draws",
                            "l2": f"state {2 * 12 * V * n_env / 1e6:.0f} MB > 129 MB L2, no flush",
                            "parallelism": f"env-sharded x{world}",
-                           "schedule": {"block_threads": sim.block_threads, "tma_ring_envs": sim.ring_envs,
+                           "schedule": {"threads_per_env": sim.block_threads, "envs_per_cta": sim.envs_per_cta,
+                                        "tma_ring_envs": sim.ring_envs,
                                         "resident_envs": sim.resident_envs, "launch_groups": sim.n_groups}},
                 "roofline": roofline, "cpu_baseline": cpu, "accuracy": acc, "e2e": e2e,
                 "gpu_launches": args.steps * sim.n_groups, "clocks": clk}

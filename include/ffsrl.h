@@ -76,7 +76,8 @@ typedef struct {
     double success_dist;      /* s = 1 when l < success_dist (3 mm in Sec. IV) */
     int32_t n_obs_verts;      /* sampled top-surface vertices in the observation */
     int32_t max_steps;        /* done when the step count reaches this (0 = never) */
-    int32_t block_threads;    /* CUDA threads per environment; 0 = autotuned */
+    int32_t block_threads;    /* CUDA threads per environment (128, 256, 384, 512
+                                 or 1024); 0 = autotuned (256 when forced) */
     int32_t schedule_flags;   /* 0 = autotuned; else FFSRL_SCHED_* bits forcing a schedule */
     int32_t reserved[4];      /* must be zero */
 } ffsrl_params;
@@ -86,6 +87,8 @@ typedef struct {
 #define FFSRL_SCHED_FORCE 1       /* use the bits below instead of autotuning them */
 #define FFSRL_SCHED_NO_PERMUTE 2  /* keep vertex order in shared memory, colour order of records */
 #define FFSRL_SCHED_NO_RING 4     /* read constraint records from L2 instead of the TMA ring */
+#define FFSRL_SCHED_ENVS2 8       /* two envs per CTA sharing one ring (else one) */
+#define FFSRL_SCHED_ENVS4 16      /* four envs per CTA sharing one ring */
 
 /* Sizes of a created simulator. */
 typedef struct {
@@ -94,10 +97,12 @@ typedef struct {
     int32_t obs_dim;          /* 3 + 3 * n_obs_verts */
     int32_t max_verts;        /* largest V over the meshes */
     int64_t total_verts;      /* sum over envs of their mesh's V (packed rows) */
-    int32_t block_threads;    /* threads per environment in use (largest group) */
+    int32_t block_threads;    /* CUDA threads per env in use (largest group) */
     int32_t resident_envs;    /* envs whose state stays in shared memory */
     int32_t n_groups;         /* step-kernel launches per step */
     int32_t ring_envs;        /* envs whose constraint records stream through the TMA ring */
+    int32_t envs_per_cta;     /* envs sharing one CTA (largest group) */
+    int32_t reserved;
 } ffsrl_info;
 
 /* Creates n_env environments; env e uses meshes[env_mesh[e]] (env_mesh NULL:

@@ -43,8 +43,8 @@ struct LaunchGroup {
     int mesh = 0;
     int n = 0;
     int* d_list = nullptr;
-    bool resident = false, ring = false, permute = true;
-    int block = 256;
+    StepConfig cfg;
+    bool permute = true;
     size_t smem = 0;
 };
 
@@ -58,14 +58,15 @@ struct TuneKey {
     }
 };
 struct TuneChoice {
-    int block;
-    bool ring, permute;
+    StepConfig cfg;
+    bool permute;
     float ms;
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneChoice> g_tune_cache;
 
-const int kBlocks[] = {128, 256, 384, 512};
+const int kSubs[] = {128, 256, 384, 512};
+const int kEnvsPerCta[] = {1, 2, 4};
 
 }  // namespace
 
@@ -122,10 +123,13 @@ int check_params(const ffsrl_params& p) {
     if (p.n_obs_verts < 0) return fail(FFSRL_E_INVAL, "n_obs_verts must be >= 0");
     if (p.max_steps < 0) return fail(FFSRL_E_INVAL, "max_steps must be >= 0");
     const int b = p.block_threads;
-    if (b != 0 && b != 128 && b != 256 && b != 384 && b != 512 && b != 768 && b != 1024)
-        return fail(FFSRL_E_INVAL, "block_threads must be 0, 128, 256, 384, 512, 768 or 1024");
-    if (p.schedule_flags & ~(FFSRL_SCHED_FORCE | FFSRL_SCHED_NO_PERMUTE | FFSRL_SCHED_NO_RING))
+    if (b != 0 && b != 128 && b != 256 && b != 384 && b != 512 && b != 1024)
+        return fail(FFSRL_E_INVAL, "block_threads must be 0, 128, 256, 384, 512 or 1024");
+    if (p.schedule_flags & ~(FFSRL_SCHED_FORCE | FFSRL_SCHED_NO_PERMUTE | FFSRL_SCHED_NO_RING |
+                             FFSRL_SCHED_ENVS2 | FFSRL_SCHED_ENVS4))
         return fail(FFSRL_E_INVAL, "unknown schedule_flags bits");
+    if ((p.schedule_flags & FFSRL_SCHED_ENVS2) && (p.schedule_flags & FFSRL_SCHED_ENVS4))
+        return fail(FFSRL_E_INVAL, "FFSRL_SCHED_ENVS2 and FFSRL_SCHED_ENVS4 are exclusive");
     for (int k = 0; k < 4; ++k)
         if (p.reserved[k] != 0) return fail(FFSRL_E_INVAL, "reserved params must be zero");
     return FFSRL_OK;
@@ -180,83 +184,99 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, bool permute, MeshDev& d) {
     return FFSRL_OK;
 }
 
-// Shared memory a group needs, or 0 if the configuration does not fit.
-size_t group_smem(const ffsrl_sim* s, const MeshDev& d, bool resident, bool ring) {
-    const size_t b = step_smem_bytes(d.Vp, resident, ring, d.ring_bytes, d.n_seg);
-    return b + 128 <= s->max_smem ? b : 0;  // 128 B left for the kernel's static shared memory
+// Shared memory a configuration needs, or 0 if it is not compiled or does not fit.
+size_t group_smem(const ffsrl_sim* s, const MeshDev& d, const StepConfig& c) {
+    if (!step_config_supported(c.sub, c.envs, c.resident, c.ring)) return 0;
+    const size_t b = step_smem_bytes(d.Vp, c.resident, c.ring, d.ring_bytes, d.n_seg, c.envs);
+    return b + 256 <= s->max_smem ? b : 0;  // room for the kernel's static shared memory
 }
 
 cudaError_t launch_group(ffsrl_sim* s, const LaunchGroup& g, const float* a, float* o, float* r, uint8_t* d) {
     SimDev S = s->S;
     S.meshes = s->d_meshes[g.permute ? 1 : 0];
-    return launch_step(S, g.resident, g.ring, g.block, g.d_list, g.n, g.smem, s->stream, a, o, r, d);
+    return launch_step(S, g.cfg, g.d_list, g.n, g.smem, s->stream, a, o, r, d);
 }
 
 // Times candidate schedules of one group on its own envs (device-drawn
-// actions, no outputs) and keeps the fastest. The envs are reset afterwards.
+// actions, no outputs) and keeps the fastest: threads per env, envs per CTA,
+// the TMA ring and the bank-aware slot permutation. The envs are reset
+// afterwards by the caller.
 int autotune_group(ffsrl_sim* s, LaunchGroup& g) {
     const ffsrl_params& p = s->params;
     const HostMesh& m = s->meshes[g.mesh];
     const TuneKey key{m.V, m.E, m.T, g.n, p.substeps, p.iterations};
     const bool force_sched = (p.schedule_flags & FFSRL_SCHED_FORCE) != 0;
-    {
+    const bool resident = g.cfg.resident;
+    if (!p.block_threads && !force_sched) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end() && !p.block_threads && !force_sched) {
-            g.block = it->second.block;
-            g.ring = it->second.ring && group_smem(s, s->h_meshes[1][g.mesh], g.resident, true);
+        if (it != g_tune_cache.end() && it->second.cfg.resident == resident) {
+            g.cfg = it->second.cfg;
             g.permute = it->second.permute;
-            g.smem = group_smem(s, s->h_meshes[g.permute][g.mesh], g.resident, g.ring);
-            return FFSRL_OK;
+            g.smem = group_smem(s, s->h_meshes[g.permute][g.mesh], g.cfg);
+            if (g.smem) return FFSRL_OK;
         }
     }
-    std::vector<int> blocks;
-    if (p.block_threads) blocks.push_back(p.block_threads);
-    else blocks.assign(std::begin(kBlocks), std::end(kBlocks));
-    std::vector<std::pair<bool, bool>> scheds;  // (permute, ring)
+    std::vector<StepConfig> cands;
+    std::vector<bool> perms;
+    const bool force_perm = !(p.schedule_flags & FFSRL_SCHED_NO_PERMUTE);
+    const bool force_ring = !(p.schedule_flags & FFSRL_SCHED_NO_RING);
     if (force_sched) {
-        scheds.push_back({!(p.schedule_flags & FFSRL_SCHED_NO_PERMUTE), !(p.schedule_flags & FFSRL_SCHED_NO_RING)});
+        // one forced candidate: block_threads (default 256) per env, envs per CTA from the flags
+        StepConfig c;
+        c.sub = p.block_threads ? p.block_threads : 256;
+        c.envs = (p.schedule_flags & FFSRL_SCHED_ENVS4) ? 4 : (p.schedule_flags & FFSRL_SCHED_ENVS2) ? 2 : 1;
+        c.resident = resident;
+        c.ring = force_ring;
+        cands.push_back(c);
     } else {
-        scheds = {{true, true}, {true, false}, {false, true}, {false, false}};
+        const std::vector<int> subs = p.block_threads ? std::vector<int>{p.block_threads}
+                                                      : std::vector<int>(std::begin(kSubs), std::end(kSubs));
+        for (int envs : kEnvsPerCta)
+            for (int sub : subs)
+                for (int ring = 1; ring >= 0; --ring) {
+                    StepConfig c;
+                    c.sub = sub;
+                    c.envs = envs;
+                    c.resident = resident;
+                    c.ring = ring;
+                    cands.push_back(c);
+                }
     }
-    cudaEvent_t e0, e1;
-    FFSRL_CUDA(cudaEventCreate(&e0));
-    FFSRL_CUDA(cudaEventCreate(&e1));
-    TuneChoice best{0, false, false, 1e30f};
-    int tried = 0;
-    for (auto [perm, ring] : scheds) {
-        if (ring && !group_smem(s, s->h_meshes[perm][g.mesh], g.resident, true)) continue;
-        for (int b : blocks) {
+    std::vector<int> perm_opts = force_sched ? std::vector<int>{force_perm ? 1 : 0} : std::vector<int>{1, 0};
+    struct Cand { StepConfig c; bool perm; size_t smem; };
+    std::vector<Cand> feasible;
+    for (const StepConfig& c : cands)
+        for (int pm : perm_opts) {
+            const size_t sm = group_smem(s, s->h_meshes[pm][g.mesh], c);
+            if (sm) feasible.push_back({c, bool(pm), sm});
+        }
+    if (feasible.empty()) return fail(FFSRL_E_INVAL, "no step schedule fits this device");
+    TuneChoice best{feasible[0].c, feasible[0].perm, 1e30f};
+    if (feasible.size() > 1) {
+        cudaEvent_t e0, e1;
+        FFSRL_CUDA(cudaEventCreate(&e0));
+        FFSRL_CUDA(cudaEventCreate(&e1));
+        for (const Cand& cd : feasible) {
             LaunchGroup c = g;
-            c.block = b;
-            c.ring = ring;
-            c.permute = perm;
-            c.smem = group_smem(s, s->h_meshes[perm][g.mesh], g.resident, ring);
-            if (!c.smem) continue;
-            const int reps = (blocks.size() * scheds.size() == 1) ? 0 : 2;
-            if (reps == 0) {
-                best = {b, ring, perm, 0.f};
-                ++tried;
-                continue;
-            }
+            c.cfg = cd.c;
+            c.permute = cd.perm;
+            c.smem = cd.smem;
             FFSRL_CUDA(launch_group(s, c, nullptr, nullptr, nullptr, nullptr));  // warm-up
             FFSRL_CUDA(cudaEventRecord(e0, s->stream));
-            for (int i = 0; i < reps; ++i) FFSRL_CUDA(launch_group(s, c, nullptr, nullptr, nullptr, nullptr));
+            for (int i = 0; i < 2; ++i) FFSRL_CUDA(launch_group(s, c, nullptr, nullptr, nullptr, nullptr));
             FFSRL_CUDA(cudaEventRecord(e1, s->stream));
             FFSRL_CUDA(cudaEventSynchronize(e1));
             float ms = 0;
             FFSRL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            ++tried;
-            if (ms < best.ms) best = {b, ring, perm, ms};
+            if (ms < best.ms) best = {cd.c, cd.perm, ms};
         }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    if (!tried) return fail(FFSRL_E_INVAL, "no step schedule fits this device");
-    g.block = best.block;
-    g.ring = best.ring;
+    g.cfg = best.cfg;
     g.permute = best.permute;
-    g.smem = group_smem(s, s->h_meshes[g.permute][g.mesh], g.resident, g.ring);
+    g.smem = group_smem(s, s->h_meshes[g.permute][g.mesh], g.cfg);
     if (!p.block_threads && !force_sched) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = best;
@@ -359,8 +379,11 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
         LaunchGroup g;
         g.mesh = int(mi);
         g.n = int(list.size());
-        g.resident = group_smem(s, md[mi], true, false) != 0;
-        any_streaming |= !g.resident;
+        StepConfig probe;
+        probe.sub = 128;
+        probe.ring = false;
+        g.cfg.resident = group_smem(s, md[mi], probe) != 0;
+        any_streaming |= !g.cfg.resident;
         FFSRL_CUDA(s->upload(&g.d_list, list.data(), list.size()));
         s->groups.push_back(g);
     }
@@ -383,8 +406,8 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
     for (LaunchGroup& g : s->groups) {
         int rc = autotune_group(s, g);
         if (rc) return rc;
-        if (g.resident) s->resident_envs += g.n;
-        if (g.ring) s->ring_envs += g.n;
+        if (g.cfg.resident) s->resident_envs += g.n;
+        if (g.cfg.ring) s->ring_envs += g.n;
     }
     return FFSRL_OK;
 }
@@ -542,7 +565,8 @@ int ffsrl_get_info(const ffsrl_sim* sim, ffsrl_info* out) {
     for (const HostMesh& m : sim->meshes) mv = std::max(mv, m.V);
     out->max_verts = mv;
     out->total_verts = sim->total_verts;
-    out->block_threads = sim->groups.empty() ? 0 : sim->groups.front().block;
+    out->block_threads = sim->groups.empty() ? 0 : sim->groups.front().cfg.sub;
+    out->envs_per_cta = sim->groups.empty() ? 0 : sim->groups.front().cfg.envs;
     out->resident_envs = sim->resident_envs;
     out->n_groups = int(sim->groups.size());
     out->ring_envs = sim->ring_envs;

@@ -9,12 +9,24 @@
 
 namespace ffsrl {
 
-// Dynamic shared memory of one step CTA: positions (resident only), the
-// two-stage constraint ring (ring only), the segment table and contact bits.
-size_t step_smem_bytes(int Vp, bool resident, bool ring, int ring_bytes, int n_seg);
+// Execution schedule of one step-kernel launch.
+struct StepConfig {
+    int sub = 256;        // threads per env
+    int envs = 1;         // envs per CTA (sharing one constraint ring)
+    bool resident = true; // positions in shared memory
+    bool ring = true;     // constraint records through the TMA double buffer
+};
 
-// Step kernel over n_blocks envs (env_list NULL: envs 0..n_blocks-1).
-cudaError_t launch_step(const SimDev& S, bool resident, bool ring, int block, const int* env_list, int n_blocks,
+// Dynamic shared memory of one step CTA: positions of its envs (resident
+// only), the two-stage constraint ring (ring only), the segment table and
+// contact bits.
+size_t step_smem_bytes(int Vp, bool resident, bool ring, int ring_bytes, int n_seg, int envs);
+
+// Whether a (sub, envs, resident, ring) combination is compiled.
+bool step_config_supported(int sub, int envs, bool resident, bool ring);
+
+// Step kernel over the n_list envs of env_list (NULL: envs 0..n_list-1), all of one mesh.
+cudaError_t launch_step(const SimDev& S, const StepConfig& c, const int* env_list, int n_list,
                         size_t smem_bytes, cudaStream_t stream, const float* actions, float* obs,
                         float* reward, uint8_t* done);
 cudaError_t launch_reset(const SimDev& S, const uint8_t* mask, unsigned long long seed, cudaStream_t st);

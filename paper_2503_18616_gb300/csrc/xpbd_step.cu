@@ -139,22 +139,23 @@ __device__ __forceinline__ void project_tet(float4* X, uint4 rec, float at, floa
 
 __host__ __device__ __forceinline__ size_t align128(size_t b) { return (b + 127) / 128 * 128; }
 
-// Dynamic shared-memory layout: [X (resident only)] [ring (2 stages)] [segment table] [contact bits]
+// Dynamic shared-memory layout of a CTA holding `envs` envs:
+// [X of each env (resident only)] [ring (2 stages, shared)] [segment table] [contact bits of each env]
 struct SmemLayout {
     size_t x_off, ring_off, seg_off, bits_off, total;
-    __host__ __device__ SmemLayout(int Vp, bool res, bool ring, int ring_bytes, int n_seg) {
+    __host__ __device__ SmemLayout(int Vp, bool res, bool ring, int ring_bytes, int n_seg, int envs) {
         x_off = 0;
-        ring_off = align128(res ? size_t(Vp) * 16 : 0);
+        ring_off = align128(res ? size_t(envs) * Vp * 16 : 0);
         seg_off = align128(ring_off + (ring ? 2 * size_t(ring_bytes) : 0));
         bits_off = align128(seg_off + size_t(n_seg) * 16);
-        total = bits_off + size_t(Vp / 32) * 4;
+        total = bits_off + size_t(envs) * (Vp / 32) * 4;
     }
 };
 
 }  // namespace
 
-size_t step_smem_bytes(int Vp, bool resident, bool ring, int ring_bytes, int n_seg) {
-    return SmemLayout(Vp, resident, ring, ring_bytes, n_seg).total;
+size_t step_smem_bytes(int Vp, bool resident, bool ring, int ring_bytes, int n_seg, int envs) {
+    return SmemLayout(Vp, resident, ring, ring_bytes, n_seg, envs).total;
 }
 
 // CTAs per SM the register allocation targets for each block size (about 85
@@ -163,54 +164,60 @@ constexpr int min_ctas_per_sm(int block) {
     return block <= 128 ? 6 : block <= 256 ? 3 : block <= 512 ? 2 : 1;
 }
 
-template <int BLOCK, bool RES, bool RING>
-__global__ void __launch_bounds__(BLOCK, min_ctas_per_sm(BLOCK)) xpbd_step_kernel(SimDev S, const int* __restrict__ env_list,
-                                                          const float* __restrict__ actions,
-                                                          float* __restrict__ obs,
-                                                          float* __restrict__ reward,
-                                                          uint8_t* __restrict__ done) {
+// One CTA advances ENVS environments of the same mesh, SUB threads each; the
+// envs share the constraint ring and the CTA's barriers.
+template <int SUB, int ENVS, bool RES, bool RING>
+__global__ void __launch_bounds__(SUB * ENVS, min_ctas_per_sm(SUB * ENVS))
+    xpbd_step_kernel(SimDev S, const int* __restrict__ env_list, int n_list, const float* __restrict__ actions,
+                     float* __restrict__ obs, float* __restrict__ reward, uint8_t* __restrict__ done) {
+    constexpr int BLOCK = SUB * ENVS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ double s_tool[3];
+    __shared__ double s_tool[ENVS][3];
 
-    const int env = env_list ? env_list[blockIdx.x] : int(blockIdx.x);
     const int tid = threadIdx.x;
+    const int el = ENVS == 1 ? 0 : tid / SUB;   // env slot of this thread in the CTA
+    const int st = ENVS == 1 ? tid : tid % SUB; // thread index inside the env's subgroup
+    const int li = blockIdx.x * ENVS + el;
+    const bool active = li < n_list;
+    const int env = active ? (env_list ? env_list[li] : li) : 0;
     const EnvDev ed = S.envs[env];
-    const MeshDev M = S.meshes[ed.mesh];
+    const int mesh = S.envs[env_list ? env_list[blockIdx.x * ENVS] : blockIdx.x * ENVS].mesh;
+    const MeshDev M = S.meshes[mesh];
     const int V = M.V, Vp = M.Vp, n_seg = M.n_seg, n_ecol = M.n_ecol;
     const long long stride = S.stride;
-    const SmemLayout L(Vp, RES, RING, M.ring_bytes, n_seg);
+    const SmemLayout L(Vp, RES, RING, M.ring_bytes, n_seg, ENVS);
 
-    float4* X = RES ? reinterpret_cast<float4*>(smem_raw + L.x_off) : S.xg + ed.voff;
+    float4* X = RES ? reinterpret_cast<float4*>(smem_raw + L.x_off) + size_t(el) * Vp : S.xg + ed.voff;
     unsigned char* ring = smem_raw + L.ring_off;
     int4* segs = reinterpret_cast<int4*>(smem_raw + L.seg_off);
-    unsigned* bits = reinterpret_cast<unsigned*>(smem_raw + L.bits_off);
+    unsigned* bits = reinterpret_cast<unsigned*>(smem_raw + L.bits_off) + size_t(el) * (Vp / 32);
     float* Px = S.pg + ed.voff;
     float* Py = Px + stride;
     float* Pz = Py + stride;
 
     const int K = S.substeps * S.iterations * n_seg;  // colour phases in this step
     for (int c = tid; c < n_seg; c += BLOCK) segs[c] = M.segs[c];
-    for (int w = tid; w < Vp / 32; w += BLOCK) bits[w] = 0u;
-    if (tid == 0) {
-        if (RING) {
-            mbar_init(&mbar[0], 1);
-            mbar_init(&mbar[1], 1);
-            fence_mbar_init();
-        }
+    for (int w = st; w < Vp / 32; w += SUB) bits[w] = 0u;
+    if (RING && tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+    }
+    if (st == 0 && active) {
         // Tool update once per step (Algorithm 1, "evaluate instrument
         // state"): c <- clamp(c + scale * a), a from the caller or from the
         // env's counter-based stream at its step count. Rounded product then
         // rounded sum, so the float64 tool position is reproducible.
         const unsigned long long t = (unsigned long long)S.t_step[env];
-        const unsigned long long st = env_stream(S.seed[env], (unsigned long long)env, 0u);
+        const unsigned long long rs = env_stream(S.seed[env], (unsigned long long)env, 0u);
         for (int k = 0; k < 3; ++k) {
-            const double a = actions ? (double)actions[3 * env + k] : to_unit_pm1(splitmix64_nth(st, 3ull * t + k));
+            const double a = actions ? (double)actions[3 * env + k] : to_unit_pm1(splitmix64_nth(rs, 3ull * t + k));
             double c = __dadd_rn(S.tool[3 * env + k], __dmul_rn(S.action_scale, a));
             c = c < M.box_lo[k] ? M.box_lo[k] : c;
             c = c > M.box_hi[k] ? M.box_hi[k] : c;
             S.tool[3 * env + k] = c;
-            s_tool[k] = c;
+            s_tool[el][k] = c;
         }
     }
     __syncthreads();
@@ -223,12 +230,12 @@ __global__ void __launch_bounds__(BLOCK, min_ctas_per_sm(BLOCK)) xpbd_step_kerne
 
     const float h = S.h, inv_h = S.inv_h;
     const float hgx = h * S.gx, hgy = h * S.gy, hgz = h * S.gz;
-    {
+    if (active) {
         // Load the state (vertex order, coalesced) into slot order and predict
         // for the first substep (Algorithm 1: v~ = v + h g, x~ = x + h v~).
         const float* gx = S.x + ed.voff;
         const float* gv = S.v + ed.voff;
-        for (int i = tid; i < V; i += BLOCK) {
+        for (int i = st; i < V; i += SUB) {
             const int s = M.slot_of[i];
             float4 xi = make_float4(gx[i], gx[stride + i], gx[2 * stride + i], M.rest_w[i].w);
             Px[s] = xi.x;
@@ -244,7 +251,7 @@ __global__ void __launch_bounds__(BLOCK, min_ctas_per_sm(BLOCK)) xpbd_step_kerne
     }
     __syncthreads();
 
-    const float cx = float(s_tool[0]), cy = float(s_tool[1]), cz = float(s_tool[2]);
+    const float cx = float(s_tool[el][0]), cy = float(s_tool[el][1]), cz = float(s_tool[el][2]);
     const float r = S.radius, r2 = r * r;
     const float at_d = ed.alpha_d, at_v = S.alpha_v;
     float* lam = S.lambda ? S.lambda + ed.loff : nullptr;
@@ -252,24 +259,6 @@ __global__ void __launch_bounds__(BLOCK, min_ctas_per_sm(BLOCK)) xpbd_step_kerne
     bool failed = false;
 
     for (int sub = 0; sub < S.substeps && !failed; ++sub) {
-        if (sub > 0) {
-            // Velocity update of the previous substep, v = (x - x_prev) / h,
-            // fused with this substep's prediction.
-            for (int s = tid; s < V; s += BLOCK) {
-                float4 xi = X[s];
-                const float vx = (xi.x - Px[s]) * inv_h, vy = (xi.y - Py[s]) * inv_h, vz = (xi.z - Pz[s]) * inv_h;
-                Px[s] = xi.x;
-                Py[s] = xi.y;
-                Pz[s] = xi.z;
-                if (xi.w > 0.f) {
-                    xi.x += h * (vx + hgx);
-                    xi.y += h * (vy + hgy);
-                    xi.z += h * (vz + hgz);
-                    X[s] = xi;
-                }
-            }
-            __syncthreads();
-        }
         for (int it = 0; it < S.iterations && !failed; ++it) {
             for (int c = 0; c < n_seg; ++c, ++k) {
                 const int4 sg = segs[c];
@@ -288,17 +277,17 @@ __global__ void __launch_bounds__(BLOCK, min_ctas_per_sm(BLOCK)) xpbd_step_kerne
                     base = ring + (k & 1) * M.ring_bytes;
                 }
                 const bool carry = lam != nullptr;
-                if (ok) {
+                if (ok && active) {
                     if (c < n_ecol) {
                         const uint2* rec = reinterpret_cast<const uint2*>(base);
-                        for (int q = tid; q < sg.z; q += BLOCK) {
+                        for (int q = st; q < sg.z; q += SUB) {
                             float l = (carry && it > 0) ? lam[sg.w + q] : 0.f;
                             project_edge(X, rec[q], at_d, M.min_len2, l);
                             if (carry) lam[sg.w + q] = l;
                         }
                     } else {
                         const uint4* rec = reinterpret_cast<const uint4*>(base);
-                        for (int q = tid; q < sg.z; q += BLOCK) {
+                        for (int q = st; q < sg.z; q += SUB) {
                             float l = (carry && it > 0) ? lam[sg.w + q] : 0.f;
                             project_tet(X, rec[q], at_v, l);
                             if (carry) lam[sg.w + q] = l;
@@ -315,12 +304,23 @@ __global__ void __launch_bounds__(BLOCK, min_ctas_per_sm(BLOCK)) xpbd_step_kerne
         // Sphere-tool collision (Sec. III-A "Collisions"): a free vertex
         // closer than r to the centre moves onto the sphere along the
         // centre-to-vertex direction (straight up if it sits on the centre).
+        // Except after the last substep, the same pass performs the velocity
+        // update v = (x - x_prev) / h and the next substep's prediction.
         const bool last = sub == S.substeps - 1;
-        for (int s = tid; s < V; s += BLOCK) {
-            float4 xi = X[s];
-            if (xi.w > 0.f) {
+        if (active) {
+            for (int s = st; s < V; s += SUB) {
+                float4 xi = X[s];
+                if (!(xi.w > 0.f)) {
+                    if (!last) {
+                        Px[s] = xi.x;
+                        Py[s] = xi.y;
+                        Pz[s] = xi.z;
+                    }
+                    continue;
+                }
                 const float dx = xi.x - cx, dy = xi.y - cy, dz = xi.z - cz;
                 const float l2 = dx * dx + dy * dy + dz * dz;
+                bool moved = false;
                 if (l2 < r2) {
                     const float len = sqrtf(l2);
                     if (len > 0.f) {
@@ -333,31 +333,42 @@ __global__ void __launch_bounds__(BLOCK, min_ctas_per_sm(BLOCK)) xpbd_step_kerne
                         xi.y = cy;
                         xi.z = cz + r;
                     }
-                    X[s] = xi;
+                    moved = true;
                     if (last) {
                         const int i = M.vert_of[s];
                         atomicOr(&bits[i >> 5], 1u << (i & 31));
                     }
                 }
+                if (!last) {
+                    const float vx = (xi.x - Px[s]) * inv_h, vy = (xi.y - Py[s]) * inv_h,
+                                vz = (xi.z - Pz[s]) * inv_h;
+                    Px[s] = xi.x;
+                    Py[s] = xi.y;
+                    Pz[s] = xi.z;
+                    xi.x += h * (vx + hgx);
+                    xi.y += h * (vy + hgy);
+                    xi.z += h * (vz + hgz);
+                    moved = true;
+                }
+                if (moved) X[s] = xi;
             }
         }
+        __syncthreads();
     }
     if (failed) {
         // A constraint copy did not arrive: drain the copy that may still be
-        // in flight (bounded), flag the env and leave the state untouched.
-        if (tid == 0) {
-            if (RING && k + 1 < K) mbar_wait_bounded(&mbar[(k + 1) & 1], uint32_t(((k + 1) >> 1) & 1));
-            S.err[env] |= kErrTimeout;
-        }
+        // in flight (bounded), flag the envs and leave their state untouched.
+        if (tid == 0 && RING && k + 1 < K) mbar_wait_bounded(&mbar[(k + 1) & 1], uint32_t(((k + 1) >> 1) & 1));
+        if (st == 0 && active) atomicOr(&S.err[env], kErrTimeout);
         return;
     }
-    __syncthreads();
+    if (!active) return;  // no barrier below this point
 
     // Write back x and v = (x - x_prev) / h in vertex order; flag non-finite positions.
     float* ox = S.x + ed.voff;
     float* ov = S.v + ed.voff;
-    int bad = 0;
-    for (int i = tid; i < V; i += BLOCK) {
+    bool bad = false;
+    for (int i = st; i < V; i += SUB) {
         const int s = M.slot_of[i];
         const float4 xi = X[s];
         ox[i] = xi.x;
@@ -368,10 +379,10 @@ __global__ void __launch_bounds__(BLOCK, min_ctas_per_sm(BLOCK)) xpbd_step_kerne
         ov[2 * stride + i] = (xi.z - Pz[s]) * inv_h;
         bad |= !(isfinite(xi.x) && isfinite(xi.y) && isfinite(xi.z));
     }
-    bad = __syncthreads_or(bad);
+    if (bad) atomicOr(&S.err[env], kErrNonFinite);
 
-    // Contact list of the last substep, ascending vertex ids (warp 0).
-    const int lane = tid & 31, warp = tid >> 5;
+    // Contact list of the last substep, ascending vertex ids (first warp of the env).
+    const int lane = st & 31, warp = st >> 5;
     if (warp == 0) {
         const int nwords = Vp / 32;
         int base = 0;
@@ -398,10 +409,10 @@ __global__ void __launch_bounds__(BLOCK, min_ctas_per_sm(BLOCK)) xpbd_step_kerne
     if (obs) {
         float* o = obs + (long long)env * S.obs_dim;
         const int* ids = S.obs_ids + (long long)env * S.n_obs;
-        for (int j = tid; j < S.obs_dim; j += BLOCK) {
+        for (int j = st; j < S.obs_dim; j += SUB) {
             float val;
             if (j < 3) {
-                val = float(s_tool[j]);
+                val = float(s_tool[el][j]);
             } else {
                 const int q = (j - 3) / 3, kk = (j - 3) - 3 * q;
                 const float4 xv = X[M.slot_of[ids[q]]];
@@ -411,9 +422,10 @@ __global__ void __launch_bounds__(BLOCK, min_ctas_per_sm(BLOCK)) xpbd_step_kerne
         }
     }
     // Reward R = w_l l + w_d (l - l_prev) + w_s s and termination (Sec. IV, Sec. III-B).
-    if (tid == 0) {
+    if (st == 0) {
         const float4 xt = X[M.slot_of[S.target[env]]];
-        const double dx = s_tool[0] - double(xt.x), dy = s_tool[1] - double(xt.y), dz = s_tool[2] - double(xt.z);
+        const double dx = s_tool[el][0] - double(xt.x), dy = s_tool[el][1] - double(xt.y),
+                     dz = s_tool[el][2] - double(xt.z);
         const double l = sqrt(dx * dx + dy * dy + dz * dz);
         const int succ = l < S.success_dist;
         const double R = S.w_l * l + S.w_d * (l - double(S.l_prev[env])) + S.w_s * double(succ);
@@ -422,7 +434,6 @@ __global__ void __launch_bounds__(BLOCK, min_ctas_per_sm(BLOCK)) xpbd_step_kerne
         S.t_step[env] = t;
         if (reward) reward[env] = float(R);
         if (done) done[env] = uint8_t(((S.max_steps > 0 && t >= S.max_steps) || succ) ? 1 : 0);
-        if (bad) S.err[env] |= kErrNonFinite;
     }
 }
 
@@ -510,48 +521,57 @@ __global__ void unpack_state_kernel(SimDev S, const int* __restrict__ pstart, co
 // Launchers
 // ---------------------------------------------------------------------------
 
-template <int BLOCK, bool RES, bool RING>
-static cudaError_t launch_one(const SimDev& S, const int* env_list, int n_blocks, size_t smem,
-                              cudaStream_t st, const float* actions, float* obs, float* reward, uint8_t* done) {
+template <int SUB, int ENVS, bool RES, bool RING>
+static cudaError_t launch_one(const SimDev& S, const int* env_list, int n_list, size_t smem, cudaStream_t st,
+                              const float* actions, float* obs, float* reward, uint8_t* done) {
     // Raise the kernel's dynamic shared-memory limit to what this launch needs
     // (the limit plus the kernel's static shared memory must stay within the
     // device's per-block opt-in maximum).
     static size_t configured = 48 * 1024;
     if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(xpbd_step_kernel<BLOCK, RES, RING>,
+        cudaError_t e = cudaFuncSetAttribute(xpbd_step_kernel<SUB, ENVS, RES, RING>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
         configured = smem;
     }
-    xpbd_step_kernel<BLOCK, RES, RING><<<n_blocks, BLOCK, smem, st>>>(S, env_list, actions, obs, reward, done);
+    const int n_blocks = (n_list + ENVS - 1) / ENVS;
+    xpbd_step_kernel<SUB, ENVS, RES, RING>
+        <<<n_blocks, SUB * ENVS, smem, st>>>(S, env_list, n_list, actions, obs, reward, done);
     return cudaGetLastError();
 }
 
-template <bool RES, bool RING>
-static cudaError_t launch_block(int block, const SimDev& S, const int* env_list, int n_blocks, size_t smem,
-                                cudaStream_t st, const float* a, float* o, float* r, uint8_t* d) {
-    switch (block) {
-    case 128: return launch_one<128, RES, RING>(S, env_list, n_blocks, smem, st, a, o, r, d);
-    case 256: return launch_one<256, RES, RING>(S, env_list, n_blocks, smem, st, a, o, r, d);
-    case 384: return launch_one<384, RES, RING>(S, env_list, n_blocks, smem, st, a, o, r, d);
-    case 512: return launch_one<512, RES, RING>(S, env_list, n_blocks, smem, st, a, o, r, d);
-    case 768: return launch_one<768, RES, RING>(S, env_list, n_blocks, smem, st, a, o, r, d);
-    case 1024: return launch_one<1024, RES, RING>(S, env_list, n_blocks, smem, st, a, o, r, d);
-    default: return cudaErrorInvalidValue;
-    }
+bool step_config_supported(int sub, int envs, bool resident, bool ring) {
+    if (envs == 1) return sub == 128 || sub == 256 || sub == 384 || sub == 512 || sub == 1024;
+    if (!resident || !ring) return false;
+    if (envs == 2) return sub == 128 || sub == 256 || sub == 384 || sub == 512;
+    if (envs == 4) return sub == 128 || sub == 256;
+    return false;
 }
 
-cudaError_t launch_step(const SimDev& S, bool resident, bool ring, int block, const int* env_list, int n_blocks,
-                        size_t smem_bytes, cudaStream_t stream, const float* actions, float* obs,
-                        float* reward, uint8_t* done) {
-    if (n_blocks <= 0) return cudaSuccess;
-    if (resident && ring)
-        return launch_block<true, true>(block, S, env_list, n_blocks, smem_bytes, stream, actions, obs, reward, done);
-    if (resident)
-        return launch_block<true, false>(block, S, env_list, n_blocks, smem_bytes, stream, actions, obs, reward, done);
-    if (ring)
-        return launch_block<false, true>(block, S, env_list, n_blocks, smem_bytes, stream, actions, obs, reward, done);
-    return launch_block<false, false>(block, S, env_list, n_blocks, smem_bytes, stream, actions, obs, reward, done);
+cudaError_t launch_step(const SimDev& S, const StepConfig& c, const int* env_list, int n_list,
+                        size_t smem_bytes, cudaStream_t stream, const float* a, float* o, float* r,
+                        uint8_t* d) {
+    if (n_list <= 0) return cudaSuccess;
+#define FFSRL_CASE(SUB_, ENVS_, RES_, RING_)                                                      \
+    if (c.sub == SUB_ && c.envs == ENVS_ && c.resident == RES_ && c.ring == RING_)                \
+        return launch_one<SUB_, ENVS_, RES_, RING_>(S, env_list, n_list, smem_bytes, stream, a, o, r, d);
+#define FFSRL_CASE4(SUB_)                                                                         \
+    FFSRL_CASE(SUB_, 1, true, true) FFSRL_CASE(SUB_, 1, true, false) FFSRL_CASE(SUB_, 1, false, true) \
+    FFSRL_CASE(SUB_, 1, false, false)
+    FFSRL_CASE4(128)
+    FFSRL_CASE4(256)
+    FFSRL_CASE4(384)
+    FFSRL_CASE4(512)
+    FFSRL_CASE4(1024)
+    FFSRL_CASE(128, 2, true, true)
+    FFSRL_CASE(256, 2, true, true)
+    FFSRL_CASE(384, 2, true, true)
+    FFSRL_CASE(512, 2, true, true)
+    FFSRL_CASE(128, 4, true, true)
+    FFSRL_CASE(256, 4, true, true)
+#undef FFSRL_CASE4
+#undef FFSRL_CASE
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_reset(const SimDev& S, const uint8_t* mask, unsigned long long seed, cudaStream_t st) {

@@ -53,14 +53,15 @@ class ffsrl_params(ctypes.Structure):
                 ("max_steps", ctypes.c_int32), ("block_threads", ctypes.c_int32),
                 ("schedule_flags", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
-SCHED_FORCE, SCHED_NO_PERMUTE, SCHED_NO_RING = 1, 2, 4
+SCHED_FORCE, SCHED_NO_PERMUTE, SCHED_NO_RING, SCHED_ENVS2, SCHED_ENVS4 = 1, 2, 4, 8, 16
 
 
 class ffsrl_info(ctypes.Structure):
     _fields_ = [("n_env", ctypes.c_int32), ("n_meshes", ctypes.c_int32), ("obs_dim", ctypes.c_int32),
                 ("max_verts", ctypes.c_int32), ("total_verts", ctypes.c_int64),
                 ("block_threads", ctypes.c_int32), ("resident_envs", ctypes.c_int32),
-                ("n_groups", ctypes.c_int32), ("ring_envs", ctypes.c_int32)]
+                ("n_groups", ctypes.c_int32), ("ring_envs", ctypes.c_int32),
+                ("envs_per_cta", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -185,6 +186,7 @@ class Sim:
         self.resident_envs = info.resident_envs
         self.n_groups = info.n_groups
         self.ring_envs = info.ring_envs
+        self.envs_per_cta = info.envs_per_cta
         self.device = torch.device("cuda", torch.cuda.current_device())
 
     def close(self) -> None:

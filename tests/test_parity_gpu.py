@@ -166,13 +166,25 @@ def test_small_and_ragged_meshes(mesh):
 @pytest.mark.parametrize("iterations", [0, 2, 3])
 def test_iteration_counts_carry_lambda(iterations):
     m = grid((9, 9, 5))
-    # without constraints the unpinned tissue would free-fall far from its
-    # extent, so that case runs without gravity (the tool still acts)
-    grav = (0.0, 0.0, 0.0) if iterations == 0 else (0.0, 0.0, -9.81)
-    p = P(iterations=iterations, alpha_d=1e-4, alpha_v=1e-10, gravity=grav, radius=4e-3)
+    # without constraints nothing holds the tissue together, so that case runs
+    # without gravity and tool (free drift from a perturbed, moving start)
+    if iterations == 0:
+        p = P(iterations=0, gravity=(0.0, 0.0, 0.0), radius=0.0)
+    else:
+        p = P(iterations=iterations, alpha_d=1e-4, alpha_v=1e-10, radius=4e-3)
     n_env, steps = 2, 20
     sim = make_sim([m], p, n_env, seed=4)
     oenvs, _ = oracle_envs([m], p, n_env, seed=4)
+    if iterations == 0:
+        rest, w, _ = m
+        x32 = np.concatenate([inputs.perturbed_positions(rest, 3e-4, 20 + e, inv_mass=w) for e in range(n_env)])
+        v32 = np.random.default_rng(3).normal(0, 0.01, x32.shape)
+        v32[np.tile(w, n_env) == 0] = 0
+        x32, v32 = x32.astype(np.float32), v32.astype(np.float32)
+        sim.set_state(torch.from_numpy(x32).cuda(), torch.from_numpy(v32).cuda())
+        V = len(rest)
+        for e, oe in oenvs.items():
+            oe.set_state(x=x32[e * V:(e + 1) * V].astype(np.float64), v=v32[e * V:(e + 1) * V].astype(np.float64))
     for _ in range(steps):
         sim.step()
     for oe in oenvs.values():
@@ -231,7 +243,7 @@ def test_collision_contacts_bit_exact_on_identical_inputs():
 
 
 def test_uneven_meshes_per_env_compliance_and_streaming_path():
-    shapes = [(9, 9, 5), (13, 13, 7), (27, 27, 14)]     # the last exceeds one CTA's shared memory
+    shapes = [(9, 9, 5), (13, 13, 7), (33, 33, 17)]     # the last (18513 vertices) exceeds one CTA's shared memory
     meshes = [grid(s) for s in shapes]
     n_env, steps = 7, 8
     env_mesh = np.array([2, 0, 1, 2, 1, 0, 2], dtype=np.int32)
@@ -338,17 +350,25 @@ def test_every_schedule_gives_bit_identical_results():
     p = P(iterations=2, alpha_d=1e-4)
     n_env, steps = 3, 12
     ref = None
+    configs = []
     for flags in (0, ffsrl.SCHED_NO_PERMUTE, ffsrl.SCHED_NO_RING, ffsrl.SCHED_NO_PERMUTE | ffsrl.SCHED_NO_RING):
         for block in (128, 256, 384, 512, 1024):
-            sim = make_sim([m], p, n_env, block_threads=block, schedule_flags=ffsrl.SCHED_FORCE | flags, seed=3)
-            assert sim.ring_envs == (0 if flags & ffsrl.SCHED_NO_RING else n_env)
-            for _ in range(steps):
-                obs, rew, done = sim.step()
-            x, v, _ = sim.get_state()
-            out = (x.cpu().numpy(), v.cpu().numpy(), obs.cpu().numpy(), rew.cpu().numpy())
-            if ref is None:
-                ref = out
-            else:
-                for a, b in zip(ref, out):
-                    assert np.array_equal(a, b), (flags, block)
-            sim.close()
+            configs.append((flags, block))
+    for envs_flag, blocks in ((ffsrl.SCHED_ENVS2, (128, 256, 384, 512)), (ffsrl.SCHED_ENVS4, (128, 256))):
+        for flags in (0, ffsrl.SCHED_NO_PERMUTE):
+            for block in blocks:
+                configs.append((flags | envs_flag, block))
+    for flags, block in configs:
+        sim = make_sim([m], p, n_env, block_threads=block, schedule_flags=ffsrl.SCHED_FORCE | flags, seed=3)
+        assert sim.ring_envs == (0 if flags & ffsrl.SCHED_NO_RING else n_env)
+        assert sim.envs_per_cta == (4 if flags & ffsrl.SCHED_ENVS4 else 2 if flags & ffsrl.SCHED_ENVS2 else 1)
+        for _ in range(steps):
+            obs, rew, done = sim.step()
+        x, v, _ = sim.get_state()
+        out = (x.cpu().numpy(), v.cpu().numpy(), obs.cpu().numpy(), rew.cpu().numpy())
+        if ref is None:
+            ref = out
+        else:
+            for a, b in zip(ref, out):
+                assert np.array_equal(a, b), (flags, block)
+        sim.close()
