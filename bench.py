@@ -256,7 +256,13 @@ def run_ours(args):
 
     w, mesh, params = workload(args.workload)
     n_env = args.envs or w["n_env"]
-    sim = ffsrl.Sim([mesh], params, n_env)
+    block, flags = 0, 0
+    if args.schedule:   # forced schedule "threads_per_env:envs_per_cta:ring:permute" (profiling)
+        sub, envs, ring, perm = (int(x) for x in args.schedule.split(":"))
+        block = sub
+        flags = ffsrl.SCHED_FORCE | (0 if ring else ffsrl.SCHED_NO_RING) | (0 if perm else ffsrl.SCHED_NO_PERMUTE)
+        flags |= {1: 0, 2: ffsrl.SCHED_ENVS2, 4: ffsrl.SCHED_ENVS4}[envs]
+    sim = ffsrl.Sim([mesh], params, n_env, block_threads=block, schedule_flags=flags)
     seed = args.seed + 1000003 * rank          # each rank owns its own env shard
     sim.reset(seed)
     stream = sim.stream
@@ -382,6 +388,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--envs", type=int, default=0, help="override the workload's env count")
+    ap.add_argument("--schedule", default="", help="force threads_per_env:envs_per_cta:ring:permute")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

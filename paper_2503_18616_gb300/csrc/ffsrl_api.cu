@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -269,6 +270,9 @@ int autotune_group(ffsrl_sim* s, LaunchGroup& g) {
             FFSRL_CUDA(cudaEventSynchronize(e1));
             float ms = 0;
             FFSRL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (std::getenv("FFSRL_TUNE_LOG"))
+                std::fprintf(stderr, "ffsrl autotune V=%d envs=%d: sub=%d envs_per_cta=%d ring=%d permute=%d %.3f ms\n",
+                             m.V, g.n, cd.c.sub, cd.c.envs, int(cd.c.ring), int(cd.perm), ms / 2);
             if (ms < best.ms) best = {cd.c, cd.perm, ms};
         }
         cudaEventDestroy(e0);

@@ -22,7 +22,7 @@ def P(**over):
     return inputs.default_params(**over)
 
 
-def compare_states(sim, oenvs, meshes, n_env, env_mesh=None, label=""):
+def compare_states(sim, oenvs, meshes, n_env, env_mesh=None, label="", tol=POS_TOL):
     x, v, tool = gpu_positions(sim)
     off = packed_offsets(meshes, n_env, env_mesh)
     h = sim.params["dt"] / sim.params["substeps"]
@@ -35,8 +35,8 @@ def compare_states(sim, oenvs, meshes, n_env, env_mesh=None, label=""):
         ex = np.max(np.abs(gx - ox)) / ext
         ev = np.max(np.abs(gv - ov)) * h / ext
         worst = max(worst, ex)
-        assert ex <= POS_TOL, f"{label} env {e}: position error {ex:.3e} x extent"
-        assert ev <= POS_TOL, f"{label} env {e}: velocity error {ev:.3e} x extent / h"
+        assert ex <= tol, f"{label} env {e}: position error {ex:.3e} x extent"
+        assert ev <= tol, f"{label} env {e}: velocity error {ev:.3e} x extent / h"
         assert np.allclose(tool[e], oc, rtol=0, atol=1e-12), f"{label} env {e}: tool"
     return worst
 
@@ -189,7 +189,20 @@ def test_iteration_counts_carry_lambda(iterations):
         sim.step()
     for oe in oenvs.values():
         oe.run(steps, want_obs=False)
-    compare_states(sim, oenvs, [m], n_env, label=f"iterations={iterations}")
+    tol = POS_TOL
+    if iterations == 0:
+        # Free drift has no constraint to damp the float32 cancellation in
+        # v = (x - x_prev) / h, so the bar is the float32 oracle's own distance
+        # from the float64 oracle (times 4), if that exceeds the tissue tolerance.
+        import oracle
+        o32 = oracle.Env(oracle.Mesh(*m, precision="f32"), p)
+        o32.reset(4, 1)
+        V = len(m[0])
+        o32.set_state(x=x32[V:2 * V].astype(np.float64), v=v32[V:2 * V].astype(np.float64))
+        o32.run(steps, want_obs=False)
+        floor = np.max(np.abs(o32.state()[0] - oenvs[1].state()[0])) / oenvs[1].mesh.extent
+        tol = max(POS_TOL, 4 * floor)
+    compare_states(sim, oenvs, [m], n_env, label=f"iterations={iterations}", tol=tol)
 
 
 def test_rest_state_stays_put():
