@@ -37,6 +37,12 @@ FLOP_EDGE, FLOP_TET, FLOP_VERT = 32, 115, 28
 # Algorithmic HBM bytes per env-step: x and v read and written once (48 B per
 # vertex), per-env scalars and the observation written.
 BYTES_VERT = 48
+# Algorithmic shared-memory bytes of the resident step kernel: per edge and tet
+# projection its vertices' float4 loaded and stored (2 x 2 x 16, 2 x 4 x 16),
+# per vertex and substep one float4 load and store in the fused
+# collision / prediction pass.
+SMEM_EDGE, SMEM_TET, SMEM_VERT = 64, 128, 32
+SMEM_BYTES_PER_CLK_SM = 128   # 32 banks x 4 B per clock
 
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
 N_SM, FP32_LANES = 152, 128
@@ -63,6 +69,11 @@ def workload(name: str):
 def flops_per_env_step(V, E, T, params):
     s, it = params["substeps"], params["iterations"]
     return s * (it * (E * FLOP_EDGE + T * FLOP_TET) + V * FLOP_VERT)
+
+
+def smem_bytes_per_env_step(V, E, T, params):
+    s, it = params["substeps"], params["iterations"]
+    return s * (it * (E * SMEM_EDGE + T * SMEM_TET) + V * SMEM_VERT)
 
 
 class ClockSampler:
@@ -225,11 +236,9 @@ def run_e2e(args, sim, n_env, world, rank, seed, barrier, dist):
     for k in range(args.steps):
         sim.step_host(pool[k % len(pool)], h_obs, h_rew, h_done)
     t_e2e = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    return {"value": world * n_env * args.steps / t_e2e, "unit": UNIT,
+    from paper_2503_18616_gb300 import sharding
+    t_e2e = sharding.max_over_ranks(t_e2e, dist, "cuda")
+    return {"value": sharding.throughput(n_env, world, args.steps, t_e2e), "unit": UNIT,
            "h2d_bytes_per_step": int(pool[0].nbytes),
            "d2h_bytes_per_step": int(h_obs.nbytes + h_rew.nbytes + h_done.nbytes)}
 
@@ -239,7 +248,7 @@ def run_ours(args):
     import numpy as np
     import torch
     import __graft_entry__
-    from paper_2503_18616_gb300 import ffsrl, inputs
+    from paper_2503_18616_gb300 import ffsrl, inputs, sharding
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -263,7 +272,7 @@ def run_ours(args):
         flags = ffsrl.SCHED_FORCE | (0 if ring else ffsrl.SCHED_NO_RING) | (0 if perm else ffsrl.SCHED_NO_PERMUTE)
         flags |= {1: 0, 2: ffsrl.SCHED_ENVS2, 4: ffsrl.SCHED_ENVS4}[envs]
     sim = ffsrl.Sim([mesh], params, n_env, block_threads=block, schedule_flags=flags)
-    seed = args.seed + 1000003 * rank          # each rank owns its own env shard
+    seed = sharding.rank_seed(args.seed, rank)   # each rank owns its own env shard
     sim.reset(seed)
     stream = sim.stream
 
@@ -296,11 +305,8 @@ def run_ours(args):
     clk = clocks.stop()
     t_ms = ev0.elapsed_time(ev1)
     sim.sync()
-    if dist is not None:
-        t = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
-    value = world * n_env * args.steps / (t_ms / 1e3)
+    t_ms = sharding.max_over_ranks(t_ms, dist, "cuda")
+    value = sharding.throughput(n_env, world, args.steps, t_ms / 1e3)
 
     # End to end through the public host-buffer call: actions copied in,
     # observation, reward and done copied out, every step.
@@ -315,23 +321,28 @@ def run_ours(args):
         om = oracle.Mesh(*mesh)
         V, E, T = om.V, om.E, om.T
         ms_kernel = t_ms / args.steps          # one step-kernel launch per step
-        flops = flops_per_env_step(V, E, T, params) * n_env
         clock_mhz = float(peaks.get("sm_max_mhz", FALLBACK_PEAKS["sm_max_mhz"]))
+        sec = ms_kernel / 1e3
+        smem_bytes = smem_bytes_per_env_step(V, E, T, params) * n_env
+        smem_peak = SMEM_BYTES_PER_CLK_SM * N_SM * clock_mhz * 1e6 / 1e9
+        flops = flops_per_env_step(V, E, T, params) * n_env
         alu_peak = 2 * FP32_LANES * N_SM * clock_mhz * 1e6 / 1e12
-        achieved = flops / (ms_kernel / 1e3) / 1e12
-        traffic = ncu_traffic("xpbd_step_block17x17x9_4096env.txt")
         hbm_bytes = (BYTES_VERT * V + 4 * sim.obs_dim + 16) * n_env
-        roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                    "frac": achieved / alu_peak, "traffic": traffic,
+        hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
+        traffic = ncu_traffic("xpbd_step_block17x17x9_4096env.txt") if (n_env == 4096 and V == 2601) else None
+        roofline = {"bound": "smem", "achieved": smem_bytes / sec / 1e9, "peak": smem_peak, "unit": "GB/s",
+                    "frac": smem_bytes / sec / 1e9 / smem_peak, "traffic": traffic,
                     "kernel": f"xpbd_step_kernel<{sim.block_threads},{sim.envs_per_cta},resident,"
                               f"{'ring' if sim.ring_envs else 'l2'}>",
-                    "peak_source": f"{N_SM} SMs x {FP32_LANES} FP32 lanes x 2 x {clock_mhz:.0f} MHz "
-                                   f"(max SM clock, {peak_src})",
-                    "algorithmic_flops_per_launch": flops,
-                    "hbm": {"achieved_gbs": hbm_bytes / (ms_kernel / 1e3) / 1e9,
-                            "peak_gbs": float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"])),
-                            "algorithmic_bytes_per_launch": hbm_bytes, "peak_source": peak_src}}
-        roofline["hbm"]["frac"] = roofline["hbm"]["achieved_gbs"] / roofline["hbm"]["peak_gbs"]
+                    "peak_source": f"shared memory: {SMEM_BYTES_PER_CLK_SM} B/clk/SM x {N_SM} SMs x "
+                                   f"{clock_mhz:.0f} MHz max SM clock ({peak_src})",
+                    "algorithmic_bytes_per_launch": smem_bytes,
+                    "alu": {"achieved_tflops": flops / sec / 1e12, "peak_tflops": alu_peak,
+                            "frac": flops / sec / 1e12 / alu_peak, "algorithmic_flops_per_launch": flops,
+                            "peak_source": f"{N_SM} SMs x {FP32_LANES} FP32 lanes x 2 x {clock_mhz:.0f} MHz"},
+                    "hbm": {"achieved_gbs": hbm_bytes / sec / 1e9, "peak_gbs": hbm_peak,
+                            "frac": hbm_bytes / sec / 1e9 / hbm_peak, "algorithmic_bytes_per_launch": hbm_bytes,
+                            "peak_source": peak_src}}
 
         # Accuracy and CPU baseline: the FP64 oracle advances two sampled envs
         # for a bounded number of steps on one host thread; the GPU replays the
