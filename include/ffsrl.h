@@ -169,6 +169,50 @@ int ffsrl_get_mesh_table(const ffsrl_sim* sim, int32_t mesh, int32_t which, int3
 int ffsrl_get_env_ints(ffsrl_sim* sim, int32_t env, int32_t* step_count, int32_t* target,
                        int32_t* obs_ids_host, int32_t* n_contacts, int32_t* contacts_host);
 
+/* --- allocation-free step (no counterpart in the paper) ------------------- */
+
+/* Size of the static device scratch array used by ffsrl_step_noalloc. */
+#define FFSRL_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* One simulation step of caller-owned states that allocates no memory.
+ *
+ * Who needs it: callers that must not call cudaMalloc or cudaFree while they
+ * step the simulation - for example a real-time control loop, where those
+ * calls can synchronise the whole device and stall for milliseconds, a
+ * process whose device memory is reserved up front by another allocator
+ * (a deep-learning framework's caching allocator), so a further cudaMalloc
+ * fails or fragments memory, or a plugin host that forbids allocation inside
+ * its per-step callback. Such a caller creates the simulator once, where it
+ * may allocate, and then steps states it owns itself with this call.
+ *
+ * What it does: advances every env of `sim` by one step exactly as ffsrl_step
+ * does (same kernels, same schedule, same results), but on the state in the
+ * caller's arrays instead of the sim's own state: x_dev and v_dev are packed
+ * [total_verts][3] float32 positions and velocities, tool_dev is [n_env][3]
+ * float64 tool centres; all three are read and overwritten in place.
+ * actions_dev [n_env][3] is required (caller-owned state has no step counter
+ * for device-drawn actions). No observation, reward or done flags are
+ * produced. The sim's own state is neither read nor changed; only its
+ * constraint tables, parameters and schedule are used. Asynchronous on the
+ * sim's stream.
+ *
+ * Scratch: the working copies of the state, the substep-start positions, the
+ * per-env counters and (with iterations > 1) the Lagrange multipliers live in
+ * one file-scope static device array of FFSRL_NOALLOC_SCRATCH_BYTES (32 MiB),
+ * which every GPU that loads the library holds until the process exits. A sim
+ * whose scratch would exceed it (about 36 B per padded vertex row plus 16 B per
+ * env, more with iterations > 1 or meshes too large for shared memory) is
+ * rejected with FFSRL_E_INVAL and a message giving both sizes; for the
+ * 2601-vertex block that is about 340 envs. The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture. Every call shares the one
+ * array and it keeps the last call's contents: the call clears what must start
+ * at zero, and calls that overlap on the GPU (two streams, two sims, two
+ * threads) race on it and must be ordered by the caller. The call never
+ * allocates or frees device or pinned host memory. */
+int ffsrl_step_noalloc(ffsrl_sim* sim, const float* actions_dev, float* x_dev, float* v_dev,
+                       double* tool_dev);
+
 #ifdef __cplusplus
 }
 #endif

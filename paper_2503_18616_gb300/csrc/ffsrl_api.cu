@@ -642,3 +642,98 @@ int ffsrl_get_env_ints(ffsrl_sim* sim, int32_t env, int32_t* step_count, int32_t
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free step on caller-owned state (see ffsrl_step_noalloc in
+// include/ffsrl.h). Its scratch is this file-scope device array; host code
+// reaches it only through the address cudaGetSymbolAddress returns for the
+// current device (the symbol itself is a host-side stand-in).
+// ---------------------------------------------------------------------------
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[FFSRL_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on `device` (which must be current);
+// looked up once per device.
+int noalloc_scratch(int device, unsigned char** out) {
+    if (device < 0 || device >= kMaxDevices) return fail(FFSRL_E_CUDA, "device id out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(FFSRL_E_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+        g_noalloc_addr[device] = static_cast<unsigned char*>(p);
+    }
+    *out = g_noalloc_addr[device];
+    return FFSRL_OK;
+}
+
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+}  // namespace
+
+extern "C" int ffsrl_step_noalloc(ffsrl_sim* sim, const float* actions_dev, float* x_dev, float* v_dev,
+                                  double* tool_dev) {
+    if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
+    if (!actions_dev || !x_dev || !v_dev || !tool_dev)
+        return fail(FFSRL_E_INVAL, "ffsrl_step_noalloc needs actions_dev, x_dev, v_dev and tool_dev");
+    const size_t rows = size_t(sim->stride), n = size_t(sim->n_env);
+    bool any_streaming = false;
+    for (const LaunchGroup& g : sim->groups) any_streaming |= !g.cfg.resident;
+    size_t lam_slots = 0;
+    if (sim->params.iterations > 1)
+        for (int e = 0; e < sim->n_env; ++e) {
+            const HostMesh& m = sim->meshes[sim->env_mesh[e]];
+            lam_slots += size_t(m.E + m.T);
+        }
+    // Scratch layout: x, v and x_prev ([3][rows] float each), the working
+    // positions of non-resident envs ([rows] float4), contacts ([rows] int),
+    // per-env counters (4 x [n] int32/float), multipliers.
+    size_t off = 0;
+    const size_t o_x = off; off = align256(off + 3 * rows * sizeof(float));
+    const size_t o_v = off; off = align256(off + 3 * rows * sizeof(float));
+    const size_t o_p = off; off = align256(off + 3 * rows * sizeof(float));
+    const size_t o_xg = off; off = align256(off + (any_streaming ? rows * sizeof(float4) : 0));
+    const size_t o_c = off; off = align256(off + rows * sizeof(int));
+    const size_t o_env = off; off = align256(off + 4 * n * sizeof(int));
+    const size_t o_lam = off; off = align256(off + lam_slots * sizeof(float));
+    if (off > size_t(FFSRL_NOALLOC_SCRATCH_BYTES))
+        return fail(FFSRL_E_INVAL, "ffsrl_step_noalloc: this sim needs " + std::to_string(off) +
+                                       " bytes of scratch but the static scratch array holds " +
+                                       std::to_string(size_t(FFSRL_NOALLOC_SCRATCH_BYTES)) +
+                                       " bytes (FFSRL_NOALLOC_SCRATCH_BYTES); use fewer envs per sim");
+    FFSRL_CUDA(cudaSetDevice(sim->device));
+    unsigned char* base = nullptr;
+    int rc = noalloc_scratch(sim->device, &base);
+    if (rc) return rc;
+
+    SimDev S = sim->S;
+    S.x = reinterpret_cast<float*>(base + o_x);
+    S.v = reinterpret_cast<float*>(base + o_v);
+    S.pg = reinterpret_cast<float*>(base + o_p);
+    S.xg = any_streaming ? reinterpret_cast<float4*>(base + o_xg) : nullptr;
+    S.contacts = reinterpret_cast<int*>(base + o_c);
+    int* env_ints = reinterpret_cast<int*>(base + o_env);
+    S.t_step = env_ints;
+    S.n_contacts = env_ints + n;
+    S.err = env_ints + 2 * n;
+    S.l_prev = reinterpret_cast<float*>(env_ints + 3 * n);
+    S.lambda = lam_slots ? reinterpret_cast<float*>(base + o_lam) : nullptr;
+    S.tool = tool_dev;
+    // Step counters, contact counts, error flags and last distances start at zero.
+    FFSRL_CUDA(cudaMemsetAsync(env_ints, 0, 4 * n * sizeof(int), sim->stream));
+    FFSRL_CUDA(launch_unpack(S, sim->d_pstart, x_dev, v_dev, sim->stream));
+    for (const LaunchGroup& g : sim->groups) {
+        SimDev Sg = S;
+        Sg.meshes = sim->d_meshes[g.permute ? 1 : 0];
+        FFSRL_CUDA(launch_step(Sg, g.cfg, g.d_list, g.n, g.smem, sim->stream, actions_dev, nullptr, nullptr, nullptr));
+    }
+    FFSRL_CUDA(launch_pack(S, sim->d_pstart, x_dev, v_dev, sim->stream));
+    return FFSRL_OK;
+}

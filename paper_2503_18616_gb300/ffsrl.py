@@ -27,7 +27,9 @@ TABLES = {"tets": 0, "flipped": 1, "edges": 2, "ecolor": 3, "tcolor": 4, "eorder
 # every symbol include/ffsrl.h declares
 EXPORTS = ["ffsrl_create", "ffsrl_reset", "ffsrl_step", "ffsrl_step_host", "ffsrl_sync",
            "ffsrl_destroy", "ffsrl_get_info", "ffsrl_last_error", "ffsrl_get_state",
-           "ffsrl_set_state", "ffsrl_get_mesh_table", "ffsrl_get_env_ints"]
+           "ffsrl_set_state", "ffsrl_get_mesh_table", "ffsrl_get_env_ints", "ffsrl_step_noalloc"]
+
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class FfsrlError(RuntimeError):
@@ -98,6 +100,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.ffsrl_get_mesh_table.argtypes = [P, I32, I32, P, ctypes.POINTER(ctypes.c_int64)]
     L.ffsrl_get_env_ints.restype = ctypes.c_int
     L.ffsrl_get_env_ints.argtypes = [P, I32, P, P, P, P, P]
+    L.ffsrl_step_noalloc.restype = ctypes.c_int
+    L.ffsrl_step_noalloc.argtypes = [P, P, P, P, P]
     _lib = L
     return L
 
@@ -234,6 +238,12 @@ class Sim:
         _check(self._L.ffsrl_step_host(self._h, _np_ptr(a) if a is not None else None, _np_ptr(obs),
                                        _np_ptr(reward), _np_ptr(done)))
         return obs, reward, done
+
+    def step_noalloc(self, actions, x, v, tool) -> None:
+        """ffsrl_step_noalloc: one step of the caller's packed state tensors
+        (x, v [total_verts][3] float32, tool [n_env][3] float64, updated in
+        place) with this sim's meshes; allocates nothing."""
+        _check(self._L.ffsrl_step_noalloc(self._h, _dptr(actions), _dptr(x), _dptr(v), _dptr(tool)))
 
     def sync(self) -> None:
         _check(self._L.ffsrl_sync(self._h))
