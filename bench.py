@@ -23,6 +23,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -57,13 +59,46 @@ def load_peaks():
         return dict(FALLBACK_PEAKS), "fallback"
 
 
-def workload(name: str):
-    from paper_2503_18616_gb300 import inputs
-    w = inputs.WORKLOADS[name]
-    if "shape" not in w:
-        raise SystemExit(f"workload {name} is not a single-mesh batch")
-    mesh = inputs.grid_block(*w["shape"])
-    return w, mesh, inputs.default_params()
+class Batch:
+    """A workload: meshes, the env -> mesh map, per-env edge compliance and the parameters."""
+
+    def __init__(self, name: str, n_env_override: int = 0):
+        from paper_2503_18616_gb300 import inputs
+        w = inputs.WORKLOADS[name]
+        self.name = name
+        self.params = inputs.default_params()
+        self.n_env = n_env_override or w["n_env"]
+        self.steps = w["steps"]
+        if "shape" in w:
+            self.shapes = [w["shape"]]
+            self.env_mesh = None
+            self.env_alpha = None
+        else:
+            self.shapes, env_mesh = inputs.uneven_batch(w["n_env"], *w["v_range"], seed=12345)
+            env_mesh = env_mesh[:self.n_env]
+            used = sorted(set(int(m) for m in env_mesh))   # keep only meshes still referenced
+            self.shapes = [self.shapes[m] for m in used]
+            self.env_mesh = np.array([used.index(int(m)) for m in env_mesh], dtype=np.int32)
+            self.env_alpha = inputs.compliance_draws(w["n_env"], *w["alpha_range"], seed=12345)[:self.n_env]
+        self.meshes = [inputs.grid_block(*sh) for sh in self.shapes]
+
+    def mesh_index(self, e: int) -> int:
+        return 0 if self.env_mesh is None else int(self.env_mesh[e])
+
+    def env_params(self, e: int) -> dict:
+        p = dict(self.params)
+        if self.env_alpha is not None:
+            p["alpha_d"] = float(self.env_alpha[e])
+        return p
+
+    def verts(self, e: int) -> int:
+        return len(self.meshes[self.mesh_index(e)][0])
+
+    def describe(self) -> str:
+        if len(self.shapes) == 1:
+            return f"{self.n_env} envs of the {self.verts(0)}-vertex block"
+        vs = [self.verts(e) for e in range(self.n_env)]
+        return f"{self.n_env} envs of {len(self.shapes)} block sizes, {min(vs)}-{max(vs)} vertices"
 
 
 def flops_per_env_step(V, E, T, params):
@@ -150,52 +185,65 @@ def ncu_traffic(profile: str):
         return None
 
 
-def oracle_rate(mesh, params, seconds: float, seed: int, envs=(0,), max_steps=None):
+def oracle_rate(batch, seconds: float, seed: int, envs, max_steps=None):
     """FP64 oracle env-steps/s on one host thread over a bounded sample; also
-    returns the oracle states after the sampled steps for the accuracy check."""
-    import numpy as np  # noqa: F401
+    returns the oracle envs after the sampled steps for the accuracy check."""
     import oracle
-    om = oracle.Mesh(*mesh)
+    meshes = {}
     oes = []
     for e in envs:
-        oe = oracle.Env(om, params)
+        mi = batch.mesh_index(e)
+        if mi not in meshes:
+            meshes[mi] = oracle.Mesh(*batch.meshes[mi])
+        oe = oracle.Env(meshes[mi], batch.env_params(e))
         oe.reset(seed, e)
         oes.append(oe)
     t0 = time.perf_counter()
-    oes[0].run(3, want_obs=False)
-    per_step = (time.perf_counter() - t0) / 3
-    n = max(5, int(seconds / (per_step * len(oes))))
+    for oe in oes:
+        oe.run(2, want_obs=False)
+    per_round = (time.perf_counter() - t0) / 2
+    n = max(5, int(seconds / per_round))
     if max_steps is not None:
         n = min(n, max_steps)
-    for oe in oes:   # restart from reset so all envs run exactly n steps
-        oe.reset(seed, envs[oes.index(oe)])
+    for e, oe in zip(envs, oes):   # restart from reset so all envs run exactly n steps
+        oe.reset(seed, e)
     t0 = time.perf_counter()
     for oe in oes:
         oe.run(n, want_obs=False)
     dt = time.perf_counter() - t0
-    return len(oes) * n / dt, n, dt, oes, om
+    return len(oes) * n / dt, n, dt, oes
 
 
 def run_reference(args):
-    """The oracle as it stands, timed on host cores (rank 0 only)."""
+    """The oracle as it stands, timed on host cores (rank 0 only). Each bench
+    step advances a bounded, evenly spaced sample of the workload's envs by one
+    step on one host thread."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle
-    w, mesh, params = workload(args.workload)
-    om = oracle.Mesh(*mesh)
-    probe = oracle.Env(om, params)
-    probe.reset(args.seed, 0)
-    t0 = time.perf_counter()
-    probe.run(3, want_obs=False)
-    per_env_step = (time.perf_counter() - t0) / 3
-    budget = 120.0
-    n_sample = max(1, min(w["n_env"], int(budget / ((args.steps + args.warmup) * per_env_step))))
-    envs = []
-    for e in range(n_sample):
-        oe = oracle.Env(om, params)
+    batch = Batch(args.workload, args.envs)
+    probe_envs = list(range(0, batch.n_env, max(1, batch.n_env // 16)))
+    meshes = {}
+
+    def make(e):
+        mi = batch.mesh_index(e)
+        if mi not in meshes:
+            meshes[mi] = oracle.Mesh(*batch.meshes[mi])
+        oe = oracle.Env(meshes[mi], batch.env_params(e))
         oe.reset(args.seed, e)
-        envs.append(oe)
+        return oe
+
+    probes = [make(e) for e in probe_envs]
+    t0 = time.perf_counter()
+    for oe in probes:
+        oe.run(1, want_obs=False)
+    per_env_step = (time.perf_counter() - t0) / len(probes)
+    budget = 120.0
+    n_sample = max(1, min(batch.n_env, int(budget / ((args.steps + args.warmup) * per_env_step))))
+    sample_envs = [int(e) for e in np.linspace(0, batch.n_env - 1, n_sample).round()]
+    sample_envs = sorted(set(sample_envs))
+    envs = [make(e) for e in sample_envs]
     for _ in range(args.warmup):
         for oe in envs:
             oe.step()
@@ -204,16 +252,14 @@ def run_reference(args):
         for oe in envs:
             oe.step()
     dt = time.perf_counter() - t0
-    value = n_sample * args.steps / dt
-    sample = (f"{n_sample} of {w['n_env']} envs of the {om.V}-vertex block per step, "
-              f"FP64 oracle, 1 host thread")
+    value = len(envs) * args.steps / dt
+    sample = f"{len(envs)} evenly spaced of {batch.describe()} per step, FP64 oracle, 1 host thread"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload, "n_env": w["n_env"], "verts_per_env": om.V,
-                       "tets_per_env": om.T, "substeps": params["substeps"],
-                       "iterations": params["iterations"]},
+            "config": {"workload": args.workload, "n_env": batch.n_env, "envs": batch.describe(),
+                       "substeps": batch.params["substeps"], "iterations": batch.params["iterations"]},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -263,15 +309,17 @@ def run_ours(args):
     if rank == 0 or world > 1:
         __graft_entry__.build()
 
-    w, mesh, params = workload(args.workload)
-    n_env = args.envs or w["n_env"]
+    batch = Batch(args.workload, args.envs)
+    params = batch.params
+    n_env = batch.n_env
     block, flags = 0, 0
     if args.schedule:   # forced schedule "threads_per_env:envs_per_cta:ring:permute" (profiling)
         sub, envs, ring, perm = (int(x) for x in args.schedule.split(":"))
         block = sub
         flags = ffsrl.SCHED_FORCE | (0 if ring else ffsrl.SCHED_NO_RING) | (0 if perm else ffsrl.SCHED_NO_PERMUTE)
         flags |= {1: 0, 2: ffsrl.SCHED_ENVS2, 4: ffsrl.SCHED_ENVS4}[envs]
-    sim = ffsrl.Sim([mesh], params, n_env, block_threads=block, schedule_flags=flags)
+    sim = ffsrl.Sim(batch.meshes, params, n_env, env_mesh=batch.env_mesh, env_compliance=batch.env_alpha,
+                    block_threads=block, schedule_flags=flags)
     seed = sharding.rank_seed(args.seed, rank)   # each rank owns its own env shard
     sim.reset(seed)
     stream = sim.stream
@@ -293,17 +341,20 @@ def run_ours(args):
     time.sleep(0.3)
     barrier()
     torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    # one event between consecutive steps: per-step latency without any sync
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with torch.cuda.stream(stream):
-        ev0.record(stream)
-        for _ in range(args.steps):
+        evs[0].record(stream)
+        for k in range(args.steps):
             sim.step_into(None, obs, rew, done)
-        ev1.record(stream)
+            evs[k + 1].record(stream)
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    t_ms = ev0.elapsed_time(ev1)
+    t_ms = evs[0].elapsed_time(evs[-1])
+    lat = np.array([evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)])
+    latency = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+               "max_ms": float(lat.max()), "unit": "ms per step (all envs)"}
     sim.sync()
     t_ms = sharding.max_over_ranks(t_ms, dist, "cuda")
     value = sharding.throughput(n_env, world, args.steps, t_ms / 1e3)
@@ -317,23 +368,29 @@ def run_ours(args):
     line = None
     if rank == 0:
         peaks, peak_src = load_peaks()
-        import oracle
-        om = oracle.Mesh(*mesh)
-        V, E, T = om.V, om.E, om.T
-        ms_kernel = t_ms / args.steps          # one step-kernel launch per step
+        counts = []   # (V, E, T) per env from the library's own tables
+        mesh_counts = []
+        for mi in range(len(batch.meshes)):
+            mesh_counts.append((len(batch.meshes[mi][0]), len(sim.mesh_table("edges", mi)) // 2,
+                                len(sim.mesh_table("tets", mi)) // 4))
+        counts = [mesh_counts[batch.mesh_index(e)] for e in range(n_env)]
+        ms_step = t_ms / args.steps
         clock_mhz = float(peaks.get("sm_max_mhz", FALLBACK_PEAKS["sm_max_mhz"]))
-        sec = ms_kernel / 1e3
-        smem_bytes = smem_bytes_per_env_step(V, E, T, params) * n_env
+        sec = ms_step / 1e3
+        smem_bytes = sum(smem_bytes_per_env_step(V, E, T, params) for V, E, T in counts)
         smem_peak = SMEM_BYTES_PER_CLK_SM * N_SM * clock_mhz * 1e6 / 1e9
-        flops = flops_per_env_step(V, E, T, params) * n_env
+        flops = sum(flops_per_env_step(V, E, T, params) for V, E, T in counts)
         alu_peak = 2 * FP32_LANES * N_SM * clock_mhz * 1e6 / 1e12
-        hbm_bytes = (BYTES_VERT * V + 4 * sim.obs_dim + 16) * n_env
+        hbm_bytes = sum(BYTES_VERT * V + 4 * sim.obs_dim + 16 for V, _, _ in counts)
         hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
-        traffic = ncu_traffic("xpbd_step_block17x17x9_4096env.txt") if (n_env == 4096 and V == 2601) else None
+        single = len(batch.meshes) == 1
+        traffic = ncu_traffic("xpbd_step_block17x17x9_4096env.txt") if (
+            single and n_env == 4096 and counts[0][0] == 2601) else None
+        kernel = (f"xpbd_step_kernel<{sim.block_threads},{sim.envs_per_cta},resident,"
+                  f"{'ring' if sim.ring_envs else 'l2'}>" if single else
+                  f"xpbd_step_kernel, {sim.n_groups} size classes launched concurrently")
         roofline = {"bound": "smem", "achieved": smem_bytes / sec / 1e9, "peak": smem_peak, "unit": "GB/s",
-                    "frac": smem_bytes / sec / 1e9 / smem_peak, "traffic": traffic,
-                    "kernel": f"xpbd_step_kernel<{sim.block_threads},{sim.envs_per_cta},resident,"
-                              f"{'ring' if sim.ring_envs else 'l2'}>",
+                    "frac": smem_bytes / sec / 1e9 / smem_peak, "traffic": traffic, "kernel": kernel,
                     "peak_source": f"shared memory: {SMEM_BYTES_PER_CLK_SM} B/clk/SM x {N_SM} SMs x "
                                    f"{clock_mhz:.0f} MHz max SM clock ({peak_src})",
                     "algorithmic_bytes_per_launch": smem_bytes,
@@ -343,6 +400,7 @@ def run_ours(args):
                     "hbm": {"achieved_gbs": hbm_bytes / sec / 1e9, "peak_gbs": hbm_peak,
                             "frac": hbm_bytes / sec / 1e9 / hbm_peak, "algorithmic_bytes_per_launch": hbm_bytes,
                             "peak_source": peak_src}}
+        V_total = sum(c[0] for c in counts)
 
         # Accuracy and CPU baseline: the FP64 oracle advances two sampled envs
         # for a bounded number of steps on one host thread; the GPU replays the
@@ -350,35 +408,42 @@ def run_ours(args):
         cpu = None
         acc = None
         if world == 1 and not args.no_cpu_baseline:
-            sample_envs = (0, n_env - 1)
-            rate, n_steps, dt, oes, om = oracle_rate(mesh, params, args.cpu_seconds, seed, envs=sample_envs,
-                                                     max_steps=max(args.steps, 50))
+            # the first and last env, or the smallest and the largest of an uneven batch
+            if single:
+                sample_envs = (0, n_env - 1)
+            else:
+                vs = [c[0] for c in counts]
+                sample_envs = (int(np.argmin(vs)), int(np.argmax(vs)))
+            rate, n_steps, dt, oes = oracle_rate(batch, args.cpu_seconds, seed, sample_envs,
+                                                 max_steps=max(args.steps, 50))
             sim.reset(seed)
             for _ in range(n_steps):
                 sim.step_into(None, None, None, None)
             x, _, _ = sim.get_state()
             x = x.cpu().numpy().astype(np.float64)
+            off = np.concatenate([[0], np.cumsum([c[0] for c in counts])])
             errs = []
             for e, oe in zip(sample_envs, oes):
                 ox, _, _ = oe.state()
-                errs.append(float(np.max(np.abs(x[e * V:(e + 1) * V] - ox)) / om.extent))
+                errs.append(float(np.max(np.abs(x[off[e]:off[e + 1]] - ox)) / oe.mesh.extent))
             acc = {"max_pos_err_over_extent": max(errs), "tolerance": POS_TOL, "envs": list(sample_envs),
-                   "steps": n_steps, "within_tolerance": max(errs) <= POS_TOL}
+                   "verts": [counts[e][0] for e in sample_envs], "steps": n_steps,
+                   "within_tolerance": max(errs) <= POS_TOL}
             cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"envs {list(sample_envs)} x {n_steps} steps of the {V}-vertex block, "
-                             f"FP64 oracle, 1 host thread, {dt:.1f} s"}
+                   "sample": f"envs {list(sample_envs)} ({[counts[e][0] for e in sample_envs]} vertices) x "
+                             f"{n_steps} steps, FP64 oracle, 1 host thread, {dt:.1f} s"}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": args.workload, "n_env_per_gpu": n_env, "verts_per_env": V,
-                           "edges_per_env": E, "tets_per_env": T, "substeps": params["substeps"],
+                "config": {"workload": args.workload, "n_env_per_gpu": n_env, "envs": batch.describe(),
+                           "verts_total": V_total, "substeps": params["substeps"],
                            "iterations": params["iterations"], "actions": "device counter-based draws",
-                           "l2": f"state {2 * 12 * V * n_env / 1e6:.0f} MB > 129 MB L2, no flush",
+                           "l2": f"state {24 * V_total / 1e6:.0f} MB > 129 MB L2, no flush",
                            "parallelism": f"env-sharded x{world}",
                            "schedule": {"threads_per_env": sim.block_threads, "envs_per_cta": sim.envs_per_cta,
                                         "tma_ring_envs": sim.ring_envs,
                                         "resident_envs": sim.resident_envs, "launch_groups": sim.n_groups}},
-                "roofline": roofline, "cpu_baseline": cpu, "accuracy": acc, "e2e": e2e,
+                "roofline": roofline, "cpu_baseline": cpu, "accuracy": acc, "e2e": e2e, "latency": latency,
                 "gpu_launches": args.steps * sim.n_groups, "clocks": clk}
         print(json.dumps(line), flush=True)
     sim.close()

@@ -39,23 +39,28 @@ int fail(int code, const std::string& msg) {
 
 int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
-// One step-kernel launch: the envs of one mesh with one execution schedule.
+// One step-kernel launch: the envs of one shared-memory size class (one or
+// more meshes, largest envs first) with one execution schedule. Groups run
+// concurrently on their own streams.
 struct LaunchGroup {
-    int mesh = 0;
+    std::vector<int> meshes;  // distinct meshes of the group
     int n = 0;
+    long long verts = 0;      // total vertices (work estimate)
     int* d_list = nullptr;
     StepConfig cfg;
     bool permute = true;
     size_t smem = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
 };
 
 // Autotuner choices, cached per mesh size class and batch size for the
 // lifetime of the process.
 struct TuneKey {
-    int V, E, T, n_env, substeps, iterations;
+    std::vector<long long> shape;  // (V, E, T, envs) of every mesh of the group
+    int substeps, iterations;
     bool operator<(const TuneKey& o) const {
-        return std::tie(V, E, T, n_env, substeps, iterations) <
-               std::tie(o.V, o.E, o.T, o.n_env, o.substeps, o.iterations);
+        return std::tie(shape, substeps, iterations) < std::tie(o.shape, o.substeps, o.iterations);
     }
 };
 struct TuneChoice {
@@ -88,6 +93,7 @@ struct ffsrl_sim {
     std::vector<MeshDev> h_meshes[2];
     int* d_pstart = nullptr;
     std::vector<LaunchGroup> groups;
+    cudaEvent_t fork = nullptr;
     int resident_envs = 0, ring_envs = 0;
 
     template <class T>
@@ -107,6 +113,11 @@ struct ffsrl_sim {
         return e;
     }
     ~ffsrl_sim() {
+        for (LaunchGroup& g : groups) {
+            if (g.stream) cudaStreamDestroy(g.stream);
+            if (g.done) cudaEventDestroy(g.done);
+        }
+        if (fork) cudaEventDestroy(fork);
         for (void* p : dev_allocs) cudaFree(p);
         if (h_pinned) cudaFreeHost(h_pinned);
     }
@@ -192,10 +203,44 @@ size_t group_smem(const ffsrl_sim* s, const MeshDev& d, const StepConfig& c) {
     return b + 256 <= s->max_smem ? b : 0;  // room for the kernel's static shared memory
 }
 
-cudaError_t launch_group(ffsrl_sim* s, const LaunchGroup& g, const float* a, float* o, float* r, uint8_t* d) {
+// Largest shared memory over the meshes of a group (0 if one does not fit).
+size_t group_smem(const ffsrl_sim* s, const LaunchGroup& g, bool permute, const StepConfig& c) {
+    if (c.envs > 1 && g.meshes.size() > 1) return 0;   // envs of one CTA share one mesh's ring
+    size_t mx = 0;
+    for (int mi : g.meshes) {
+        const size_t b = group_smem(s, s->h_meshes[permute ? 1 : 0][mi], c);
+        if (!b) return 0;
+        mx = std::max(mx, b);
+    }
+    return mx;
+}
+
+cudaError_t launch_group(ffsrl_sim* s, const LaunchGroup& g, cudaStream_t st, const float* a, float* o, float* r,
+                         uint8_t* d) {
     SimDev S = s->S;
     S.meshes = s->d_meshes[g.permute ? 1 : 0];
-    return launch_step(S, g.cfg, g.d_list, g.n, g.smem, s->stream, a, o, r, d);
+    return launch_step(S, g.cfg, g.d_list, g.n, g.smem, st, a, o, r, d);
+}
+
+// All groups of one step: forked onto the groups' streams after the work
+// already queued on the sim's stream, joined back before the step returns.
+cudaError_t launch_all(ffsrl_sim* s, const SimDev* Sx, const float* a, float* o, float* r, uint8_t* d) {
+    if (s->groups.size() == 1) {
+        const LaunchGroup& g = s->groups[0];
+        SimDev S = Sx ? *Sx : s->S;
+        S.meshes = s->d_meshes[g.permute ? 1 : 0];
+        return launch_step(S, g.cfg, g.d_list, g.n, g.smem, s->stream, a, o, r, d);
+    }
+    cudaError_t e = cudaEventRecord(s->fork, s->stream);
+    for (const LaunchGroup& g : s->groups) {
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(g.stream, s->fork, 0);
+        SimDev S = Sx ? *Sx : s->S;
+        S.meshes = s->d_meshes[g.permute ? 1 : 0];
+        if (e == cudaSuccess) e = launch_step(S, g.cfg, g.d_list, g.n, g.smem, g.stream, a, o, r, d);
+        if (e == cudaSuccess) e = cudaEventRecord(g.done, g.stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, g.done, 0);
+    }
+    return e;
 }
 
 // Times candidate schedules of one group on its own envs (device-drawn
@@ -204,8 +249,15 @@ cudaError_t launch_group(ffsrl_sim* s, const LaunchGroup& g, const float* a, flo
 // afterwards by the caller.
 int autotune_group(ffsrl_sim* s, LaunchGroup& g) {
     const ffsrl_params& p = s->params;
-    const HostMesh& m = s->meshes[g.mesh];
-    const TuneKey key{m.V, m.E, m.T, g.n, p.substeps, p.iterations};
+    TuneKey key;
+    for (int mi : g.meshes) {
+        const HostMesh& m = s->meshes[mi];
+        long long cnt = 0;
+        for (int e = 0; e < s->n_env; ++e) cnt += s->env_mesh[e] == mi;
+        key.shape.insert(key.shape.end(), {m.V, m.E, m.T, cnt});
+    }
+    key.substeps = p.substeps;
+    key.iterations = p.iterations;
     const bool force_sched = (p.schedule_flags & FFSRL_SCHED_FORCE) != 0;
     const bool resident = g.cfg.resident;
     if (!p.block_threads && !force_sched) {
@@ -214,12 +266,11 @@ int autotune_group(ffsrl_sim* s, LaunchGroup& g) {
         if (it != g_tune_cache.end() && it->second.cfg.resident == resident) {
             g.cfg = it->second.cfg;
             g.permute = it->second.permute;
-            g.smem = group_smem(s, s->h_meshes[g.permute][g.mesh], g.cfg);
+            g.smem = group_smem(s, g, g.permute, g.cfg);
             if (g.smem) return FFSRL_OK;
         }
     }
     std::vector<StepConfig> cands;
-    std::vector<bool> perms;
     const bool force_perm = !(p.schedule_flags & FFSRL_SCHED_NO_PERMUTE);
     const bool force_ring = !(p.schedule_flags & FFSRL_SCHED_NO_RING);
     if (force_sched) {
@@ -249,10 +300,13 @@ int autotune_group(ffsrl_sim* s, LaunchGroup& g) {
     std::vector<Cand> feasible;
     for (const StepConfig& c : cands)
         for (int pm : perm_opts) {
-            const size_t sm = group_smem(s, s->h_meshes[pm][g.mesh], c);
+            const size_t sm = group_smem(s, g, bool(pm), c);
             if (sm) feasible.push_back({c, bool(pm), sm});
         }
-    if (feasible.empty()) return fail(FFSRL_E_INVAL, "no step schedule fits this device");
+    if (feasible.empty()) {
+        if (force_sched) return fail(FFSRL_E_INVAL, "the forced step schedule is not available for this mesh");
+        return fail(FFSRL_E_INVAL, "no step schedule fits this device");
+    }
     TuneChoice best{feasible[0].c, feasible[0].perm, 1e30f};
     if (feasible.size() > 1) {
         cudaEvent_t e0, e1;
@@ -263,16 +317,16 @@ int autotune_group(ffsrl_sim* s, LaunchGroup& g) {
             c.cfg = cd.c;
             c.permute = cd.perm;
             c.smem = cd.smem;
-            FFSRL_CUDA(launch_group(s, c, nullptr, nullptr, nullptr, nullptr));  // warm-up
+            FFSRL_CUDA(launch_group(s, c, s->stream, nullptr, nullptr, nullptr, nullptr));  // warm-up
             FFSRL_CUDA(cudaEventRecord(e0, s->stream));
-            for (int i = 0; i < 2; ++i) FFSRL_CUDA(launch_group(s, c, nullptr, nullptr, nullptr, nullptr));
+            for (int i = 0; i < 2; ++i) FFSRL_CUDA(launch_group(s, c, s->stream, nullptr, nullptr, nullptr, nullptr));
             FFSRL_CUDA(cudaEventRecord(e1, s->stream));
             FFSRL_CUDA(cudaEventSynchronize(e1));
             float ms = 0;
             FFSRL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
             if (std::getenv("FFSRL_TUNE_LOG"))
-                std::fprintf(stderr, "ffsrl autotune V=%d envs=%d: sub=%d envs_per_cta=%d ring=%d permute=%d %.3f ms\n",
-                             m.V, g.n, cd.c.sub, cd.c.envs, int(cd.c.ring), int(cd.perm), ms / 2);
+                std::fprintf(stderr, "ffsrl autotune meshes=%zu envs=%d resident=%d: sub=%d envs_per_cta=%d ring=%d permute=%d %.3f ms\n",
+                             g.meshes.size(), g.n, int(resident), cd.c.sub, cd.c.envs, int(cd.c.ring), int(cd.perm), ms / 2);
             if (ms < best.ms) best = {cd.c, cd.perm, ms};
         }
         cudaEventDestroy(e0);
@@ -280,7 +334,7 @@ int autotune_group(ffsrl_sim* s, LaunchGroup& g) {
     }
     g.cfg = best.cfg;
     g.permute = best.permute;
-    g.smem = group_smem(s, s->h_meshes[g.permute][g.mesh], g.cfg);
+    g.smem = group_smem(s, g, g.permute, g.cfg);
     if (!p.block_threads && !force_sched) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = best;
@@ -373,21 +427,36 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
     S.w_s = p.w_s;
     S.success_dist = p.success_dist;
 
-    // Launch groups: one per mesh; resident in shared memory when it fits.
-    bool any_streaming = false;
+    // Launch groups: one per shared-memory size class, i.e. by how many CTAs of
+    // a mesh's resident configuration fit on one SM (3 or more, 2, 1, or none:
+    // the global-memory variant). Inside a group the largest envs come first.
+    int smem_sm = 0;
+    FFSRL_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, s->device));
+    std::vector<int> mesh_class(md.size());
     for (size_t mi = 0; mi < md.size(); ++mi) {
-        std::vector<int> list;
-        for (int e = 0; e < n_env; ++e)
-            if (s->env_mesh[e] == int(mi)) list.push_back(e);
-        if (list.empty()) continue;
-        LaunchGroup g;
-        g.mesh = int(mi);
-        g.n = int(list.size());
         StepConfig probe;
-        probe.sub = 128;
-        probe.ring = false;
-        g.cfg.resident = group_smem(s, md[mi], probe) != 0;
-        any_streaming |= !g.cfg.resident;
+        const size_t b = group_smem(s, md[mi], probe);   // 256 threads, resident, ring
+        mesh_class[mi] = b ? std::min<int>(3, int(size_t(smem_sm) / (b + 1024))) : 0;
+        if (b && mesh_class[mi] == 0) mesh_class[mi] = 1;
+    }
+    bool any_streaming = false;
+    for (int cls = 3; cls >= 0; --cls) {
+        LaunchGroup g;
+        std::vector<std::pair<int, int>> members;   // (-V, env)
+        for (int e = 0; e < n_env; ++e)
+            if (mesh_class[s->env_mesh[e]] == cls) members.push_back({-md[s->env_mesh[e]].V, e});
+        if (members.empty()) continue;
+        std::sort(members.begin(), members.end());
+        std::vector<int> list;
+        for (auto& pr : members) {
+            list.push_back(pr.second);
+            g.verts += -pr.first;
+            const int mi = s->env_mesh[pr.second];
+            if (std::find(g.meshes.begin(), g.meshes.end(), mi) == g.meshes.end()) g.meshes.push_back(mi);
+        }
+        g.n = int(list.size());
+        g.cfg.resident = cls > 0;
+        any_streaming |= cls == 0;
         FFSRL_CUDA(s->upload(&g.d_list, list.data(), list.size()));
         s->groups.push_back(g);
     }
@@ -403,10 +472,17 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
     // autotuner runs steps on it.
     FFSRL_CUDA(launch_reset(S, nullptr, 0ull, s->stream));
     FFSRL_CUDA(cudaStreamSynchronize(s->stream));
-    // Execution schedule per group (autotuned unless forced), largest groups first.
-    std::sort(s->groups.begin(), s->groups.end(), [&](const LaunchGroup& a, const LaunchGroup& b) {
-        return size_t(a.n) * md[a.mesh].V > size_t(b.n) * md[b.mesh].V;
-    });
+    // Execution schedule per group (autotuned unless forced), largest groups
+    // first; each group gets its own stream when there are several.
+    std::sort(s->groups.begin(), s->groups.end(),
+              [](const LaunchGroup& a, const LaunchGroup& b) { return a.verts > b.verts; });
+    if (s->groups.size() > 1) {
+        FFSRL_CUDA(cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming));
+        for (LaunchGroup& g : s->groups) {
+            FFSRL_CUDA(cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking));
+            FFSRL_CUDA(cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming));
+        }
+    }
     for (LaunchGroup& g : s->groups) {
         int rc = autotune_group(s, g);
         if (rc) return rc;
@@ -501,8 +577,7 @@ int ffsrl_step(ffsrl_sim* sim, const float* actions_dev, float* obs_dev, float* 
                uint8_t* done_dev) {
     if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
     FFSRL_CUDA(cudaSetDevice(sim->device));
-    for (const LaunchGroup& g : sim->groups)
-        FFSRL_CUDA(launch_group(sim, g, actions_dev, obs_dev, reward_dev, done_dev));
+    FFSRL_CUDA(launch_all(sim, nullptr, actions_dev, obs_dev, reward_dev, done_dev));
     return FFSRL_OK;
 }
 
@@ -729,11 +804,7 @@ extern "C" int ffsrl_step_noalloc(ffsrl_sim* sim, const float* actions_dev, floa
     // Step counters, contact counts, error flags and last distances start at zero.
     FFSRL_CUDA(cudaMemsetAsync(env_ints, 0, 4 * n * sizeof(int), sim->stream));
     FFSRL_CUDA(launch_unpack(S, sim->d_pstart, x_dev, v_dev, sim->stream));
-    for (const LaunchGroup& g : sim->groups) {
-        SimDev Sg = S;
-        Sg.meshes = sim->d_meshes[g.permute ? 1 : 0];
-        FFSRL_CUDA(launch_step(Sg, g.cfg, g.d_list, g.n, g.smem, sim->stream, actions_dev, nullptr, nullptr, nullptr));
-    }
+    FFSRL_CUDA(launch_all(sim, &S, actions_dev, nullptr, nullptr, nullptr));
     FFSRL_CUDA(launch_pack(S, sim->d_pstart, x_dev, v_dev, sim->stream));
     return FFSRL_OK;
 }

@@ -385,3 +385,25 @@ def test_every_schedule_gives_bit_identical_results():
             for a, b in zip(ref, out):
                 assert np.array_equal(a, b), (flags, block)
         sim.close()
+
+
+def test_uneven_1024_env_batch_sampled():
+    """The uneven-batching configuration: 1024 envs, vertex counts log-uniform in
+    [500, 20000] (37 block sizes), per-env edge compliance, all size classes
+    launched concurrently; the smallest, a middle and the largest env are
+    checked against the oracle."""
+    shapes, env_mesh = inputs.uneven_batch(1024, 500, 20000, seed=12345)
+    meshes = [grid(s) for s in shapes]
+    alpha = inputs.compliance_draws(1024, 1e-7, 1e-5, seed=12345)
+    p = P()
+    steps = 30
+    sim = make_sim(meshes, p, 1024, env_mesh=env_mesh, env_compliance=alpha, seed=8)
+    assert sim.n_groups >= 2 and sim.resident_envs < 1024
+    vs = np.array([len(meshes[m][0]) for m in env_mesh])
+    sample = [int(np.argmin(vs)), int(np.argsort(vs)[512]), int(np.argmax(vs))]
+    oenvs, _ = oracle_envs(meshes, p, 1024, env_mesh=env_mesh, env_compliance=alpha, seed=8, envs=sample)
+    for _ in range(steps):
+        sim.step()
+    for oe in oenvs.values():
+        oe.run(steps, want_obs=False)
+    compare_states(sim, oenvs, meshes, 1024, env_mesh=env_mesh, label="uneven 1024")
