@@ -422,13 +422,22 @@ def run_ours(args):
             x, _, _ = sim.get_state()
             x = x.cpu().numpy().astype(np.float64)
             off = np.concatenate([[0], np.cumsum([c[0] for c in counts])])
-            errs = []
+            errs, floors = [], []
+            import oracle
             for e, oe in zip(sample_envs, oes):
                 ox, _, _ = oe.state()
                 errs.append(float(np.max(np.abs(x[off[e]:off[e + 1]] - ox)) / oe.mesh.extent))
-            acc = {"max_pos_err_over_extent": max(errs), "tolerance": POS_TOL, "envs": list(sample_envs),
+                # the oracle's own float32 build over the same steps: the rounding floor
+                o32 = oracle.Env(oracle.Mesh(*batch.meshes[batch.mesh_index(e)], precision="f32"),
+                                 batch.env_params(e))
+                o32.reset(seed, e)
+                o32.run(n_steps, want_obs=False)
+                floors.append(float(np.max(np.abs(o32.state()[0] - ox)) / oe.mesh.extent))
+            acc = {"max_pos_err_over_extent": max(errs), "per_env": errs, "tolerance": POS_TOL,
+                   "fp32_oracle_err_over_extent": floors, "envs": list(sample_envs),
                    "verts": [counts[e][0] for e in sample_envs], "steps": n_steps,
-                   "within_tolerance": max(errs) <= POS_TOL}
+                   "within_tolerance": max(errs) <= POS_TOL,
+                   "within_fp32_floor": all(g <= max(POS_TOL, 10 * f) for g, f in zip(errs, floors))}
             cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"envs {list(sample_envs)} ({[counts[e][0] for e in sample_envs]} vertices) x "
                              f"{n_steps} steps, FP64 oracle, 1 host thread, {dt:.1f} s"}

@@ -91,6 +91,12 @@ def _lib(precision: str = "f64") -> ctypes.CDLL:
             L.orc_project_edge.argtypes = [P, P, R, R, R, R, P, R]
             L.orc_project_tet.restype = R
             L.orc_project_tet.argtypes = [P, P, P, P, P, R, R, P]
+            L.orc_mlp_forward.argtypes = [P, P, P]
+            L.orc_env_residual.restype = D
+            L.orc_env_residual.argtypes = [P]
+            L.orc_env_features.argtypes = [P, P, P]
+            L.orc_env_step_surrogate.restype = I
+            L.orc_env_step_surrogate.argtypes = [P, P, P, D, P, D, I, P, P, P, P, P, P]
             _LIBS[precision] = L
         return _LIBS[precision]
 
@@ -170,6 +176,42 @@ class Params(ctypes.Structure):
             else:
                 setattr(p, name, val)
         return p
+
+
+class Net(ctypes.Structure):
+    """Warm-start network parameters with frozen normalisation (orc_mlp)."""
+    _fields_ = [
+        ("W1", (ctypes.c_double * 15) * 64), ("b1", ctypes.c_double * 64),
+        ("W2", (ctypes.c_double * 64) * 64), ("b2", ctypes.c_double * 64),
+        ("W3", (ctypes.c_double * 64) * 3), ("b3", ctypes.c_double * 3),
+        ("in_mean", ctypes.c_double * 15), ("in_std", ctypes.c_double * 15),
+        ("out_mean", ctypes.c_double * 3), ("out_std", ctypes.c_double * 3),
+        ("bf16", ctypes.c_int),
+    ]
+
+    @classmethod
+    def from_params(cls, p: dict, in_mean=None, in_std=None, out_mean=None, out_std=None, bf16=False):
+        n = cls()
+        for k in ("W1", "b1", "W2", "b2", "W3", "b3"):
+            arr = np.ascontiguousarray(p[k], dtype=np.float64)
+            ctypes.memmove(ctypes.addressof(getattr(n, k)), arr.ctypes.data, arr.nbytes)
+        for k, val, size in (("in_mean", in_mean, 15), ("in_std", in_std, 15),
+                             ("out_mean", out_mean, 3), ("out_std", out_std, 3)):
+            default = 0.0 if "mean" in k else 1.0
+            arr = np.full(size, default) if val is None else np.ascontiguousarray(val, dtype=np.float64)
+            ctypes.memmove(ctypes.addressof(getattr(n, k)), arr.ctypes.data, arr.nbytes)
+        n.bf16 = int(bool(bf16))
+        return n
+
+
+def net_forward(net: "Net", feats) -> np.ndarray:
+    """The C oracle's network on feature rows [n][15] (de-normalised output [n][3])."""
+    L = _lib()
+    F = np.ascontiguousarray(feats, dtype=np.float64).reshape(-1, 15)
+    out = np.zeros((len(F), 3))
+    for i in range(len(F)):
+        L.orc_mlp_forward(ctypes.byref(net), _ptr(F[i]), _ptr(out[i]))
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -324,6 +366,43 @@ class Env:
         obs_ids = out[4:4 + n_obs].copy()
         contacts = out[4 + n_obs:4 + n_obs + n_c].copy()
         return {"t": t, "target": target, "obs_ids": obs_ids, "contacts": contacts}
+
+    def features(self) -> np.ndarray:
+        """Features [V][15] of the next substep's predicted state."""
+        F = np.zeros((self.mesh.V, 15))
+        self._L.orc_env_features(self._h, ctypes.byref(self._p), _ptr(F))
+        return F
+
+    def residual(self) -> float:
+        return float(self._L.orc_env_residual(self._h))
+
+    def step_surrogate(self, net, threshold: float, n_full: int, action=None, alpha_d: float = -1.0):
+        """Surrogate-assisted step; returns (obs, reward, done, fallbacks)."""
+        obs = np.zeros(self.obs_dim)
+        rew = np.zeros(1)
+        done = np.zeros(1, dtype=np.uint8)
+        fb = np.zeros(1, dtype=np.int32)
+        a = None if action is None else np.ascontiguousarray(action, dtype=np.float64).reshape(3)
+        rc = self._L.orc_env_step_surrogate(self._h, ctypes.byref(self._p), _ptr(a) if a is not None else None,
+                                            float(alpha_d), ctypes.byref(net), float(threshold), int(n_full),
+                                            _ptr(obs), _ptr(rew), _ptr(done), _ptr(fb), None, None)
+        if rc != 0:
+            raise ValueError(f"orc_env_step_surrogate rc={rc}")
+        return obs, float(rew[0]), int(done[0]), int(fb[0])
+
+    def step_record(self, n_full: int, action=None, alpha_d: float = -1.0):
+        """Plain step with `n_full` iterations recording per substep the
+        features [S][V][15] and targets [S][V][3] (solve minus prediction)."""
+        S, V = self.params["substeps"], self.mesh.V
+        F = np.zeros((S, V, 15))
+        T = np.zeros((S, V, 3))
+        a = None if action is None else np.ascontiguousarray(action, dtype=np.float64).reshape(3)
+        rc = self._L.orc_env_step_surrogate(self._h, ctypes.byref(self._p), _ptr(a) if a is not None else None,
+                                            float(alpha_d), None, 0.0, int(n_full), None, None, None, None,
+                                            _ptr(F), _ptr(T))
+        if rc != 0:
+            raise ValueError(f"orc_env_step_surrogate rc={rc}")
+        return F, T
 
     def tool_box(self):
         lo = np.zeros(3); hi = np.zeros(3)

@@ -651,3 +651,246 @@ void orc_env_get_tool_box(const orc_env* s, double* lo, double* hi) {
     for (int k = 0; k < 3; ++k) { lo[k] = (double)s->lo[k]; hi[k] = (double)s->hi[k]; }
 }
 int orc_real_size(void) { return (int)sizeof(REAL); }
+
+/* ------------------------------------------------------------------------ */
+/* Learned warm-start (not in the paper; the surrogate-assisted substep of   */
+/* the workload). The network is a per-vertex perceptron 15 -> 64 -> ReLU -> */
+/* 64 -> ReLU -> 3 whose output, de-normalised, is added to the predicted    */
+/* positions before one constraint iteration; a constraint residual above    */
+/* the threshold restores the prediction and runs the full solve instead.    */
+/* ------------------------------------------------------------------------ */
+
+#define ORC_NN_IN 15
+#define ORC_NN_HID 64
+#define ORC_NN_OUT 3
+
+/* Network parameters (output-major weights) and the frozen normalisation. */
+typedef struct {
+    double W1[ORC_NN_HID][ORC_NN_IN], b1[ORC_NN_HID];
+    double W2[ORC_NN_HID][ORC_NN_HID], b2[ORC_NN_HID];
+    double W3[ORC_NN_OUT][ORC_NN_HID], b3[ORC_NN_OUT];
+    double in_mean[ORC_NN_IN], in_std[ORC_NN_IN];
+    double out_mean[ORC_NN_OUT], out_std[ORC_NN_OUT];
+    int bf16;   /* round inputs, weights and hidden activations to bfloat16 */
+} orc_mlp;
+
+/* Round to the nearest bfloat16 (ties to even) through float32. */
+static double bf16r(double x) {
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+    memcpy(&f, &u, 4);
+    return (double)f;
+}
+
+/* y = W3 relu(W2 relu(W1 f + b1) + b2) + b3 on normalised input; returns the
+ * de-normalised output. */
+void orc_mlp_forward(const orc_mlp* n, const double* feat, double* out) {
+    double f[ORC_NN_IN], h1[ORC_NN_HID], h2[ORC_NN_HID];
+    for (int k = 0; k < ORC_NN_IN; ++k) {
+        f[k] = (feat[k] - n->in_mean[k]) / n->in_std[k];
+        if (n->bf16) f[k] = bf16r(f[k]);
+    }
+    for (int o = 0; o < ORC_NN_HID; ++o) {
+        double z = n->b1[o];
+        for (int k = 0; k < ORC_NN_IN; ++k) z += (n->bf16 ? bf16r(n->W1[o][k]) : n->W1[o][k]) * f[k];
+        h1[o] = z > 0 ? z : 0;
+        if (n->bf16) h1[o] = bf16r(h1[o]);
+    }
+    for (int o = 0; o < ORC_NN_HID; ++o) {
+        double z = n->b2[o];
+        for (int k = 0; k < ORC_NN_HID; ++k) z += (n->bf16 ? bf16r(n->W2[o][k]) : n->W2[o][k]) * h1[k];
+        h2[o] = z > 0 ? z : 0;
+        if (n->bf16) h2[o] = bf16r(h2[o]);
+    }
+    for (int o = 0; o < ORC_NN_OUT; ++o) {
+        double z = n->b3[o];
+        for (int k = 0; k < ORC_NN_HID; ++k) z += (n->bf16 ? bf16r(n->W3[o][k]) : n->W3[o][k]) * h2[k];
+        out[o] = z * n->out_std[o] + n->out_mean[o];
+    }
+}
+
+/* 1-ring of every vertex: the vertices sharing an edge with it. */
+static void one_ring(const orc_mesh* m, int* off, int* nbr) {
+    for (int i = 0; i <= m->V; ++i) off[i] = 0;
+    for (int e = 0; e < m->E; ++e) { off[m->edge[2 * e] + 1]++; off[m->edge[2 * e + 1] + 1]++; }
+    for (int i = 0; i < m->V; ++i) off[i + 1] += off[i];
+    int* fill = (int*)calloc((size_t)(m->V > 0 ? m->V : 1), sizeof(int));
+    for (int e = 0; e < m->E; ++e) {
+        int a = m->edge[2 * e], b = m->edge[2 * e + 1];
+        nbr[off[a] + fill[a]++] = b;
+        nbr[off[b] + fill[b]++] = a;
+    }
+    free(fill);
+}
+
+/* Features of every vertex from predicted positions xh and velocities vh:
+ * displacement from rest, velocity, 1-ring mean position and velocity as
+ * offsets from the vertex, offset from the tool centre. */
+static void features(const orc_env* s, const REAL* xh, const REAL* vh, double* F) {
+    const orc_mesh* m = s->m;
+    int* off = (int*)malloc(sizeof(int) * (m->V + 1));
+    int* nbr = (int*)malloc(sizeof(int) * (2 * m->E + 1));
+    one_ring(m, off, nbr);
+    for (int i = 0; i < m->V; ++i) {
+        double* f = &F[(size_t)ORC_NN_IN * i];
+        double mx[3] = {0, 0, 0}, mv[3] = {0, 0, 0};
+        int deg = off[i + 1] - off[i];
+        for (int q = off[i]; q < off[i + 1]; ++q)
+            for (int k = 0; k < 3; ++k) { mx[k] += (double)xh[3 * nbr[q] + k]; mv[k] += (double)vh[3 * nbr[q] + k]; }
+        for (int k = 0; k < 3; ++k) {
+            double xi = (double)xh[3 * i + k], vi = (double)vh[3 * i + k];
+            f[k] = xi - (double)m->rest[3 * i + k];
+            f[3 + k] = vi;
+            f[6 + k] = deg ? mx[k] / deg - xi : 0.0;
+            f[9 + k] = deg ? mv[k] / deg - vi : 0.0;
+            f[12 + k] = xi - (double)s->c[k];
+        }
+    }
+    free(off);
+    free(nbr);
+}
+
+/* Largest relative constraint violation at the current positions:
+ * |C| / d for edges, |C| / |V0| for tets. */
+double orc_env_residual(const orc_env* s) {
+    const orc_mesh* m = s->m;
+    double r = 0;
+    for (int e = 0; e < m->E; ++e) {
+        REAL ab[3];
+        vsub(&s->x[3 * m->edge[2 * e]], &s->x[3 * m->edge[2 * e + 1]], ab);
+        double c = fabs((double)(vnorm(ab) - m->d[e])) / (double)m->d[e];
+        if (c > r) r = c;
+    }
+    for (int t = 0; t < m->T; ++t) {
+        const int* q = &m->tet[4 * t];
+        double c = fabs((double)(tet_volume(&s->x[3 * q[0]], &s->x[3 * q[1]], &s->x[3 * q[2]], &s->x[3 * q[3]]) -
+                                 m->V0[t])) / fabs((double)m->V0[t]);
+        if (c > r) r = c;
+    }
+    return r;
+}
+
+/* Predicted state of the next substep (no change to the env): positions and
+ * velocities after the prediction of Algorithm 1. */
+static void predicted(const orc_env* s, const orc_params* p, REAL h, REAL* xh, REAL* vh) {
+    const orc_mesh* m = s->m;
+    for (int i = 0; i < m->V; ++i)
+        for (int k = 0; k < 3; ++k) {
+            xh[3 * i + k] = s->x[3 * i + k];
+            vh[3 * i + k] = s->v[3 * i + k];
+            if (m->w[i] > 0) {
+                vh[3 * i + k] += h * (REAL)p->gravity[k];
+                xh[3 * i + k] += h * vh[3 * i + k];
+            }
+        }
+}
+
+/* Features [V][15] of the next substep's predicted state. */
+void orc_env_features(const orc_env* s, const orc_params* p, double* F) {
+    REAL h = (REAL)(p->dt / p->substeps);
+    REAL* xh = (REAL*)malloc(sizeof(REAL) * 3 * s->V);
+    REAL* vh = (REAL*)malloc(sizeof(REAL) * 3 * s->V);
+    predicted(s, p, h, xh, vh);
+    features(s, xh, vh, F);
+    free(xh);
+    free(vh);
+}
+
+/* One constraint sweep (all distance colours, then all volume colours). */
+static void sweep(orc_env* s, const orc_params* p, REAL h, REAL alpha_d) {
+    const orc_mesh* m = s->m;
+    const REAL min_len = (REAL)1e-12 * m->extent;
+    REAL at_d = alpha_d / (h * h), at_v = (REAL)p->alpha_v / (h * h);
+    for (int c = 0; c < m->n_ecol; ++c)
+        for (int q = m->ecol_off[c]; q < m->ecol_off[c + 1]; ++q) {
+            int e = m->eorder[q], a = m->edge[2 * e], b = m->edge[2 * e + 1];
+            orc_project_edge(&s->x[3 * a], &s->x[3 * b], m->w[a], m->w[b], m->d[e], at_d, &s->lam_e[e], min_len);
+        }
+    for (int c = 0; c < m->n_tcol; ++c)
+        for (int q = m->tcol_off[c]; q < m->tcol_off[c + 1]; ++q) {
+            int t = m->torder[q];
+            const int* v4 = &m->tet[4 * t];
+            REAL w4[4] = {m->w[v4[0]], m->w[v4[1]], m->w[v4[2]], m->w[v4[3]]};
+            orc_project_tet(&s->x[3 * v4[0]], &s->x[3 * v4[1]], &s->x[3 * v4[2]], &s->x[3 * v4[3]], w4, m->V0[t],
+                            at_v, &s->lam_t[t]);
+        }
+}
+
+/* Surrogate-assisted step: per substep predict, add the network's correction
+ * to free vertices, one constraint iteration, residual check; above
+ * `threshold` the prediction is restored and `n_full` iterations run instead.
+ * Then collision and velocity update as in the plain substep. `fallbacks`
+ * (may be NULL) receives the number of substeps that fell back. When
+ * `record_F`/`record_T` are given (and `net` is NULL) the step is the plain
+ * full solve and records, per substep, the features [substeps][V][15] and the
+ * targets [substeps][V][3] = positions after the full solve minus prediction. */
+int orc_env_step_surrogate(orc_env* s, const orc_params* p, const double* action, double alpha_d,
+                           const orc_mlp* net, double threshold, int n_full, double* obs, double* reward,
+                           unsigned char* done, int* fallbacks, double* record_F, double* record_T) {
+    const orc_mesh* m = s->m;
+    double a[3];
+    for (int k = 0; k < 3; ++k)
+        a[k] = action ? action[k] : orc_action(s->seed, s->env, (uint64_t)s->t, k);
+    for (int k = 0; k < 3; ++k) {
+        REAL c = s->c[k] + (REAL)(p->action_scale * a[k]);
+        if (c < s->lo[k]) c = s->lo[k];
+        if (c > s->hi[k]) c = s->hi[k];
+        s->c[k] = c;
+    }
+    REAL h = (REAL)(p->dt / p->substeps);
+    REAL ad = (REAL)(alpha_d >= 0 ? alpha_d : p->alpha_d);
+    REAL* xh = (REAL*)malloc(sizeof(REAL) * 3 * m->V);
+    REAL* vh = (REAL*)malloc(sizeof(REAL) * 3 * m->V);
+    double* F = (double*)malloc(sizeof(double) * ORC_NN_IN * m->V);
+    int nfb = 0;
+    for (int sub = 0; sub < p->substeps; ++sub) {
+        predicted(s, p, h, xh, vh);
+        for (int i = 0; i < 3 * m->V; ++i) { s->xprev[i] = s->x[i]; s->x[i] = xh[i]; s->v[i] = vh[i]; }
+        for (int e = 0; e < m->E; ++e) s->lam_e[e] = 0;
+        for (int t = 0; t < m->T; ++t) s->lam_t[t] = 0;
+        if (net) {
+            features(s, xh, vh, F);
+            for (int i = 0; i < m->V; ++i) {
+                if (m->w[i] == 0) continue;
+                double dx[3];
+                orc_mlp_forward(net, &F[(size_t)ORC_NN_IN * i], dx);
+                for (int k = 0; k < 3; ++k) s->x[3 * i + k] += (REAL)dx[k];
+            }
+            sweep(s, p, h, ad);
+            if (orc_env_residual(s) > threshold) {
+                ++nfb;
+                for (int i = 0; i < 3 * m->V; ++i) s->x[i] = xh[i];
+                for (int e = 0; e < m->E; ++e) s->lam_e[e] = 0;
+                for (int t = 0; t < m->T; ++t) s->lam_t[t] = 0;
+                for (int it = 0; it < n_full; ++it) sweep(s, p, h, ad);
+            }
+        } else {
+            if (record_F) features(s, xh, vh, &record_F[(size_t)sub * ORC_NN_IN * m->V]);
+            for (int it = 0; it < n_full; ++it) sweep(s, p, h, ad);
+            if (record_T)
+                for (int i = 0; i < 3 * m->V; ++i)
+                    record_T[(size_t)sub * 3 * m->V + i] = (double)(s->x[i] - xh[i]);
+        }
+        collide_sphere(s, (REAL)p->radius, sub == p->substeps - 1);
+        for (int i = 0; i < 3 * m->V; ++i) s->v[i] = (s->x[i] - s->xprev[i]) / h;
+    }
+    free(xh);
+    free(vh);
+    free(F);
+    if (fallbacks) *fallbacks = nfb;
+    if (obs) {
+        for (int k = 0; k < 3; ++k) obs[k] = (double)s->c[k];
+        for (int q = 0; q < s->n_obs; ++q)
+            for (int k = 0; k < 3; ++k) obs[3 + 3 * q + k] = (double)s->x[3 * s->obs[q] + k];
+    }
+    REAL l = dist3(s->c, &s->x[3 * s->target]);
+    int succ = l < (REAL)p->success_dist;
+    REAL R = (REAL)p->w_l * l + (REAL)p->w_d * (l - s->l_prev) + (REAL)p->w_s * (REAL)succ;
+    s->l_prev = l;
+    s->t += 1;
+    if (reward) *reward = (double)R;
+    if (done) *done = (unsigned char)(((p->max_steps > 0 && s->t >= p->max_steps) || succ) ? 1 : 0);
+    return ORC_OK;
+}
