@@ -169,6 +169,25 @@ int ffsrl_get_mesh_table(const ffsrl_sim* sim, int32_t mesh, int32_t which, int3
 int ffsrl_get_env_ints(ffsrl_sim* sim, int32_t env, int32_t* step_count, int32_t* target,
                        int32_t* obs_ids_host, int32_t* n_contacts, int32_t* contacts_host);
 
+/* --- learned warm-start network (not in the paper; the workload's per-vertex
+ *     15-64-64-3 ReLU perceptron, BF16 weights and activations, FP32
+ *     accumulation, run on the tensor cores) --------------------------------- */
+
+#define FFSRL_NET_PARAMS 5283  /* W1[64][15], b1[64], W2[64][64], b2[64], W3[3][64], b3[3] */
+#define FFSRL_NET_NORM 36      /* in_mean[15], in_std[15], out_mean[3], out_std[3] */
+
+/* Installs the network: params_host [FFSRL_NET_PARAMS] float32 master weights
+ * (rounded to BF16 inside), norm_host [FFSRL_NET_NORM] the frozen feature and
+ * output normalisation (std > 0). Host buffers; the call copies them. */
+int ffsrl_set_network(ffsrl_sim* sim, const float* params_host, const float* norm_host);
+
+/* out_dev[r] = (network output of features_dev[r], 0) for r < rows:
+ * features_dev [rows][16] float32 raw features (the 16th is ignored), output
+ * [rows][4] float32 de-normalised (x, y, z, 0). Asynchronous on the sim's
+ * stream; a tensor-core completion timeout is reported by ffsrl_sync
+ * (FFSRL_E_TIMEOUT). */
+int ffsrl_network_forward(ffsrl_sim* sim, const float* features_dev, float* out_dev, int64_t rows);
+
 /* --- allocation-free step (no counterpart in the paper) ------------------- */
 
 /* Size of the static device scratch array used by ffsrl_step_noalloc. */

@@ -11,10 +11,12 @@
 #include <tuple>
 #include <vector>
 
+#include <cstdint>
 #include <cuda_runtime.h>
 
 #include "../../include/ffsrl.h"
 #include "mesh_setup.h"
+#include "mlp_tc.h"
 #include "xpbd_device.cuh"
 #include "xpbd_launch.h"
 
@@ -95,6 +97,13 @@ struct ffsrl_sim {
     std::vector<LaunchGroup> groups;
     cudaEvent_t fork = nullptr;
     int resident_envs = 0, ring_envs = 0;
+    int n_sm = 0;
+    // warm-start network (tensor-core tiles, biases, normalisation)
+    bool has_net = false;
+    MlpDev net{};
+    uint16_t* d_wtiles = nullptr;
+    float* d_bias = nullptr;
+    int* d_net_err = nullptr;
 
     template <class T>
     cudaError_t alloc(T** p, size_t count) {
@@ -350,6 +359,9 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
     int max_optin = 0;
     FFSRL_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device));
     s->max_smem = size_t(max_optin);
+    FFSRL_CUDA(cudaDeviceGetAttribute(&s->n_sm, cudaDevAttrMultiProcessorCount, s->device));
+    FFSRL_CUDA(s->alloc(&s->d_net_err, 1));
+    FFSRL_CUDA(cudaMemset(s->d_net_err, 0, sizeof(int)));
 
     for (int v = 0; v < 2; ++v) {
         s->h_meshes[v].resize(s->meshes.size());
@@ -618,6 +630,12 @@ int ffsrl_sync(ffsrl_sim* sim) {
     if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
     FFSRL_CUDA(cudaSetDevice(sim->device));
     FFSRL_CUDA(cudaStreamSynchronize(sim->stream));
+    int net_err = 0;
+    FFSRL_CUDA(cudaMemcpy(&net_err, sim->d_net_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (net_err) {
+        FFSRL_CUDA(cudaMemset(sim->d_net_err, 0, sizeof(int)));
+        return fail(FFSRL_E_TIMEOUT, "a tensor-core completion wait of the warm-start network timed out");
+    }
     std::vector<int> err(sim->n_env);
     FFSRL_CUDA(cudaMemcpy(err.data(), sim->S.err, err.size() * sizeof(int), cudaMemcpyDeviceToHost));
     int first = -1, bits = 0;
@@ -632,6 +650,54 @@ int ffsrl_sync(ffsrl_sim* sim) {
             return fail(FFSRL_E_TIMEOUT, "a constraint-record copy timed out in env " + std::to_string(first));
         return fail(FFSRL_E_NAN, "non-finite positions in env " + std::to_string(first));
     }
+    return FFSRL_OK;
+}
+
+int ffsrl_set_network(ffsrl_sim* sim, const float* params_host, const float* norm_host) {
+    if (!sim || !params_host || !norm_host) return fail(FFSRL_E_INVAL, "sim, params and norm must be non-NULL");
+    for (int i = 0; i < FFSRL_NET_PARAMS; ++i)
+        if (!std::isfinite(params_host[i])) return fail(FFSRL_E_INVAL, "non-finite network parameter");
+    for (int i = 0; i < FFSRL_NET_NORM; ++i)
+        if (!std::isfinite(norm_host[i])) return fail(FFSRL_E_INVAL, "non-finite normalisation value");
+    for (int k = 0; k < 15; ++k)
+        if (!(norm_host[15 + k] > 0)) return fail(FFSRL_E_INVAL, "feature std must be > 0");
+    for (int k = 0; k < 3; ++k)
+        if (!(norm_host[33 + k] > 0)) return fail(FFSRL_E_INVAL, "output std must be > 0");
+    FFSRL_CUDA(cudaSetDevice(sim->device));
+    std::vector<uint16_t> tiles(kMlpWeightBytes / 2, 0);
+    std::vector<float> bias(144, 0.f);
+    pack_mlp_weights(params_host, tiles.data(), bias.data());
+    if (!sim->d_wtiles) {
+        FFSRL_CUDA(sim->alloc(&sim->d_wtiles, tiles.size()));
+        FFSRL_CUDA(sim->alloc(&sim->d_bias, bias.size()));
+    }
+    FFSRL_CUDA(cudaMemcpyAsync(sim->d_wtiles, tiles.data(), tiles.size() * 2, cudaMemcpyHostToDevice, sim->stream));
+    FFSRL_CUDA(cudaMemcpyAsync(sim->d_bias, bias.data(), bias.size() * 4, cudaMemcpyHostToDevice, sim->stream));
+    FFSRL_CUDA(cudaStreamSynchronize(sim->stream));
+    MlpDev& n = sim->net;
+    n.wtiles = sim->d_wtiles;
+    n.bias = sim->d_bias;
+    for (int k = 0; k < 16; ++k) {
+        n.in_mean[k] = k < 15 ? norm_host[k] : 0.f;
+        n.in_inv_std[k] = k < 15 ? 1.0f / norm_host[15 + k] : 0.f;
+    }
+    for (int k = 0; k < 4; ++k) {
+        n.out_mean[k] = k < 3 ? norm_host[30 + k] : 0.f;
+        n.out_std[k] = k < 3 ? norm_host[33 + k] : 0.f;
+    }
+    sim->has_net = true;
+    return FFSRL_OK;
+}
+
+int ffsrl_network_forward(ffsrl_sim* sim, const float* features_dev, float* out_dev, int64_t rows) {
+    if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
+    if (!sim->has_net) return fail(FFSRL_E_INVAL, "no network installed (ffsrl_set_network)");
+    if (rows < 0 || (rows > 0 && (!features_dev || !out_dev))) return fail(FFSRL_E_INVAL, "bad rows or buffers");
+    if ((reinterpret_cast<uintptr_t>(features_dev) | reinterpret_cast<uintptr_t>(out_dev)) & 15)
+        return fail(FFSRL_E_INVAL, "features and output must be 16-byte aligned");
+    FFSRL_CUDA(cudaSetDevice(sim->device));
+    FFSRL_CUDA(launch_mlp_forward(sim->net, reinterpret_cast<const float4*>(features_dev),
+                                  reinterpret_cast<float4*>(out_dev), rows, sim->d_net_err, sim->n_sm, sim->stream));
     return FFSRL_OK;
 }
 

@@ -1,0 +1,38 @@
+// Warm-start network on tensor cores (internal to the library).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ffsrl {
+
+// BF16 weight tiles: W1 (64 x 16), W2 (64 x 64), W3 (16 x 64), K-major core-matrix layout.
+constexpr int kMlpWeightBytes = (64 * 16 + 64 * 64 + 16 * 64) * 2;
+constexpr int kMlpParams = 64 * 15 + 64 + 64 * 64 + 64 + 3 * 64 + 3;   // float32 master parameters
+
+struct MlpDev {
+    const uint16_t* wtiles;   // kMlpWeightBytes
+    const float* bias;        // b1[64], b2[64], b3[16] (zero padded)
+    float in_mean[16], in_inv_std[16];
+    float out_mean[4], out_std[4];
+};
+
+// Instruction descriptor of tcgen05.mma kind::f16: BF16 A and B (both
+// K-major), FP32 accumulator, M x N tile.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+size_t mlp_forward_smem_bytes();
+
+// out[r] = (de-normalised network output of feat[r], 0); feat is [rows][16]
+// raw features (the 16th ignored); err gets bit 0 on an MMA timeout.
+cudaError_t launch_mlp_forward(const MlpDev& net, const float4* feat, float4* out, long long rows, int* err,
+                               int n_sm, cudaStream_t st);
+
+// Packs float32 master parameters (W1[64][15], b1, W2[64][64], b2, W3[3][64],
+// b3) into BF16 tiles and the padded bias vector.
+void pack_mlp_weights(const float* params, uint16_t* tiles, float* bias);
+
+}  // namespace ffsrl

@@ -27,7 +27,8 @@ TABLES = {"tets": 0, "flipped": 1, "edges": 2, "ecolor": 3, "tcolor": 4, "eorder
 # every symbol include/ffsrl.h declares
 EXPORTS = ["ffsrl_create", "ffsrl_reset", "ffsrl_step", "ffsrl_step_host", "ffsrl_sync",
            "ffsrl_destroy", "ffsrl_get_info", "ffsrl_last_error", "ffsrl_get_state",
-           "ffsrl_set_state", "ffsrl_get_mesh_table", "ffsrl_get_env_ints", "ffsrl_step_noalloc"]
+           "ffsrl_set_state", "ffsrl_get_mesh_table", "ffsrl_get_env_ints", "ffsrl_step_noalloc",
+           "ffsrl_set_network", "ffsrl_network_forward"]
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -102,6 +103,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.ffsrl_get_env_ints.argtypes = [P, I32, P, P, P, P, P]
     L.ffsrl_step_noalloc.restype = ctypes.c_int
     L.ffsrl_step_noalloc.argtypes = [P, P, P, P, P]
+    L.ffsrl_set_network.restype = ctypes.c_int
+    L.ffsrl_set_network.argtypes = [P, P, P]
+    L.ffsrl_network_forward.restype = ctypes.c_int
+    L.ffsrl_network_forward.argtypes = [P, P, P, ctypes.c_int64]
     _lib = L
     return L
 
@@ -244,6 +249,23 @@ class Sim:
         (x, v [total_verts][3] float32, tool [n_env][3] float64, updated in
         place) with this sim's meshes; allocates nothing."""
         _check(self._L.ffsrl_step_noalloc(self._h, _dptr(actions), _dptr(x), _dptr(v), _dptr(tool)))
+
+    # -- warm-start network ---------------------------------------------------
+    def set_network(self, params: dict, in_mean, in_std, out_mean, out_std) -> None:
+        """Installs float32 master weights (dict W1, b1, W2, b2, W3, b3) and the normalisation."""
+        flat = np.concatenate([np.asarray(params[k], np.float32).reshape(-1)
+                               for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+        norm = np.concatenate([np.asarray(a, np.float32).reshape(-1) for a in (in_mean, in_std, out_mean, out_std)])
+        assert flat.size == 5283 and norm.size == 36
+        _check(self._L.ffsrl_set_network(self._h, _np_ptr(flat), _np_ptr(norm)))
+
+    def network_forward(self, features, out=None):
+        """features: CUDA tensor [rows][16] float32 -> output [rows][4]."""
+        torch = self._torch
+        if out is None:
+            out = torch.empty((features.shape[0], 4), dtype=torch.float32, device=features.device)
+        _check(self._L.ffsrl_network_forward(self._h, _dptr(features), _dptr(out), int(features.shape[0])))
+        return out
 
     def sync(self) -> None:
         _check(self._L.ffsrl_sync(self._h))

@@ -1,0 +1,81 @@
+"""The tensor-core warm-start network (tcgen05, BF16 operands, FP32
+accumulation) against the oracle network evaluated with the same bfloat16
+rounding points (inputs after normalisation, weights, hidden activations).
+
+The remaining differences come from FP32 versus FP64 accumulation and the
+occasional bfloat16 rounding flip they cause (one bf16 ulp = 2^-8 relative),
+so the bar is 3e-2 of the output scale per element and 2e-3 on average.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_18616_gb300 import inputs
+from sim_helpers import grid, make_sim
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+def _network(seed):
+    p = oracle.mlp_init(seed)
+    rng = np.random.default_rng(seed + 100)
+    for k in ("b1", "b2", "b3"):
+        p[k] = rng.normal(0, 0.1, p[k].shape)
+    in_mean = rng.normal(0, 1e-3, 15)
+    in_std = rng.uniform(1e-3, 5e-3, 15)
+    out_mean = rng.normal(0, 1e-6, 3)
+    out_std = rng.uniform(1e-6, 5e-6, 3)
+    return p, in_mean, in_std, out_mean, out_std
+
+
+def _features(n, in_mean, in_std, seed):
+    rng = np.random.default_rng(seed)
+    F = np.zeros((n, 16), dtype=np.float32)
+    F[:, :15] = rng.normal(size=(n, 15)) * in_std + in_mean
+    return F
+
+
+def _check(sim, net, F_gpu_rows, F_host, out_gpu, out_std):
+    ref = oracle.net_forward(net, F_host[:, :15].astype(np.float64))
+    got = out_gpu[:, :3].astype(np.float64)
+    assert np.all(out_gpu[:, 3] == 0)
+    err = np.abs(got - ref) / out_std
+    assert err.max() <= 3e-2, err.max()
+    assert err.mean() <= 2e-3, err.mean()
+    # and the network is not trivially zero
+    assert np.abs(ref / out_std).mean() > 0.05
+
+
+@pytest.mark.parametrize("rows", [1, 127, 128, 129, 1000, 4711])
+def test_network_forward_matches_bf16_oracle(rows):
+    p, im, isd, om, osd = _network(3)
+    sim = make_sim([grid((3, 3, 2))], inputs.default_params(n_obs=4), 1)
+    sim.set_network(p, im, isd, om, osd)
+    F = _features(rows, im, isd, 7 + rows)
+    out = sim.network_forward(torch.from_numpy(F).cuda())
+    sim.sync()
+    net = oracle.Net.from_params(p, im, isd, om, osd, bf16=True)
+    _check(sim, net, None, F, out.cpu().numpy(), osd)
+
+
+def test_network_forward_full_batch_sampled():
+    """All 4096 x 2601 vertex rows of the warm-start workload in one launch;
+    sampled rows are checked (rows are independent)."""
+    p, im, isd, om, osd = _network(5)
+    sim = make_sim([grid((3, 3, 2))], inputs.default_params(n_obs=4), 1)
+    sim.set_network(p, im, isd, om, osd)
+    rows = 4096 * 2601
+    g = torch.Generator(device="cuda").manual_seed(11)
+    F = torch.randn((rows, 16), generator=g, device="cuda")
+    F[:, :15] = F[:, :15] * torch.tensor(isd, dtype=torch.float32, device="cuda") + \
+        torch.tensor(im, dtype=torch.float32, device="cuda")
+    out = sim.network_forward(F)
+    sim.sync()
+    idx = np.concatenate([np.arange(0, 300), np.random.default_rng(0).integers(0, rows, 3000),
+                          np.arange(rows - 300, rows)])
+    net = oracle.Net.from_params(p, im, isd, om, osd, bf16=True)
+    _check(sim, net, idx, F[idx].cpu().numpy(), out[idx].cpu().numpy(), osd)
