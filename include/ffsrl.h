@@ -173,7 +173,7 @@ int ffsrl_get_env_ints(ffsrl_sim* sim, int32_t env, int32_t* step_count, int32_t
  *     15-64-64-3 ReLU perceptron, BF16 weights and activations, FP32
  *     accumulation, run on the tensor cores) --------------------------------- */
 
-#define FFSRL_NET_PARAMS 5283  /* W1[64][15], b1[64], W2[64][64], b2[64], W3[3][64], b3[3] */
+#define FFSRL_NET_PARAMS 5379  /* W1[64][15], b1[64], W2[64][64], b2[64], W3[3][64], b3[3] */
 #define FFSRL_NET_NORM 36      /* in_mean[15], in_std[15], out_mean[3], out_std[3] */
 
 /* Installs the network: params_host [FFSRL_NET_PARAMS] float32 master weights

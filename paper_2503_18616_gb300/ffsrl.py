@@ -31,6 +31,8 @@ EXPORTS = ["ffsrl_create", "ffsrl_reset", "ffsrl_step", "ffsrl_step_host", "ffsr
            "ffsrl_set_network", "ffsrl_network_forward"]
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
+NET_PARAMS = 64 * 15 + 64 + 64 * 64 + 64 + 3 * 64 + 3   # FFSRL_NET_PARAMS
+NET_NORM = 15 + 15 + 3 + 3                              # FFSRL_NET_NORM
 
 
 class FfsrlError(RuntimeError):
@@ -256,7 +258,7 @@ class Sim:
         flat = np.concatenate([np.asarray(params[k], np.float32).reshape(-1)
                                for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
         norm = np.concatenate([np.asarray(a, np.float32).reshape(-1) for a in (in_mean, in_std, out_mean, out_std)])
-        assert flat.size == 5283 and norm.size == 36
+        assert flat.size == NET_PARAMS and norm.size == NET_NORM
         _check(self._L.ffsrl_set_network(self._h, _np_ptr(flat), _np_ptr(norm)))
 
     def network_forward(self, features, out=None):

@@ -86,3 +86,11 @@ def test_no_gpu_means_cuda_error_not_fallback(lib):
         pytest.skip("a GPU is present")
     rc, h = _create(lib, _params_struct(n_obs=4))
     assert rc == -2 and not h.value
+
+
+def test_header_constants_match_the_binding():
+    text = open(os.path.join(ROOT, "include", "ffsrl.h")).read()
+    consts = dict(re.findall(r"#define (FFSRL_[A-Z_0-9]+) \(?([0-9]+)", text))
+    assert int(consts["FFSRL_NET_PARAMS"]) == ffsrl.NET_PARAMS == 5379
+    assert int(consts["FFSRL_NET_NORM"]) == ffsrl.NET_NORM == 36
+    assert ffsrl.NOALLOC_SCRATCH_BYTES == 32 << 20
