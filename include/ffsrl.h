@@ -188,6 +188,28 @@ int ffsrl_set_network(ffsrl_sim* sim, const float* params_host, const float* nor
  * (FFSRL_E_TIMEOUT). */
 int ffsrl_network_forward(ffsrl_sim* sim, const float* features_dev, float* out_dev, int64_t rows);
 
+/* Surrogate-assisted step of every env (the warm-start; requires a network):
+ * per substep, predict (Algorithm 1), add the network's correction to free
+ * vertices, run one constraint iteration, and if the largest relative
+ * constraint violation of the env (|C|/d for edges, |C|/|V0| for tets) exceeds
+ * `threshold`, restore the prediction and run `n_full` iterations instead;
+ * then collision and velocity update. Outputs as ffsrl_step; fallbacks_dev
+ * [n_env] int32 (may be NULL) is incremented once per fallen-back substep.
+ * Asynchronous. */
+int ffsrl_step_surrogate(ffsrl_sim* sim, const float* actions_dev, float* obs_dev, float* reward_dev,
+                         uint8_t* done_dev, double threshold, int32_t n_full, int32_t* fallbacks_dev);
+
+/* Plain step with `n_full` iterations per substep that records training data:
+ * features_dev [substeps][rows][16] (features of every vertex row at each
+ * substep's prediction) and targets_dev [substeps][rows][4] (positions after
+ * the solve minus the prediction, before collision). Rows: ffsrl_get_rows. */
+int ffsrl_record_step(ffsrl_sim* sim, const float* actions_dev, int32_t n_full, float* features_dev,
+                      float* targets_dev);
+
+/* Row layout of per-vertex buffers: *n_rows rows; env e's vertices occupy
+ * rows row_off_host[e] .. row_off_host[e] + V_e - 1 (row_off_host [n_env] or NULL). */
+int ffsrl_get_rows(const ffsrl_sim* sim, int64_t* n_rows, int32_t* row_off_host);
+
 /* --- allocation-free step (no counterpart in the paper) ------------------- */
 
 /* Size of the static device scratch array used by ffsrl_step_noalloc. */

@@ -19,6 +19,7 @@
 #include "mlp_tc.h"
 #include "xpbd_device.cuh"
 #include "xpbd_launch.h"
+#include "xpbd_surrogate.h"
 
 using namespace ffsrl;
 
@@ -104,6 +105,11 @@ struct ffsrl_sim {
     uint16_t* d_wtiles = nullptr;
     float* d_bias = nullptr;
     int* d_net_err = nullptr;
+    // surrogate-assisted substeps (allocated on first use)
+    long long lambda_slots = 0;
+    float4* d_feat = nullptr;     // [stride][4] features
+    float4* d_dx = nullptr;       // [stride] network corrections
+    float* d_lambda_full = nullptr;
 
     template <class T>
     cudaError_t alloc(T** p, size_t count) {
@@ -191,6 +197,22 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, bool permute, MeshDev& d) {
     d.vert_of = d_vert;
     d.rest_w = d_rw;
     d.top = d_top;
+    {
+        // 1-ring adjacency (vertices sharing an edge), vertex order
+        std::vector<int> off(m.V + 1, 0), nb(2 * size_t(m.E));
+        for (int e = 0; e < m.E; ++e) { ++off[m.edge[2 * e] + 1]; ++off[m.edge[2 * e + 1] + 1]; }
+        for (int i = 0; i < m.V; ++i) off[i + 1] += off[i];
+        std::vector<int> fill(off.begin(), off.end() - 1);
+        for (int e = 0; e < m.E; ++e) {
+            nb[fill[m.edge[2 * e]]++] = m.edge[2 * e + 1];
+            nb[fill[m.edge[2 * e + 1]]++] = m.edge[2 * e];
+        }
+        int *d_off, *d_nb;
+        FFSRL_CUDA(s->upload(&d_off, off.data(), off.size()));
+        FFSRL_CUDA(s->upload(&d_nb, nb.data(), nb.size()));
+        d.nbr_off = d_off;
+        d.nbr = d_nb;
+    }
     // Tool box around the rest bounding box and tool start above the top face.
     for (int k = 0; k < 2; ++k) {
         d.box_lo[k] = m.bbmin[k] - p.tool_margin_xy;
@@ -389,7 +411,7 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
         s->pstart[e] = int(pst);
         voff += d.Vp;
         pst += d.V;
-        if (p.iterations > 1) loff += d.E + d.T;
+        loff += d.E + d.T;   // multiplier slots (used with more than one iteration)
         if (voff > 0x7fffffffLL || pst > 0x7fffffffLL || loff > 0x7fffffffLL)
             return fail(FFSRL_E_INVAL, "too many vertices in total (more than 2^31 rows)");
     }
@@ -421,6 +443,7 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
     FFSRL_CUDA(s->alloc(&S.err, n_env));
     FFSRL_CUDA(cudaMemset(S.err, 0, n_env * sizeof(int)));
     S.lambda = nullptr;
+    s->lambda_slots = loff;
     if (p.iterations > 1) FFSRL_CUDA(s->alloc(&S.lambda, size_t(loff)));
     S.h = float(h);
     S.inv_h = float(1.0 / h);
@@ -698,6 +721,100 @@ int ffsrl_network_forward(ffsrl_sim* sim, const float* features_dev, float* out_
     FFSRL_CUDA(cudaSetDevice(sim->device));
     FFSRL_CUDA(launch_mlp_forward(sim->net, reinterpret_cast<const float4*>(features_dev),
                                   reinterpret_cast<float4*>(out_dev), rows, sim->d_net_err, sim->n_sm, sim->stream));
+    return FFSRL_OK;
+}
+
+namespace {
+
+int ensure_surrogate_buffers(ffsrl_sim* sim) {
+    if (sim->d_feat) return FFSRL_OK;
+    FFSRL_CUDA(sim->alloc(&sim->d_feat, 4 * size_t(sim->stride)));
+    FFSRL_CUDA(sim->alloc(&sim->d_dx, size_t(sim->stride)));
+    FFSRL_CUDA(cudaMemset(sim->d_feat, 0, 4 * size_t(sim->stride) * sizeof(float4)));
+    FFSRL_CUDA(cudaMemset(sim->d_dx, 0, size_t(sim->stride) * sizeof(float4)));
+    FFSRL_CUDA(sim->alloc(&sim->d_lambda_full, size_t(sim->lambda_slots)));
+    if (!sim->S.xg) {
+        for (const LaunchGroup& g : sim->groups)
+            if (!g.cfg.resident) return fail(FFSRL_E_INVAL, "internal: non-resident group without working copy");
+    }
+    return FFSRL_OK;
+}
+
+// Shared memory of the substep kernel for a group (0: not resident).
+size_t substep_smem(const ffsrl_sim* s, const LaunchGroup& g, bool& resident) {
+    int vp = 0;
+    for (int mi : g.meshes) vp = std::max(vp, s->h_meshes[1][mi].Vp);
+    const size_t res = substep_smem_bytes(vp, true);
+    resident = g.cfg.resident && res + 256 <= s->max_smem;
+    return resident ? res : substep_smem_bytes(vp, false);
+}
+
+// One surrogate or record step of every env: per substep the features, the
+// network (surrogate mode) and the substep kernel.
+int run_substeps(ffsrl_sim* sim, int mode, const float* actions, float* obs, float* reward, uint8_t* done,
+                 float threshold, int n_full, int* fallbacks, float* feat_out, float* target_out) {
+    int rc = ensure_surrogate_buffers(sim);
+    if (rc) return rc;
+    const int S_sub = sim->params.substeps;
+    const size_t rows = size_t(sim->stride);
+    for (int sub = 0; sub < S_sub; ++sub) {
+        float4* F = feat_out ? reinterpret_cast<float4*>(feat_out) + size_t(sub) * rows * 4 : sim->d_feat;
+        for (const LaunchGroup& g : sim->groups) {
+            SimDev S = sim->S;
+            S.meshes = sim->d_meshes[g.permute ? 1 : 0];
+            FFSRL_CUDA(launch_features(S, g.d_list, g.n, sub == 0, actions, F, sim->stream));
+        }
+        if (mode == kSubstepSurrogate)
+            FFSRL_CUDA(launch_mlp_forward(sim->net, F, sim->d_dx, (long long)rows, sim->d_net_err, sim->n_sm,
+                                          sim->stream));
+        SubstepCtl C{};
+        C.mode = mode;
+        C.last = sub == S_sub - 1;
+        C.dx = sim->d_dx;
+        C.target = target_out ? reinterpret_cast<float4*>(target_out) + size_t(sub) * rows : nullptr;
+        C.threshold = threshold;
+        C.n_full = n_full;
+        C.lambda = sim->d_lambda_full;
+        C.fallbacks = fallbacks;
+        for (const LaunchGroup& g : sim->groups) {
+            SimDev S = sim->S;
+            S.meshes = sim->d_meshes[g.permute ? 1 : 0];
+            bool resident = false;
+            const size_t smem = substep_smem(sim, g, resident);
+            FFSRL_CUDA(launch_substep(S, C, g.d_list, g.n, resident, smem, sim->stream, C.last ? obs : nullptr,
+                                      C.last ? reward : nullptr, C.last ? done : nullptr));
+        }
+    }
+    return FFSRL_OK;
+}
+
+}  // namespace
+
+int ffsrl_step_surrogate(ffsrl_sim* sim, const float* actions_dev, float* obs_dev, float* reward_dev,
+                         uint8_t* done_dev, double threshold, int32_t n_full, int32_t* fallbacks_dev) {
+    if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
+    if (!sim->has_net) return fail(FFSRL_E_INVAL, "no network installed (ffsrl_set_network)");
+    if (n_full < 1) return fail(FFSRL_E_INVAL, "n_full must be >= 1");
+    FFSRL_CUDA(cudaSetDevice(sim->device));
+    return run_substeps(sim, kSubstepSurrogate, actions_dev, obs_dev, reward_dev, done_dev, float(threshold), n_full,
+                        fallbacks_dev, nullptr, nullptr);
+}
+
+int ffsrl_record_step(ffsrl_sim* sim, const float* actions_dev, int32_t n_full, float* features_dev,
+                      float* targets_dev) {
+    if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
+    if (n_full < 1) return fail(FFSRL_E_INVAL, "n_full must be >= 1");
+    if ((reinterpret_cast<uintptr_t>(features_dev) | reinterpret_cast<uintptr_t>(targets_dev)) & 15)
+        return fail(FFSRL_E_INVAL, "features and targets must be 16-byte aligned");
+    FFSRL_CUDA(cudaSetDevice(sim->device));
+    return run_substeps(sim, kSubstepRecord, actions_dev, nullptr, nullptr, nullptr, 0.f, n_full, nullptr,
+                        features_dev, targets_dev);
+}
+
+int ffsrl_get_rows(const ffsrl_sim* sim, int64_t* n_rows, int32_t* row_off_host) {
+    if (!sim || !n_rows) return fail(FFSRL_E_INVAL, "sim and n_rows must be non-NULL");
+    *n_rows = sim->stride;
+    if (row_off_host) std::memcpy(row_off_host, sim->voff.data(), sim->voff.size() * sizeof(int32_t));
     return FFSRL_OK;
 }
 

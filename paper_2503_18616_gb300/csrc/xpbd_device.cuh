@@ -34,6 +34,8 @@ struct MeshDev {
     const uint16_t* vert_of;          // [V] vertex of each slot
     const float4* rest_w;             // [V] rest position and inverse mass (vertex order)
     const int* top;                   // [n_top] top-face vertex ids
+    const int* nbr_off;               // [V + 1] 1-ring of each vertex (vertex order, CSR)
+    const int* nbr;                   // [2E]
     double box_lo[3], box_hi[3], tool_start[3];
     float min_len2;                   // edges with |x_ab|^2 below this are skipped
     int pad1;

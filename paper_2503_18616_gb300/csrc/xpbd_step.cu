@@ -26,6 +26,7 @@
 
 #include "xpbd_device.cuh"
 #include "xpbd_launch.h"
+#include "xpbd_project.cuh"
 
 namespace ffsrl {
 
@@ -73,68 +74,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     for (uint32_t i = 0; i < (1u << 22); ++i)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
-}
-
-// ---- constraint projections ------------------------------------------------
-
-// Edge-distance constraint C = |x_a - x_b| - d in XPBD form (Eq. 1 with
-// compliance): dlambda = (-C - at lambda) / (w_a + w_b + at), x_a += w_a dlambda n,
-// x_b -= w_b dlambda n, n = (x_a - x_b) / |x_a - x_b|.
-__device__ __forceinline__ void project_edge(float4* X, uint2 rec, float at, float min_len2, float& lam) {
-    const int a = int(rec.x & 0xffffu), b = int(rec.x >> 16);
-    const float d = __uint_as_float(rec.y);
-    float4 xa = X[a], xb = X[b];
-    const float dx = xa.x - xb.x, dy = xa.y - xb.y, dz = xa.z - xb.z;
-    const float l2 = dx * dx + dy * dy + dz * dz;
-    const float denom = xa.w + xb.w + at;
-    if (l2 < min_len2 || denom == 0.f) return;
-    const float len = sqrtf(l2);
-    const float C = len - d;
-    const float dl = __fdividef(-C - at * lam, denom);
-    const float s = __fdividef(dl, len);
-    const float sa = xa.w * s, sb = xb.w * s;
-    xa.x += sa * dx; xa.y += sa * dy; xa.z += sa * dz;
-    xb.x -= sb * dx; xb.y -= sb * dy; xb.z -= sb * dz;
-    X[a] = xa;
-    X[b] = xb;
-    lam += dl;
-}
-
-__device__ __forceinline__ float3 sub3(float4 a, float4 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
-    return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-
-// Tet-volume constraint C = (x_ba x x_ca) . x_da / 6 - V0 with gradients
-// g_b = x_ca x x_da / 6, g_c = x_da x x_ba / 6, g_d = x_ba x x_ca / 6,
-// g_a = -(g_b + g_c + g_d) (the consistent reading of Eq. 2), scaled as in
-// Eq. 3 with inverse masses and compliance: dlambda = (-C - at lambda) /
-// (sum w_i |g_i|^2 + at), x_i += w_i dlambda g_i.
-__device__ __forceinline__ void project_tet(float4* X, uint4 rec, float at, float& lam) {
-    const int a = int(rec.x & 0xffffu), b = int(rec.x >> 16);
-    const int c = int(rec.y & 0xffffu), d = int(rec.y >> 16);
-    const float V0 = __uint_as_float(rec.z);
-    float4 xa = X[a], xb = X[b], xc = X[c], xd = X[d];
-    const float3 ba = sub3(xb, xa), ca = sub3(xc, xa), da = sub3(xd, xa);
-    const float3 g1 = cross3(ca, da), g2 = cross3(da, ba), g3 = cross3(ba, ca);  // 6 x gradient
-    const float3 g0 = make_float3(-(g1.x + g2.x + g3.x), -(g1.y + g2.y + g3.y), -(g1.z + g2.z + g3.z));
-    const float C = dot3(g3, da) * (1.0f / 6.0f) - V0;
-    const float sw = xa.w * dot3(g0, g0) + xb.w * dot3(g1, g1) + xc.w * dot3(g2, g2) + xd.w * dot3(g3, g3);
-    const float denom = sw * (1.0f / 36.0f) + at;
-    if (denom == 0.f) return;
-    const float dl = __fdividef(-C - at * lam, denom);
-    const float s = dl * (1.0f / 6.0f);
-    const float sa = xa.w * s, sb = xb.w * s, sc = xc.w * s, sd = xd.w * s;
-    xa.x += sa * g0.x; xa.y += sa * g0.y; xa.z += sa * g0.z;
-    xb.x += sb * g1.x; xb.y += sb * g1.y; xb.z += sb * g1.z;
-    xc.x += sc * g2.x; xc.y += sc * g2.y; xc.z += sc * g2.z;
-    xd.x += sd * g3.x; xd.y += sd * g3.y; xd.z += sd * g3.z;
-    X[a] = xa;
-    X[b] = xb;
-    X[c] = xc;
-    X[d] = xd;
-    lam += dl;
 }
 
 __host__ __device__ __forceinline__ size_t align128(size_t b) { return (b + 127) / 128 * 128; }

@@ -1,0 +1,33 @@
+// Surrogate-assisted substep kernels (internal to the library).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "xpbd_device.cuh"
+
+namespace ffsrl {
+
+constexpr int kSubstepSurrogate = 1;  // add the network's correction, 1 iteration, residual check, fallback
+constexpr int kSubstepRecord = 2;     // full solve, write training targets
+
+struct SubstepCtl {
+    int mode;
+    int last;               // last substep of the step: contacts, observation, reward, done
+    const float4* dx;       // [stride] network corrections (surrogate mode)
+    float4* target;         // [stride] solve minus prediction (record mode; may be null)
+    float threshold;        // residual above which the surrogate substep falls back
+    int n_full;             // iterations of the full solve
+    float* lambda;          // multipliers of the full solve (per env at EnvDev::loff)
+    int* fallbacks;         // [n_env] counters (may be null)
+};
+
+size_t substep_smem_bytes(int Vp, bool resident);
+
+cudaError_t launch_features(const SimDev& S, const int* env_list, int n_list, bool update_tool,
+                            const float* actions, float4* F, cudaStream_t st);
+cudaError_t launch_substep(const SimDev& S, const SubstepCtl& C, const int* env_list, int n_list, bool resident,
+                           size_t smem, cudaStream_t st, float* obs, float* reward, uint8_t* done);
+
+}  // namespace ffsrl

@@ -28,7 +28,8 @@ TABLES = {"tets": 0, "flipped": 1, "edges": 2, "ecolor": 3, "tcolor": 4, "eorder
 EXPORTS = ["ffsrl_create", "ffsrl_reset", "ffsrl_step", "ffsrl_step_host", "ffsrl_sync",
            "ffsrl_destroy", "ffsrl_get_info", "ffsrl_last_error", "ffsrl_get_state",
            "ffsrl_set_state", "ffsrl_get_mesh_table", "ffsrl_get_env_ints", "ffsrl_step_noalloc",
-           "ffsrl_set_network", "ffsrl_network_forward"]
+           "ffsrl_set_network", "ffsrl_network_forward", "ffsrl_step_surrogate", "ffsrl_record_step",
+           "ffsrl_get_rows"]
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
 NET_PARAMS = 64 * 15 + 64 + 64 * 64 + 64 + 3 * 64 + 3   # FFSRL_NET_PARAMS
@@ -109,6 +110,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.ffsrl_set_network.argtypes = [P, P, P]
     L.ffsrl_network_forward.restype = ctypes.c_int
     L.ffsrl_network_forward.argtypes = [P, P, P, ctypes.c_int64]
+    L.ffsrl_step_surrogate.restype = ctypes.c_int
+    L.ffsrl_step_surrogate.argtypes = [P, P, P, P, P, ctypes.c_double, I32, P]
+    L.ffsrl_record_step.restype = ctypes.c_int
+    L.ffsrl_record_step.argtypes = [P, P, I32, P, P]
+    L.ffsrl_get_rows.restype = ctypes.c_int
+    L.ffsrl_get_rows.argtypes = [P, ctypes.POINTER(ctypes.c_int64), P]
     _lib = L
     return L
 
@@ -268,6 +275,37 @@ class Sim:
             out = torch.empty((features.shape[0], 4), dtype=torch.float32, device=features.device)
         _check(self._L.ffsrl_network_forward(self._h, _dptr(features), _dptr(out), int(features.shape[0])))
         return out
+
+    def rows(self):
+        """(n_rows, row offset of each env) of per-vertex row buffers."""
+        n = ctypes.c_int64(0)
+        off = np.zeros(self.n_env, np.int32)
+        _check(self._L.ffsrl_get_rows(self._h, ctypes.byref(n), _np_ptr(off)))
+        return int(n.value), off
+
+    def step_surrogate(self, threshold: float, n_full: int, actions=None, obs=None, reward=None, done=None,
+                       fallbacks=None):
+        torch = self._torch
+        if obs is None:
+            obs = torch.empty((self.n_env, self.obs_dim), dtype=torch.float32, device=self.device)
+        if reward is None:
+            reward = torch.empty(self.n_env, dtype=torch.float32, device=self.device)
+        if done is None:
+            done = torch.empty(self.n_env, dtype=torch.uint8, device=self.device)
+        _check(self._L.ffsrl_step_surrogate(self._h, _dptr(actions), _dptr(obs), _dptr(reward), _dptr(done),
+                                            float(threshold), int(n_full), _dptr(fallbacks)))
+        return obs, reward, done
+
+    def record_step(self, n_full: int, actions=None, features=None, targets=None):
+        torch = self._torch
+        n, _ = self.rows()
+        S = self.params["substeps"]
+        if features is None:
+            features = torch.empty((S, n, 16), dtype=torch.float32, device=self.device)
+        if targets is None:
+            targets = torch.empty((S, n, 4), dtype=torch.float32, device=self.device)
+        _check(self._L.ffsrl_record_step(self._h, _dptr(actions), int(n_full), _dptr(features), _dptr(targets)))
+        return features, targets
 
     def sync(self) -> None:
         _check(self._L.ffsrl_sync(self._h))

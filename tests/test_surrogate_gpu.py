@@ -1,0 +1,113 @@
+"""Surrogate-assisted substeps on the GPU against the oracle.
+
+Features and recorded training targets of the GPU pipeline must match the
+oracle's within float32 rounding of positions (1e-5 x extent for targets
+measured in position units, and the same relative bar for velocity-based
+features); whole surrogate steps must match the oracle's surrogate step
+within the trajectory tolerance, including the limiting cases (zero network
+without fallback, fallback in every substep) and a random BF16 network.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_18616_gb300 import inputs
+from sim_helpers import POS_TOL, gpu_positions, grid, make_sim, oracle_envs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+ZERO_NORM = (np.zeros(15), np.ones(15), np.zeros(3), np.ones(3))
+
+
+def _perturbed(sim, m, n_env, oenvs, seed):
+    rest, w, _ = m
+    V = len(rest)
+    x = np.concatenate([inputs.perturbed_positions(rest, 3e-4, seed + e, inv_mass=w) for e in range(n_env)])
+    v = np.random.default_rng(seed).normal(0, 0.01, x.shape)
+    v[np.tile(w, n_env) == 0] = 0
+    x32, v32 = x.astype(np.float32), v.astype(np.float32)
+    sim.set_state(torch.from_numpy(x32).cuda(), torch.from_numpy(v32).cuda())
+    for e, oe in oenvs.items():
+        oe.set_state(x=x32[e * V:(e + 1) * V].astype(np.float64), v=v32[e * V:(e + 1) * V].astype(np.float64))
+
+
+def test_recorded_features_and_targets_match_oracle():
+    m = grid((9, 9, 5))
+    p = inputs.default_params(radius=4e-3)
+    n_env = 3
+    sim = make_sim([m], p, n_env, seed=2)
+    oenvs, om = oracle_envs([m], p, n_env, seed=2)
+    _perturbed(sim, m, n_env, oenvs, 5)
+    zeros = torch.zeros((n_env, 3), dtype=torch.float32, device="cuda")
+    feats, targs = sim.record_step(10, actions=zeros)
+    n_rows, off = sim.rows()
+    feats, targs = feats.cpu().numpy(), targs.cpu().numpy()
+    ext = om[0].extent
+    V = om[0].V
+    h = p["dt"] / p["substeps"]
+    pos_cols = [0, 1, 2, 6, 7, 8, 12, 13, 14]
+    vel_cols = [3, 4, 5, 9, 10, 11]
+    for e, oe in oenvs.items():
+        Fo, To = oe.step_record(10, action=np.zeros(3))
+        Fg = feats[:, off[e]:off[e] + V, :]
+        assert np.max(np.abs(Fg[..., pos_cols] - Fo[..., pos_cols])) <= POS_TOL * ext
+        assert np.max(np.abs(Fg[..., vel_cols] - Fo[..., vel_cols])) <= POS_TOL * ext / h
+        assert np.all(Fg[..., 15] == 0)
+        assert np.max(np.abs(targs[:, off[e]:off[e] + V, :3] - To)) <= POS_TOL * ext
+    x, _, _ = gpu_positions(sim)
+    for e, oe in oenvs.items():
+        assert np.max(np.abs(x[e * V:(e + 1) * V] - oe.state()[0])) <= POS_TOL * ext
+
+
+def _install(sim, params, norm):
+    sim.set_network(params, *norm)
+
+
+@pytest.mark.parametrize("case", ["zero_no_fallback", "always_fallback", "random_network"])
+def test_surrogate_step_matches_oracle(case):
+    m = grid((9, 9, 5))
+    p = inputs.default_params(radius=4e-3)
+    n_env, steps = 3, 6
+    sim = make_sim([m], p, n_env, seed=4)
+    oenvs, om = oracle_envs([m], p, n_env, seed=4)
+    if case == "zero_no_fallback":
+        params = {k: np.zeros_like(v) for k, v in oracle.mlp_init(0).items()}
+        norm, thr = ZERO_NORM, np.inf
+    elif case == "always_fallback":
+        params = oracle.mlp_init(1)
+        norm, thr = (np.zeros(15), np.full(15, 1e-3), np.zeros(3), np.full(3, 1e-5)), -1.0
+    else:
+        params = oracle.mlp_init(2)
+        rng = np.random.default_rng(3)
+        for k in ("b1", "b2", "b3"):
+            params[k] = rng.normal(0, 0.1, params[k].shape)
+        norm, thr = (np.zeros(15), np.full(15, 2e-3), np.zeros(3), np.full(3, 2e-7)), np.inf
+    _install(sim, params, norm)
+    net = oracle.Net.from_params(params, *norm, bf16=True)
+    fb = torch.zeros(n_env, dtype=torch.int32, device="cuda")
+    for _ in range(steps):
+        obs, rew, _ = sim.step_surrogate(thr if np.isfinite(thr) else 1e30, 10, fallbacks=fb)
+    ofb = {}
+    for e, oe in oenvs.items():
+        ofb[e] = 0
+        for _ in range(steps):
+            o_obs, o_rew, _, f = oe.step_surrogate(net, thr, 10)
+            ofb[e] += f
+    sim.sync()
+    x, v, tool = gpu_positions(sim)
+    ext = om[0].extent
+    V = om[0].V
+    for e, oe in oenvs.items():
+        ox, ov, oc = oe.state()
+        assert np.max(np.abs(x[e * V:(e + 1) * V] - ox)) <= POS_TOL * ext, e
+        assert np.array_equal(tool[e], oc)
+        assert int(fb[e]) == ofb[e]
+        assert abs(float(rew[e]) - o_rew) <= POS_TOL * ext
+    if case == "always_fallback":
+        assert all(f == steps * p["substeps"] for f in ofb.values())
+    else:
+        assert all(f == 0 for f in ofb.values())
