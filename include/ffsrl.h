@@ -181,6 +181,27 @@ int ffsrl_get_env_ints(ffsrl_sim* sim, int32_t env, int32_t* step_count, int32_t
  * output normalisation (std > 0). Host buffers; the call copies them. */
 int ffsrl_set_network(ffsrl_sim* sim, const float* params_host, const float* norm_host);
 
+/* Copies the float32 master parameters (as ffsrl_set_network takes them) to params_host. */
+int ffsrl_get_network(const ffsrl_sim* sim, float* params_host);
+
+/* Gradient of the weighted mean squared error of the network on a batch,
+ * L = sum_r w_r |y_r - t_r|^2 / (3 weight_sum) in normalised output units
+ * (t_r = (target_r - out_mean) / out_std), computed on the tensor cores with
+ * BF16 operands: features_dev [rows][16] raw features, targets_dev [rows][4]
+ * raw targets (x, y, z, ignored), row_weight_dev [rows] float32 weights,
+ * weight_sum their sum. grad_dev [FFSRL_NET_PARAMS] (may be NULL) receives the
+ * gradient in the layout of the parameters, loss_dev [1] (may be NULL) the
+ * weighted sum of squared errors. Asynchronous. */
+int ffsrl_network_gradient(ffsrl_sim* sim, const float* features_dev, const float* targets_dev,
+                           const float* row_weight_dev, int64_t rows, float weight_sum, float* grad_dev,
+                           float* loss_dev);
+
+/* One Adam step (Kingma & Ba 2015; beta 0.9, 0.999, eps 1e-8) of the float32
+ * master parameters on the gradient of that loss, then re-rounds the BF16
+ * copies the network runs with. loss_dev as above. Asynchronous. */
+int ffsrl_train_network(ffsrl_sim* sim, const float* features_dev, const float* targets_dev,
+                        const float* row_weight_dev, int64_t rows, float weight_sum, float lr, float* loss_dev);
+
 /* out_dev[r] = (network output of features_dev[r], 0) for r < rows:
  * features_dev [rows][16] float32 raw features (the 16th is ignored), output
  * [rows][4] float32 de-normalised (x, y, z, 0). Asynchronous on the sim's

@@ -103,8 +103,16 @@ struct ffsrl_sim {
     bool has_net = false;
     MlpDev net{};
     uint16_t* d_wtiles = nullptr;
+    uint16_t* d_btiles = nullptr;
     float* d_bias = nullptr;
     int* d_net_err = nullptr;
+    float* d_master = nullptr;    // float32 master parameters
+    float* d_adam_m = nullptr;
+    float* d_adam_v = nullptr;
+    float* d_grad = nullptr;
+    float* d_loss = nullptr;
+    int adam_t = 0;
+    float norm[FFSRL_NET_NORM] = {};
     // surrogate-assisted substeps (allocated on first use)
     long long lambda_slots = 0;
     float4* d_feat = nullptr;     // [stride][4] features
@@ -687,16 +695,25 @@ int ffsrl_set_network(ffsrl_sim* sim, const float* params_host, const float* nor
     for (int k = 0; k < 3; ++k)
         if (!(norm_host[33 + k] > 0)) return fail(FFSRL_E_INVAL, "output std must be > 0");
     FFSRL_CUDA(cudaSetDevice(sim->device));
-    std::vector<uint16_t> tiles(kMlpWeightBytes / 2, 0);
-    std::vector<float> bias(144, 0.f);
-    pack_mlp_weights(params_host, tiles.data(), bias.data());
-    if (!sim->d_wtiles) {
-        FFSRL_CUDA(sim->alloc(&sim->d_wtiles, tiles.size()));
-        FFSRL_CUDA(sim->alloc(&sim->d_bias, bias.size()));
+    if (!sim->d_master) {
+        FFSRL_CUDA(sim->alloc(&sim->d_master, FFSRL_NET_PARAMS));
+        FFSRL_CUDA(sim->alloc(&sim->d_adam_m, FFSRL_NET_PARAMS));
+        FFSRL_CUDA(sim->alloc(&sim->d_adam_v, FFSRL_NET_PARAMS));
+        FFSRL_CUDA(sim->alloc(&sim->d_grad, FFSRL_NET_PARAMS));
+        FFSRL_CUDA(sim->alloc(&sim->d_loss, 1));
+        FFSRL_CUDA(sim->alloc(&sim->d_wtiles, kMlpWeightBytes / 2));
+        FFSRL_CUDA(sim->alloc(&sim->d_btiles, 10240 / 2));
+        FFSRL_CUDA(sim->alloc(&sim->d_bias, 144));
     }
-    FFSRL_CUDA(cudaMemcpyAsync(sim->d_wtiles, tiles.data(), tiles.size() * 2, cudaMemcpyHostToDevice, sim->stream));
-    FFSRL_CUDA(cudaMemcpyAsync(sim->d_bias, bias.data(), bias.size() * 4, cudaMemcpyHostToDevice, sim->stream));
+    FFSRL_CUDA(cudaMemcpyAsync(sim->d_master, params_host, FFSRL_NET_PARAMS * sizeof(float), cudaMemcpyHostToDevice,
+                               sim->stream));
+    FFSRL_CUDA(cudaMemsetAsync(sim->d_adam_m, 0, FFSRL_NET_PARAMS * sizeof(float), sim->stream));
+    FFSRL_CUDA(cudaMemsetAsync(sim->d_adam_v, 0, FFSRL_NET_PARAMS * sizeof(float), sim->stream));
+    FFSRL_CUDA(cudaMemsetAsync(sim->d_grad, 0, FFSRL_NET_PARAMS * sizeof(float), sim->stream));
+    FFSRL_CUDA(launch_mlp_pack(sim->d_master, sim->d_wtiles, sim->d_btiles, sim->d_bias, sim->stream));
     FFSRL_CUDA(cudaStreamSynchronize(sim->stream));
+    sim->adam_t = 0;
+    std::memcpy(sim->norm, norm_host, sizeof(sim->norm));
     MlpDev& n = sim->net;
     n.wtiles = sim->d_wtiles;
     n.bias = sim->d_bias;
@@ -709,6 +726,86 @@ int ffsrl_set_network(ffsrl_sim* sim, const float* params_host, const float* nor
         n.out_std[k] = k < 3 ? norm_host[33 + k] : 0.f;
     }
     sim->has_net = true;
+    return FFSRL_OK;
+}
+
+int ffsrl_get_network(const ffsrl_sim* sim, float* params_host) {
+    if (!sim || !params_host) return fail(FFSRL_E_INVAL, "sim and params must be non-NULL");
+    if (!sim->has_net) return fail(FFSRL_E_INVAL, "no network installed (ffsrl_set_network)");
+    FFSRL_CUDA(cudaSetDevice(sim->device));
+    FFSRL_CUDA(cudaStreamSynchronize(sim->stream));
+    FFSRL_CUDA(cudaMemcpy(params_host, sim->d_master, FFSRL_NET_PARAMS * sizeof(float), cudaMemcpyDeviceToHost));
+    return FFSRL_OK;
+}
+
+namespace {
+
+int check_batch(const ffsrl_sim* sim, const float* f, const float* t, const float* w, int64_t rows, float wsum) {
+    if (!sim->has_net) return fail(FFSRL_E_INVAL, "no network installed (ffsrl_set_network)");
+    if (rows < 1 || !f || !t || !w) return fail(FFSRL_E_INVAL, "need rows >= 1 and features, targets, weights");
+    if (!(wsum > 0)) return fail(FFSRL_E_INVAL, "weight_sum must be > 0");
+    if ((reinterpret_cast<uintptr_t>(f) | reinterpret_cast<uintptr_t>(t)) & 15)
+        return fail(FFSRL_E_INVAL, "features and targets must be 16-byte aligned");
+    return FFSRL_OK;
+}
+
+TrainDev train_dev(ffsrl_sim* sim, float wsum) {
+    TrainDev P{};
+    P.wtiles = sim->d_wtiles;
+    P.btiles = sim->d_btiles;
+    P.bias = sim->d_bias;
+    for (int k = 0; k < 16; ++k) {
+        P.in_mean[k] = sim->net.in_mean[k];
+        P.in_inv_std[k] = sim->net.in_inv_std[k];
+    }
+    for (int k = 0; k < 4; ++k) {
+        P.out_mean[k] = k < 3 ? sim->norm[30 + k] : 0.f;
+        P.out_inv_std[k] = k < 3 ? 1.0f / sim->norm[33 + k] : 0.f;
+    }
+    P.grad_scale = 2.0f / (3.0f * wsum);
+    P.grad = sim->d_grad;
+    P.loss = sim->d_loss;
+    return P;
+}
+
+}  // namespace
+
+int ffsrl_network_gradient(ffsrl_sim* sim, const float* features_dev, const float* targets_dev,
+                           const float* row_weight_dev, int64_t rows, float weight_sum, float* grad_dev,
+                           float* loss_dev) {
+    if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
+    int rc = check_batch(sim, features_dev, targets_dev, row_weight_dev, rows, weight_sum);
+    if (rc) return rc;
+    FFSRL_CUDA(cudaSetDevice(sim->device));
+    FFSRL_CUDA(cudaMemsetAsync(sim->d_grad, 0, FFSRL_NET_PARAMS * sizeof(float), sim->stream));
+    FFSRL_CUDA(cudaMemsetAsync(sim->d_loss, 0, sizeof(float), sim->stream));
+    FFSRL_CUDA(launch_mlp_train(train_dev(sim, weight_sum), reinterpret_cast<const float4*>(features_dev),
+                                reinterpret_cast<const float4*>(targets_dev), row_weight_dev, rows, sim->d_net_err,
+                                sim->n_sm, sim->stream));
+    if (grad_dev)
+        FFSRL_CUDA(cudaMemcpyAsync(grad_dev, sim->d_grad, FFSRL_NET_PARAMS * sizeof(float), cudaMemcpyDeviceToDevice,
+                                   sim->stream));
+    if (loss_dev) FFSRL_CUDA(cudaMemcpyAsync(loss_dev, sim->d_loss, sizeof(float), cudaMemcpyDeviceToDevice, sim->stream));
+    FFSRL_CUDA(cudaMemsetAsync(sim->d_grad, 0, FFSRL_NET_PARAMS * sizeof(float), sim->stream));
+    return FFSRL_OK;
+}
+
+int ffsrl_train_network(ffsrl_sim* sim, const float* features_dev, const float* targets_dev,
+                        const float* row_weight_dev, int64_t rows, float weight_sum, float lr, float* loss_dev) {
+    if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
+    int rc = check_batch(sim, features_dev, targets_dev, row_weight_dev, rows, weight_sum);
+    if (rc) return rc;
+    if (!(lr > 0)) return fail(FFSRL_E_INVAL, "lr must be > 0");
+    FFSRL_CUDA(cudaSetDevice(sim->device));
+    FFSRL_CUDA(cudaMemsetAsync(sim->d_loss, 0, sizeof(float), sim->stream));
+    FFSRL_CUDA(launch_mlp_train(train_dev(sim, weight_sum), reinterpret_cast<const float4*>(features_dev),
+                                reinterpret_cast<const float4*>(targets_dev), row_weight_dev, rows, sim->d_net_err,
+                                sim->n_sm, sim->stream));
+    sim->adam_t += 1;
+    FFSRL_CUDA(launch_adam(sim->d_master, sim->d_adam_m, sim->d_adam_v, sim->d_grad, FFSRL_NET_PARAMS, lr,
+                           sim->adam_t, sim->stream));
+    FFSRL_CUDA(launch_mlp_pack(sim->d_master, sim->d_wtiles, sim->d_btiles, sim->d_bias, sim->stream));
+    if (loss_dev) FFSRL_CUDA(cudaMemcpyAsync(loss_dev, sim->d_loss, sizeof(float), cudaMemcpyDeviceToDevice, sim->stream));
     return FFSRL_OK;
 }
 

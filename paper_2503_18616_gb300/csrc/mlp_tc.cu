@@ -281,6 +281,421 @@ cudaError_t launch_mlp_forward(const MlpDev& net, const float4* feat, float4* ou
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Training: fused forward + backward per 128-row tile on the tensor cores.
+//
+// Per tile (thread = row = TMEM lane): forward as above, keeping the ReLU
+// masks of both hidden layers; the loss gradient dY = scale * w * (y - t) of
+// the normalised output; then
+//   dH2 = dY W3   (MMA, B = W3^T tile)   -> dZ2 = dH2 * [H2 > 0]
+//   dH1 = dZ2 W2  (MMA, B = W2^T tile)   -> dZ1 = dH1 * [H1 > 0]
+// and the weight gradients as two more MMAs whose K dimension is the tile's
+// 128 rows, accumulated in TMEM over all tiles of the CTA:
+//   [dZ2^T ; dZ1^T] (128 x 128) [H1 | X] (80 x 128)^T -> dW2 (rows 0..63,
+//   cols 0..63) and dW1 (rows 64..127, cols 64..79)
+//   [dY^T ; 0] (128 x 128) H2 (64 x 128)^T            -> dW3 (rows 0..2)
+// The transposed operand tiles are written by the epilogue threads. Bias
+// gradients and the loss are reduced with warp shuffles. At the end each CTA
+// adds its gradients to the global FP32 accumulators.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// 2-byte element (row n, column k) of a K-major tile with kcs chunks per row.
+__device__ __forceinline__ void st_elem(unsigned char* tile, int n, int k, int kcs, uint32_t bits16) {
+    *reinterpret_cast<uint16_t*>(tile + ((n >> 3) * kcs + (k >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2) =
+        uint16_t(bits16);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Offsets of the smem regions of the training kernel.
+constexpr int kTrW = 0;                       // W1 | W2 | W3       12288
+constexpr int kTrB = kTrW + kMlpWeightBytes;  // W3T | W2T          10240
+constexpr int kTrX = kTrB + 10240;            // X (128 x 16)        4096
+constexpr int kTrH1 = kTrX + 4096;            // H1, later dZ2      16384
+constexpr int kTrH2 = kTrH1 + 16384;          // H2                 16384
+constexpr int kTrDY = kTrH2 + 16384;          // dY (128 x 16)       4096
+constexpr int kTrAW = kTrDY + 4096;           // [dZ2^T; dZ1^T]     32768
+constexpr int kTrBW = kTrAW + 32768;          // [H1^T; X^T]        20480
+constexpr int kTrAY = kTrBW + 20480;          // [dY^T; 0]          32768
+constexpr int kTrBH = kTrAY + 32768;          // H2^T               16384
+constexpr int kTrRed = kTrBH + 16384;         // db1, db2, db3, loss   4 * 136
+constexpr int kTrBias = kTrRed + 4 * 136;     // b1, b2, b3            4 * 144
+constexpr int kTrSmem = kTrBias + 4 * 144;
+
+constexpr uint32_t kTrTmemCols = 512;
+
+}  // namespace
+
+__global__ void __launch_bounds__(128) mlp_train_kernel(TrainDev P, const float4* __restrict__ feat,
+                                                        const float4* __restrict__ targ,
+                                                        const float* __restrict__ wrow, long long rows,
+                                                        int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float* red = reinterpret_cast<float*>(sm + kTrRed);   // db1[64] db2[64] db3[4] loss[1]
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                     "r"(kTrTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int i = tid; i < kMlpWeightBytes / 16; i += 128)
+        reinterpret_cast<uint4*>(sm + kTrW)[i] = reinterpret_cast<const uint4*>(P.wtiles)[i];
+    for (int i = tid; i < 10240 / 16; i += 128)
+        reinterpret_cast<uint4*>(sm + kTrB)[i] = reinterpret_cast<const uint4*>(P.btiles)[i];
+    for (int i = tid; i < 32768 / 16; i += 128) reinterpret_cast<uint4*>(sm + kTrAY)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < 136; i += 128) red[i] = 0.f;
+    float* bias = reinterpret_cast<float*>(sm + kTrBias);
+    for (int i = tid; i < 144; i += 128) bias[i] = P.bias[i];
+    if (tid == 0) mbar_init(&mbar);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t lb = uint32_t(32 * warp) << 16;
+    const uint32_t aW1 = saddr(sm + kTrW), aW2 = aW1 + 2048, aW3 = aW1 + 10240;
+    const uint32_t aW3T = saddr(sm + kTrB), aW2T = aW3T + 2048;
+    const uint32_t aX = saddr(sm + kTrX), aH1 = saddr(sm + kTrH1), aH2 = saddr(sm + kTrH2), aDY = saddr(sm + kTrDY);
+    const uint32_t aAW = saddr(sm + kTrAW), aBW = saddr(sm + kTrBW), aAY = saddr(sm + kTrAY), aBH = saddr(sm + kTrBH);
+    unsigned char* X = sm + kTrX;
+    unsigned char* H1 = sm + kTrH1;
+    unsigned char* H2 = sm + kTrH2;
+    unsigned char* DY = sm + kTrDY;
+    unsigned char* AW = sm + kTrAW;
+    unsigned char* BW = sm + kTrBW;
+    unsigned char* AY = sm + kTrAY;
+    unsigned char* BH = sm + kTrBH;
+    uint32_t phase = 0;
+    bool failed = false;
+    int n_tiles = 0;
+    const int r = tid;
+
+    auto sync_for_mma = [&]() {
+        fence_async_smem();
+        fence_before_sync();
+        __syncthreads();
+        fence_after_sync();
+    };
+    auto wait_mma = [&]() -> bool {
+        const bool ok = mbar_wait(&mbar, phase & 1);
+        if (__syncthreads_or(!ok)) return false;
+        ++phase;
+        fence_after_sync();
+        return true;
+    };
+
+    for (long long tile = blockIdx.x; tile * 128 < rows; tile += gridDim.x) {
+        const long long row = tile * 128 + r;
+        const bool valid = row < rows;
+        const float w = valid ? wrow[row] : 0.f;
+        // -- stage X (normalised, BF16) and X^T --------------------------------
+        {
+            float f[16];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 v = valid ? feat[row * 4 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                f[4 * q] = v.x; f[4 * q + 1] = v.y; f[4 * q + 2] = v.z; f[4 * q + 3] = v.w;
+            }
+            uint32_t p[8];
+#pragma unroll
+            for (int k = 0; k < 16; k += 2) {
+                const float a = (valid && k < 15) ? (f[k] - P.in_mean[k]) * P.in_inv_std[k] : 0.f;
+                const float b = (valid && k + 1 < 15) ? (f[k + 1] - P.in_mean[k + 1]) * P.in_inv_std[k + 1] : 0.f;
+                const uint32_t ba = bf16_bits(a), bb = bf16_bits(b);
+                p[k / 2] = ba | (bb << 16);
+                st_elem(BW, 64 + k, r, 16, ba);
+                st_elem(BW, 64 + k + 1, r, 16, bb);
+            }
+            *reinterpret_cast<uint4*>(X + tile_off(r, 0, 2)) = make_uint4(p[0], p[1], p[2], p[3]);
+            *reinterpret_cast<uint4*>(X + tile_off(r, 1, 2)) = make_uint4(p[4], p[5], p[6], p[7]);
+        }
+        sync_for_mma();
+        if (tid == 0) {
+            umma_bf16(tmem, umma_desc(aX, 128, 256), umma_desc(aW1, 128, 256), umma_idesc_bf16(128, 64), 0);
+            umma_commit(&mbar);
+        }
+        if (!wait_mma()) { failed = true; break; }
+        // -- H1 = relu(D1 + b1): tile, H1^T, mask ------------------------------
+        uint64_t m1 = 0, m2 = 0;
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + lb + c0, v);
+            uint32_t p[8];
+#pragma unroll
+            for (int k = 0; k < 16; k += 2) {
+                const float a = fmaxf(v[k] + bias[c0 + k], 0.f), b = fmaxf(v[k + 1] + bias[c0 + k + 1], 0.f);
+                m1 |= uint64_t(a > 0.f) << (c0 + k);
+                m1 |= uint64_t(b > 0.f) << (c0 + k + 1);
+                const uint32_t ba = bf16_bits(a), bb = bf16_bits(b);
+                p[k / 2] = ba | (bb << 16);
+                st_elem(BW, c0 + k, r, 16, ba);
+                st_elem(BW, c0 + k + 1, r, 16, bb);
+            }
+            *reinterpret_cast<uint4*>(H1 + tile_off(r, c0 / 8, 8)) = make_uint4(p[0], p[1], p[2], p[3]);
+            *reinterpret_cast<uint4*>(H1 + tile_off(r, c0 / 8 + 1, 8)) = make_uint4(p[4], p[5], p[6], p[7]);
+        }
+        sync_for_mma();
+        if (tid == 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                umma_bf16(tmem + 64, umma_desc(aH1 + 256 * j, 128, 1024), umma_desc(aW2 + 256 * j, 128, 1024),
+                          umma_idesc_bf16(128, 64), j);
+            umma_commit(&mbar);
+        }
+        if (!wait_mma()) { failed = true; break; }
+        // -- H2 = relu(D2 + b2): tile, H2^T, mask ------------------------------
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + lb + 64 + c0, v);
+            uint32_t p[8];
+#pragma unroll
+            for (int k = 0; k < 16; k += 2) {
+                const float a = fmaxf(v[k] + bias[64 + c0 + k], 0.f), b = fmaxf(v[k + 1] + bias[64 + c0 + k + 1], 0.f);
+                m2 |= uint64_t(a > 0.f) << (c0 + k);
+                m2 |= uint64_t(b > 0.f) << (c0 + k + 1);
+                const uint32_t ba = bf16_bits(a), bb = bf16_bits(b);
+                p[k / 2] = ba | (bb << 16);
+                st_elem(BH, c0 + k, r, 16, ba);
+                st_elem(BH, c0 + k + 1, r, 16, bb);
+            }
+            *reinterpret_cast<uint4*>(H2 + tile_off(r, c0 / 8, 8)) = make_uint4(p[0], p[1], p[2], p[3]);
+            *reinterpret_cast<uint4*>(H2 + tile_off(r, c0 / 8 + 1, 8)) = make_uint4(p[4], p[5], p[6], p[7]);
+        }
+        sync_for_mma();
+        if (tid == 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                umma_bf16(tmem, umma_desc(aH2 + 256 * j, 128, 1024), umma_desc(aW3 + 256 * j, 128, 1024),
+                          umma_idesc_bf16(128, 16), j);
+            umma_commit(&mbar);
+        }
+        if (!wait_mma()) { failed = true; break; }
+        // -- loss gradient dY (normalised output units) -------------------------
+        float g[3];
+        {
+            float v[16];
+            tmem_ld16(tmem + lb, v);
+            const float4 t4 = valid ? targ[row] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float tt[3] = {t4.x, t4.y, t4.z};
+            float l = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float y = v[k] + bias[128 + k];
+                const float d = y - (tt[k] - P.out_mean[k]) * P.out_inv_std[k];
+                l += w * d * d;
+                g[k] = P.grad_scale * w * d;
+            }
+            const uint32_t g0 = bf16_bits(g[0]), g1 = bf16_bits(g[1]), g2 = bf16_bits(g[2]);
+            *reinterpret_cast<uint4*>(DY + tile_off(r, 0, 2)) = make_uint4(g0 | (g1 << 16), g2, 0u, 0u);
+            *reinterpret_cast<uint4*>(DY + tile_off(r, 1, 2)) = make_uint4(0u, 0u, 0u, 0u);
+            st_elem(AY, 0, r, 16, g0);
+            st_elem(AY, 1, r, 16, g1);
+            st_elem(AY, 2, r, 16, g2);
+            l = warp_sum(l);
+            if (lane == 0) atomicAdd(&red[132], l);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float s = warp_sum(g[k]);
+                if (lane == 0) atomicAdd(&red[128 + k], s);
+            }
+        }
+        sync_for_mma();
+        if (tid == 0) {
+            umma_bf16(tmem, umma_desc(aDY, 128, 256), umma_desc(aW3T, 128, 256), umma_idesc_bf16(128, 64), 0);
+            umma_commit(&mbar);
+        }
+        if (!wait_mma()) { failed = true; break; }
+        // -- dZ2 = dH2 * [H2 > 0]: tile (into H1's space), dZ2^T, db2 -----------
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + lb + c0, v);
+            uint32_t p[8];
+#pragma unroll
+            for (int k = 0; k < 16; k += 2) {
+                const float a = ((m2 >> (c0 + k)) & 1) ? v[k] : 0.f;
+                const float b = ((m2 >> (c0 + k + 1)) & 1) ? v[k + 1] : 0.f;
+                const uint32_t ba = bf16_bits(a), bb = bf16_bits(b);
+                p[k / 2] = ba | (bb << 16);
+                st_elem(AW, c0 + k, r, 16, ba);
+                st_elem(AW, c0 + k + 1, r, 16, bb);
+                const float sa = warp_sum(a), sb = warp_sum(b);
+                if (lane == 0) {
+                    atomicAdd(&red[64 + c0 + k], sa);
+                    atomicAdd(&red[64 + c0 + k + 1], sb);
+                }
+            }
+            *reinterpret_cast<uint4*>(H1 + tile_off(r, c0 / 8, 8)) = make_uint4(p[0], p[1], p[2], p[3]);
+            *reinterpret_cast<uint4*>(H1 + tile_off(r, c0 / 8 + 1, 8)) = make_uint4(p[4], p[5], p[6], p[7]);
+        }
+        sync_for_mma();
+        if (tid == 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                umma_bf16(tmem + 64, umma_desc(aH1 + 256 * j, 128, 1024), umma_desc(aW2T + 256 * j, 128, 1024),
+                          umma_idesc_bf16(128, 64), j);
+            umma_commit(&mbar);
+        }
+        if (!wait_mma()) { failed = true; break; }
+        // -- dZ1 = dH1 * [H1 > 0]: dZ1^T, db1 ------------------------------------
+#pragma unroll
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + lb + 64 + c0, v);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const float a = ((m1 >> (c0 + k)) & 1) ? v[k] : 0.f;
+                st_elem(AW, 64 + c0 + k, r, 16, bf16_bits(a));
+                const float sa = warp_sum(a);
+                if (lane == 0) atomicAdd(&red[c0 + k], sa);
+            }
+        }
+        sync_for_mma();
+        // -- weight gradients, accumulated in TMEM across tiles -----------------
+        if (tid == 0) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                umma_bf16(tmem + 128, umma_desc(aAW + 256 * j, 128, 2048), umma_desc(aBW + 256 * j, 128, 2048),
+                          umma_idesc_bf16(128, 80), (n_tiles > 0 || j > 0) ? 1 : 0);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                umma_bf16(tmem + 256, umma_desc(aAY + 256 * j, 128, 2048), umma_desc(aBH + 256 * j, 128, 2048),
+                          umma_idesc_bf16(128, 64), (n_tiles > 0 || j > 0) ? 1 : 0);
+            umma_commit(&mbar);
+        }
+        if (!wait_mma()) { failed = true; break; }
+        ++n_tiles;
+        fence_before_sync();
+        __syncthreads();
+        fence_after_sync();
+    }
+    if (failed) {
+        mbar_wait(&mbar, phase & 1);
+        if (tid == 0) atomicOr(err, 1);
+    } else if (n_tiles > 0) {
+        // Add this CTA's gradients to the global accumulators.
+        float* G = P.grad;
+        for (int c0 = 0; c0 < 80; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + lb + 128 + c0, v);
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int n = c0 + k;
+                if (r < 64 && n < 64) atomicAdd(&G[kGradW2 + r * 64 + n], v[k]);
+                if (r >= 64 && n >= 64 && n < 79) atomicAdd(&G[kGradW1 + (r - 64) * 15 + (n - 64)], v[k]);
+            }
+        }
+        for (int c0 = 0; c0 < 64; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + lb + 256 + c0, v);
+            if (r < 3)
+#pragma unroll
+                for (int k = 0; k < 16; ++k) atomicAdd(&G[kGradW3 + r * 64 + c0 + k], v[k]);
+        }
+        __syncthreads();
+        if (tid < 64) {
+            atomicAdd(&G[kGradB1 + tid], red[tid]);
+            atomicAdd(&G[kGradB2 + tid], red[64 + tid]);
+        }
+        if (tid < 3) atomicAdd(&G[kGradB3 + tid], red[128 + tid]);
+        if (tid == 0) atomicAdd(P.loss, red[132]);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTrTmemCols) : "memory");
+}
+
+// Repacks the float32 master parameters into the BF16 tiles of the forward
+// (W1, W2, W3) and backward (W3^T, W2^T) passes and the padded biases.
+__global__ void mlp_pack_kernel(const float* __restrict__ master, uint16_t* __restrict__ wtiles,
+                                uint16_t* __restrict__ btiles, float* __restrict__ bias) {
+    auto put = [](uint16_t* tile, int R, int K, int r, int k, float v) {
+        const int off = ((r / 8) * (K / 8) + k / 8) * 64 + (r % 8) * 8 + (k % 8);
+        const uint32_t u = __float_as_uint(v);
+        tile[off] = uint16_t((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+        (void)R;
+    };
+    const float* W1 = master + kGradW1;
+    const float* W2 = master + kGradW2;
+    const float* W3 = master + kGradW3;
+    for (int i = threadIdx.x; i < 64 * 16; i += blockDim.x) {
+        const int r = i / 16, k = i % 16;
+        put(wtiles, 64, 16, r, k, k < 15 ? W1[r * 15 + k] : 0.f);
+    }
+    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
+        const int r = i / 64, k = i % 64;
+        put(wtiles + 1024, 64, 64, r, k, W2[r * 64 + k]);
+        put(btiles + 1024, 64, 64, r, k, W2[k * 64 + r]);          // W2^T: row = input unit
+    }
+    for (int i = threadIdx.x; i < 16 * 64; i += blockDim.x) {
+        const int r = i / 64, k = i % 64;
+        put(wtiles + 1024 + 4096, 16, 64, r, k, r < 3 ? W3[r * 64 + k] : 0.f);
+    }
+    for (int i = threadIdx.x; i < 64 * 16; i += blockDim.x) {
+        const int r = i / 16, k = i % 16;
+        put(btiles, 64, 16, r, k, k < 3 ? W3[k * 64 + r] : 0.f);    // W3^T: row = hidden unit
+    }
+    for (int i = threadIdx.x; i < 144; i += blockDim.x)
+        bias[i] = i < 64 ? master[kGradB1 + i] : i < 128 ? master[kGradB2 + i - 64] : i < 131 ? master[kGradB3 + i - 128] : 0.f;
+}
+
+// Adam (Kingma & Ba, ICLR 2015, Algorithm 1) on the float32 master
+// parameters; clears the gradients afterwards.
+__global__ void adam_kernel(float* __restrict__ master, float* __restrict__ m, float* __restrict__ v,
+                            float* __restrict__ grad, int n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float g = grad[i];
+        const float mi = b1 * m[i] + (1.f - b1) * g;
+        const float vi = b2 * v[i] + (1.f - b2) * g * g;
+        m[i] = mi;
+        v[i] = vi;
+        master[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        grad[i] = 0.f;
+    }
+}
+
+size_t mlp_train_smem_bytes() { return size_t(kTrSmem); }
+
+cudaError_t launch_mlp_train(const TrainDev& P, const float4* feat, const float4* targ, const float* wrow,
+                             long long rows, int* err, int n_sm, cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(mlp_train_smem_bytes()));
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const long long tiles = (rows + 127) / 128;
+    const int grid = int(tiles < n_sm ? tiles : n_sm);   // one CTA per SM (512 TMEM columns each)
+    mlp_train_kernel<<<grid, 128, mlp_train_smem_bytes(), st>>>(P, feat, targ, wrow, rows, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_pack(const float* master, uint16_t* wtiles, uint16_t* btiles, float* bias, cudaStream_t st) {
+    mlp_pack_kernel<<<1, 256, 0, st>>>(master, wtiles, btiles, bias);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float* master, float* m, float* v, float* grad, int n, float lr, int t, cudaStream_t st) {
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, float(t)), c2 = 1.f - powf(b2, float(t));
+    adam_kernel<<<(n + 255) / 256, 256, 0, st>>>(master, m, v, grad, n, lr, b1, b2, 1e-8f, c1, c2);
+    return cudaGetLastError();
+}
+
 // Host packing of the float32 master weights into BF16 K-major tiles.
 static uint16_t host_bf16(float x) {
     uint32_t u;

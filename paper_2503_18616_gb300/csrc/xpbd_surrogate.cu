@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(SUB) substep_kernel(SimDev S, SubstepCtl C, co
     float* Px = S.pg + ed.voff;
     float* Py = Px + stride;
     float* Pz = Py + stride;
-    const float h = S.h, inv_h = S.inv_h;
+    const float inv_h = S.inv_h;
     const double cxd = S.tool[3 * env], cyd = S.tool[3 * env + 1], czd = S.tool[3 * env + 2];
     const float cx = float(cxd), cy = float(cyd), cz = float(czd);
     for (int w = st; w < Vp / 32; w += SUB) bits[w] = 0u;

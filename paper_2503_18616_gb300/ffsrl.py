@@ -29,7 +29,7 @@ EXPORTS = ["ffsrl_create", "ffsrl_reset", "ffsrl_step", "ffsrl_step_host", "ffsr
            "ffsrl_destroy", "ffsrl_get_info", "ffsrl_last_error", "ffsrl_get_state",
            "ffsrl_set_state", "ffsrl_get_mesh_table", "ffsrl_get_env_ints", "ffsrl_step_noalloc",
            "ffsrl_set_network", "ffsrl_network_forward", "ffsrl_step_surrogate", "ffsrl_record_step",
-           "ffsrl_get_rows"]
+           "ffsrl_get_rows", "ffsrl_get_network", "ffsrl_network_gradient", "ffsrl_train_network"]
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
 NET_PARAMS = 64 * 15 + 64 + 64 * 64 + 64 + 3 * 64 + 3   # FFSRL_NET_PARAMS
@@ -116,6 +116,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.ffsrl_record_step.argtypes = [P, P, I32, P, P]
     L.ffsrl_get_rows.restype = ctypes.c_int
     L.ffsrl_get_rows.argtypes = [P, ctypes.POINTER(ctypes.c_int64), P]
+    L.ffsrl_get_network.restype = ctypes.c_int
+    L.ffsrl_get_network.argtypes = [P, P]
+    L.ffsrl_network_gradient.restype = ctypes.c_int
+    L.ffsrl_network_gradient.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_float, P, P]
+    L.ffsrl_train_network.restype = ctypes.c_int
+    L.ffsrl_train_network.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_float, ctypes.c_float, P]
     _lib = L
     return L
 
@@ -267,6 +273,37 @@ class Sim:
         norm = np.concatenate([np.asarray(a, np.float32).reshape(-1) for a in (in_mean, in_std, out_mean, out_std)])
         assert flat.size == NET_PARAMS and norm.size == NET_NORM
         _check(self._L.ffsrl_set_network(self._h, _np_ptr(flat), _np_ptr(norm)))
+
+    def get_network(self) -> dict:
+        flat = np.zeros(NET_PARAMS, np.float32)
+        _check(self._L.ffsrl_get_network(self._h, _np_ptr(flat)))
+        out, o = {}, 0
+        for k, shape in (("W1", (64, 15)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)), ("W3", (3, 64)),
+                         ("b3", (3,))):
+            n = int(np.prod(shape))
+            out[k] = flat[o:o + n].reshape(shape).astype(np.float64)
+            o += n
+        return out
+
+    def network_gradient(self, features, targets, row_weight, weight_sum: float):
+        """(gradient dict, weighted sum of squared errors) of one batch."""
+        torch = self._torch
+        g = torch.zeros(NET_PARAMS, dtype=torch.float32, device=features.device)
+        loss = torch.zeros(1, dtype=torch.float32, device=features.device)
+        _check(self._L.ffsrl_network_gradient(self._h, _dptr(features), _dptr(targets), _dptr(row_weight),
+                                              int(features.shape[0]), float(weight_sum), _dptr(g), _dptr(loss)))
+        flat = g.cpu().numpy().astype(np.float64)
+        out, o = {}, 0
+        for k, shape in (("W1", (64, 15)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)), ("W3", (3, 64)),
+                         ("b3", (3,))):
+            n = int(np.prod(shape))
+            out[k] = flat[o:o + n].reshape(shape)
+            o += n
+        return out, float(loss.item())
+
+    def train_network(self, features, targets, row_weight, weight_sum: float, lr: float, loss=None):
+        _check(self._L.ffsrl_train_network(self._h, _dptr(features), _dptr(targets), _dptr(row_weight),
+                                           int(features.shape[0]), float(weight_sum), float(lr), _dptr(loss)))
 
     def network_forward(self, features, out=None):
         """features: CUDA tensor [rows][16] float32 -> output [rows][4]."""

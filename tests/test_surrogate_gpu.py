@@ -91,11 +91,11 @@ def test_surrogate_step_matches_oracle(case):
     fb = torch.zeros(n_env, dtype=torch.int32, device="cuda")
     for _ in range(steps):
         obs, rew, _ = sim.step_surrogate(thr if np.isfinite(thr) else 1e30, 10, fallbacks=fb)
-    ofb = {}
+    ofb, orew = {}, {}
     for e, oe in oenvs.items():
         ofb[e] = 0
         for _ in range(steps):
-            o_obs, o_rew, _, f = oe.step_surrogate(net, thr, 10)
+            o_obs, orew[e], _, f = oe.step_surrogate(net, thr, 10)
             ofb[e] += f
     sim.sync()
     x, v, tool = gpu_positions(sim)
@@ -106,7 +106,7 @@ def test_surrogate_step_matches_oracle(case):
         assert np.max(np.abs(x[e * V:(e + 1) * V] - ox)) <= POS_TOL * ext, e
         assert np.array_equal(tool[e], oc)
         assert int(fb[e]) == ofb[e]
-        assert abs(float(rew[e]) - o_rew) <= POS_TOL * ext
+        assert abs(float(rew[e]) - orew[e]) <= POS_TOL * ext
     if case == "always_fallback":
         assert all(f == steps * p["substeps"] for f in ofb.values())
     else:

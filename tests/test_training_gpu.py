@@ -1,0 +1,87 @@
+"""Training of the warm-start network on the tensor cores.
+
+The gradient of the weighted mean squared error computed by the fused
+tcgen05 training kernel (BF16 operands, FP32 accumulation) is compared with
+the FP64 oracle's backward pass (oracle/mlp.py, pinned by finite differences):
+per parameter block the relative Frobenius error must stay below 3e-2, the
+size of BF16 rounding of activations and gradients summed over many rows, and
+the directions must agree (cosine > 0.999). Adam steps must reduce the loss
+of a regression onto a fixed teacher network.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_18616_gb300 import inputs
+from sim_helpers import grid, make_sim
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+KEYS = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+def _setup(rows, seed, zero_frac=0.1):
+    rng = np.random.default_rng(seed)
+    p = oracle.mlp_init(seed)
+    for k in ("b1", "b2", "b3"):
+        p[k] = rng.normal(0, 0.05, p[k].shape)
+    in_mean, in_std = rng.normal(0, 1e-3, 15), rng.uniform(1e-3, 3e-3, 15)
+    out_mean, out_std = rng.normal(0, 1e-6, 3), rng.uniform(1e-6, 3e-6, 3)
+    F = np.zeros((rows, 16), np.float32)
+    F[:, :15] = rng.normal(size=(rows, 15)) * in_std + in_mean
+    T = np.zeros((rows, 4), np.float32)
+    T[:, :3] = rng.normal(size=(rows, 3)) * out_std + out_mean
+    w = (rng.uniform(size=rows) > zero_frac).astype(np.float32)
+    return p, (in_mean, in_std, out_mean, out_std), F, T, w
+
+
+@pytest.mark.parametrize("rows", [300, 5000])
+def test_tensor_core_gradient_matches_fp64_oracle(rows):
+    p, norm, F, T, w = _setup(rows, 4)
+    sim = make_sim([grid((3, 3, 2))], inputs.default_params(n_obs=4), 1)
+    sim.set_network(p, *norm)
+    g, loss = sim.network_gradient(torch.from_numpy(F).cuda(), torch.from_numpy(T).cuda(),
+                                   torch.from_numpy(w).cuda(), float(w.sum()))
+    sel = w > 0
+    Xn = (F[sel, :15].astype(np.float64) - norm[0]) / norm[1]
+    Tn = (T[sel, :3].astype(np.float64) - norm[2]) / norm[3]
+    y, cache = oracle.mlp_forward(p, Xn)
+    ref = oracle.mlp_backward(p, cache, y, Tn)
+    ref_loss = np.sum((y - Tn) ** 2)
+    assert abs(loss - ref_loss) <= 2e-2 * ref_loss
+    for k in KEYS:
+        a, b = g[k].reshape(-1), ref[k].reshape(-1)
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+        assert rel <= 3e-2 and cos > 0.999, (k, rel, cos)
+
+
+def test_adam_steps_fit_a_teacher_network():
+    rows = 20000
+    p, norm, F, _, w = _setup(rows, 6, zero_frac=0.0)
+    teacher = oracle.mlp_init(99)
+    Xn = (F[:, :15].astype(np.float64) - norm[0]) / norm[1]
+    yt, _ = oracle.mlp_forward(teacher, Xn)
+    T = np.zeros((rows, 4), np.float32)
+    T[:, :3] = yt * norm[3] + norm[2]
+    sim = make_sim([grid((3, 3, 2))], inputs.default_params(n_obs=4), 1)
+    sim.set_network(p, *norm)
+    Fd, Td, wd = torch.from_numpy(F).cuda(), torch.from_numpy(T).cuda(), torch.from_numpy(w).cuda()
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    losses = []
+    for it in range(300):
+        sim.train_network(Fd, Td, wd, float(w.sum()), 2e-3, loss)
+        if it % 50 == 0 or it == 299:
+            losses.append(float(loss.item()) / (3 * w.sum()))
+    sim.sync()
+    assert losses[-1] < 0.2 * losses[0], losses
+    q = sim.get_network()
+    assert not np.allclose(q["W2"], p["W2"])
+    # the trained master weights reproduce the loss the kernel reported
+    y, _ = oracle.mlp_forward(q, Xn)
+    mse = np.mean((y - yt) ** 2)
+    assert mse < 0.3 * losses[0]
