@@ -215,17 +215,21 @@ int ffsrl_network_forward(ffsrl_sim* sim, const float* features_dev, float* out_
  * constraint violation of the env (|C|/d for edges, |C|/|V0| for tets) exceeds
  * `threshold`, restore the prediction and run `n_full` iterations instead;
  * then collision and velocity update. Outputs as ffsrl_step; fallbacks_dev
- * [n_env] int32 (may be NULL) is incremented once per fallen-back substep.
- * Asynchronous. */
+ * [n_env] int32 (may be NULL) is incremented once per fallen-back substep;
+ * residual_dev [n_env] float32 (may be NULL) is raised to the largest checked
+ * residual (the caller initialises it, e.g. to zero). Asynchronous. */
 int ffsrl_step_surrogate(ffsrl_sim* sim, const float* actions_dev, float* obs_dev, float* reward_dev,
-                         uint8_t* done_dev, double threshold, int32_t n_full, int32_t* fallbacks_dev);
+                         uint8_t* done_dev, double threshold, int32_t n_full, int32_t* fallbacks_dev,
+                         float* residual_dev);
 
 /* Plain step with `n_full` iterations per substep that records training data:
  * features_dev [substeps][rows][16] (features of every vertex row at each
  * substep's prediction) and targets_dev [substeps][rows][4] (positions after
- * the solve minus the prediction, before collision). Rows: ffsrl_get_rows. */
+ * the solve minus the prediction, before collision), either may be NULL.
+ * residual_dev [n_env] (may be NULL) is raised to the largest residual the
+ * solve leaves. Rows: ffsrl_get_rows. */
 int ffsrl_record_step(ffsrl_sim* sim, const float* actions_dev, int32_t n_full, float* features_dev,
-                      float* targets_dev);
+                      float* targets_dev, float* residual_dev);
 
 /* Row layout of per-vertex buffers: *n_rows rows; env e's vertices occupy
  * rows row_off_host[e] .. row_off_host[e] + V_e - 1 (row_off_host [n_env] or NULL). */

@@ -849,7 +849,7 @@ size_t substep_smem(const ffsrl_sim* s, const LaunchGroup& g, bool& resident) {
 // One surrogate or record step of every env: per substep the features, the
 // network (surrogate mode) and the substep kernel.
 int run_substeps(ffsrl_sim* sim, int mode, const float* actions, float* obs, float* reward, uint8_t* done,
-                 float threshold, int n_full, int* fallbacks, float* feat_out, float* target_out) {
+                 float threshold, int n_full, int* fallbacks, float* residual, float* feat_out, float* target_out) {
     int rc = ensure_surrogate_buffers(sim);
     if (rc) return rc;
     const int S_sub = sim->params.substeps;
@@ -873,6 +873,7 @@ int run_substeps(ffsrl_sim* sim, int mode, const float* actions, float* obs, flo
         C.n_full = n_full;
         C.lambda = sim->d_lambda_full;
         C.fallbacks = fallbacks;
+        C.residual = residual;
         for (const LaunchGroup& g : sim->groups) {
             SimDev S = sim->S;
             S.meshes = sim->d_meshes[g.permute ? 1 : 0];
@@ -888,24 +889,25 @@ int run_substeps(ffsrl_sim* sim, int mode, const float* actions, float* obs, flo
 }  // namespace
 
 int ffsrl_step_surrogate(ffsrl_sim* sim, const float* actions_dev, float* obs_dev, float* reward_dev,
-                         uint8_t* done_dev, double threshold, int32_t n_full, int32_t* fallbacks_dev) {
+                         uint8_t* done_dev, double threshold, int32_t n_full, int32_t* fallbacks_dev,
+                         float* residual_dev) {
     if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
     if (!sim->has_net) return fail(FFSRL_E_INVAL, "no network installed (ffsrl_set_network)");
     if (n_full < 1) return fail(FFSRL_E_INVAL, "n_full must be >= 1");
     FFSRL_CUDA(cudaSetDevice(sim->device));
     return run_substeps(sim, kSubstepSurrogate, actions_dev, obs_dev, reward_dev, done_dev, float(threshold), n_full,
-                        fallbacks_dev, nullptr, nullptr);
+                        fallbacks_dev, residual_dev, nullptr, nullptr);
 }
 
 int ffsrl_record_step(ffsrl_sim* sim, const float* actions_dev, int32_t n_full, float* features_dev,
-                      float* targets_dev) {
+                      float* targets_dev, float* residual_dev) {
     if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
     if (n_full < 1) return fail(FFSRL_E_INVAL, "n_full must be >= 1");
     if ((reinterpret_cast<uintptr_t>(features_dev) | reinterpret_cast<uintptr_t>(targets_dev)) & 15)
         return fail(FFSRL_E_INVAL, "features and targets must be 16-byte aligned");
     FFSRL_CUDA(cudaSetDevice(sim->device));
     return run_substeps(sim, kSubstepRecord, actions_dev, nullptr, nullptr, nullptr, 0.f, n_full, nullptr,
-                        features_dev, targets_dev);
+                        residual_dev, features_dev, targets_dev);
 }
 
 int ffsrl_get_rows(const ffsrl_sim* sim, int64_t* n_rows, int32_t* row_off_host) {

@@ -136,6 +136,31 @@ __device__ void iterate(float4* X, const MeshDev& M, int n_iter, float at_d, flo
     }
 }
 
+// Largest relative violation (|C| / d, |C| / |V0|) over the env's
+// constraints, reduced over the CTA (the result is the same in every thread).
+template <int SUB>
+__device__ float env_residual(const float4* X, const MeshDev& M, int* s_max) {
+    const int st = threadIdx.x;
+    float r = 0.f;
+    for (int c = 0; c < M.n_seg; ++c) {
+        const int4 sg = M.segs[c];
+        const unsigned char* base = M.recs + sg.x;
+        if (c < M.n_ecol) {
+            for (int q = st; q < sg.z; q += SUB)
+                r = fmaxf(r, edge_violation(X, __ldg(reinterpret_cast<const uint2*>(base) + q)));
+        } else {
+            for (int q = st; q < sg.z; q += SUB)
+                r = fmaxf(r, tet_violation(X, __ldg(reinterpret_cast<const uint4*>(base) + q)));
+        }
+    }
+    // non-negative floats order like their bit patterns; NaN maps above +inf
+    atomicMax(s_max, isnan(r) ? 0x7f800001 : __float_as_int(r));
+    __syncthreads();
+    const float out = __int_as_float(*s_max);
+    __syncthreads();
+    return out;
+}
+
 }  // namespace
 
 template <int SUB, bool RES>
@@ -144,6 +169,7 @@ __global__ void __launch_bounds__(SUB) substep_kernel(SimDev S, SubstepCtl C, co
                                                       uint8_t* __restrict__ done) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_red;
+    __shared__ int s_resid;
     const int env = env_list[blockIdx.x];
     const int st = threadIdx.x;
     const EnvDev ed = S.envs[env];
@@ -159,7 +185,10 @@ __global__ void __launch_bounds__(SUB) substep_kernel(SimDev S, SubstepCtl C, co
     const double cxd = S.tool[3 * env], cyd = S.tool[3 * env + 1], czd = S.tool[3 * env + 2];
     const float cx = float(cxd), cy = float(cyd), cz = float(czd);
     for (int w = st; w < Vp / 32; w += SUB) bits[w] = 0u;
-    if (st == 0) s_red = 0;
+    if (st == 0) {
+        s_red = 0;
+        s_resid = 0;
+    }
 
     // Load and predict (vertex order in, slot order in X); add the correction.
     for (int i = st; i < V; i += SUB) {
@@ -183,19 +212,8 @@ __global__ void __launch_bounds__(SUB) substep_kernel(SimDev S, SubstepCtl C, co
     float* lam = C.lambda ? C.lambda + ed.loff : nullptr;
     if (C.mode == kSubstepSurrogate) {
         iterate<SUB>(X, M, 1, ed.alpha_d, S.alpha_v, nullptr);
-        // Largest relative violation over the env's constraints.
-        float r = 0.f;
-        for (int c = 0; c < M.n_seg; ++c) {
-            const int4 sg = M.segs[c];
-            const unsigned char* base = M.recs + sg.x;
-            if (c < M.n_ecol) {
-                for (int q = st; q < sg.z; q += SUB)
-                    r = fmaxf(r, edge_violation(X, __ldg(reinterpret_cast<const uint2*>(base) + q)));
-            } else {
-                for (int q = st; q < sg.z; q += SUB)
-                    r = fmaxf(r, tet_violation(X, __ldg(reinterpret_cast<const uint4*>(base) + q)));
-            }
-        }
+        const float r = env_residual<SUB>(X, M, &s_resid);
+        if (st == 0 && C.residual) C.residual[env] = fmaxf(C.residual[env], r);
         if (!(r <= C.threshold)) atomicMax(&s_red, 1);   // a NaN residual also falls back
         __syncthreads();
         if (s_red) {
@@ -212,6 +230,10 @@ __global__ void __launch_bounds__(SUB) substep_kernel(SimDev S, SubstepCtl C, co
         }
     } else {
         iterate<SUB>(X, M, C.n_full, ed.alpha_d, S.alpha_v, C.n_full > 1 ? lam : nullptr);
+        if (C.residual) {
+            const float r = env_residual<SUB>(X, M, &s_resid);
+            if (st == 0) C.residual[env] = fmaxf(C.residual[env], r);
+        }
         if (C.target) {
             for (int i = st; i < V; i += SUB) {
                 float3 xh, vh;

@@ -21,6 +21,7 @@ struct SubstepCtl {
     int n_full;             // iterations of the full solve
     float* lambda;          // multipliers of the full solve (per env at EnvDev::loff)
     int* fallbacks;         // [n_env] counters (may be null)
+    float* residual;        // [n_env] running max of the checked residual (may be null)
 };
 
 size_t substep_smem_bytes(int Vp, bool resident);

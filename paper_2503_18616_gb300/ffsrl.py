@@ -111,9 +111,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.ffsrl_network_forward.restype = ctypes.c_int
     L.ffsrl_network_forward.argtypes = [P, P, P, ctypes.c_int64]
     L.ffsrl_step_surrogate.restype = ctypes.c_int
-    L.ffsrl_step_surrogate.argtypes = [P, P, P, P, P, ctypes.c_double, I32, P]
+    L.ffsrl_step_surrogate.argtypes = [P, P, P, P, P, ctypes.c_double, I32, P, P]
     L.ffsrl_record_step.restype = ctypes.c_int
-    L.ffsrl_record_step.argtypes = [P, P, I32, P, P]
+    L.ffsrl_record_step.argtypes = [P, P, I32, P, P, P]
     L.ffsrl_get_rows.restype = ctypes.c_int
     L.ffsrl_get_rows.argtypes = [P, ctypes.POINTER(ctypes.c_int64), P]
     L.ffsrl_get_network.restype = ctypes.c_int
@@ -321,7 +321,7 @@ class Sim:
         return int(n.value), off
 
     def step_surrogate(self, threshold: float, n_full: int, actions=None, obs=None, reward=None, done=None,
-                       fallbacks=None):
+                       fallbacks=None, residual=None):
         torch = self._torch
         if obs is None:
             obs = torch.empty((self.n_env, self.obs_dim), dtype=torch.float32, device=self.device)
@@ -330,18 +330,20 @@ class Sim:
         if done is None:
             done = torch.empty(self.n_env, dtype=torch.uint8, device=self.device)
         _check(self._L.ffsrl_step_surrogate(self._h, _dptr(actions), _dptr(obs), _dptr(reward), _dptr(done),
-                                            float(threshold), int(n_full), _dptr(fallbacks)))
+                                            float(threshold), int(n_full), _dptr(fallbacks), _dptr(residual)))
         return obs, reward, done
 
-    def record_step(self, n_full: int, actions=None, features=None, targets=None):
+    def record_step(self, n_full: int, actions=None, features=None, targets=None, residual=None, want=True):
+        """Full-solve step; returns (features [S][rows][16], targets [S][rows][4]) unless want=False."""
         torch = self._torch
         n, _ = self.rows()
         S = self.params["substeps"]
-        if features is None:
+        if want and features is None:
             features = torch.empty((S, n, 16), dtype=torch.float32, device=self.device)
-        if targets is None:
+        if want and targets is None:
             targets = torch.empty((S, n, 4), dtype=torch.float32, device=self.device)
-        _check(self._L.ffsrl_record_step(self._h, _dptr(actions), int(n_full), _dptr(features), _dptr(targets)))
+        _check(self._L.ffsrl_record_step(self._h, _dptr(actions), int(n_full), _dptr(features), _dptr(targets),
+                                         _dptr(residual)))
         return features, targets
 
     def sync(self) -> None:

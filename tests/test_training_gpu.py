@@ -2,10 +2,11 @@
 
 The gradient of the weighted mean squared error computed by the fused
 tcgen05 training kernel (BF16 operands, FP32 accumulation) is compared with
-the FP64 oracle's backward pass (oracle/mlp.py, pinned by finite differences):
-per parameter block the relative Frobenius error must stay below 3e-2, the
-size of BF16 rounding of activations and gradients summed over many rows, and
-the directions must agree (cosine > 0.999). Adam steps must reduce the loss
+the FP64 oracle's backward pass (oracle/mlp.py, pinned by finite differences)
+evaluated with BF16 rounding at the kernel's rounding points: per parameter
+block the relative Frobenius error must stay below 1e-2 (FP32 accumulation
+order). Against the unrounded FP64 gradient the bar is 6e-2 and a cosine
+above 0.998. Adam steps must reduce the loss
 of a regression onto a fixed teacher network.
 """
 import numpy as np
@@ -39,6 +40,28 @@ def _setup(rows, seed, zero_frac=0.1):
     return p, (in_mean, in_std, out_mean, out_std), F, T, w
 
 
+def _bf16_reference_gradient(p, Xn, Tn):
+    """The oracle's backward pass with BF16 rounding applied where the kernel
+    rounds: inputs, weights, hidden activations, dY, dZ2, dZ1 (bias gradients
+    and the loss use the unrounded values)."""
+    bf = oracle.bf16_round
+    W1, W2, W3 = bf(p["W1"]), bf(p["W2"]), bf(p["W3"])
+    Xb = bf(Xn)
+    h1 = np.maximum(Xb @ W1.T + p["b1"], 0)
+    H1 = bf(h1)
+    h2 = np.maximum(H1 @ W2.T + p["b2"], 0)
+    H2 = bf(h2)
+    y = H2 @ W3.T + p["b3"]
+    g = 2.0 * (y - Tn) / (3 * len(Xn))
+    gb = bf(g)
+    dz2 = (gb @ W3) * (h2 > 0)
+    dz2b = bf(dz2)
+    dz1 = (dz2b @ W2) * (h1 > 0)
+    dz1b = bf(dz1)
+    return {"W3": gb.T @ H2, "b3": g.sum(0), "W2": dz2b.T @ H1, "b2": dz2.sum(0),
+            "W1": dz1b.T @ Xb, "b1": dz1.sum(0)}
+
+
 @pytest.mark.parametrize("rows", [300, 5000])
 def test_tensor_core_gradient_matches_fp64_oracle(rows):
     p, norm, F, T, w = _setup(rows, 4)
@@ -53,11 +76,16 @@ def test_tensor_core_gradient_matches_fp64_oracle(rows):
     ref = oracle.mlp_backward(p, cache, y, Tn)
     ref_loss = np.sum((y - Tn) ** 2)
     assert abs(loss - ref_loss) <= 2e-2 * ref_loss
+    refb = _bf16_reference_gradient(p, Xn, Tn)
     for k in KEYS:
-        a, b = g[k].reshape(-1), ref[k].reshape(-1)
+        a, b, c = g[k].reshape(-1), ref[k].reshape(-1), refb[k].reshape(-1)
+        # tight: same rounding points, FP32 versus FP64 accumulation
+        assert np.linalg.norm(a - c) / np.linalg.norm(c) <= 1e-2, k
+        # loose: against the unrounded FP64 gradient (BF16 rounding compounds
+        # through dY, dZ2 and dZ1 before reaching the first layer)
         rel = np.linalg.norm(a - b) / np.linalg.norm(b)
         cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
-        assert rel <= 3e-2 and cos > 0.999, (k, rel, cos)
+        assert rel <= 6e-2 and cos > 0.998, (k, rel, cos)
 
 
 def test_adam_steps_fit_a_teacher_network():
