@@ -290,6 +290,133 @@ def run_e2e(args, sim, n_env, world, rank, seed, barrier, dist):
 
 
 
+def run_warmstart(args):
+    """Learned warm-start against plain XPBD at equal position error.
+
+    The network is trained on the simulator's own full-solve trajectories
+    (untimed, reported). Then, on the 4096-env workload, each path runs K
+    timed steps (CUDA events) and, separately, N steps from the same reset
+    whose positions are compared with the FP64 oracle running the full solve:
+    plain XPBD with k = 1, 2, 3, 5, 7, 10 iterations, and the warm-start
+    (network + 1 iteration) with the residual-triggered fallback at the
+    configured threshold and at multiples of the full solve's own median
+    residual. `value` is the warm-start's env-steps/s without fallback; the
+    comparison at equal error picks the cheapest plain k whose error is not
+    larger than the warm-start's."""
+    import torch
+    import __graft_entry__
+    import oracle
+    from paper_2503_18616_gb300 import ffsrl, inputs, surrogate
+    __graft_entry__.build()
+    w = inputs.WORKLOADS[args.workload]
+    mesh = inputs.grid_block(*w["shape"])
+    n_env = args.envs or w["n_env"]
+    base = inputs.default_params()
+    n_full = w["n_full"]
+    # 1. training (untimed)
+    tsim = ffsrl.Sim([mesh], base, w["train_envs"])
+    tr = surrogate.train(tsim, [mesh], n_full=n_full, env_substeps=w["train_env_substeps"], lr=1e-3, epochs=2,
+                         seed=args.seed)
+    tsim.close()
+    sim = ffsrl.Sim([mesh], base, n_env)
+    sim.set_network(tr["params"], *tr["norm"])
+    # full-solve residual level (median over envs of the largest residual of 10 steps)
+    sim.reset(args.seed + 1)
+    rf = torch.zeros(n_env, device="cuda")
+    for _ in range(10):
+        sim.record_step(n_full, residual=rf, want=False)
+    full_resid = float(np.median(rf.cpu().numpy()))
+    # 2. FP64 oracle reference (full solve) on sampled envs
+    N = args.acc_steps
+    samp = [0, 1, n_env // 2, n_env - 1]
+    om = oracle.Mesh(*mesh)
+    V = om.V
+    ref = {}
+    t0 = time.perf_counter()
+    for e in samp:
+        oe = oracle.Env(om, inputs.default_params(iterations=n_full))
+        oe.reset(args.seed, e)
+        oe.run(N, want_obs=False)
+        ref[e] = oe.state()[0]
+    t_oracle = time.perf_counter() - t0
+
+    def error(s):
+        x, _, _ = s.get_state()
+        x = x.cpu().numpy().astype(np.float64)
+        return float(max(np.abs(x[e * V:(e + 1) * V] - ref[e]).max() for e in samp) / om.extent)
+
+    def timed(step, s):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(s.stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(s.stream)
+        torch.cuda.synchronize()
+        return n_env * args.steps / (ev0.elapsed_time(ev1) / 1e3)
+
+    plain = {}
+    for k in (1, 2, 3, 5, 7, 10):
+        ps = ffsrl.Sim([mesh], inputs.default_params(iterations=k), n_env)
+        ps.reset(args.seed)
+        for _ in range(N):
+            ps.step_into(None, None, None, None)
+        err = error(ps)
+        ps.reset(args.seed)
+        rate = timed(lambda: ps.step_into(None, None, None, None), ps)
+        plain[k] = {"env_steps_per_s": rate, "max_pos_err_over_extent": err}
+        ps.close()
+    warm = {}
+    fb = torch.zeros(n_env, dtype=torch.int32, device="cuda")
+    obs = torch.empty((n_env, sim.obs_dim), dtype=torch.float32, device="cuda")
+    rew = torch.empty(n_env, dtype=torch.float32, device="cuda")
+    done = torch.empty(n_env, dtype=torch.uint8, device="cuda")
+    for label, thr in (("no_fallback", 1e30), ("threshold_configured", w["threshold"]),
+                       ("threshold_5x_full_solve_residual", 5 * full_resid),
+                       ("threshold_2x_full_solve_residual", 2 * full_resid)):
+        sim.reset(args.seed)
+        fb.zero_()
+        for _ in range(N):
+            sim.step_surrogate(thr, n_full, fallbacks=fb)
+        err = error(sim)
+        frate = float(fb.sum().item()) / (n_env * N * base["substeps"])
+        sim.reset(args.seed)
+        rate = timed(lambda: sim.step_surrogate(thr, n_full, obs=obs, reward=rew, done=done), sim)
+        warm[label] = {"threshold": thr if thr < 1e29 else None, "env_steps_per_s": rate,
+                       "max_pos_err_over_extent": err, "fallback_rate": frate}
+    # the same step as per-substep launches (features, network, substep kernels)
+    pipe = ffsrl.Sim([mesh], base, n_env, schedule_flags=ffsrl.SCHED_SURROGATE_PIPELINE)
+    pipe.set_network(tr["params"], *tr["norm"])
+    pipe.reset(args.seed)
+    warm["no_fallback_per_substep_launches"] = {
+        "threshold": None, "env_steps_per_s": timed(lambda: pipe.step_surrogate(1e30, n_full, obs=obs, reward=rew,
+                                                                               done=done), pipe)}
+    pipe.close()
+    sim.sync()
+    wv = warm["no_fallback"]
+    eq = [k for k in sorted(plain) if plain[k]["max_pos_err_over_extent"] <= wv["max_pos_err_over_extent"]]
+    k_eq = eq[0] if eq else None
+    line = {"metric": METRIC, "value": wv["env_steps_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * n_env / wv["env_steps_per_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+            "config": {"workload": args.workload, "n_env": n_env, "verts_per_env": V, "n_full": n_full,
+                       "accuracy_steps": N, "accuracy_envs": samp, "reference": f"FP64 oracle, {n_full} iterations"},
+            "training": {"seconds": tr["seconds"], "env_substeps": tr["env_substeps"], "adam_steps": tr["adam_steps"],
+                         "loss_first": tr["losses"][0], "loss_last": tr["losses"][-1],
+                         "loss_unit": "mean squared error of normalised corrections"},
+            "full_solve_residual_median": full_resid,
+            "warmstart": warm, "plain": {str(k): v for k, v in plain.items()},
+            "equal_error": {"plain_iterations": k_eq,
+                            "speedup": (wv["env_steps_per_s"] / plain[k_eq]["env_steps_per_s"]) if k_eq else None},
+            "cpu_baseline": {"value": len(samp) * N / t_oracle, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"envs {samp} x {N} steps, {n_full} iterations, FP64 oracle, 1 host thread"},
+            "gpu_launches": args.steps}
+    print(json.dumps(line), flush=True)
+    return line
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -474,11 +601,15 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--envs", type=int, default=0, help="override the workload's env count")
     ap.add_argument("--schedule", default="", help="force threads_per_env:envs_per_cta:ring:permute")
+    ap.add_argument("--acc-steps", type=int, default=50, help="steps of the warm-start accuracy comparison")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    from paper_2503_18616_gb300 import inputs
     if args.impl == "reference":
         run_reference(args)
+    elif inputs.WORKLOADS[args.workload].get("warmstart"):
+        run_warmstart(args)
     else:
         run_ours(args)
 

@@ -89,6 +89,8 @@ typedef struct {
 #define FFSRL_SCHED_NO_RING 4     /* read constraint records from L2 instead of the TMA ring */
 #define FFSRL_SCHED_ENVS2 8       /* two envs per CTA sharing one ring (else one) */
 #define FFSRL_SCHED_ENVS4 16      /* four envs per CTA sharing one ring */
+#define FFSRL_SCHED_SURROGATE_PIPELINE 32  /* warm-start step as per-substep launches (features,
+                                              network, substep) instead of one fused kernel */
 
 /* Sizes of a created simulator. */
 typedef struct {
@@ -221,6 +223,24 @@ int ffsrl_network_forward(ffsrl_sim* sim, const float* features_dev, float* out_
 int ffsrl_step_surrogate(ffsrl_sim* sim, const float* actions_dev, float* obs_dev, float* reward_dev,
                          uint8_t* done_dev, double threshold, int32_t n_full, int32_t* fallbacks_dev,
                          float* residual_dev);
+/* Implementation note: envs whose mesh fits one CTA's shared memory take the
+ * whole step in one fused kernel (state resident on chip, the network on the
+ * tensor cores of the same CTA); larger meshes, or every mesh when
+ * FFSRL_SCHED_SURROGATE_PIPELINE is set, take three launches per substep
+ * (features, network, substep). Both compute the same operations. */
+
+/* Mixed rollout: from the next ffsrl_step (and ffsrl_step_host) on, the envs
+ * whose byte in mask_host [n_env] is non-zero take the surrogate-assisted step
+ * of ffsrl_step_surrogate (same threshold and n_full semantics), the others
+ * the plain step, both within the one call and without a host round trip.
+ * mask_host NULL switches back to plain stepping for every env. fallbacks_dev
+ * (may be NULL) is caller-owned int32 [n_env], incremented per fallen-back
+ * substep for as long as the setting lasts. Requires a network
+ * (ffsrl_set_network) and meshes that fit the fused kernel (FFSRL_E_INVAL
+ * otherwise). The mask is copied; ffsrl_step_noalloc rejects a sim in this
+ * mode. */
+int ffsrl_set_surrogate_envs(ffsrl_sim* sim, const uint8_t* mask_host, double threshold, int32_t n_full,
+                             int32_t* fallbacks_dev);
 
 /* Plain step with `n_full` iterations per substep that records training data:
  * features_dev [substeps][rows][16] (features of every vertex row at each

@@ -50,6 +50,11 @@ struct LaunchGroup {
     int n = 0;
     long long verts = 0;      // total vertices (work estimate)
     int* d_list = nullptr;
+    std::vector<int> list;    // host copy of the env list
+    // mixed rollout (ffsrl_set_surrogate_envs): plain and warm-start sublists
+    int* d_plain = nullptr;
+    int* d_warm = nullptr;
+    int n_plain = 0, n_warm = 0;
     StepConfig cfg;
     bool permute = true;
     size_t smem = 0;
@@ -118,6 +123,13 @@ struct ffsrl_sim {
     float4* d_feat = nullptr;     // [stride][4] features
     float4* d_dx = nullptr;       // [stride] network corrections
     float* d_lambda_full = nullptr;
+    // mixed rollout: warm-start envs stepped beside the plain ones
+    bool mixed = false;
+    float mix_threshold = 0.f;
+    int mix_n_full = 1;
+    int* mix_fallbacks = nullptr;
+    cudaStream_t warm_stream = nullptr;
+    cudaEvent_t warm_done = nullptr;
 
     template <class T>
     cudaError_t alloc(T** p, size_t count) {
@@ -141,6 +153,8 @@ struct ffsrl_sim {
             if (g.done) cudaEventDestroy(g.done);
         }
         if (fork) cudaEventDestroy(fork);
+        if (warm_stream) cudaStreamDestroy(warm_stream);
+        if (warm_done) cudaEventDestroy(warm_done);
         for (void* p : dev_allocs) cudaFree(p);
         if (h_pinned) cudaFreeHost(h_pinned);
     }
@@ -161,7 +175,7 @@ int check_params(const ffsrl_params& p) {
     if (b != 0 && b != 128 && b != 256 && b != 384 && b != 512 && b != 1024)
         return fail(FFSRL_E_INVAL, "block_threads must be 0, 128, 256, 384, 512 or 1024");
     if (p.schedule_flags & ~(FFSRL_SCHED_FORCE | FFSRL_SCHED_NO_PERMUTE | FFSRL_SCHED_NO_RING |
-                             FFSRL_SCHED_ENVS2 | FFSRL_SCHED_ENVS4))
+                             FFSRL_SCHED_ENVS2 | FFSRL_SCHED_ENVS4 | FFSRL_SCHED_SURROGATE_PIPELINE))
         return fail(FFSRL_E_INVAL, "unknown schedule_flags bits");
     if ((p.schedule_flags & FFSRL_SCHED_ENVS2) && (p.schedule_flags & FFSRL_SCHED_ENVS4))
         return fail(FFSRL_E_INVAL, "FFSRL_SCHED_ENVS2 and FFSRL_SCHED_ENVS4 are exclusive");
@@ -220,6 +234,25 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, bool permute, MeshDev& d) {
         FFSRL_CUDA(s->upload(&d_nb, nb.data(), nb.size()));
         d.nbr_off = d_off;
         d.nbr = d_nb;
+        // the same adjacency indexed by shared-memory slot (fused warm-start step)
+        std::vector<int> soff(m.V + 1, 0);
+        std::vector<uint16_t> snb(nb.size());
+        std::vector<float4> rs(m.V);
+        for (int q = 0; q < m.V; ++q) {
+            const int i = sc.vert_of[q];
+            soff[q + 1] = soff[q] + (off[i + 1] - off[i]);
+            for (int k = off[i]; k < off[i + 1]; ++k) snb[soff[q] + (k - off[i])] = sc.slot_of[nb[k]];
+            rs[q] = rw[i];
+        }
+        int* d_soff;
+        uint16_t* d_snb;
+        float4* d_rs;
+        FFSRL_CUDA(s->upload(&d_soff, soff.data(), soff.size()));
+        FFSRL_CUDA(s->upload(&d_snb, snb.data(), snb.size()));
+        FFSRL_CUDA(s->upload(&d_rs, rs.data(), rs.size()));
+        d.snbr_off = d_soff;
+        d.snbr = d_snb;
+        d.rest_s = d_rs;
     }
     // Tool box around the rest bounding box and tool start above the top face.
     for (int k = 0; k < 2; ++k) {
@@ -263,19 +296,23 @@ cudaError_t launch_group(ffsrl_sim* s, const LaunchGroup& g, cudaStream_t st, co
 
 // All groups of one step: forked onto the groups' streams after the work
 // already queued on the sim's stream, joined back before the step returns.
+// In a mixed rollout only the plain sublists are launched here.
 cudaError_t launch_all(ffsrl_sim* s, const SimDev* Sx, const float* a, float* o, float* r, uint8_t* d) {
     if (s->groups.size() == 1) {
         const LaunchGroup& g = s->groups[0];
         SimDev S = Sx ? *Sx : s->S;
         S.meshes = s->d_meshes[g.permute ? 1 : 0];
-        return launch_step(S, g.cfg, g.d_list, g.n, g.smem, s->stream, a, o, r, d);
+        return s->mixed ? launch_step(S, g.cfg, g.d_plain, g.n_plain, g.smem, s->stream, a, o, r, d)
+                        : launch_step(S, g.cfg, g.d_list, g.n, g.smem, s->stream, a, o, r, d);
     }
     cudaError_t e = cudaEventRecord(s->fork, s->stream);
     for (const LaunchGroup& g : s->groups) {
         if (e == cudaSuccess) e = cudaStreamWaitEvent(g.stream, s->fork, 0);
         SimDev S = Sx ? *Sx : s->S;
         S.meshes = s->d_meshes[g.permute ? 1 : 0];
-        if (e == cudaSuccess) e = launch_step(S, g.cfg, g.d_list, g.n, g.smem, g.stream, a, o, r, d);
+        if (e == cudaSuccess)
+            e = s->mixed ? launch_step(S, g.cfg, g.d_plain, g.n_plain, g.smem, g.stream, a, o, r, d)
+                         : launch_step(S, g.cfg, g.d_list, g.n, g.smem, g.stream, a, o, r, d);
         if (e == cudaSuccess) e = cudaEventRecord(g.done, g.stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, g.done, 0);
     }
@@ -501,6 +538,7 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
         g.cfg.resident = cls > 0;
         any_streaming |= cls == 0;
         FFSRL_CUDA(s->upload(&g.d_list, list.data(), list.size()));
+        g.list = list;
         s->groups.push_back(g);
     }
     S.xg = nullptr;
@@ -616,11 +654,26 @@ int ffsrl_reset(ffsrl_sim* sim, const uint8_t* env_mask_dev, uint64_t seed) {
     return FFSRL_OK;
 }
 
+namespace {
+int launch_warm_groups(ffsrl_sim* sim, cudaStream_t st, bool sublists, const float* actions, float* obs,
+                       float* reward, uint8_t* done, float threshold, int n_full, int* fallbacks, float* residual);
+}  // namespace
+
 int ffsrl_step(ffsrl_sim* sim, const float* actions_dev, float* obs_dev, float* reward_dev,
                uint8_t* done_dev) {
     if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
     FFSRL_CUDA(cudaSetDevice(sim->device));
+    if (sim->mixed) {
+        // warm-start envs on their own stream, beside the plain groups
+        FFSRL_CUDA(cudaEventRecord(sim->fork, sim->stream));
+        FFSRL_CUDA(cudaStreamWaitEvent(sim->warm_stream, sim->fork, 0));
+        const int rc = launch_warm_groups(sim, sim->warm_stream, true, actions_dev, obs_dev, reward_dev, done_dev,
+                                          sim->mix_threshold, sim->mix_n_full, sim->mix_fallbacks, nullptr);
+        if (rc) return rc;
+        FFSRL_CUDA(cudaEventRecord(sim->warm_done, sim->warm_stream));
+    }
     FFSRL_CUDA(launch_all(sim, nullptr, actions_dev, obs_dev, reward_dev, done_dev));
+    if (sim->mixed) FFSRL_CUDA(cudaStreamWaitEvent(sim->stream, sim->warm_done, 0));
     return FFSRL_OK;
 }
 
@@ -678,7 +731,9 @@ int ffsrl_sync(ffsrl_sim* sim) {
     if (first >= 0) {
         FFSRL_CUDA(cudaMemset(sim->S.err, 0, err.size() * sizeof(int)));
         if (bits & kErrTimeout)
-            return fail(FFSRL_E_TIMEOUT, "a constraint-record copy timed out in env " + std::to_string(first));
+            return fail(FFSRL_E_TIMEOUT,
+                        "a bounded wait (constraint-record copy or tensor-core completion) timed out in env " +
+                            std::to_string(first));
         return fail(FFSRL_E_NAN, "non-finite positions in env " + std::to_string(first));
     }
     return FFSRL_OK;
@@ -846,17 +901,62 @@ size_t substep_smem(const ffsrl_sim* s, const LaunchGroup& g, bool& resident) {
     return resident ? res : substep_smem_bytes(vp, false);
 }
 
-// One surrogate or record step of every env: per substep the features, the
-// network (surrogate mode) and the substep kernel.
+// Shared memory of the fused warm-start step for a group (0: does not fit).
+size_t warm_smem(const ffsrl_sim* s, const LaunchGroup& g) {
+    int vp = 0;
+    for (int mi : g.meshes) vp = std::max(vp, s->h_meshes[g.permute ? 1 : 0][mi].Vp);
+    const size_t b = warm_smem_bytes(vp);
+    return b + 1024 + 256 <= s->max_smem ? b : 0;   // room for the kernel's static shared memory
+}
+
+// Fused warm-start steps of the groups that fit (all envs of each group, or
+// their warm-start sublists in a mixed rollout).
+int launch_warm_groups(ffsrl_sim* sim, cudaStream_t st, bool sublists, const float* actions, float* obs,
+                       float* reward, uint8_t* done, float threshold, int n_full, int* fallbacks, float* residual) {
+    SubstepCtl C{};
+    C.mode = kSubstepSurrogate;
+    C.threshold = threshold;
+    C.n_full = n_full;
+    C.lambda = sim->d_lambda_full;
+    C.fallbacks = fallbacks;
+    C.residual = residual;
+    C.scratch = sim->d_dx;
+    for (const LaunchGroup& g : sim->groups) {
+        const int n = sublists ? g.n_warm : g.n;
+        const size_t smem = warm_smem(sim, g);
+        if (!n || !smem) continue;
+        SimDev S = sim->S;
+        S.meshes = sim->d_meshes[g.permute ? 1 : 0];
+        FFSRL_CUDA(launch_warm_step(S, sim->net, C, sublists ? g.d_warm : g.d_list, n, smem, actions, obs, reward,
+                                    done, st));
+    }
+    return FFSRL_OK;
+}
+
+// One surrogate or record step of every env. Surrogate mode: groups that fit
+// the fused kernel take one launch; the others (and every group in record mode
+// or with FFSRL_SCHED_SURROGATE_PIPELINE) per substep the features, the network
+// and the substep kernel.
 int run_substeps(ffsrl_sim* sim, int mode, const float* actions, float* obs, float* reward, uint8_t* done,
                  float threshold, int n_full, int* fallbacks, float* residual, float* feat_out, float* target_out) {
     int rc = ensure_surrogate_buffers(sim);
     if (rc) return rc;
     const int S_sub = sim->params.substeps;
     const size_t rows = size_t(sim->stride);
+    const bool fused = mode == kSubstepSurrogate && !(sim->params.schedule_flags & FFSRL_SCHED_SURROGATE_PIPELINE);
+    std::vector<const LaunchGroup*> pipe;
+    for (const LaunchGroup& g : sim->groups)
+        if (!fused || !warm_smem(sim, g)) pipe.push_back(&g);
+    if (fused) {
+        rc = launch_warm_groups(sim, sim->stream, false, actions, obs, reward, done, threshold, n_full, fallbacks,
+                                residual);
+        if (rc) return rc;
+    }
+    if (pipe.empty()) return FFSRL_OK;
     for (int sub = 0; sub < S_sub; ++sub) {
         float4* F = feat_out ? reinterpret_cast<float4*>(feat_out) + size_t(sub) * rows * 4 : sim->d_feat;
-        for (const LaunchGroup& g : sim->groups) {
+        for (const LaunchGroup* gp : pipe) {
+            const LaunchGroup& g = *gp;
             SimDev S = sim->S;
             S.meshes = sim->d_meshes[g.permute ? 1 : 0];
             FFSRL_CUDA(launch_features(S, g.d_list, g.n, sub == 0, actions, F, sim->stream));
@@ -874,7 +974,8 @@ int run_substeps(ffsrl_sim* sim, int mode, const float* actions, float* obs, flo
         C.lambda = sim->d_lambda_full;
         C.fallbacks = fallbacks;
         C.residual = residual;
-        for (const LaunchGroup& g : sim->groups) {
+        for (const LaunchGroup* gp : pipe) {
+            const LaunchGroup& g = *gp;
             SimDev S = sim->S;
             S.meshes = sim->d_meshes[g.permute ? 1 : 0];
             bool resident = false;
@@ -897,6 +998,48 @@ int ffsrl_step_surrogate(ffsrl_sim* sim, const float* actions_dev, float* obs_de
     FFSRL_CUDA(cudaSetDevice(sim->device));
     return run_substeps(sim, kSubstepSurrogate, actions_dev, obs_dev, reward_dev, done_dev, float(threshold), n_full,
                         fallbacks_dev, residual_dev, nullptr, nullptr);
+}
+
+int ffsrl_set_surrogate_envs(ffsrl_sim* sim, const uint8_t* mask_host, double threshold, int32_t n_full,
+                             int32_t* fallbacks_dev) {
+    if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
+    if (!mask_host) {
+        sim->mixed = false;
+        return FFSRL_OK;
+    }
+    if (!sim->has_net) return fail(FFSRL_E_INVAL, "no network installed (ffsrl_set_network)");
+    if (n_full < 1) return fail(FFSRL_E_INVAL, "n_full must be >= 1");
+    FFSRL_CUDA(cudaSetDevice(sim->device));
+    int rc = ensure_surrogate_buffers(sim);
+    if (rc) return rc;
+    for (const LaunchGroup& g : sim->groups) {
+        bool any = false;
+        for (int e : g.list) any |= mask_host[e] != 0;
+        if (any && !warm_smem(sim, g))
+            return fail(FFSRL_E_INVAL, "a warm-start env's mesh does not fit the fused kernel's shared memory");
+    }
+    if (!sim->warm_stream) {
+        FFSRL_CUDA(cudaStreamCreateWithFlags(&sim->warm_stream, cudaStreamNonBlocking));
+        FFSRL_CUDA(cudaEventCreateWithFlags(&sim->warm_done, cudaEventDisableTiming));
+    }
+    if (!sim->fork) FFSRL_CUDA(cudaEventCreateWithFlags(&sim->fork, cudaEventDisableTiming));
+    for (LaunchGroup& g : sim->groups) {
+        std::vector<int> plain, warm;
+        for (int e : g.list) (mask_host[e] ? warm : plain).push_back(e);
+        if (!g.d_plain) {
+            FFSRL_CUDA(sim->alloc(&g.d_plain, g.list.size()));
+            FFSRL_CUDA(sim->alloc(&g.d_warm, g.list.size()));
+        }
+        FFSRL_CUDA(cudaMemcpy(g.d_plain, plain.data(), plain.size() * sizeof(int), cudaMemcpyHostToDevice));
+        FFSRL_CUDA(cudaMemcpy(g.d_warm, warm.data(), warm.size() * sizeof(int), cudaMemcpyHostToDevice));
+        g.n_plain = int(plain.size());
+        g.n_warm = int(warm.size());
+    }
+    sim->mix_threshold = float(threshold);
+    sim->mix_n_full = n_full;
+    sim->mix_fallbacks = fallbacks_dev;
+    sim->mixed = true;
+    return FFSRL_OK;
 }
 
 int ffsrl_record_step(ffsrl_sim* sim, const float* actions_dev, int32_t n_full, float* features_dev,
@@ -1040,6 +1183,7 @@ extern "C" int ffsrl_step_noalloc(ffsrl_sim* sim, const float* actions_dev, floa
     if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
     if (!actions_dev || !x_dev || !v_dev || !tool_dev)
         return fail(FFSRL_E_INVAL, "ffsrl_step_noalloc needs actions_dev, x_dev, v_dev and tool_dev");
+    if (sim->mixed) return fail(FFSRL_E_INVAL, "ffsrl_step_noalloc does not step warm-start envs (mixed rollout)");
     const size_t rows = size_t(sim->stride), n = size_t(sim->n_env);
     bool any_streaming = false;
     for (const LaunchGroup& g : sim->groups) any_streaming |= !g.cfg.resident;

@@ -36,6 +36,9 @@ struct MeshDev {
     const int* top;                   // [n_top] top-face vertex ids
     const int* nbr_off;               // [V + 1] 1-ring of each vertex (vertex order, CSR)
     const int* nbr;                   // [2E]
+    const int* snbr_off;              // [V + 1] 1-ring of each slot (slot order, CSR, same neighbour order)
+    const uint16_t* snbr;             // [2E] slots of the neighbours
+    const float4* rest_s;             // [V] rest position and inverse mass (slot order)
     double box_lo[3], box_hi[3], tool_start[3];
     float min_len2;                   // edges with |x_ab|^2 below this are skipped
     int pad1;

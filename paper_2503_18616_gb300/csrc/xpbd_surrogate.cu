@@ -17,6 +17,7 @@
 // substep need every vertex of the env), unlike the resident plain step.
 #include <cstdint>
 
+#include "tc_prims.cuh"
 #include "xpbd_device.cuh"
 #include "xpbd_project.cuh"
 #include "xpbd_surrogate.h"
@@ -363,6 +364,464 @@ cudaError_t launch_substep(const SimDev& S, const SubstepCtl& C, const int* env_
     } else {
         substep_kernel<256, false><<<n_list, 256, smem, st>>>(S, C, env_list, n_list, obs, reward, done);
     }
+    return cudaGetLastError();
+}
+
+// ---- fused warm-start step ---------------------------------------------------
+//
+// One CTA of 256 threads advances one env through all substeps of a step with
+// its state resident in shared memory, as the plain step kernel does, and runs
+// the warm-start network inside the same CTA on the tensor cores:
+//   per substep: features of every vertex at the predicted state (from the
+//   resident positions and predicted velocities), the network tile by tile
+//   (128 rows per tile, tcgen05.mma into TMEM, BF16 operands), the corrections
+//   added to the free vertices once every tile is done, one constraint
+//   iteration, the residual check with the fallback to the full solve, then
+//   collision, the velocity update and the next prediction.
+// Rows of the network are shared-memory slots. The predicted velocities stay
+// in shared memory (the features need them for the 1-ring means); the
+// substep-start positions live in global memory (slot order, L2-resident) as
+// in the plain kernel; the corrections pass through a global scratch row per
+// slot, because every tile's features must see the uncorrected prediction.
+// The fallback rebuilds the prediction exactly: x~ = fma(h, v~, x_prev) is the
+// same rounded operation that made it.
+namespace {
+
+struct WarmLayout {
+    size_t x, vh, w, h, bias, bits, total;
+    __host__ __device__ explicit WarmLayout(int Vp) {
+        x = 0;
+        vh = x + size_t(Vp) * 16;
+        w = (vh + size_t(Vp) * 12 + 127) / 128 * 128;
+        h = w + size_t(kMlpWeightBytes);
+        bias = h + 16384;
+        bits = bias + 144 * 4;
+        total = bits + size_t(Vp / 32) * 4;
+    }
+};
+
+constexpr uint32_t kWarmTmemCols = 128;
+
+}  // namespace
+
+size_t warm_smem_bytes(int Vp) { return WarmLayout(Vp).total; }
+
+__global__ void __launch_bounds__(kWarmThreads, 2)
+    warm_step_kernel(SimDev S, MlpDev net, SubstepCtl C, const int* __restrict__ env_list, int n_list,
+                     const float* __restrict__ actions, float* __restrict__ obs, float* __restrict__ reward,
+                     uint8_t* __restrict__ done) {
+    using namespace tc;
+    constexpr int SUB = kWarmThreads;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ double s_tool[3];
+    __shared__ int s_resid;
+    if (int(blockIdx.x) >= n_list) return;
+    const int env = env_list[blockIdx.x];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const EnvDev ed = S.envs[env];
+    const MeshDev M = S.meshes[ed.mesh];
+    const int V = M.V, Vp = M.Vp;
+    const long long stride = S.stride;
+    const WarmLayout L(Vp);
+    float4* X = reinterpret_cast<float4*>(sm + L.x);
+    float* Vx = reinterpret_cast<float*>(sm + L.vh);
+    float* Vy = Vx + Vp;
+    float* Vz = Vy + Vp;
+    unsigned char* Wt = sm + L.w;
+    unsigned char* Ht = sm + L.h;
+    unsigned char* At = Ht;   // the input tile is dead once layer 1 has read it
+    float* bias = reinterpret_cast<float*>(sm + L.bias);
+    unsigned* bits = reinterpret_cast<unsigned*>(sm + L.bits);
+    float* Px = S.pg + ed.voff;
+    float* Py = Px + stride;
+    float* Pz = Py + stride;
+    float4* DX = C.scratch + ed.voff;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                     "r"(kWarmTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int i = tid; i < kMlpWeightBytes / 16; i += SUB)
+        reinterpret_cast<uint4*>(Wt)[i] = reinterpret_cast<const uint4*>(net.wtiles)[i];
+    for (int i = tid; i < 144; i += SUB) bias[i] = net.bias[i];
+    for (int w = tid; w < Vp / 32; w += SUB) bits[w] = 0u;
+    if (tid == 0) {
+        mbar_init(&mbar);
+        update_tool(S, M, env, actions, s_tool);
+    }
+    // Load the state (vertex order in, slot order out) and predict the first substep.
+    const float h = S.h, inv_h = S.inv_h;
+    const float hgx = h * S.gx, hgy = h * S.gy, hgz = h * S.gz;
+    {
+        const float* gx = S.x + ed.voff;
+        const float* gv = S.v + ed.voff;
+        for (int i = tid; i < V; i += SUB) {
+            const int s = M.slot_of[i];
+            const float w = M.rest_w[i].w;
+            const float x0 = gx[i], x1 = gx[stride + i], x2 = gx[2 * stride + i];
+            float v0 = gv[i], v1 = gv[stride + i], v2 = gv[2 * stride + i];
+            Px[s] = x0;
+            Py[s] = x1;
+            Pz[s] = x2;
+            if (w > 0.f) {
+                v0 += hgx;
+                v1 += hgy;
+                v2 += hgz;
+                X[s] = make_float4(__fmaf_rn(h, v0, x0), __fmaf_rn(h, v1, x1), __fmaf_rn(h, v2, x2), w);
+            } else {
+                X[s] = make_float4(x0, x1, x2, w);
+            }
+            Vx[s] = v0;
+            Vy[s] = v1;
+            Vz[s] = v2;
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc64 = umma_idesc_bf16(128, 64), idesc16 = umma_idesc_bf16(128, 16);
+    const uint32_t aW1 = saddr(Wt), aW2 = aW1 + 2048, aW3 = aW1 + 10240, aA = saddr(At), aH = saddr(Ht);
+    const float cx = float(s_tool[0]), cy = float(s_tool[1]), cz = float(s_tool[2]);
+    const float rad = S.radius, rad2 = rad * rad;
+    const float at_d = ed.alpha_d, at_v = S.alpha_v;
+    float* lam = C.lambda ? C.lambda + ed.loff : nullptr;
+    const int n_tiles = (V + 127) / 128;
+    // TMEM lanes of this warp (a warp reaches the 32 lanes of its quarter) and
+    // the column half it reads back in the hidden-layer epilogues.
+    const int q4 = warp & 3, chalf = warp >> 2;
+    const uint32_t tlane = uint32_t(32 * q4) << 16;
+    const int erow = 32 * q4 + lane;
+    uint32_t phase = 0;
+    bool failed = false;
+    int n_fallback = 0;
+
+    for (int sub = 0; sub < S.substeps && !failed; ++sub) {
+        const bool last = sub == S.substeps - 1;
+        if (tid == 0) s_resid = 0;
+        // -- features and network, one 128-row tile at a time
+        for (int t = 0; t < n_tiles; ++t) {
+            {
+                // Row r of the tile: threads 0..127 the position features
+                // (displacement from rest, 1-ring mean offset, offset from the
+                // tool), threads 128..255 the velocity features (velocity,
+                // 1-ring mean offset) and the zero padding column.
+                const int r = tid & 127, s = t * 128 + r;
+                const bool pos = tid < 128;
+                float f[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (s < V) {
+                    // pos: x and its 1-ring mean over X; else v and its 1-ring mean over V~
+                    float a0, a1, a2;
+                    if (pos) {
+                        const float4 xs = X[s];
+                        a0 = xs.x; a1 = xs.y; a2 = xs.z;
+                    } else {
+                        a0 = Vx[s]; a1 = Vy[s]; a2 = Vz[s];
+                    }
+                    const int b = M.snbr_off[s], e = M.snbr_off[s + 1];
+                    float mx = 0.f, my = 0.f, mz = 0.f;
+                    for (int q = b; q < e; ++q) {
+                        const int j = M.snbr[q];
+                        if (pos) {
+                            const float4 xj = X[j];
+                            mx += xj.x;
+                            my += xj.y;
+                            mz += xj.z;
+                        } else {
+                            mx += Vx[j];
+                            my += Vy[j];
+                            mz += Vz[j];
+                        }
+                    }
+                    const float inv = e > b ? 1.0f / float(e - b) : 0.f;
+                    f[3] = e > b ? mx * inv - a0 : 0.f;
+                    f[4] = e > b ? my * inv - a1 : 0.f;
+                    f[5] = e > b ? mz * inv - a2 : 0.f;
+                    if (pos) {
+                        const float4 rs = M.rest_s[s];
+                        f[0] = a0 - rs.x; f[1] = a1 - rs.y; f[2] = a2 - rs.z;
+                        f[6] = a0 - cx; f[7] = a1 - cy; f[8] = a2 - cz;
+                    } else {
+                        f[0] = a0; f[1] = a1; f[2] = a2;
+                    }
+                }
+                // feature columns: pos -> 0-2, 6-8, 12-14; velocity -> 3-5, 9-11 and the padding 15
+#pragma unroll
+                for (int j = 0; j < 9; ++j) {
+                    const int k = pos ? (j / 3) * 6 + j % 3 : (j < 6 ? (j / 3) * 6 + 3 + j % 3 : 15);
+                    if (pos || j < 7) {
+                        const float a = (s < V && k < 15) ? (f[j] - net.in_mean[k]) * net.in_inv_std[k] : 0.f;
+                        *reinterpret_cast<uint16_t*>(At + tile_off(r, k >> 3, 2) + (k & 7) * 2) =
+                            uint16_t(bf16_bits(a));
+                    }
+                }
+            }
+            fence_async_smem();
+            fence_before_sync();
+            __syncthreads();
+            fence_after_sync();
+            // Layer 1: D[0:64) = A (128 x 16) W1^T.
+            if (tid == 0) {
+                umma_bf16(tmem, umma_desc(aA, 128, 256), umma_desc(aW1, 128, 256), idesc64, 0);
+                umma_commit(&mbar);
+            }
+            if (__syncthreads_or(!mbar_wait(&mbar, phase & 1))) {
+                failed = true;
+                break;
+            }
+            ++phase;
+            fence_after_sync();
+            // Epilogue 1: bias, ReLU, BF16 -> hidden tile (each warp: 32 rows x 32 columns).
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int c0 = 32 * chalf + 16 * c;
+                float v[16];
+                tmem_ld16(tmem + tlane + c0, v);
+                uint32_t p[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    p[k] = bf16_bits(fmaxf(v[2 * k] + bias[c0 + 2 * k], 0.f)) |
+                           (bf16_bits(fmaxf(v[2 * k + 1] + bias[c0 + 2 * k + 1], 0.f)) << 16);
+                *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8, 8)) = make_uint4(p[0], p[1], p[2], p[3]);
+                *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8 + 1, 8)) = make_uint4(p[4], p[5], p[6], p[7]);
+            }
+            fence_async_smem();
+            fence_before_sync();
+            __syncthreads();
+            fence_after_sync();
+            // Layer 2: D[64:128) = H1 (128 x 64) W2^T, four K = 16 steps.
+            if (tid == 0) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    umma_bf16(tmem + 64, umma_desc(aH + 256 * j, 128, 1024), umma_desc(aW2 + 256 * j, 128, 1024),
+                              idesc64, j);
+                umma_commit(&mbar);
+            }
+            if (__syncthreads_or(!mbar_wait(&mbar, phase & 1))) {
+                failed = true;
+                break;
+            }
+            ++phase;
+            fence_after_sync();
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int c0 = 32 * chalf + 16 * c;
+                float v[16];
+                tmem_ld16(tmem + tlane + 64 + c0, v);
+                uint32_t p[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    p[k] = bf16_bits(fmaxf(v[2 * k] + bias[64 + c0 + 2 * k], 0.f)) |
+                           (bf16_bits(fmaxf(v[2 * k + 1] + bias[64 + c0 + 2 * k + 1], 0.f)) << 16);
+                *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8, 8)) = make_uint4(p[0], p[1], p[2], p[3]);
+                *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8 + 1, 8)) = make_uint4(p[4], p[5], p[6], p[7]);
+            }
+            fence_async_smem();
+            fence_before_sync();
+            __syncthreads();
+            fence_after_sync();
+            // Layer 3: D[0:16) = H2 (128 x 64) W3^T (rows 3..15 of W3 are zero).
+            if (tid == 0) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    umma_bf16(tmem, umma_desc(aH + 256 * j, 128, 1024), umma_desc(aW3 + 256 * j, 128, 1024), idesc16,
+                              j);
+                umma_commit(&mbar);
+            }
+            if (__syncthreads_or(!mbar_wait(&mbar, phase & 1))) {
+                failed = true;
+                break;
+            }
+            ++phase;
+            fence_after_sync();
+            if (warp < 4) {
+                float v[16];
+                tmem_ld16(tmem + tlane, v);
+                const int s = t * 128 + erow;
+                if (s < V) {
+                    const float y0 = (v[0] + bias[128]) * net.out_std[0] + net.out_mean[0];
+                    const float y1 = (v[1] + bias[129]) * net.out_std[1] + net.out_mean[1];
+                    const float y2 = (v[2] + bias[130]) * net.out_std[2] + net.out_mean[2];
+                    DX[s] = make_float4(y0, y1, y2, 0.f);
+                }
+            }
+            fence_before_sync();
+            __syncthreads();   // the next tile overwrites the input tile and TMEM columns 0..63
+            fence_after_sync();
+        }
+        if (failed) break;
+        // -- corrections of the free vertices (the features above saw none of them)
+        for (int s = tid; s < V; s += SUB) {
+            float4 xi = X[s];
+            if (xi.w > 0.f) {
+                const float4 d = DX[s];
+                xi.x += d.x;
+                xi.y += d.y;
+                xi.z += d.z;
+                X[s] = xi;
+            }
+        }
+        __syncthreads();
+        // -- one iteration, residual check, fallback to the full solve
+        iterate<SUB>(X, M, 1, at_d, at_v, nullptr);
+        const float res = env_residual<SUB>(X, M, &s_resid);
+        if (tid == 0 && C.residual) C.residual[env] = fmaxf(C.residual[env], res);
+        if (!(res <= C.threshold)) {   // a NaN residual also falls back (uniform over the CTA)
+            for (int s = tid; s < V; s += SUB) {
+                const float w = M.rest_s[s].w;
+                const float p0 = Px[s], p1 = Py[s], p2 = Pz[s];
+                X[s] = w > 0.f ? make_float4(__fmaf_rn(h, Vx[s], p0), __fmaf_rn(h, Vy[s], p1),
+                                             __fmaf_rn(h, Vz[s], p2), w)
+                               : make_float4(p0, p1, p2, w);
+            }
+            __syncthreads();
+            iterate<SUB>(X, M, C.n_full, at_d, at_v, lam);
+            ++n_fallback;
+        }
+        // -- collision, velocity update and the next prediction
+        for (int s = tid; s < V; s += SUB) {
+            float4 xi = X[s];
+            const float w = xi.w;
+            if (w > 0.f) {
+                const float dx = xi.x - cx, dy = xi.y - cy, dz = xi.z - cz;
+                const float l2 = dx * dx + dy * dy + dz * dz;
+                if (l2 < rad2) {
+                    const float len = sqrtf(l2);
+                    if (len > 0.f) {
+                        const float f = __fdividef(rad, len);
+                        xi.x = cx + f * dx;
+                        xi.y = cy + f * dy;
+                        xi.z = cz + f * dz;
+                    } else {
+                        xi.x = cx;
+                        xi.y = cy;
+                        xi.z = cz + rad;
+                    }
+                    if (last) {
+                        const int i = M.vert_of[s];
+                        atomicOr(&bits[i >> 5], 1u << (i & 31));
+                    }
+                }
+            }
+            if (last) {
+                X[s] = xi;
+                continue;
+            }
+            float v0 = (xi.x - Px[s]) * inv_h, v1 = (xi.y - Py[s]) * inv_h, v2 = (xi.z - Pz[s]) * inv_h;
+            Px[s] = xi.x;
+            Py[s] = xi.y;
+            Pz[s] = xi.z;
+            if (w > 0.f) {
+                v0 += hgx;
+                v1 += hgy;
+                v2 += hgz;
+                xi.x = __fmaf_rn(h, v0, xi.x);
+                xi.y = __fmaf_rn(h, v1, xi.y);
+                xi.z = __fmaf_rn(h, v2, xi.z);
+            }
+            Vx[s] = v0;
+            Vy[s] = v1;
+            Vz[s] = v2;
+            X[s] = xi;
+        }
+        __syncthreads();
+    }
+    if (failed) {
+        // An MMA chain did not signal completion: wait once more (bounded) for
+        // the commit in flight, free TMEM, flag the env and leave its state.
+        mbar_wait(&mbar, phase & 1);
+        if (tid == 0) atomicOr(&S.err[env], kErrTimeout);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWarmTmemCols)
+                     : "memory");
+    if (failed) return;
+    if (tid == 0 && C.fallbacks && n_fallback) C.fallbacks[env] += n_fallback;
+
+    // Write back x and v = (x - x_prev) / h in vertex order; flag non-finite positions.
+    float* ox = S.x + ed.voff;
+    float* ov = S.v + ed.voff;
+    bool bad = false;
+    for (int i = tid; i < V; i += SUB) {
+        const int s = M.slot_of[i];
+        const float4 xi = X[s];
+        ox[i] = xi.x;
+        ox[stride + i] = xi.y;
+        ox[2 * stride + i] = xi.z;
+        ov[i] = (xi.x - Px[s]) * inv_h;
+        ov[stride + i] = (xi.y - Py[s]) * inv_h;
+        ov[2 * stride + i] = (xi.z - Pz[s]) * inv_h;
+        bad |= !(isfinite(xi.x) && isfinite(xi.y) && isfinite(xi.z));
+    }
+    if (bad) atomicOr(&S.err[env], kErrNonFinite);
+    // Contacts of the last substep (ascending vertex ids), observation, reward, termination.
+    if (warp == 0) {
+        const int nwords = Vp / 32;
+        int base = 0;
+        for (int w0 = 0; w0 < nwords; w0 += 32) {
+            unsigned word = (w0 + lane < nwords) ? bits[w0 + lane] : 0u;
+            const int cnt = __popc(word);
+            int incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int tt = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += tt;
+            }
+            int pos = base + incl - cnt;
+            while (word) {
+                const int bit = __ffs(word) - 1;
+                word &= word - 1;
+                S.contacts[ed.voff + pos++] = (w0 + lane) * 32 + bit;
+            }
+            base += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) S.n_contacts[env] = base;
+    }
+    if (obs) {
+        float* o = obs + (long long)env * S.obs_dim;
+        const int* ids = S.obs_ids + (long long)env * S.n_obs;
+        for (int j = tid; j < S.obs_dim; j += SUB) {
+            float val;
+            if (j < 3) {
+                val = float(s_tool[j]);
+            } else {
+                const int q = (j - 3) / 3, kk = (j - 3) - 3 * q;
+                const float4 xv = X[M.slot_of[ids[q]]];
+                val = kk == 0 ? xv.x : (kk == 1 ? xv.y : xv.z);
+            }
+            o[j] = val;
+        }
+    }
+    if (tid == 0) {
+        const float4 xt = X[M.slot_of[S.target[env]]];
+        const double dx = s_tool[0] - double(xt.x), dy = s_tool[1] - double(xt.y), dz = s_tool[2] - double(xt.z);
+        const double l = sqrt(dx * dx + dy * dy + dz * dz);
+        const int succ = l < S.success_dist;
+        const double R = S.w_l * l + S.w_d * (l - double(S.l_prev[env])) + S.w_s * double(succ);
+        S.l_prev[env] = float(l);
+        const int tt = S.t_step[env] + 1;
+        S.t_step[env] = tt;
+        if (reward) reward[env] = float(R);
+        if (done) done[env] = uint8_t(((S.max_steps > 0 && tt >= S.max_steps) || succ) ? 1 : 0);
+    }
+}
+
+cudaError_t launch_warm_step(const SimDev& S, const MlpDev& net, const SubstepCtl& C, const int* env_list,
+                             int n_list, size_t smem, const float* actions, float* obs, float* reward, uint8_t* done,
+                             cudaStream_t st) {
+    if (n_list <= 0) return cudaSuccess;
+    static size_t configured = 48 * 1024;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(warm_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    warm_step_kernel<<<n_list, kWarmThreads, smem, st>>>(S, net, C, env_list, n_list, actions, obs, reward, done);
     return cudaGetLastError();
 }
 

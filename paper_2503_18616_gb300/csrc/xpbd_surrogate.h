@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "mlp_tc.h"
 #include "xpbd_device.cuh"
 
 namespace ffsrl {
@@ -22,6 +23,7 @@ struct SubstepCtl {
     float* lambda;          // multipliers of the full solve (per env at EnvDev::loff)
     int* fallbacks;         // [n_env] counters (may be null)
     float* residual;        // [n_env] running max of the checked residual (may be null)
+    float4* scratch;        // [stride] corrections of the fused step (slot order per env)
 };
 
 size_t substep_smem_bytes(int Vp, bool resident);
@@ -30,5 +32,15 @@ cudaError_t launch_features(const SimDev& S, const int* env_list, int n_list, bo
                             const float* actions, float4* F, cudaStream_t st);
 cudaError_t launch_substep(const SimDev& S, const SubstepCtl& C, const int* env_list, int n_list, bool resident,
                            size_t smem, cudaStream_t st, float* obs, float* reward, uint8_t* done);
+
+// Fused warm-start step: every substep of the step in one launch, one CTA of
+// kWarmThreads threads per env with the env resident in shared memory (the
+// network on the tensor cores inside the same CTA). C.scratch holds [stride]
+// float4; C.mode, C.last, C.dx and C.target are ignored.
+constexpr int kWarmThreads = 256;
+size_t warm_smem_bytes(int Vp);
+cudaError_t launch_warm_step(const SimDev& S, const MlpDev& net, const SubstepCtl& C, const int* env_list,
+                             int n_list, size_t smem, const float* actions, float* obs, float* reward, uint8_t* done,
+                             cudaStream_t st);
 
 }  // namespace ffsrl

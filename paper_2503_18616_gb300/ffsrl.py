@@ -29,7 +29,8 @@ EXPORTS = ["ffsrl_create", "ffsrl_reset", "ffsrl_step", "ffsrl_step_host", "ffsr
            "ffsrl_destroy", "ffsrl_get_info", "ffsrl_last_error", "ffsrl_get_state",
            "ffsrl_set_state", "ffsrl_get_mesh_table", "ffsrl_get_env_ints", "ffsrl_step_noalloc",
            "ffsrl_set_network", "ffsrl_network_forward", "ffsrl_step_surrogate", "ffsrl_record_step",
-           "ffsrl_get_rows", "ffsrl_get_network", "ffsrl_network_gradient", "ffsrl_train_network"]
+           "ffsrl_get_rows", "ffsrl_get_network", "ffsrl_network_gradient", "ffsrl_train_network",
+           "ffsrl_set_surrogate_envs"]
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
 NET_PARAMS = 64 * 15 + 64 + 64 * 64 + 64 + 3 * 64 + 3   # FFSRL_NET_PARAMS
@@ -60,6 +61,7 @@ class ffsrl_params(ctypes.Structure):
                 ("schedule_flags", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 SCHED_FORCE, SCHED_NO_PERMUTE, SCHED_NO_RING, SCHED_ENVS2, SCHED_ENVS4 = 1, 2, 4, 8, 16
+SCHED_SURROGATE_PIPELINE = 32
 
 
 class ffsrl_info(ctypes.Structure):
@@ -122,6 +124,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.ffsrl_network_gradient.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_float, P, P]
     L.ffsrl_train_network.restype = ctypes.c_int
     L.ffsrl_train_network.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_float, ctypes.c_float, P]
+    L.ffsrl_set_surrogate_envs.restype = ctypes.c_int
+    L.ffsrl_set_surrogate_envs.argtypes = [P, P, ctypes.c_double, I32, P]
     _lib = L
     return L
 
@@ -332,6 +336,19 @@ class Sim:
         _check(self._L.ffsrl_step_surrogate(self._h, _dptr(actions), _dptr(obs), _dptr(reward), _dptr(done),
                                             float(threshold), int(n_full), _dptr(fallbacks), _dptr(residual)))
         return obs, reward, done
+
+    def set_surrogate_envs(self, mask, threshold: float = 1e30, n_full: int = 10, fallbacks=None) -> None:
+        """Mixed rollout: envs with a non-zero mask byte take the warm-start
+        step inside step()/step_host(); mask None switches back to plain."""
+        if mask is None:
+            _check(self._L.ffsrl_set_surrogate_envs(self._h, None, 0.0, 1, None))
+            return
+        m = np.ascontiguousarray(np.asarray(mask).reshape(-1) != 0, dtype=np.uint8)
+        if m.size != self.n_env:
+            raise ValueError("mask needs one byte per env")
+        self._mix_keep = fallbacks
+        _check(self._L.ffsrl_set_surrogate_envs(self._h, _np_ptr(m), float(threshold), int(n_full),
+                                                _dptr(fallbacks)))
 
     def record_step(self, n_full: int, actions=None, features=None, targets=None, residual=None, want=True):
         """Full-solve step; returns (features [S][rows][16], targets [S][rows][4]) unless want=False."""

@@ -67,25 +67,34 @@ def _install(sim, params, norm):
     sim.set_network(params, *norm)
 
 
+def _case_network(case):
+    if case == "zero_no_fallback":
+        params = {k: np.zeros_like(v) for k, v in oracle.mlp_init(0).items()}
+        return params, ZERO_NORM, np.inf
+    if case == "always_fallback":
+        params = oracle.mlp_init(1)
+        return params, (np.zeros(15), np.full(15, 1e-3), np.zeros(3), np.full(3, 1e-5)), -1.0
+    params = oracle.mlp_init(2)
+    rng = np.random.default_rng(3)
+    for k in ("b1", "b2", "b3"):
+        params[k] = rng.normal(0, 0.1, params[k].shape)
+    return params, (np.zeros(15), np.full(15, 2e-3), np.zeros(3), np.full(3, 2e-7)), np.inf
+
+
+@pytest.mark.parametrize("path", ["fused", "pipeline"])
 @pytest.mark.parametrize("case", ["zero_no_fallback", "always_fallback", "random_network"])
-def test_surrogate_step_matches_oracle(case):
+def test_surrogate_step_matches_oracle(case, path):
+    """Both implementations of the surrogate step: the fused kernel (state
+    resident, network on the tensor cores of the same CTA) and the per-substep
+    pipeline (features, network, substep launches)."""
+    from paper_2503_18616_gb300 import ffsrl
     m = grid((9, 9, 5))
     p = inputs.default_params(radius=4e-3)
     n_env, steps = 3, 6
-    sim = make_sim([m], p, n_env, seed=4)
+    flags = ffsrl.SCHED_SURROGATE_PIPELINE if path == "pipeline" else 0
+    sim = make_sim([m], p, n_env, seed=4, schedule_flags=flags)
     oenvs, om = oracle_envs([m], p, n_env, seed=4)
-    if case == "zero_no_fallback":
-        params = {k: np.zeros_like(v) for k, v in oracle.mlp_init(0).items()}
-        norm, thr = ZERO_NORM, np.inf
-    elif case == "always_fallback":
-        params = oracle.mlp_init(1)
-        norm, thr = (np.zeros(15), np.full(15, 1e-3), np.zeros(3), np.full(3, 1e-5)), -1.0
-    else:
-        params = oracle.mlp_init(2)
-        rng = np.random.default_rng(3)
-        for k in ("b1", "b2", "b3"):
-            params[k] = rng.normal(0, 0.1, params[k].shape)
-        norm, thr = (np.zeros(15), np.full(15, 2e-3), np.zeros(3), np.full(3, 2e-7)), np.inf
+    params, norm, thr = _case_network(case)
     _install(sim, params, norm)
     net = oracle.Net.from_params(params, *norm, bf16=True)
     fb = torch.zeros(n_env, dtype=torch.int32, device="cuda")
@@ -111,3 +120,67 @@ def test_surrogate_step_matches_oracle(case):
         assert all(f == steps * p["substeps"] for f in ofb.values())
     else:
         assert all(f == 0 for f in ofb.values())
+
+
+def test_fused_step_on_the_4096_env_mesh_matches_oracle():
+    """The 17 x 17 x 9 block: 21 network tiles per substep with a ragged last
+    tile (2601 = 20 x 128 + 41 rows); random network, no fallback, then a
+    fallback in every substep."""
+    m = grid((17, 17, 9))
+    p = inputs.default_params()
+    n_env, steps = 2, 3
+    for case in ("random_network", "always_fallback"):
+        sim = make_sim([m], p, n_env, seed=6)
+        oenvs, om = oracle_envs([m], p, n_env, seed=6)
+        params, norm, thr = _case_network(case)
+        _install(sim, params, norm)
+        net = oracle.Net.from_params(params, *norm, bf16=True)
+        fb = torch.zeros(n_env, dtype=torch.int32, device="cuda")
+        for _ in range(steps):
+            sim.step_surrogate(thr if np.isfinite(thr) else 1e30, 10, fallbacks=fb)
+        sim.sync()
+        x, _, tool = gpu_positions(sim)
+        V, ext = om[0].V, om[0].extent
+        for e, oe in oenvs.items():
+            f = 0
+            for _ in range(steps):
+                f += oe.step_surrogate(net, thr, 10)[3]
+            assert np.max(np.abs(x[e * V:(e + 1) * V] - oe.state()[0])) <= POS_TOL * ext, (case, e)
+            assert np.array_equal(tool[e], oe.state()[2])
+            assert int(fb[e]) == f
+
+
+def test_mixed_rollout_steps_plain_and_warm_start_envs_together():
+    """ffsrl_set_surrogate_envs: odd envs take the warm-start step inside
+    ffsrl_step, even envs the plain step; every env matches the oracle's
+    corresponding step, and switching the mask off restores plain stepping."""
+    m = grid((9, 9, 5))
+    p = inputs.default_params(radius=4e-3)
+    n_env, steps = 4, 5
+    sim = make_sim([m], p, n_env, seed=8)
+    oenvs, om = oracle_envs([m], p, n_env, seed=8)
+    params, norm, thr = _case_network("random_network")
+    _install(sim, params, norm)
+    net = oracle.Net.from_params(params, *norm, bf16=True)
+    mask = np.array([e % 2 for e in range(n_env)], np.uint8)
+    fb = torch.zeros(n_env, dtype=torch.int32, device="cuda")
+    sim.set_surrogate_envs(mask, threshold=1e30, n_full=10, fallbacks=fb)
+    for _ in range(steps):
+        obs, rew, done = sim.step()
+    sim.set_surrogate_envs(None)
+    obs, rew, done = sim.step()            # one plain step for every env
+    sim.sync()
+    x, _, tool = gpu_positions(sim)
+    V, ext = om[0].V, om[0].extent
+    for e, oe in oenvs.items():
+        for _ in range(steps):
+            if mask[e]:
+                oe.step_surrogate(net, thr, 10)
+            else:
+                oe.step()
+        o_obs, o_rew, _ = oe.step()
+        assert np.max(np.abs(x[e * V:(e + 1) * V] - oe.state()[0])) <= POS_TOL * ext, e
+        assert np.array_equal(tool[e], oe.state()[2])
+        assert abs(float(rew[e]) - o_rew) <= POS_TOL * ext
+        assert np.max(np.abs(obs[e].cpu().numpy() - o_obs)) <= POS_TOL * ext
+    assert int(fb.sum()) == 0
