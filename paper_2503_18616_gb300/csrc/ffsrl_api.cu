@@ -122,6 +122,8 @@ struct ffsrl_sim {
     long long lambda_slots = 0;
     float4* d_feat = nullptr;     // [stride][4] features
     float4* d_dx = nullptr;       // [stride] network corrections
+    float4* d_vpred = nullptr;    // [stride] predicted velocities (fused warm-start step)
+    uint4* d_arows = nullptr;     // network input tiles (fused warm-start step)
     float* d_lambda_full = nullptr;
     // mixed rollout: warm-start envs stepped beside the plain ones
     bool mixed = false;
@@ -234,24 +236,55 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, bool permute, MeshDev& d) {
         FFSRL_CUDA(s->upload(&d_nb, nb.data(), nb.size()));
         d.nbr_off = d_off;
         d.nbr = d_nb;
-        // the same adjacency indexed by shared-memory slot (fused warm-start step)
-        std::vector<int> soff(m.V + 1, 0);
-        std::vector<uint16_t> snb(nb.size());
+        // the same adjacency indexed by shared-memory slot, in 16-byte chunks
+        // of 8 neighbour slots (fused warm-start step)
+        std::vector<int> hdr(m.V);
+        std::vector<uint16_t> chunks;
         std::vector<float4> rs(m.V);
+        int max_deg = 0;
         for (int q = 0; q < m.V; ++q) {
             const int i = sc.vert_of[q];
-            soff[q + 1] = soff[q] + (off[i + 1] - off[i]);
-            for (int k = off[i]; k < off[i + 1]; ++k) snb[soff[q] + (k - off[i])] = sc.slot_of[nb[k]];
+            const int deg = off[i + 1] - off[i];
+            max_deg = std::max(max_deg, deg);
+            hdr[q] = int(chunks.size() / 8) << 5 | std::min(deg, 31);
+            for (int k = off[i]; k < off[i + 1]; ++k) chunks.push_back(sc.slot_of[nb[k]]);
+            while (chunks.size() % 8) chunks.push_back(0);
             rs[q] = rw[i];
         }
-        int* d_soff;
-        uint16_t* d_snb;
+        if (chunks.empty()) chunks.resize(8, 0);
+        int* d_hdr;
+        uint4* d_ch;
         float4* d_rs;
-        FFSRL_CUDA(s->upload(&d_soff, soff.data(), soff.size()));
-        FFSRL_CUDA(s->upload(&d_snb, snb.data(), snb.size()));
+        FFSRL_CUDA(s->upload(&d_hdr, hdr.data(), hdr.size()));
+        FFSRL_CUDA(s->upload(&d_ch, reinterpret_cast<const uint4*>(chunks.data()), chunks.size() / 8));
         FFSRL_CUDA(s->upload(&d_rs, rs.data(), rs.size()));
-        d.snbr_off = d_soff;
-        d.snbr = d_snb;
+        // the records without segment padding (order-free residual sweeps)
+        std::vector<uint2> er;
+        std::vector<uint4> tr;
+        for (int c = 0; c < d.n_seg; ++c) {
+            const int32_t* sg = &sc.segs[4 * c];
+            const unsigned char* base = sc.stream.data() + sg[0];
+            for (int q = 0; q < sg[2]; ++q) {
+                if (c < m.n_ecol) {
+                    uint2 r;
+                    std::memcpy(&r, base + 8 * size_t(q), 8);
+                    er.push_back(r);
+                } else {
+                    uint4 r;
+                    std::memcpy(&r, base + 16 * size_t(q), 16);
+                    tr.push_back(r);
+                }
+            }
+        }
+        uint2* d_er;
+        uint4* d_tr;
+        FFSRL_CUDA(s->upload(&d_er, er.data(), er.size()));
+        FFSRL_CUDA(s->upload(&d_tr, tr.data(), tr.size()));
+        d.erec = d_er;
+        d.trec = d_tr;
+        d.snbr_hdr = d_hdr;
+        d.snbr_ch = d_ch;
+        d.max_deg = max_deg;
         d.rest_s = d_rs;
     }
     // Tool box around the rest bounding box and tool start above the top face.
@@ -882,6 +915,8 @@ int ensure_surrogate_buffers(ffsrl_sim* sim) {
     if (sim->d_feat) return FFSRL_OK;
     FFSRL_CUDA(sim->alloc(&sim->d_feat, 4 * size_t(sim->stride)));
     FFSRL_CUDA(sim->alloc(&sim->d_dx, size_t(sim->stride)));
+    FFSRL_CUDA(sim->alloc(&sim->d_vpred, size_t(sim->stride)));
+    FFSRL_CUDA(sim->alloc(&sim->d_arows, 2 * (size_t(sim->stride) + 128 * size_t(sim->n_env))));
     FFSRL_CUDA(cudaMemset(sim->d_feat, 0, 4 * size_t(sim->stride) * sizeof(float4)));
     FFSRL_CUDA(cudaMemset(sim->d_dx, 0, size_t(sim->stride) * sizeof(float4)));
     FFSRL_CUDA(sim->alloc(&sim->d_lambda_full, size_t(sim->lambda_slots)));
@@ -903,9 +938,12 @@ size_t substep_smem(const ffsrl_sim* s, const LaunchGroup& g, bool& resident) {
 
 // Shared memory of the fused warm-start step for a group (0: does not fit).
 size_t warm_smem(const ffsrl_sim* s, const LaunchGroup& g) {
-    int vp = 0;
-    for (int mi : g.meshes) vp = std::max(vp, s->h_meshes[g.permute ? 1 : 0][mi].Vp);
-    const size_t b = warm_smem_bytes(vp);
+    size_t b = 0;
+    for (int mi : g.meshes) {
+        const MeshDev& d = s->h_meshes[g.permute ? 1 : 0][mi];
+        if (d.max_deg > kWarmMaxDegree) return 0;
+        b = std::max(b, warm_smem_bytes(d.Vp, d.ring_bytes, d.n_seg));
+    }
     return b + 1024 + 256 <= s->max_smem ? b : 0;   // room for the kernel's static shared memory
 }
 
@@ -921,6 +959,8 @@ int launch_warm_groups(ffsrl_sim* sim, cudaStream_t st, bool sublists, const flo
     C.fallbacks = fallbacks;
     C.residual = residual;
     C.scratch = sim->d_dx;
+    C.vpred = sim->d_vpred;
+    C.arows = sim->d_arows;
     for (const LaunchGroup& g : sim->groups) {
         const int n = sublists ? g.n_warm : g.n;
         const size_t smem = warm_smem(sim, g);

@@ -70,6 +70,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     return false;
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(saddr(bar)),
+        "r"(bytes)
+        : "memory");
+}
+// Bulk copy global -> this CTA's shared memory, completion counted on `bar`
+// (dst, src and bytes multiples of 16).
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(saddr(dst)),
+        "l"(src), "r"(bytes), "r"(saddr(bar))
+        : "memory");
+}
+
 // Round-to-nearest-even BF16 bits of a float (finite inputs).
 __device__ __forceinline__ uint32_t bf16_bits(float x) {
     const uint32_t u = __float_as_uint(x);

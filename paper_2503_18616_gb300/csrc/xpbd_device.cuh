@@ -36,9 +36,16 @@ struct MeshDev {
     const int* top;                   // [n_top] top-face vertex ids
     const int* nbr_off;               // [V + 1] 1-ring of each vertex (vertex order, CSR)
     const int* nbr;                   // [2E]
-    const int* snbr_off;              // [V + 1] 1-ring of each slot (slot order, CSR, same neighbour order)
-    const uint16_t* snbr;             // [2E] slots of the neighbours
+    // 1-ring of each slot in slot terms (same neighbour order as nbr): slot s
+    // owns 16-byte chunks of 8 neighbour slots (uint16) from chunk
+    // snbr_hdr[s] >> 5 on; its degree is snbr_hdr[s] & 31 (at most 24).
+    const int* snbr_hdr;              // [V]
+    const uint4* snbr_ch;
     const float4* rest_s;             // [V] rest position and inverse mass (slot order)
+    int max_deg;                      // largest vertex degree
+    int pad2;
+    const uint2* erec;                // [E] edge records of the stream, unpadded, stream order
+    const uint4* trec;                // [T] tet records of the stream, unpadded, stream order
     double box_lo[3], box_hi[3], tool_start[3];
     float min_len2;                   // edges with |x_ab|^2 below this are skipped
     int pad1;

@@ -370,50 +370,118 @@ cudaError_t launch_substep(const SimDev& S, const SubstepCtl& C, const int* env_
 // ---- fused warm-start step ---------------------------------------------------
 //
 // One CTA of 256 threads advances one env through all substeps of a step with
-// its state resident in shared memory, as the plain step kernel does, and runs
-// the warm-start network inside the same CTA on the tensor cores:
-//   per substep: features of every vertex at the predicted state (from the
-//   resident positions and predicted velocities), the network tile by tile
-//   (128 rows per tile, tcgen05.mma into TMEM, BF16 operands), the corrections
-//   added to the free vertices once every tile is done, one constraint
-//   iteration, the residual check with the fallback to the full solve, then
-//   collision, the velocity update and the next prediction.
-// Rows of the network are shared-memory slots. The predicted velocities stay
-// in shared memory (the features need them for the 1-ring means); the
-// substep-start positions live in global memory (slot order, L2-resident) as
-// in the plain kernel; the corrections pass through a global scratch row per
-// slot, because every tile's features must see the uncorrected prediction.
-// The fallback rebuilds the prediction exactly: x~ = fma(h, v~, x_prev) is the
-// same rounded operation that made it.
+// its positions resident in shared memory, as the plain step kernel does, and
+// runs the warm-start network inside the same CTA on the tensor cores. Per
+// substep:
+//   1. features of every row (shared-memory slot) at the predicted state, one
+//      row per thread, normalised, rounded to BF16 and written to global
+//      scratch already in the tensor-core operand layout (4 KB per 128 rows);
+//   2. the network tile by tile: the tile's input copied to shared memory
+//      (fetched into registers during the previous tile), three tcgen05.mma
+//      chains into TMEM with the bias/ReLU/BF16 epilogues in between, the
+//      corrections to global scratch;
+//   3. the corrections added to the free vertices (every tile's features saw
+//      the uncorrected prediction), one constraint iteration with the records
+//      streamed through a TMA double buffer, the residual sweep (order-free,
+//      records from L2), the fallback to the full solve if the residual
+//      exceeds the threshold;
+//   4. collision, the velocity update and the next prediction.
+// Shared memory holds the positions and one region used in turn by the record
+// ring (constraint phases) and by the weight and hidden tiles (network phase),
+// so three CTAs fit on an SM. Predicted velocities and substep-start
+// positions live in global memory in slot order (L1/L2-resident while the CTA
+// runs). The fallback rebuilds the prediction exactly: x~ = fma(h, v~, x_prev)
+// is the same rounded operation that made it.
 namespace {
 
+constexpr int kNetBytes = kMlpWeightBytes + 16384;   // weight tiles + one hidden tile
+
 struct WarmLayout {
-    size_t x, vh, w, h, bias, bits, total;
-    __host__ __device__ explicit WarmLayout(int Vp) {
+    size_t x, u, bias, segs, bits, total;
+    __host__ __device__ WarmLayout(int Vp, int ring_bytes, int n_seg) {
         x = 0;
-        vh = x + size_t(Vp) * 16;
-        w = (vh + size_t(Vp) * 12 + 127) / 128 * 128;
-        h = w + size_t(kMlpWeightBytes);
-        bias = h + 16384;
-        bits = bias + 144 * 4;
+        u = size_t(Vp) * 16;
+        const size_t un = 2 * size_t(ring_bytes) > size_t(kNetBytes) ? 2 * size_t(ring_bytes) : size_t(kNetBytes);
+        bias = u + (un + 127) / 128 * 128;
+        segs = bias + 144 * 4;
+        bits = segs + size_t(n_seg) * 16;
         total = bits + size_t(Vp / 32) * 4;
     }
 };
 
 constexpr uint32_t kWarmTmemCols = 128;
 
+// n_proj ring-buffered projection passes over the constraint records, colour
+// by colour (multipliers carried in lam when n_proj > 1). Copy k of the step's
+// running count goes to stage k & 1; one copy is in flight ahead of the colour
+// being processed. Returns false (uniformly) if a copy did not arrive within
+// the bounded wait.
+__device__ bool ring_sweep(float4* X, const MeshDev& M, const int4* segs, unsigned char* ring, uint64_t* mbar,
+                           uint32_t& k, int n_proj, float at_d, float at_v, float* lam) {
+    using namespace tc;
+    const int st = threadIdx.x;
+    const int n_seg = M.n_seg, n_ecol = M.n_ecol;
+    const int K = n_proj * n_seg;
+    if (K == 0) return true;
+    fence_async_smem();   // generic writes to the region before the copies overwrite it
+    __syncthreads();
+    if (st == 0) {
+        const int4 sg = segs[0];
+        mbar_expect_tx(&mbar[k & 1], uint32_t(sg.y));
+        bulk_copy_g2s(ring + (k & 1) * M.ring_bytes, M.recs + sg.x, uint32_t(sg.y), &mbar[k & 1]);
+    }
+    for (int j = 0; j < K; ++j, ++k) {
+        const int pass = j / n_seg, c = j - pass * n_seg;
+        if (st == 0 && j + 1 < K) {
+            const int cn = c + 1 == n_seg ? 0 : c + 1;
+            const int4 nx = segs[cn];
+            uint64_t* b = &mbar[(k + 1) & 1];
+            mbar_expect_tx(b, uint32_t(nx.y));
+            bulk_copy_g2s(ring + ((k + 1) & 1) * M.ring_bytes, M.recs + nx.x, uint32_t(nx.y), b);
+        }
+        const bool ok = mbar_wait(&mbar[k & 1], (k >> 1) & 1);
+        if (ok) {
+            const int4 sg = segs[c];
+            const unsigned char* base = ring + (k & 1) * M.ring_bytes;
+            const bool carry = lam != nullptr && n_proj > 1;
+            if (c < n_ecol) {
+                const uint2* rec = reinterpret_cast<const uint2*>(base);
+                for (int q = st; q < sg.z; q += kWarmThreads) {
+                    float l = (carry && pass > 0) ? lam[sg.w + q] : 0.f;
+                    project_edge(X, rec[q], at_d, M.min_len2, l);
+                    if (carry) lam[sg.w + q] = l;
+                }
+            } else {
+                const uint4* rec = reinterpret_cast<const uint4*>(base);
+                for (int q = st; q < sg.z; q += kWarmThreads) {
+                    float l = (carry && pass > 0) ? lam[sg.w + q] : 0.f;
+                    project_tet(X, rec[q], at_v, l);
+                    if (carry) lam[sg.w + q] = l;
+                }
+            }
+        }
+        if (__syncthreads_or(!ok)) {
+            // drain the copy that may still be in flight (bounded) before leaving
+            if (st == 0 && j + 1 < K) mbar_wait(&mbar[(k + 1) & 1], ((k + 1) >> 1) & 1);
+            ++k;
+            return false;
+        }
+    }
+    return true;
+}
+
 }  // namespace
 
-size_t warm_smem_bytes(int Vp) { return WarmLayout(Vp).total; }
+size_t warm_smem_bytes(int Vp, int ring_bytes, int n_seg) { return WarmLayout(Vp, ring_bytes, n_seg).total; }
 
-__global__ void __launch_bounds__(kWarmThreads, 2)
+__global__ void __launch_bounds__(kWarmThreads, 3)
     warm_step_kernel(SimDev S, MlpDev net, SubstepCtl C, const int* __restrict__ env_list, int n_list,
                      const float* __restrict__ actions, float* __restrict__ obs, float* __restrict__ reward,
                      uint8_t* __restrict__ done) {
     using namespace tc;
     constexpr int SUB = kWarmThreads;
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar[3];   // [0], [1] record ring; [2] tensor-core completion
     __shared__ uint32_t tmem_slot;
     __shared__ double s_tool[3];
     __shared__ int s_resid;
@@ -421,23 +489,24 @@ __global__ void __launch_bounds__(kWarmThreads, 2)
     const int env = env_list[blockIdx.x];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const EnvDev ed = S.envs[env];
-    const MeshDev M = S.meshes[ed.mesh];
+    const MeshDev& M = S.meshes[ed.mesh];
     const int V = M.V, Vp = M.Vp;
     const long long stride = S.stride;
-    const WarmLayout L(Vp);
+    const WarmLayout L(Vp, M.ring_bytes, M.n_seg);
     float4* X = reinterpret_cast<float4*>(sm + L.x);
-    float* Vx = reinterpret_cast<float*>(sm + L.vh);
-    float* Vy = Vx + Vp;
-    float* Vz = Vy + Vp;
-    unsigned char* Wt = sm + L.w;
-    unsigned char* Ht = sm + L.h;
-    unsigned char* At = Ht;   // the input tile is dead once layer 1 has read it
+    unsigned char* U = sm + L.u;            // record ring, or weight tiles + hidden tile
+    unsigned char* Wt = U;
+    unsigned char* Ht = U + kMlpWeightBytes;
+    unsigned char* At = Ht;                 // the input tile is dead once layer 1 has read it
     float* bias = reinterpret_cast<float*>(sm + L.bias);
+    int4* segs = reinterpret_cast<int4*>(sm + L.segs);
     unsigned* bits = reinterpret_cast<unsigned*>(sm + L.bits);
     float* Px = S.pg + ed.voff;
     float* Py = Px + stride;
     float* Pz = Py + stride;
-    float4* DX = C.scratch + ed.voff;
+    float4* DX = C.scratch + ed.voff;       // corrections, slot order
+    float4* VH = C.vpred + ed.voff;         // predicted velocities, slot order
+    uint4* AR = C.arows + 2 * (ed.voff + 128ll * env);   // network input tiles, 4 KB each
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
@@ -445,12 +514,13 @@ __global__ void __launch_bounds__(kWarmThreads, 2)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    for (int i = tid; i < kMlpWeightBytes / 16; i += SUB)
-        reinterpret_cast<uint4*>(Wt)[i] = reinterpret_cast<const uint4*>(net.wtiles)[i];
     for (int i = tid; i < 144; i += SUB) bias[i] = net.bias[i];
+    for (int c = tid; c < M.n_seg; c += SUB) segs[c] = M.segs[c];
     for (int w = tid; w < Vp / 32; w += SUB) bits[w] = 0u;
     if (tid == 0) {
-        mbar_init(&mbar);
+        mbar_init(&mbar[0]);
+        mbar_init(&mbar[1]);
+        mbar_init(&mbar[2]);
         update_tool(S, M, env, actions, s_tool);
     }
     // Load the state (vertex order in, slot order out) and predict the first substep.
@@ -475,9 +545,7 @@ __global__ void __launch_bounds__(kWarmThreads, 2)
             } else {
                 X[s] = make_float4(x0, x1, x2, w);
             }
-            Vx[s] = v0;
-            Vy[s] = v1;
-            Vz[s] = v2;
+            VH[s] = make_float4(v0, v1, v2, 0.f);
         }
     }
     fence_before_sync();
@@ -487,79 +555,75 @@ __global__ void __launch_bounds__(kWarmThreads, 2)
     const uint32_t idesc64 = umma_idesc_bf16(128, 64), idesc16 = umma_idesc_bf16(128, 16);
     const uint32_t aW1 = saddr(Wt), aW2 = aW1 + 2048, aW3 = aW1 + 10240, aA = saddr(At), aH = saddr(Ht);
     const float cx = float(s_tool[0]), cy = float(s_tool[1]), cz = float(s_tool[2]);
-    const float rad = S.radius, rad2 = rad * rad;
-    const float at_d = ed.alpha_d, at_v = S.alpha_v;
-    float* lam = C.lambda ? C.lambda + ed.loff : nullptr;
     const int n_tiles = (V + 127) / 128;
     // TMEM lanes of this warp (a warp reaches the 32 lanes of its quarter) and
     // the column half it reads back in the hidden-layer epilogues.
     const int q4 = warp & 3, chalf = warp >> 2;
     const uint32_t tlane = uint32_t(32 * q4) << 16;
     const int erow = 32 * q4 + lane;
-    uint32_t phase = 0;
+    uint32_t phase = 0;   // tensor-core completions so far
+    uint32_t k = 0;       // record copies so far
     bool failed = false;
     int n_fallback = 0;
 
     for (int sub = 0; sub < S.substeps && !failed; ++sub) {
         const bool last = sub == S.substeps - 1;
         if (tid == 0) s_resid = 0;
-        // -- features and network, one 128-row tile at a time
-        for (int t = 0; t < n_tiles; ++t) {
-            {
-                // Row r of the tile: threads 0..127 the position features
-                // (displacement from rest, 1-ring mean offset, offset from the
-                // tool), threads 128..255 the velocity features (velocity,
-                // 1-ring mean offset) and the zero padding column.
-                const int r = tid & 127, s = t * 128 + r;
-                const bool pos = tid < 128;
-                float f[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                if (s < V) {
-                    // pos: x and its 1-ring mean over X; else v and its 1-ring mean over V~
-                    float a0, a1, a2;
-                    if (pos) {
-                        const float4 xs = X[s];
-                        a0 = xs.x; a1 = xs.y; a2 = xs.z;
-                    } else {
-                        a0 = Vx[s]; a1 = Vy[s]; a2 = Vz[s];
-                    }
-                    const int b = M.snbr_off[s], e = M.snbr_off[s + 1];
-                    float mx = 0.f, my = 0.f, mz = 0.f;
-                    for (int q = b; q < e; ++q) {
-                        const int j = M.snbr[q];
-                        if (pos) {
-                            const float4 xj = X[j];
-                            mx += xj.x;
-                            my += xj.y;
-                            mz += xj.z;
-                        } else {
-                            mx += Vx[j];
-                            my += Vy[j];
-                            mz += Vz[j];
-                        }
-                    }
-                    const float inv = e > b ? 1.0f / float(e - b) : 0.f;
-                    f[3] = e > b ? mx * inv - a0 : 0.f;
-                    f[4] = e > b ? my * inv - a1 : 0.f;
-                    f[5] = e > b ? mz * inv - a2 : 0.f;
-                    if (pos) {
-                        const float4 rs = M.rest_s[s];
-                        f[0] = a0 - rs.x; f[1] = a1 - rs.y; f[2] = a2 - rs.z;
-                        f[6] = a0 - cx; f[7] = a1 - cy; f[8] = a2 - cz;
-                    } else {
-                        f[0] = a0; f[1] = a1; f[2] = a2;
-                    }
-                }
-                // feature columns: pos -> 0-2, 6-8, 12-14; velocity -> 3-5, 9-11 and the padding 15
+        // -- the weight tiles into the shared region (the ring used it last)
+        for (int i = tid; i < kMlpWeightBytes / 16; i += SUB)
+            reinterpret_cast<uint4*>(Wt)[i] = reinterpret_cast<const uint4*>(net.wtiles)[i];
+        // -- features of every row at the predicted state, normalised and
+        //    rounded to BF16, written as the network's input tiles (the
+        //    tensor-core operand layout) to global scratch: one row per thread
+        for (int s = tid; s < n_tiles * 128; s += SUB) {
+            float f[16];
 #pragma unroll
-                for (int j = 0; j < 9; ++j) {
-                    const int k = pos ? (j / 3) * 6 + j % 3 : (j < 6 ? (j / 3) * 6 + 3 + j % 3 : 15);
-                    if (pos || j < 7) {
-                        const float a = (s < V && k < 15) ? (f[j] - net.in_mean[k]) * net.in_inv_std[k] : 0.f;
-                        *reinterpret_cast<uint16_t*>(At + tile_off(r, k >> 3, 2) + (k & 7) * 2) =
-                            uint16_t(bf16_bits(a));
+            for (int q = 0; q < 16; ++q) f[q] = 0.f;
+            if (s < V) {
+                const float4 xs = X[s];
+                const float4 vs = VH[s];
+                const int hd = M.snbr_hdr[s], deg = hd & 31;
+                const uint4* ch = M.snbr_ch + (hd >> 5);
+                const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+                const uint4 c0 = ch[0], c1 = deg > 8 ? ch[1] : zero, c2 = deg > 16 ? ch[2] : zero;
+                const uint32_t w[12] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y, c2.z, c2.w};
+                float m0 = 0.f, m1 = 0.f, m2 = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f;
+#pragma unroll
+                for (int q = 0; q < kWarmMaxDegree; ++q) {
+                    if (q < deg) {
+                        const int j = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFF;
+                        const float4 xj = X[j];
+                        const float4 vj = VH[j];
+                        m0 += xj.x; m1 += xj.y; m2 += xj.z;
+                        n0 += vj.x; n1 += vj.y; n2 += vj.z;
                     }
                 }
+                const float4 rs = M.rest_s[s];
+                f[0] = xs.x - rs.x; f[1] = xs.y - rs.y; f[2] = xs.z - rs.z;
+                f[3] = vs.x; f[4] = vs.y; f[5] = vs.z;
+                if (deg > 0) {
+                    const float inv = 1.0f / float(deg);
+                    f[6] = m0 * inv - xs.x; f[7] = m1 * inv - xs.y; f[8] = m2 * inv - xs.z;
+                    f[9] = n0 * inv - vs.x; f[10] = n1 * inv - vs.y; f[11] = n2 * inv - vs.z;
+                }
+                f[12] = xs.x - cx; f[13] = xs.y - cy; f[14] = xs.z - cz;
+#pragma unroll
+                for (int q = 0; q < 15; ++q) f[q] = (f[q] - net.in_mean[q]) * net.in_inv_std[q];
             }
+            uint32_t pk[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) pk[q] = bf16_bits(f[2 * q]) | (bf16_bits(f[2 * q + 1]) << 16);
+            unsigned char* tile = reinterpret_cast<unsigned char*>(AR) + size_t(s >> 7) * 4096;
+            *reinterpret_cast<uint4*>(tile + tile_off(s & 127, 0, 2)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            *reinterpret_cast<uint4*>(tile + tile_off(s & 127, 1, 2)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+        __syncthreads();
+        // -- the network, one 128-row tile at a time (the next tile's input
+        //    is fetched into registers while the current tile runs)
+        uint4 a_next = AR[tid];
+        for (int t = 0; t < n_tiles; ++t) {
+            reinterpret_cast<uint4*>(At)[tid] = a_next;
+            if (t + 1 < n_tiles) a_next = AR[(t + 1) * 256 + tid];
             fence_async_smem();
             fence_before_sync();
             __syncthreads();
@@ -567,9 +631,9 @@ __global__ void __launch_bounds__(kWarmThreads, 2)
             // Layer 1: D[0:64) = A (128 x 16) W1^T.
             if (tid == 0) {
                 umma_bf16(tmem, umma_desc(aA, 128, 256), umma_desc(aW1, 128, 256), idesc64, 0);
-                umma_commit(&mbar);
+                umma_commit(&mbar[2]);
             }
-            if (__syncthreads_or(!mbar_wait(&mbar, phase & 1))) {
+            if (__syncthreads_or(!mbar_wait(&mbar[2], phase & 1))) {
                 failed = true;
                 break;
             }
@@ -581,13 +645,14 @@ __global__ void __launch_bounds__(kWarmThreads, 2)
                 const int c0 = 32 * chalf + 16 * c;
                 float v[16];
                 tmem_ld16(tmem + tlane + c0, v);
-                uint32_t p[8];
+                uint32_t pk[8];
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    p[k] = bf16_bits(fmaxf(v[2 * k] + bias[c0 + 2 * k], 0.f)) |
-                           (bf16_bits(fmaxf(v[2 * k + 1] + bias[c0 + 2 * k + 1], 0.f)) << 16);
-                *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8, 8)) = make_uint4(p[0], p[1], p[2], p[3]);
-                *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8 + 1, 8)) = make_uint4(p[4], p[5], p[6], p[7]);
+                for (int q = 0; q < 8; ++q)
+                    pk[q] = bf16_bits(fmaxf(v[2 * q] + bias[c0 + 2 * q], 0.f)) |
+                            (bf16_bits(fmaxf(v[2 * q + 1] + bias[c0 + 2 * q + 1], 0.f)) << 16);
+                *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8, 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8 + 1, 8)) =
+                    make_uint4(pk[4], pk[5], pk[6], pk[7]);
             }
             fence_async_smem();
             fence_before_sync();
@@ -599,9 +664,9 @@ __global__ void __launch_bounds__(kWarmThreads, 2)
                 for (int j = 0; j < 4; ++j)
                     umma_bf16(tmem + 64, umma_desc(aH + 256 * j, 128, 1024), umma_desc(aW2 + 256 * j, 128, 1024),
                               idesc64, j);
-                umma_commit(&mbar);
+                umma_commit(&mbar[2]);
             }
-            if (__syncthreads_or(!mbar_wait(&mbar, phase & 1))) {
+            if (__syncthreads_or(!mbar_wait(&mbar[2], phase & 1))) {
                 failed = true;
                 break;
             }
@@ -612,13 +677,14 @@ __global__ void __launch_bounds__(kWarmThreads, 2)
                 const int c0 = 32 * chalf + 16 * c;
                 float v[16];
                 tmem_ld16(tmem + tlane + 64 + c0, v);
-                uint32_t p[8];
+                uint32_t pk[8];
 #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    p[k] = bf16_bits(fmaxf(v[2 * k] + bias[64 + c0 + 2 * k], 0.f)) |
-                           (bf16_bits(fmaxf(v[2 * k + 1] + bias[64 + c0 + 2 * k + 1], 0.f)) << 16);
-                *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8, 8)) = make_uint4(p[0], p[1], p[2], p[3]);
-                *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8 + 1, 8)) = make_uint4(p[4], p[5], p[6], p[7]);
+                for (int q = 0; q < 8; ++q)
+                    pk[q] = bf16_bits(fmaxf(v[2 * q] + bias[64 + c0 + 2 * q], 0.f)) |
+                            (bf16_bits(fmaxf(v[2 * q + 1] + bias[64 + c0 + 2 * q + 1], 0.f)) << 16);
+                *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8, 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8 + 1, 8)) =
+                    make_uint4(pk[4], pk[5], pk[6], pk[7]);
             }
             fence_async_smem();
             fence_before_sync();
@@ -630,9 +696,9 @@ __global__ void __launch_bounds__(kWarmThreads, 2)
                 for (int j = 0; j < 4; ++j)
                     umma_bf16(tmem, umma_desc(aH + 256 * j, 128, 1024), umma_desc(aW3 + 256 * j, 128, 1024), idesc16,
                               j);
-                umma_commit(&mbar);
+                umma_commit(&mbar[2]);
             }
-            if (__syncthreads_or(!mbar_wait(&mbar, phase & 1))) {
+            if (__syncthreads_or(!mbar_wait(&mbar[2], phase & 1))) {
                 failed = true;
                 break;
             }
@@ -665,75 +731,111 @@ __global__ void __launch_bounds__(kWarmThreads, 2)
                 X[s] = xi;
             }
         }
+        // -- one iteration and the residual sweep, then the fallback to the full solve
+        float rmax = 0.f;
+        if (!ring_sweep(X, M, segs, U, mbar, k, 1, ed.alpha_d, S.alpha_v, nullptr)) {
+            failed = true;
+            break;
+        }
+        // residual sweep: it only reads positions, so it needs neither the
+        // colour order nor barriers; the unpadded record lists come from L2
+        {
+            const uint2* er = M.erec;
+            const uint4* tr = M.trec;
+#pragma unroll 4
+            for (int q = tid; q < M.E; q += SUB) rmax = fmaxf(rmax, edge_violation(X, __ldg(er + q)));
+#pragma unroll 4
+            for (int q = tid; q < M.T; q += SUB) rmax = fmaxf(rmax, tet_violation(X, __ldg(tr + q)));
+        }
+        // non-negative floats order like their bit patterns; NaN maps above +inf
+        atomicMax(&s_resid, isnan(rmax) ? 0x7f800001 : __float_as_int(rmax));
         __syncthreads();
-        // -- one iteration, residual check, fallback to the full solve
-        iterate<SUB>(X, M, 1, at_d, at_v, nullptr);
-        const float res = env_residual<SUB>(X, M, &s_resid);
+        const float res = __int_as_float(s_resid);
         if (tid == 0 && C.residual) C.residual[env] = fmaxf(C.residual[env], res);
         if (!(res <= C.threshold)) {   // a NaN residual also falls back (uniform over the CTA)
             for (int s = tid; s < V; s += SUB) {
-                const float w = M.rest_s[s].w;
+                const float w = X[s].w;
+                const float4 vh = VH[s];
                 const float p0 = Px[s], p1 = Py[s], p2 = Pz[s];
-                X[s] = w > 0.f ? make_float4(__fmaf_rn(h, Vx[s], p0), __fmaf_rn(h, Vy[s], p1),
-                                             __fmaf_rn(h, Vz[s], p2), w)
+                X[s] = w > 0.f ? make_float4(__fmaf_rn(h, vh.x, p0), __fmaf_rn(h, vh.y, p1), __fmaf_rn(h, vh.z, p2), w)
                                : make_float4(p0, p1, p2, w);
             }
-            __syncthreads();
-            iterate<SUB>(X, M, C.n_full, at_d, at_v, lam);
+            if (!ring_sweep(X, M, segs, U, mbar, k, C.n_full, ed.alpha_d, S.alpha_v,
+                            C.lambda ? C.lambda + ed.loff : nullptr)) {
+                failed = true;
+                break;
+            }
             ++n_fallback;
         }
-        // -- collision, velocity update and the next prediction
-        for (int s = tid; s < V; s += SUB) {
-            float4 xi = X[s];
-            const float w = xi.w;
-            if (w > 0.f) {
-                const float dx = xi.x - cx, dy = xi.y - cy, dz = xi.z - cz;
-                const float l2 = dx * dx + dy * dy + dz * dz;
-                if (l2 < rad2) {
-                    const float len = sqrtf(l2);
-                    if (len > 0.f) {
-                        const float f = __fdividef(rad, len);
-                        xi.x = cx + f * dx;
-                        xi.y = cy + f * dy;
-                        xi.z = cz + f * dz;
-                    } else {
-                        xi.x = cx;
-                        xi.y = cy;
-                        xi.z = cz + rad;
-                    }
-                    if (last) {
-                        const int i = M.vert_of[s];
-                        atomicOr(&bits[i >> 5], 1u << (i & 31));
-                    }
+        // -- collision, velocity update and the next prediction (two vertices
+        //    per thread and trip, their global loads issued together)
+        const float rad = S.radius, rad2 = rad * rad;
+        for (int s0 = tid; s0 < V; s0 += 2 * SUB) {
+            float4 xv[2];
+            float p0[2], p1[2], p2[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int s = s0 + u * SUB;
+                if (s < V) {
+                    xv[u] = X[s];
+                    p0[u] = Px[s];
+                    p1[u] = Py[s];
+                    p2[u] = Pz[s];
                 }
             }
-            if (last) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int s = s0 + u * SUB;
+                if (s >= V) continue;
+                float4 xi = xv[u];
+                const float w = xi.w;
+                if (w > 0.f) {
+                    const float dx = xi.x - cx, dy = xi.y - cy, dz = xi.z - cz;
+                    const float l2 = dx * dx + dy * dy + dz * dz;
+                    if (l2 < rad2) {
+                        const float len = sqrtf(l2);
+                        if (len > 0.f) {
+                            const float f = __fdividef(rad, len);
+                            xi.x = cx + f * dx;
+                            xi.y = cy + f * dy;
+                            xi.z = cz + f * dz;
+                        } else {
+                            xi.x = cx;
+                            xi.y = cy;
+                            xi.z = cz + rad;
+                        }
+                        if (last) {
+                            const int i = M.vert_of[s];
+                            atomicOr(&bits[i >> 5], 1u << (i & 31));
+                        }
+                    }
+                }
+                if (last) {
+                    X[s] = xi;
+                    continue;
+                }
+                float v0 = (xi.x - p0[u]) * inv_h, v1 = (xi.y - p1[u]) * inv_h, v2 = (xi.z - p2[u]) * inv_h;
+                Px[s] = xi.x;
+                Py[s] = xi.y;
+                Pz[s] = xi.z;
+                if (w > 0.f) {
+                    v0 += hgx;
+                    v1 += hgy;
+                    v2 += hgz;
+                    xi.x = __fmaf_rn(h, v0, xi.x);
+                    xi.y = __fmaf_rn(h, v1, xi.y);
+                    xi.z = __fmaf_rn(h, v2, xi.z);
+                }
+                VH[s] = make_float4(v0, v1, v2, 0.f);
                 X[s] = xi;
-                continue;
             }
-            float v0 = (xi.x - Px[s]) * inv_h, v1 = (xi.y - Py[s]) * inv_h, v2 = (xi.z - Pz[s]) * inv_h;
-            Px[s] = xi.x;
-            Py[s] = xi.y;
-            Pz[s] = xi.z;
-            if (w > 0.f) {
-                v0 += hgx;
-                v1 += hgy;
-                v2 += hgz;
-                xi.x = __fmaf_rn(h, v0, xi.x);
-                xi.y = __fmaf_rn(h, v1, xi.y);
-                xi.z = __fmaf_rn(h, v2, xi.z);
-            }
-            Vx[s] = v0;
-            Vy[s] = v1;
-            Vz[s] = v2;
-            X[s] = xi;
         }
         __syncthreads();
     }
     if (failed) {
-        // An MMA chain did not signal completion: wait once more (bounded) for
-        // the commit in flight, free TMEM, flag the env and leave its state.
-        mbar_wait(&mbar, phase & 1);
+        // A bounded wait gave up: let the tensor-core commit in flight land
+        // (bounded), free TMEM, flag the env and leave its state.
+        mbar_wait(&mbar[2], phase & 1);
         if (tid == 0) atomicOr(&S.err[env], kErrTimeout);
     }
     fence_before_sync();

@@ -24,6 +24,8 @@ struct SubstepCtl {
     int* fallbacks;         // [n_env] counters (may be null)
     float* residual;        // [n_env] running max of the checked residual (may be null)
     float4* scratch;        // [stride] corrections of the fused step (slot order per env)
+    float4* vpred;          // [stride] predicted velocities of the fused step (slot order per env)
+    uint4* arows;           // [2 (stride + 128 n_env)] network input tiles of the fused step
 };
 
 size_t substep_smem_bytes(int Vp, bool resident);
@@ -35,10 +37,13 @@ cudaError_t launch_substep(const SimDev& S, const SubstepCtl& C, const int* env_
 
 // Fused warm-start step: every substep of the step in one launch, one CTA of
 // kWarmThreads threads per env with the env resident in shared memory (the
-// network on the tensor cores inside the same CTA). C.scratch holds [stride]
-// float4; C.mode, C.last, C.dx and C.target are ignored.
+// network on the tensor cores inside the same CTA). C.scratch and C.vpred hold
+// [stride] float4 each, C.arows 32 bytes per row plus 4 KB per env (env e's
+// tiles start at row voff_e + 128 e); C.mode, C.last, C.dx and C.target are
+// ignored.
 constexpr int kWarmThreads = 256;
-size_t warm_smem_bytes(int Vp);
+constexpr int kWarmMaxDegree = 24;   // 1-ring size the fused kernel gathers (three index chunks)
+size_t warm_smem_bytes(int Vp, int ring_bytes, int n_seg);
 cudaError_t launch_warm_step(const SimDev& S, const MlpDev& net, const SubstepCtl& C, const int* env_list,
                              int n_list, size_t smem, const float* actions, float* obs, float* reward, uint8_t* done,
                              cudaStream_t st);
