@@ -111,6 +111,21 @@ def smem_bytes_per_env_step(V, E, T, params):
     return s * (it * (E * SMEM_EDGE + T * SMEM_TET) + V * SMEM_VERT)
 
 
+# Shared-memory bytes of one warm-start substep beyond the plain iteration:
+# residual sweep reads (2 / 4 float4 per edge / tet), 1-ring feature gathers
+# (16 B per vertex and per edge end), network operands per row (input tile
+# store + tensor-core read 32 + 32 B, two hidden tiles stored and read 4 x 128 B,
+# weight tiles 12 KB per 128 rows = 96 B), the correction pass (16 B read +
+# 16 B write per vertex).
+SMEM_RES_EDGE, SMEM_RES_TET, SMEM_FEAT, SMEM_NET_ROW, SMEM_CORR = 32, 64, 16, 672, 32
+
+
+def smem_bytes_per_warm_env_step(V, E, T, params):
+    s = params["substeps"]
+    return s * (E * (SMEM_EDGE + SMEM_RES_EDGE) + T * (SMEM_TET + SMEM_RES_TET) + (V + 2 * E) * SMEM_FEAT
+                + V * (SMEM_NET_ROW + SMEM_CORR + SMEM_VERT))
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -417,6 +432,80 @@ def run_warmstart(args):
     return line
 
 
+def setup_mixed(args, sim, batch, seed):
+    """Mixed rollout: trains the warm-start network (untimed, on its own
+    512-env sim), installs it, sets the residual threshold to twice the median
+    residual the full solve itself leaves (the configured 1e-4 sits below that
+    median, so it would send every substep to the fallback), and switches the
+    odd envs to the warm-start step."""
+    import numpy as np
+    import torch
+    from paper_2503_18616_gb300 import ffsrl, inputs, surrogate
+    w = inputs.WORKLOADS[args.workload]
+    tsim = ffsrl.Sim(batch.meshes, batch.params, w["train_envs"])
+    tr = surrogate.train(tsim, batch.meshes, n_full=w["n_full"], env_substeps=w["train_env_substeps"], seed=seed)
+    tsim.close()
+    sim.set_network(tr["params"], *tr["norm"])
+    sim.reset(seed + 1)
+    rf = torch.zeros(sim.n_env, device="cuda")
+    for _ in range(10):
+        sim.record_step(w["n_full"], residual=rf, want=False)
+    thr = 2.0 * float(np.median(rf.cpu().numpy()))
+    mask = (np.arange(sim.n_env) % 2).astype(np.uint8)
+    fb = torch.zeros(sim.n_env, dtype=torch.int32, device="cuda")
+    sim.set_surrogate_envs(mask, thr, w["n_full"], fb)
+    return {"params": tr["params"], "norm": tr["norm"], "threshold": thr, "n_full": w["n_full"], "fallbacks": fb,
+            "mask": mask, "training": {"seconds": tr["seconds"], "env_substeps": tr["env_substeps"],
+                                       "adam_steps": tr["adam_steps"], "loss_first": tr["losses"][0],
+                                       "loss_last": tr["losses"][-1]}}
+
+
+def mixed_accuracy(batch, sim, mixed, seed, seconds, max_steps):
+    """FP64 oracle on env 0 (plain step) and env 1 (warm-start step with the
+    same BF16 network and threshold) from the same reset; returns the CPU rate
+    and the position errors of the GPU replay."""
+    import numpy as np
+    import oracle
+    om = oracle.Mesh(*batch.meshes[0])
+    net = oracle.Net.from_params(mixed["params"], *mixed["norm"], bf16=True)
+    oes = []
+    for e in (0, 1):
+        oe = oracle.Env(om, batch.env_params(e))
+        oe.reset(seed, e)
+        oes.append(oe)
+
+    def advance(n):
+        fb1 = 0
+        for _ in range(n):
+            oes[0].step()
+            fb1 += oes[1].step_surrogate(net, mixed["threshold"], mixed["n_full"])[3]
+        return fb1
+
+    t0 = time.perf_counter()
+    advance(1)
+    per = time.perf_counter() - t0
+    n = max(5, min(max_steps, int(seconds / per)))
+    for e, oe in zip((0, 1), oes):
+        oe.reset(seed, e)
+    t0 = time.perf_counter()
+    ofb = advance(n)
+    dt = time.perf_counter() - t0
+    sim.reset(seed)
+    mixed["fallbacks"].zero_()
+    for _ in range(n):
+        sim.step_into(None, None, None, None)
+    x, _, _ = sim.get_state()
+    x = x.cpu().numpy().astype(np.float64)
+    V = om.V
+    errs = [float(np.max(np.abs(x[e * V:(e + 1) * V] - oes[e].state()[0])) / om.extent) for e in (0, 1)]
+    acc = {"max_pos_err_over_extent": max(errs), "per_env": errs, "envs": [0, 1], "steps": n,
+           "kinds": ["plain", "warm-start"], "tolerance": POS_TOL, "within_tolerance": max(errs) <= POS_TOL,
+           "warm_env_fallbacks": {"gpu": int(mixed["fallbacks"][1].item()), "oracle": int(ofb)}}
+    cpu = {"value": 2 * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"env 0 (plain) and env 1 (warm-start) x {n} steps, FP64 oracle, 1 host thread, {dt:.1f} s"}
+    return acc, cpu
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -448,6 +537,7 @@ def run_ours(args):
     sim = ffsrl.Sim(batch.meshes, params, n_env, env_mesh=batch.env_mesh, env_compliance=batch.env_alpha,
                     block_threads=block, schedule_flags=flags)
     seed = sharding.rank_seed(args.seed, rank)   # each rank owns its own env shard
+    mixed = setup_mixed(args, sim, batch, seed) if inputs.WORKLOADS[args.workload].get("mixed") else None
     sim.reset(seed)
     stream = sim.stream
 
@@ -463,6 +553,8 @@ def run_ours(args):
         sim.step_into(None, obs, rew, done)
     torch.cuda.synchronize()
     sim.sync()
+    if mixed is not None:
+        mixed["fallbacks"].zero_()
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -483,6 +575,10 @@ def run_ours(args):
     latency = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                "max_ms": float(lat.max()), "unit": "ms per step (all envs)"}
     sim.sync()
+    fallback_rate = None
+    if mixed is not None:
+        n_warm = int(mixed["mask"].sum())
+        fallback_rate = float(mixed["fallbacks"].sum().item()) / (n_warm * args.steps * params["substeps"])
     t_ms = sharding.max_over_ranks(t_ms, dist, "cuda")
     value = sharding.throughput(n_env, world, args.steps, t_ms / 1e3)
 
@@ -528,13 +624,25 @@ def run_ours(args):
                             "frac": hbm_bytes / sec / 1e9 / hbm_peak, "algorithmic_bytes_per_launch": hbm_bytes,
                             "peak_source": peak_src}}
         V_total = sum(c[0] for c in counts)
+        if mixed is not None:
+            V, E, T = counts[0]
+            n_warm = int(mixed["mask"].sum())
+            b_mix = (n_env - n_warm) * smem_bytes_per_env_step(V, E, T, params) + \
+                n_warm * smem_bytes_per_warm_env_step(V, E, T, params)
+            roofline = {"bound": "smem", "achieved": b_mix / sec / 1e9, "peak": smem_peak, "unit": "GB/s",
+                        "frac": b_mix / sec / 1e9 / smem_peak, "traffic": None,
+                        "kernel": "xpbd_step_kernel (even envs) and warm_step_kernel (odd envs) on two streams",
+                        "peak_source": roofline["peak_source"], "algorithmic_bytes_per_launch": b_mix,
+                        "hbm": roofline["hbm"]}
 
         # Accuracy and CPU baseline: the FP64 oracle advances two sampled envs
         # for a bounded number of steps on one host thread; the GPU replays the
         # same envs from the same reset and the positions are compared.
         cpu = None
         acc = None
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and mixed is not None:
+            acc, cpu = mixed_accuracy(batch, sim, mixed, seed, args.cpu_seconds, max(args.steps, 50))
+        elif world == 1 and not args.no_cpu_baseline:
             # the first and last env, or the smallest and the largest of an uneven batch
             if single:
                 sample_envs = (0, n_env - 1)
@@ -580,7 +688,13 @@ def run_ours(args):
                                         "tma_ring_envs": sim.ring_envs,
                                         "resident_envs": sim.resident_envs, "launch_groups": sim.n_groups}},
                 "roofline": roofline, "cpu_baseline": cpu, "accuracy": acc, "e2e": e2e, "latency": latency,
-                "gpu_launches": args.steps * sim.n_groups, "clocks": clk}
+                "gpu_launches": args.steps * (sim.n_groups + (1 if mixed is not None else 0)), "clocks": clk}
+        if mixed is not None:
+            line["dtype"] = "f32+bf16"
+            line["mixed"] = {"warm_start_envs": "odd env ids", "n_warm_start": int(mixed["mask"].sum()),
+                             "threshold": mixed["threshold"], "threshold_rule": "2 x median full-solve residual",
+                             "n_full": mixed["n_full"], "fallback_rate": fallback_rate,
+                             "training": mixed["training"]}
         print(json.dumps(line), flush=True)
     sim.close()
     if dist is not None:
