@@ -39,7 +39,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     cc = nvcc()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "ffsrl.h"))
-    flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
+    flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3", "-Xcompiler", "-pthread",
              "--expt-relaxed-constexpr", "-I", os.path.join(os.path.dirname(HERE), "include")] + ARCH
     if verbose:
         flags += ["-Xptxas", "-v"]
@@ -61,7 +61,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         objs = list(ex.map(compile_one, SOURCES))
     if force or _stale(LIB, objs):
         tmp = LIB + f".{os.getpid()}.tmp"
-        cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart"]
+        cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-lcudart", "-Xcompiler", "-pthread"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

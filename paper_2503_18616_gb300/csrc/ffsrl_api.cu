@@ -1,6 +1,7 @@
 // C ABI of the batched XPBD simulator: creation, reset, step, state access,
 // plus the launch planner and autotuner. Contracts are in include/ffsrl.h.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -8,6 +9,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -187,10 +189,8 @@ int check_params(const ffsrl_params& p) {
 }
 
 // Upload one mesh's schedule variant and fill its device descriptor.
-int upload_mesh(ffsrl_sim* s, const HostMesh& m, bool permute, MeshDev& d) {
+int upload_mesh(ffsrl_sim* s, const HostMesh& m, const Schedule& sc, MeshDev& d) {
     const ffsrl_params& p = s->params;
-    Schedule sc;
-    build_schedule(m, 0x5EEDull + uint64_t(m.V), permute, sc);
     d = MeshDev{};
     d.V = m.V;
     d.Vp = round_up(m.V, 32);
@@ -463,10 +463,35 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
     FFSRL_CUDA(s->alloc(&s->d_net_err, 1));
     FFSRL_CUDA(cudaMemset(s->d_net_err, 0, sizeof(int)));
 
+    // Schedules of every mesh in both variants, built on host threads
+    // (largest meshes first; the bank-aware variant searches for a while).
+    const int n_mesh = int(s->meshes.size());
+    std::vector<Schedule> sched(2 * size_t(n_mesh));
+    {
+        std::vector<int> jobs(2 * n_mesh);
+        for (int j = 0; j < 2 * n_mesh; ++j) jobs[j] = j;
+        std::stable_sort(jobs.begin(), jobs.end(), [&](int a, int b) {
+            return s->meshes[a / 2].V + (a & 1) * (1 << 30) > s->meshes[b / 2].V + (b & 1) * (1 << 30);
+        });
+        std::atomic<int> next{0};
+        auto work = [&]() {
+            for (int q; (q = next.fetch_add(1)) < 2 * n_mesh;) {
+                const int j = jobs[q];
+                const HostMesh& m = s->meshes[j / 2];
+                build_schedule(m, 0x5EEDull + uint64_t(m.V), (j & 1) == 1, sched[j]);
+            }
+        };
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        const int n_thr = int(std::min<unsigned>(hw, unsigned(2 * n_mesh)));
+        std::vector<std::thread> pool;
+        for (int t = 1; t < n_thr; ++t) pool.emplace_back(work);
+        work();
+        for (std::thread& t : pool) t.join();
+    }
     for (int v = 0; v < 2; ++v) {
         s->h_meshes[v].resize(s->meshes.size());
-        for (size_t mi = 0; mi < s->meshes.size(); ++mi) {
-            int rc = upload_mesh(s, s->meshes[mi], v == 1, s->h_meshes[v][mi]);
+        for (int mi = 0; mi < n_mesh; ++mi) {
+            int rc = upload_mesh(s, s->meshes[mi], sched[2 * mi + v], s->h_meshes[v][mi]);
             if (rc) return rc;
         }
         FFSRL_CUDA(s->upload(&s->d_meshes[v], s->h_meshes[v].data(), s->h_meshes[v].size()));

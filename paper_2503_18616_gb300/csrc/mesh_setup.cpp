@@ -173,42 +173,193 @@ int build_host_mesh(int V, int T, const double* rest, const double* inv_mass,
 
 namespace {
 
-// Orders the records of one colour in groups of 8 whose slot residues mod 8
-// are pairwise distinct in every vertex position, scanning a bounded window
-// of the remaining records; a group that cannot be completed is filled with
-// the earliest remaining records.
+// Shared-memory bank model behind the schedule: positions are float4 rows, so
+// a 16-byte access of slot s uses bank group s & 7, and the 8 lanes of each
+// quarter-warp of a gather (records 8g .. 8g+7 of a colour, one per lane) are
+// served in one wavefront only if their slots' groups are pairwise distinct.
+// The schedule therefore (1) chooses the slot of every vertex so that, within
+// each colour and vertex position, the bank groups are as evenly used as
+// possible, and (2) orders the records of each colour in groups of 8 with few
+// repeated groups per position. Edge records may also swap their two vertices
+// (the projection is antisymmetric in a and b, bit for bit). None of this
+// changes results: a colour's constraints touch disjoint vertices.
+
+// A record while it is being placed: the slots of its vertices in positions
+// 0 .. ARITY-1 and the constraint index in position 4.
+using Rec = std::array<int, 5>;
+
+// Cost of one group of records: for each vertex position, the largest number
+// of records sharing a bank group (1 = conflict-free).
 template <int ARITY>
-std::vector<int> group_by_banks(const std::vector<std::array<int, ARITY>>& recs) {
+int group_cost(const Rec* g, int n) {
+    int c = 0;
+    for (int k = 0; k < ARITY; ++k) {
+        int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0}, mx = 0;
+        for (int l = 0; l < n; ++l) mx = std::max(mx, ++cnt[g[l][k] & 7]);
+        c += mx;
+    }
+    return c;
+}
+
+// Greedy start: groups of 8 records with pairwise distinct bank groups in
+// every position, scanning a bounded window of the remaining records (edges
+// may be flipped); a group that cannot be completed takes the earliest
+// remaining records.
+template <int ARITY>
+std::vector<Rec> group_greedy(const std::vector<Rec>& recs, bool flip) {
     const int n = int(recs.size());
-    const int window = 512;   // untaken records considered per group
-    std::vector<int> order;
-    order.reserve(n);
+    const int window = 512;
+    std::vector<Rec> out;
+    out.reserve(n);
     std::vector<char> taken(n, 0);
-    int start = 0;            // first untaken record
-    while (int(order.size()) < n) {
+    int start = 0;
+    while (int(out.size()) < n) {
         while (taken[start]) ++start;
         unsigned used[ARITY] = {};
         int got = 0, seen = 0;
         for (int j = start; j < n && got < 8 && seen < window; ++j) {
             if (taken[j]) continue;
             ++seen;
-            const auto& r = recs[j];
-            bool ok = true;
-            for (int k = 0; k < ARITY; ++k) ok &= !(used[k] & (1u << (r[k] & 7)));
+            Rec r = recs[j];
+            auto fits = [&]() {
+                for (int k = 0; k < ARITY; ++k)
+                    if (used[k] & (1u << (r[k] & 7))) return false;
+                return true;
+            };
+            bool ok = fits();
+            if (!ok && flip) {
+                std::swap(r[0], r[1]);
+                ok = fits();
+            }
             if (!ok) continue;
             for (int k = 0; k < ARITY; ++k) used[k] |= 1u << (r[k] & 7);
             taken[j] = 1;
-            order.push_back(j);
+            out.push_back(r);
             ++got;
         }
         for (int j = start; j < n && got < 8; ++j)
             if (!taken[j]) {
                 taken[j] = 1;
-                order.push_back(j);
+                out.push_back(recs[j]);
                 ++got;
             }
     }
-    return order;
+    return out;
+}
+
+// Local search: move a record of a conflicted group into a random other group
+// (swapping with one of its records, an edge record flipped if that helps)
+// whenever the two groups' cost does not rise.
+template <int ARITY>
+void group_improve(std::vector<Rec>& g, std::mt19937_64& rng, long long iters, bool flip) {
+    const int n = int(g.size()), G = (n + 7) / 8;
+    if (G < 2) return;
+    auto size_of = [&](int a) { return std::min(8, n - 8 * a); };
+    std::vector<int> cost(G), bad;
+    for (int a = 0; a < G; ++a) cost[a] = group_cost<ARITY>(&g[8 * a], size_of(a));
+    for (long long it = 0; it < iters; ++it) {
+        if ((it & 1023) == 0) {
+            bad.clear();
+            for (int a = 0; a < G; ++a)
+                if (cost[a] > ARITY) bad.push_back(a);
+            if (bad.empty()) return;
+        }
+        const int a = bad[rng() % bad.size()], b = int(rng() % G);
+        if (a == b) continue;
+        const int i = 8 * a + int(rng() % size_of(a)), j = 8 * b + int(rng() % size_of(b));
+        const int before = cost[a] + cost[b];
+        std::swap(g[i], g[j]);
+        const int cb = group_cost<ARITY>(&g[8 * b], size_of(b));
+        int ca = group_cost<ARITY>(&g[8 * a], size_of(a));
+        bool flipped = false;
+        if (ca + cb > before && flip) {
+            std::swap(g[i][0], g[i][1]);
+            const int cf = group_cost<ARITY>(&g[8 * a], size_of(a));
+            if (cf < ca) {
+                ca = cf;
+                flipped = true;
+            } else {
+                std::swap(g[i][0], g[i][1]);
+            }
+        }
+        if (ca + cb <= before) {
+            cost[a] = ca;
+            cost[b] = cb;
+        } else {
+            if (flipped) std::swap(g[i][0], g[i][1]);
+            std::swap(g[i], g[j]);
+        }
+    }
+}
+
+// Slots of the vertices: a permutation inside each aligned block of 32
+// vertices (so vertex-order passes stay coalesced), chosen by descent on the
+// imbalance of bank groups per (colour, vertex position): sum over keys and
+// groups of the count above ceil(n_key / 8). Moves swap the slots of two
+// vertices of one block in different bank groups; `iters` moves are tried.
+std::vector<int> balanced_slots(const HostMesh& m, std::mt19937_64& rng, long long iters) {
+    const int V = m.V, ne = m.n_ecol, nt = m.n_tcol, K = 2 * ne + 4 * nt;
+    std::vector<int> slot(V);
+    for (int b = 0; b < V; b += 32) {   // a permutation inside each aligned block of 32 vertices
+        const int n = std::min(32, V - b);
+        std::vector<int> p(n);
+        for (int i = 0; i < n; ++i) p[i] = b + i;
+        std::shuffle(p.begin(), p.end(), rng);
+        for (int i = 0; i < n; ++i) slot[b + i] = p[i];
+    }
+    if (V < 2 || iters <= 0) return slot;
+    std::vector<int> off(V + 1, 0), keys;   // CSR: (colour, position) keys of each vertex
+    for (int e = 0; e < m.E; ++e)
+        for (int p = 0; p < 2; ++p) ++off[m.edge[2 * e + p] + 1];
+    for (int t = 0; t < m.T; ++t)
+        for (int p = 0; p < 4; ++p) ++off[m.tet[4 * t + p] + 1];
+    for (int i = 0; i < V; ++i) off[i + 1] += off[i];
+    keys.resize(off[V]);
+    std::vector<int> fill(off.begin(), off.end() - 1), n_key(K, 0);
+    for (int e = 0; e < m.E; ++e)
+        for (int p = 0; p < 2; ++p) {
+            const int k = 2 * m.ecolor[e] + p;
+            keys[fill[m.edge[2 * e + p]]++] = k;
+            ++n_key[k];
+        }
+    for (int t = 0; t < m.T; ++t)
+        for (int p = 0; p < 4; ++p) {
+            const int k = 2 * ne + 4 * m.tcolor[t] + p;
+            keys[fill[m.tet[4 * t + p]]++] = k;
+            ++n_key[k];
+        }
+    std::vector<std::array<int, 8>> h(K);
+    for (auto& a : h) a.fill(0);
+    for (int i = 0; i < V; ++i)
+        for (int q = off[i]; q < off[i + 1]; ++q) ++h[keys[q]][slot[i] & 7];
+    auto pen = [&](int k, int cnt) {
+        const int cap = (n_key[k] + 7) / 8;
+        return cnt > cap ? cnt - cap : 0;
+    };
+    auto move = [&](int x, int from, int to) {   // returns the change of penalty
+        long long d = 0;
+        for (int q = off[x]; q < off[x + 1]; ++q) {
+            const int k = keys[q];
+            d -= pen(k, h[k][from]) + pen(k, h[k][to]);
+            --h[k][from];
+            ++h[k][to];
+            d += pen(k, h[k][from]) + pen(k, h[k][to]);
+        }
+        return d;
+    };
+    for (long long it = 0; it < iters; ++it) {
+        const int u = int(rng() % V), b = u & ~31, v = b + int(rng() % std::min(32, V - b));
+        const int ru = slot[u] & 7, rv = slot[v] & 7;
+        if (ru == rv) continue;
+        const long long d = move(u, ru, rv) + move(v, rv, ru);
+        if (d <= 0) {
+            std::swap(slot[u], slot[v]);
+        } else {
+            move(v, ru, rv);
+            move(u, rv, ru);
+        }
+    }
+    return slot;
 }
 
 void append_segment(Schedule& out, const void* data, int bytes, int count, int first) {
@@ -228,53 +379,56 @@ void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& ou
     out.slot_of.resize(V);
     out.vert_of.resize(V);
     std::mt19937_64 rng(seed);
-    for (int b = 0; b < V; b += 32) {
-        const int n = std::min(32, V - b);
-        std::vector<int> p(n);
-        for (int i = 0; i < n; ++i) p[i] = i;
-        if (permute) std::shuffle(p.begin(), p.end(), rng);
-        for (int i = 0; i < n; ++i) {
-            out.slot_of[b + i] = uint16_t(b + p[i]);
-            out.vert_of[b + p[i]] = uint16_t(b + i);
-        }
+    std::vector<int> slot(V);
+    if (permute) {
+        slot = balanced_slots(m, rng, 100ll * V);
+    } else {
+        for (int i = 0; i < V; ++i) slot[i] = i;
+    }
+    for (int i = 0; i < V; ++i) {
+        out.slot_of[i] = uint16_t(slot[i]);
+        out.vert_of[slot[i]] = uint16_t(i);
     }
     for (int c = 0; c < m.n_ecol; ++c) {
         const int beg = m.ecol_off[c], end = m.ecol_off[c + 1];
-        std::vector<std::array<int, 2>> r(end - beg);
+        std::vector<Rec> r(end - beg);
         for (int q = beg; q < end; ++q) {
             const int e = m.eorder[q];
-            r[q - beg] = {out.slot_of[m.edge[2 * e]], out.slot_of[m.edge[2 * e + 1]]};
+            r[q - beg] = {out.slot_of[m.edge[2 * e]], out.slot_of[m.edge[2 * e + 1]], 0, 0, e};
         }
-        const std::vector<int> ord = permute ? group_by_banks<2>(r) : std::vector<int>();
+        if (permute) {
+            r = group_greedy<2>(r, true);
+            group_improve<2>(r, rng, 100ll * (end - beg), true);
+        }
         std::vector<uint32_t> buf(2 * size_t(end - beg));
         for (int j = 0; j < end - beg; ++j) {
-            const int src = permute ? ord[j] : j;
-            const int e = m.eorder[beg + src];
-            float d = m.rest_len[e];
+            float d = m.rest_len[r[j][4]];
             uint32_t dbits;
             std::memcpy(&dbits, &d, 4);
-            buf[2 * j] = uint32_t(r[src][0]) | (uint32_t(r[src][1]) << 16);
+            buf[2 * j] = uint32_t(r[j][0]) | (uint32_t(r[j][1]) << 16);
             buf[2 * j + 1] = dbits;
         }
         append_segment(out, buf.data(), int(buf.size() * 4), end - beg, beg);
     }
     for (int c = 0; c < m.n_tcol; ++c) {
         const int beg = m.tcol_off[c], end = m.tcol_off[c + 1];
-        std::vector<std::array<int, 4>> r(end - beg);
+        std::vector<Rec> r(end - beg);
         for (int q = beg; q < end; ++q) {
             const int t = m.torder[q];
-            for (int k = 0; k < 4; ++k) r[q - beg][k] = out.slot_of[m.tet[4 * t + k]];
+            r[q - beg] = {out.slot_of[m.tet[4 * t]], out.slot_of[m.tet[4 * t + 1]], out.slot_of[m.tet[4 * t + 2]],
+                          out.slot_of[m.tet[4 * t + 3]], t};
         }
-        const std::vector<int> ord = permute ? group_by_banks<4>(r) : std::vector<int>();
+        if (permute) {
+            r = group_greedy<4>(r, false);
+            group_improve<4>(r, rng, 100ll * (end - beg), false);
+        }
         std::vector<uint32_t> buf(4 * size_t(end - beg));
         for (int j = 0; j < end - beg; ++j) {
-            const int src = permute ? ord[j] : j;
-            const int t = m.torder[beg + src];
-            float v0 = m.V0[t];
+            float v0 = m.V0[r[j][4]];
             uint32_t vbits;
             std::memcpy(&vbits, &v0, 4);
-            buf[4 * j] = uint32_t(r[src][0]) | (uint32_t(r[src][1]) << 16);
-            buf[4 * j + 1] = uint32_t(r[src][2]) | (uint32_t(r[src][3]) << 16);
+            buf[4 * j] = uint32_t(r[j][0]) | (uint32_t(r[j][1]) << 16);
+            buf[4 * j + 1] = uint32_t(r[j][2]) | (uint32_t(r[j][3]) << 16);
             buf[4 * j + 2] = vbits;
             buf[4 * j + 3] = 0;
         }
