@@ -127,6 +127,22 @@ struct ffsrl_sim {
     float4* d_vpred = nullptr;    // [stride] predicted velocities (fused warm-start step)
     uint4* d_arows = nullptr;     // network input tiles (fused warm-start step)
     float* d_lambda_full = nullptr;
+    // steps with more than one launch replay a captured CUDA graph, one per
+    // set of output pointers (a few kept), on a stream of the library's own
+    struct StepGraph {
+        const float* a;
+        float* o;
+        float* r;
+        uint8_t* d;
+        cudaGraphExec_t exec;
+    };
+    std::vector<StepGraph> graphs;
+    cudaStream_t graph_stream = nullptr;
+    cudaEvent_t graph_in = nullptr, graph_out = nullptr;
+    void drop_graphs() {
+        for (StepGraph& g : graphs) cudaGraphExecDestroy(g.exec);
+        graphs.clear();
+    }
     // mixed rollout: warm-start envs stepped beside the plain ones
     bool mixed = false;
     float mix_threshold = 0.f;
@@ -157,6 +173,10 @@ struct ffsrl_sim {
             if (g.done) cudaEventDestroy(g.done);
         }
         if (fork) cudaEventDestroy(fork);
+        drop_graphs();
+        if (graph_stream) cudaStreamDestroy(graph_stream);
+        if (graph_in) cudaEventDestroy(graph_in);
+        if (graph_out) cudaEventDestroy(graph_out);
         if (warm_stream) cudaStreamDestroy(warm_stream);
         if (warm_done) cudaEventDestroy(warm_done);
         for (void* p : dev_allocs) cudaFree(p);
@@ -330,15 +350,16 @@ cudaError_t launch_group(ffsrl_sim* s, const LaunchGroup& g, cudaStream_t st, co
 // All groups of one step: forked onto the groups' streams after the work
 // already queued on the sim's stream, joined back before the step returns.
 // In a mixed rollout only the plain sublists are launched here.
-cudaError_t launch_all(ffsrl_sim* s, const SimDev* Sx, const float* a, float* o, float* r, uint8_t* d) {
+cudaError_t launch_all(ffsrl_sim* s, const SimDev* Sx, const float* a, float* o, float* r, uint8_t* d,
+                       cudaStream_t main) {
     if (s->groups.size() == 1) {
         const LaunchGroup& g = s->groups[0];
         SimDev S = Sx ? *Sx : s->S;
         S.meshes = s->d_meshes[g.permute ? 1 : 0];
-        return s->mixed ? launch_step(S, g.cfg, g.d_plain, g.n_plain, g.smem, s->stream, a, o, r, d)
-                        : launch_step(S, g.cfg, g.d_list, g.n, g.smem, s->stream, a, o, r, d);
+        return s->mixed ? launch_step(S, g.cfg, g.d_plain, g.n_plain, g.smem, main, a, o, r, d)
+                        : launch_step(S, g.cfg, g.d_list, g.n, g.smem, main, a, o, r, d);
     }
-    cudaError_t e = cudaEventRecord(s->fork, s->stream);
+    cudaError_t e = cudaEventRecord(s->fork, main);
     for (const LaunchGroup& g : s->groups) {
         if (e == cudaSuccess) e = cudaStreamWaitEvent(g.stream, s->fork, 0);
         SimDev S = Sx ? *Sx : s->S;
@@ -347,7 +368,7 @@ cudaError_t launch_all(ffsrl_sim* s, const SimDev* Sx, const float* a, float* o,
             e = s->mixed ? launch_step(S, g.cfg, g.d_plain, g.n_plain, g.smem, g.stream, a, o, r, d)
                          : launch_step(S, g.cfg, g.d_list, g.n, g.smem, g.stream, a, o, r, d);
         if (e == cudaSuccess) e = cudaEventRecord(g.done, g.stream);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, g.done, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(main, g.done, 0);
     }
     return e;
 }
@@ -715,23 +736,76 @@ int ffsrl_reset(ffsrl_sim* sim, const uint8_t* env_mask_dev, uint64_t seed) {
 namespace {
 int launch_warm_groups(ffsrl_sim* sim, cudaStream_t st, bool sublists, const float* actions, float* obs,
                        float* reward, uint8_t* done, float threshold, int n_full, int* fallbacks, float* residual);
+size_t warm_smem(const ffsrl_sim* s, const LaunchGroup& g);
+}  // namespace
+
+namespace {
+
+// Every launch of one step on `main` (forked onto the group and warm-start
+// streams and joined back).
+int step_body(ffsrl_sim* sim, cudaStream_t main, const float* a, float* o, float* r, uint8_t* d) {
+    if (sim->mixed) {
+        // warm-start envs on their own stream, beside the plain groups
+        FFSRL_CUDA(cudaEventRecord(sim->fork, main));
+        FFSRL_CUDA(cudaStreamWaitEvent(sim->warm_stream, sim->fork, 0));
+        const int rc = launch_warm_groups(sim, sim->warm_stream, true, a, o, r, d, sim->mix_threshold,
+                                          sim->mix_n_full, sim->mix_fallbacks, nullptr);
+        if (rc) return rc;
+        FFSRL_CUDA(cudaEventRecord(sim->warm_done, sim->warm_stream));
+    }
+    FFSRL_CUDA(launch_all(sim, nullptr, a, o, r, d, main));
+    if (sim->mixed) FFSRL_CUDA(cudaStreamWaitEvent(main, sim->warm_done, 0));
+    return FFSRL_OK;
+}
+
 }  // namespace
 
 int ffsrl_step(ffsrl_sim* sim, const float* actions_dev, float* obs_dev, float* reward_dev,
                uint8_t* done_dev) {
     if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
     FFSRL_CUDA(cudaSetDevice(sim->device));
-    if (sim->mixed) {
-        // warm-start envs on their own stream, beside the plain groups
-        FFSRL_CUDA(cudaEventRecord(sim->fork, sim->stream));
-        FFSRL_CUDA(cudaStreamWaitEvent(sim->warm_stream, sim->fork, 0));
-        const int rc = launch_warm_groups(sim, sim->warm_stream, true, actions_dev, obs_dev, reward_dev, done_dev,
-                                          sim->mix_threshold, sim->mix_n_full, sim->mix_fallbacks, nullptr);
-        if (rc) return rc;
-        FFSRL_CUDA(cudaEventRecord(sim->warm_done, sim->warm_stream));
+    if (sim->groups.size() == 1 && !sim->mixed)
+        return step_body(sim, sim->stream, actions_dev, obs_dev, reward_dev, done_dev);
+    // Several launches: replay the step's CUDA graph for these pointers,
+    // capturing it on first use (on the library's stream, so the caller's
+    // stream may be the legacy default stream).
+    if (!sim->graph_stream) {
+        FFSRL_CUDA(cudaStreamCreateWithFlags(&sim->graph_stream, cudaStreamNonBlocking));
+        FFSRL_CUDA(cudaEventCreateWithFlags(&sim->graph_in, cudaEventDisableTiming));
+        FFSRL_CUDA(cudaEventCreateWithFlags(&sim->graph_out, cudaEventDisableTiming));
     }
-    FFSRL_CUDA(launch_all(sim, nullptr, actions_dev, obs_dev, reward_dev, done_dev));
-    if (sim->mixed) FFSRL_CUDA(cudaStreamWaitEvent(sim->stream, sim->warm_done, 0));
+    cudaGraphExec_t exec = nullptr;
+    for (const ffsrl_sim::StepGraph& g : sim->graphs)
+        if (g.a == actions_dev && g.o == obs_dev && g.r == reward_dev && g.d == done_dev) exec = g.exec;
+    if (!exec) {
+        // kernel attributes are set outside the capture
+        for (const LaunchGroup& g : sim->groups) {
+            FFSRL_CUDA(configure_step(g.cfg, g.smem));
+            if (sim->mixed && g.n_warm) FFSRL_CUDA(configure_warm_step(warm_smem(sim, g)));
+        }
+        FFSRL_CUDA(cudaStreamBeginCapture(sim->graph_stream, cudaStreamCaptureModeThreadLocal));
+        const int rc = step_body(sim, sim->graph_stream, actions_dev, obs_dev, reward_dev, done_dev);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(sim->graph_stream, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        FFSRL_CUDA(ec);
+        const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        FFSRL_CUDA(ei);
+        if (sim->graphs.size() >= 4) {
+            cudaGraphExecDestroy(sim->graphs.front().exec);
+            sim->graphs.erase(sim->graphs.begin());
+        }
+        sim->graphs.push_back({actions_dev, obs_dev, reward_dev, done_dev, exec});
+    }
+    FFSRL_CUDA(cudaEventRecord(sim->graph_in, sim->stream));
+    FFSRL_CUDA(cudaStreamWaitEvent(sim->graph_stream, sim->graph_in, 0));
+    FFSRL_CUDA(cudaGraphLaunch(exec, sim->graph_stream));
+    FFSRL_CUDA(cudaEventRecord(sim->graph_out, sim->graph_stream));
+    FFSRL_CUDA(cudaStreamWaitEvent(sim->stream, sim->graph_out, 0));
     return FFSRL_OK;
 }
 
@@ -839,6 +913,7 @@ int ffsrl_set_network(ffsrl_sim* sim, const float* params_host, const float* nor
         n.out_std[k] = k < 3 ? norm_host[33 + k] : 0.f;
     }
     sim->has_net = true;
+    sim->drop_graphs();   // captured steps hold the previous network's normalisation
     return FFSRL_OK;
 }
 
@@ -1068,6 +1143,7 @@ int ffsrl_step_surrogate(ffsrl_sim* sim, const float* actions_dev, float* obs_de
 int ffsrl_set_surrogate_envs(ffsrl_sim* sim, const uint8_t* mask_host, double threshold, int32_t n_full,
                              int32_t* fallbacks_dev) {
     if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
+    sim->drop_graphs();   // captured steps hold the previous lists and threshold
     if (!mask_host) {
         sim->mixed = false;
         return FFSRL_OK;
@@ -1295,7 +1371,7 @@ extern "C" int ffsrl_step_noalloc(ffsrl_sim* sim, const float* actions_dev, floa
     // Step counters, contact counts, error flags and last distances start at zero.
     FFSRL_CUDA(cudaMemsetAsync(env_ints, 0, 4 * n * sizeof(int), sim->stream));
     FFSRL_CUDA(launch_unpack(S, sim->d_pstart, x_dev, v_dev, sim->stream));
-    FFSRL_CUDA(launch_all(sim, &S, actions_dev, nullptr, nullptr, nullptr));
+    FFSRL_CUDA(launch_all(sim, &S, actions_dev, nullptr, nullptr, nullptr, sim->stream));
     FFSRL_CUDA(launch_pack(S, sim->d_pstart, x_dev, v_dev, sim->stream));
     return FFSRL_OK;
 }

@@ -29,6 +29,9 @@ bool step_config_supported(int sub, int envs, bool resident, bool ring);
 cudaError_t launch_step(const SimDev& S, const StepConfig& c, const int* env_list, int n_list,
                         size_t smem_bytes, cudaStream_t stream, const float* actions, float* obs,
                         float* reward, uint8_t* done);
+// Sets the kernel's dynamic shared-memory limit for a launch of this size
+// (done by launch_step too; called ahead of stream capture).
+cudaError_t configure_step(const StepConfig& c, size_t smem_bytes);
 cudaError_t launch_reset(const SimDev& S, const uint8_t* mask, unsigned long long seed, cudaStream_t st);
 cudaError_t launch_pack(const SimDev& S, const int* pstart, float* x, float* v, cudaStream_t st);
 cudaError_t launch_unpack(const SimDev& S, const int* pstart, const float* x, const float* v, cudaStream_t st);

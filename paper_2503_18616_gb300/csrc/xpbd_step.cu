@@ -461,9 +461,8 @@ __global__ void unpack_state_kernel(SimDev S, const int* __restrict__ pstart, co
 // ---------------------------------------------------------------------------
 
 template <int SUB, int ENVS, bool RES, bool RING>
-static cudaError_t launch_one(const SimDev& S, const int* env_list, int n_list, size_t smem, cudaStream_t st,
-                              const float* actions, float* obs, float* reward, uint8_t* done) {
-    // Raise the kernel's dynamic shared-memory limit to what this launch needs
+static cudaError_t configure_one(size_t smem) {
+    // Raise the kernel's dynamic shared-memory limit to what a launch needs
     // (the limit plus the kernel's static shared memory must stay within the
     // device's per-block opt-in maximum).
     static size_t configured = 48 * 1024;
@@ -473,6 +472,14 @@ static cudaError_t launch_one(const SimDev& S, const int* env_list, int n_list, 
         if (e != cudaSuccess) return e;
         configured = smem;
     }
+    return cudaSuccess;
+}
+
+template <int SUB, int ENVS, bool RES, bool RING>
+static cudaError_t launch_one(const SimDev& S, const int* env_list, int n_list, size_t smem, cudaStream_t st,
+                              const float* actions, float* obs, float* reward, uint8_t* done) {
+    const cudaError_t ce = configure_one<SUB, ENVS, RES, RING>(smem);
+    if (ce != cudaSuccess) return ce;
     const int n_blocks = (n_list + ENVS - 1) / ENVS;
     xpbd_step_kernel<SUB, ENVS, RES, RING>
         <<<n_blocks, SUB * ENVS, smem, st>>>(S, env_list, n_list, actions, obs, reward, done);
@@ -494,6 +501,29 @@ cudaError_t launch_step(const SimDev& S, const StepConfig& c, const int* env_lis
 #define FFSRL_CASE(SUB_, ENVS_, RES_, RING_)                                                      \
     if (c.sub == SUB_ && c.envs == ENVS_ && c.resident == RES_ && c.ring == RING_)                \
         return launch_one<SUB_, ENVS_, RES_, RING_>(S, env_list, n_list, smem_bytes, stream, a, o, r, d);
+#define FFSRL_CASE4(SUB_)                                                                         \
+    FFSRL_CASE(SUB_, 1, true, true) FFSRL_CASE(SUB_, 1, true, false) FFSRL_CASE(SUB_, 1, false, true) \
+    FFSRL_CASE(SUB_, 1, false, false)
+    FFSRL_CASE4(128)
+    FFSRL_CASE4(256)
+    FFSRL_CASE4(384)
+    FFSRL_CASE4(512)
+    FFSRL_CASE4(1024)
+    FFSRL_CASE(128, 2, true, true)
+    FFSRL_CASE(256, 2, true, true)
+    FFSRL_CASE(384, 2, true, true)
+    FFSRL_CASE(512, 2, true, true)
+    FFSRL_CASE(128, 4, true, true)
+    FFSRL_CASE(256, 4, true, true)
+#undef FFSRL_CASE4
+#undef FFSRL_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t configure_step(const StepConfig& c, size_t smem_bytes) {
+#define FFSRL_CASE(SUB_, ENVS_, RES_, RING_)                                                      \
+    if (c.sub == SUB_ && c.envs == ENVS_ && c.resident == RES_ && c.ring == RING_)                \
+        return configure_one<SUB_, ENVS_, RES_, RING_>(smem_bytes);
 #define FFSRL_CASE4(SUB_)                                                                         \
     FFSRL_CASE(SUB_, 1, true, true) FFSRL_CASE(SUB_, 1, true, false) FFSRL_CASE(SUB_, 1, false, true) \
     FFSRL_CASE(SUB_, 1, false, false)

@@ -913,16 +913,22 @@ __global__ void __launch_bounds__(kWarmThreads, 3)
     }
 }
 
-cudaError_t launch_warm_step(const SimDev& S, const MlpDev& net, const SubstepCtl& C, const int* env_list,
-                             int n_list, size_t smem, const float* actions, float* obs, float* reward, uint8_t* done,
-                             cudaStream_t st) {
-    if (n_list <= 0) return cudaSuccess;
+cudaError_t configure_warm_step(size_t smem) {
     static size_t configured = 48 * 1024;
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(warm_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
         configured = smem;
     }
+    return cudaSuccess;
+}
+
+cudaError_t launch_warm_step(const SimDev& S, const MlpDev& net, const SubstepCtl& C, const int* env_list,
+                             int n_list, size_t smem, const float* actions, float* obs, float* reward, uint8_t* done,
+                             cudaStream_t st) {
+    if (n_list <= 0) return cudaSuccess;
+    const cudaError_t ce = configure_warm_step(smem);
+    if (ce != cudaSuccess) return ce;
     warm_step_kernel<<<n_list, kWarmThreads, smem, st>>>(S, net, C, env_list, n_list, actions, obs, reward, done);
     return cudaGetLastError();
 }

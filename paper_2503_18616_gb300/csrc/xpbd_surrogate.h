@@ -44,6 +44,7 @@ cudaError_t launch_substep(const SimDev& S, const SubstepCtl& C, const int* env_
 constexpr int kWarmThreads = 256;
 constexpr int kWarmMaxDegree = 24;   // 1-ring size the fused kernel gathers (three index chunks)
 size_t warm_smem_bytes(int Vp, int ring_bytes, int n_seg);
+cudaError_t configure_warm_step(size_t smem);   // shared-memory limit, ahead of stream capture
 cudaError_t launch_warm_step(const SimDev& S, const MlpDev& net, const SubstepCtl& C, const int* env_list,
                              int n_list, size_t smem, const float* actions, float* obs, float* reward, uint8_t* done,
                              cudaStream_t st);
