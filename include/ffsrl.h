@@ -91,6 +91,8 @@ typedef struct {
 #define FFSRL_SCHED_ENVS4 16      /* four envs per CTA sharing one ring */
 #define FFSRL_SCHED_SURROGATE_PIPELINE 32  /* warm-start step as per-substep launches (features,
                                               network, substep) instead of one fused kernel */
+#define FFSRL_SCHED_NO_CLUSTER 64  /* meshes above one CTA's shared memory use the global-memory
+                                      working copy instead of a thread-block cluster */
 
 /* Sizes of a created simulator. */
 typedef struct {

@@ -59,6 +59,7 @@ struct LaunchGroup {
     int n_plain = 0, n_warm = 0;
     StepConfig cfg;
     bool permute = true;
+    int cluster = 0;          // > 1: CTAs per env of the cluster kernel (meshes above one CTA's shared memory)
     size_t smem = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
@@ -99,8 +100,10 @@ struct ffsrl_sim {
     float* h_pinned = nullptr;  // staging for ffsrl_step_host
     float* d_stage = nullptr;
     SimDev S{};
-    MeshDev* d_meshes[2] = {nullptr, nullptr};  // [0] plain schedule, [1] permuted schedule
-    std::vector<MeshDev> h_meshes[2];
+    // [0] plain schedule, [1] bank-aware schedule, [2] the bank-aware schedule
+    // split for thread-block clusters (meshes of cluster groups; else as [1])
+    MeshDev* d_meshes[3] = {nullptr, nullptr, nullptr};
+    std::vector<MeshDev> h_meshes[3];
     int* d_pstart = nullptr;
     std::vector<LaunchGroup> groups;
     cudaEvent_t fork = nullptr;
@@ -199,7 +202,8 @@ int check_params(const ffsrl_params& p) {
     if (b != 0 && b != 128 && b != 256 && b != 384 && b != 512 && b != 1024)
         return fail(FFSRL_E_INVAL, "block_threads must be 0, 128, 256, 384, 512 or 1024");
     if (p.schedule_flags & ~(FFSRL_SCHED_FORCE | FFSRL_SCHED_NO_PERMUTE | FFSRL_SCHED_NO_RING |
-                             FFSRL_SCHED_ENVS2 | FFSRL_SCHED_ENVS4 | FFSRL_SCHED_SURROGATE_PIPELINE))
+                             FFSRL_SCHED_ENVS2 | FFSRL_SCHED_ENVS4 | FFSRL_SCHED_SURROGATE_PIPELINE |
+                             FFSRL_SCHED_NO_CLUSTER))
         return fail(FFSRL_E_INVAL, "unknown schedule_flags bits");
     if ((p.schedule_flags & FFSRL_SCHED_ENVS2) && (p.schedule_flags & FFSRL_SCHED_ENVS4))
         return fail(FFSRL_E_INVAL, "FFSRL_SCHED_ENVS2 and FFSRL_SCHED_ENVS4 are exclusive");
@@ -219,8 +223,10 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, const Schedule& sc, MeshDev& d)
     d.n_ecol = m.n_ecol;
     d.n_tcol = m.n_tcol;
     d.n_top = int(m.top.size());
-    d.n_seg = m.n_ecol + m.n_tcol;
+    d.n_seg = (m.n_ecol + m.n_tcol) * sc.parts;
     d.ring_bytes = sc.ring_bytes;
+    d.parts = sc.parts;
+    d.part_slots = sc.part_slots;
     std::vector<float4> rw(m.V);
     for (int i = 0; i < m.V; ++i)
         rw[i] = make_float4(m.rest[3 * i], m.rest[3 * i + 1], m.rest[3 * i + 2], m.inv_mass[i]);
@@ -340,11 +346,20 @@ size_t group_smem(const ffsrl_sim* s, const LaunchGroup& g, bool permute, const 
     return mx;
 }
 
+// One group's step kernel over `list` (the group's envs or a sublist).
+cudaError_t group_launch(const ffsrl_sim* s, const LaunchGroup& g, SimDev S, const int* list, int n, cudaStream_t st,
+                         const float* a, float* o, float* r, uint8_t* d) {
+    if (g.cluster > 1) {
+        S.meshes = s->d_meshes[2];
+        return launch_cluster_step(S, g.cfg.sub, g.cluster, list, n, g.smem, st, a, o, r, d);
+    }
+    S.meshes = s->d_meshes[g.permute ? 1 : 0];
+    return launch_step(S, g.cfg, list, n, g.smem, st, a, o, r, d);
+}
+
 cudaError_t launch_group(ffsrl_sim* s, const LaunchGroup& g, cudaStream_t st, const float* a, float* o, float* r,
                          uint8_t* d) {
-    SimDev S = s->S;
-    S.meshes = s->d_meshes[g.permute ? 1 : 0];
-    return launch_step(S, g.cfg, g.d_list, g.n, g.smem, st, a, o, r, d);
+    return group_launch(s, g, s->S, g.d_list, g.n, st, a, o, r, d);
 }
 
 // All groups of one step: forked onto the groups' streams after the work
@@ -354,19 +369,17 @@ cudaError_t launch_all(ffsrl_sim* s, const SimDev* Sx, const float* a, float* o,
                        cudaStream_t main) {
     if (s->groups.size() == 1) {
         const LaunchGroup& g = s->groups[0];
-        SimDev S = Sx ? *Sx : s->S;
-        S.meshes = s->d_meshes[g.permute ? 1 : 0];
-        return s->mixed ? launch_step(S, g.cfg, g.d_plain, g.n_plain, g.smem, main, a, o, r, d)
-                        : launch_step(S, g.cfg, g.d_list, g.n, g.smem, main, a, o, r, d);
+        const SimDev S = Sx ? *Sx : s->S;
+        return s->mixed ? group_launch(s, g, S, g.d_plain, g.n_plain, main, a, o, r, d)
+                        : group_launch(s, g, S, g.d_list, g.n, main, a, o, r, d);
     }
     cudaError_t e = cudaEventRecord(s->fork, main);
     for (const LaunchGroup& g : s->groups) {
         if (e == cudaSuccess) e = cudaStreamWaitEvent(g.stream, s->fork, 0);
-        SimDev S = Sx ? *Sx : s->S;
-        S.meshes = s->d_meshes[g.permute ? 1 : 0];
+        const SimDev S = Sx ? *Sx : s->S;
         if (e == cudaSuccess)
-            e = s->mixed ? launch_step(S, g.cfg, g.d_plain, g.n_plain, g.smem, g.stream, a, o, r, d)
-                         : launch_step(S, g.cfg, g.d_list, g.n, g.smem, g.stream, a, o, r, d);
+            e = s->mixed ? group_launch(s, g, S, g.d_plain, g.n_plain, g.stream, a, o, r, d)
+                         : group_launch(s, g, S, g.d_list, g.n, g.stream, a, o, r, d);
         if (e == cudaSuccess) e = cudaEventRecord(g.done, g.stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(main, g.done, 0);
     }
@@ -379,6 +392,7 @@ cudaError_t launch_all(ffsrl_sim* s, const SimDev* Sx, const float* a, float* o,
 // afterwards by the caller.
 int autotune_group(ffsrl_sim* s, LaunchGroup& g) {
     const ffsrl_params& p = s->params;
+    if (g.cluster > 1) return FFSRL_OK;   // one compiled cluster schedule
     TuneKey key;
     for (int mi : g.meshes) {
         const HostMesh& m = s->meshes[mi];
@@ -598,8 +612,52 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
         mesh_class[mi] = b ? std::min<int>(3, int(size_t(smem_sm) / (b + 1024))) : 0;
         if (b && mesh_class[mi] == 0) mesh_class[mi] = 1;
     }
+    // Meshes above one CTA's shared memory: a cluster of 2 or 4 CTAs holds
+    // the env on chip (class -CL) when it fits and can be scheduled; else the
+    // global-memory variant (class 0).
+    std::vector<int> part_slots(md.size(), 0);
+    std::vector<size_t> cl_smem(md.size(), 0);
+    if (!(p.schedule_flags & FFSRL_SCHED_NO_CLUSTER)) {
+        for (size_t mi = 0; mi < md.size(); ++mi) {
+            if (mesh_class[mi] != 0) continue;
+            for (int cl : {2, 4}) {
+                const int P = ((md[mi].V + cl - 1) / cl + 31) / 32 * 32;
+                const size_t b = cluster_smem_bytes(P);
+                if (b + 1024 + 256 > s->max_smem || cluster_max_active(kClusterThreads, cl, b) <= 0) continue;
+                mesh_class[mi] = -cl;
+                part_slots[mi] = P;
+                cl_smem[mi] = b;
+                break;
+            }
+        }
+    }
+    {
+        // schedules split by cluster rank for those meshes
+        std::vector<int> todo;
+        for (size_t mi = 0; mi < md.size(); ++mi)
+            if (mesh_class[mi] < 0) todo.push_back(int(mi));
+        std::vector<Schedule> sc(todo.size());
+        std::atomic<int> next{0};
+        auto work = [&]() {
+            for (int q; (q = next.fetch_add(1)) < int(todo.size());) {
+                const HostMesh& m = s->meshes[todo[q]];
+                build_schedule(m, 0x5EEDull + uint64_t(m.V), true, sc[q], -mesh_class[todo[q]]);
+            }
+        };
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        std::vector<std::thread> pool;
+        for (unsigned t = 1; t < std::min<unsigned>(hw, unsigned(todo.size())); ++t) pool.emplace_back(work);
+        work();
+        for (std::thread& t : pool) t.join();
+        s->h_meshes[2] = s->h_meshes[1];
+        for (size_t q = 0; q < todo.size(); ++q) {
+            int rc = upload_mesh(s, s->meshes[todo[q]], sc[q], s->h_meshes[2][todo[q]]);
+            if (rc) return rc;
+        }
+        FFSRL_CUDA(s->upload(&s->d_meshes[2], s->h_meshes[2].data(), s->h_meshes[2].size()));
+    }
     bool any_streaming = false;
-    for (int cls = 3; cls >= 0; --cls) {
+    for (int cls : {3, 2, 1, -2, -4, 0}) {
         LaunchGroup g;
         std::vector<std::pair<int, int>> members;   // (-V, env)
         for (int e = 0; e < n_env; ++e)
@@ -614,8 +672,15 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
             if (std::find(g.meshes.begin(), g.meshes.end(), mi) == g.meshes.end()) g.meshes.push_back(mi);
         }
         g.n = int(list.size());
-        g.cfg.resident = cls > 0;
+        g.cfg.resident = cls != 0;
         any_streaming |= cls == 0;
+        if (cls < 0) {
+            g.cluster = -cls;
+            g.cfg.sub = kClusterThreads;
+            g.cfg.ring = false;
+            g.permute = true;
+            for (int mi : g.meshes) g.smem = std::max(g.smem, cl_smem[mi]);
+        }
         FFSRL_CUDA(s->upload(&g.d_list, list.data(), list.size()));
         g.list = list;
         s->groups.push_back(g);
@@ -780,7 +845,7 @@ int ffsrl_step(ffsrl_sim* sim, const float* actions_dev, float* obs_dev, float* 
     if (!exec) {
         // kernel attributes are set outside the capture
         for (const LaunchGroup& g : sim->groups) {
-            FFSRL_CUDA(configure_step(g.cfg, g.smem));
+            if (g.cluster <= 1) FFSRL_CUDA(configure_step(g.cfg, g.smem));
             if (sim->mixed && g.n_warm) FFSRL_CUDA(configure_warm_step(warm_smem(sim, g)));
         }
         FFSRL_CUDA(cudaStreamBeginCapture(sim->graph_stream, cudaStreamCaptureModeThreadLocal));
@@ -1021,8 +1086,10 @@ int ensure_surrogate_buffers(ffsrl_sim* sim) {
     FFSRL_CUDA(cudaMemset(sim->d_dx, 0, size_t(sim->stride) * sizeof(float4)));
     FFSRL_CUDA(sim->alloc(&sim->d_lambda_full, size_t(sim->lambda_slots)));
     if (!sim->S.xg) {
-        for (const LaunchGroup& g : sim->groups)
-            if (!g.cfg.resident) return fail(FFSRL_E_INVAL, "internal: non-resident group without working copy");
+        // the per-substep pipeline runs cluster groups on the global working copy
+        bool need = false;
+        for (const LaunchGroup& g : sim->groups) need |= !g.cfg.resident || g.cluster > 1;
+        if (need) FFSRL_CUDA(sim->alloc(&sim->S.xg, size_t(sim->stride)));
     }
     return FFSRL_OK;
 }

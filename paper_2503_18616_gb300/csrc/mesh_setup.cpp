@@ -373,9 +373,12 @@ void append_segment(Schedule& out, const void* data, int bytes, int count, int f
 
 }  // namespace
 
-void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& out) {
+void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& out, int parts) {
     out = Schedule();
     const int V = m.V;
+    parts = std::max(1, parts);
+    out.parts = parts;
+    out.part_slots = ((V + parts - 1) / parts + 31) / 32 * 32;
     out.slot_of.resize(V);
     out.vert_of.resize(V);
     std::mt19937_64 rng(seed);
@@ -389,50 +392,63 @@ void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& ou
         out.slot_of[i] = uint16_t(slot[i]);
         out.vert_of[slot[i]] = uint16_t(i);
     }
+    const int P = out.part_slots;
     for (int c = 0; c < m.n_ecol; ++c) {
         const int beg = m.ecol_off[c], end = m.ecol_off[c + 1];
-        std::vector<Rec> r(end - beg);
+        std::vector<std::vector<Rec>> part(parts);
         for (int q = beg; q < end; ++q) {
             const int e = m.eorder[q];
-            r[q - beg] = {out.slot_of[m.edge[2 * e]], out.slot_of[m.edge[2 * e + 1]], 0, 0, e};
+            const Rec r = {out.slot_of[m.edge[2 * e]], out.slot_of[m.edge[2 * e + 1]], 0, 0, e};
+            part[r[0] / P].push_back(r);
         }
-        if (permute) {
-            r = group_greedy<2>(r, true);
-            group_improve<2>(r, rng, 100ll * (end - beg), true);
+        int first = beg;
+        for (std::vector<Rec>& r : part) {
+            const int n = int(r.size());
+            if (permute) {
+                r = group_greedy<2>(r, true);
+                group_improve<2>(r, rng, 100ll * n, true);
+            }
+            std::vector<uint32_t> buf(2 * size_t(n));
+            for (int j = 0; j < n; ++j) {
+                float d = m.rest_len[r[j][4]];
+                uint32_t dbits;
+                std::memcpy(&dbits, &d, 4);
+                buf[2 * j] = uint32_t(r[j][0]) | (uint32_t(r[j][1]) << 16);
+                buf[2 * j + 1] = dbits;
+            }
+            append_segment(out, buf.data(), int(buf.size() * 4), n, first);
+            first += n;
         }
-        std::vector<uint32_t> buf(2 * size_t(end - beg));
-        for (int j = 0; j < end - beg; ++j) {
-            float d = m.rest_len[r[j][4]];
-            uint32_t dbits;
-            std::memcpy(&dbits, &d, 4);
-            buf[2 * j] = uint32_t(r[j][0]) | (uint32_t(r[j][1]) << 16);
-            buf[2 * j + 1] = dbits;
-        }
-        append_segment(out, buf.data(), int(buf.size() * 4), end - beg, beg);
     }
     for (int c = 0; c < m.n_tcol; ++c) {
         const int beg = m.tcol_off[c], end = m.tcol_off[c + 1];
-        std::vector<Rec> r(end - beg);
+        std::vector<std::vector<Rec>> part(parts);
         for (int q = beg; q < end; ++q) {
             const int t = m.torder[q];
-            r[q - beg] = {out.slot_of[m.tet[4 * t]], out.slot_of[m.tet[4 * t + 1]], out.slot_of[m.tet[4 * t + 2]],
-                          out.slot_of[m.tet[4 * t + 3]], t};
+            const Rec r = {out.slot_of[m.tet[4 * t]], out.slot_of[m.tet[4 * t + 1]], out.slot_of[m.tet[4 * t + 2]],
+                           out.slot_of[m.tet[4 * t + 3]], t};
+            part[r[0] / P].push_back(r);
         }
-        if (permute) {
-            r = group_greedy<4>(r, false);
-            group_improve<4>(r, rng, 100ll * (end - beg), false);
+        int first = m.E + beg;
+        for (std::vector<Rec>& r : part) {
+            const int n = int(r.size());
+            if (permute) {
+                r = group_greedy<4>(r, false);
+                group_improve<4>(r, rng, 100ll * n, false);
+            }
+            std::vector<uint32_t> buf(4 * size_t(n));
+            for (int j = 0; j < n; ++j) {
+                float v0 = m.V0[r[j][4]];
+                uint32_t vbits;
+                std::memcpy(&vbits, &v0, 4);
+                buf[4 * j] = uint32_t(r[j][0]) | (uint32_t(r[j][1]) << 16);
+                buf[4 * j + 1] = uint32_t(r[j][2]) | (uint32_t(r[j][3]) << 16);
+                buf[4 * j + 2] = vbits;
+                buf[4 * j + 3] = 0;
+            }
+            append_segment(out, buf.data(), int(buf.size() * 4), n, first);
+            first += n;
         }
-        std::vector<uint32_t> buf(4 * size_t(end - beg));
-        for (int j = 0; j < end - beg; ++j) {
-            float v0 = m.V0[r[j][4]];
-            uint32_t vbits;
-            std::memcpy(&vbits, &v0, 4);
-            buf[4 * j] = uint32_t(r[j][0]) | (uint32_t(r[j][1]) << 16);
-            buf[4 * j + 1] = uint32_t(r[j][2]) | (uint32_t(r[j][3]) << 16);
-            buf[4 * j + 2] = vbits;
-            buf[4 * j + 3] = 0;
-        }
-        append_segment(out, buf.data(), int(buf.size() * 4), end - beg, m.E + beg);
     }
 }
 

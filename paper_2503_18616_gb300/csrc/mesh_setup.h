@@ -43,6 +43,8 @@ struct Schedule {
     std::vector<unsigned char> stream;       // records
     std::vector<int32_t> segs;               // [n_seg][4]: byte offset, bytes, count, first constraint
     int ring_bytes = 0;                      // largest segment
+    int parts = 1;                           // segments per colour (one per cluster CTA)
+    int part_slots = 0;                      // slots per part (multiple of 32)
 };
 
 // Builds the schedule. Slots are a fixed permutation inside each aligned
@@ -51,6 +53,10 @@ struct Schedule {
 // slot residues modulo 8 in each vertex position where possible (distinct
 // shared-memory bank groups for 16-byte accesses). Both choices leave the
 // result unchanged: a colour's constraints touch disjoint vertices.
-void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& out);
+// With parts > 1 the slots are split into `parts` ranges of part_slots slots
+// (one per CTA of a thread-block cluster) and every colour into `parts`
+// segments, segment r holding the records whose first vertex lies in range r
+// (segments ordered colour-major, part-minor).
+void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& out, int parts = 1);
 
 }  // namespace ffsrl

@@ -44,6 +44,8 @@ struct MeshDev {
     const float4* rest_s;             // [V] rest position and inverse mass (slot order)
     int max_deg;                      // largest vertex degree
     int pad2;
+    int parts;                        // segments per colour (CTAs of a cluster holding one env)
+    int part_slots;                   // slots per part, a multiple of 32 (parts > 1)
     const uint2* erec;                // [E] edge records of the stream, unpadded, stream order
     const uint4* trec;                // [T] tet records of the stream, unpadded, stream order
     double box_lo[3], box_hi[3], tool_start[3];

@@ -32,6 +32,17 @@ cudaError_t launch_step(const SimDev& S, const StepConfig& c, const int* env_lis
 // Sets the kernel's dynamic shared-memory limit for a launch of this size
 // (done by launch_step too; called ahead of stream capture).
 cudaError_t configure_step(const StepConfig& c, size_t smem_bytes);
+// Cluster step (xpbd_cluster.cu): envs whose mesh variant has parts = cl
+// ranges, sub threads per CTA, cl CTAs per env; smem from cluster_smem_bytes.
+constexpr int kClusterThreads = 1024;   // threads per CTA of the cluster kernel
+size_t cluster_smem_bytes(int part_slots);
+bool cluster_config_supported(int sub, int cl);
+cudaError_t launch_cluster_step(const SimDev& S, int sub, int cl, const int* env_list, int n_list, size_t smem,
+                                cudaStream_t st, const float* actions, float* obs, float* reward, uint8_t* done);
+// Clusters of this shape that fit on the device at once (0: cannot launch);
+// also sets the kernel's shared-memory limit.
+int cluster_max_active(int sub, int cl, size_t smem);
+
 cudaError_t launch_reset(const SimDev& S, const uint8_t* mask, unsigned long long seed, cudaStream_t st);
 cudaError_t launch_pack(const SimDev& S, const int* pstart, float* x, float* v, cudaStream_t st);
 cudaError_t launch_unpack(const SimDev& S, const int* pstart, const float* x, const float* v, cudaStream_t st);

@@ -6,13 +6,24 @@
 
 namespace ffsrl {
 
+// Positions are reached through an accessor with ld(slot) / st(slot, value):
+// SmemX for a CTA's own shared memory (or a global working copy), the
+// cluster accessor of xpbd_cluster.cu for positions spread over the shared
+// memory of a thread-block cluster.
+struct SmemX {
+    float4* p;
+    __device__ __forceinline__ float4 ld(int s) const { return p[s]; }
+    __device__ __forceinline__ void st(int s, float4 v) const { p[s] = v; }
+};
+
 // Edge-distance constraint C = |x_a - x_b| - d in XPBD form (Eq. 1 with
 // compliance): dlambda = (-C - at lambda) / (w_a + w_b + at), x_a += w_a dlambda n,
 // x_b -= w_b dlambda n, n = (x_a - x_b) / |x_a - x_b|.
-__device__ __forceinline__ void project_edge(float4* X, uint2 rec, float at, float min_len2, float& lam) {
+template <class Acc>
+__device__ __forceinline__ void project_edge(const Acc& X, uint2 rec, float at, float min_len2, float& lam) {
     const int a = int(rec.x & 0xffffu), b = int(rec.x >> 16);
     const float d = __uint_as_float(rec.y);
-    float4 xa = X[a], xb = X[b];
+    float4 xa = X.ld(a), xb = X.ld(b);
     const float dx = xa.x - xb.x, dy = xa.y - xb.y, dz = xa.z - xb.z;
     const float l2 = dx * dx + dy * dy + dz * dz;
     const float denom = xa.w + xb.w + at;
@@ -24,9 +35,12 @@ __device__ __forceinline__ void project_edge(float4* X, uint2 rec, float at, flo
     const float sa = xa.w * s, sb = xb.w * s;
     xa.x += sa * dx; xa.y += sa * dy; xa.z += sa * dz;
     xb.x -= sb * dx; xb.y -= sb * dy; xb.z -= sb * dz;
-    X[a] = xa;
-    X[b] = xb;
+    X.st(a, xa);
+    X.st(b, xb);
     lam += dl;
+}
+__device__ __forceinline__ void project_edge(float4* X, uint2 rec, float at, float min_len2, float& lam) {
+    project_edge(SmemX{X}, rec, at, min_len2, lam);
 }
 
 __device__ __forceinline__ float3 sub3(float4 a, float4 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
@@ -40,11 +54,12 @@ __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a
 // g_a = -(g_b + g_c + g_d) (the consistent reading of Eq. 2), scaled as in
 // Eq. 3 with inverse masses and compliance: dlambda = (-C - at lambda) /
 // (sum w_i |g_i|^2 + at), x_i += w_i dlambda g_i.
-__device__ __forceinline__ void project_tet(float4* X, uint4 rec, float at, float& lam) {
+template <class Acc>
+__device__ __forceinline__ void project_tet(const Acc& X, uint4 rec, float at, float& lam) {
     const int a = int(rec.x & 0xffffu), b = int(rec.x >> 16);
     const int c = int(rec.y & 0xffffu), d = int(rec.y >> 16);
     const float V0 = __uint_as_float(rec.z);
-    float4 xa = X[a], xb = X[b], xc = X[c], xd = X[d];
+    float4 xa = X.ld(a), xb = X.ld(b), xc = X.ld(c), xd = X.ld(d);
     const float3 ba = sub3(xb, xa), ca = sub3(xc, xa), da = sub3(xd, xa);
     const float3 g1 = cross3(ca, da), g2 = cross3(da, ba), g3 = cross3(ba, ca);  // 6 x gradient
     const float3 g0 = make_float3(-(g1.x + g2.x + g3.x), -(g1.y + g2.y + g3.y), -(g1.z + g2.z + g3.z));
@@ -59,13 +74,15 @@ __device__ __forceinline__ void project_tet(float4* X, uint4 rec, float at, floa
     xb.x += sb * g1.x; xb.y += sb * g1.y; xb.z += sb * g1.z;
     xc.x += sc * g2.x; xc.y += sc * g2.y; xc.z += sc * g2.z;
     xd.x += sd * g3.x; xd.y += sd * g3.y; xd.z += sd * g3.z;
-    X[a] = xa;
-    X[b] = xb;
-    X[c] = xc;
-    X[d] = xd;
+    X.st(a, xa);
+    X.st(b, xb);
+    X.st(c, xc);
+    X.st(d, xd);
     lam += dl;
 }
-
+__device__ __forceinline__ void project_tet(float4* X, uint4 rec, float at, float& lam) {
+    project_tet(SmemX{X}, rec, at, lam);
+}
 
 // Largest relative violation of an edge record: |C| / d.
 __device__ __forceinline__ float edge_violation(const float4* X, uint2 rec) {

@@ -62,6 +62,7 @@ class ffsrl_params(ctypes.Structure):
 
 SCHED_FORCE, SCHED_NO_PERMUTE, SCHED_NO_RING, SCHED_ENVS2, SCHED_ENVS4 = 1, 2, 4, 8, 16
 SCHED_SURROGATE_PIPELINE = 32
+SCHED_NO_CLUSTER = 64
 
 
 class ffsrl_info(ctypes.Structure):

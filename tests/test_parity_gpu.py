@@ -255,21 +255,57 @@ def test_collision_contacts_bit_exact_on_identical_inputs():
     compare_states(sim, oenvs, [m], n_env, label="collision")
 
 
-def test_uneven_meshes_per_env_compliance_and_streaming_path():
-    shapes = [(9, 9, 5), (13, 13, 7), (33, 33, 17)]     # the last (18513 vertices) exceeds one CTA's shared memory
+@pytest.mark.parametrize("path", ["cluster", "streaming"])
+def test_uneven_meshes_per_env_compliance_and_large_mesh_paths(path):
+    """The 33 x 33 x 17 block (18513 vertices) exceeds one CTA's shared
+    memory: by default a 2-CTA cluster holds it on chip (distributed shared
+    memory), with FFSRL_SCHED_NO_CLUSTER the global-memory working copy runs."""
+    from paper_2503_18616_gb300 import ffsrl
+    shapes = [(9, 9, 5), (13, 13, 7), (33, 33, 17)]
     meshes = [grid(s) for s in shapes]
     n_env, steps = 7, 8
     env_mesh = np.array([2, 0, 1, 2, 1, 0, 2], dtype=np.int32)
     alpha = inputs.compliance_draws(n_env, 1e-7, 1e-5, 3)
     p = P()
-    sim = make_sim(meshes, p, n_env, env_mesh=env_mesh, env_compliance=alpha, seed=6)
-    assert sim.resident_envs == int(np.sum(env_mesh != 2))
+    flags = ffsrl.SCHED_NO_CLUSTER if path == "streaming" else 0
+    sim = make_sim(meshes, p, n_env, env_mesh=env_mesh, env_compliance=alpha, seed=6, schedule_flags=flags)
+    assert sim.resident_envs == (int(np.sum(env_mesh != 2)) if path == "streaming" else n_env)
     oenvs, _ = oracle_envs(meshes, p, n_env, env_mesh=env_mesh, env_compliance=alpha, seed=6)
     for _ in range(steps):
         sim.step()
     for oe in oenvs.values():
         oe.run(steps, want_obs=False)
-    compare_states(sim, oenvs, meshes, n_env, env_mesh=env_mesh, label="uneven")
+    compare_states(sim, oenvs, meshes, n_env, env_mesh=env_mesh, label="uneven " + path)
+
+
+@pytest.mark.parametrize("iterations", [1, 2])
+def test_cluster_and_streaming_paths_are_bit_identical(iterations):
+    """Same envs through the cluster kernel and the global-memory kernel:
+    positions, velocities, observations, rewards and contact lists agree bit
+    for bit (the same arithmetic in the same colour order; with 2 iterations
+    the multipliers are carried per record)."""
+    from paper_2503_18616_gb300 import ffsrl
+    meshes = [grid((33, 33, 17)), grid((9, 9, 5))]
+    n_env, steps = 3, 6
+    env_mesh = np.array([0, 1, 0], dtype=np.int32)
+    p = P(radius=6e-3, iterations=iterations)
+    out = {}
+    for path, flags in (("cluster", 0), ("streaming", ffsrl.SCHED_NO_CLUSTER)):
+        sim = make_sim(meshes, p, n_env, env_mesh=env_mesh, seed=9, schedule_flags=flags)
+        for _ in range(steps):
+            obs, rew, done = sim.step()
+        sim.sync()
+        x, v, tool = sim.get_state()
+        ints = [sim.env_ints(e) for e in range(n_env)]
+        out[path] = (x.cpu().numpy(), v.cpu().numpy(), tool.cpu().numpy(), obs.cpu().numpy(), rew.cpu().numpy(), ints)
+    a, b = out["cluster"], out["streaming"]
+    for k in range(5):
+        assert np.array_equal(a[k], b[k]), k
+    for ia, ib in zip(a[5], b[5]):
+        for key in ia:
+            assert np.array_equal(np.asarray(ia[key]), np.asarray(ib[key])), key
+    if iterations == 1:   # the tool reaches the tissue (the contact lists are exercised)
+        assert any(len(np.asarray(i.get("contacts", []))) > 0 for i in a[5])
 
 
 def test_block17x17x9_4096_envs_sampled_1000_steps():
@@ -390,15 +426,15 @@ def test_every_schedule_gives_bit_identical_results():
 def test_uneven_1024_env_batch_sampled():
     """The uneven-batching configuration: 1024 envs, vertex counts log-uniform in
     [500, 20000] (37 block sizes), per-env edge compliance, all size classes
-    launched concurrently; the smallest, a middle and the largest env are
-    checked against the oracle."""
+    launched concurrently (the largest meshes on 2-CTA clusters); the
+    smallest, a middle and the largest env are checked against the oracle."""
     shapes, env_mesh = inputs.uneven_batch(1024, 500, 20000, seed=12345)
     meshes = [grid(s) for s in shapes]
     alpha = inputs.compliance_draws(1024, 1e-7, 1e-5, seed=12345)
     p = P()
     steps = 30
     sim = make_sim(meshes, p, 1024, env_mesh=env_mesh, env_compliance=alpha, seed=8)
-    assert sim.n_groups >= 2 and sim.resident_envs < 1024
+    assert sim.n_groups >= 2 and sim.resident_envs == 1024   # every env on chip
     vs = np.array([len(meshes[m][0]) for m in env_mesh])
     sample = [int(np.argmin(vs)), int(np.argsort(vs)[512]), int(np.argmax(vs))]
     oenvs, _ = oracle_envs(meshes, p, 1024, env_mesh=env_mesh, env_compliance=alpha, seed=8, envs=sample)
