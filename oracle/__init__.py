@@ -64,6 +64,8 @@ def _lib(precision: str = "f64") -> ctypes.CDLL:
             L.orc_sample_indices.argtypes = [U64, U64, I, I, P]
             L.orc_target_index.restype = I
             L.orc_target_index.argtypes = [U64, U64, I]
+            L.orc_episode_seed.restype = U64
+            L.orc_episode_seed.argtypes = [U64, I]
             L.orc_mesh_create.restype = P
             L.orc_mesh_create.argtypes = [I, P, P, I, P, I, P, ctypes.POINTER(I)]
             L.orc_mesh_destroy.argtypes = [P]
@@ -137,6 +139,11 @@ def sample_indices(seed: int, env: int, n: int, k: int) -> np.ndarray:
     return out[:k].copy()
 
 
+def episode_seed(seed0: int, k: int) -> int:
+    """Seed of episode k >= 1 started by auto-reset."""
+    return int(_lib().orc_episode_seed(seed0, k))
+
+
 def target_index(seed: int, env: int, n: int) -> int:
     return int(_lib().orc_target_index(seed, env, n))
 
@@ -164,13 +171,15 @@ class Params(ctypes.Structure):
         ("success_dist", ctypes.c_double),
         ("n_obs", ctypes.c_int),
         ("max_steps", ctypes.c_int),
+        ("solver", ctypes.c_int),
+        ("auto_reset", ctypes.c_int),
     ]
 
     @classmethod
     def from_dict(cls, d: dict) -> "Params":
         p = cls()
         for name, _ in cls._fields_:
-            val = d[name]
+            val = d.get(name, 0) if name in ("solver", "auto_reset") else d[name]
             if name == "gravity":
                 p.gravity[:] = [float(g) for g in val]
             else:
@@ -365,7 +374,8 @@ class Env:
         t, target, n_obs, n_c = (int(v) for v in out[:4])
         obs_ids = out[4:4 + n_obs].copy()
         contacts = out[4 + n_obs:4 + n_obs + n_c].copy()
-        return {"t": t, "target": target, "obs_ids": obs_ids, "contacts": contacts}
+        return {"t": t, "target": target, "obs_ids": obs_ids, "contacts": contacts,
+                "episode": int(out[4 + n_obs + n_c])}
 
     def features(self) -> np.ndarray:
         """Features [V][15] of the next substep's predicted state."""

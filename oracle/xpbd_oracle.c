@@ -48,6 +48,15 @@
  *       shorter than 1e-12 x extent. A tet with negative rest volume has its
  *       last two vertices swapped at setup.
  *   R9  Counter-based RNG: SplitMix64 (Steele, Lea, Flood, OOPSLA 2014).
+ *   R10 The paper's own GPU scheme (Sec. III-A) as an option: Jacobi
+ *       iterations in which every constraint steps from the iteration's start
+ *       positions and each vertex moves by the sum of its corrections divided
+ *       by the number of constraints (distance and volume) that contain it;
+ *       multipliers as in R2.
+ *   R11 Optional auto-reset: an env whose step reported done starts episode
+ *       k+1 at its next step, from the rest state with the draws of seed
+ *       splitmix64_nth(seed, 2^40 + k+1) (seed = the one given to reset; the
+ *       actions of the episode use that seed too).
  */
 #include <math.h>
 #include <stdint.h>
@@ -380,28 +389,48 @@ int orc_mesh_get_real(const orc_mesh* m, int which, double* out) {
 /* ------------------------------------------------------------------------ */
 
 /* Distance constraint C = |x_a - x_b| - d. Gradient wrt x_a is n = x_ab/|x_ab|,
- * wrt x_b is -n. Returns the constraint value before the update. */
-REAL orc_project_edge(REAL* xa, REAL* xb, REAL wa, REAL wb, REAL d, REAL alpha_t,
-                      REAL* lambda, REAL min_len) {
+ * wrt x_b is -n. The multiplier step dl = (-C - alpha~ lambda) / (w_a + w_b +
+ * alpha~) and the corrections da = w_a dl n, db = -w_b dl n at the given
+ * positions (zero, with dl = 0, for a skipped constraint, R8). Returns C. */
+static REAL edge_step(const REAL* xa, const REAL* xb, REAL wa, REAL wb, REAL d, REAL alpha_t, REAL lambda,
+                      REAL min_len, REAL* dl_out, REAL* da, REAL* db) {
     REAL ab[3];
     vsub(xa, xb, ab);
     REAL len = vnorm(ab);
     REAL C = len - d;
     REAL denom = wa + wb + alpha_t;
+    *dl_out = 0;
+    for (int k = 0; k < 3; ++k) { da[k] = 0; db[k] = 0; }
     if (len < min_len || denom == 0) return C;
     REAL n[3] = {ab[0] / len, ab[1] / len, ab[2] / len};
-    REAL dl = (-C - alpha_t * (*lambda)) / denom;
+    REAL dl = (-C - alpha_t * lambda) / denom;
     for (int k = 0; k < 3; ++k) {
-        xa[k] += wa * dl * n[k];
-        xb[k] -= wb * dl * n[k];
+        da[k] = wa * dl * n[k];
+        db[k] = -(wb * dl * n[k]);
+    }
+    *dl_out = dl;
+    return C;
+}
+
+/* Gauss-Seidel projection of one distance constraint: the step above,
+ * applied at once. Returns the constraint value before the update. */
+REAL orc_project_edge(REAL* xa, REAL* xb, REAL wa, REAL wb, REAL d, REAL alpha_t,
+                      REAL* lambda, REAL min_len) {
+    REAL dl, da[3], db[3];
+    REAL C = edge_step(xa, xb, wa, wb, d, alpha_t, *lambda, min_len, &dl, da, db);
+    for (int k = 0; k < 3; ++k) {
+        xa[k] += da[k];
+        xb[k] += db[k];
     }
     *lambda += dl;
     return C;
 }
 
-/* Volume constraint C = (x_ba x x_ca).x_da / 6 - V0 with the gradients of R1. */
-REAL orc_project_tet(REAL* xa, REAL* xb, REAL* xc, REAL* xd, const REAL* w4, REAL V0,
-                     REAL alpha_t, REAL* lambda) {
+/* Volume constraint C = (x_ba x x_ca).x_da / 6 - V0 with the gradients of R1:
+ * the multiplier step dl = (-C - alpha~ lambda) / (sum_i w_i |g_i|^2 + alpha~)
+ * and the corrections dx_i = w_i dl g_i at the given positions. Returns C. */
+static REAL tet_step(const REAL* xa, const REAL* xb, const REAL* xc, const REAL* xd, const REAL* w4, REAL V0,
+                     REAL alpha_t, REAL lambda, REAL* dl_out, REAL dx[4][3]) {
     REAL ba[3], ca[3], da[3], g[4][3];
     vsub(xb, xa, ba); vsub(xc, xa, ca); vsub(xd, xa, da);
     vcross(ca, da, g[1]);
@@ -414,11 +443,25 @@ REAL orc_project_tet(REAL* xa, REAL* xb, REAL* xc, REAL* xd, const REAL* w4, REA
     REAL C = tet_volume(xa, xb, xc, xd) - V0; /* C^v by its definition */
     REAL denom = alpha_t;
     for (int i = 0; i < 4; ++i) denom += w4[i] * vdot(g[i], g[i]);
+    *dl_out = 0;
+    for (int i = 0; i < 4; ++i)
+        for (int k = 0; k < 3; ++k) dx[i][k] = 0;
     if (denom == 0) return C;
-    REAL dl = (-C - alpha_t * (*lambda)) / denom;
+    REAL dl = (-C - alpha_t * lambda) / denom;
+    for (int i = 0; i < 4; ++i)
+        for (int k = 0; k < 3; ++k) dx[i][k] = w4[i] * dl * g[i][k];
+    *dl_out = dl;
+    return C;
+}
+
+/* Gauss-Seidel projection of one volume constraint (the step, applied). */
+REAL orc_project_tet(REAL* xa, REAL* xb, REAL* xc, REAL* xd, const REAL* w4, REAL V0,
+                     REAL alpha_t, REAL* lambda) {
+    REAL dl, dx[4][3];
+    REAL C = tet_step(xa, xb, xc, xd, w4, V0, alpha_t, *lambda, &dl, dx);
     REAL* x[4] = {xa, xb, xc, xd};
     for (int i = 0; i < 4; ++i)
-        for (int k = 0; k < 3; ++k) x[i][k] += w4[i] * dl * g[i][k];
+        for (int k = 0; k < 3; ++k) x[i][k] += dx[i][k];
     *lambda += dl;
     return C;
 }
@@ -437,6 +480,8 @@ typedef struct {
     double margin_xy, margin_below, margin_above; /* tool box (R7) */
     double w_l, w_d, w_s, success_dist;           /* reward weights (Sec. IV) */
     int n_obs, max_steps;
+    int solver;      /* 0: colour Gauss-Seidel (R4); 1: Jacobi with averaging (Sec. III-A, R10) */
+    int auto_reset;  /* 1: a done env starts its next episode at its next step (R11) */
 } orc_params;
 
 typedef struct orc_env {
@@ -451,7 +496,10 @@ typedef struct orc_env {
     REAL lo[3], hi[3];
     REAL l_prev;
     int t;        /* steps since reset */
-    uint64_t seed, env;
+    uint64_t seed, env;   /* seed of the current episode's draws */
+    uint64_t seed0;       /* seed given to reset (R11) */
+    int episode;          /* episodes started by auto-reset since then */
+    int done_prev;        /* the last step reported done */
     int* obs;     /* [n_obs] vertex ids */
     int n_obs;
     int target;
@@ -487,7 +535,7 @@ static REAL dist3(const REAL* a, const REAL* b) {
 /* Episode reset (Sec. III-B): rest positions, zero velocity, tool at its
  * start above the centre of the top face, fresh observation sample and
  * target vertex drawn from (seed, env). */
-int orc_env_reset(orc_env* s, const orc_params* p, uint64_t seed, uint64_t env) {
+static int reset_state(orc_env* s, const orc_params* p, uint64_t seed, uint64_t env) {
     const orc_mesh* m = s->m;
     if (p->n_obs < 0 || p->n_obs > m->n_top || m->n_top == 0) return ORC_E_INVAL;
     for (int i = 0; i < 3 * m->V; ++i) { s->x[i] = m->rest[i]; s->v[i] = 0; }
@@ -510,6 +558,16 @@ int orc_env_reset(orc_env* s, const orc_params* p, uint64_t seed, uint64_t env) 
     s->n_contacts = 0;
     return ORC_OK;
 }
+
+int orc_env_reset(orc_env* s, const orc_params* p, uint64_t seed, uint64_t env) {
+    s->seed0 = seed;
+    s->episode = 0;
+    s->done_prev = 0;
+    return reset_state(s, p, seed, env);
+}
+
+/* Seed of episode k >= 1 started by auto-reset (R11). */
+uint64_t orc_episode_seed(uint64_t seed0, int k) { return orc_sm64(seed0, (1ULL << 40) + (uint64_t)k); }
 
 /* Tool-tissue collision against the sphere proxy (Sec. III-A "Collisions",
  * readings R5, R6). Records contacts when `record` is set. */
@@ -534,6 +592,42 @@ static void collide_sphere(orc_env* s, REAL r, int record) {
     }
 }
 
+/* One Jacobi iteration, the paper's own parallel scheme (Sec. III-A): every
+ * distance and volume constraint takes its step at the positions the
+ * iteration starts from, the corrections are summed per vertex, and each
+ * vertex moves by its sum divided by n_i, the number of constraints of both
+ * families that contain it (R10). Multipliers are carried as in R2. */
+static void jacobi_iteration(orc_env* s, REAL at_d, REAL at_v, REAL min_len) {
+    const orc_mesh* m = s->m;
+    REAL* acc = (REAL*)calloc(3 * (size_t)m->V, sizeof(REAL));
+    int* n = (int*)calloc((size_t)m->V, sizeof(int));
+    for (int e = 0; e < m->E; ++e) { n[m->edge[2 * e]]++; n[m->edge[2 * e + 1]]++; }
+    for (int t = 0; t < m->T; ++t)
+        for (int k = 0; k < 4; ++k) n[m->tet[4 * t + k]]++;
+    for (int e = 0; e < m->E; ++e) {
+        int a = m->edge[2 * e], b = m->edge[2 * e + 1];
+        REAL dl, da[3], db[3];
+        edge_step(&s->x[3 * a], &s->x[3 * b], m->w[a], m->w[b], m->d[e], at_d, s->lam_e[e], min_len, &dl, da, db);
+        for (int k = 0; k < 3; ++k) { acc[3 * a + k] += da[k]; acc[3 * b + k] += db[k]; }
+        s->lam_e[e] += dl;
+    }
+    for (int t = 0; t < m->T; ++t) {
+        const int* v4 = &m->tet[4 * t];
+        REAL w4[4] = {m->w[v4[0]], m->w[v4[1]], m->w[v4[2]], m->w[v4[3]]};
+        REAL dl, dx[4][3];
+        tet_step(&s->x[3 * v4[0]], &s->x[3 * v4[1]], &s->x[3 * v4[2]], &s->x[3 * v4[3]], w4, m->V0[t], at_v,
+                 s->lam_t[t], &dl, dx);
+        for (int i = 0; i < 4; ++i)
+            for (int k = 0; k < 3; ++k) acc[3 * v4[i] + k] += dx[i][k];
+        s->lam_t[t] += dl;
+    }
+    for (int i = 0; i < m->V; ++i)
+        if (n[i] > 0)
+            for (int k = 0; k < 3; ++k) s->x[3 * i + k] += acc[3 * i + k] / (REAL)n[i];
+    free(acc);
+    free(n);
+}
+
 /* One substep (Algorithm 1's inner loop with readings R2, R4, R5). */
 static void substep(orc_env* s, const orc_params* p, REAL h, REAL alpha_d, int record) {
     const orc_mesh* m = s->m;
@@ -553,6 +647,10 @@ static void substep(orc_env* s, const orc_params* p, REAL h, REAL alpha_d, int r
     for (int e = 0; e < m->E; ++e) s->lam_e[e] = 0;
     for (int t = 0; t < m->T; ++t) s->lam_t[t] = 0;
     for (int it = 0; it < p->iterations; ++it) {
+        if (p->solver == 1) {
+            jacobi_iteration(s, at_d, at_v, min_len);
+            continue;
+        }
         for (int c = 0; c < m->n_ecol; ++c)
             for (int q = m->ecol_off[c]; q < m->ecol_off[c + 1]; ++q) {
                 int e = m->eorder[q];
@@ -583,6 +681,12 @@ int orc_obs_dim(const orc_params* p) { return 3 + 3 * p->n_obs; }
 int orc_env_step(orc_env* s, const orc_params* p, const double* action, double alpha_d,
                  double* obs, double* reward, unsigned char* done) {
     const orc_mesh* m = s->m;
+    if (p->auto_reset && s->done_prev) {
+        s->episode += 1;
+        int rc = reset_state(s, p, orc_episode_seed(s->seed0, s->episode), s->env);
+        if (rc) return rc;
+        s->done_prev = 0;
+    }
     double a[3];
     for (int k = 0; k < 3; ++k)
         a[k] = action ? action[k] : orc_action(s->seed, s->env, (uint64_t)s->t, k);
@@ -606,8 +710,10 @@ int orc_env_step(orc_env* s, const orc_params* p, const double* action, double a
     REAL R = (REAL)p->w_l * l + (REAL)p->w_d * (l - s->l_prev) + (REAL)p->w_s * (REAL)succ;
     s->l_prev = l;
     s->t += 1;
+    const int dn = ((p->max_steps > 0 && s->t >= p->max_steps) || succ) ? 1 : 0;
+    s->done_prev = dn;
     if (reward) *reward = (double)R;
-    if (done) *done = (unsigned char)(((p->max_steps > 0 && s->t >= p->max_steps) || succ) ? 1 : 0);
+    if (done) *done = (unsigned char)dn;
     (void)m;
     return ORC_OK;
 }
@@ -646,6 +752,7 @@ void orc_env_get_ints(const orc_env* s, int* out) {
     out[0] = s->t; out[1] = s->target; out[2] = s->n_obs; out[3] = s->n_contacts;
     for (int q = 0; q < s->n_obs; ++q) out[4 + q] = s->obs[q];
     for (int q = 0; q < s->n_contacts; ++q) out[4 + s->n_obs + q] = s->contacts[q];
+    out[4 + s->n_obs + s->n_contacts] = s->episode;
 }
 void orc_env_get_tool_box(const orc_env* s, double* lo, double* hi) {
     for (int k = 0; k < 3; ++k) { lo[k] = (double)s->lo[k]; hi[k] = (double)s->hi[k]; }

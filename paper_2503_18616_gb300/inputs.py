@@ -157,6 +157,8 @@ def default_params(spacing: float = CELL, **over) -> dict:
         "success_dist": 3e-3,
         "n_obs": 64,
         "max_steps": 0,
+        "solver": 0,        # 0 colour Gauss-Seidel, 1 Jacobi with averaging (the paper's GPU scheme)
+        "auto_reset": 0,    # 1: a done env starts a new episode at its next step
     }
     p.update(over)
     return p
