@@ -79,8 +79,16 @@ typedef struct {
     int32_t block_threads;    /* CUDA threads per environment (128, 256, 384, 512
                                  or 1024); 0 = autotuned (256 when forced) */
     int32_t schedule_flags;   /* 0 = autotuned; else FFSRL_SCHED_* bits forcing a schedule */
-    int32_t reserved[4];      /* must be zero */
+    int32_t solver;           /* FFSRL_SOLVER_*: colour Gauss-Seidel (0, the workload's) or the
+                                 paper's Jacobi iterations with averaging (1, Sec. III-A) */
+    int32_t auto_reset;       /* 1: an env whose step reported done starts its next episode at
+                                 its next step (rest state, draws of the episode's seed
+                                 splitmix64_nth(seed, 2^40 + k) for episode k >= 1) */
+    int32_t reserved[2];      /* must be zero */
 } ffsrl_params;
+
+#define FFSRL_SOLVER_GAUSS_SEIDEL 0
+#define FFSRL_SOLVER_JACOBI 1
 
 /* schedule_flags bits (execution choices only: results do not depend on them
  * beyond float32 rounding order, and not at all for the first three). */

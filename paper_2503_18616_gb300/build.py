@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libffsrl.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ffsrl_api.cu", "xpbd_step.cu", "xpbd_cluster.cu", "xpbd_surrogate.cu", "mlp_tc.cu", "mesh_setup.cpp"]
+SOURCES = ["ffsrl_api.cu", "xpbd_step.cu", "xpbd_cluster.cu", "xpbd_jacobi.cu", "xpbd_surrogate.cu", "mlp_tc.cu", "mesh_setup.cpp"]
 
 
 def nvcc() -> str:

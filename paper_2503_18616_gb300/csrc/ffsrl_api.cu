@@ -60,6 +60,7 @@ struct LaunchGroup {
     StepConfig cfg;
     bool permute = true;
     int cluster = 0;          // > 1: CTAs per env of the cluster kernel (meshes above one CTA's shared memory)
+    bool jacobi = false;      // the Jacobi solver's kernel (FFSRL_SOLVER_JACOBI)
     size_t smem = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
@@ -207,7 +208,10 @@ int check_params(const ffsrl_params& p) {
         return fail(FFSRL_E_INVAL, "unknown schedule_flags bits");
     if ((p.schedule_flags & FFSRL_SCHED_ENVS2) && (p.schedule_flags & FFSRL_SCHED_ENVS4))
         return fail(FFSRL_E_INVAL, "FFSRL_SCHED_ENVS2 and FFSRL_SCHED_ENVS4 are exclusive");
-    for (int k = 0; k < 4; ++k)
+    if (p.solver != FFSRL_SOLVER_GAUSS_SEIDEL && p.solver != FFSRL_SOLVER_JACOBI)
+        return fail(FFSRL_E_INVAL, "solver must be FFSRL_SOLVER_GAUSS_SEIDEL or FFSRL_SOLVER_JACOBI");
+    if (p.auto_reset != 0 && p.auto_reset != 1) return fail(FFSRL_E_INVAL, "auto_reset must be 0 or 1");
+    for (int k = 0; k < 2; ++k)
         if (p.reserved[k] != 0) return fail(FFSRL_E_INVAL, "reserved params must be zero");
     return FFSRL_OK;
 }
@@ -308,6 +312,19 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, const Schedule& sc, MeshDev& d)
         FFSRL_CUDA(s->upload(&d_tr, tr.data(), tr.size()));
         d.erec = d_er;
         d.trec = d_tr;
+        // 1 / (number of constraints containing the vertex), slot order (Jacobi solver)
+        std::vector<int> ncons(m.V, 0);
+        for (int e = 0; e < m.E; ++e) { ++ncons[m.edge[2 * e]]; ++ncons[m.edge[2 * e + 1]]; }
+        for (int t = 0; t < m.T; ++t)
+            for (int k = 0; k < 4; ++k) ++ncons[m.tet[4 * t + k]];
+        std::vector<float> inv_n(m.V);
+        for (int q = 0; q < m.V; ++q) {
+            const int n = ncons[sc.vert_of[q]];
+            inv_n[q] = n > 0 ? float(1.0 / n) : 0.f;
+        }
+        float* d_invn;
+        FFSRL_CUDA(s->upload(&d_invn, inv_n.data(), inv_n.size()));
+        d.inv_ncons = d_invn;
         d.snbr_hdr = d_hdr;
         d.snbr_ch = d_ch;
         d.max_deg = max_deg;
@@ -353,6 +370,10 @@ cudaError_t group_launch(const ffsrl_sim* s, const LaunchGroup& g, SimDev S, con
         S.meshes = s->d_meshes[2];
         return launch_cluster_step(S, g.cfg.sub, g.cluster, list, n, g.smem, st, a, o, r, d);
     }
+    if (g.jacobi) {
+        S.meshes = s->d_meshes[1];
+        return launch_jacobi_step(S, list, n, g.smem, st, a, o, r, d);
+    }
     S.meshes = s->d_meshes[g.permute ? 1 : 0];
     return launch_step(S, g.cfg, list, n, g.smem, st, a, o, r, d);
 }
@@ -392,7 +413,7 @@ cudaError_t launch_all(ffsrl_sim* s, const SimDev* Sx, const float* a, float* o,
 // afterwards by the caller.
 int autotune_group(ffsrl_sim* s, LaunchGroup& g) {
     const ffsrl_params& p = s->params;
-    if (g.cluster > 1) return FFSRL_OK;   // one compiled cluster schedule
+    if (g.cluster > 1 || g.jacobi) return FFSRL_OK;   // one compiled schedule
     TuneKey key;
     for (int mi : g.meshes) {
         const HostMesh& m = s->meshes[mi];
@@ -580,6 +601,11 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
     FFSRL_CUDA(s->alloc(&S.contacts, size_t(s->stride)));
     FFSRL_CUDA(s->alloc(&S.err, n_env));
     FFSRL_CUDA(cudaMemset(S.err, 0, n_env * sizeof(int)));
+    FFSRL_CUDA(s->alloc(&S.done_flag, n_env));
+    FFSRL_CUDA(s->alloc(&S.seed0, n_env));
+    FFSRL_CUDA(s->alloc(&S.episode, n_env));
+    FFSRL_CUDA(cudaMemset(S.done_flag, 0, n_env));
+    FFSRL_CUDA(cudaMemset(S.episode, 0, n_env * sizeof(int)));
     S.lambda = nullptr;
     s->lambda_slots = loff;
     if (p.iterations > 1) FFSRL_CUDA(s->alloc(&S.lambda, size_t(loff)));
@@ -657,7 +683,29 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
         FFSRL_CUDA(s->upload(&s->d_meshes[2], s->h_meshes[2].data(), s->h_meshes[2].size()));
     }
     bool any_streaming = false;
+    if (p.solver == FFSRL_SOLVER_JACOBI) {
+        // one group of every env: the Jacobi kernel keeps each env in one CTA
+        LaunchGroup g;
+        g.jacobi = true;
+        g.cfg.sub = 256;
+        g.cfg.ring = false;
+        std::vector<int> list;
+        for (int e = 0; e < n_env; ++e) {
+            list.push_back(e);
+            const int mi = s->env_mesh[e];
+            g.verts += md[mi].V;
+            if (std::find(g.meshes.begin(), g.meshes.end(), mi) == g.meshes.end()) g.meshes.push_back(mi);
+        }
+        for (int mi : g.meshes) g.smem = std::max(g.smem, jacobi_smem_bytes(md[mi].Vp));
+        if (g.smem + 1024 + 256 > s->max_smem)
+            return fail(FFSRL_E_INVAL, "the Jacobi solver needs every env in one CTA's shared memory");
+        g.n = n_env;
+        FFSRL_CUDA(s->upload(&g.d_list, list.data(), list.size()));
+        g.list = list;
+        s->groups.push_back(g);
+    }
     for (int cls : {3, 2, 1, -2, -4, 0}) {
+        if (p.solver == FFSRL_SOLVER_JACOBI) break;
         LaunchGroup g;
         std::vector<std::pair<int, int>> members;   // (-V, env)
         for (int e = 0; e < n_env; ++e)
@@ -809,6 +857,7 @@ namespace {
 // Every launch of one step on `main` (forked onto the group and warm-start
 // streams and joined back).
 int step_body(ffsrl_sim* sim, cudaStream_t main, const float* a, float* o, float* r, uint8_t* d) {
+    if (sim->params.auto_reset) FFSRL_CUDA(launch_auto_reset(sim->S, main));
     if (sim->mixed) {
         // warm-start envs on their own stream, beside the plain groups
         FFSRL_CUDA(cudaEventRecord(sim->fork, main));
@@ -829,7 +878,7 @@ int ffsrl_step(ffsrl_sim* sim, const float* actions_dev, float* obs_dev, float* 
                uint8_t* done_dev) {
     if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
     FFSRL_CUDA(cudaSetDevice(sim->device));
-    if (sim->groups.size() == 1 && !sim->mixed)
+    if (sim->groups.size() == 1 && !sim->mixed && !sim->params.auto_reset)
         return step_body(sim, sim->stream, actions_dev, obs_dev, reward_dev, done_dev);
     // Several launches: replay the step's CUDA graph for these pointers,
     // capturing it on first use (on the library's stream, so the caller's
@@ -845,7 +894,8 @@ int ffsrl_step(ffsrl_sim* sim, const float* actions_dev, float* obs_dev, float* 
     if (!exec) {
         // kernel attributes are set outside the capture
         for (const LaunchGroup& g : sim->groups) {
-            if (g.cluster <= 1) FFSRL_CUDA(configure_step(g.cfg, g.smem));
+            if (g.jacobi) FFSRL_CUDA(configure_jacobi_step(g.smem));
+            else if (g.cluster <= 1) FFSRL_CUDA(configure_step(g.cfg, g.smem));
             if (sim->mixed && g.n_warm) FFSRL_CUDA(configure_warm_step(warm_smem(sim, g)));
         }
         FFSRL_CUDA(cudaStreamBeginCapture(sim->graph_stream, cudaStreamCaptureModeThreadLocal));
@@ -1146,8 +1196,11 @@ int launch_warm_groups(ffsrl_sim* sim, cudaStream_t st, bool sublists, const flo
 // and the substep kernel.
 int run_substeps(ffsrl_sim* sim, int mode, const float* actions, float* obs, float* reward, uint8_t* done,
                  float threshold, int n_full, int* fallbacks, float* residual, float* feat_out, float* target_out) {
+    if (sim->params.solver != FFSRL_SOLVER_GAUSS_SEIDEL)
+        return fail(FFSRL_E_INVAL, "the warm-start and recording steps use the Gauss-Seidel solve");
     int rc = ensure_surrogate_buffers(sim);
     if (rc) return rc;
+    if (sim->params.auto_reset) FFSRL_CUDA(launch_auto_reset(sim->S, sim->stream));
     const int S_sub = sim->params.substeps;
     const size_t rows = size_t(sim->stride);
     const bool fused = mode == kSubstepSurrogate && !(sim->params.schedule_flags & FFSRL_SCHED_SURROGATE_PIPELINE);
@@ -1217,6 +1270,8 @@ int ffsrl_set_surrogate_envs(ffsrl_sim* sim, const uint8_t* mask_host, double th
     }
     if (!sim->has_net) return fail(FFSRL_E_INVAL, "no network installed (ffsrl_set_network)");
     if (n_full < 1) return fail(FFSRL_E_INVAL, "n_full must be >= 1");
+    if (sim->params.solver != FFSRL_SOLVER_GAUSS_SEIDEL)
+        return fail(FFSRL_E_INVAL, "the warm-start step uses the Gauss-Seidel solve");
     FFSRL_CUDA(cudaSetDevice(sim->device));
     int rc = ensure_surrogate_buffers(sim);
     if (rc) return rc;
@@ -1392,6 +1447,7 @@ extern "C" int ffsrl_step_noalloc(ffsrl_sim* sim, const float* actions_dev, floa
     if (!actions_dev || !x_dev || !v_dev || !tool_dev)
         return fail(FFSRL_E_INVAL, "ffsrl_step_noalloc needs actions_dev, x_dev, v_dev and tool_dev");
     if (sim->mixed) return fail(FFSRL_E_INVAL, "ffsrl_step_noalloc does not step warm-start envs (mixed rollout)");
+    if (sim->params.auto_reset) return fail(FFSRL_E_INVAL, "ffsrl_step_noalloc does not auto-reset");
     const size_t rows = size_t(sim->stride), n = size_t(sim->n_env);
     bool any_streaming = false;
     for (const LaunchGroup& g : sim->groups) any_streaming |= !g.cfg.resident;

@@ -289,8 +289,10 @@ __global__ void __launch_bounds__(SUB, 1)
             S.l_prev[env] = float(l);
             const int t = S.t_step[env] + 1;
             S.t_step[env] = t;
+            const uint8_t dn = uint8_t(((S.max_steps > 0 && t >= S.max_steps) || succ) ? 1 : 0);
+            S.done_flag[env] = dn;
             if (reward) reward[env] = float(R);
-            if (done) done[env] = uint8_t(((S.max_steps > 0 && t >= S.max_steps) || succ) ? 1 : 0);
+            if (done) done[env] = dn;
         }
     }
     cl_sync();   // no CTA leaves while CTA 0 still reads its shared memory

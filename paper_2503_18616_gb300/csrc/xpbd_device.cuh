@@ -46,6 +46,7 @@ struct MeshDev {
     int pad2;
     int parts;                        // segments per colour (CTAs of a cluster holding one env)
     int part_slots;                   // slots per part, a multiple of 32 (parts > 1)
+    const float* inv_ncons;           // [V] 1 / (constraints containing the slot's vertex), slot order
     const uint2* erec;                // [E] edge records of the stream, unpadded, stream order
     const uint4* trec;                // [T] tet records of the stream, unpadded, stream order
     double box_lo[3], box_hi[3], tool_start[3];
@@ -82,6 +83,9 @@ struct SimDev {
     int* contacts;            // [stride]: env e's list at voff_e
     int* err;                 // [n_env] kErr* bits
     float* lambda;            // multipliers carried across iterations (iterations > 1)
+    uint8_t* done_flag;       // [n_env] done of the env's last step (auto-reset)
+    unsigned long long* seed0;  // [n_env] seed given to reset
+    int* episode;             // [n_env] episodes started by auto-reset since then
     float4* xg;               // [stride] working positions (slot order) of envs not resident in SMEM
     float* pg;                // [3][stride] substep-start positions (slot order)
     float h, inv_h, gx, gy, gz;

@@ -43,7 +43,15 @@ cudaError_t launch_cluster_step(const SimDev& S, int sub, int cl, const int* env
 // also sets the kernel's shared-memory limit.
 int cluster_max_active(int sub, int cl, size_t smem);
 
+// Jacobi step (xpbd_jacobi.cu): one CTA of 256 threads per env, positions and
+// the per-vertex correction sums in shared memory.
+size_t jacobi_smem_bytes(int Vp);
+cudaError_t configure_jacobi_step(size_t smem);
+cudaError_t launch_jacobi_step(const SimDev& S, const int* env_list, int n_list, size_t smem, cudaStream_t st,
+                               const float* actions, float* obs, float* reward, uint8_t* done);
+
 cudaError_t launch_reset(const SimDev& S, const uint8_t* mask, unsigned long long seed, cudaStream_t st);
+cudaError_t launch_auto_reset(const SimDev& S, cudaStream_t st);
 cudaError_t launch_pack(const SimDev& S, const int* pstart, float* x, float* v, cudaStream_t st);
 cudaError_t launch_unpack(const SimDev& S, const int* pstart, const float* x, const float* v, cudaStream_t st);
 

@@ -84,6 +84,53 @@ __device__ __forceinline__ void project_tet(float4* X, uint4 rec, float at, floa
     project_tet(SmemX{X}, rec, at, lam);
 }
 
+// Jacobi forms (the paper's parallel scheme, Sec. III-A): the same steps
+// evaluated at the given positions, returning the corrections instead of
+// applying them (zero for a skipped constraint) and carrying lambda.
+__device__ __forceinline__ void edge_delta(const float4* X, uint2 rec, float at, float min_len2, float& lam,
+                                          float3& da, float3& db) {
+    const int a = int(rec.x & 0xffffu), b = int(rec.x >> 16);
+    const float d = __uint_as_float(rec.y);
+    const float4 xa = X[a], xb = X[b];
+    const float dx = xa.x - xb.x, dy = xa.y - xb.y, dz = xa.z - xb.z;
+    const float l2 = dx * dx + dy * dy + dz * dz;
+    const float denom = xa.w + xb.w + at;
+    da = make_float3(0.f, 0.f, 0.f);
+    db = da;
+    if (l2 < min_len2 || denom == 0.f) return;
+    const float len = sqrtf(l2);
+    const float C = len - d;
+    const float dl = __fdividef(-C - at * lam, denom);
+    const float s = __fdividef(dl, len);
+    const float sa = xa.w * s, sb = xb.w * s;
+    da = make_float3(sa * dx, sa * dy, sa * dz);
+    db = make_float3(-(sb * dx), -(sb * dy), -(sb * dz));
+    lam += dl;
+}
+
+__device__ __forceinline__ void tet_delta(const float4* X, uint4 rec, float at, float& lam, float3* dxs) {
+    const int a = int(rec.x & 0xffffu), b = int(rec.x >> 16);
+    const int c = int(rec.y & 0xffffu), d = int(rec.y >> 16);
+    const float V0 = __uint_as_float(rec.z);
+    const float4 xa = X[a], xb = X[b], xc = X[c], xd = X[d];
+    const float3 ba = sub3(xb, xa), ca = sub3(xc, xa), da = sub3(xd, xa);
+    const float3 g1 = cross3(ca, da), g2 = cross3(da, ba), g3 = cross3(ba, ca);  // 6 x gradient
+    const float3 g0 = make_float3(-(g1.x + g2.x + g3.x), -(g1.y + g2.y + g3.y), -(g1.z + g2.z + g3.z));
+    const float C = dot3(g3, da) * (1.0f / 6.0f) - V0;
+    const float sw = xa.w * dot3(g0, g0) + xb.w * dot3(g1, g1) + xc.w * dot3(g2, g2) + xd.w * dot3(g3, g3);
+    const float denom = sw * (1.0f / 36.0f) + at;
+    for (int i = 0; i < 4; ++i) dxs[i] = make_float3(0.f, 0.f, 0.f);
+    if (denom == 0.f) return;
+    const float dl = __fdividef(-C - at * lam, denom);
+    const float s = dl * (1.0f / 6.0f);
+    const float sa = xa.w * s, sb = xb.w * s, sc = xc.w * s, sd = xd.w * s;
+    dxs[0] = make_float3(sa * g0.x, sa * g0.y, sa * g0.z);
+    dxs[1] = make_float3(sb * g1.x, sb * g1.y, sb * g1.z);
+    dxs[2] = make_float3(sc * g2.x, sc * g2.y, sc * g2.z);
+    dxs[3] = make_float3(sd * g3.x, sd * g3.y, sd * g3.z);
+    lam += dl;
+}
+
 // Largest relative violation of an edge record: |C| / d.
 __device__ __forceinline__ float edge_violation(const float4* X, uint2 rec) {
     const float4 xa = X[rec.x & 0xffffu], xb = X[rec.x >> 16];

@@ -371,17 +371,21 @@ __global__ void __launch_bounds__(SUB * ENVS, min_ctas_per_sm(SUB * ENVS))
         S.l_prev[env] = float(l);
         const int t = S.t_step[env] + 1;
         S.t_step[env] = t;
+        const uint8_t dn = uint8_t(((S.max_steps > 0 && t >= S.max_steps) || succ) ? 1 : 0);
+        S.done_flag[env] = dn;
         if (reward) reward[env] = float(R);
-        if (done) done[env] = uint8_t(((S.max_steps > 0 && t >= S.max_steps) || succ) ? 1 : 0);
+        if (done) done[env] = dn;
     }
 }
 
 // Episode reset (Sec. III-B): rest positions, zero velocities, tool at its
 // start, fresh observed vertices (Floyd's sampling without replacement from
 // the top face, sorted) and target vertex from the env's counter-based streams.
-__global__ void reset_kernel(SimDev S, const uint8_t* __restrict__ mask, unsigned long long seed) {
-    const int env = blockIdx.x;
-    if (mask && !mask[env]) return;
+// Episode reset of one env by its CTA (Sec. III-B): rest positions, zero
+// velocities, tool at its start, fresh observed vertices (Floyd's sampling
+// without replacement from the top face, sorted) and target vertex from the
+// counter-based streams of `seed`.
+__device__ void reset_env(const SimDev& S, int env, unsigned long long seed) {
     const EnvDev ed = S.envs[env];
     const MeshDev& M = S.meshes[ed.mesh];
     const long long stride = S.stride;
@@ -426,6 +430,32 @@ __global__ void reset_kernel(SimDev S, const uint8_t* __restrict__ mask, unsigne
         S.t_step[env] = 0;
         S.seed[env] = seed;
         S.n_contacts[env] = 0;
+    }
+}
+
+__global__ void reset_kernel(SimDev S, const uint8_t* __restrict__ mask, unsigned long long seed) {
+    const int env = blockIdx.x;
+    if (mask && !mask[env]) return;
+    reset_env(S, env, seed);
+    if (threadIdx.x == 0) {
+        S.seed0[env] = seed;
+        S.episode[env] = 0;
+        S.done_flag[env] = 0;
+    }
+}
+
+// Auto-reset: an env whose last step reported done starts episode k + 1 with
+// the draws of seed splitmix64_nth(seed0, 2^40 + k + 1).
+__global__ void auto_reset_kernel(SimDev S) {
+    const int env = blockIdx.x;
+    const bool was_done = S.done_flag[env] != 0;
+    __syncthreads();   // every thread has read the flag before thread 0 clears it
+    if (!was_done) return;
+    const int k = S.episode[env] + 1;
+    reset_env(S, env, splitmix64_nth(S.seed0[env], (1ull << 40) + (unsigned long long)k));
+    if (threadIdx.x == 0) {
+        S.episode[env] = k;
+        S.done_flag[env] = 0;
     }
 }
 
@@ -545,6 +575,11 @@ cudaError_t configure_step(const StepConfig& c, size_t smem_bytes) {
 
 cudaError_t launch_reset(const SimDev& S, const uint8_t* mask, unsigned long long seed, cudaStream_t st) {
     reset_kernel<<<S.n_env, 256, 0, st>>>(S, mask, seed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_auto_reset(const SimDev& S, cudaStream_t st) {
+    auto_reset_kernel<<<S.n_env, 256, 0, st>>>(S);
     return cudaGetLastError();
 }
 

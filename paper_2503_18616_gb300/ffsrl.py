@@ -58,7 +58,8 @@ class ffsrl_params(ctypes.Structure):
                 ("w_l", ctypes.c_double), ("w_d", ctypes.c_double), ("w_s", ctypes.c_double),
                 ("success_dist", ctypes.c_double), ("n_obs_verts", ctypes.c_int32),
                 ("max_steps", ctypes.c_int32), ("block_threads", ctypes.c_int32),
-                ("schedule_flags", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("schedule_flags", ctypes.c_int32), ("solver", ctypes.c_int32), ("auto_reset", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 SCHED_FORCE, SCHED_NO_PERMUTE, SCHED_NO_RING, SCHED_ENVS2, SCHED_ENVS4 = 1, 2, 4, 8, 16
 SCHED_SURROGATE_PIPELINE = 32
@@ -168,6 +169,8 @@ def make_params(d: dict, block_threads: int = 0, schedule_flags: int = 0) -> ffs
     p.max_steps = d["max_steps"]
     p.block_threads = block_threads
     p.schedule_flags = schedule_flags
+    p.solver = int(d.get("solver", 0))
+    p.auto_reset = int(d.get("auto_reset", 0))
     return p
 
 
