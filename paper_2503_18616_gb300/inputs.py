@@ -170,6 +170,8 @@ WORKLOADS = {
     "block17x17x9_4096env_1000steps": {"shape": (17, 17, 9), "n_env": 4096, "steps": 1000},
     "uneven500-20000_1024env_500steps": {"n_env": 1024, "v_range": (500, 20000), "steps": 500,
                                           "alpha_range": (1e-7, 1e-5)},
+    # the paper's Jacobi iterations against colour Gauss-Seidel at equal error
+    "solvers_block17x17x9_4096env": {"shape": (17, 17, 9), "n_env": 4096, "steps": 100, "solvers": True},
     # full device-resident rollout: odd envs take the warm-start step (network
     # + 1 iteration, fallback to the 10-iteration solve), even envs the plain step
     "block17x17x9_16384env_2000steps": {"shape": (17, 17, 9), "n_env": 16384, "steps": 2000, "mixed": True,
