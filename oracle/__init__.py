@@ -70,6 +70,9 @@ def _lib(precision: str = "f64") -> ctypes.CDLL:
             L.orc_mesh_create.argtypes = [I, P, P, I, P, I, P, ctypes.POINTER(I)]
             L.orc_mesh_destroy.argtypes = [P]
             L.orc_mesh_info.argtypes = [P, P]
+            L.orc_mesh_faces.argtypes = [P, P]
+            L.orc_closest_segment_triangle.restype = D
+            L.orc_closest_segment_triangle.argtypes = [P, P, P, P, P, P, P, P]
             L.orc_mesh_get_int.argtypes = [P, I, P]
             L.orc_mesh_get_real.argtypes = [P, I, P]
             L.orc_env_create.restype = P
@@ -173,13 +176,20 @@ class Params(ctypes.Structure):
         ("max_steps", ctypes.c_int),
         ("solver", ctypes.c_int),
         ("auto_reset", ctypes.c_int),
+        ("tool_model", ctypes.c_int),
+        ("rcm_height", ctypes.c_double),
+        ("shaft_radius", ctypes.c_double),
+        ("clamp_length", ctypes.c_double),
+        ("clamp_radius", ctypes.c_double),
+        ("clamp_angle", ctypes.c_double),
     ]
 
     @classmethod
     def from_dict(cls, d: dict) -> "Params":
         p = cls()
         for name, _ in cls._fields_:
-            val = d.get(name, 0) if name in ("solver", "auto_reset") else d[name]
+            val = d.get(name, 0) if name in ("solver", "auto_reset", "tool_model", "rcm_height", "shaft_radius",
+                                             "clamp_length", "clamp_radius", "clamp_angle") else d[name]
             if name == "gravity":
                 p.gravity[:] = [float(g) for g in val]
             else:
@@ -251,6 +261,9 @@ class Mesh:
         info = np.zeros(6, dtype=np.int32)
         self._L.orc_mesh_info(self._h, _ptr(info))
         self.V, self.T, self.E, self.n_ecol, self.n_tcol, self.n_top = (int(v) for v in info)
+        fi = np.zeros(2, dtype=np.int32)
+        self._L.orc_mesh_faces(self._h, _ptr(fi))
+        self.F, self.n_fcol = int(fi[0]), int(fi[1])
         self.rest = rest.copy()
         self.inv_mass = w.copy()
 
@@ -290,6 +303,14 @@ class Mesh:
     def tcol_off(self): return self._ints(8, self.n_tcol + 1)
     @property
     def top(self): return self._ints(9, self.n_top)
+    @property
+    def faces(self): return self._ints(10, 3 * self.F).reshape(-1, 3)
+    @property
+    def face_opposite(self): return self._ints(11, self.F)
+    @property
+    def forder(self): return self._ints(12, self.F)
+    @property
+    def fcol_off(self): return self._ints(13, self.n_fcol + 1)
     @property
     def rest_len(self): return self._reals(0, self.E)
     @property
@@ -423,6 +444,15 @@ class Env:
 # --------------------------------------------------------------------------
 # Single-constraint projections (exposed for the pins)
 # --------------------------------------------------------------------------
+
+def closest_segment_triangle(q0, q1, a, b, c, precision="f64"):
+    """(distance, point on triangle, point on segment, barycentric weights)."""
+    dt = np.float64 if precision == "f64" else np.float32
+    args = [np.ascontiguousarray(v, dtype=dt) for v in (q0, q1, a, b, c)]
+    p, q, w = np.zeros(3, dt), np.zeros(3, dt), np.zeros(3, dt)
+    d = _lib(precision).orc_closest_segment_triangle(*[_ptr(v) for v in args], _ptr(p), _ptr(q), _ptr(w))
+    return float(d), p, q, w
+
 
 def project_edge(xa, xb, wa, wb, d, alpha_t, lam=0.0, min_len=0.0, precision="f64"):
     dt = np.float64 if precision == "f64" else np.float32

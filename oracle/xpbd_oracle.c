@@ -53,6 +53,25 @@
  *       positions and each vertex moves by the sum of its corrections divided
  *       by the number of constraints (distance and volume) that contain it;
  *       multipliers as in R2.
+ *   R12 Optional grasper tool (Sec. III-A "Surgical tool model"): the tool
+ *       point c (moved by the actions as in R7) is the end of the shaft; the
+ *       shaft runs from the remote centre of motion (above the centre of the
+ *       top face) to c, so it always passes through that centre; two clamps
+ *       leave c at +-alpha from the shaft axis in the plane of the axis and
+ *       world x. Each part is a capsule (segment and radius). The tool starts
+ *       with the clamp tips touching the centre of the top face.
+ *   R13 Grasper collision (Sec. III-A "Collisions"): once per substep after
+ *       the iterations, the surface faces (faces of exactly one tet with a
+ *       free vertex) are visited colour by colour (first-fit, ascending
+ *       triples); each face against the shaft, then the clamps: with p the
+ *       face's closest point to the capsule axis (barycentric b) and q the
+ *       axis point, if |p - q| < r the face is pushed along n = (p-q)/|p-q| by
+ *       a PBD step of stiffness 1: x_j -= w_j b_j (|p-q| - r) n / sum w b^2.
+ *       If the axis crosses the face, n points from the axis to the face's
+ *       centroid (or, if that is on the axis too, into the tissue).
+ *   R14 The per-element local optimisation the paper follows finds the
+ *       face's point of least capsule distance; here that point is computed
+ *       exactly (segment-triangle closest points).
  *   R11 Optional auto-reset: an env whose step reported done starts episode
  *       k+1 at its next step, from the rest state with the draws of seed
  *       splitmix64_nth(seed, 2^40 + k+1) (seed = the one given to reset; the
@@ -182,6 +201,15 @@ typedef struct orc_mesh {
     int* top;       /* ascending ids of vertices with z == max z */
     REAL bbmin[3], bbmax[3];
     REAL extent;    /* max side of the rest bounding box */
+    /* surface faces (faces of exactly one tet) with at least one free vertex,
+     * ascending by sorted vertex triple, for the grasper collision (R13) */
+    int F;
+    int* face;      /* [F][3] ascending vertex ids */
+    int* fopp;      /* [F] the fourth vertex of the face's tet (outward normal points away from it) */
+    int n_fcol;
+    int* fcolor;    /* [F] first-fit colour */
+    int* forder;    /* [F] colour-major order */
+    int* fcol_off;  /* [n_fcol + 1] */
 } orc_mesh;
 
 void orc_mesh_destroy(orc_mesh* m) {
@@ -189,7 +217,16 @@ void orc_mesh_destroy(orc_mesh* m) {
     free(m->rest); free(m->w); free(m->tet); free(m->flipped); free(m->V0);
     free(m->edge); free(m->d); free(m->ecolor); free(m->tcolor);
     free(m->eorder); free(m->torder); free(m->ecol_off); free(m->tcol_off);
-    free(m->top); free(m);
+    free(m->top); free(m->face); free(m->fopp); free(m->fcolor); free(m->forder); free(m->fcol_off);
+    free(m);
+}
+
+static int cmp_triple(const void* pa, const void* pb) {
+    const int* a = (const int*)pa;
+    const int* b = (const int*)pb;
+    for (int k = 0; k < 3; ++k)
+        if (a[k] != b[k]) return a[k] < b[k] ? -1 : 1;
+    return 0;
 }
 
 static int cmp_pair(const void* pa, const void* pb) {
@@ -344,11 +381,48 @@ orc_mesh* orc_mesh_create(int V, const double* rest, const double* w, int T, con
     m->n_top = 0;
     for (int i = 0; i < V; ++i)
         if (m->rest[3 * i + 2] == m->bbmax[2]) m->top[m->n_top++] = i;
+    /* surface faces: each tet's four faces as sorted triples with the opposite
+     * vertex; a triple that occurs once is on the surface (R13) */
+    int* fr = (int*)malloc(sizeof(int) * 4 * (4 * T > 0 ? 4 * T : 1));
+    static const int FA[4][4] = {{1, 2, 3, 0}, {0, 2, 3, 1}, {0, 1, 3, 2}, {0, 1, 2, 3}};
+    for (int t = 0; t < T; ++t)
+        for (int k = 0; k < 4; ++k) {
+            int v[3] = {m->tet[4 * t + FA[k][0]], m->tet[4 * t + FA[k][1]], m->tet[4 * t + FA[k][2]]};
+            for (int a = 0; a < 2; ++a)   /* sort the triple */
+                for (int b = 0; b < 2 - a; ++b)
+                    if (v[b] > v[b + 1]) { int tmp = v[b]; v[b] = v[b + 1]; v[b + 1] = tmp; }
+            int* r = &fr[4 * (4 * t + k)];
+            r[0] = v[0]; r[1] = v[1]; r[2] = v[2]; r[3] = m->tet[4 * t + FA[k][3]];
+        }
+    qsort(fr, (size_t)(4 * T), sizeof(int) * 4, cmp_triple);
+    m->face = (int*)malloc(sizeof(int) * 3 * (4 * T > 0 ? 4 * T : 1));
+    m->fopp = (int*)malloc(sizeof(int) * (4 * T > 0 ? 4 * T : 1));
+    m->F = 0;
+    for (int q = 0; q < 4 * T;) {
+        int n = 1;
+        while (q + n < 4 * T && cmp_triple(&fr[4 * q], &fr[4 * (q + n)]) == 0) ++n;
+        const int* r = &fr[4 * q];
+        if (n == 1 && (m->w[r[0]] > 0 || m->w[r[1]] > 0 || m->w[r[2]] > 0)) {
+            m->face[3 * m->F] = r[0]; m->face[3 * m->F + 1] = r[1]; m->face[3 * m->F + 2] = r[2];
+            m->fopp[m->F] = r[3];
+            m->F++;
+        }
+        q += n;
+    }
+    free(fr);
+    m->fcolor = (int*)malloc(sizeof(int) * (m->F > 0 ? m->F : 1));
+    m->forder = (int*)malloc(sizeof(int) * (m->F > 0 ? m->F : 1));
+    rc = color_first_fit(m->F, 3, m->face, V, m->fcolor, &m->n_fcol);
+    if (rc != ORC_OK) { orc_mesh_destroy(m); *err = rc; return NULL; }
+    m->fcol_off = (int*)malloc(sizeof(int) * (m->n_fcol + 1));
+    color_major(m->F, m->fcolor, m->n_fcol, m->forder, m->fcol_off);
     *err = ORC_OK;
     return m;
 }
 
 /* Read-only views for the test suite. which: 0 info, see below. */
+void orc_mesh_faces(const orc_mesh* m, int* out /* 2 */) { out[0] = m->F; out[1] = m->n_fcol; }
+
 void orc_mesh_info(const orc_mesh* m, int* out /* 6 */) {
     out[0] = m->V; out[1] = m->T; out[2] = m->E;
     out[3] = m->n_ecol; out[4] = m->n_tcol; out[5] = m->n_top;
@@ -367,6 +441,10 @@ int orc_mesh_get_int(const orc_mesh* m, int which, int* out) {
     case 7: memcpy(out, m->ecol_off, sizeof(int) * (m->n_ecol + 1)); break;
     case 8: memcpy(out, m->tcol_off, sizeof(int) * (m->n_tcol + 1)); break;
     case 9: memcpy(out, m->top, sizeof(int) * m->n_top); break;
+    case 10: memcpy(out, m->face, sizeof(int) * 3 * m->F); break;
+    case 11: memcpy(out, m->fopp, sizeof(int) * m->F); break;
+    case 12: memcpy(out, m->forder, sizeof(int) * m->F); break;
+    case 13: memcpy(out, m->fcol_off, sizeof(int) * (m->n_fcol + 1)); break;
     default: return ORC_E_INVAL;
     }
     return ORC_OK;
@@ -482,6 +560,9 @@ typedef struct {
     int n_obs, max_steps;
     int solver;      /* 0: colour Gauss-Seidel (R4); 1: Jacobi with averaging (Sec. III-A, R10) */
     int auto_reset;  /* 1: a done env starts its next episode at its next step (R11) */
+    int tool_model;  /* 0: sphere proxy (R6); 1: three-capsule grasper through a remote centre (R12, R13) */
+    double rcm_height;                 /* remote centre of motion above the centre of the top face */
+    double shaft_radius, clamp_length, clamp_radius, clamp_angle;  /* grasper capsules (R12) */
 } orc_params;
 
 typedef struct orc_env {
@@ -544,7 +625,9 @@ static int reset_state(orc_env* s, const orc_params* p, uint64_t seed, uint64_t 
         s->lo[k] = m->bbmin[k] - (REAL)p->margin_xy;
         s->hi[k] = m->bbmax[k] + (REAL)p->margin_xy;
     }
-    s->c[2] = m->bbmax[2] + (REAL)p->radius;
+    /* the tool touches the top face: the sphere's lowest point, or the clamp tips (R12) */
+    s->c[2] = m->bbmax[2] + (p->tool_model == 1 ? (REAL)(p->clamp_length * cos(p->clamp_angle) + p->clamp_radius)
+                                                : (REAL)p->radius);
     s->lo[2] = m->bbmax[2] - (REAL)p->margin_below;
     s->hi[2] = m->bbmax[2] + (REAL)p->margin_above;
     s->t = 0; s->seed = seed; s->env = env;
@@ -589,6 +672,205 @@ static void collide_sphere(orc_env* s, REAL r, int record) {
             }
             if (record) s->contacts[s->n_contacts++] = i;
         }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Grasper tool (Sec. III-A "Surgical tool model" and "Collisions"; R12-R14). */
+/* ------------------------------------------------------------------------ */
+
+/* Closest point of triangle (a, b, c) to point x with its barycentric
+ * coordinates w[3] (R14): the Voronoi-region case analysis of Ericson,
+ * Real-Time Collision Detection (2005), Sec. 5.1.5. */
+static void closest_on_triangle(const REAL* x, const REAL* a, const REAL* b, const REAL* c, REAL* out, REAL* w) {
+    REAL ab[3], ac[3], ax[3], bx[3], cx[3];
+    vsub(b, a, ab); vsub(c, a, ac); vsub(x, a, ax); vsub(x, b, bx); vsub(x, c, cx);
+    const REAL d1 = vdot(ab, ax), d2 = vdot(ac, ax);
+    const REAL d3 = vdot(ab, bx), d4 = vdot(ac, bx);
+    const REAL d5 = vdot(ab, cx), d6 = vdot(ac, cx);
+    const REAL vc = d1 * d4 - d3 * d2, vb = d5 * d2 - d1 * d6, va = d3 * d6 - d5 * d4;
+    if (d1 <= 0 && d2 <= 0) { w[0] = 1; w[1] = 0; w[2] = 0; }                       /* vertex a */
+    else if (d3 >= 0 && d4 <= d3) { w[0] = 0; w[1] = 1; w[2] = 0; }                 /* vertex b */
+    else if (vc <= 0 && d1 >= 0 && d3 <= 0) {                                       /* edge ab */
+        const REAL t = d1 / (d1 - d3); w[0] = 1 - t; w[1] = t; w[2] = 0;
+    } else if (d6 >= 0 && d5 <= d6) { w[0] = 0; w[1] = 0; w[2] = 1; }               /* vertex c */
+    else if (vb <= 0 && d2 >= 0 && d6 <= 0) {                                       /* edge ac */
+        const REAL t = d2 / (d2 - d6); w[0] = 1 - t; w[1] = 0; w[2] = t;
+    } else if (va <= 0 && (d4 - d3) >= 0 && (d5 - d6) >= 0) {                       /* edge bc */
+        const REAL t = (d4 - d3) / ((d4 - d3) + (d5 - d6)); w[0] = 0; w[1] = 1 - t; w[2] = t;
+    } else {                                                                        /* interior */
+        const REAL den = va + vb + vc;
+        w[1] = vb / den; w[2] = vc / den; w[0] = 1 - w[1] - w[2];
+    }
+    for (int k = 0; k < 3; ++k) out[k] = w[0] * a[k] + w[1] * b[k] + w[2] * c[k];
+}
+
+/* Closest points of segments p0-p1 and q0-q1: parameters s, t in [0, 1]
+ * (Ericson, Sec. 5.1.9). */
+static void closest_segments(const REAL* p0, const REAL* p1, const REAL* q0, const REAL* q1, REAL* s, REAL* t) {
+    REAL d1[3], d2[3], r[3];
+    vsub(p1, p0, d1); vsub(q1, q0, d2); vsub(p0, q0, r);
+    const REAL a = vdot(d1, d1), e = vdot(d2, d2), f = vdot(d2, r);
+    const REAL tiny = (REAL)1e-30;
+    REAL ss, tt;
+    if (a <= tiny && e <= tiny) { ss = 0; tt = 0; }
+    else if (a <= tiny) { ss = 0; tt = f / e; tt = tt < 0 ? 0 : (tt > 1 ? 1 : tt); }
+    else {
+        const REAL c = vdot(d1, r);
+        if (e <= tiny) { tt = 0; ss = -c / a; ss = ss < 0 ? 0 : (ss > 1 ? 1 : ss); }
+        else {
+            const REAL b = vdot(d1, d2), den = a * e - b * b;
+            ss = den != 0 ? (b * f - c * e) / den : 0;
+            ss = ss < 0 ? 0 : (ss > 1 ? 1 : ss);
+            tt = (b * ss + f) / e;
+            if (tt < 0) { tt = 0; ss = -c / a; ss = ss < 0 ? 0 : (ss > 1 ? 1 : ss); }
+            else if (tt > 1) { tt = 1; ss = (b - c) / a; ss = ss < 0 ? 0 : (ss > 1 ? 1 : ss); }
+        }
+    }
+    *s = ss; *t = tt;
+}
+
+/* Closest points of segment q0-q1 and triangle (a, b, c) (R14): p on the
+ * triangle with barycentric w[3], q on the segment; returns |p - q|. The
+ * pair is the segment's crossing of the triangle if there is one, else the
+ * nearest of: each segment end against the triangle, each triangle edge
+ * against the segment (in that order, ties keeping the earlier). */
+REAL orc_closest_segment_triangle(const REAL* q0, const REAL* q1, const REAL* a, const REAL* b, const REAL* c,
+                                  REAL* p, REAL* q, REAL* w) {
+    REAL ab[3], ac[3], n[3], dq[3], aq[3];
+    vsub(b, a, ab); vsub(c, a, ac); vcross(ab, ac, n); vsub(q1, q0, dq); vsub(a, q0, aq);
+    const REAL den = vdot(n, dq);
+    if (den != 0) {
+        const REAL t = vdot(n, aq) / den;
+        if (t >= 0 && t <= 1) {
+            REAL y[3], py[3], wy[3];
+            for (int k = 0; k < 3; ++k) y[k] = q0[k] + t * dq[k];
+            closest_on_triangle(y, a, b, c, py, wy);
+            if (wy[0] > 0 && wy[1] > 0 && wy[2] > 0) {   /* strictly inside: the segment crosses */
+                for (int k = 0; k < 3; ++k) { p[k] = y[k]; q[k] = y[k]; w[k] = wy[k]; }
+                return 0;
+            }
+        }
+    }
+    REAL best = -1;
+    const REAL* ends[2] = {q0, q1};
+    for (int e = 0; e < 2; ++e) {
+        REAL pe[3], we[3];
+        closest_on_triangle(ends[e], a, b, c, pe, we);
+        const REAL d = dist3(pe, ends[e]);
+        if (best < 0 || d < best) {
+            best = d;
+            for (int k = 0; k < 3; ++k) { p[k] = pe[k]; q[k] = ends[e][k]; w[k] = we[k]; }
+        }
+    }
+    const REAL* tv[3] = {a, b, c};
+    for (int e = 0; e < 3; ++e) {
+        const REAL* u = tv[e];
+        const REAL* v = tv[(e + 1) % 3];
+        REAL s_, t_;
+        closest_segments(q0, q1, u, v, &s_, &t_);
+        REAL cq[3], cp[3];
+        for (int k = 0; k < 3; ++k) { cq[k] = q0[k] + s_ * dq[k]; cp[k] = u[k] + t_ * (v[k] - u[k]); }
+        const REAL d = dist3(cp, cq);
+        if (d < best) {
+            best = d;
+            REAL we[3] = {0, 0, 0};
+            we[e] = 1 - t_; we[(e + 1) % 3] = t_;
+            for (int k = 0; k < 3; ++k) { p[k] = cp[k]; q[k] = cq[k]; w[k] = we[k]; }
+        }
+    }
+    return best;
+}
+
+/* The grasper's three capsules at tool point c (R12): the shaft from the
+ * remote centre of motion to c, and two clamps from c at angles +alpha and
+ * -alpha from the shaft axis in the plane of the axis and the world x axis
+ * (y if the axis is along x). seg [3][2][3], radius [3]. */
+static void grasper_capsules(const orc_env* s, const orc_params* p, REAL seg[3][2][3], REAL* radius) {
+    const orc_mesh* m = s->m;
+    const REAL rcm[3] = {(m->bbmin[0] + m->bbmax[0]) / 2, (m->bbmin[1] + m->bbmax[1]) / 2,
+                         m->bbmax[2] + (REAL)p->rcm_height};
+    REAL d[3];
+    vsub(s->c, rcm, d);
+    const REAL L = vnorm(d);
+    if (L > 0) { d[0] /= L; d[1] /= L; d[2] /= L; }
+    else { d[0] = 0; d[1] = 0; d[2] = -1; }
+    REAL u[3] = {1 - d[0] * d[0], -d[0] * d[1], -d[0] * d[2]};   /* e_x minus its part along d */
+    if (vnorm(u) < (REAL)1e-6) { u[0] = -d[1] * d[0]; u[1] = 1 - d[1] * d[1]; u[2] = -d[1] * d[2]; }
+    const REAL lu = vnorm(u);
+    u[0] /= lu; u[1] /= lu; u[2] /= lu;
+    const REAL ca = cos((REAL)p->clamp_angle), sa = sin((REAL)p->clamp_angle), lc = (REAL)p->clamp_length;
+    for (int k = 0; k < 3; ++k) {
+        seg[0][0][k] = rcm[k]; seg[0][1][k] = s->c[k];
+        seg[1][0][k] = s->c[k]; seg[1][1][k] = s->c[k] + lc * (ca * d[k] + sa * u[k]);
+        seg[2][0][k] = s->c[k]; seg[2][1][k] = s->c[k] + lc * (ca * d[k] - sa * u[k]);
+    }
+    radius[0] = (REAL)p->shaft_radius;
+    radius[1] = radius[2] = (REAL)p->clamp_radius;
+}
+
+/* Grasper-tissue collision (R13): surface faces colour by colour, each face
+ * against the shaft, then the two clamps; a face whose closest point lies
+ * inside a capsule is pushed out along the penetration direction by a PBD
+ * step of stiffness 1 on its vertices weighted by the barycentric
+ * coordinates. Records the vertices of pushed faces when `record` is set. */
+static void collide_grasper(orc_env* s, const orc_params* p, int record) {
+    const orc_mesh* m = s->m;
+    REAL seg[3][2][3], rad[3];
+    grasper_capsules(s, p, seg, rad);
+    unsigned char* hit = record ? (unsigned char*)calloc((size_t)m->V, 1) : NULL;
+    for (int qf = 0; qf < m->F; ++qf) {
+        const int f = m->forder[qf];
+        const int* v = &m->face[3 * f];
+        for (int k = 0; k < 3; ++k) {
+            REAL* x0 = &s->x[3 * v[0]];
+            REAL* x1 = &s->x[3 * v[1]];
+            REAL* x2 = &s->x[3 * v[2]];
+            REAL pp[3], qq[3], w[3];
+            const REAL dist = orc_closest_segment_triangle(seg[k][0], seg[k][1], x0, x1, x2, pp, qq, w);
+            if (!(dist < rad[k])) continue;
+            REAL n[3];
+            if (dist > (REAL)1e-12 * m->extent) {
+                for (int j = 0; j < 3; ++j) n[j] = (pp[j] - qq[j]) / dist;
+            } else {
+                /* The axis crosses the face: push radially, away from the axis
+                 * through the face's centroid; if the centroid is on the axis
+                 * too, into the tissue against the outward normal. */
+                REAL g[3], ax[3], rel[3];
+                for (int j = 0; j < 3; ++j) g[j] = (x0[j] + x1[j] + x2[j]) / 3;
+                vsub(seg[k][1], seg[k][0], ax);
+                vsub(g, seg[k][0], rel);
+                const REAL la2 = vdot(ax, ax);
+                const REAL tt = la2 > 0 ? vdot(rel, ax) / la2 : 0;
+                for (int j = 0; j < 3; ++j) n[j] = rel[j] - tt * ax[j];
+                REAL ln = vnorm(n);
+                if (!(ln > (REAL)1e-12 * m->extent)) {
+                    REAL e1[3], e2[3], e3[3];
+                    vsub(x1, x0, e1); vsub(x2, x0, e2); vcross(e1, e2, n);
+                    vsub(&s->x[3 * m->fopp[f]], x0, e3);
+                    ln = vnorm(n);
+                    if (!(ln > 0)) continue;
+                    if (vdot(n, e3) < 0) ln = -ln;   /* n / ln points toward the tet: inward */
+                }
+                for (int j = 0; j < 3; ++j) n[j] /= ln;
+            }
+            const REAL C = dist - rad[k];
+            const REAL den = m->w[v[0]] * w[0] * w[0] + m->w[v[1]] * w[1] * w[1] + m->w[v[2]] * w[2] * w[2];
+            if (!(den > 0)) continue;
+            const REAL sc = C / den;
+            REAL* xs[3] = {x0, x1, x2};
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) xs[i][j] -= m->w[v[i]] * w[i] * sc * n[j];
+            if (record)
+                for (int i = 0; i < 3; ++i)
+                    if (m->w[v[i]] > 0 && w[i] > 0) hit[v[i]] = 1;
+        }
+    }
+    if (record) {
+        s->n_contacts = 0;
+        for (int i = 0; i < m->V; ++i)
+            if (hit[i]) s->contacts[s->n_contacts++] = i;
+        free(hit);
     }
 }
 
@@ -667,7 +949,8 @@ static void substep(orc_env* s, const orc_params* p, REAL h, REAL alpha_d, int r
                                 w4, m->V0[t], at_v, &s->lam_t[t]);
             }
     }
-    collide_sphere(s, (REAL)p->radius, record);
+    if (p->tool_model == 1) collide_grasper(s, p, record);
+    else collide_sphere(s, (REAL)p->radius, record);
     /* velocity update */
     for (int i = 0; i < 3 * m->V; ++i) s->v[i] = (s->x[i] - s->xprev[i]) / h;
 }
@@ -980,7 +1263,8 @@ int orc_env_step_surrogate(orc_env* s, const orc_params* p, const double* action
                 for (int i = 0; i < 3 * m->V; ++i)
                     record_T[(size_t)sub * 3 * m->V + i] = (double)(s->x[i] - xh[i]);
         }
-        collide_sphere(s, (REAL)p->radius, sub == p->substeps - 1);
+        if (p->tool_model == 1) collide_grasper(s, p, sub == p->substeps - 1);
+        else collide_sphere(s, (REAL)p->radius, sub == p->substeps - 1);
         for (int i = 0; i < 3 * m->V; ++i) s->v[i] = (s->x[i] - s->xprev[i]) / h;
     }
     free(xh);

@@ -1,0 +1,185 @@
+"""Pins of the oracle's grasper tool (Sec. III-A "Surgical tool model" and
+"Collisions"): three capsules (shaft through the remote centre of motion,
+two clamps) collide with the surface faces of the tissue.
+
+The closest-point routine is checked against brute force (dense sampling of
+both the segment and the triangle); a pushed face moves out of the capsule
+and repeated pushes converge to its surface; a tool pressed into the tissue
+displaces it away from the tool; a tool far from the tissue leaves it exactly
+as the sphere-tool step does; the surface faces of a grid block are counted
+in closed form and coloured validly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2503_18616_gb300 import inputs
+
+
+def params(**over):
+    return inputs.default_params(**over)
+
+
+def _brute(q0, q1, a, b, c, n=60):
+    s = np.linspace(0, 1, 4 * n)
+    seg = q0[None, :] + s[:, None] * (q1 - q0)[None, :]
+    u, v = np.meshgrid(np.linspace(0, 1, n), np.linspace(0, 1, n))
+    keep = (u + v) <= 1
+    tri = a[None, :] + u[keep][:, None] * (b - a)[None, :] + v[keep][:, None] * (c - a)[None, :]
+    d = np.linalg.norm(seg[:, None, :] - tri[None, :, :], axis=2)
+    return d.min()
+
+
+def test_closest_segment_triangle_against_brute_force():
+    rng = np.random.default_rng(0)
+    worst = 0.0
+    for case in range(150):
+        a, b, c = (rng.normal(size=3) for _ in range(3))
+        q0, q1 = rng.normal(size=3) * 1.5, rng.normal(size=3) * 1.5
+        if case % 5 == 0:   # segment through the triangle
+            y = 0.3 * a + 0.3 * b + 0.4 * c
+            q0, q1 = y - rng.normal(size=3), None
+            q1 = 2 * y - q0
+        d, p, q, w = oracle.closest_segment_triangle(q0, q1, a, b, c)
+        bf = _brute(q0, q1, a, b, c)
+        # the pair is consistent: p on the triangle with weights w, q on the segment
+        assert np.all(w >= -1e-12) and abs(w.sum() - 1) < 1e-12
+        assert np.allclose(p, w[0] * a + w[1] * b + w[2] * c, atol=1e-12)
+        t = np.dot(q - q0, q1 - q0) / np.dot(q1 - q0, q1 - q0)
+        assert -1e-12 <= t <= 1 + 1e-12 and np.allclose(q, q0 + t * (q1 - q0), atol=1e-12)
+        assert abs(np.linalg.norm(p - q) - d) < 1e-12
+        # no sampled pair is closer, and the sampling gets within its resolution
+        assert d <= bf + 1e-12
+        h = 2 * max(np.linalg.norm(b - a), np.linalg.norm(c - a), np.linalg.norm(q1 - q0)) / 60
+        assert bf - d <= h, (case, d, bf)
+        worst = max(worst, bf - d)
+    assert worst > 0   # the brute force is coarser than the exact answer
+
+
+def _single_face_env(tool_xyz, **over):
+    """One tet with three pinned vertices on the bottom and a free apex; the
+    grasper comes down from above."""
+    s = inputs.CELL
+    rest = np.array([[0, 0, 0], [s, 0, 0], [0, s, 0], [0.3 * s, 0.3 * s, s]], dtype=np.float64)
+    w = np.array([0.0, 0.0, 0.0, 1.0 / inputs.MASS])
+    m = oracle.Mesh(rest, w, np.array([[0, 1, 2, 3]], dtype=np.int32))
+    return m, rest, w
+
+
+def test_surface_faces_of_a_grid_block():
+    for shape in [(3, 3, 2), (5, 4, 3), (9, 9, 5)]:
+        nx, ny, nz = shape
+        rest, w, tets = inputs.grid_block(*shape)
+        m = oracle.Mesh(rest, w, tets)
+        # two triangles per boundary cell face, minus the pinned bottom face
+        cells = 2 * ((nx - 1) * (ny - 1) + (nx - 1) * (nz - 1) + (ny - 1) * (nz - 1))
+        assert m.F == 2 * cells - 2 * (nx - 1) * (ny - 1)
+        faces = m.faces
+        assert np.all(faces[:, 0] < faces[:, 1]) and np.all(faces[:, 1] < faces[:, 2])
+        on_box = [np.all(np.isclose(rest[f][:, k], rest[f][0, k])) for f in faces for k in range(3)]
+        assert all(any(on_box[3 * i:3 * i + 3]) for i in range(len(faces)))   # every face lies on a box side
+        # colouring: faces of one colour share no vertex
+        off, order = m.fcol_off, m.forder
+        for c in range(m.n_fcol):
+            vs = faces[order[off[c]:off[c + 1]]].ravel()
+            assert len(vs) == len(set(vs.tolist()))
+
+
+def test_grasper_far_above_the_tissue_leaves_the_step_unchanged():
+    rest, w, tets = inputs.grid_block(9, 9, 5)
+    m = oracle.Mesh(rest, w, tets)
+    outs = []
+    for tool in (0, 1):
+        p = params(tool_model=tool, radius=0.0, margin_below=-0.5, margin_above=0.6)   # box far above
+        e = oracle.Env(m, p)
+        e.reset(3)
+        e.run(5, want_obs=False)
+        outs.append(e.state()[0])
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_grasper_pressed_into_the_tissue_pushes_it_away():
+    """Tool driven down into the tissue for 12 steps against the same steps
+    with the tool far away: the touched top-layer vertices are displaced away
+    from the tool (down, or outward from the shaft axis), as a wrong push
+    direction would not do; the contact list is ascending."""
+    rest, w, tets = inputs.grid_block(9, 9, 5)
+    m = oracle.Mesh(rest, w, tets)
+    top = rest[:, 2].max()
+    act = np.array([0.3, -0.2, -1.0])
+    runs = {}
+    for tool in (1, None):
+        p = params(tool_model=1) if tool else params(tool_model=1, margin_below=-0.5, margin_above=0.6)
+        e = oracle.Env(m, p)
+        e.reset(1)
+        for _ in range(12):
+            e.step(act)
+        runs[tool] = e
+    e, free = runs[1], runs[None]
+    x, _, c = e.state()
+    x0 = free.state()[0]
+    assert c[2] < top + 1e-12   # the tool point reached the top face
+    contacts = e.ints()["contacts"]
+    assert len(contacts) > 0 and np.all(np.diff(contacts) > 0)
+    moved = np.linalg.norm(x - x0, axis=1) > 1e-4
+    assert moved.sum() >= 3
+    rcm = np.array([0.0, 0.0, top + params()["rcm_height"]])
+    axis = (c - rcm) / np.linalg.norm(c - rcm)
+    score = 0.0
+    for i in np.nonzero(moved)[0]:
+        rel = x0[i] - rcm
+        radial = rel - np.dot(rel, axis) * axis        # from the axis to the vertex
+        dx = x[i] - x0[i]
+        score += np.dot(dx, radial / (np.linalg.norm(radial) + 1e-12)) - min(dx[2], 0.0)
+    assert score > 0
+
+
+def test_pushed_face_ends_on_the_capsule_surface():
+    """One tet with a free apex; the shaft (from the remote centre to the tool
+    point) is placed so that exactly one face lies inside it. One collision
+    pass moves that face out to the capsule surface (PBD with stiffness 1);
+    the pinned vertices stay."""
+    s = inputs.CELL
+    rest = np.array([[0, 0, 0], [2 * s, 0, 0], [0, 2 * s, 0], [0.5 * s, 0.5 * s, s]], dtype=np.float64)
+    w = np.array([0.0, 0.0, 0.0, 1.0 / inputs.MASS])
+    m = oracle.Mesh(rest, w, np.array([[0, 1, 2, 3]], dtype=np.int32))
+    r = 0.3 * s
+    p = params(tool_model=1, gravity=(0.0, 0.0, 0.0), substeps=1, iterations=0, n_obs=1, action_scale=0.0,
+               rcm_height=8 * s, shaft_radius=r, clamp_length=0.0, clamp_radius=0.0,
+               margin_below=10 * s, margin_xy=10 * s)
+    top = rest[:, 2].max()
+    rcm = np.array([(rest[:, 0].min() + rest[:, 0].max()) / 2, (rest[:, 1].min() + rest[:, 1].max()) / 2,
+                    top + p["rcm_height"]])
+    faces = m.faces
+
+    def dists(x, c):
+        return [oracle.closest_segment_triangle(rcm, c, *x[f])[0] for f in faces]
+
+    # the slanted face (1, 2, 3): the tool point just outside it, along its outward normal
+    g = rest[[1, 2, 3]].mean(axis=0)
+    nrm = np.cross(rest[2] - rest[1], rest[3] - rest[1])
+    nrm /= np.linalg.norm(nrm)
+    nrm = nrm if np.dot(nrm, g - rest[0]) > 0 else -nrm
+    c0 = next(g + k * r * nrm for k in np.linspace(0.05, 1.0, 40)
+              if sum(d < r for d in dists(rest, g + k * r * nrm)) == 1)
+    e = oracle.Env(m, p)
+    e.reset(0)
+    e.set_state(c=c0)
+    x0 = e.state()[0].copy()
+    e.step(np.zeros(3))
+    x1 = e.state()[0]
+    before, after = dists(x0, c0), dists(x1, c0)
+    i = int(np.argmin(before))
+    assert before[i] < r and sum(d < r for d in before) == 1
+    # one pass moves the face's closest point to the surface; the face then
+    # turns about its pinned edge, so a neighbouring point may still be
+    # slightly inside: the distance grows, and repeated passes (velocity
+    # cleared, so only the pushes move the apex) converge to r
+    assert after[i] > before[i] + 0.5 * (r - before[i])
+    for _ in range(30):
+        e.set_state(v=np.zeros_like(x0))
+        e.step(np.zeros(3))
+    assert dists(e.state()[0], c0)[i] == pytest.approx(r, rel=1e-3)
+    assert np.array_equal(e.state()[0][:3], rest[:3])
