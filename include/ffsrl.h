@@ -84,8 +84,21 @@ typedef struct {
     int32_t auto_reset;       /* 1: an env whose step reported done starts its next episode at
                                  its next step (rest state, draws of the episode's seed
                                  splitmix64_nth(seed, 2^40 + k) for episode k >= 1) */
-    int32_t reserved[2];      /* must be zero */
+    int32_t tool_model;       /* FFSRL_TOOL_*: the workload's sphere proxy (0) or the paper's
+                                 grasper (1, Sec. III-A): a shaft capsule from the remote centre
+                                 of motion (rcm_height above the centre of the top face) to the
+                                 tool point and two clamp capsules leaving the tool point at
+                                 +-clamp_angle from the shaft axis, against the surface faces */
+    int32_t reserved;         /* must be zero */
+    double rcm_height;        /* grasper: remote centre of motion above the top face */
+    double shaft_radius;      /* grasper: shaft capsule radius */
+    double clamp_length;      /* grasper: clamp capsule length */
+    double clamp_radius;      /* grasper: clamp capsule radius */
+    double clamp_angle;       /* grasper: clamp opening angle from the shaft axis, radians */
 } ffsrl_params;
+
+#define FFSRL_TOOL_SPHERE 0
+#define FFSRL_TOOL_GRASPER 1
 
 #define FFSRL_SOLVER_GAUSS_SEIDEL 0
 #define FFSRL_SOLVER_JACOBI 1
@@ -169,7 +182,10 @@ int ffsrl_set_state(ffsrl_sim* sim, const float* x_dev, const float* v_dev, cons
  * which: 0 oriented tets [T][4], 1 flipped [T], 2 edges [E][2] (min,max),
  * 3 edge colour [E], 4 tet colour [T], 5 edge colour-major order [E],
  * 6 tet colour-major order [T], 7 edge colour offsets [n_ecol+1],
- * 8 tet colour offsets [n_tcol+1], 9 top-face vertices [n_top].
+ * 8 tet colour offsets [n_tcol+1], 9 top-face vertices [n_top],
+ * 10 surface faces [F][3] (ascending triples with a free vertex),
+ * 11 their opposite tet vertices [F], 12 face colour-major order [F],
+ * 13 face colour offsets [n_fcol+1].
  * With out_host NULL only *count is written (number of int32 values). */
 int ffsrl_get_mesh_table(const ffsrl_sim* sim, int32_t mesh, int32_t which, int32_t* out_host,
                          int64_t* count);

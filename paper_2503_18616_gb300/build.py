@@ -40,6 +40,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "ffsrl.h"))
     flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3", "-Xcompiler", "-pthread",
+             "-Xcompiler", "-ffp-contract=off",   # host arithmetic (tool start, bounds) rounded as written
              "--expt-relaxed-constexpr", "-I", os.path.join(os.path.dirname(HERE), "include")] + ARCH
     if verbose:
         flags += ["-Xptxas", "-v"]

@@ -211,8 +211,16 @@ int check_params(const ffsrl_params& p) {
     if (p.solver != FFSRL_SOLVER_GAUSS_SEIDEL && p.solver != FFSRL_SOLVER_JACOBI)
         return fail(FFSRL_E_INVAL, "solver must be FFSRL_SOLVER_GAUSS_SEIDEL or FFSRL_SOLVER_JACOBI");
     if (p.auto_reset != 0 && p.auto_reset != 1) return fail(FFSRL_E_INVAL, "auto_reset must be 0 or 1");
-    for (int k = 0; k < 2; ++k)
-        if (p.reserved[k] != 0) return fail(FFSRL_E_INVAL, "reserved params must be zero");
+    if (p.reserved != 0) return fail(FFSRL_E_INVAL, "reserved params must be zero");
+    if (p.tool_model != FFSRL_TOOL_SPHERE && p.tool_model != FFSRL_TOOL_GRASPER)
+        return fail(FFSRL_E_INVAL, "tool_model must be FFSRL_TOOL_SPHERE or FFSRL_TOOL_GRASPER");
+    if (p.tool_model == FFSRL_TOOL_GRASPER) {
+        if (!(p.shaft_radius >= 0) || !(p.clamp_length >= 0) || !(p.clamp_radius >= 0) ||
+            !std::isfinite(p.rcm_height) || !std::isfinite(p.clamp_angle))
+            return fail(FFSRL_E_INVAL, "grasper sizes must be finite and >= 0");
+        if (p.solver != FFSRL_SOLVER_GAUSS_SEIDEL)
+            return fail(FFSRL_E_INVAL, "the grasper runs with the Gauss-Seidel solver");
+    }
     return FFSRL_OK;
 }
 
@@ -338,7 +346,31 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, const Schedule& sc, MeshDev& d)
     }
     d.box_lo[2] = m.bbmax[2] - p.tool_margin_below;
     d.box_hi[2] = m.bbmax[2] + p.tool_margin_above;
-    d.tool_start[2] = m.bbmax[2] + p.tool_radius;
+    // the tool touches the top face: the sphere's lowest point, or the grasper's clamp tips
+    d.tool_start[2] = m.bbmax[2] + (p.tool_model == FFSRL_TOOL_GRASPER
+                                        ? p.clamp_length * std::cos(p.clamp_angle) + p.clamp_radius
+                                        : p.tool_radius);
+    d.rcm[0] = float((m.bbmin[0] + m.bbmax[0]) / 2);
+    d.rcm[1] = float((m.bbmin[1] + m.bbmax[1]) / 2);
+    d.rcm[2] = float(m.bbmax[2] + p.rcm_height);
+    {
+        // surface faces in colour-major order, as slots
+        std::vector<uint4> fr(std::max(1, m.F));
+        for (int q = 0; q < m.F; ++q) {
+            const int f = m.forder[q];
+            const int a = sc.slot_of[m.face[3 * f]], b = sc.slot_of[m.face[3 * f + 1]];
+            const int c = sc.slot_of[m.face[3 * f + 2]], o = sc.slot_of[m.fopp[f]];
+            fr[q] = make_uint4(uint32_t(a) | (uint32_t(b) << 16), uint32_t(c) | (uint32_t(o) << 16), 0u, 0u);
+        }
+        uint4* d_fr;
+        int* d_fo;
+        FFSRL_CUDA(s->upload(&d_fr, fr.data(), fr.size()));
+        FFSRL_CUDA(s->upload(&d_fo, m.fcol_off.data(), m.fcol_off.size()));
+        d.F = m.F;
+        d.n_fcol = m.n_fcol;
+        d.frec = d_fr;
+        d.fcol_off = d_fo;
+    }
     const double min_len = 1e-12 * m.extent;
     d.min_len2 = float(min_len * min_len);
     return FFSRL_OK;
@@ -625,6 +657,12 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
     S.w_d = p.w_d;
     S.w_s = p.w_s;
     S.success_dist = p.success_dist;
+    S.tool_model = p.tool_model;
+    S.shaft_radius = float(p.shaft_radius);
+    S.clamp_length = float(p.clamp_length);
+    S.clamp_radius = float(p.clamp_radius);
+    S.clamp_cos = float(std::cos(p.clamp_angle));
+    S.clamp_sin = float(std::sin(p.clamp_angle));
 
     // Launch groups: one per shared-memory size class, i.e. by how many CTAs of
     // a mesh's resident configuration fit on one SM (3 or more, 2, 1, or none:
@@ -643,7 +681,7 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
     // global-memory variant (class 0).
     std::vector<int> part_slots(md.size(), 0);
     std::vector<size_t> cl_smem(md.size(), 0);
-    if (!(p.schedule_flags & FFSRL_SCHED_NO_CLUSTER)) {
+    if (!(p.schedule_flags & FFSRL_SCHED_NO_CLUSTER) && p.tool_model == FFSRL_TOOL_SPHERE) {
         for (size_t mi = 0; mi < md.size(); ++mi) {
             if (mesh_class[mi] != 0) continue;
             for (int cl : {2, 4}) {
@@ -1196,8 +1234,8 @@ int launch_warm_groups(ffsrl_sim* sim, cudaStream_t st, bool sublists, const flo
 // and the substep kernel.
 int run_substeps(ffsrl_sim* sim, int mode, const float* actions, float* obs, float* reward, uint8_t* done,
                  float threshold, int n_full, int* fallbacks, float* residual, float* feat_out, float* target_out) {
-    if (sim->params.solver != FFSRL_SOLVER_GAUSS_SEIDEL)
-        return fail(FFSRL_E_INVAL, "the warm-start and recording steps use the Gauss-Seidel solve");
+    if (sim->params.solver != FFSRL_SOLVER_GAUSS_SEIDEL || sim->params.tool_model != FFSRL_TOOL_SPHERE)
+        return fail(FFSRL_E_INVAL, "the warm-start and recording steps use the Gauss-Seidel solve and the sphere tool");
     int rc = ensure_surrogate_buffers(sim);
     if (rc) return rc;
     if (sim->params.auto_reset) FFSRL_CUDA(launch_auto_reset(sim->S, sim->stream));
@@ -1270,8 +1308,8 @@ int ffsrl_set_surrogate_envs(ffsrl_sim* sim, const uint8_t* mask_host, double th
     }
     if (!sim->has_net) return fail(FFSRL_E_INVAL, "no network installed (ffsrl_set_network)");
     if (n_full < 1) return fail(FFSRL_E_INVAL, "n_full must be >= 1");
-    if (sim->params.solver != FFSRL_SOLVER_GAUSS_SEIDEL)
-        return fail(FFSRL_E_INVAL, "the warm-start step uses the Gauss-Seidel solve");
+    if (sim->params.solver != FFSRL_SOLVER_GAUSS_SEIDEL || sim->params.tool_model != FFSRL_TOOL_SPHERE)
+        return fail(FFSRL_E_INVAL, "the warm-start step uses the Gauss-Seidel solve and the sphere tool");
     FFSRL_CUDA(cudaSetDevice(sim->device));
     int rc = ensure_surrogate_buffers(sim);
     if (rc) return rc;
@@ -1377,6 +1415,10 @@ int ffsrl_get_mesh_table(const ffsrl_sim* sim, int32_t mesh, int32_t which, int3
     case 7: src = &m.ecol_off; break;
     case 8: src = &m.tcol_off; break;
     case 9: src = &m.top; break;
+    case 10: src = &m.face; break;
+    case 11: src = &m.fopp; break;
+    case 12: src = &m.forder; break;
+    case 13: src = &m.fcol_off; break;
     default: return fail(FFSRL_E_INVAL, "unknown table");
     }
     *count = int64_t(src->size());

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <random>
+#include <tuple>
 
 #include "../../include/ffsrl.h"
 
@@ -168,6 +169,36 @@ int build_host_mesh(int V, int T, const double* rest, const double* inv_mass,
 
     for (int i = 0; i < V; ++i)
         if (rest[3 * i + 2] == m.bbmax[2]) m.top.push_back(i);
+
+    // Surface faces: every tet's four faces as sorted triples with the
+    // opposite vertex; triples that occur once and have a free vertex.
+    static const int FA[4][4] = {{1, 2, 3, 0}, {0, 2, 3, 1}, {0, 1, 3, 2}, {0, 1, 2, 3}};
+    std::vector<std::array<int32_t, 4>> fr(4 * size_t(T));
+    for (int t = 0; t < T; ++t)
+        for (int k = 0; k < 4; ++k) {
+            std::array<int32_t, 3> v = {m.tet[4 * t + FA[k][0]], m.tet[4 * t + FA[k][1]], m.tet[4 * t + FA[k][2]]};
+            std::sort(v.begin(), v.end());
+            fr[4 * t + k] = {v[0], v[1], v[2], m.tet[4 * t + FA[k][3]]};
+        }
+    std::sort(fr.begin(), fr.end(), [](const std::array<int32_t, 4>& a, const std::array<int32_t, 4>& b) {
+        return std::tie(a[0], a[1], a[2]) < std::tie(b[0], b[1], b[2]);
+    });
+    for (size_t q = 0; q < fr.size();) {
+        size_t n = 1;
+        while (q + n < fr.size() && fr[q + n][0] == fr[q][0] && fr[q + n][1] == fr[q][1] && fr[q + n][2] == fr[q][2]) ++n;
+        const auto& r = fr[q];
+        if (n == 1 && (m.inv_mass[r[0]] > 0 || m.inv_mass[r[1]] > 0 || m.inv_mass[r[2]] > 0)) {
+            m.face.insert(m.face.end(), {r[0], r[1], r[2]});
+            m.fopp.push_back(r[3]);
+        }
+        q += n;
+    }
+    m.F = int(m.fopp.size());
+    if (m.F > 0) {
+        rc = colour_first_fit<3>(m.F, m.face.data(), V, m.fcolor, m.n_fcol);
+        if (rc != FFSRL_OK) { err = "more than 256 face colours needed"; return rc; }
+    }
+    colour_major(m.fcolor, m.n_fcol, m.forder, m.fcol_off);
     return FFSRL_OK;
 }
 

@@ -27,6 +27,12 @@ struct HostMesh {
     std::vector<int32_t> eorder, torder;      // colour-major position -> constraint
     std::vector<int32_t> ecol_off, tcol_off;  // [n_col + 1]
     std::vector<int32_t> top;                 // ascending ids with z == max z
+    // surface faces (faces of exactly one tet with a free vertex), ascending
+    // by sorted vertex triple, for the grasper collision; colour-major order
+    int F = 0, n_fcol = 0;
+    std::vector<int32_t> face;                // [F][3] ascending vertex ids
+    std::vector<int32_t> fopp;                // [F] fourth vertex of the face's tet
+    std::vector<int32_t> fcolor, forder, fcol_off;
     double bbmin[3] = {0, 0, 0}, bbmax[3] = {0, 0, 0};
     double extent = 0;
 };

@@ -47,6 +47,13 @@ struct MeshDev {
     int parts;                        // segments per colour (CTAs of a cluster holding one env)
     int part_slots;                   // slots per part, a multiple of 32 (parts > 1)
     const float* inv_ncons;           // [V] 1 / (constraints containing the slot's vertex), slot order
+    // surface faces for the grasper: record {slot a | slot b << 16, slot c | slot of the
+    // opposite tet vertex << 16, 0, 0} in colour-major order, colour offsets
+    int F, n_fcol;
+    const uint4* frec;
+    const int* fcol_off;              // [n_fcol + 1]
+    float rcm[3];                     // remote centre of motion of the grasper
+    int pad3;
     const uint2* erec;                // [E] edge records of the stream, unpadded, stream order
     const uint4* trec;                // [T] tet records of the stream, unpadded, stream order
     double box_lo[3], box_hi[3], tool_start[3];
@@ -94,6 +101,8 @@ struct SimDev {
     double action_scale;
     int substeps, iterations, n_obs, max_steps;
     double w_l, w_d, w_s, success_dist;
+    int tool_model;           // 0 sphere, 1 grasper
+    float shaft_radius, clamp_length, clamp_radius, clamp_cos, clamp_sin;
 };
 
 // SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): the n-th output of the

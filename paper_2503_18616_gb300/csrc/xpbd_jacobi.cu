@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kJacobiThreads, 3)
         }
     }
     const float h = S.h, inv_h = S.inv_h;
-    const float hgx = h * S.gx, hgy = h * S.gy, hgz = h * S.gz;
+    const float hgx = __fmul_rn(h, S.gx), hgy = __fmul_rn(h, S.gy), hgz = __fmul_rn(h, S.gz);
     {
         const float* gx = S.x + ed.voff;
         const float* gv = S.v + ed.voff;
@@ -86,17 +86,17 @@ __global__ void __launch_bounds__(kJacobiThreads, 3)
             Px[s] = xi.x;
             Py[s] = xi.y;
             Pz[s] = xi.z;
-            if (xi.w > 0.f) {
-                xi.x += h * (gv[i] + hgx);
-                xi.y += h * (gv[stride + i] + hgy);
-                xi.z += h * (gv[2 * stride + i] + hgz);
+            if (xi.w > 0.f) {   // rounding spelled out, as in the single-CTA kernel
+                xi.x = __fmaf_rn(h, __fadd_rn(gv[i], hgx), xi.x);
+                xi.y = __fmaf_rn(h, __fadd_rn(gv[stride + i], hgy), xi.y);
+                xi.z = __fmaf_rn(h, __fadd_rn(gv[2 * stride + i], hgz), xi.z);
             }
             X[s] = xi;
         }
     }
     __syncthreads();
     const float cx = float(s_tool[0]), cy = float(s_tool[1]), cz = float(s_tool[2]);
-    const float rad = S.radius, rad2 = rad * rad;
+    const float rad = S.radius, rad2 = __fmul_rn(rad, rad);
     const float at_d = ed.alpha_d, at_v = S.alpha_v;
     float* lam = S.lambda ? S.lambda + ed.loff : nullptr;   // edges at [0, E), tets at [E, E + T)
 
@@ -161,19 +161,19 @@ __global__ void __launch_bounds__(kJacobiThreads, 3)
                 }
                 continue;
             }
-            const float dx = xi.x - cx, dy = xi.y - cy, dz = xi.z - cz;
-            const float l2 = dx * dx + dy * dy + dz * dz;
+            const float dx = __fsub_rn(xi.x, cx), dy = __fsub_rn(xi.y, cy), dz = __fsub_rn(xi.z, cz);
+            const float l2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
             if (l2 < rad2) {
                 const float len = sqrtf(l2);
                 if (len > 0.f) {
                     const float f = __fdividef(rad, len);
-                    xi.x = cx + f * dx;
-                    xi.y = cy + f * dy;
-                    xi.z = cz + f * dz;
+                    xi.x = __fmaf_rn(f, dx, cx);
+                    xi.y = __fmaf_rn(f, dy, cy);
+                    xi.z = __fmaf_rn(f, dz, cz);
                 } else {
                     xi.x = cx;
                     xi.y = cy;
-                    xi.z = cz + rad;
+                    xi.z = __fadd_rn(cz, rad);
                 }
                 if (last) {
                     const int i = M.vert_of[s];
@@ -181,13 +181,15 @@ __global__ void __launch_bounds__(kJacobiThreads, 3)
                 }
             }
             if (!last) {
-                const float vx = (xi.x - Px[s]) * inv_h, vy = (xi.y - Py[s]) * inv_h, vz = (xi.z - Pz[s]) * inv_h;
+                const float vx = __fmul_rn(__fsub_rn(xi.x, Px[s]), inv_h),
+                            vy = __fmul_rn(__fsub_rn(xi.y, Py[s]), inv_h),
+                            vz = __fmul_rn(__fsub_rn(xi.z, Pz[s]), inv_h);
                 Px[s] = xi.x;
                 Py[s] = xi.y;
                 Pz[s] = xi.z;
-                xi.x += h * (vx + hgx);
-                xi.y += h * (vy + hgy);
-                xi.z += h * (vz + hgz);
+                xi.x = __fmaf_rn(h, __fadd_rn(vx, hgx), xi.x);
+                xi.y = __fmaf_rn(h, __fadd_rn(vy, hgy), xi.y);
+                xi.z = __fmaf_rn(h, __fadd_rn(vz, hgz), xi.z);
             }
             X[s] = xi;
         }
@@ -203,9 +205,9 @@ __global__ void __launch_bounds__(kJacobiThreads, 3)
         ox[i] = xi.x;
         ox[stride + i] = xi.y;
         ox[2 * stride + i] = xi.z;
-        ov[i] = (xi.x - Px[s]) * inv_h;
-        ov[stride + i] = (xi.y - Py[s]) * inv_h;
-        ov[2 * stride + i] = (xi.z - Pz[s]) * inv_h;
+        ov[i] = __fmul_rn(__fsub_rn(xi.x, Px[s]), inv_h);
+        ov[stride + i] = __fmul_rn(__fsub_rn(xi.y, Py[s]), inv_h);
+        ov[2 * stride + i] = __fmul_rn(__fsub_rn(xi.z, Pz[s]), inv_h);
         bad |= !(isfinite(xi.x) && isfinite(xi.y) && isfinite(xi.z));
     }
     if (bad) atomicOr(&S.err[env], kErrNonFinite);

@@ -25,6 +25,7 @@
 #include <cstdint>
 
 #include "xpbd_device.cuh"
+#include "xpbd_grasper.cuh"
 #include "xpbd_launch.h"
 #include "xpbd_project.cuh"
 
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(SUB * ENVS, min_ctas_per_sm(SUB * ENVS))
     }
 
     const float h = S.h, inv_h = S.inv_h;
-    const float hgx = h * S.gx, hgy = h * S.gy, hgz = h * S.gz;
+    const float hgx = __fmul_rn(h, S.gx), hgy = __fmul_rn(h, S.gy), hgz = __fmul_rn(h, S.gz);
     if (active) {
         // Load the state (vertex order, coalesced) into slot order and predict
         // for the first substep (Algorithm 1: v~ = v + h g, x~ = x + h v~).
@@ -180,10 +181,10 @@ __global__ void __launch_bounds__(SUB * ENVS, min_ctas_per_sm(SUB * ENVS))
             Px[s] = xi.x;
             Py[s] = xi.y;
             Pz[s] = xi.z;
-            if (xi.w > 0.f) {
-                xi.x += h * (gv[i] + hgx);
-                xi.y += h * (gv[stride + i] + hgy);
-                xi.z += h * (gv[2 * stride + i] + hgz);
+            if (xi.w > 0.f) {   // rounding spelled out: the same bits in every kernel instantiation
+                xi.x = __fmaf_rn(h, __fadd_rn(gv[i], hgx), xi.x);
+                xi.y = __fmaf_rn(h, __fadd_rn(gv[stride + i], hgy), xi.y);
+                xi.z = __fmaf_rn(h, __fadd_rn(gv[2 * stride + i], hgz), xi.z);
             }
             X[s] = xi;
         }
@@ -191,7 +192,14 @@ __global__ void __launch_bounds__(SUB * ENVS, min_ctas_per_sm(SUB * ENVS))
     __syncthreads();
 
     const float cx = float(s_tool[el][0]), cy = float(s_tool[el][1]), cz = float(s_tool[el][2]);
-    const float r = S.radius, r2 = r * r;
+    const bool grasper = S.tool_model == 1;
+    const float r = grasper ? 0.f : S.radius, r2 = __fmul_rn(r, r);   // the grasper replaces the sphere
+    // the grasper's capsules (the tool holds still through the step), built
+    // once per env in shared memory
+    __shared__ Capsules s_caps[ENVS];
+    if (grasper && st == 0 && active) grasper_capsules(S, M, s_tool[el], s_caps[el]);
+    __syncthreads();
+    const float tiny_len = sqrtf(M.min_len2);   // 1e-12 x extent: the axis crosses the face
     const float at_d = ed.alpha_d, at_v = S.alpha_v;
     float* lam = S.lambda ? S.lambda + ed.loff : nullptr;
     int k = 0;
@@ -240,12 +248,22 @@ __global__ void __launch_bounds__(SUB * ENVS, min_ctas_per_sm(SUB * ENVS))
             }
         }
         if (failed) break;
+        const bool last = sub == S.substeps - 1;
+        if (grasper) {
+            // Grasper against the surface faces, colour by colour (faces of
+            // one colour share no vertex).
+            for (int fc = 0; fc < M.n_fcol; ++fc) {
+                if (active)
+                    for (int q = M.fcol_off[fc] + st; q < M.fcol_off[fc + 1]; q += SUB)
+                        grasper_face(X, M.frec[q], s_caps[el], tiny_len, last ? bits : nullptr, M.vert_of);
+                __syncthreads();
+            }
+        }
         // Sphere-tool collision (Sec. III-A "Collisions"): a free vertex
         // closer than r to the centre moves onto the sphere along the
         // centre-to-vertex direction (straight up if it sits on the centre).
         // Except after the last substep, the same pass performs the velocity
         // update v = (x - x_prev) / h and the next substep's prediction.
-        const bool last = sub == S.substeps - 1;
         if (active) {
             for (int s = st; s < V; s += SUB) {
                 float4 xi = X[s];
@@ -257,20 +275,20 @@ __global__ void __launch_bounds__(SUB * ENVS, min_ctas_per_sm(SUB * ENVS))
                     }
                     continue;
                 }
-                const float dx = xi.x - cx, dy = xi.y - cy, dz = xi.z - cz;
-                const float l2 = dx * dx + dy * dy + dz * dz;
+                const float dx = __fsub_rn(xi.x, cx), dy = __fsub_rn(xi.y, cy), dz = __fsub_rn(xi.z, cz);
+                const float l2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
                 bool moved = false;
                 if (l2 < r2) {
                     const float len = sqrtf(l2);
                     if (len > 0.f) {
                         const float f = __fdividef(r, len);
-                        xi.x = cx + f * dx;
-                        xi.y = cy + f * dy;
-                        xi.z = cz + f * dz;
+                        xi.x = __fmaf_rn(f, dx, cx);
+                        xi.y = __fmaf_rn(f, dy, cy);
+                        xi.z = __fmaf_rn(f, dz, cz);
                     } else {
                         xi.x = cx;
                         xi.y = cy;
-                        xi.z = cz + r;
+                        xi.z = __fadd_rn(cz, r);
                     }
                     moved = true;
                     if (last) {
@@ -279,14 +297,15 @@ __global__ void __launch_bounds__(SUB * ENVS, min_ctas_per_sm(SUB * ENVS))
                     }
                 }
                 if (!last) {
-                    const float vx = (xi.x - Px[s]) * inv_h, vy = (xi.y - Py[s]) * inv_h,
-                                vz = (xi.z - Pz[s]) * inv_h;
+                    const float vx = __fmul_rn(__fsub_rn(xi.x, Px[s]), inv_h),
+                                vy = __fmul_rn(__fsub_rn(xi.y, Py[s]), inv_h),
+                                vz = __fmul_rn(__fsub_rn(xi.z, Pz[s]), inv_h);
                     Px[s] = xi.x;
                     Py[s] = xi.y;
                     Pz[s] = xi.z;
-                    xi.x += h * (vx + hgx);
-                    xi.y += h * (vy + hgy);
-                    xi.z += h * (vz + hgz);
+                    xi.x = __fmaf_rn(h, __fadd_rn(vx, hgx), xi.x);
+                    xi.y = __fmaf_rn(h, __fadd_rn(vy, hgy), xi.y);
+                    xi.z = __fmaf_rn(h, __fadd_rn(vz, hgz), xi.z);
                     moved = true;
                 }
                 if (moved) X[s] = xi;
@@ -313,9 +332,9 @@ __global__ void __launch_bounds__(SUB * ENVS, min_ctas_per_sm(SUB * ENVS))
         ox[i] = xi.x;
         ox[stride + i] = xi.y;
         ox[2 * stride + i] = xi.z;
-        ov[i] = (xi.x - Px[s]) * inv_h;
-        ov[stride + i] = (xi.y - Py[s]) * inv_h;
-        ov[2 * stride + i] = (xi.z - Pz[s]) * inv_h;
+        ov[i] = __fmul_rn(__fsub_rn(xi.x, Px[s]), inv_h);
+        ov[stride + i] = __fmul_rn(__fsub_rn(xi.y, Py[s]), inv_h);
+        ov[2 * stride + i] = __fmul_rn(__fsub_rn(xi.z, Pz[s]), inv_h);
         bad |= !(isfinite(xi.x) && isfinite(xi.y) && isfinite(xi.z));
     }
     if (bad) atomicOr(&S.err[env], kErrNonFinite);
