@@ -64,6 +64,7 @@ def _lib(precision: str = "f64") -> ctypes.CDLL:
             L.orc_sample_indices.argtypes = [U64, U64, I, I, P]
             L.orc_target_index.restype = I
             L.orc_target_index.argtypes = [U64, U64, I]
+            L.orc_env_set_clamp.argtypes = [P, D]
             L.orc_episode_seed.restype = U64
             L.orc_episode_seed.argtypes = [U64, I]
             L.orc_mesh_create.restype = P
@@ -182,6 +183,7 @@ class Params(ctypes.Structure):
         ("clamp_length", ctypes.c_double),
         ("clamp_radius", ctypes.c_double),
         ("clamp_angle", ctypes.c_double),
+        ("grasp_radius", ctypes.c_double),
     ]
 
     @classmethod
@@ -189,7 +191,7 @@ class Params(ctypes.Structure):
         p = cls()
         for name, _ in cls._fields_:
             val = d.get(name, 0) if name in ("solver", "auto_reset", "tool_model", "rcm_height", "shaft_radius",
-                                             "clamp_length", "clamp_radius", "clamp_angle") else d[name]
+                                             "clamp_length", "clamp_radius", "clamp_angle", "grasp_radius") else d[name]
             if name == "gravity":
                 p.gravity[:] = [float(g) for g in val]
             else:
@@ -396,7 +398,11 @@ class Env:
         obs_ids = out[4:4 + n_obs].copy()
         contacts = out[4 + n_obs:4 + n_obs + n_c].copy()
         return {"t": t, "target": target, "obs_ids": obs_ids, "contacts": contacts,
-                "episode": int(out[4 + n_obs + n_c])}
+                "episode": int(out[4 + n_obs + n_c]), "grasp": int(out[5 + n_obs + n_c])}
+
+    def set_clamp(self, angle: float) -> None:
+        """Grasper clamp opening (radians) from the next step on."""
+        self._L.orc_env_set_clamp(self._h, float(angle))
 
     def features(self) -> np.ndarray:
         """Features [V][15] of the next substep's predicted state."""

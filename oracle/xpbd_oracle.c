@@ -72,6 +72,14 @@
  *   R14 The per-element local optimisation the paper follows finds the
  *       face's point of least capsule distance; here that point is computed
  *       exactly (segment-triangle closest points).
+ *   R15 Grasping (Sec. III-A, dragging): the dragging point is the end of the
+ *       closed clamps, clamp_length beyond the tool point along the shaft
+ *       axis. At the start of a step, clamps closed below 3 degrees take the
+ *       free vertex nearest to it within grasp_radius (ties: lower id; kept
+ *       until the clamps open to 3 degrees or more); each substep, after the
+ *       iterations and before the face collision, a distance constraint of
+ *       stiffness 1 keeps that vertex at its grasp-time distance from the
+ *       dragging point (the tool is kinematic: only the vertex moves).
  *   R11 Optional auto-reset: an env whose step reported done starts episode
  *       k+1 at its next step, from the rest state with the draws of seed
  *       splitmix64_nth(seed, 2^40 + k+1) (seed = the one given to reset; the
@@ -563,6 +571,7 @@ typedef struct {
     int tool_model;  /* 0: sphere proxy (R6); 1: three-capsule grasper through a remote centre (R12, R13) */
     double rcm_height;                 /* remote centre of motion above the centre of the top face */
     double shaft_radius, clamp_length, clamp_radius, clamp_angle;  /* grasper capsules (R12) */
+    double grasp_radius;               /* dragging: largest distance of a grasped vertex (R15) */
 } orc_params;
 
 typedef struct orc_env {
@@ -581,6 +590,9 @@ typedef struct orc_env {
     uint64_t seed0;       /* seed given to reset (R11) */
     int episode;          /* episodes started by auto-reset since then */
     int done_prev;        /* the last step reported done */
+    REAL clamp_angle;     /* grasper: current clamp opening (R12, R15) */
+    int grasp_v;          /* grasped vertex, -1 if none (R15) */
+    REAL grasp_d0;        /* its distance to the dragging point when grasped */
     int* obs;     /* [n_obs] vertex ids */
     int n_obs;
     int target;
@@ -631,6 +643,9 @@ static int reset_state(orc_env* s, const orc_params* p, uint64_t seed, uint64_t 
     s->lo[2] = m->bbmax[2] - (REAL)p->margin_below;
     s->hi[2] = m->bbmax[2] + (REAL)p->margin_above;
     s->t = 0; s->seed = seed; s->env = env;
+    s->clamp_angle = (REAL)p->clamp_angle;
+    s->grasp_v = -1;
+    s->grasp_d0 = 0;
     s->n_obs = p->n_obs;
     int* idx = (int*)malloc(sizeof(int) * (p->n_obs > 0 ? p->n_obs : 1));
     orc_sample_indices(seed, env, m->n_top, p->n_obs, idx);
@@ -648,6 +663,9 @@ int orc_env_reset(orc_env* s, const orc_params* p, uint64_t seed, uint64_t env) 
     s->done_prev = 0;
     return reset_state(s, p, seed, env);
 }
+
+/* Grasper clamp opening for the next steps (radians). */
+void orc_env_set_clamp(orc_env* s, double angle) { s->clamp_angle = (REAL)angle; }
 
 /* Seed of episode k >= 1 started by auto-reset (R11). */
 uint64_t orc_episode_seed(uint64_t seed0, int k) { return orc_sm64(seed0, (1ULL << 40) + (uint64_t)k); }
@@ -786,20 +804,33 @@ REAL orc_closest_segment_triangle(const REAL* q0, const REAL* q1, const REAL* a,
  * remote centre of motion to c, and two clamps from c at angles +alpha and
  * -alpha from the shaft axis in the plane of the axis and the world x axis
  * (y if the axis is along x). seg [3][2][3], radius [3]. */
-static void grasper_capsules(const orc_env* s, const orc_params* p, REAL seg[3][2][3], REAL* radius) {
+static void grasper_frame(const orc_env* s, const orc_params* p, REAL* rcm, REAL* d, REAL* u) {
     const orc_mesh* m = s->m;
-    const REAL rcm[3] = {(m->bbmin[0] + m->bbmax[0]) / 2, (m->bbmin[1] + m->bbmax[1]) / 2,
-                         m->bbmax[2] + (REAL)p->rcm_height};
-    REAL d[3];
+    rcm[0] = (m->bbmin[0] + m->bbmax[0]) / 2;
+    rcm[1] = (m->bbmin[1] + m->bbmax[1]) / 2;
+    rcm[2] = m->bbmax[2] + (REAL)p->rcm_height;
     vsub(s->c, rcm, d);
     const REAL L = vnorm(d);
     if (L > 0) { d[0] /= L; d[1] /= L; d[2] /= L; }
     else { d[0] = 0; d[1] = 0; d[2] = -1; }
-    REAL u[3] = {1 - d[0] * d[0], -d[0] * d[1], -d[0] * d[2]};   /* e_x minus its part along d */
+    u[0] = 1 - d[0] * d[0]; u[1] = -d[0] * d[1]; u[2] = -d[0] * d[2];   /* e_x minus its part along d */
     if (vnorm(u) < (REAL)1e-6) { u[0] = -d[1] * d[0]; u[1] = 1 - d[1] * d[1]; u[2] = -d[1] * d[2]; }
     const REAL lu = vnorm(u);
     u[0] /= lu; u[1] /= lu; u[2] /= lu;
-    const REAL ca = cos((REAL)p->clamp_angle), sa = sin((REAL)p->clamp_angle), lc = (REAL)p->clamp_length;
+}
+
+/* The dragging point: the end of the closed clamps, clamp_length along the
+ * shaft axis beyond the tool point (R15). */
+static void dragging_point(const orc_env* s, const orc_params* p, REAL* out) {
+    REAL rcm[3], d[3], u[3];
+    grasper_frame(s, p, rcm, d, u);
+    for (int k = 0; k < 3; ++k) out[k] = s->c[k] + (REAL)p->clamp_length * d[k];
+}
+
+static void grasper_capsules(const orc_env* s, const orc_params* p, REAL seg[3][2][3], REAL* radius) {
+    REAL rcm[3], d[3], u[3];
+    grasper_frame(s, p, rcm, d, u);
+    const REAL ca = cos(s->clamp_angle), sa = sin(s->clamp_angle), lc = (REAL)p->clamp_length;
     for (int k = 0; k < 3; ++k) {
         seg[0][0][k] = rcm[k]; seg[0][1][k] = s->c[k];
         seg[1][0][k] = s->c[k]; seg[1][1][k] = s->c[k] + lc * (ca * d[k] + sa * u[k]);
@@ -872,6 +903,42 @@ static void collide_grasper(orc_env* s, const orc_params* p, int record) {
             if (hit[i]) s->contacts[s->n_contacts++] = i;
         free(hit);
     }
+}
+
+/* Grasp state at the start of a step (R15): with the clamps closed below 3
+ * degrees an ungrasped tool takes the free vertex nearest to the dragging
+ * point within grasp_radius (ties: the lower id) and keeps its distance;
+ * opening the clamps to 3 degrees or more releases it. */
+static void update_grasp(orc_env* s, const orc_params* p) {
+    const orc_mesh* m = s->m;
+    const REAL closed = (REAL)(3.0 * 3.14159265358979323846 / 180.0);
+    if (!(s->clamp_angle < closed)) { s->grasp_v = -1; return; }
+    if (s->grasp_v >= 0) return;
+    REAL g[3];
+    dragging_point(s, p, g);
+    int best = -1;
+    REAL bd = 0;
+    for (int i = 0; i < m->V; ++i) {
+        if (m->w[i] == 0) continue;
+        const REAL d = dist3(&s->x[3 * i], g);
+        if (d < (REAL)p->grasp_radius && (best < 0 || d < bd)) { best = i; bd = d; }
+    }
+    s->grasp_v = best;
+    s->grasp_d0 = bd;
+}
+
+/* Dragging constraint (R15): distance d0 between the grasped vertex and the
+ * dragging point, stiffness 1, the tool kinematic: the vertex moves by -C n. */
+static void project_grasp(orc_env* s, const orc_params* p) {
+    if (s->grasp_v < 0) return;
+    REAL g[3], dv[3];
+    dragging_point(s, p, g);
+    REAL* x = &s->x[3 * s->grasp_v];
+    vsub(x, g, dv);
+    const REAL len = vnorm(dv);
+    if (!(len > 0)) return;
+    const REAL C = len - s->grasp_d0;
+    for (int k = 0; k < 3; ++k) x[k] -= C * dv[k] / len;
 }
 
 /* One Jacobi iteration, the paper's own parallel scheme (Sec. III-A): every
@@ -949,8 +1016,12 @@ static void substep(orc_env* s, const orc_params* p, REAL h, REAL alpha_d, int r
                                 w4, m->V0[t], at_v, &s->lam_t[t]);
             }
     }
-    if (p->tool_model == 1) collide_grasper(s, p, record);
-    else collide_sphere(s, (REAL)p->radius, record);
+    if (p->tool_model == 1) {
+        project_grasp(s, p);
+        collide_grasper(s, p, record);
+    } else {
+        collide_sphere(s, (REAL)p->radius, record);
+    }
     /* velocity update */
     for (int i = 0; i < 3 * m->V; ++i) s->v[i] = (s->x[i] - s->xprev[i]) / h;
 }
@@ -981,6 +1052,7 @@ int orc_env_step(orc_env* s, const orc_params* p, const double* action, double a
     }
     REAL h = (REAL)(p->dt / p->substeps);
     REAL ad = (REAL)(alpha_d >= 0 ? alpha_d : p->alpha_d);
+    if (p->tool_model == 1) update_grasp(s, p);
     for (int sub = 0; sub < p->substeps; ++sub) substep(s, p, h, ad, sub == p->substeps - 1);
     /* observation: tool centre, then the sampled surface vertices */
     if (obs) {
@@ -1036,6 +1108,7 @@ void orc_env_get_ints(const orc_env* s, int* out) {
     for (int q = 0; q < s->n_obs; ++q) out[4 + q] = s->obs[q];
     for (int q = 0; q < s->n_contacts; ++q) out[4 + s->n_obs + q] = s->contacts[q];
     out[4 + s->n_obs + s->n_contacts] = s->episode;
+    out[5 + s->n_obs + s->n_contacts] = s->grasp_v;
 }
 void orc_env_get_tool_box(const orc_env* s, double* lo, double* hi) {
     for (int k = 0; k < 3; ++k) { lo[k] = (double)s->lo[k]; hi[k] = (double)s->hi[k]; }

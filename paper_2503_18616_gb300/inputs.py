@@ -168,6 +168,7 @@ def default_params(spacing: float = CELL, **over) -> dict:
         "clamp_length": 2.0 * spacing,
         "clamp_radius": 0.25 * spacing,
         "clamp_angle": math.radians(10.0),
+        "grasp_radius": 0.5 * spacing,   # dragging: nearest free vertex within this of the clamp end
     }
     p.update(over)
     return p

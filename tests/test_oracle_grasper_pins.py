@@ -3,7 +3,9 @@
 two clamps) collide with the surface faces of the tissue.
 
 The closest-point routine is checked against brute force (dense sampling of
-both the segment and the triangle); a pushed face moves out of the capsule
+both the segment and the triangle); grasping takes the nearest free vertex
+in reach (brute force), keeps it at its grasp distance from the lifted tool
+and releases it when the clamps open; a pushed face moves out of the capsule
 and repeated pushes converge to its surface; a tool pressed into the tissue
 displaces it away from the tool; a tool far from the tissue leaves it exactly
 as the sphere-tool step does; the surface faces of a grid block are counted
@@ -183,3 +185,65 @@ def test_pushed_face_ends_on_the_capsule_surface():
         e.step(np.zeros(3))
     assert dists(e.state()[0], c0)[i] == pytest.approx(r, rel=1e-3)
     assert np.array_equal(e.state()[0][:3], rest[:3])
+
+
+def _vertical_tool_env(**over):
+    """9x9x5 block, grasper straight above the centre (its shaft is vertical,
+    so the dragging point is the tool point minus clamp_length in z)."""
+    rest, w, tets = inputs.grid_block(9, 9, 5)
+    m = oracle.Mesh(rest, w, tets)
+    p = params(tool_model=1, **over)
+    e = oracle.Env(m, p)
+    e.reset(2)
+    return m, rest, w, p, e
+
+
+def test_grasp_takes_the_nearest_free_vertex_within_the_radius():
+    m, rest, w, p, e = _vertical_tool_env(clamp_angle=math.radians(1.0), grasp_radius=3e-3)
+    c = e.state()[2].copy()
+    c[2] = rest[:, 2].max() + p["clamp_length"] + 0.4e-3   # clamp end just above the top centre
+    c[:2] = [0.0, 0.0]
+    e.set_state(c=c)
+    x0 = e.state()[0].copy()
+    e.step(np.zeros(3))
+    g = c - np.array([0.0, 0.0, p["clamp_length"]])
+    d = np.linalg.norm(x0 - g, axis=1)
+    d[w == 0] = np.inf
+    expect = int(np.argmin(d)) if d.min() < p["grasp_radius"] else -1
+    assert expect >= 0 and e.ints()["grasp"] == expect
+
+
+def test_grasped_vertex_follows_the_lifted_tool_at_its_grasp_distance():
+    m, rest, w, p, e = _vertical_tool_env(clamp_angle=math.radians(1.0), grasp_radius=3e-3,
+                                          shaft_radius=0.0, clamp_radius=0.0)
+    c = e.state()[2].copy()
+    c[2] = rest[:, 2].max() + p["clamp_length"] + 0.5e-3
+    e.set_state(c=c)
+    x0 = e.state()[0].copy()
+    e.step(np.zeros(3))
+    v = e.ints()["grasp"]
+    assert v >= 0
+    d0 = np.linalg.norm(x0[v] - (c - np.array([0.0, 0.0, p["clamp_length"]])))
+    z_before = e.state()[0][v, 2]
+    for _ in range(5):
+        e.step(np.array([0.0, 0.0, 1.0]))   # lift
+        x, _, ct = e.state()
+        g = ct - np.array([0.0, 0.0, p["clamp_length"]])
+        assert abs(np.linalg.norm(x[v] - g) - d0) < 1e-12
+        assert e.ints()["grasp"] == v
+    assert e.state()[0][v, 2] > z_before + 5e-3   # the tissue is lifted with the tool
+    e.set_clamp(math.radians(10.0))              # open: released at the next step
+    e.step(np.zeros(3))
+    assert e.ints()["grasp"] == -1
+
+
+def test_no_grasp_with_open_clamps_or_nothing_in_reach():
+    m, rest, w, p, e = _vertical_tool_env(grasp_radius=3e-3)   # clamps open at 10 degrees
+    c = e.state()[2].copy()
+    c[2] = rest[:, 2].max() + p["clamp_length"] + 0.5e-3
+    e.set_state(c=c)
+    e.step(np.zeros(3))
+    assert e.ints()["grasp"] == -1
+    m, rest, w, p, e = _vertical_tool_env(clamp_angle=math.radians(1.0), grasp_radius=1e-4)
+    e.step(np.zeros(3))                           # the clamp end starts 1.25 mm above the surface
+    assert e.ints()["grasp"] == -1
