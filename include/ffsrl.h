@@ -94,7 +94,11 @@ typedef struct {
     double shaft_radius;      /* grasper: shaft capsule radius */
     double clamp_length;      /* grasper: clamp capsule length */
     double clamp_radius;      /* grasper: clamp capsule radius */
-    double clamp_angle;       /* grasper: clamp opening angle from the shaft axis, radians */
+    double clamp_angle;       /* grasper: clamp opening angle from the shaft axis at reset, radians */
+    double grasp_radius;      /* grasper: clamps closed below 3 degrees grasp the nearest free
+                                 vertex within this distance of the dragging point (the clamp end,
+                                 clamp_length beyond the tool point along the shaft) and keep it at
+                                 its grasp-time distance (Sec. III-A dragging); opening releases */
 } ffsrl_params;
 
 #define FFSRL_TOOL_SPHERE 0
@@ -267,6 +271,16 @@ int ffsrl_step_surrogate(ffsrl_sim* sim, const float* actions_dev, float* obs_de
  * mode. */
 int ffsrl_set_surrogate_envs(ffsrl_sim* sim, const uint8_t* mask_host, double threshold, int32_t n_full,
                              int32_t* fallbacks_dev);
+
+/* Grasper clamp openings (radians) from the next step on: angles_dev [n_env]
+ * float32 device array, read by a kernel on the sim's stream (asynchronous:
+ * keep it valid until the stream has passed the call). Below 3
+ * degrees the clamps count as closed and grasp (ffsrl_params.grasp_radius).
+ * Reset restores ffsrl_params.clamp_angle. FFSRL_E_INVAL without the grasper. */
+int ffsrl_set_clamp_angles(ffsrl_sim* sim, const float* angles_dev);
+
+/* Grasped vertex of every env (-1: none) into grasp_host [n_env]; synchronises. */
+int ffsrl_get_grasp(ffsrl_sim* sim, int32_t* grasp_host);
 
 /* Plain step with `n_full` iterations per substep that records training data:
  * features_dev [substeps][rows][16] (features of every vertex row at each

@@ -216,7 +216,7 @@ int check_params(const ffsrl_params& p) {
         return fail(FFSRL_E_INVAL, "tool_model must be FFSRL_TOOL_SPHERE or FFSRL_TOOL_GRASPER");
     if (p.tool_model == FFSRL_TOOL_GRASPER) {
         if (!(p.shaft_radius >= 0) || !(p.clamp_length >= 0) || !(p.clamp_radius >= 0) ||
-            !std::isfinite(p.rcm_height) || !std::isfinite(p.clamp_angle))
+            !(p.grasp_radius >= 0) || !std::isfinite(p.rcm_height) || !std::isfinite(p.clamp_angle))
             return fail(FFSRL_E_INVAL, "grasper sizes must be finite and >= 0");
         if (p.solver != FFSRL_SOLVER_GAUSS_SEIDEL)
             return fail(FFSRL_E_INVAL, "the grasper runs with the Gauss-Seidel solver");
@@ -661,8 +661,13 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
     S.shaft_radius = float(p.shaft_radius);
     S.clamp_length = float(p.clamp_length);
     S.clamp_radius = float(p.clamp_radius);
-    S.clamp_cos = float(std::cos(p.clamp_angle));
-    S.clamp_sin = float(std::sin(p.clamp_angle));
+    S.clamp_angle0 = float(p.clamp_angle);
+    S.clamp_cs0 = make_float2(float(std::cos(double(S.clamp_angle0))), float(std::sin(double(S.clamp_angle0))));
+    FFSRL_CUDA(s->alloc(&S.clamp_cs, n_env));
+    S.grasp_radius = float(p.grasp_radius);
+    FFSRL_CUDA(s->alloc(&S.clamp_angle, n_env));
+    FFSRL_CUDA(s->alloc(&S.grasp_v, n_env));
+    FFSRL_CUDA(s->alloc(&S.grasp_d0, n_env));
 
     // Launch groups: one per shared-memory size class, i.e. by how many CTAs of
     // a mesh's resident configuration fit on one SM (3 or more, 2, 1, or none:
@@ -1340,6 +1345,22 @@ int ffsrl_set_surrogate_envs(ffsrl_sim* sim, const uint8_t* mask_host, double th
     sim->mix_n_full = n_full;
     sim->mix_fallbacks = fallbacks_dev;
     sim->mixed = true;
+    return FFSRL_OK;
+}
+
+int ffsrl_set_clamp_angles(ffsrl_sim* sim, const float* angles_dev) {
+    if (!sim || !angles_dev) return fail(FFSRL_E_INVAL, "sim and angles_dev must be non-NULL");
+    if (sim->params.tool_model != FFSRL_TOOL_GRASPER) return fail(FFSRL_E_INVAL, "the sim has no grasper tool");
+    FFSRL_CUDA(cudaSetDevice(sim->device));
+    FFSRL_CUDA(launch_set_clamp(sim->S, angles_dev, sim->stream));
+    return FFSRL_OK;
+}
+
+int ffsrl_get_grasp(ffsrl_sim* sim, int32_t* grasp_host) {
+    if (!sim || !grasp_host) return fail(FFSRL_E_INVAL, "sim and grasp_host must be non-NULL");
+    FFSRL_CUDA(cudaSetDevice(sim->device));
+    FFSRL_CUDA(cudaStreamSynchronize(sim->stream));
+    FFSRL_CUDA(cudaMemcpy(grasp_host, sim->S.grasp_v, size_t(sim->n_env) * sizeof(int32_t), cudaMemcpyDeviceToHost));
     return FFSRL_OK;
 }
 

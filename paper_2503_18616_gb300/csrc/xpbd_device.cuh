@@ -102,7 +102,14 @@ struct SimDev {
     int substeps, iterations, n_obs, max_steps;
     double w_l, w_d, w_s, success_dist;
     int tool_model;           // 0 sphere, 1 grasper
-    float shaft_radius, clamp_length, clamp_radius, clamp_cos, clamp_sin;
+    float shaft_radius, clamp_length, clamp_radius;
+    float clamp_angle0;       // clamp opening at reset (radians)
+    float2 clamp_cs0;         // its cosine and sine
+    float grasp_radius;
+    float* clamp_angle;       // [n_env] current clamp opening (radians)
+    float2* clamp_cs;         // [n_env] its cosine and sine (kept beside it, so the step needs no trigonometry)
+    int* grasp_v;             // [n_env] grasped vertex or -1
+    float* grasp_d0;          // [n_env] its grasp-time distance to the dragging point
 };
 
 // SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): the n-th output of the

@@ -46,18 +46,32 @@ __device__ __forceinline__ float3 f3bary(const float* w, float3 a, float3 b, flo
                        fa(fa(fm(w[0], a.z), fm(w[1], b.z)), fm(w[2], c.z)));
 }
 
-// Capsules of the grasper at tool point c.
-__device__ __forceinline__ void grasper_capsules(const SimDev& S, const MeshDev& M, const double* c, Capsules& K) {
+// Unit shaft axis from the remote centre towards tool point c.
+__device__ __forceinline__ float3 grasper_axis(const MeshDev& M, float3 cc) {
+    const float3 rcm = make_float3(M.rcm[0], M.rcm[1], M.rcm[2]);
+    const float3 d = f3sub(cc, rcm);
+    const float L = sqrtf(f3dot(d, d));
+    return L > 0.f ? make_float3(d.x / L, d.y / L, d.z / L) : make_float3(0.f, 0.f, -1.f);
+}
+
+// The dragging point: the end of the closed clamps, clamp_length beyond the
+// tool point along the shaft axis.
+__device__ __forceinline__ float3 grasper_drag_point(const SimDev& S, const MeshDev& M, const double* c) {
+    const float3 cc = make_float3(float(c[0]), float(c[1]), float(c[2]));
+    return f3axpy(S.clamp_length, grasper_axis(M, cc), cc);
+}
+
+// Capsules of the grasper at tool point c with clamp opening cs = (cos, sin).
+__device__ __forceinline__ void grasper_capsules(const SimDev& S, const MeshDev& M, const double* c, float2 cs,
+                                                 Capsules& K) {
     const float3 rcm = make_float3(M.rcm[0], M.rcm[1], M.rcm[2]);
     const float3 cc = make_float3(float(c[0]), float(c[1]), float(c[2]));
-    float3 d = f3sub(cc, rcm);
-    const float L = sqrtf(f3dot(d, d));
-    d = L > 0.f ? make_float3(d.x / L, d.y / L, d.z / L) : make_float3(0.f, 0.f, -1.f);
+    const float3 d = grasper_axis(M, cc);
     float3 u = make_float3(fs(1.f, fm(d.x, d.x)), -fm(d.x, d.y), -fm(d.x, d.z));   // e_x minus its part along d
     if (sqrtf(f3dot(u, u)) < 1e-6f) u = make_float3(-fm(d.y, d.x), fs(1.f, fm(d.y, d.y)), -fm(d.y, d.z));
     const float lu = sqrtf(f3dot(u, u));
     u = make_float3(u.x / lu, u.y / lu, u.z / lu);
-    const float lc = S.clamp_length, ca = S.clamp_cos, sa = S.clamp_sin;
+    const float lc = S.clamp_length, ca = cs.x, sa = cs.y;
     const float3 dp = f3axpy(sa, u, f3scale(ca, d)), dm = f3axpy(-sa, u, f3scale(ca, d));
     const float3 e1 = f3axpy(lc, dp, cc), e2 = f3axpy(lc, dm, cc);
     const float3 A[3] = {rcm, cc, cc}, B[3] = {cc, e1, e2};
@@ -216,6 +230,20 @@ __device__ __forceinline__ void grasper_face(float4* X, uint4 rec, const Capsule
                 }
         }
     }
+}
+
+// Dragging constraint: the grasped vertex (slot sv) kept at distance d0 from
+// the dragging point g, stiffness 1, the tool kinematic.
+__device__ __forceinline__ void grasper_drag(float4* X, int sv, float3 g, float d0) {
+    float4 x = X[sv];
+    const float3 dv = make_float3(fs(x.x, g.x), fs(x.y, g.y), fs(x.z, g.z));
+    const float len = sqrtf(f3dot(dv, dv));
+    if (!(len > 0.f)) return;
+    const float C = fs(len, d0);
+    x.x = fs(x.x, fm(C, dv.x) / len);
+    x.y = fs(x.y, fm(C, dv.y) / len);
+    x.z = fs(x.z, fm(C, dv.z) / len);
+    X[sv] = x;
 }
 
 }  // namespace ffsrl

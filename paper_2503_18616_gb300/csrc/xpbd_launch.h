@@ -52,6 +52,7 @@ cudaError_t launch_jacobi_step(const SimDev& S, const int* env_list, int n_list,
 
 cudaError_t launch_reset(const SimDev& S, const uint8_t* mask, unsigned long long seed, cudaStream_t st);
 cudaError_t launch_auto_reset(const SimDev& S, cudaStream_t st);
+cudaError_t launch_set_clamp(const SimDev& S, const float* angles, cudaStream_t st);
 cudaError_t launch_pack(const SimDev& S, const int* pstart, float* x, float* v, cudaStream_t st);
 cudaError_t launch_unpack(const SimDev& S, const int* pstart, const float* x, const float* v, cudaStream_t st);
 

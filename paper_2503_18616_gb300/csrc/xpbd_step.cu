@@ -194,11 +194,56 @@ __global__ void __launch_bounds__(SUB * ENVS, min_ctas_per_sm(SUB * ENVS))
     const float cx = float(s_tool[el][0]), cy = float(s_tool[el][1]), cz = float(s_tool[el][2]);
     const bool grasper = S.tool_model == 1;
     const float r = grasper ? 0.f : S.radius, r2 = __fmul_rn(r, r);   // the grasper replaces the sphere
-    // the grasper's capsules (the tool holds still through the step), built
-    // once per env in shared memory
+    // Grasper: capsules, dragging point and grasp state, once per env and
+    // step (the tool holds still through the step), in shared memory.
     __shared__ Capsules s_caps[ENVS];
-    if (grasper && st == 0 && active) grasper_capsules(S, M, s_tool[el], s_caps[el]);
-    __syncthreads();
+    __shared__ float s_drag[ENVS][4];              // dragging point, grasp distance
+    __shared__ int s_grasp[ENVS];                  // grasped slot or -1
+    __shared__ unsigned long long s_key[ENVS];     // (distance bits, vertex) of the nearest candidate
+    const float closed = 3.0f * 3.14159265f / 180.0f;   // clamps below 3 degrees grasp
+    if (grasper) {
+        if (st == 0 && active) {
+            const float angle = S.clamp_angle[env];
+            grasper_capsules(S, M, s_tool[el], S.clamp_cs[env], s_caps[el]);
+            const float3 g = grasper_drag_point(S, M, s_tool[el]);
+            s_drag[el][0] = g.x;
+            s_drag[el][1] = g.y;
+            s_drag[el][2] = g.z;
+            s_key[el] = ~0ull;
+            if (!(angle < closed)) S.grasp_v[env] = -1;   // open clamps release
+        }
+        __syncthreads();
+        // Closed clamps without a grasp take the free vertex nearest to the
+        // dragging point within the grasp radius (positions at the step's
+        // start; ties: the lower vertex id).
+        if (active && S.clamp_angle[env] < closed && S.grasp_v[env] < 0) {
+            const float gx0 = s_drag[el][0], gy0 = s_drag[el][1], gz0 = s_drag[el][2];
+            const float* px = S.x + ed.voff;
+            unsigned long long best = ~0ull;
+            for (int i = st; i < V; i += SUB) {
+                if (!(M.rest_w[i].w > 0.f)) continue;
+                const float ddx = __fsub_rn(px[i], gx0), ddy = __fsub_rn(px[stride + i], gy0),
+                            ddz = __fsub_rn(px[2 * stride + i], gz0);
+                const float d = sqrtf(__fadd_rn(__fadd_rn(__fmul_rn(ddx, ddx), __fmul_rn(ddy, ddy)), __fmul_rn(ddz, ddz)));
+                if (d < S.grasp_radius) {
+                    const unsigned long long key = (static_cast<unsigned long long>(__float_as_uint(d)) << 32) | unsigned(i);
+                    best = key < best ? key : best;
+                }
+            }
+            if (best != ~0ull) atomicMin(&s_key[el], best);
+        }
+        __syncthreads();
+        if (st == 0 && active) {
+            if (s_key[el] != ~0ull) {
+                S.grasp_v[env] = int(s_key[el] & 0xffffffffull);
+                S.grasp_d0[env] = __uint_as_float(unsigned(s_key[el] >> 32));
+            }
+            const int gv = S.grasp_v[env];
+            s_grasp[el] = gv >= 0 ? int(M.slot_of[gv]) : -1;
+            s_drag[el][3] = S.grasp_d0[env];
+        }
+        __syncthreads();
+    }
     const float tiny_len = sqrtf(M.min_len2);   // 1e-12 x extent: the axis crosses the face
     const float at_d = ed.alpha_d, at_v = S.alpha_v;
     float* lam = S.lambda ? S.lambda + ed.loff : nullptr;
@@ -250,8 +295,12 @@ __global__ void __launch_bounds__(SUB * ENVS, min_ctas_per_sm(SUB * ENVS))
         if (failed) break;
         const bool last = sub == S.substeps - 1;
         if (grasper) {
-            // Grasper against the surface faces, colour by colour (faces of
-            // one colour share no vertex).
+            // Dragging constraint of the grasped vertex, then the grasper
+            // against the surface faces, colour by colour (faces of one
+            // colour share no vertex).
+            if (st == 0 && active && s_grasp[el] >= 0)
+                grasper_drag(X, s_grasp[el], make_float3(s_drag[el][0], s_drag[el][1], s_drag[el][2]), s_drag[el][3]);
+            __syncthreads();
             for (int fc = 0; fc < M.n_fcol; ++fc) {
                 if (active)
                     for (int q = M.fcol_off[fc] + st; q < M.fcol_off[fc + 1]; q += SUB)
@@ -449,6 +498,10 @@ __device__ void reset_env(const SimDev& S, int env, unsigned long long seed) {
         S.t_step[env] = 0;
         S.seed[env] = seed;
         S.n_contacts[env] = 0;
+        S.clamp_angle[env] = S.clamp_angle0;
+        S.clamp_cs[env] = S.clamp_cs0;
+        S.grasp_v[env] = -1;
+        S.grasp_d0[env] = 0.f;
     }
 }
 
@@ -594,6 +647,20 @@ cudaError_t configure_step(const StepConfig& c, size_t smem_bytes) {
 
 cudaError_t launch_reset(const SimDev& S, const uint8_t* mask, unsigned long long seed, cudaStream_t st) {
     reset_kernel<<<S.n_env, 256, 0, st>>>(S, mask, seed);
+    return cudaGetLastError();
+}
+
+// New clamp openings: the angle and its cosine and sine, per env.
+__global__ void clamp_kernel(SimDev S, const float* angles) {
+    const int env = blockIdx.x * blockDim.x + threadIdx.x;
+    if (env >= S.n_env) return;
+    const float a = angles[env];
+    S.clamp_angle[env] = a;
+    S.clamp_cs[env] = make_float2(cosf(a), sinf(a));
+}
+
+cudaError_t launch_set_clamp(const SimDev& S, const float* angles, cudaStream_t st) {
+    clamp_kernel<<<(S.n_env + 255) / 256, 256, 0, st>>>(S, angles);
     return cudaGetLastError();
 }
 

@@ -31,7 +31,7 @@ EXPORTS = ["ffsrl_create", "ffsrl_reset", "ffsrl_step", "ffsrl_step_host", "ffsr
            "ffsrl_set_state", "ffsrl_get_mesh_table", "ffsrl_get_env_ints", "ffsrl_step_noalloc",
            "ffsrl_set_network", "ffsrl_network_forward", "ffsrl_step_surrogate", "ffsrl_record_step",
            "ffsrl_get_rows", "ffsrl_get_network", "ffsrl_network_gradient", "ffsrl_train_network",
-           "ffsrl_set_surrogate_envs"]
+           "ffsrl_set_surrogate_envs", "ffsrl_set_clamp_angles", "ffsrl_get_grasp"]
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
 NET_PARAMS = 64 * 15 + 64 + 64 * 64 + 64 + 3 * 64 + 3   # FFSRL_NET_PARAMS
@@ -62,7 +62,8 @@ class ffsrl_params(ctypes.Structure):
                 ("schedule_flags", ctypes.c_int32), ("solver", ctypes.c_int32), ("auto_reset", ctypes.c_int32),
                 ("tool_model", ctypes.c_int32), ("reserved", ctypes.c_int32), ("rcm_height", ctypes.c_double),
                 ("shaft_radius", ctypes.c_double), ("clamp_length", ctypes.c_double),
-                ("clamp_radius", ctypes.c_double), ("clamp_angle", ctypes.c_double)]
+                ("clamp_radius", ctypes.c_double), ("clamp_angle", ctypes.c_double),
+                ("grasp_radius", ctypes.c_double)]
 
 SCHED_FORCE, SCHED_NO_PERMUTE, SCHED_NO_RING, SCHED_ENVS2, SCHED_ENVS4 = 1, 2, 4, 8, 16
 SCHED_SURROGATE_PIPELINE = 32
@@ -129,6 +130,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.ffsrl_network_gradient.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_float, P, P]
     L.ffsrl_train_network.restype = ctypes.c_int
     L.ffsrl_train_network.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_float, ctypes.c_float, P]
+    L.ffsrl_set_clamp_angles.restype = ctypes.c_int
+    L.ffsrl_set_clamp_angles.argtypes = [P, P]
+    L.ffsrl_get_grasp.restype = ctypes.c_int
+    L.ffsrl_get_grasp.argtypes = [P, P]
     L.ffsrl_set_surrogate_envs.restype = ctypes.c_int
     L.ffsrl_set_surrogate_envs.argtypes = [P, P, ctypes.c_double, I32, P]
     _lib = L
@@ -175,7 +180,7 @@ def make_params(d: dict, block_threads: int = 0, schedule_flags: int = 0) -> ffs
     p.solver = int(d.get("solver", 0))
     p.auto_reset = int(d.get("auto_reset", 0))
     p.tool_model = int(d.get("tool_model", 0))
-    for k in ("rcm_height", "shaft_radius", "clamp_length", "clamp_radius", "clamp_angle"):
+    for k in ("rcm_height", "shaft_radius", "clamp_length", "clamp_radius", "clamp_angle", "grasp_radius"):
         setattr(p, k, float(d.get(k, 0.0)))
     return p
 
@@ -359,6 +364,17 @@ class Sim:
         self._mix_keep = fallbacks
         _check(self._L.ffsrl_set_surrogate_envs(self._h, _np_ptr(m), float(threshold), int(n_full),
                                                 _dptr(fallbacks)))
+
+    def set_clamp_angles(self, angles) -> None:
+        """Grasper clamp openings (radians, float32 device tensor [n_env])."""
+        self._keep_clamp = angles
+        _check(self._L.ffsrl_set_clamp_angles(self._h, _dptr(angles)))
+
+    def grasp(self) -> np.ndarray:
+        """Grasped vertex of every env (-1: none)."""
+        out = np.zeros(self.n_env, np.int32)
+        _check(self._L.ffsrl_get_grasp(self._h, _np_ptr(out)))
+        return out
 
     def record_step(self, n_full: int, actions=None, features=None, targets=None, residual=None, want=True):
         """Full-solve step; returns (features [S][rows][16], targets [S][rows][4]) unless want=False."""

@@ -105,3 +105,57 @@ def test_grasper_every_schedule_gives_bit_identical_results():
             for a, b in zip(ref[4], out[4]):
                 assert np.array_equal(a, b), (flags, block)
         sim.close()
+
+
+def test_dragging_matches_oracle():
+    """Dragging constraint (Sec. III-A): four envs of a 9x9x5 block with the
+    tool placed over the top face; env 0 and 1 close their clamps within reach
+    of a vertex (grasped, then lifted), env 2 keeps them open, env 3 closes
+    them out of reach. Grasped ids must equal the oracle's; positions follow
+    the trajectory bar; opening the clamps releases."""
+    import math
+    m = grid((9, 9, 5))
+    p = P(grasp_radius=3e-3)
+    n_env = 4
+    sim = make_sim([m], p, n_env, seed=2)
+    oenvs, om = oracle_envs([m], p, n_env, seed=2)
+    top = float(m[0][:, 2].max())
+    L = p["clamp_length"]
+    c = np.array([[0.0, 0.0, top + L + 0.4e-3], [3.5e-3, -1.0e-3, top + L + 0.4e-3],
+                  [0.0, 0.0, top + L + 0.4e-3], [0.0, 0.0, top + L + 6e-3]])
+    angles = np.array([math.radians(1.0), math.radians(1.0), math.radians(10.0), math.radians(1.0)])
+    sim.set_state(tool=torch.from_numpy(c).cuda())
+    sim.set_clamp_angles(torch.from_numpy(angles.astype(np.float32)).cuda())
+    for e, oe in oenvs.items():
+        oe.set_state(c=c[e])
+        oe.set_clamp(float(np.float32(angles[e])))
+    om32 = oracle.Mesh(*m, precision="f32")
+    o32 = {}
+    for e in range(n_env):
+        o32[e] = oracle.Env(om32, p)
+        o32[e].reset(2, e)
+        o32[e].set_state(c=c[e])
+        o32[e].set_clamp(float(np.float32(angles[e])))
+    acts = [np.zeros(3)] + [np.array([0.0, 0.0, 1.0])] * 5
+    for a in acts:
+        sim.step(torch.from_numpy(np.tile(a, (n_env, 1)).astype(np.float32)).cuda())
+        for e in range(n_env):
+            oenvs[e].step(a)
+            o32[e].step(a)
+        g = sim.grasp()
+        assert [int(x) for x in g] == [oenvs[e].ints()["grasp"] for e in range(n_env)]
+    assert g[0] >= 0 and g[1] >= 0 and g[0] != g[1] and g[2] == -1 and g[3] == -1
+    x, v, tool = gpu_positions(sim)
+    off = packed_offsets([m], n_env)
+    ext = om[0].extent
+    for e in range(n_env):
+        ox = oenvs[e].state()[0]
+        floor = np.max(np.abs(o32[e].state()[0] - ox))
+        tol = max(POS_TOL * ext, 4 * floor)
+        assert np.max(np.abs(x[off[e]:off[e + 1]] - ox)) <= tol, (e, floor / ext)
+    for e in (0, 1):   # the grasped vertex went up with the tool
+        assert x[off[e] + g[e], 2] > top + 5e-3
+    sim.set_clamp_angles(torch.full((n_env,), math.radians(10.0), dtype=torch.float32).cuda())
+    sim.step(torch.zeros((n_env, 3), dtype=torch.float32).cuda())
+    assert (sim.grasp() == -1).all()
+    sim.close()
