@@ -68,7 +68,7 @@ def _lib(precision: str = "f64") -> ctypes.CDLL:
             L.orc_episode_seed.restype = U64
             L.orc_episode_seed.argtypes = [U64, I]
             L.orc_mesh_create.restype = P
-            L.orc_mesh_create.argtypes = [I, P, P, I, P, I, P, ctypes.POINTER(I)]
+            L.orc_mesh_create.argtypes = [I, P, P, I, P, I, P, D, ctypes.POINTER(I)]
             L.orc_mesh_destroy.argtypes = [P]
             L.orc_mesh_info.argtypes = [P, P]
             L.orc_mesh_faces.argtypes = [P, P]
@@ -95,6 +95,9 @@ def _lib(precision: str = "f64") -> ctypes.CDLL:
             R = D if precision == "f64" else ctypes.c_float
             L.orc_project_edge.restype = R
             L.orc_project_edge.argtypes = [P, P, R, R, R, R, P, R]
+            L.orc_mesh_conns.argtypes = [P, P]
+            L.orc_project_conn.restype = R
+            L.orc_project_conn.argtypes = [P, P, P, P, P, R, R, P, R]
             L.orc_project_tet.restype = R
             L.orc_project_tet.argtypes = [P, P, P, P, P, R, R, P]
             L.orc_mlp_forward.argtypes = [P, P, P]
@@ -242,7 +245,7 @@ def net_forward(net: "Net", feats) -> np.ndarray:
 class Mesh:
     """Constraint tables built by the oracle from a tet mesh."""
 
-    def __init__(self, rest, inv_mass, tets, edges=None, precision: str = "f64"):
+    def __init__(self, rest, inv_mass, tets, edges=None, precision: str = "f64", conn_radius: float = 0.0):
         self.precision = precision
         self._L = _lib(precision)
         rest = np.ascontiguousarray(rest, dtype=np.float64).reshape(-1, 3)
@@ -252,10 +255,10 @@ class Mesh:
         if edges is not None:
             edges = np.ascontiguousarray(edges, dtype=np.int32).reshape(-1, 2)
             h = self._L.orc_mesh_create(len(rest), _ptr(rest), _ptr(w), len(tets), _ptr(tets),
-                                        len(edges), _ptr(edges), ctypes.byref(err))
+                                        len(edges), _ptr(edges), float(conn_radius), ctypes.byref(err))
         else:
             h = self._L.orc_mesh_create(len(rest), _ptr(rest), _ptr(w), len(tets), _ptr(tets),
-                                        0, None, ctypes.byref(err))
+                                        0, None, float(conn_radius), ctypes.byref(err))
         if not h:
             raise ValueError(f"oracle mesh rejected (code {err.value})")
         self._h = ctypes.c_void_p(h)
@@ -266,6 +269,9 @@ class Mesh:
         fi = np.zeros(2, dtype=np.int32)
         self._L.orc_mesh_faces(self._h, _ptr(fi))
         self.F, self.n_fcol = int(fi[0]), int(fi[1])
+        ci = np.zeros(3, dtype=np.int32)
+        self._L.orc_mesh_conns(self._h, _ptr(ci))
+        self.C, self.n_ccol, self.n_obj = int(ci[0]), int(ci[1]), int(ci[2])
         self.rest = rest.copy()
         self.inv_mass = w.copy()
 
@@ -313,6 +319,16 @@ class Mesh:
     def forder(self): return self._ints(12, self.F)
     @property
     def fcol_off(self): return self._ints(13, self.n_fcol + 1)
+    @property
+    def conns(self): return self._ints(14, 4 * self.C).reshape(-1, 4)
+    @property
+    def corder(self): return self._ints(15, self.C)
+    @property
+    def ccol_off(self): return self._ints(16, self.n_ccol + 1)
+    @property
+    def objects(self): return self._ints(17, self.V)
+    @property
+    def conn_d0(self): return self._reals(5, self.C)
     @property
     def rest_len(self): return self._reals(0, self.E)
     @property
@@ -473,4 +489,14 @@ def project_tet(x4, w4, V0, alpha_t, lam=0.0, precision="f64"):
     w = np.array(w4, dtype=dt); L = np.array([lam], dtype=dt)
     C = _lib(precision).orc_project_tet(_ptr(xs[0]), _ptr(xs[1]), _ptr(xs[2]), _ptr(xs[3]), _ptr(w),
                                         V0, alpha_t, _ptr(L))
+    return xs, float(L[0]), float(C)
+
+
+def project_conn(x4, w4, d0, alpha_t, lam=0.0, min_len=0.0, precision="f64"):
+    """Tissue connection (R16) of vertex x4[0] to the centroid of x4[1..3]."""
+    dt = np.float64 if precision == "f64" else np.float32
+    xs = [np.array(x, dtype=dt) for x in x4]
+    w = np.array(w4, dtype=dt); L = np.array([lam], dtype=dt)
+    C = _lib(precision).orc_project_conn(_ptr(xs[0]), _ptr(xs[1]), _ptr(xs[2]), _ptr(xs[3]), _ptr(w),
+                                         d0, alpha_t, _ptr(L), min_len)
     return xs, float(L[0]), float(C)

@@ -80,6 +80,18 @@
  *       iterations and before the face collision, a distance constraint of
  *       stiffness 1 keeps that vertex at its grasp-time distance from the
  *       dragging point (the tool is kinematic: only the vertex moves).
+ *   R16 Tissue connections (Sec. III-A): a mesh may hold several objects
+ *       (the connected components of its tets, numbered by their lowest
+ *       vertex). Every vertex of a surface face (R13) of object o connects to
+ *       the surface face of a lower-numbered object whose centroid is nearest
+ *       at rest (ties: the first face in ascending triple order), if that
+ *       distance is at most conn_radius. The constraint keeps the distance
+ *       from the vertex to the face's centroid at its rest value:
+ *       C = |x_v - (x_a + x_b + x_c) / 3| - d0, gradients n at v and -n/3 at
+ *       a, b, c; a distance constraint with the distance compliance (R2).
+ *       Connections are coloured first-fit in vertex order and projected in
+ *       every iteration after the volume colours; the selection is computed
+ *       in double from the input rest positions in either build.
  *   R11 Optional auto-reset: an env whose step reported done starts episode
  *       k+1 at its next step, from the rest state with the draws of seed
  *       splitmix64_nth(seed, 2^40 + k+1) (seed = the one given to reset; the
@@ -218,6 +230,16 @@ typedef struct orc_mesh {
     int* fcolor;    /* [F] first-fit colour */
     int* forder;    /* [F] colour-major order */
     int* fcol_off;  /* [n_fcol + 1] */
+    /* tissue connections (R16) */
+    int n_obj;
+    int* obj;       /* [V] object (connected component) of each vertex */
+    int C;
+    int* conn;      /* [C][4] vertex, then the face's ascending triple */
+    REAL* cd0;      /* [C] rest distance from the vertex to the face's centroid */
+    int n_ccol;
+    int* ccolor;    /* [C] first-fit colour */
+    int* corder;    /* [C] colour-major order */
+    int* ccol_off;  /* [n_ccol + 1] */
 } orc_mesh;
 
 void orc_mesh_destroy(orc_mesh* m) {
@@ -226,6 +248,7 @@ void orc_mesh_destroy(orc_mesh* m) {
     free(m->edge); free(m->d); free(m->ecolor); free(m->tcolor);
     free(m->eorder); free(m->torder); free(m->ecol_off); free(m->tcol_off);
     free(m->top); free(m->face); free(m->fopp); free(m->fcolor); free(m->forder); free(m->fcol_off);
+    free(m->obj); free(m->conn); free(m->cd0); free(m->ccolor); free(m->corder); free(m->ccol_off);
     free(m);
 }
 
@@ -281,11 +304,87 @@ static void color_major(int n, const int* color, int nc, int* order, int* off) {
     off[nc] = p;
 }
 
+/* Objects and tissue connections (R16), from the input rest positions in
+ * double. Returns ORC_OK or an error code. */
+static int build_connections(orc_mesh* m, const double* rest, double conn_radius) {
+    const int V = m->V;
+    /* objects: connected components of the tets, labelled from the lowest
+     * unlabelled vertex upwards (so object ids follow their lowest vertex) */
+    m->obj = (int*)malloc(sizeof(int) * V);
+    int* vt_off = (int*)calloc(V + 1, sizeof(int));
+    int* vt = (int*)malloc(sizeof(int) * (4 * m->T > 0 ? 4 * m->T : 1));
+    int* stack = (int*)malloc(sizeof(int) * V);
+    for (int t = 0; t < m->T; ++t)
+        for (int k = 0; k < 4; ++k) vt_off[m->tet[4 * t + k] + 1]++;
+    for (int i = 0; i < V; ++i) vt_off[i + 1] += vt_off[i];
+    int* fill = (int*)malloc(sizeof(int) * (V > 0 ? V : 1));
+    for (int i = 0; i < V; ++i) fill[i] = vt_off[i];
+    for (int t = 0; t < m->T; ++t)
+        for (int k = 0; k < 4; ++k) vt[fill[m->tet[4 * t + k]]++] = t;
+    for (int i = 0; i < V; ++i) m->obj[i] = -1;
+    m->n_obj = 0;
+    for (int i = 0; i < V; ++i) {
+        if (m->obj[i] >= 0) continue;
+        int top = 0;
+        stack[top++] = i;
+        m->obj[i] = m->n_obj;
+        while (top > 0) {
+            const int u = stack[--top];
+            for (int q = vt_off[u]; q < vt_off[u + 1]; ++q)
+                for (int k = 0; k < 4; ++k) {
+                    const int x = m->tet[4 * vt[q] + k];
+                    if (m->obj[x] < 0) { m->obj[x] = m->n_obj; stack[top++] = x; }
+                }
+        }
+        m->n_obj++;
+    }
+    free(vt_off); free(vt); free(stack); free(fill);
+    /* connections: each vertex of a surface face, in ascending order */
+    m->conn = (int*)malloc(sizeof(int) * 4 * (V > 0 ? V : 1));
+    m->cd0 = (REAL*)malloc(sizeof(REAL) * (V > 0 ? V : 1));
+    m->C = 0;
+    unsigned char* on_face = (unsigned char*)calloc(V > 0 ? V : 1, 1);
+    for (int f = 0; f < m->F; ++f)
+        for (int k = 0; k < 3; ++k) on_face[m->face[3 * f + k]] = 1;
+    if (conn_radius > 0)
+        for (int i = 0; i < V; ++i) {
+            if (!on_face[i]) continue;
+            int best = -1;
+            double bd2 = 0;
+            for (int f = 0; f < m->F; ++f) {
+                const int* fv = &m->face[3 * f];
+                if (!(m->obj[fv[0]] < m->obj[i])) continue;
+                double d2 = 0;
+                for (int k = 0; k < 3; ++k) {
+                    const double centroid = (rest[3 * fv[0] + k] + rest[3 * fv[1] + k] + rest[3 * fv[2] + k]) / 3.0;
+                    const double dk = rest[3 * i + k] - centroid;
+                    d2 += dk * dk;
+                }
+                if (best < 0 || d2 < bd2) { best = f; bd2 = d2; }
+            }
+            if (best < 0 || !(sqrt(bd2) <= conn_radius)) continue;
+            int* c = &m->conn[4 * m->C];
+            c[0] = i;
+            c[1] = m->face[3 * best]; c[2] = m->face[3 * best + 1]; c[3] = m->face[3 * best + 2];
+            m->cd0[m->C] = (REAL)sqrt(bd2);
+            m->C++;
+        }
+    free(on_face);
+    m->ccolor = (int*)malloc(sizeof(int) * (m->C > 0 ? m->C : 1));
+    m->corder = (int*)malloc(sizeof(int) * (m->C > 0 ? m->C : 1));
+    int rc = color_first_fit(m->C, 4, m->conn, V, m->ccolor, &m->n_ccol);
+    if (rc != ORC_OK) return rc;
+    m->ccol_off = (int*)malloc(sizeof(int) * (m->n_ccol + 1));
+    color_major(m->C, m->ccolor, m->n_ccol, m->corder, m->ccol_off);
+    return ORC_OK;
+}
+
 /* Builds the mesh tables. If edges_in is given (n_edges_in pairs), it replaces
  * the edge extraction from tets (used only by pins with a single constraint).
- * Returns NULL and sets *err on failure. */
+ * conn_radius > 0 adds the tissue connections of R16. Returns NULL and sets
+ * *err on failure. */
 orc_mesh* orc_mesh_create(int V, const double* rest, const double* w, int T, const int* tets,
-                          int n_edges_in, const int* edges_in, int* err) {
+                          int n_edges_in, const int* edges_in, double conn_radius, int* err) {
     *err = ORC_E_INVAL;
     if (V <= 0 || T < 0 || (T == 0 && !edges_in)) return NULL;
     orc_mesh* m = (orc_mesh*)calloc(1, sizeof(orc_mesh));
@@ -424,12 +523,15 @@ orc_mesh* orc_mesh_create(int V, const double* rest, const double* w, int T, con
     if (rc != ORC_OK) { orc_mesh_destroy(m); *err = rc; return NULL; }
     m->fcol_off = (int*)malloc(sizeof(int) * (m->n_fcol + 1));
     color_major(m->F, m->fcolor, m->n_fcol, m->forder, m->fcol_off);
+    rc = build_connections(m, rest, conn_radius);
+    if (rc != ORC_OK) { orc_mesh_destroy(m); *err = rc; return NULL; }
     *err = ORC_OK;
     return m;
 }
 
 /* Read-only views for the test suite. which: 0 info, see below. */
 void orc_mesh_faces(const orc_mesh* m, int* out /* 2 */) { out[0] = m->F; out[1] = m->n_fcol; }
+void orc_mesh_conns(const orc_mesh* m, int* out /* 3 */) { out[0] = m->C; out[1] = m->n_ccol; out[2] = m->n_obj; }
 
 void orc_mesh_info(const orc_mesh* m, int* out /* 6 */) {
     out[0] = m->V; out[1] = m->T; out[2] = m->E;
@@ -453,6 +555,10 @@ int orc_mesh_get_int(const orc_mesh* m, int which, int* out) {
     case 11: memcpy(out, m->fopp, sizeof(int) * m->F); break;
     case 12: memcpy(out, m->forder, sizeof(int) * m->F); break;
     case 13: memcpy(out, m->fcol_off, sizeof(int) * (m->n_fcol + 1)); break;
+    case 14: memcpy(out, m->conn, sizeof(int) * 4 * m->C); break;
+    case 15: memcpy(out, m->corder, sizeof(int) * m->C); break;
+    case 16: memcpy(out, m->ccol_off, sizeof(int) * (m->n_ccol + 1)); break;
+    case 17: memcpy(out, m->obj, sizeof(int) * m->V); break;
     default: return ORC_E_INVAL;
     }
     return ORC_OK;
@@ -465,6 +571,7 @@ int orc_mesh_get_real(const orc_mesh* m, int which, double* out) {
     case 2: for (int k = 0; k < 3; ++k) out[k] = m->bbmin[k]; break;
     case 3: for (int k = 0; k < 3; ++k) out[k] = m->bbmax[k]; break;
     case 4: out[0] = m->extent; break;
+    case 5: for (int c = 0; c < m->C; ++c) out[c] = m->cd0[c]; break;
     default: return ORC_E_INVAL;
     }
     return ORC_OK;
@@ -552,6 +659,45 @@ REAL orc_project_tet(REAL* xa, REAL* xb, REAL* xc, REAL* xd, const REAL* w4, REA
     return C;
 }
 
+/* Tissue connection (R16): C = |x_v - p| - d0 with p = (x_a + x_b + x_c) / 3.
+ * Gradients: n = (x_v - p)/|x_v - p| at v, -n/3 at a, b and c, so
+ * sum w |g|^2 = w_v + (w_a + w_b + w_c) / 9. Multiplier step and corrections
+ * as in R2 (skipped as in R8 when |x_v - p| is below min_len or the
+ * denominator is zero). Returns C. */
+static REAL conn_step(const REAL* xv, const REAL* xa, const REAL* xb, const REAL* xc, const REAL* w4, REAL d0,
+                      REAL alpha_t, REAL lambda, REAL min_len, REAL* dl_out, REAL dx[4][3]) {
+    REAL p[3], r[3];
+    for (int k = 0; k < 3; ++k) p[k] = (xa[k] + xb[k] + xc[k]) / 3;
+    vsub(xv, p, r);
+    const REAL len = vnorm(r);
+    const REAL C = len - d0;
+    const REAL denom = w4[0] + (w4[1] + w4[2] + w4[3]) / 9 + alpha_t;
+    *dl_out = 0;
+    for (int i = 0; i < 4; ++i)
+        for (int k = 0; k < 3; ++k) dx[i][k] = 0;
+    if (len < min_len || denom == 0) return C;
+    const REAL dl = (-C - alpha_t * lambda) / denom;
+    for (int k = 0; k < 3; ++k) {
+        const REAL n = r[k] / len;
+        dx[0][k] = w4[0] * dl * n;
+        for (int i = 1; i < 4; ++i) dx[i][k] = -(w4[i] * dl * n / 3);
+    }
+    *dl_out = dl;
+    return C;
+}
+
+/* Gauss-Seidel projection of one tissue connection (the step, applied). */
+REAL orc_project_conn(REAL* xv, REAL* xa, REAL* xb, REAL* xc, const REAL* w4, REAL d0, REAL alpha_t,
+                      REAL* lambda, REAL min_len) {
+    REAL dl, dx[4][3];
+    REAL C = conn_step(xv, xa, xb, xc, w4, d0, alpha_t, *lambda, min_len, &dl, dx);
+    REAL* x[4] = {xv, xa, xb, xc};
+    for (int i = 0; i < 4; ++i)
+        for (int k = 0; k < 3; ++k) x[i][k] += dx[i][k];
+    *lambda += dl;
+    return C;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Environment: parameters, state, reset and step.                           */
 /* ------------------------------------------------------------------------ */
@@ -582,6 +728,7 @@ typedef struct orc_env {
     REAL* xprev;  /* [V][3] */
     REAL* lam_e;  /* [E] */
     REAL* lam_t;  /* [T] */
+    REAL* lam_c;  /* [C] */
     REAL c[3];    /* tool centre */
     REAL lo[3], hi[3];
     REAL l_prev;
@@ -602,7 +749,7 @@ typedef struct orc_env {
 
 void orc_env_destroy(orc_env* s) {
     if (!s) return;
-    free(s->x); free(s->v); free(s->xprev); free(s->lam_e); free(s->lam_t);
+    free(s->x); free(s->v); free(s->xprev); free(s->lam_e); free(s->lam_t); free(s->lam_c);
     free(s->obs); free(s->contacts); free(s);
 }
 
@@ -614,6 +761,7 @@ orc_env* orc_env_create(const orc_mesh* m) {
     s->xprev = (REAL*)calloc(3 * m->V, sizeof(REAL));
     s->lam_e = (REAL*)calloc(m->E > 0 ? m->E : 1, sizeof(REAL));
     s->lam_t = (REAL*)calloc(m->T > 0 ? m->T : 1, sizeof(REAL));
+    s->lam_c = (REAL*)calloc(m->C > 0 ? m->C : 1, sizeof(REAL));
     s->obs = (int*)calloc(m->V, sizeof(int));
     s->contacts = (int*)calloc(m->V, sizeof(int));
     return s;
@@ -995,6 +1143,7 @@ static void substep(orc_env* s, const orc_params* p, REAL h, REAL alpha_d, int r
     REAL at_v = (REAL)p->alpha_v / (h * h);
     for (int e = 0; e < m->E; ++e) s->lam_e[e] = 0;
     for (int t = 0; t < m->T; ++t) s->lam_t[t] = 0;
+    for (int c = 0; c < m->C; ++c) s->lam_c[c] = 0;
     for (int it = 0; it < p->iterations; ++it) {
         if (p->solver == 1) {
             jacobi_iteration(s, at_d, at_v, min_len);
@@ -1014,6 +1163,15 @@ static void substep(orc_env* s, const orc_params* p, REAL h, REAL alpha_d, int r
                 REAL w4[4] = {m->w[v4[0]], m->w[v4[1]], m->w[v4[2]], m->w[v4[3]]};
                 orc_project_tet(&s->x[3 * v4[0]], &s->x[3 * v4[1]], &s->x[3 * v4[2]], &s->x[3 * v4[3]],
                                 w4, m->V0[t], at_v, &s->lam_t[t]);
+            }
+        /* tissue connections (R16), with the distance compliance */
+        for (int c = 0; c < m->n_ccol; ++c)
+            for (int q = m->ccol_off[c]; q < m->ccol_off[c + 1]; ++q) {
+                const int k = m->corder[q];
+                const int* v4 = &m->conn[4 * k];
+                REAL w4[4] = {m->w[v4[0]], m->w[v4[1]], m->w[v4[2]], m->w[v4[3]]};
+                orc_project_conn(&s->x[3 * v4[0]], &s->x[3 * v4[1]], &s->x[3 * v4[2]], &s->x[3 * v4[3]],
+                                 w4, m->cd0[k], at_d, &s->lam_c[k], min_len);
             }
     }
     if (p->tool_model == 1) {
@@ -1035,6 +1193,7 @@ int orc_obs_dim(const orc_params* p) { return 3 + 3 * p->n_obs; }
 int orc_env_step(orc_env* s, const orc_params* p, const double* action, double alpha_d,
                  double* obs, double* reward, unsigned char* done) {
     const orc_mesh* m = s->m;
+    if (p->solver == 1 && m->C > 0) return ORC_E_INVAL;   /* R10 covers distance and volume constraints only */
     if (p->auto_reset && s->done_prev) {
         s->episode += 1;
         int rc = reset_state(s, p, orc_episode_seed(s->seed0, s->episode), s->env);
@@ -1293,6 +1452,7 @@ int orc_env_step_surrogate(orc_env* s, const orc_params* p, const double* action
                            const orc_mlp* net, double threshold, int n_full, double* obs, double* reward,
                            unsigned char* done, int* fallbacks, double* record_F, double* record_T) {
     const orc_mesh* m = s->m;
+    if (m->C > 0) return ORC_E_INVAL;   /* the warm-start network sees no connections */
     double a[3];
     for (int k = 0; k < 3; ++k)
         a[k] = action ? action[k] : orc_action(s->seed, s->env, (uint64_t)s->t, k);

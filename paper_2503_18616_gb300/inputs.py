@@ -66,6 +66,22 @@ def grid_block(nx: int, ny: int, nz: int, spacing: float = CELL, mass: float = M
     return rest, inv_mass, np.asarray(tets, dtype=np.int32)
 
 
+def stacked_blocks(nx: int, ny: int, nz_base: int, nz_top: int, gap: float = 0.0, spacing: float = CELL,
+                   mass: float = MASS):
+    """Two objects in one mesh: a base block (an organ, bottom face pinned) and
+    a tissue block of the same footprint laid on it `gap` above its top face,
+    free (its bottom face unpinned), for the tissue-connection scene of the
+    paper's retraction task (Sec. III-A, Sec. IV). Base vertices come first.
+
+    Returns (rest [V,3], inv_mass [V], tets [T,4])."""
+    r0, w0, t0 = grid_block(nx, ny, nz_base, spacing, mass, pin_bottom=True)
+    r1, w1, t1 = grid_block(nx, ny, nz_top, spacing, mass, pin_bottom=False)
+    r1 = r1.copy()
+    r1[:, 2] += r0[:, 2].max() + gap
+    return (np.concatenate([r0, r1]), np.concatenate([w0, w1]),
+            np.concatenate([t0, t1 + len(r0)]).astype(np.int32))
+
+
 def two_tet_mesh(spacing: float = CELL, mass: float = MASS):
     """Two tets sharing one face (5 vertices, 9 edges), no pinned vertex."""
     s = spacing
@@ -169,6 +185,7 @@ def default_params(spacing: float = CELL, **over) -> dict:
         "clamp_radius": 0.25 * spacing,
         "clamp_angle": math.radians(10.0),
         "grasp_radius": 0.5 * spacing,   # dragging: nearest free vertex within this of the clamp end
+        "conn_radius": 0.0,  # > 0: tissue connections between the objects of a mesh, up to this rest distance
     }
     p.update(over)
     return p
