@@ -99,6 +99,14 @@ typedef struct {
                                  vertex within this distance of the dragging point (the clamp end,
                                  clamp_length beyond the tool point along the shaft) and keep it at
                                  its grasp-time distance (Sec. III-A dragging); opening releases */
+    double conn_radius;       /* > 0: tissue connections (Sec. III-A) between the objects of a mesh
+                                 (connected components of its tets, numbered by lowest vertex):
+                                 every vertex of a surface face connects to the surface face of a
+                                 lower object whose centroid is nearest at rest, if within this
+                                 distance; a distance constraint keeps the vertex at its rest
+                                 distance from the centroid, compliance compliance_dist, projected
+                                 after the volume colours of each iteration. Gauss-Seidel only; no
+                                 warm-start or recording step with connections */
 } ffsrl_params;
 
 #define FFSRL_TOOL_SPHERE 0
@@ -189,7 +197,9 @@ int ffsrl_set_state(ffsrl_sim* sim, const float* x_dev, const float* v_dev, cons
  * 8 tet colour offsets [n_tcol+1], 9 top-face vertices [n_top],
  * 10 surface faces [F][3] (ascending triples with a free vertex),
  * 11 their opposite tet vertices [F], 12 face colour-major order [F],
- * 13 face colour offsets [n_fcol+1].
+ * 13 face colour offsets [n_fcol+1], 14 tissue connections [C][4] (vertex,
+ * then the face's ascending triple), 15 connection colour-major order [C],
+ * 16 connection colour offsets [n_ccol+1], 17 object of each vertex [V].
  * With out_host NULL only *count is written (number of int32 values). */
 int ffsrl_get_mesh_table(const ffsrl_sim* sim, int32_t mesh, int32_t which, int32_t* out_host,
                          int64_t* count);

@@ -149,6 +149,7 @@ struct ffsrl_sim {
     }
     // mixed rollout: warm-start envs stepped beside the plain ones
     bool mixed = false;
+    bool has_conn = false;          // some mesh holds tissue connections
     float mix_threshold = 0.f;
     int mix_n_full = 1;
     int* mix_fallbacks = nullptr;
@@ -214,6 +215,8 @@ int check_params(const ffsrl_params& p) {
     if (p.reserved != 0) return fail(FFSRL_E_INVAL, "reserved params must be zero");
     if (p.tool_model != FFSRL_TOOL_SPHERE && p.tool_model != FFSRL_TOOL_GRASPER)
         return fail(FFSRL_E_INVAL, "tool_model must be FFSRL_TOOL_SPHERE or FFSRL_TOOL_GRASPER");
+    if (!(p.conn_radius >= 0) || !std::isfinite(p.conn_radius))
+        return fail(FFSRL_E_INVAL, "conn_radius must be finite and >= 0");
     if (p.tool_model == FFSRL_TOOL_GRASPER) {
         if (!(p.shaft_radius >= 0) || !(p.clamp_length >= 0) || !(p.clamp_radius >= 0) ||
             !(p.grasp_radius >= 0) || !std::isfinite(p.rcm_height) || !std::isfinite(p.clamp_angle))
@@ -235,7 +238,8 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, const Schedule& sc, MeshDev& d)
     d.n_ecol = m.n_ecol;
     d.n_tcol = m.n_tcol;
     d.n_top = int(m.top.size());
-    d.n_seg = (m.n_ecol + m.n_tcol) * sc.parts;
+    d.n_dseg = (m.n_ecol + m.n_tcol) * sc.parts;
+    d.n_seg = (m.n_ecol + m.n_tcol + m.n_ccol) * sc.parts;
     d.ring_bytes = sc.ring_bytes;
     d.parts = sc.parts;
     d.part_slots = sc.part_slots;
@@ -299,7 +303,7 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, const Schedule& sc, MeshDev& d)
         // the records without segment padding (order-free residual sweeps)
         std::vector<uint2> er;
         std::vector<uint4> tr;
-        for (int c = 0; c < d.n_seg; ++c) {
+        for (int c = 0; c < d.n_dseg; ++c) {   // distance and volume records only
             const int32_t* sg = &sc.segs[4 * c];
             const unsigned char* base = sc.stream.data() + sg[0];
             for (int q = 0; q < sg[2]; ++q) {
@@ -602,7 +606,7 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
         s->pstart[e] = int(pst);
         voff += d.Vp;
         pst += d.V;
-        loff += d.E + d.T;   // multiplier slots (used with more than one iteration)
+        loff += d.E + d.T + s->meshes[ev[e].mesh].C;   // multiplier slots (used with more than one iteration)
         if (voff > 0x7fffffffLL || pst > 0x7fffffffLL || loff > 0x7fffffffLL)
             return fail(FFSRL_E_INVAL, "too many vertices in total (more than 2^31 rows)");
     }
@@ -688,7 +692,7 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
     std::vector<size_t> cl_smem(md.size(), 0);
     if (!(p.schedule_flags & FFSRL_SCHED_NO_CLUSTER) && p.tool_model == FFSRL_TOOL_SPHERE) {
         for (size_t mi = 0; mi < md.size(); ++mi) {
-            if (mesh_class[mi] != 0) continue;
+            if (mesh_class[mi] != 0 || s->meshes[mi].C > 0) continue;
             for (int cl : {2, 4}) {
                 const int P = ((md[mi].V + cl - 1) / cl + 31) / 32 * 32;
                 const size_t b = cluster_smem_bytes(P);
@@ -836,11 +840,16 @@ int ffsrl_create(const ffsrl_mesh* meshes, int32_t n_meshes, const int32_t* env_
     for (int i = 0; i < n_meshes; ++i) {
         std::string err;
         rc = build_host_mesh(meshes[i].n_verts, meshes[i].n_tets, meshes[i].rest_pos, meshes[i].inv_mass,
-                             meshes[i].tets, s->meshes[i], err);
+                             meshes[i].tets, s->meshes[i], err, params->conn_radius);
         if (rc) {
             delete s;
             return fail(rc, "mesh " + std::to_string(i) + ": " + err);
         }
+        s->has_conn |= s->meshes[i].C > 0;
+    }
+    if (s->has_conn && params->solver != FFSRL_SOLVER_GAUSS_SEIDEL) {
+        delete s;
+        return fail(FFSRL_E_INVAL, "tissue connections run with the Gauss-Seidel solver");
     }
     s->env_mesh.assign(n_env, 0);
     for (int e = 0; e < n_env; ++e) {
@@ -1239,8 +1248,10 @@ int launch_warm_groups(ffsrl_sim* sim, cudaStream_t st, bool sublists, const flo
 // and the substep kernel.
 int run_substeps(ffsrl_sim* sim, int mode, const float* actions, float* obs, float* reward, uint8_t* done,
                  float threshold, int n_full, int* fallbacks, float* residual, float* feat_out, float* target_out) {
-    if (sim->params.solver != FFSRL_SOLVER_GAUSS_SEIDEL || sim->params.tool_model != FFSRL_TOOL_SPHERE)
-        return fail(FFSRL_E_INVAL, "the warm-start and recording steps use the Gauss-Seidel solve and the sphere tool");
+    if (sim->params.solver != FFSRL_SOLVER_GAUSS_SEIDEL || sim->params.tool_model != FFSRL_TOOL_SPHERE ||
+        sim->has_conn)
+        return fail(FFSRL_E_INVAL,
+                    "the warm-start and recording steps use the Gauss-Seidel solve, the sphere tool and no connections");
     int rc = ensure_surrogate_buffers(sim);
     if (rc) return rc;
     if (sim->params.auto_reset) FFSRL_CUDA(launch_auto_reset(sim->S, sim->stream));
@@ -1313,8 +1324,9 @@ int ffsrl_set_surrogate_envs(ffsrl_sim* sim, const uint8_t* mask_host, double th
     }
     if (!sim->has_net) return fail(FFSRL_E_INVAL, "no network installed (ffsrl_set_network)");
     if (n_full < 1) return fail(FFSRL_E_INVAL, "n_full must be >= 1");
-    if (sim->params.solver != FFSRL_SOLVER_GAUSS_SEIDEL || sim->params.tool_model != FFSRL_TOOL_SPHERE)
-        return fail(FFSRL_E_INVAL, "the warm-start step uses the Gauss-Seidel solve and the sphere tool");
+    if (sim->params.solver != FFSRL_SOLVER_GAUSS_SEIDEL || sim->params.tool_model != FFSRL_TOOL_SPHERE ||
+        sim->has_conn)
+        return fail(FFSRL_E_INVAL, "the warm-start step uses the Gauss-Seidel solve, the sphere tool and no connections");
     FFSRL_CUDA(cudaSetDevice(sim->device));
     int rc = ensure_surrogate_buffers(sim);
     if (rc) return rc;
@@ -1440,6 +1452,10 @@ int ffsrl_get_mesh_table(const ffsrl_sim* sim, int32_t mesh, int32_t which, int3
     case 11: src = &m.fopp; break;
     case 12: src = &m.forder; break;
     case 13: src = &m.fcol_off; break;
+    case 14: src = &m.conn; break;
+    case 15: src = &m.corder; break;
+    case 16: src = &m.ccol_off; break;
+    case 17: src = &m.obj; break;
     default: return fail(FFSRL_E_INVAL, "unknown table");
     }
     *count = int64_t(src->size());
@@ -1518,7 +1534,7 @@ extern "C" int ffsrl_step_noalloc(ffsrl_sim* sim, const float* actions_dev, floa
     if (sim->params.iterations > 1)
         for (int e = 0; e < sim->n_env; ++e) {
             const HostMesh& m = sim->meshes[sim->env_mesh[e]];
-            lam_slots += size_t(m.E + m.T);
+            lam_slots += size_t(m.E + m.T + m.C);
         }
     // Scratch layout: x, v and x_prev ([3][rows] float each), the working
     // positions of non-resident envs ([rows] float4), contacts ([rows] int),

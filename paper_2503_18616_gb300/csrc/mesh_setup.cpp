@@ -73,7 +73,7 @@ void colour_major(const std::vector<int32_t>& colour, int n_colours, std::vector
 }  // namespace
 
 int build_host_mesh(int V, int T, const double* rest, const double* inv_mass,
-                    const int32_t* tets, HostMesh& m, std::string& err) {
+                    const int32_t* tets, HostMesh& m, std::string& err, double conn_radius) {
     if (V < 1 || V > 65535) { err = "n_verts must be in [1, 65535]"; return FFSRL_E_INVAL; }
     if (T < 1) { err = "n_tets must be >= 1"; return FFSRL_E_INVAL; }
     if (!rest || !inv_mass || !tets) { err = "mesh arrays must be non-NULL"; return FFSRL_E_INVAL; }
@@ -199,6 +199,86 @@ int build_host_mesh(int V, int T, const double* rest, const double* inv_mass,
         if (rc != FFSRL_OK) { err = "more than 256 face colours needed"; return rc; }
     }
     colour_major(m.fcolor, m.n_fcol, m.forder, m.fcol_off);
+    return build_connections(m, rest, conn_radius, err);
+}
+
+int build_connections(HostMesh& m, const double* rest, double conn_radius, std::string& err) {
+    const int V = m.V;
+    // Objects: connected components of the tets, numbered in the order of
+    // their lowest vertex (union-find, then a relabelling pass in vertex order).
+    std::vector<int> parent(V);
+    for (int i = 0; i < V; ++i) parent[i] = i;
+    auto find = [&](int x) {
+        while (parent[x] != x) x = parent[x] = parent[parent[x]];
+        return x;
+    };
+    for (int t = 0; t < m.T; ++t)
+        for (int k = 1; k < 4; ++k) {
+            const int a = find(m.tet[4 * t]), b = find(m.tet[4 * t + k]);
+            if (a != b) parent[std::max(a, b)] = std::min(a, b);
+        }
+    m.obj.assign(V, -1);
+    std::vector<int> label(V, -1);
+    m.n_obj = 0;
+    for (int i = 0; i < V; ++i) {
+        const int r = find(i);
+        if (label[r] < 0) label[r] = m.n_obj++;
+        m.obj[i] = label[r];
+    }
+    // Connections: each vertex of a surface face to the nearest face centroid
+    // of a lower object, within conn_radius (rest positions as given, double;
+    // ties: the first face).
+    m.C = 0;
+    m.conn.clear();
+    m.conn_d0.clear();
+    if (conn_radius > 0 && m.n_obj > 1) {
+        std::vector<char> on_face(V, 0);
+        for (int f = 0; f < m.F; ++f)
+            for (int k = 0; k < 3; ++k) on_face[m.face[3 * f + k]] = 1;
+        std::vector<double> cen(3 * size_t(m.F));
+        for (int f = 0; f < m.F; ++f)
+            for (int k = 0; k < 3; ++k) {
+                const int32_t* fv = &m.face[3 * f];
+                cen[3 * f + k] = (rest[3 * fv[0] + k] + rest[3 * fv[1] + k] + rest[3 * fv[2] + k]) / 3.0;
+            }
+        for (int i = 0; i < V; ++i) {
+            if (!on_face[i]) continue;
+            int best = -1;
+            double bd2 = 0;
+            for (int f = 0; f < m.F; ++f) {
+                if (!(m.obj[m.face[3 * f]] < m.obj[i])) continue;
+                double d2 = 0;
+                for (int k = 0; k < 3; ++k) {
+                    const double dk = rest[3 * i + k] - cen[3 * f + k];
+                    d2 += dk * dk;
+                }
+                if (best < 0 || d2 < bd2) {
+                    best = f;
+                    bd2 = d2;
+                }
+            }
+            if (best < 0 || !(std::sqrt(bd2) <= conn_radius)) continue;
+            const int32_t* fv = &m.face[3 * best];
+            m.conn.insert(m.conn.end(), {int32_t(i), fv[0], fv[1], fv[2]});
+            // rest distance of the float32 state, so C = 0 at rest up to float rounding
+            double r2 = 0;
+            for (int k = 0; k < 3; ++k) {
+                const double c = (double(m.rest[3 * fv[0] + k]) + double(m.rest[3 * fv[1] + k]) +
+                                  double(m.rest[3 * fv[2] + k])) / 3.0;
+                const double dk = double(m.rest[3 * i + k]) - c;
+                r2 += dk * dk;
+            }
+            m.conn_d0.push_back(float(std::sqrt(r2)));
+            ++m.C;
+        }
+    }
+    m.n_ccol = 0;
+    m.ccolor.clear();
+    if (m.C > 0) {
+        const int rc = colour_first_fit<4>(m.C, m.conn.data(), V, m.ccolor, m.n_ccol);
+        if (rc != FFSRL_OK) { err = "more than 256 connection colours needed"; return rc; }
+    }
+    colour_major(m.ccolor, m.n_ccol, m.corder, m.ccol_off);
     return FFSRL_OK;
 }
 
@@ -329,7 +409,7 @@ void group_improve(std::vector<Rec>& g, std::mt19937_64& rng, long long iters, b
 // groups of the count above ceil(n_key / 8). Moves swap the slots of two
 // vertices of one block in different bank groups; `iters` moves are tried.
 std::vector<int> balanced_slots(const HostMesh& m, std::mt19937_64& rng, long long iters) {
-    const int V = m.V, ne = m.n_ecol, nt = m.n_tcol, K = 2 * ne + 4 * nt;
+    const int V = m.V, ne = m.n_ecol, nt = m.n_tcol, K = 2 * ne + 4 * nt + 4 * m.n_ccol;
     std::vector<int> slot(V);
     for (int b = 0; b < V; b += 32) {   // a permutation inside each aligned block of 32 vertices
         const int n = std::min(32, V - b);
@@ -344,6 +424,8 @@ std::vector<int> balanced_slots(const HostMesh& m, std::mt19937_64& rng, long lo
         for (int p = 0; p < 2; ++p) ++off[m.edge[2 * e + p] + 1];
     for (int t = 0; t < m.T; ++t)
         for (int p = 0; p < 4; ++p) ++off[m.tet[4 * t + p] + 1];
+    for (int c = 0; c < m.C; ++c)
+        for (int p = 0; p < 4; ++p) ++off[m.conn[4 * c + p] + 1];
     for (int i = 0; i < V; ++i) off[i + 1] += off[i];
     keys.resize(off[V]);
     std::vector<int> fill(off.begin(), off.end() - 1), n_key(K, 0);
@@ -357,6 +439,12 @@ std::vector<int> balanced_slots(const HostMesh& m, std::mt19937_64& rng, long lo
         for (int p = 0; p < 4; ++p) {
             const int k = 2 * ne + 4 * m.tcolor[t] + p;
             keys[fill[m.tet[4 * t + p]]++] = k;
+            ++n_key[k];
+        }
+    for (int c = 0; c < m.C; ++c)
+        for (int p = 0; p < 4; ++p) {
+            const int k = 2 * ne + 4 * nt + 4 * m.ccolor[c] + p;
+            keys[fill[m.conn[4 * c + p]]++] = k;
             ++n_key[k];
         }
     std::vector<std::array<int, 8>> h(K);
@@ -475,6 +563,37 @@ void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& ou
                 buf[4 * j] = uint32_t(r[j][0]) | (uint32_t(r[j][1]) << 16);
                 buf[4 * j + 1] = uint32_t(r[j][2]) | (uint32_t(r[j][3]) << 16);
                 buf[4 * j + 2] = vbits;
+                buf[4 * j + 3] = 0;
+            }
+            append_segment(out, buf.data(), int(buf.size() * 4), n, first);
+            first += n;
+        }
+    }
+    // Tissue connections: records (vertex, face triple) like tets, d0 in z.
+    for (int c = 0; c < m.n_ccol; ++c) {
+        const int beg = m.ccol_off[c], end = m.ccol_off[c + 1];
+        std::vector<std::vector<Rec>> part(parts);
+        for (int q = beg; q < end; ++q) {
+            const int k = m.corder[q];
+            const Rec r = {out.slot_of[m.conn[4 * k]], out.slot_of[m.conn[4 * k + 1]], out.slot_of[m.conn[4 * k + 2]],
+                           out.slot_of[m.conn[4 * k + 3]], k};
+            part[r[0] / P].push_back(r);
+        }
+        int first = m.E + m.T + beg;
+        for (std::vector<Rec>& r : part) {
+            const int n = int(r.size());
+            if (permute) {
+                r = group_greedy<4>(r, false);
+                group_improve<4>(r, rng, 100ll * n, false);
+            }
+            std::vector<uint32_t> buf(4 * size_t(n));
+            for (int j = 0; j < n; ++j) {
+                float d0 = m.conn_d0[r[j][4]];
+                uint32_t dbits;
+                std::memcpy(&dbits, &d0, 4);
+                buf[4 * j] = uint32_t(r[j][0]) | (uint32_t(r[j][1]) << 16);
+                buf[4 * j + 1] = uint32_t(r[j][2]) | (uint32_t(r[j][3]) << 16);
+                buf[4 * j + 2] = dbits;
                 buf[4 * j + 3] = 0;
             }
             append_segment(out, buf.data(), int(buf.size() * 4), n, first);

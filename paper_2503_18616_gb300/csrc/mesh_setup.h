@@ -33,16 +33,30 @@ struct HostMesh {
     std::vector<int32_t> face;                // [F][3] ascending vertex ids
     std::vector<int32_t> fopp;                // [F] fourth vertex of the face's tet
     std::vector<int32_t> fcolor, forder, fcol_off;
+    // objects (connected components of the tets, numbered by lowest vertex)
+    // and tissue connections: vertex, then a surface face of a lower object
+    // whose centroid is nearest at rest within the connection radius
+    int n_obj = 0, C = 0, n_ccol = 0;
+    std::vector<int32_t> obj;                 // [V]
+    std::vector<int32_t> conn;                // [C][4]
+    std::vector<float> conn_d0;               // [C] rest distance, vertex to centroid
+    std::vector<int32_t> ccolor, corder, ccol_off;
     double bbmin[3] = {0, 0, 0}, bbmax[3] = {0, 0, 0};
     double extent = 0;
 };
 
 // Returns 0 or a negative FFSRL_E_* code with a message in err.
+// conn_radius > 0 adds tissue connections between the mesh's objects.
 int build_host_mesh(int V, int T, const double* rest, const double* inv_mass,
-                    const int32_t* tets, HostMesh& out, std::string& err);
+                    const int32_t* tets, HostMesh& out, std::string& err, double conn_radius = 0.0);
+
+// Objects and tissue connections of a mesh whose faces are built (rest: the
+// positions as given); called by build_host_mesh.
+int build_connections(HostMesh& m, const double* rest, double conn_radius, std::string& err);
 
 // Execution schedule of one mesh on the GPU: vertex -> shared-memory slot map
-// and the colour-major constraint stream (edge colours, then tet colours),
+// and the colour-major constraint stream (edge colours, then tet colours,
+// then connection colours),
 // each colour a 16-byte aligned segment of records.
 struct Schedule {
     std::vector<uint16_t> slot_of, vert_of;  // [V]

@@ -25,9 +25,9 @@ namespace ffsrl {
 
 struct MeshDev {
     int V, Vp, E, T;
-    int n_ecol, n_tcol, n_top, n_seg;  // n_seg = n_ecol + n_tcol
+    int n_ecol, n_tcol, n_top, n_seg;  // segments: edge colours, tet colours, connection colours
     int ring_bytes;                   // largest segment in bytes (one ring stage)
-    int pad0;
+    int n_dseg;                       // edge and tet segments (the rest are tissue connections)
     const unsigned char* recs;        // constraint stream
     const int4* segs;                 // [n_seg] {byte offset, bytes, count, first constraint}
     const uint16_t* slot_of;          // [V] shared-memory slot of each vertex

@@ -84,6 +84,49 @@ __device__ __forceinline__ void project_tet(float4* X, uint4 rec, float at, floa
     project_tet(SmemX{X}, rec, at, lam);
 }
 
+// Tissue connection (Sec. III-A): C = |x_v - p| - d0 with p the centroid of
+// face (a, b, c); gradients n = (x_v - p)/|x_v - p| at v and -n/3 at a, b, c,
+// so sum w |g|^2 = w_v + (w_a + w_b + w_c)/9; XPBD step with the distance
+// compliance. Skipped when |x_v - p|^2 < min_len2 or the denominator is 0.
+// Rounding is spelled out so every build gives the same bits.
+template <class Acc>
+__device__ __forceinline__ void project_conn(const Acc& X, uint4 rec, float at, float min_len2, float& lam) {
+    const int v = int(rec.x & 0xffffu), a = int(rec.x >> 16);
+    const int b = int(rec.y & 0xffffu), c = int(rec.y >> 16);
+    const float d0 = __uint_as_float(rec.z);
+    float4 xv = X.ld(v), xa = X.ld(a), xb = X.ld(b), xc = X.ld(c);
+    const float third = 1.0f / 3.0f;
+    const float rx = __fsub_rn(xv.x, __fmul_rn(__fadd_rn(__fadd_rn(xa.x, xb.x), xc.x), third));
+    const float ry = __fsub_rn(xv.y, __fmul_rn(__fadd_rn(__fadd_rn(xa.y, xb.y), xc.y), third));
+    const float rz = __fsub_rn(xv.z, __fmul_rn(__fadd_rn(__fadd_rn(xa.z, xb.z), xc.z), third));
+    const float l2 = __fadd_rn(__fadd_rn(__fmul_rn(rx, rx), __fmul_rn(ry, ry)), __fmul_rn(rz, rz));
+    const float denom = __fadd_rn(__fadd_rn(xv.w, __fmul_rn(__fadd_rn(__fadd_rn(xa.w, xb.w), xc.w), 1.0f / 9.0f)), at);
+    if (l2 < min_len2 || denom == 0.f) return;
+    const float len = sqrtf(l2);
+    const float C = __fsub_rn(len, d0);
+    const float dl = __fdiv_rn(__fsub_rn(-C, __fmul_rn(at, lam)), denom);
+    const float s = __fdiv_rn(dl, len);
+    const float sv = __fmul_rn(xv.w, s);
+    xv.x = __fadd_rn(xv.x, __fmul_rn(sv, rx));
+    xv.y = __fadd_rn(xv.y, __fmul_rn(sv, ry));
+    xv.z = __fadd_rn(xv.z, __fmul_rn(sv, rz));
+    float4* f[3] = {&xa, &xb, &xc};
+    for (int k = 0; k < 3; ++k) {
+        const float sk = __fmul_rn(__fmul_rn(f[k]->w, s), third);
+        f[k]->x = __fsub_rn(f[k]->x, __fmul_rn(sk, rx));
+        f[k]->y = __fsub_rn(f[k]->y, __fmul_rn(sk, ry));
+        f[k]->z = __fsub_rn(f[k]->z, __fmul_rn(sk, rz));
+    }
+    X.st(v, xv);
+    X.st(a, xa);
+    X.st(b, xb);
+    X.st(c, xc);
+    lam = __fadd_rn(lam, dl);
+}
+__device__ __forceinline__ void project_conn(float4* X, uint4 rec, float at, float min_len2, float& lam) {
+    project_conn(SmemX{X}, rec, at, min_len2, lam);
+}
+
 // Jacobi forms (the paper's parallel scheme, Sec. III-A): the same steps
 // evaluated at the given positions, returning the corrections instead of
 // applying them (zero for a skipped constraint) and carrying lambda.

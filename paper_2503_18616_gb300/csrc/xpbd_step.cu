@@ -277,11 +277,19 @@ __global__ void __launch_bounds__(SUB * ENVS, min_ctas_per_sm(SUB * ENVS))
                             project_edge(X, rec[q], at_d, M.min_len2, l);
                             if (carry) lam[sg.w + q] = l;
                         }
-                    } else {
+                    } else if (c < M.n_dseg) {
                         const uint4* rec = reinterpret_cast<const uint4*>(base);
                         for (int q = st; q < sg.z; q += SUB) {
                             float l = (carry && it > 0) ? lam[sg.w + q] : 0.f;
                             project_tet(X, rec[q], at_v, l);
+                            if (carry) lam[sg.w + q] = l;
+                        }
+                    } else {
+                        // tissue connections, after the volume colours
+                        const uint4* rec = reinterpret_cast<const uint4*>(base);
+                        for (int q = st; q < sg.z; q += SUB) {
+                            float l = (carry && it > 0) ? lam[sg.w + q] : 0.f;
+                            project_conn(X, rec[q], at_d, M.min_len2, l);
                             if (carry) lam[sg.w + q] = l;
                         }
                     }

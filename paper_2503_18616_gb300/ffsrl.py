@@ -23,7 +23,7 @@ ERRORS = {-1: "FFSRL_E_INVAL", -2: "FFSRL_E_CUDA", -3: "FFSRL_E_OOM", -4: "FFSRL
 # ffsrl_get_mesh_table selectors
 TABLES = {"tets": 0, "flipped": 1, "edges": 2, "ecolor": 3, "tcolor": 4, "eorder": 5,
           "torder": 6, "ecol_off": 7, "tcol_off": 8, "top": 9, "faces": 10, "face_opposite": 11,
-          "forder": 12, "fcol_off": 13}
+          "forder": 12, "fcol_off": 13, "conns": 14, "corder": 15, "ccol_off": 16, "objects": 17}
 
 # every symbol include/ffsrl.h declares
 EXPORTS = ["ffsrl_create", "ffsrl_reset", "ffsrl_step", "ffsrl_step_host", "ffsrl_sync",
@@ -63,7 +63,7 @@ class ffsrl_params(ctypes.Structure):
                 ("tool_model", ctypes.c_int32), ("reserved", ctypes.c_int32), ("rcm_height", ctypes.c_double),
                 ("shaft_radius", ctypes.c_double), ("clamp_length", ctypes.c_double),
                 ("clamp_radius", ctypes.c_double), ("clamp_angle", ctypes.c_double),
-                ("grasp_radius", ctypes.c_double)]
+                ("grasp_radius", ctypes.c_double), ("conn_radius", ctypes.c_double)]
 
 SCHED_FORCE, SCHED_NO_PERMUTE, SCHED_NO_RING, SCHED_ENVS2, SCHED_ENVS4 = 1, 2, 4, 8, 16
 SCHED_SURROGATE_PIPELINE = 32
@@ -180,7 +180,8 @@ def make_params(d: dict, block_threads: int = 0, schedule_flags: int = 0) -> ffs
     p.solver = int(d.get("solver", 0))
     p.auto_reset = int(d.get("auto_reset", 0))
     p.tool_model = int(d.get("tool_model", 0))
-    for k in ("rcm_height", "shaft_radius", "clamp_length", "clamp_radius", "clamp_angle", "grasp_radius"):
+    for k in ("rcm_height", "shaft_radius", "clamp_length", "clamp_radius", "clamp_angle", "grasp_radius",
+              "conn_radius"):
         setattr(p, k, float(d.get(k, 0.0)))
     return p
 
