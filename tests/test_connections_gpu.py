@@ -162,8 +162,9 @@ def test_connections_refuse_jacobi_and_warm_start():
     from paper_2503_18616_gb300 import ffsrl
     mesh = inputs.stacked_blocks(5, 5, 2, 2, gap=1e-3)
     with pytest.raises(ffsrl.FfsrlError):
-        _sim(mesh, inputs.default_params(conn_radius=R, solver=1), 1)
-    sim = _sim(mesh, inputs.default_params(conn_radius=R), 2)
+        _sim(mesh, inputs.default_params(conn_radius=R, solver=1, n_obs=4), 1)
+    _sim(mesh, inputs.default_params(solver=1, n_obs=4), 1).close()   # without connections: accepted
+    sim = _sim(mesh, inputs.default_params(conn_radius=R, n_obs=4), 2)
     with pytest.raises(ffsrl.FfsrlError):
         sim.record_step(10)
     sim.close()
