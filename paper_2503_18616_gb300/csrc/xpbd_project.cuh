@@ -18,26 +18,34 @@ struct SmemX {
 
 // Edge-distance constraint C = |x_a - x_b| - d in XPBD form (Eq. 1 with
 // compliance): dlambda = (-C - at lambda) / (w_a + w_b + at), x_a += w_a dlambda n,
-// x_b -= w_b dlambda n, n = (x_a - x_b) / |x_a - x_b|.
+// x_b -= w_b dlambda n, n = (x_a - x_b) / |x_a - x_b|. Applied to register
+// copies; false (nothing changed) for a skipped constraint. Every rounding
+// step is spelled out (fused multiply-adds where written), so all kernels
+// that call this give the same bits whatever their register budget.
+__device__ __forceinline__ bool edge_update(float4& xa, float4& xb, float d, float at, float min_len2, float& lam) {
+    const float dx = __fsub_rn(xa.x, xb.x), dy = __fsub_rn(xa.y, xb.y), dz = __fsub_rn(xa.z, xb.z);
+    const float l2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    const float denom = __fadd_rn(__fadd_rn(xa.w, xb.w), at);
+    if (l2 < min_len2 || denom == 0.f) return false;
+    const float len = sqrtf(l2);
+    const float C = __fsub_rn(len, d);
+    const float dl = __fdividef(__fmaf_rn(-at, lam, -C), denom);
+    const float s = __fdividef(dl, len);
+    const float sa = __fmul_rn(xa.w, s), sb = __fmul_rn(xb.w, s);
+    xa.x = __fmaf_rn(sa, dx, xa.x); xa.y = __fmaf_rn(sa, dy, xa.y); xa.z = __fmaf_rn(sa, dz, xa.z);
+    xb.x = __fmaf_rn(-sb, dx, xb.x); xb.y = __fmaf_rn(-sb, dy, xb.y); xb.z = __fmaf_rn(-sb, dz, xb.z);
+    lam = __fadd_rn(lam, dl);
+    return true;
+}
+
 template <class Acc>
 __device__ __forceinline__ void project_edge(const Acc& X, uint2 rec, float at, float min_len2, float& lam) {
     const int a = int(rec.x & 0xffffu), b = int(rec.x >> 16);
-    const float d = __uint_as_float(rec.y);
     float4 xa = X.ld(a), xb = X.ld(b);
-    const float dx = xa.x - xb.x, dy = xa.y - xb.y, dz = xa.z - xb.z;
-    const float l2 = dx * dx + dy * dy + dz * dz;
-    const float denom = xa.w + xb.w + at;
-    if (l2 < min_len2 || denom == 0.f) return;
-    const float len = sqrtf(l2);
-    const float C = len - d;
-    const float dl = __fdividef(-C - at * lam, denom);
-    const float s = __fdividef(dl, len);
-    const float sa = xa.w * s, sb = xb.w * s;
-    xa.x += sa * dx; xa.y += sa * dy; xa.z += sa * dz;
-    xb.x -= sb * dx; xb.y -= sb * dy; xb.z -= sb * dz;
-    X.st(a, xa);
-    X.st(b, xb);
-    lam += dl;
+    if (edge_update(xa, xb, __uint_as_float(rec.y), at, min_len2, lam)) {
+        X.st(a, xa);
+        X.st(b, xb);
+    }
 }
 __device__ __forceinline__ void project_edge(float4* X, uint2 rec, float at, float min_len2, float& lam) {
     project_edge(SmemX{X}, rec, at, min_len2, lam);
@@ -49,36 +57,58 @@ __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
 }
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
+// The same operations with their rounding spelled out.
+__device__ __forceinline__ float3 sub3_rn(float4 a, float4 b) {
+    return make_float3(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y), __fsub_rn(a.z, b.z));
+}
+__device__ __forceinline__ float3 cross3_rn(float3 a, float3 b) {
+    return make_float3(__fmaf_rn(a.y, b.z, -__fmul_rn(a.z, b.y)), __fmaf_rn(a.z, b.x, -__fmul_rn(a.x, b.z)),
+                       __fmaf_rn(a.x, b.y, -__fmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ float dot3_rn(float3 a, float3 b) {
+    return __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, __fmul_rn(a.x, b.x)));
+}
+
 // Tet-volume constraint C = (x_ba x x_ca) . x_da / 6 - V0 with gradients
 // g_b = x_ca x x_da / 6, g_c = x_da x x_ba / 6, g_d = x_ba x x_ca / 6,
 // g_a = -(g_b + g_c + g_d) (the consistent reading of Eq. 2), scaled as in
 // Eq. 3 with inverse masses and compliance: dlambda = (-C - at lambda) /
-// (sum w_i |g_i|^2 + at), x_i += w_i dlambda g_i.
+// (sum w_i |g_i|^2 + at), x_i += w_i dlambda g_i. Register copies, rounding
+// spelled out as for edges.
+__device__ __forceinline__ bool tet_update(float4& xa, float4& xb, float4& xc, float4& xd, float V0, float at,
+                                           float& lam) {
+    const float3 ba = sub3_rn(xb, xa), ca = sub3_rn(xc, xa), da = sub3_rn(xd, xa);
+    const float3 g1 = cross3_rn(ca, da), g2 = cross3_rn(da, ba), g3 = cross3_rn(ba, ca);  // 6 x gradient
+    const float3 g0 = make_float3(-__fadd_rn(__fadd_rn(g1.x, g2.x), g3.x), -__fadd_rn(__fadd_rn(g1.y, g2.y), g3.y),
+                                  -__fadd_rn(__fadd_rn(g1.z, g2.z), g3.z));
+    const float C = __fmaf_rn(dot3_rn(g3, da), 1.0f / 6.0f, -V0);
+    const float sw = __fmaf_rn(xd.w, dot3_rn(g3, g3),
+                               __fmaf_rn(xc.w, dot3_rn(g2, g2), __fmaf_rn(xb.w, dot3_rn(g1, g1),
+                                                                          __fmul_rn(xa.w, dot3_rn(g0, g0)))));
+    const float denom = __fmaf_rn(sw, 1.0f / 36.0f, at);
+    if (denom == 0.f) return false;
+    const float dl = __fdividef(__fmaf_rn(-at, lam, -C), denom);
+    const float s = __fmul_rn(dl, 1.0f / 6.0f);
+    const float sa = __fmul_rn(xa.w, s), sb = __fmul_rn(xb.w, s), sc = __fmul_rn(xc.w, s), sd = __fmul_rn(xd.w, s);
+    xa.x = __fmaf_rn(sa, g0.x, xa.x); xa.y = __fmaf_rn(sa, g0.y, xa.y); xa.z = __fmaf_rn(sa, g0.z, xa.z);
+    xb.x = __fmaf_rn(sb, g1.x, xb.x); xb.y = __fmaf_rn(sb, g1.y, xb.y); xb.z = __fmaf_rn(sb, g1.z, xb.z);
+    xc.x = __fmaf_rn(sc, g2.x, xc.x); xc.y = __fmaf_rn(sc, g2.y, xc.y); xc.z = __fmaf_rn(sc, g2.z, xc.z);
+    xd.x = __fmaf_rn(sd, g3.x, xd.x); xd.y = __fmaf_rn(sd, g3.y, xd.y); xd.z = __fmaf_rn(sd, g3.z, xd.z);
+    lam = __fadd_rn(lam, dl);
+    return true;
+}
+
 template <class Acc>
 __device__ __forceinline__ void project_tet(const Acc& X, uint4 rec, float at, float& lam) {
     const int a = int(rec.x & 0xffffu), b = int(rec.x >> 16);
     const int c = int(rec.y & 0xffffu), d = int(rec.y >> 16);
-    const float V0 = __uint_as_float(rec.z);
     float4 xa = X.ld(a), xb = X.ld(b), xc = X.ld(c), xd = X.ld(d);
-    const float3 ba = sub3(xb, xa), ca = sub3(xc, xa), da = sub3(xd, xa);
-    const float3 g1 = cross3(ca, da), g2 = cross3(da, ba), g3 = cross3(ba, ca);  // 6 x gradient
-    const float3 g0 = make_float3(-(g1.x + g2.x + g3.x), -(g1.y + g2.y + g3.y), -(g1.z + g2.z + g3.z));
-    const float C = dot3(g3, da) * (1.0f / 6.0f) - V0;
-    const float sw = xa.w * dot3(g0, g0) + xb.w * dot3(g1, g1) + xc.w * dot3(g2, g2) + xd.w * dot3(g3, g3);
-    const float denom = sw * (1.0f / 36.0f) + at;
-    if (denom == 0.f) return;
-    const float dl = __fdividef(-C - at * lam, denom);
-    const float s = dl * (1.0f / 6.0f);
-    const float sa = xa.w * s, sb = xb.w * s, sc = xc.w * s, sd = xd.w * s;
-    xa.x += sa * g0.x; xa.y += sa * g0.y; xa.z += sa * g0.z;
-    xb.x += sb * g1.x; xb.y += sb * g1.y; xb.z += sb * g1.z;
-    xc.x += sc * g2.x; xc.y += sc * g2.y; xc.z += sc * g2.z;
-    xd.x += sd * g3.x; xd.y += sd * g3.y; xd.z += sd * g3.z;
-    X.st(a, xa);
-    X.st(b, xb);
-    X.st(c, xc);
-    X.st(d, xd);
-    lam += dl;
+    if (tet_update(xa, xb, xc, xd, __uint_as_float(rec.z), at, lam)) {
+        X.st(a, xa);
+        X.st(b, xb);
+        X.st(c, xc);
+        X.st(d, xd);
+    }
 }
 __device__ __forceinline__ void project_tet(float4* X, uint4 rec, float at, float& lam) {
     project_tet(SmemX{X}, rec, at, lam);

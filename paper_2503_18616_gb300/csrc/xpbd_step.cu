@@ -270,17 +270,18 @@ __global__ void __launch_bounds__(SUB * ENVS, min_ctas_per_sm(SUB * ENVS))
                 }
                 const bool carry = lam != nullptr;
                 if (ok && active) {
+                    const bool lin = carry && it > 0;
                     if (c < n_ecol) {
                         const uint2* rec = reinterpret_cast<const uint2*>(base);
                         for (int q = st; q < sg.z; q += SUB) {
-                            float l = (carry && it > 0) ? lam[sg.w + q] : 0.f;
+                            float l = lin ? lam[sg.w + q] : 0.f;
                             project_edge(X, rec[q], at_d, M.min_len2, l);
                             if (carry) lam[sg.w + q] = l;
                         }
                     } else if (c < M.n_dseg) {
                         const uint4* rec = reinterpret_cast<const uint4*>(base);
                         for (int q = st; q < sg.z; q += SUB) {
-                            float l = (carry && it > 0) ? lam[sg.w + q] : 0.f;
+                            float l = lin ? lam[sg.w + q] : 0.f;
                             project_tet(X, rec[q], at_v, l);
                             if (carry) lam[sg.w + q] = l;
                         }
