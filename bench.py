@@ -229,10 +229,39 @@ def oracle_rate(batch, seconds: float, seed: int, envs, max_steps=None):
     return len(oes) * n / dt, n, dt, oes
 
 
+def _ref_worker(workload, n_envs_flag, env_ids, seed, steps, warmup, barrier, out):
+    """One host process of the reference arm: its envs, warm-up, then the
+    timed steps between two barriers shared with the other processes."""
+    import oracle
+    batch = Batch(workload, n_envs_flag)
+    meshes = {}
+    envs = []
+    for e in env_ids:
+        mi = batch.mesh_index(e)
+        if mi not in meshes:
+            meshes[mi] = oracle.Mesh(*batch.meshes[mi])
+        oe = oracle.Env(meshes[mi], batch.env_params(e))
+        oe.reset(seed, e)
+        envs.append(oe)
+    for _ in range(warmup):
+        for oe in envs:
+            oe.step()
+    barrier.wait()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for oe in envs:
+            oe.step()
+    out.put(time.perf_counter() - t0)
+    barrier.wait()
+
+
 def run_reference(args):
     """The oracle as it stands, timed on host cores (rank 0 only). Each bench
     step advances a bounded, evenly spaced sample of the workload's envs by one
-    step on one host thread."""
+    step; the sample is split over one spawned process per host core (envs are
+    independent), each running the unmodified oracle, and the rate is the
+    sample's env-steps over the slowest process's time."""
+    import multiprocessing as mp
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -240,42 +269,48 @@ def run_reference(args):
     batch = Batch(args.workload, args.envs)
     probe_envs = list(range(0, batch.n_env, max(1, batch.n_env // 16)))
     meshes = {}
-
-    def make(e):
+    probes = []
+    for e in probe_envs:
         mi = batch.mesh_index(e)
         if mi not in meshes:
             meshes[mi] = oracle.Mesh(*batch.meshes[mi])
         oe = oracle.Env(meshes[mi], batch.env_params(e))
         oe.reset(args.seed, e)
-        return oe
-
-    probes = [make(e) for e in probe_envs]
+        probes.append(oe)
     t0 = time.perf_counter()
     for oe in probes:
         oe.run(1, want_obs=False)
     per_env_step = (time.perf_counter() - t0) / len(probes)
-    budget = 120.0
-    n_sample = max(1, min(batch.n_env, int(budget / ((args.steps + args.warmup) * per_env_step))))
-    sample_envs = [int(e) for e in np.linspace(0, batch.n_env - 1, n_sample).round()]
-    sample_envs = sorted(set(sample_envs))
-    envs = [make(e) for e in sample_envs]
-    for _ in range(args.warmup):
-        for oe in envs:
-            oe.step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        for oe in envs:
-            oe.step()
-    dt = time.perf_counter() - t0
-    value = len(envs) * args.steps / dt
-    sample = f"{len(envs)} evenly spaced of {batch.describe()} per step, FP64 oracle, 1 host thread"
+    procs = max(1, args.ref_procs or (os.cpu_count() or 1))
+    budget = 100.0   # seconds of oracle work per process
+    per_proc = max(1, int(budget / ((args.steps + args.warmup) * per_env_step)))
+    n_sample = max(1, min(batch.n_env, per_proc * procs))
+    sample_envs = sorted(set(int(e) for e in np.linspace(0, batch.n_env - 1, n_sample).round()))
+    procs = min(procs, len(sample_envs))
+    parts = [sample_envs[i::procs] for i in range(procs)]
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(procs)
+    out = ctx.Queue()
+    workers = [ctx.Process(target=_ref_worker, args=(args.workload, args.envs, part, args.seed, args.steps,
+                                                     args.warmup, barrier, out)) for part in parts]
+    for w in workers:
+        w.start()
+    times = [out.get() for _ in workers]
+    for w in workers:
+        w.join()
+        if w.exitcode != 0:
+            raise SystemExit(f"reference worker exited with {w.exitcode}")
+    dt = max(times)
+    value = len(sample_envs) * args.steps / dt
+    sample = (f"{len(sample_envs)} evenly spaced of {batch.describe()} per step, FP64 oracle, "
+              f"{procs} host processes of 1 thread")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get("WORLD_SIZE", "1")),
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": args.workload, "n_env": batch.n_env, "envs": batch.describe(),
                        "substeps": batch.params["substeps"], "iterations": batch.params["iterations"]},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -786,6 +821,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ref-procs", type=int, default=0, help="host processes of the reference arm (0: one per core)")
     ap.add_argument("--workload", default="block17x17x9_4096env_1000steps")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
