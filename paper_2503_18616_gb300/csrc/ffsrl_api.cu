@@ -235,11 +235,11 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, const Schedule& sc, MeshDev& d)
     d.Vp = round_up(m.V, 32);
     d.E = m.E;
     d.T = m.T;
-    d.n_ecol = m.n_ecol;
-    d.n_tcol = m.n_tcol;
+    d.n_ecol = sc.n_ephase;   // execution phases (the colours, or their refinement)
+    d.n_tcol = sc.n_tphase;
     d.n_top = int(m.top.size());
-    d.n_dseg = (m.n_ecol + m.n_tcol) * sc.parts;
-    d.n_seg = (m.n_ecol + m.n_tcol + m.n_ccol) * sc.parts;
+    d.n_dseg = (sc.n_ephase + sc.n_tphase) * sc.parts;
+    d.n_seg = (sc.n_ephase + sc.n_tphase + sc.n_cphase) * sc.parts;
     d.ring_bytes = sc.ring_bytes;
     d.parts = sc.parts;
     d.part_slots = sc.part_slots;
@@ -307,7 +307,7 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, const Schedule& sc, MeshDev& d)
             const int32_t* sg = &sc.segs[4 * c];
             const unsigned char* base = sc.stream.data() + sg[0];
             for (int q = 0; q < sg[2]; ++q) {
-                if (c < m.n_ecol) {
+                if (c < sc.n_ephase * sc.parts) {
                     uint2 r;
                     std::memcpy(&r, base + 8 * size_t(q), 8);
                     er.push_back(r);

@@ -5,6 +5,7 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <queue>
 #include <random>
 #include <tuple>
 
@@ -403,13 +404,83 @@ void group_improve(std::vector<Rec>& g, std::mt19937_64& rng, long long iters, b
     }
 }
 
+// Execution phases of one constraint family (arity A, constraints `cons`,
+// oracle order `order` = colour-major with colour offsets `off`). A
+// Gauss-Seidel sweep depends only on the order of the constraints that share
+// a vertex, so any sequence of phases that keeps, at every vertex, the
+// oracle's order of the constraints containing it gives the same bits (a
+// phase is then automatically free of shared vertices). unit = 0: the colours
+// are the phases. unit > 0: list scheduling over that dependency graph,
+// longest remaining chain first (then oracle order), closes each phase at a
+// whole multiple of `unit` ready constraints (all of them when fewer are
+// ready), so that a phase costs whole rounds of `unit` threads.
+template <int A>
+std::vector<std::vector<int>> constraint_phases(int n, const int32_t* cons, const std::vector<int32_t>& order,
+                                                const std::vector<int32_t>& off, int n_col, int V, int unit) {
+    std::vector<std::vector<int>> ph;
+    if (unit <= 0) {
+        for (int c = 0; c < n_col; ++c) ph.emplace_back(order.begin() + off[c], order.begin() + off[c + 1]);
+        return ph;
+    }
+    std::vector<int> pos(n), last(V, -1), sc_off(n + 1, 0), npred(n, 0), height(n, 1);
+    for (int q = 0; q < n; ++q) pos[order[q]] = q;
+    // dependency edges: consecutive constraints of each vertex's sequence
+    std::vector<std::pair<int, int>> dep;
+    dep.reserve(size_t(A) * n);
+    for (int q = 0; q < n; ++q) {
+        const int i = order[q];
+        for (int k = 0; k < A; ++k) {
+            const int v = cons[A * i + k];
+            if (last[v] >= 0) dep.emplace_back(last[v], i);
+            last[v] = i;
+        }
+    }
+    for (const auto& d : dep) ++sc_off[d.first + 1];
+    for (int i = 0; i < n; ++i) sc_off[i + 1] += sc_off[i];
+    std::vector<int> succ(dep.size()), fill(sc_off.begin(), sc_off.end() - 1);
+    for (const auto& d : dep) {
+        succ[fill[d.first]++] = d.second;
+        ++npred[d.second];
+    }
+    for (int q = n - 1; q >= 0; --q) {
+        const int i = order[q];
+        for (int e = sc_off[i]; e < sc_off[i + 1]; ++e) height[i] = std::max(height[i], height[succ[e]] + 1);
+    }
+    auto key = [&](int i) { return (int64_t(height[i]) << 32) | int64_t(uint32_t(n - 1 - pos[i])); };
+    std::priority_queue<std::pair<int64_t, int>> ready;
+    for (int i = 0; i < n; ++i)
+        if (npred[i] == 0) ready.push({key(i), i});
+    int placed = 0;
+    std::vector<int> fresh;
+    while (placed < n) {
+        const int k = int(ready.size());
+        const int take = k < unit ? k : k / unit * unit;
+        std::vector<int> phase(take);
+        for (int t = 0; t < take; ++t) {
+            phase[t] = ready.top().second;
+            ready.pop();
+        }
+        fresh.clear();
+        for (int i : phase)
+            for (int e = sc_off[i]; e < sc_off[i + 1]; ++e)
+                if (--npred[succ[e]] == 0) fresh.push_back(succ[e]);
+        for (int i : fresh) ready.push({key(i), i});
+        std::sort(phase.begin(), phase.end(), [&](int a, int b) { return pos[a] < pos[b]; });
+        placed += take;
+        ph.push_back(std::move(phase));
+    }
+    return ph;
+}
+
 // Slots of the vertices: a permutation inside each aligned block of 32
 // vertices (so vertex-order passes stay coalesced), chosen by descent on the
 // imbalance of bank groups per (colour, vertex position): sum over keys and
 // groups of the count above ceil(n_key / 8). Moves swap the slots of two
 // vertices of one block in different bank groups; `iters` moves are tried.
-std::vector<int> balanced_slots(const HostMesh& m, std::mt19937_64& rng, long long iters) {
-    const int V = m.V, ne = m.n_ecol, nt = m.n_tcol, K = 2 * ne + 4 * nt + 4 * m.n_ccol;
+std::vector<int> balanced_slots(const HostMesh& m, const std::vector<int>& ephase, int ne,
+                                const std::vector<int>& tphase, int nt, const std::vector<int>& cphase, int nc,
+                                std::mt19937_64& rng, long long iters) {
+    const int V = m.V, K = 2 * ne + 4 * nt + 4 * nc;
     std::vector<int> slot(V);
     for (int b = 0; b < V; b += 32) {   // a permutation inside each aligned block of 32 vertices
         const int n = std::min(32, V - b);
@@ -431,19 +502,19 @@ std::vector<int> balanced_slots(const HostMesh& m, std::mt19937_64& rng, long lo
     std::vector<int> fill(off.begin(), off.end() - 1), n_key(K, 0);
     for (int e = 0; e < m.E; ++e)
         for (int p = 0; p < 2; ++p) {
-            const int k = 2 * m.ecolor[e] + p;
+            const int k = 2 * ephase[e] + p;
             keys[fill[m.edge[2 * e + p]]++] = k;
             ++n_key[k];
         }
     for (int t = 0; t < m.T; ++t)
         for (int p = 0; p < 4; ++p) {
-            const int k = 2 * ne + 4 * m.tcolor[t] + p;
+            const int k = 2 * ne + 4 * tphase[t] + p;
             keys[fill[m.tet[4 * t + p]]++] = k;
             ++n_key[k];
         }
     for (int c = 0; c < m.C; ++c)
         for (int p = 0; p < 4; ++p) {
-            const int k = 2 * ne + 4 * nt + 4 * m.ccolor[c] + p;
+            const int k = 2 * ne + 4 * nt + 4 * cphase[c] + p;
             keys[fill[m.conn[4 * c + p]]++] = k;
             ++n_key[k];
         }
@@ -501,9 +572,24 @@ void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& ou
     out.slot_of.resize(V);
     out.vert_of.resize(V);
     std::mt19937_64 rng(seed);
+    // phases of each family (the colours unless permuted; see constraint_phases)
+    const int unit = permute ? kPhaseUnit : 0;
+    const auto eph = constraint_phases<2>(m.E, m.edge.data(), m.eorder, m.ecol_off, m.n_ecol, V, unit);
+    const auto tph = constraint_phases<4>(m.T, m.tet.data(), m.torder, m.tcol_off, m.n_tcol, V, unit);
+    const auto cph = constraint_phases<4>(m.C, m.conn.data(), m.corder, m.ccol_off, m.n_ccol, V, unit);
+    out.n_ephase = int(eph.size());
+    out.n_tphase = int(tph.size());
+    out.n_cphase = int(cph.size());
     std::vector<int> slot(V);
     if (permute) {
-        slot = balanced_slots(m, rng, 100ll * V);
+        std::vector<int> ep(m.E), tp(m.T), cp(m.C);
+        for (int q = 0; q < out.n_ephase; ++q)
+            for (int e : eph[q]) ep[e] = q;
+        for (int q = 0; q < out.n_tphase; ++q)
+            for (int t : tph[q]) tp[t] = q;
+        for (int q = 0; q < out.n_cphase; ++q)
+            for (int c : cph[q]) cp[c] = q;
+        slot = balanced_slots(m, ep, out.n_ephase, tp, out.n_tphase, cp, out.n_cphase, rng, 100ll * V);
     } else {
         for (int i = 0; i < V; ++i) slot[i] = i;
     }
@@ -512,15 +598,13 @@ void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& ou
         out.vert_of[slot[i]] = uint16_t(i);
     }
     const int P = out.part_slots;
-    for (int c = 0; c < m.n_ecol; ++c) {
-        const int beg = m.ecol_off[c], end = m.ecol_off[c + 1];
+    int first = 0;   // multiplier slot of the next record
+    for (const std::vector<int>& phase : eph) {
         std::vector<std::vector<Rec>> part(parts);
-        for (int q = beg; q < end; ++q) {
-            const int e = m.eorder[q];
+        for (int e : phase) {
             const Rec r = {out.slot_of[m.edge[2 * e]], out.slot_of[m.edge[2 * e + 1]], 0, 0, e};
             part[r[0] / P].push_back(r);
         }
-        int first = beg;
         for (std::vector<Rec>& r : part) {
             const int n = int(r.size());
             if (permute) {
@@ -539,16 +623,13 @@ void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& ou
             first += n;
         }
     }
-    for (int c = 0; c < m.n_tcol; ++c) {
-        const int beg = m.tcol_off[c], end = m.tcol_off[c + 1];
+    for (const std::vector<int>& phase : tph) {
         std::vector<std::vector<Rec>> part(parts);
-        for (int q = beg; q < end; ++q) {
-            const int t = m.torder[q];
+        for (int t : phase) {
             const Rec r = {out.slot_of[m.tet[4 * t]], out.slot_of[m.tet[4 * t + 1]], out.slot_of[m.tet[4 * t + 2]],
                            out.slot_of[m.tet[4 * t + 3]], t};
             part[r[0] / P].push_back(r);
         }
-        int first = m.E + beg;
         for (std::vector<Rec>& r : part) {
             const int n = int(r.size());
             if (permute) {
@@ -570,16 +651,13 @@ void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& ou
         }
     }
     // Tissue connections: records (vertex, face triple) like tets, d0 in z.
-    for (int c = 0; c < m.n_ccol; ++c) {
-        const int beg = m.ccol_off[c], end = m.ccol_off[c + 1];
+    for (const std::vector<int>& phase : cph) {
         std::vector<std::vector<Rec>> part(parts);
-        for (int q = beg; q < end; ++q) {
-            const int k = m.corder[q];
+        for (int k : phase) {
             const Rec r = {out.slot_of[m.conn[4 * k]], out.slot_of[m.conn[4 * k + 1]], out.slot_of[m.conn[4 * k + 2]],
                            out.slot_of[m.conn[4 * k + 3]], k};
             part[r[0] / P].push_back(r);
         }
-        int first = m.E + m.T + beg;
         for (std::vector<Rec>& r : part) {
             const int n = int(r.size());
             if (permute) {

@@ -55,9 +55,12 @@ int build_host_mesh(int V, int T, const double* rest, const double* inv_mass,
 int build_connections(HostMesh& m, const double* rest, double conn_radius, std::string& err);
 
 // Execution schedule of one mesh on the GPU: vertex -> shared-memory slot map
-// and the colour-major constraint stream (edge colours, then tet colours,
-// then connection colours),
-// each colour a 16-byte aligned segment of records.
+// and the constraint stream in phases (edge phases, then tet phases, then
+// connection phases), each phase a 16-byte aligned segment of records. The
+// phases are the colours, or (permuted schedules) a refinement of the
+// colouring into phases of whole multiples of kPhaseUnit constraints that
+// keeps, at every vertex, the colour order of the constraints containing it,
+// and therefore gives the same bits.
 struct Schedule {
     std::vector<uint16_t> slot_of, vert_of;  // [V]
     std::vector<unsigned char> stream;       // records
@@ -65,18 +68,23 @@ struct Schedule {
     int ring_bytes = 0;                      // largest segment
     int parts = 1;                           // segments per colour (one per cluster CTA)
     int part_slots = 0;                      // slots per part (multiple of 32)
+    int n_ephase = 0, n_tphase = 0, n_cphase = 0;   // phases per family
 };
 
+constexpr int kPhaseUnit = 256;              // threads per env of the common step configuration
+
 // Builds the schedule. Slots are a fixed permutation inside each aligned
-// block of 32 vertices (seeded by `seed`); inside each colour the records are
+// block of 32 vertices (seeded by `seed`); inside each phase the records are
 // grouped so that the 8 records of every aligned group of 8 use distinct
 // slot residues modulo 8 in each vertex position where possible (distinct
-// shared-memory bank groups for 16-byte accesses). Both choices leave the
-// result unchanged: a colour's constraints touch disjoint vertices.
+// shared-memory bank groups for 16-byte accesses). With `permute` the phases
+// are the refinement described above, else the colours. None of these
+// choices changes the result: a phase's constraints touch disjoint vertices
+// and every vertex sees its constraints in colour order.
 // With parts > 1 the slots are split into `parts` ranges of part_slots slots
-// (one per CTA of a thread-block cluster) and every colour into `parts`
+// (one per CTA of a thread-block cluster) and every phase into `parts`
 // segments, segment r holding the records whose first vertex lies in range r
-// (segments ordered colour-major, part-minor).
+// (segments ordered phase-major, part-minor).
 void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& out, int parts = 1);
 
 }  // namespace ffsrl
