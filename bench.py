@@ -642,11 +642,14 @@ def run_ours(args):
     params = batch.params
     n_env = batch.n_env
     block, flags = 0, 0
-    if args.schedule:   # forced schedule "threads_per_env:envs_per_cta:ring:permute" (profiling)
-        sub, envs, ring, perm = (int(x) for x in args.schedule.split(":"))
+    if args.schedule:   # forced schedule "threads_per_env:envs_per_cta:ring:permute[:ctas_per_sm]" (profiling)
+        fields = [int(x) for x in args.schedule.split(":")]
+        sub, envs, ring, perm = fields[:4]
         block = sub
         flags = ffsrl.SCHED_FORCE | (0 if ring else ffsrl.SCHED_NO_RING) | (0 if perm else ffsrl.SCHED_NO_PERMUTE)
         flags |= {1: 0, 2: ffsrl.SCHED_ENVS2, 4: ffsrl.SCHED_ENVS4}[envs]
+        if len(fields) > 4 and fields[4] == 4:
+            flags |= ffsrl.SCHED_FOUR_CTAS
     sim = ffsrl.Sim(batch.meshes, params, n_env, env_mesh=batch.env_mesh, env_compliance=batch.env_alpha,
                     block_threads=block, schedule_flags=flags)
     seed = sharding.rank_seed(args.seed, rank)   # each rank owns its own env shard
@@ -723,7 +726,7 @@ def run_ours(args):
         traffic = ncu_traffic("xpbd_step_block17x17x9_4096env.txt") if (
             single and n_env == 4096 and counts[0][0] == 2601) else None
         kernel = (f"xpbd_step_kernel<{sim.block_threads},{sim.envs_per_cta},resident,"
-                  f"{'ring' if sim.ring_envs else 'l2'}>" if single else
+                  f"{'ring' if sim.ring_envs else 'l2'}> ({sim.ctas_per_sm} CTAs/SM)" if single else
                   f"xpbd_step_kernel, {sim.n_groups} size classes launched concurrently")
         roofline = {"bound": "smem", "achieved": smem_bytes / sec / 1e9, "peak": smem_peak, "unit": "GB/s",
                     "frac": smem_bytes / sec / 1e9 / smem_peak, "traffic": traffic, "kernel": kernel,
@@ -798,6 +801,7 @@ def run_ours(args):
                            "l2": f"state {24 * V_total / 1e6:.0f} MB > 129 MB L2, no flush",
                            "parallelism": f"env-sharded x{world}",
                            "schedule": {"threads_per_env": sim.block_threads, "envs_per_cta": sim.envs_per_cta,
+                                        "ctas_per_sm": sim.ctas_per_sm,
                                         "tma_ring_envs": sim.ring_envs,
                                         "resident_envs": sim.resident_envs, "launch_groups": sim.n_groups}},
                 "roofline": roofline, "cpu_baseline": cpu, "accuracy": acc, "e2e": e2e, "latency": latency,
@@ -828,7 +832,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--envs", type=int, default=0, help="override the workload's env count")
-    ap.add_argument("--schedule", default="", help="force threads_per_env:envs_per_cta:ring:permute")
+    ap.add_argument("--schedule", default="", help="force threads_per_env:envs_per_cta:ring:permute[:ctas_per_sm]")
     ap.add_argument("--acc-steps", type=int, default=50, help="steps of the warm-start accuracy comparison")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -126,6 +126,9 @@ typedef struct {
                                               network, substep) instead of one fused kernel */
 #define FFSRL_SCHED_NO_CLUSTER 64  /* meshes above one CTA's shared memory use the global-memory
                                       working copy instead of a thread-block cluster */
+#define FFSRL_SCHED_FOUR_CTAS 128  /* with FFSRL_SCHED_FORCE: the 256-thread, one-env, resident, ring
+                                      kernel with registers budgeted for four CTAs per SM (64 per
+                                      thread); FFSRL_E_INVAL where four CTAs do not fit an SM */
 
 /* Sizes of a created simulator. */
 typedef struct {
@@ -139,7 +142,7 @@ typedef struct {
     int32_t n_groups;         /* step-kernel launches per step */
     int32_t ring_envs;        /* envs whose constraint records stream through the TMA ring */
     int32_t envs_per_cta;     /* envs sharing one CTA (largest group) */
-    int32_t reserved;
+    int32_t ctas_per_sm;      /* CTAs per SM the step kernel's registers are budgeted for (largest group) */
 } ffsrl_info;
 
 /* Creates n_env environments; env e uses meshes[env_mesh[e]] (env_mesh NULL:

@@ -205,7 +205,7 @@ int check_params(const ffsrl_params& p) {
         return fail(FFSRL_E_INVAL, "block_threads must be 0, 128, 256, 384, 512 or 1024");
     if (p.schedule_flags & ~(FFSRL_SCHED_FORCE | FFSRL_SCHED_NO_PERMUTE | FFSRL_SCHED_NO_RING |
                              FFSRL_SCHED_ENVS2 | FFSRL_SCHED_ENVS4 | FFSRL_SCHED_SURROGATE_PIPELINE |
-                             FFSRL_SCHED_NO_CLUSTER))
+                             FFSRL_SCHED_NO_CLUSTER | FFSRL_SCHED_FOUR_CTAS))
         return fail(FFSRL_E_INVAL, "unknown schedule_flags bits");
     if ((p.schedule_flags & FFSRL_SCHED_ENVS2) && (p.schedule_flags & FFSRL_SCHED_ENVS4))
         return fail(FFSRL_E_INVAL, "FFSRL_SCHED_ENVS2 and FFSRL_SCHED_ENVS4 are exclusive");
@@ -382,9 +382,12 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, const Schedule& sc, MeshDev& d)
 
 // Shared memory a configuration needs, or 0 if it is not compiled or does not fit.
 size_t group_smem(const ffsrl_sim* s, const MeshDev& d, const StepConfig& c) {
-    if (!step_config_supported(c.sub, c.envs, c.resident, c.ring)) return 0;
+    if (!step_config_supported(c.sub, c.envs, c.resident, c.ring, c.occ)) return 0;
     const size_t b = step_smem_bytes(d.Vp, c.resident, c.ring, d.ring_bytes, d.n_seg, c.envs);
-    return b + 256 <= s->max_smem ? b : 0;  // room for the kernel's static shared memory
+    if (b + 256 > s->max_smem) return 0;  // room for the kernel's static shared memory
+    // the 4-CTA register budget only pays when four CTAs fit an SM's shared memory
+    if (c.occ && step_max_active(c, b) < c.occ) return 0;
+    return b;
 }
 
 // Largest shared memory over the meshes of a group (0 if one does not fit).
@@ -481,6 +484,7 @@ int autotune_group(ffsrl_sim* s, LaunchGroup& g) {
         c.envs = (p.schedule_flags & FFSRL_SCHED_ENVS4) ? 4 : (p.schedule_flags & FFSRL_SCHED_ENVS2) ? 2 : 1;
         c.resident = resident;
         c.ring = force_ring;
+        c.occ = (p.schedule_flags & FFSRL_SCHED_FOUR_CTAS) ? 4 : 0;
         cands.push_back(c);
     } else {
         const std::vector<int> subs = p.block_threads ? std::vector<int>{p.block_threads}
@@ -494,6 +498,10 @@ int autotune_group(ffsrl_sim* s, LaunchGroup& g) {
                     c.resident = resident;
                     c.ring = ring;
                     cands.push_back(c);
+                    if (sub == 256 && envs == 1 && ring && resident) {
+                        c.occ = 4;   // the same kernel budgeted for four CTAs per SM
+                        cands.push_back(c);
+                    }
                 }
     }
     std::vector<int> perm_opts = force_sched ? std::vector<int>{force_perm ? 1 : 0} : std::vector<int>{1, 0};
@@ -526,8 +534,9 @@ int autotune_group(ffsrl_sim* s, LaunchGroup& g) {
             float ms = 0;
             FFSRL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
             if (std::getenv("FFSRL_TUNE_LOG"))
-                std::fprintf(stderr, "ffsrl autotune meshes=%zu envs=%d resident=%d: sub=%d envs_per_cta=%d ring=%d permute=%d %.3f ms\n",
-                             g.meshes.size(), g.n, int(resident), cd.c.sub, cd.c.envs, int(cd.c.ring), int(cd.perm), ms / 2);
+                std::fprintf(stderr, "ffsrl autotune meshes=%zu envs=%d resident=%d: sub=%d envs_per_cta=%d ring=%d occ=%d permute=%d %.3f ms\n",
+                             g.meshes.size(), g.n, int(resident), cd.c.sub, cd.c.envs, int(cd.c.ring), cd.c.occ,
+                             int(cd.perm), ms / 2);
             if (ms < best.ms) best = {cd.c, cd.perm, ms};
         }
         cudaEventDestroy(e0);
@@ -1405,6 +1414,7 @@ int ffsrl_get_info(const ffsrl_sim* sim, ffsrl_info* out) {
     out->total_verts = sim->total_verts;
     out->block_threads = sim->groups.empty() ? 0 : sim->groups.front().cfg.sub;
     out->envs_per_cta = sim->groups.empty() ? 0 : sim->groups.front().cfg.envs;
+    out->ctas_per_sm = sim->groups.empty() ? 0 : step_ctas_per_sm(sim->groups.front().cfg);
     out->resident_envs = sim->resident_envs;
     out->n_groups = int(sim->groups.size());
     out->ring_envs = sim->ring_envs;

@@ -412,11 +412,13 @@ void group_improve(std::vector<Rec>& g, std::mt19937_64& rng, long long iters, b
 // phase is then automatically free of shared vertices). unit = 0: the colours
 // are the phases. unit > 0: list scheduling over that dependency graph,
 // longest remaining chain first (then oracle order), closes each phase at a
-// whole multiple of `unit` ready constraints (all of them when fewer are
-// ready), so that a phase costs whole rounds of `unit` threads.
+// whole multiple of `unit` ready constraints, at most `cap` (all of them when
+// fewer than `unit` are ready), so that a phase costs whole rounds of `unit`
+// threads and its records fit a small ring stage.
 template <int A>
 std::vector<std::vector<int>> constraint_phases(int n, const int32_t* cons, const std::vector<int32_t>& order,
-                                                const std::vector<int32_t>& off, int n_col, int V, int unit) {
+                                                const std::vector<int32_t>& off, int n_col, int V, int unit,
+                                                int cap) {
     std::vector<std::vector<int>> ph;
     if (unit <= 0) {
         for (int c = 0; c < n_col; ++c) ph.emplace_back(order.begin() + off[c], order.begin() + off[c + 1]);
@@ -454,7 +456,7 @@ std::vector<std::vector<int>> constraint_phases(int n, const int32_t* cons, cons
     std::vector<int> fresh;
     while (placed < n) {
         const int k = int(ready.size());
-        const int take = k < unit ? k : k / unit * unit;
+        const int take = k < unit ? k : std::min(cap, k / unit * unit);
         std::vector<int> phase(take);
         for (int t = 0; t < take; ++t) {
             phase[t] = ready.top().second;
@@ -574,9 +576,10 @@ void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& ou
     std::mt19937_64 rng(seed);
     // phases of each family (the colours unless permuted; see constraint_phases)
     const int unit = permute ? kPhaseUnit : 0;
-    const auto eph = constraint_phases<2>(m.E, m.edge.data(), m.eorder, m.ecol_off, m.n_ecol, V, unit);
-    const auto tph = constraint_phases<4>(m.T, m.tet.data(), m.torder, m.tcol_off, m.n_tcol, V, unit);
-    const auto cph = constraint_phases<4>(m.C, m.conn.data(), m.corder, m.ccol_off, m.n_ccol, V, unit);
+    // (phases of at most 4 KB of records: 512 edges, 256 tets or connections)
+    const auto eph = constraint_phases<2>(m.E, m.edge.data(), m.eorder, m.ecol_off, m.n_ecol, V, unit, 2 * unit);
+    const auto tph = constraint_phases<4>(m.T, m.tet.data(), m.torder, m.tcol_off, m.n_tcol, V, unit, unit);
+    const auto cph = constraint_phases<4>(m.C, m.conn.data(), m.corder, m.ccol_off, m.n_ccol, V, unit, unit);
     out.n_ephase = int(eph.size());
     out.n_tphase = int(tph.size());
     out.n_cphase = int(cph.size());

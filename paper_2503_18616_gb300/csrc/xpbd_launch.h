@@ -15,6 +15,7 @@ struct StepConfig {
     int envs = 1;         // envs per CTA (sharing one constraint ring)
     bool resident = true; // positions in shared memory
     bool ring = true;     // constraint records through the TMA double buffer
+    int occ = 0;          // CTAs per SM the registers are budgeted for (0: the block size's default)
 };
 
 // Dynamic shared memory of one step CTA: positions of its envs (resident
@@ -22,8 +23,8 @@ struct StepConfig {
 // contact bits.
 size_t step_smem_bytes(int Vp, bool resident, bool ring, int ring_bytes, int n_seg, int envs);
 
-// Whether a (sub, envs, resident, ring) combination is compiled.
-bool step_config_supported(int sub, int envs, bool resident, bool ring);
+// Whether a (sub, envs, resident, ring, occ) combination is compiled.
+bool step_config_supported(int sub, int envs, bool resident, bool ring, int occ = 0);
 
 // Step kernel over the n_list envs of env_list (NULL: envs 0..n_list-1), all of one mesh.
 cudaError_t launch_step(const SimDev& S, const StepConfig& c, const int* env_list, int n_list,
@@ -32,6 +33,10 @@ cudaError_t launch_step(const SimDev& S, const StepConfig& c, const int* env_lis
 // Sets the kernel's dynamic shared-memory limit for a launch of this size
 // (done by launch_step too; called ahead of stream capture).
 cudaError_t configure_step(const StepConfig& c, size_t smem_bytes);
+// CTAs of this configuration that fit one SM with smem_bytes of dynamic shared memory.
+int step_max_active(const StepConfig& c, size_t smem_bytes);
+// CTAs per SM the configuration's registers are budgeted for.
+int step_ctas_per_sm(const StepConfig& c);
 // Cluster step (xpbd_cluster.cu): envs whose mesh variant has parts = cl
 // ranges, sub threads per CTA, cl CTAs per env; smem from cluster_smem_bytes.
 constexpr int kClusterThreads = 1024;   // threads per CTA of the cluster kernel

@@ -106,8 +106,8 @@ constexpr int min_ctas_per_sm(int block) {
 
 // One CTA advances ENVS environments of the same mesh, SUB threads each; the
 // envs share the constraint ring and the CTA's barriers.
-template <int SUB, int ENVS, bool RES, bool RING>
-__global__ void __launch_bounds__(SUB * ENVS, min_ctas_per_sm(SUB * ENVS))
+template <int SUB, int ENVS, bool RES, bool RING, int OCC = 0>
+__global__ void __launch_bounds__(SUB * ENVS, OCC ? OCC : min_ctas_per_sm(SUB * ENVS))
     xpbd_step_kernel(SimDev S, const int* __restrict__ env_list, int n_list, const float* __restrict__ actions,
                      float* __restrict__ obs, float* __restrict__ reward, uint8_t* __restrict__ done) {
     constexpr int BLOCK = SUB * ENVS;
@@ -571,14 +571,14 @@ __global__ void unpack_state_kernel(SimDev S, const int* __restrict__ pstart, co
 // Launchers
 // ---------------------------------------------------------------------------
 
-template <int SUB, int ENVS, bool RES, bool RING>
+template <int SUB, int ENVS, bool RES, bool RING, int OCC = 0>
 static cudaError_t configure_one(size_t smem) {
     // Raise the kernel's dynamic shared-memory limit to what a launch needs
     // (the limit plus the kernel's static shared memory must stay within the
     // device's per-block opt-in maximum).
     static size_t configured = 48 * 1024;
     if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(xpbd_step_kernel<SUB, ENVS, RES, RING>,
+        cudaError_t e = cudaFuncSetAttribute(xpbd_step_kernel<SUB, ENVS, RES, RING, OCC>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
         configured = smem;
@@ -586,18 +586,19 @@ static cudaError_t configure_one(size_t smem) {
     return cudaSuccess;
 }
 
-template <int SUB, int ENVS, bool RES, bool RING>
+template <int SUB, int ENVS, bool RES, bool RING, int OCC = 0>
 static cudaError_t launch_one(const SimDev& S, const int* env_list, int n_list, size_t smem, cudaStream_t st,
                               const float* actions, float* obs, float* reward, uint8_t* done) {
-    const cudaError_t ce = configure_one<SUB, ENVS, RES, RING>(smem);
+    const cudaError_t ce = configure_one<SUB, ENVS, RES, RING, OCC>(smem);
     if (ce != cudaSuccess) return ce;
     const int n_blocks = (n_list + ENVS - 1) / ENVS;
-    xpbd_step_kernel<SUB, ENVS, RES, RING>
+    xpbd_step_kernel<SUB, ENVS, RES, RING, OCC>
         <<<n_blocks, SUB * ENVS, smem, st>>>(S, env_list, n_list, actions, obs, reward, done);
     return cudaGetLastError();
 }
 
-bool step_config_supported(int sub, int envs, bool resident, bool ring) {
+bool step_config_supported(int sub, int envs, bool resident, bool ring, int occ) {
+    if (occ) return occ == 4 && sub == 256 && envs == 1 && resident && ring;   // 64 registers, 4 CTAs per SM
     if (envs == 1) return sub == 128 || sub == 256 || sub == 384 || sub == 512 || sub == 1024;
     if (!resident || !ring) return false;
     if (envs == 2) return sub == 128 || sub == 256 || sub == 384 || sub == 512;
@@ -609,6 +610,9 @@ cudaError_t launch_step(const SimDev& S, const StepConfig& c, const int* env_lis
                         size_t smem_bytes, cudaStream_t stream, const float* a, float* o, float* r,
                         uint8_t* d) {
     if (n_list <= 0) return cudaSuccess;
+    if (c.occ == 4 && c.sub == 256 && c.envs == 1 && c.resident && c.ring)
+        return launch_one<256, 1, true, true, 4>(S, env_list, n_list, smem_bytes, stream, a, o, r, d);
+    if (c.occ) return cudaErrorInvalidValue;
 #define FFSRL_CASE(SUB_, ENVS_, RES_, RING_)                                                      \
     if (c.sub == SUB_ && c.envs == ENVS_ && c.resident == RES_ && c.ring == RING_)                \
         return launch_one<SUB_, ENVS_, RES_, RING_>(S, env_list, n_list, smem_bytes, stream, a, o, r, d);
@@ -631,7 +635,23 @@ cudaError_t launch_step(const SimDev& S, const StepConfig& c, const int* env_lis
     return cudaErrorInvalidValue;
 }
 
+int step_ctas_per_sm(const StepConfig& c) { return c.occ ? c.occ : min_ctas_per_sm(c.sub * c.envs); }
+
+int step_max_active(const StepConfig& c, size_t smem_bytes) {
+    int n = 0;
+    if (c.occ == 4 && c.sub == 256 && c.envs == 1 && c.resident && c.ring) {
+        if (configure_one<256, 1, true, true, 4>(smem_bytes) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, xpbd_step_kernel<256, 1, true, true, 4>, 256,
+                                                          smem_bytes) != cudaSuccess)
+            return 0;
+    }
+    return n;
+}
+
 cudaError_t configure_step(const StepConfig& c, size_t smem_bytes) {
+    if (c.occ == 4 && c.sub == 256 && c.envs == 1 && c.resident && c.ring)
+        return configure_one<256, 1, true, true, 4>(smem_bytes);
+    if (c.occ) return cudaErrorInvalidValue;
 #define FFSRL_CASE(SUB_, ENVS_, RES_, RING_)                                                      \
     if (c.sub == SUB_ && c.envs == ENVS_ && c.resident == RES_ && c.ring == RING_)                \
         return configure_one<SUB_, ENVS_, RES_, RING_>(smem_bytes);

@@ -68,6 +68,7 @@ class ffsrl_params(ctypes.Structure):
 SCHED_FORCE, SCHED_NO_PERMUTE, SCHED_NO_RING, SCHED_ENVS2, SCHED_ENVS4 = 1, 2, 4, 8, 16
 SCHED_SURROGATE_PIPELINE = 32
 SCHED_NO_CLUSTER = 64
+SCHED_FOUR_CTAS = 128
 
 
 class ffsrl_info(ctypes.Structure):
@@ -75,7 +76,7 @@ class ffsrl_info(ctypes.Structure):
                 ("max_verts", ctypes.c_int32), ("total_verts", ctypes.c_int64),
                 ("block_threads", ctypes.c_int32), ("resident_envs", ctypes.c_int32),
                 ("n_groups", ctypes.c_int32), ("ring_envs", ctypes.c_int32),
-                ("envs_per_cta", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("envs_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32)]
 
 
 def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
@@ -231,6 +232,7 @@ class Sim:
         self.n_groups = info.n_groups
         self.ring_envs = info.ring_envs
         self.envs_per_cta = info.envs_per_cta
+        self.ctas_per_sm = info.ctas_per_sm
         self.device = torch.device("cuda", torch.cuda.current_device())
 
     def close(self) -> None:

@@ -423,6 +423,33 @@ def test_every_schedule_gives_bit_identical_results():
         sim.close()
 
 
+def test_refined_phases_and_four_cta_kernel_give_the_colour_schedule_bits():
+    """On the 17x17x9 block the permuted schedule refines the 18 + 37 colours
+    into phases of whole multiples of 256 constraints (every vertex still
+    sees its constraints in colour order). The colour phases (no permutation),
+    the refined phases, and the kernel budgeted for four CTAs per SM must give
+    the same bits, with one and with two iterations."""
+    from paper_2503_18616_gb300 import ffsrl
+    m = grid((17, 17, 9))
+    for iters in (1, 2):
+        p = P(iterations=iters)
+        n_env, steps = 4, 6
+        ref = None
+        for flags in (ffsrl.SCHED_NO_PERMUTE, 0, ffsrl.SCHED_FOUR_CTAS):
+            sim = make_sim([m], p, n_env, block_threads=256, schedule_flags=ffsrl.SCHED_FORCE | flags, seed=8)
+            assert sim.ctas_per_sm == (4 if flags & ffsrl.SCHED_FOUR_CTAS else 3)
+            for _ in range(steps):
+                obs, rew, done = sim.step()
+            x, v, _ = sim.get_state()
+            out = (x.cpu().numpy(), v.cpu().numpy(), obs.cpu().numpy(), rew.cpu().numpy())
+            if ref is None:
+                ref = out
+            else:
+                for a, b in zip(ref, out):
+                    assert np.array_equal(a, b), (flags, iters)
+            sim.close()
+
+
 def test_uneven_1024_env_batch_sampled():
     """The uneven-batching configuration: 1024 envs, vertex counts log-uniform in
     [500, 20000] (37 block sizes), per-env edge compliance, all size classes
