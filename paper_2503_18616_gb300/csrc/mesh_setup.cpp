@@ -575,7 +575,7 @@ void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& ou
     out.vert_of.resize(V);
     std::mt19937_64 rng(seed);
     // phases of each family (the colours unless permuted; see constraint_phases)
-    const int unit = permute ? kPhaseUnit : 0;
+    const int unit = (permute && parts == 1 && V <= kPhaseMaxVerts) ? kPhaseUnit : 0;
     // (phases of at most 4 KB of records: 512 edges, 256 tets or connections)
     const auto eph = constraint_phases<2>(m.E, m.edge.data(), m.eorder, m.ecol_off, m.n_ecol, V, unit, 2 * unit);
     const auto tph = constraint_phases<4>(m.T, m.tet.data(), m.torder, m.tcol_off, m.n_tcol, V, unit, unit);

@@ -72,13 +72,19 @@ struct Schedule {
 };
 
 constexpr int kPhaseUnit = 256;              // threads per env of the common step configuration
+// Refined phases (capped at 4 KB of records) are built for meshes small enough
+// that four such CTAs fit an SM; larger meshes run more threads per env (or a
+// cluster) and keep the colours, where extra phase barriers would cost more
+// than the thread rounds they save.
+constexpr int kPhaseMaxVerts = 2944;
 
 // Builds the schedule. Slots are a fixed permutation inside each aligned
 // block of 32 vertices (seeded by `seed`); inside each phase the records are
 // grouped so that the 8 records of every aligned group of 8 use distinct
 // slot residues modulo 8 in each vertex position where possible (distinct
-// shared-memory bank groups for 16-byte accesses). With `permute` the phases
-// are the refinement described above, else the colours. None of these
+// shared-memory bank groups for 16-byte accesses). With `permute` (one part,
+// at most kPhaseMaxVerts vertices) the phases are the refinement described
+// above, else the colours. None of these
 // choices changes the result: a phase's constraints touch disjoint vertices
 // and every vertex sees its constraints in colour order.
 // With parts > 1 the slots are split into `parts` ranges of part_slots slots
