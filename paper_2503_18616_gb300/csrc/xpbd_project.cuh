@@ -27,10 +27,11 @@ __device__ __forceinline__ bool edge_update(float4& xa, float4& xb, float d, flo
     const float l2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
     const float denom = __fadd_rn(__fadd_rn(xa.w, xb.w), at);
     if (l2 < min_len2 || denom == 0.f) return false;
-    const float len = sqrtf(l2);
+    const float il = rsqrtf(l2);               // 1/|x_ab| (hardware estimate, within 2 ulp)
+    const float len = __fmul_rn(l2, il);
     const float C = __fsub_rn(len, d);
     const float dl = __fdividef(__fmaf_rn(-at, lam, -C), denom);
-    const float s = __fdividef(dl, len);
+    const float s = __fmul_rn(dl, il);
     const float sa = __fmul_rn(xa.w, s), sb = __fmul_rn(xb.w, s);
     xa.x = __fmaf_rn(sa, dx, xa.x); xa.y = __fmaf_rn(sa, dy, xa.y); xa.z = __fmaf_rn(sa, dz, xa.z);
     xb.x = __fmaf_rn(-sb, dx, xb.x); xb.y = __fmaf_rn(-sb, dy, xb.y); xb.z = __fmaf_rn(-sb, dz, xb.z);
