@@ -319,11 +319,13 @@ def run_e2e(args, sim, n_env, world, rank, seed, barrier, dist):
     import numpy as np
     import torch
     from paper_2503_18616_gb300 import inputs
-    pool = inputs.random_actions(8, n_env, 11 + rank).astype(np.float32)   # a fresh action array per step
-
-    h_obs = np.empty((n_env, sim.obs_dim), np.float32)
-    h_rew = np.empty(n_env, np.float32)
-    h_done = np.empty(n_env, np.uint8)
+    draws = inputs.random_actions(8, n_env, 11 + rank).astype(np.float32)
+    # page-locked host buffers: a fresh action array per step, and the outputs
+    pool = []
+    for k in range(len(draws)):
+        a, h_obs, h_rew, h_done = sim.pinned_host_buffers()
+        a[:] = draws[k]
+        pool.append(a)
     sim.reset(seed)
     for k in range(args.warmup):
         sim.step_host(pool[k % len(pool)], h_obs, h_rew, h_done)

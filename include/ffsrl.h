@@ -171,7 +171,9 @@ int ffsrl_step(ffsrl_sim* sim, const float* actions_dev, float* obs_dev, float* 
                uint8_t* done_dev);
 
 /* ffsrl_step with host buffers: copies actions_host in, runs the step, copies
- * the outputs back and waits for them (pinned staging buffers owned by sim). */
+ * the outputs back and waits for them. Page-locked caller buffers
+ * (cudaHostAlloc or registered) are copied directly; others go through
+ * page-locked staging buffers owned by sim. */
 int ffsrl_step_host(ffsrl_sim* sim, const float* actions_host, float* obs_host,
                     float* reward_host, uint8_t* done_host);
 

@@ -985,6 +985,18 @@ int ffsrl_step(ffsrl_sim* sim, const float* actions_dev, float* obs_dev, float* 
     return FFSRL_OK;
 }
 
+// Whether p is page-locked host memory (cudaHostAlloc or registered), which
+// the copy engines read and write directly.
+static bool page_locked(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 int ffsrl_step_host(ffsrl_sim* sim, const float* actions_host, float* obs_host, float* reward_host,
                     uint8_t* done_host) {
     if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
@@ -998,23 +1010,30 @@ int ffsrl_step_host(ffsrl_sim* sim, const float* actions_host, float* obs_host, 
     float* d_obs = d_act + 3 * n;
     float* d_rew = d_obs + od * n;
     uint8_t* d_done = reinterpret_cast<uint8_t*>(d_rew + n);
+    // Page-locked caller buffers are copied directly; others go through the
+    // sim's page-locked staging buffers.
+    const bool pa = page_locked(actions_host), po = page_locked(obs_host), pr = page_locked(reward_host),
+               pd = page_locked(done_host);
     if (actions_host) {
-        std::memcpy(h_act, actions_host, 3 * n * sizeof(float));
-        FFSRL_CUDA(cudaMemcpyAsync(d_act, h_act, 3 * n * sizeof(float), cudaMemcpyHostToDevice, sim->stream));
+        if (!pa) std::memcpy(h_act, actions_host, 3 * n * sizeof(float));
+        FFSRL_CUDA(cudaMemcpyAsync(d_act, pa ? actions_host : h_act, 3 * n * sizeof(float), cudaMemcpyHostToDevice,
+                                   sim->stream));
     }
     int rc = ffsrl_step(sim, actions_host ? d_act : nullptr, obs_host ? d_obs : nullptr,
                         reward_host ? d_rew : nullptr, done_host ? d_done : nullptr);
     if (rc) return rc;
     if (obs_host)
-        FFSRL_CUDA(cudaMemcpyAsync(h_obs, d_obs, od * n * sizeof(float), cudaMemcpyDeviceToHost, sim->stream));
+        FFSRL_CUDA(cudaMemcpyAsync(po ? obs_host : h_obs, d_obs, od * n * sizeof(float), cudaMemcpyDeviceToHost,
+                                   sim->stream));
     if (reward_host)
-        FFSRL_CUDA(cudaMemcpyAsync(h_rew, d_rew, n * sizeof(float), cudaMemcpyDeviceToHost, sim->stream));
+        FFSRL_CUDA(cudaMemcpyAsync(pr ? reward_host : h_rew, d_rew, n * sizeof(float), cudaMemcpyDeviceToHost,
+                                   sim->stream));
     if (done_host)
-        FFSRL_CUDA(cudaMemcpyAsync(h_done, d_done, n, cudaMemcpyDeviceToHost, sim->stream));
+        FFSRL_CUDA(cudaMemcpyAsync(pd ? done_host : h_done, d_done, n, cudaMemcpyDeviceToHost, sim->stream));
     FFSRL_CUDA(cudaStreamSynchronize(sim->stream));
-    if (obs_host) std::memcpy(obs_host, h_obs, od * n * sizeof(float));
-    if (reward_host) std::memcpy(reward_host, h_rew, n * sizeof(float));
-    if (done_host) std::memcpy(done_host, h_done, n);
+    if (obs_host && !po) std::memcpy(obs_host, h_obs, od * n * sizeof(float));
+    if (reward_host && !pr) std::memcpy(reward_host, h_rew, n * sizeof(float));
+    if (done_host && !pd) std::memcpy(done_host, h_done, n);
     return FFSRL_OK;
 }
 

@@ -281,6 +281,17 @@ class Sim:
                                        _np_ptr(reward), _np_ptr(done)))
         return obs, reward, done
 
+    def pinned_host_buffers(self):
+        """Page-locked numpy buffers (actions [n_env][3], obs, reward, done)
+        for step_host, which then copies to and from them directly."""
+        torch = self._torch
+        t = (torch.empty((self.n_env, 3), dtype=torch.float32, pin_memory=True),
+             torch.empty((self.n_env, self.obs_dim), dtype=torch.float32, pin_memory=True),
+             torch.empty(self.n_env, dtype=torch.float32, pin_memory=True),
+             torch.empty(self.n_env, dtype=torch.uint8, pin_memory=True))
+        self._keep_pinned = getattr(self, "_keep_pinned", []) + [t]
+        return tuple(x.numpy() for x in t)
+
     def step_noalloc(self, actions, x, v, tool) -> None:
         """ffsrl_step_noalloc: one step of the caller's packed state tensors
         (x, v [total_verts][3] float32, tool [n_env][3] float64, updated in

@@ -374,6 +374,15 @@ def test_step_host_matches_device_step():
     oa, _, _ = a.step()
     ob, _, _ = b.step_host(None)
     assert np.array_equal(oa.cpu().numpy(), ob)
+    # page-locked caller buffers are copied directly
+    ha, ho, hr, hd = b.pinned_host_buffers()
+    for k in range(3):
+        ha[:] = acts[k]
+        oa, ra, da = a.step(torch.from_numpy(acts[k]).cuda())
+        b.step_host(ha, ho, hr, hd)
+        assert np.array_equal(oa.cpu().numpy(), ho)
+        assert np.array_equal(ra.cpu().numpy(), hr)
+        assert np.array_equal(da.cpu().numpy(), hd)
 
 
 def test_non_finite_state_is_reported_by_sync():
