@@ -700,6 +700,29 @@ def run_ours(args):
     t_ms = sharding.max_over_ranks(t_ms, dist, "cuda")
     value = sharding.throughput(n_env, world, args.steps, t_ms / 1e3)
 
+    # Spread over seeds: the same measurement from other resets (shorter runs).
+    seed_stats = None
+    if args.seeds > 1 and mixed is None:
+        vals = []
+        n_s = max(10, min(args.steps, 200))
+        for j in range(1, args.seeds + 1):
+            sim.reset(seed + 1000 * j)
+            for _ in range(3):
+                sim.step_into(None, obs, rew, done)
+            torch.cuda.synchronize()
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                for _ in range(n_s):
+                    sim.step_into(None, obs, rew, done)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            ms = sharding.max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
+            vals.append(sharding.throughput(n_env, world, n_s, ms / 1e3))
+        seed_stats = {"seeds": args.seeds, "steps_each": n_s, "mean": float(np.mean(vals)),
+                      "std": float(np.std(vals)), "values": vals, "unit": UNIT}
+
     # End to end through the public host-buffer call: actions copied in,
     # observation, reward and done copied out, every step.
     e2e = None
@@ -807,6 +830,7 @@ def run_ours(args):
                                         "tma_ring_envs": sim.ring_envs,
                                         "resident_envs": sim.resident_envs, "launch_groups": sim.n_groups}},
                 "roofline": roofline, "cpu_baseline": cpu, "accuracy": acc, "e2e": e2e, "latency": latency,
+                "seed_spread": seed_stats,
                 "gpu_launches": args.steps * (sim.n_groups + (1 if mixed is not None else 0)), "clocks": clk}
         if mixed is not None:
             line["dtype"] = "f32+bf16"
@@ -836,6 +860,7 @@ def main():
     ap.add_argument("--envs", type=int, default=0, help="override the workload's env count")
     ap.add_argument("--schedule", default="", help="force threads_per_env:envs_per_cta:ring:permute[:ctas_per_sm]")
     ap.add_argument("--acc-steps", type=int, default=50, help="steps of the warm-start accuracy comparison")
+    ap.add_argument("--seeds", type=int, default=5, help="extra resets timed for the spread over seeds")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
