@@ -359,9 +359,9 @@ std::vector<Rec> group_greedy(const std::vector<Rec>& recs, bool flip) {
     return out;
 }
 
-// Local search: move a record of a conflicted group into a random other group
-// (swapping with one of its records, an edge record flipped if that helps)
-// whenever the two groups' cost does not rise.
+// Local search: move a conflicting record of a conflicted group into a random
+// other group (swapping with one of its records, an edge record flipped if
+// that helps) whenever the two groups' cost does not rise.
 template <int ARITY>
 void group_improve(std::vector<Rec>& g, std::mt19937_64& rng, long long iters, bool flip) {
     const int n = int(g.size()), G = (n + 7) / 8;
@@ -378,7 +378,27 @@ void group_improve(std::vector<Rec>& g, std::mt19937_64& rng, long long iters, b
         }
         const int a = bad[rng() % bad.size()], b = int(rng() % G);
         if (a == b) continue;
-        const int i = 8 * a + int(rng() % size_of(a)), j = 8 * b + int(rng() % size_of(b));
+        // a record of group a that shares its bank group with another record
+        // of the group in some position (scanning from random ones)
+        int i = 8 * a + int(rng() % size_of(a));
+        {
+            const int na = size_of(a), k0 = int(rng() % ARITY), l0 = int(rng() % na);
+            bool found = false;
+            for (int dk = 0; dk < ARITY && !found; ++dk) {
+                const int k = (k0 + dk) % ARITY;
+                int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                for (int l = 0; l < na; ++l) ++cnt[g[8 * a + l][k] & 7];
+                for (int dl = 0; dl < na; ++dl) {
+                    const int l = (l0 + dl) % na;
+                    if (cnt[g[8 * a + l][k] & 7] > 1) {
+                        i = 8 * a + l;
+                        found = true;
+                        break;
+                    }
+                }
+            }
+        }
+        const int j = 8 * b + int(rng() % size_of(b));
         const int before = cost[a] + cost[b];
         std::swap(g[i], g[j]);
         const int cb = group_cost<ARITY>(&g[8 * b], size_of(b));
@@ -576,6 +596,9 @@ void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& ou
     std::mt19937_64 rng(seed);
     // phases of each family (the colours unless permuted; see constraint_phases)
     const int unit = (permute && parts == 1 && V <= kPhaseMaxVerts) ? kPhaseUnit : 0;
+    // local-search moves per record: more for the small meshes of the
+    // four-CTA kernel, where the search time stays near a second
+    const long long search = V <= kPhaseMaxVerts ? 300 : 100;
     // (phases of at most 4 KB of records: 512 edges, 256 tets or connections)
     const auto eph = constraint_phases<2>(m.E, m.edge.data(), m.eorder, m.ecol_off, m.n_ecol, V, unit, 2 * unit);
     const auto tph = constraint_phases<4>(m.T, m.tet.data(), m.torder, m.tcol_off, m.n_tcol, V, unit, unit);
@@ -612,7 +635,7 @@ void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& ou
             const int n = int(r.size());
             if (permute) {
                 r = group_greedy<2>(r, true);
-                group_improve<2>(r, rng, 100ll * n, true);
+                group_improve<2>(r, rng, search * n, true);
             }
             std::vector<uint32_t> buf(2 * size_t(n));
             for (int j = 0; j < n; ++j) {
@@ -637,7 +660,7 @@ void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& ou
             const int n = int(r.size());
             if (permute) {
                 r = group_greedy<4>(r, false);
-                group_improve<4>(r, rng, 100ll * n, false);
+                group_improve<4>(r, rng, search * n, false);
             }
             std::vector<uint32_t> buf(4 * size_t(n));
             for (int j = 0; j < n; ++j) {
@@ -665,7 +688,7 @@ void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& ou
             const int n = int(r.size());
             if (permute) {
                 r = group_greedy<4>(r, false);
-                group_improve<4>(r, rng, 100ll * n, false);
+                group_improve<4>(r, rng, search * n, false);
             }
             std::vector<uint32_t> buf(4 * size_t(n));
             for (int j = 0; j < n; ++j) {
