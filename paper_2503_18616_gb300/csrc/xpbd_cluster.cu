@@ -147,25 +147,51 @@ __global__ void __launch_bounds__(SUB, 1)
     const float at_d = ed.alpha_d, at_v = S.alpha_v;
     float* lam = S.lambda ? S.lambda + ed.loff : nullptr;
 
+    // Constraint records come from L2. Each thread keeps its next record in
+    // flight one loop trip ahead. (Requesting a colour's first record before
+    // the previous colour's cluster barrier is slower: the barrier's release
+    // semantics wait for the load.)
+    auto first_rec = [&](int c) {
+        const int4 sg = M.segs[c * CL + rank];
+        uint4 r = make_uint4(0u, 0u, 0u, 0u);
+        if (tid < sg.z) {
+            if (c < M.n_ecol) {
+                const uint2 e = __ldg(reinterpret_cast<const uint2*>(M.recs + sg.x) + tid);
+                r = make_uint4(e.x, e.y, 0u, 0u);
+            } else {
+                r = __ldg(reinterpret_cast<const uint4*>(M.recs + sg.x) + tid);
+            }
+        }
+        return r;
+    };
     for (int sub = 0; sub < S.substeps; ++sub) {
         for (int it = 0; it < S.iterations; ++it) {
             for (int c = 0; c < n_col; ++c) {
                 const int4 sg = M.segs[c * CL + rank];
                 const unsigned char* base = M.recs + sg.x;
                 const bool carry = lam != nullptr;
+                uint4 cur = first_rec(c);
                 if (c < M.n_ecol) {
                     const uint2* rec = reinterpret_cast<const uint2*>(base);
                     for (int q = tid; q < sg.z; q += SUB) {
+                        uint4 nxt = cur;
+                        if (q + SUB < sg.z) {
+                            const uint2 e = __ldg(rec + q + SUB);
+                            nxt = make_uint4(e.x, e.y, 0u, 0u);
+                        }
                         float l = (carry && it > 0) ? lam[sg.w + q] : 0.f;
-                        project_edge(X, __ldg(rec + q), at_d, M.min_len2, l);
+                        project_edge(X, make_uint2(cur.x, cur.y), at_d, M.min_len2, l);
                         if (carry) lam[sg.w + q] = l;
+                        cur = nxt;
                     }
                 } else {
                     const uint4* rec = reinterpret_cast<const uint4*>(base);
                     for (int q = tid; q < sg.z; q += SUB) {
+                        const uint4 nxt = (q + SUB < sg.z) ? __ldg(rec + q + SUB) : cur;
                         float l = (carry && it > 0) ? lam[sg.w + q] : 0.f;
-                        project_tet(X, __ldg(rec + q), at_v, l);
+                        project_tet(X, cur, at_v, l);
                         if (carry) lam[sg.w + q] = l;
+                        cur = nxt;
                     }
                 }
                 cl_sync();
