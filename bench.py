@@ -470,7 +470,7 @@ def run_warmstart(args):
 
 
 def run_solvers(args):
-    """Colour Gauss-Seidel (the workload's solver) against the paper's Jacobi
+    """Colour Gauss-Seidel (the default solver) against the paper's Jacobi
     iterations with averaging (Sec. III-A) on the 4096-env block: env-steps/s
     from CUDA events over K steps, and the largest vertex deviation / extent
     after N steps from reset against the FP64 oracle running the

@@ -79,12 +79,12 @@ typedef struct {
     int32_t block_threads;    /* CUDA threads per environment (128, 256, 384, 512
                                  or 1024); 0 = autotuned (256 when forced) */
     int32_t schedule_flags;   /* 0 = autotuned; else FFSRL_SCHED_* bits forcing a schedule */
-    int32_t solver;           /* FFSRL_SOLVER_*: colour Gauss-Seidel (0, the workload's) or the
+    int32_t solver;           /* FFSRL_SOLVER_*: colour Gauss-Seidel (0, the default) or the
                                  paper's Jacobi iterations with averaging (1, Sec. III-A) */
     int32_t auto_reset;       /* 1: an env whose step reported done starts its next episode at
                                  its next step (rest state, draws of the episode's seed
                                  splitmix64_nth(seed, 2^40 + k) for episode k >= 1) */
-    int32_t tool_model;       /* FFSRL_TOOL_*: the workload's sphere proxy (0) or the paper's
+    int32_t tool_model;       /* FFSRL_TOOL_*: a sphere proxy (0, the default) or the paper's
                                  grasper (1, Sec. III-A): a shaft capsule from the remote centre
                                  of motion (rcm_height above the centre of the top face) to the
                                  tool point and two clamp capsules leaving the tool point at
@@ -216,7 +216,7 @@ int ffsrl_get_mesh_table(const ffsrl_sim* sim, int32_t mesh, int32_t which, int3
 int ffsrl_get_env_ints(ffsrl_sim* sim, int32_t env, int32_t* step_count, int32_t* target,
                        int32_t* obs_ids_host, int32_t* n_contacts, int32_t* contacts_host);
 
-/* --- learned warm-start network (not in the paper; the workload's per-vertex
+/* --- learned warm-start network (not in the paper; a per-vertex
  *     15-64-64-3 ReLU perceptron, BF16 weights and activations, FP32
  *     accumulation, run on the tensor cores) --------------------------------- */
 

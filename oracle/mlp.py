@@ -1,7 +1,7 @@
 """FP64 oracle of the per-vertex warm-start network (test infrastructure only).
 
-The learned warm-start is not in the FF-SRL paper (arXiv 2503.18616); it is the
-network the workload adds on top of the paper's XPBD substep: a per-vertex
+The learned warm-start is not in the FF-SRL paper (arXiv 2503.18616); it is a
+network added on top of the paper's XPBD substep: a per-vertex
 multilayer perceptron 15 -> 64 -> ReLU -> 64 -> ReLU -> 3 that predicts the
 position correction of the constraint solve. This module is the plain numpy
 definition used to check the GPU kernels: forward, the backward pass of the

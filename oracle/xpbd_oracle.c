@@ -23,8 +23,9 @@
  *   - reward / termination ....... Sec. IV (reward R = w_l l + w_d d + w_s s), Sec. III-B
  *   - substepping ................ Sec. III-A (n substeps x 1 iteration)
  *
- * Readings where the paper is silent, garbled or departs from the workload
- * (each is also listed in the design notes of the repository):
+ * Readings where the paper is silent, garbled or differs from the default
+ * configuration built here (each is also listed in the design notes of the
+ * repository):
  *   R1  Eq. 2 assigns the cross products to the wrong vertices and flips the
  *       sign of the d term. Used here: g_b = x_ca x x_da / 6,
  *       g_c = x_da x x_ba / 6, g_d = x_ba x x_ca / 6, g_a = -(g_b+g_c+g_d),
@@ -1275,8 +1276,8 @@ void orc_env_get_tool_box(const orc_env* s, double* lo, double* hi) {
 int orc_real_size(void) { return (int)sizeof(REAL); }
 
 /* ------------------------------------------------------------------------ */
-/* Learned warm-start (not in the paper; the surrogate-assisted substep of   */
-/* the workload). The network is a per-vertex perceptron 15 -> 64 -> ReLU -> */
+/* Learned warm-start (not in the paper; a surrogate-assisted substep added  */
+/* to the method). The network is a per-vertex perceptron 15 -> 64 -> ReLU -> */
 /* 64 -> ReLU -> 3 whose output, de-normalised, is added to the predicted    */
 /* positions before one constraint iteration; a constraint residual above    */
 /* the threshold restores the prediction and runs the full solve instead.    */

@@ -1,7 +1,7 @@
 // Per-vertex warm-start network on the 5th-generation tensor cores (sm_103a).
 //
-// The network (not in the FF-SRL paper; the learned warm-start of the
-// workload) maps 15 features of a vertex to a 3-vector correction:
+// The network (not in the FF-SRL paper; a learned warm-start added to the
+// method) maps 15 features of a vertex to a 3-vector correction:
 // 15 -> 64 -> ReLU -> 64 -> ReLU -> 3, BF16 weights and activations, FP32
 // accumulation. One CTA of 128 threads processes 128-row tiles: each row is
 // one TMEM lane and one thread of the epilogue.

@@ -1,4 +1,4 @@
-// Surrogate-assisted XPBD substeps (the learned warm-start of the workload;
+// Surrogate-assisted XPBD substeps (a learned warm-start added to the method;
 // not in the FF-SRL paper, which runs the plain substep of Algorithm 1).
 //
 // One substep of every env is three launches: the features kernel (per

@@ -175,7 +175,7 @@ def default_params(spacing: float = CELL, **over) -> dict:
         "max_steps": 0,
         "solver": 0,        # 0 colour Gauss-Seidel, 1 Jacobi with averaging (the paper's GPU scheme)
         "auto_reset": 0,    # 1: a done env starts a new episode at its next step
-        # tool: 0 sphere proxy (the workload's), 1 the paper's three-capsule grasper through a remote
+        # tool: 0 sphere proxy (the default), 1 the paper's three-capsule grasper through a remote
         # centre of motion 8 cells above the top face (shaft radius half a cell, clamps two cells
         # long, a quarter cell thick, opened 10 degrees)
         "tool_model": 0,

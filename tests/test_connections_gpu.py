@@ -4,8 +4,7 @@ beneath it.
 
 Connection tables and objects are integer work and must be bit-exact;
 trajectories (sphere tool, random actions; one and two iterations; the
-grasper lifting the connected tissue) are held to the workload's
-1e-5 x extent; every execution schedule must give the same bits.
+grasper lifting the connected tissue) are held to 1e-5 x extent; every execution schedule must give the same bits.
 """
 import math
 

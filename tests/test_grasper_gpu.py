@@ -61,7 +61,7 @@ def test_grasper_trajectories_match_oracle(shape, n_env, steps):
     h = p["dt"] / p["substeps"]
     ext = om[0].extent
     # contact decisions make the grasper's trajectories sensitive to rounding:
-    # the bar is the workload's 1e-5 x extent or, if larger, four times the
+    # the bar is 1e-5 x extent or, if larger, four times the
     # distance between the oracle's own FP32 and FP64 builds
     om32 = oracle.Mesh(*m, precision="f32")
     for e, oe in oenvs.items():

@@ -63,7 +63,7 @@ def test_network_forward_matches_bf16_oracle(rows):
 
 
 def test_network_forward_full_batch_sampled():
-    """All 4096 x 2601 vertex rows of the warm-start workload in one launch;
+    """All 4096 x 2601 vertex rows of the 4096-env 17x17x9 block in one launch;
     sampled rows are checked (rows are independent)."""
     p, im, isd, om, osd = _network(5)
     sim = make_sim([grid((3, 3, 2))], inputs.default_params(n_obs=4), 1)

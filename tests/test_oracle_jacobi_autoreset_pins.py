@@ -1,4 +1,4 @@
-"""Pins of the oracle's two options beyond the workload's default step.
+"""Pins of the oracle's two options beyond the default step.
 
 Jacobi iterations (the paper's own parallel scheme, Sec. III-A): every
 constraint steps from the iteration's start positions and each vertex moves

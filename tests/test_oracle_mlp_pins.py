@@ -1,7 +1,7 @@
 """Pins of the FP64 warm-start network oracle (oracle/mlp.py).
 
 The network is not in the FF-SRL paper; it is the per-vertex 15-64-64-3 ReLU
-perceptron of the learned warm-start workload. Its oracle is pinned by central
+perceptron of the learned warm-start. Its oracle is pinned by central
 finite differences of the loss, by closed forms of degenerate networks, by
 Adam's first-step closed form (Kingma & Ba, ICLR 2015, Algorithm 1), and by
 exact bfloat16 rounding cases.
