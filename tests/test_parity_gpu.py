@@ -479,3 +479,26 @@ def test_uneven_1024_env_batch_sampled():
     for oe in oenvs.values():
         oe.run(steps, want_obs=False)
     compare_states(sim, oenvs, meshes, 1024, env_mesh=env_mesh, label="uneven 1024")
+
+
+def test_largest_supported_mesh_and_the_size_limit():
+    """Shared-memory slots are 16-bit, so a mesh may have up to 65535
+    vertices: a 40x40x40 block (64000 vertices, global-memory path) matches
+    the oracle; 65536 vertices are rejected with FFSRL_E_INVAL."""
+    from paper_2503_18616_gb300 import ffsrl
+    m = grid((40, 40, 40))
+    p = P(radius=6e-3)
+    sim = make_sim([m], p, 1, seed=4)
+    assert sim.resident_envs == 0
+    oenvs, om = oracle_envs([m], p, 1, seed=4)
+    acts = inputs.random_actions(3, 1, 5)
+    acts[:, :, 2] = -1.0
+    for k in range(3):
+        sim.step(torch.from_numpy(acts[k].astype(np.float32)).cuda())
+        oenvs[0].step(acts[k, 0])
+    x, _, _ = gpu_positions(sim)
+    assert np.max(np.abs(x - oenvs[0].state()[0])) <= POS_TOL * om[0].extent
+    sim.close()
+    big = grid((64, 32, 32))   # 65536 vertices
+    with pytest.raises(ffsrl.FfsrlError):
+        make_sim([big], p, 1)
