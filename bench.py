@@ -281,7 +281,11 @@ def run_reference(args):
     for oe in probes:
         oe.run(1, want_obs=False)
     per_env_step = (time.perf_counter() - t0) / len(probes)
-    procs = max(1, args.ref_procs or (os.cpu_count() or 1))
+    try:
+        cores = len(os.sched_getaffinity(0))   # the cores this process may run on
+    except (AttributeError, OSError):
+        cores = os.cpu_count() or 1
+    procs = max(1, args.ref_procs or cores)
     budget = 100.0   # seconds of oracle work per process
     per_proc = max(1, int(budget / ((args.steps + args.warmup) * per_env_step)))
     n_sample = max(1, min(batch.n_env, per_proc * procs))
@@ -851,7 +855,8 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--ref-procs", type=int, default=0, help="host processes of the reference arm (0: one per core)")
+    ap.add_argument("--ref-procs", type=int, default=0,
+                    help="host processes of the reference arm (0: one per core this process may use)")
     ap.add_argument("--workload", default="block17x17x9_4096env_1000steps")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
