@@ -5,7 +5,8 @@
 // the sweep over the colours). Reads a mesh from stdin: V T, then rest [V][3],
 // inverse masses [V], tets [T][4]; argv[1] = connection radius.
 // Prints one line per slot order: phases per family, thread rounds of 256,
-// and ok 0/1.
+// and ok 0/1. With argv[2] = "tables" it prints the constraint tables instead,
+// one line per table: its name, then its integers.
 #include <algorithm>
 #include <array>
 #include <cstdio>
@@ -35,6 +36,32 @@ int main(int argc, char** argv) {
     if (build_host_mesh(V, T, rest.data(), w.data(), tets.data(), m, err, conn_radius)) {
         std::printf("mesh rejected: %s\n", err.c_str());
         return 1;
+    }
+    if (argc > 2 && std::string(argv[2]) == "tables") {
+        auto put = [](const char* name, const std::vector<int32_t>& v) {
+            std::printf("%s", name);
+            for (int32_t x : v) std::printf(" %d", x);
+            std::printf("\n");
+        };
+        put("tets", m.tet);
+        put("flipped", m.flipped);
+        put("edges", m.edge);
+        put("ecolor", m.ecolor);
+        put("tcolor", m.tcolor);
+        put("eorder", m.eorder);
+        put("torder", m.torder);
+        put("ecol_off", m.ecol_off);
+        put("tcol_off", m.tcol_off);
+        put("top", m.top);
+        put("faces", m.face);
+        put("face_opposite", m.fopp);
+        put("forder", m.forder);
+        put("fcol_off", m.fcol_off);
+        put("conns", m.conn);
+        put("corder", m.corder);
+        put("ccol_off", m.ccol_off);
+        put("objects", m.obj);
+        return 0;
     }
     // constraint lookup by sorted vertex tuple -> (family, colour)
     std::map<std::array<int, 4>, int> ecol, tcol, ccol;
