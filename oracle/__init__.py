@@ -65,6 +65,7 @@ def _lib(precision: str = "f64") -> ctypes.CDLL:
             L.orc_target_index.restype = I
             L.orc_target_index.argtypes = [U64, U64, I]
             L.orc_env_set_clamp.argtypes = [P, D]
+            L.orc_env_grasper.argtypes = [P, P, P, P, P]
             L.orc_episode_seed.restype = U64
             L.orc_episode_seed.argtypes = [U64, I]
             L.orc_mesh_create.restype = P
@@ -415,6 +416,13 @@ class Env:
         contacts = out[4 + n_obs:4 + n_obs + n_c].copy()
         return {"t": t, "target": target, "obs_ids": obs_ids, "contacts": contacts,
                 "episode": int(out[4 + n_obs + n_c]), "grasp": int(out[5 + n_obs + n_c])}
+
+    def grasper(self):
+        """The grasper at the current tool point: capsule segments [3][2][3]
+        (shaft, clamp +, clamp -), radii [3] and the dragging point [3]."""
+        seg, rad, drag = np.zeros((3, 2, 3)), np.zeros(3), np.zeros(3)
+        self._L.orc_env_grasper(self._h, ctypes.byref(self._p), _ptr(seg), _ptr(rad), _ptr(drag))
+        return seg, rad, drag
 
     def set_clamp(self, angle: float) -> None:
         """Grasper clamp opening (radians) from the next step on."""

@@ -989,6 +989,20 @@ static void grasper_capsules(const orc_env* s, const orc_params* p, REAL seg[3][
     radius[1] = radius[2] = (REAL)p->clamp_radius;
 }
 
+/* Read-only view for the test suite: the grasper's three capsules at the
+ * env's current tool point and clamp opening (seg [3][2][3]: shaft, clamp +,
+ * clamp -; radius [3]) and the dragging point (drag [3]). */
+void orc_env_grasper(const orc_env* s, const orc_params* p, double* seg, double* radius, double* drag) {
+    REAL sg[3][2][3], r[3], g[3];
+    grasper_capsules(s, p, sg, r);
+    dragging_point(s, p, g);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 2; ++j)
+            for (int k = 0; k < 3; ++k) seg[6 * i + 3 * j + k] = (double)sg[i][j][k];
+    for (int i = 0; i < 3; ++i) radius[i] = (double)r[i];
+    for (int k = 0; k < 3; ++k) drag[k] = (double)g[k];
+}
+
 /* Grasper-tissue collision (R13): surface faces colour by colour, each face
  * against the shaft, then the two clamps; a face whose closest point lies
  * inside a capsule is pushed out along the penetration direction by a PBD

@@ -9,7 +9,10 @@ and releases it when the clamps open; a pushed face moves out of the capsule
 and repeated pushes converge to its surface; a tool pressed into the tissue
 displaces it away from the tool; a tool far from the tissue leaves it exactly
 as the sphere-tool step does; the surface faces of a grid block are counted
-in closed form and coloured validly.
+in closed form and coloured validly; the capsules and the dragging point
+follow the closed forms of the remote-centre geometry (shaft through the
+remote centre, clamps at +-alpha in the plane of the axis and world x, or
+world y when the shaft lies along x).
 """
 import math
 
@@ -247,3 +250,70 @@ def test_no_grasp_with_open_clamps_or_nothing_in_reach():
     m, rest, w, p, e = _vertical_tool_env(clamp_angle=math.radians(1.0), grasp_radius=1e-4)
     e.step(np.zeros(3))                           # the clamp end starts 1.25 mm above the surface
     assert e.ints()["grasp"] == -1
+
+
+def _grasper_at(c, **over):
+    rest, w, tets = inputs.grid_block(9, 9, 5)
+    m = oracle.Mesh(rest, w, tets)
+    p = params(tool_model=1, **over)
+    e = oracle.Env(m, p)
+    e.reset(0)
+    e.set_state(c=np.asarray(c, dtype=np.float64))
+    return rest, p, e
+
+
+@pytest.mark.parametrize("c,angle", [((0.0, 0.0, 0.03), 10.0), ((0.012, -0.007, 0.026), 25.0),
+                                     ((-0.02, 0.015, 0.035), 3.0), ((0.004, 0.0, 0.02), 0.0)])
+def test_grasper_geometry_closed_forms(c, angle):
+    """Shaft from the remote centre (above the top-face centre by rcm_height)
+    to the tool point; clamps of clamp_length leave the tool point at +-angle
+    from the shaft axis, mirror images in the plane of the axis and world x;
+    the dragging point lies clamp_length beyond the tool point on the axis."""
+    rest, p, e = _grasper_at(c, clamp_angle=math.radians(angle))
+    seg, rad, drag = e.grasper()
+    c = np.asarray(c)
+    rcm = np.array([(rest[:, 0].min() + rest[:, 0].max()) / 2, (rest[:, 1].min() + rest[:, 1].max()) / 2,
+                    rest[:, 2].max() + p["rcm_height"]])
+    assert np.allclose(seg[0, 0], rcm, atol=1e-15) and np.allclose(seg[0, 1], c, atol=1e-15)
+    d = (c - rcm) / np.linalg.norm(c - rcm)
+    x = np.array([1.0, 0.0, 0.0])
+    u = x - np.dot(x, d) * d
+    u /= np.linalg.norm(u)
+    a = math.radians(angle)
+    for k, sgn in ((1, 1.0), (2, -1.0)):
+        assert np.allclose(seg[k, 0], c, atol=1e-15)
+        arm = seg[k, 1] - c
+        assert np.linalg.norm(arm) == pytest.approx(p["clamp_length"], rel=1e-12)
+        assert np.dot(arm, d) == pytest.approx(p["clamp_length"] * math.cos(a), rel=1e-12, abs=1e-15)
+        assert np.allclose(arm, p["clamp_length"] * (math.cos(a) * d + sgn * math.sin(a) * u), atol=1e-14)
+    # mirror images: the sum lies on the axis, the difference along u
+    s_ = (seg[1, 1] - c) + (seg[2, 1] - c)
+    assert np.allclose(np.cross(s_, d), 0.0, atol=1e-15)
+    assert np.allclose(np.cross(seg[1, 1] - seg[2, 1], u), 0.0, atol=1e-15)
+    assert np.allclose(rad, [p["shaft_radius"], p["clamp_radius"], p["clamp_radius"]])
+    assert np.allclose(drag, c + p["clamp_length"] * d, atol=1e-15)
+
+
+def test_vertical_shaft_opens_the_clamps_along_x():
+    rest, p, e = _grasper_at((0.0, 0.0, 0.03), clamp_angle=math.radians(20.0))
+    seg, _, drag = e.grasper()
+    L, a = p["clamp_length"], math.radians(20.0)
+    c = np.array([0.0, 0.0, 0.03])
+    assert np.allclose(seg[1, 1], c + L * np.array([math.sin(a), 0.0, -math.cos(a)]), atol=1e-15)
+    assert np.allclose(seg[2, 1], c + L * np.array([-math.sin(a), 0.0, -math.cos(a)]), atol=1e-15)
+    assert np.allclose(drag, c - np.array([0.0, 0.0, L]), atol=1e-15)
+
+
+def test_shaft_along_x_falls_back_to_the_y_axis():
+    """With the shaft parallel to world x the clamp plane cannot contain x;
+    the clamps then open in the plane of the axis and world y."""
+    rest, w, tets = inputs.grid_block(9, 9, 5)
+    top = rest[:, 2].max()
+    p_h = 8 * inputs.CELL
+    c = (0.05, 0.0, top + p_h)            # level with the remote centre, along +x
+    rest, p, e = _grasper_at(c, clamp_angle=math.radians(15.0))
+    seg, _, _ = e.grasper()
+    arm = seg[1, 1] - np.asarray(c)
+    a = math.radians(15.0)
+    L = p["clamp_length"]
+    assert np.allclose(arm, L * np.array([math.cos(a), math.sin(a), 0.0]), atol=1e-15)
