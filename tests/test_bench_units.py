@@ -1,0 +1,36 @@
+"""The benchmark's algorithmic units (no GPU): per env-step of the 17x17x9
+block (V 2601, E 13864, T 10240; 10 substeps x 1 iteration) the shared-memory
+bytes, FP32 operations and HBM bytes that the roofline divides by are the
+stated per-constraint and per-vertex figures, and they scale with substeps,
+iterations and mesh size as the definitions say."""
+import bench
+from paper_2503_18616_gb300 import inputs
+
+V, E, T = 2601, 13864, 10240
+
+
+def test_shared_memory_bytes_per_env_step():
+    p = inputs.default_params()
+    got = bench.smem_bytes_per_env_step(V, E, T, p)
+    # float4 load + store of both edge ends, all four tet corners, and one
+    # load + store per vertex in the fused collision / prediction pass
+    assert got == 10 * (E * 2 * 2 * 16 + T * 2 * 4 * 16 + V * 2 * 16)
+    assert abs(got / 1e6 - 22.8) < 0.05
+    p2 = inputs.default_params(iterations=3, substeps=5)
+    assert bench.smem_bytes_per_env_step(V, E, T, p2) == 5 * (3 * (E * 64 + T * 128) + V * 32)
+
+
+def test_fp32_operations_and_hbm_bytes_per_env_step():
+    p = inputs.default_params()
+    assert abs(bench.flops_per_env_step(V, E, T, p) / 1e6 - 16.9) < 0.1
+    assert bench.BYTES_VERT == 48     # x and v, read and written once per step, float32 x 3
+    assert bench.BYTES_VERT * V == 124848
+
+
+def test_units_scale_linearly_with_the_mesh():
+    p = inputs.default_params()
+    a = bench.smem_bytes_per_env_step(V, E, T, p)
+    b = bench.smem_bytes_per_env_step(2 * V, 2 * E, 2 * T, p)
+    assert b == 2 * a
+    fa = bench.flops_per_env_step(V, E, T, p)
+    assert bench.flops_per_env_step(2 * V, 2 * E, 2 * T, p) == 2 * fa
