@@ -95,3 +95,15 @@ def test_host_tables_equal_the_oracle(checker, case):
         assert np.array_equal(lib[name], np.asarray(ref).reshape(-1)), name
     if radius > 0:
         assert om.C > 0
+
+
+@pytest.mark.parametrize("shape", [(10, 10, 5), (18, 18, 9), (21, 21, 11)])
+def test_phases_on_uneven_batch_sizes(checker, shape):
+    """Sizes of the uneven batch on both sides of the refinement limit (2944
+    vertices): refined phases below it, the colours above it."""
+    rows = _run(checker, inputs.grid_block(*shape))
+    assert rows[0]["ok"] == 1 and rows[1]["ok"] == 1
+    V = shape[0] * shape[1] * shape[2]
+    if V > 2944:
+        assert rows[1]["phases"] == rows[1]["colours"]
+    assert rows[1]["rounds"] <= rows[0]["rounds"]
