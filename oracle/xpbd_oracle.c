@@ -54,6 +54,10 @@
  *       positions and each vertex moves by the sum of its corrections divided
  *       by the number of constraints (distance and volume) that contain it;
  *       multipliers as in R2.
+ *   R11 Optional auto-reset: an env whose step reported done starts episode
+ *       k+1 at its next step, from the rest state with the draws of seed
+ *       splitmix64_nth(seed, 2^40 + k+1) (seed = the one given to reset; the
+ *       actions of the episode use that seed too).
  *   R12 Optional grasper tool (Sec. III-A "Surgical tool model"): the tool
  *       point c (moved by the actions as in R7) is the end of the shaft; the
  *       shaft runs from the remote centre of motion (above the centre of the
@@ -93,10 +97,6 @@
  *       Connections are coloured first-fit in vertex order and projected in
  *       every iteration after the volume colours; the selection is computed
  *       in double from the input rest positions in either build.
- *   R11 Optional auto-reset: an env whose step reported done starts episode
- *       k+1 at its next step, from the rest state with the draws of seed
- *       splitmix64_nth(seed, 2^40 + k+1) (seed = the one given to reset; the
- *       actions of the episode use that seed too).
  */
 #include <math.h>
 #include <stdint.h>
