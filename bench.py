@@ -44,6 +44,12 @@ BYTES_VERT = 48
 # per vertex and substep one float4 load and store in the fused
 # collision / prediction pass.
 SMEM_EDGE, SMEM_TET, SMEM_VERT = 64, 128, 32
+# Tissue connections: the four float4 of vertex and face loaded and stored per
+# projection. Grasper: the three float4 of every surface face loaded once per
+# substep (stores only where a capsule pushes it). Arithmetic: connection 45,
+# face against the three capsules 3 x 150 (segment-triangle closest points).
+SMEM_CONN, SMEM_FACE = 128, 48
+FLOP_CONN, FLOP_FACE = 45, 450
 SMEM_BYTES_PER_CLK_SM = 128   # 32 banks x 4 B per clock
 
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
@@ -66,10 +72,14 @@ class Batch:
         from paper_2503_18616_gb300 import inputs
         w = inputs.WORKLOADS[name]
         self.name = name
-        self.params = inputs.default_params()
+        self.params = inputs.default_params(**w.get("params", {}))
         self.n_env = n_env_override or w["n_env"]
         self.steps = w["steps"]
-        if "shape" in w:
+        if "stacked" in w:   # base block and connected tissue block in one mesh
+            self.shapes = [w["stacked"]]
+            self.env_mesh = None
+            self.env_alpha = None
+        elif "shape" in w:
             self.shapes = [w["shape"]]
             self.env_mesh = None
             self.env_alpha = None
@@ -80,7 +90,15 @@ class Batch:
             self.shapes = [self.shapes[m] for m in used]
             self.env_mesh = np.array([used.index(int(m)) for m in env_mesh], dtype=np.int32)
             self.env_alpha = inputs.compliance_draws(w["n_env"], *w["alpha_range"], seed=12345)[:self.n_env]
-        self.meshes = [inputs.grid_block(*sh) for sh in self.shapes]
+        if "stacked" in w:
+            self.meshes = [inputs.stacked_blocks(*w["stacked"], gap=w["gap"])]
+        else:
+            self.meshes = [inputs.grid_block(*sh) for sh in self.shapes]
+
+    def oracle_mesh(self, mi: int, precision: str = "f64"):
+        import oracle
+        return oracle.Mesh(*self.meshes[mi], precision=precision,
+                           conn_radius=float(self.params.get("conn_radius", 0.0)))
 
     def mesh_index(self, e: int) -> int:
         return 0 if self.env_mesh is None else int(self.env_mesh[e])
@@ -101,14 +119,17 @@ class Batch:
         return f"{self.n_env} envs of {len(self.shapes)} block sizes, {min(vs)}-{max(vs)} vertices"
 
 
-def flops_per_env_step(V, E, T, params):
+def flops_per_env_step(V, E, T, params, C=0, F=0):
     s, it = params["substeps"], params["iterations"]
-    return s * (it * (E * FLOP_EDGE + T * FLOP_TET) + V * FLOP_VERT)
+    faces = F if params.get("tool_model", 0) == 1 else 0
+    return s * (it * (E * FLOP_EDGE + T * FLOP_TET + C * FLOP_CONN) + V * FLOP_VERT + faces * FLOP_FACE)
 
 
-def smem_bytes_per_env_step(V, E, T, params):
+def smem_bytes_per_env_step(V, E, T, params, C=0, F=0):
+    """C tissue connections; F surface faces (counted with the grasper tool)."""
     s, it = params["substeps"], params["iterations"]
-    return s * (it * (E * SMEM_EDGE + T * SMEM_TET) + V * SMEM_VERT)
+    faces = F if params.get("tool_model", 0) == 1 else 0
+    return s * (it * (E * SMEM_EDGE + T * SMEM_TET + C * SMEM_CONN) + V * SMEM_VERT + faces * SMEM_FACE)
 
 
 # Shared-memory bytes of one warm-start substep beyond the plain iteration:
@@ -209,7 +230,7 @@ def oracle_rate(batch, seconds: float, seed: int, envs, max_steps=None):
     for e in envs:
         mi = batch.mesh_index(e)
         if mi not in meshes:
-            meshes[mi] = oracle.Mesh(*batch.meshes[mi])
+            meshes[mi] = batch.oracle_mesh(mi)
         oe = oracle.Env(meshes[mi], batch.env_params(e))
         oe.reset(seed, e)
         oes.append(oe)
@@ -239,7 +260,7 @@ def _ref_worker(workload, n_envs_flag, env_ids, seed, steps, warmup, barrier, ou
     for e in env_ids:
         mi = batch.mesh_index(e)
         if mi not in meshes:
-            meshes[mi] = oracle.Mesh(*batch.meshes[mi])
+            meshes[mi] = batch.oracle_mesh(mi)
         oe = oracle.Env(meshes[mi], batch.env_params(e))
         oe.reset(seed, e)
         envs.append(oe)
@@ -273,7 +294,7 @@ def run_reference(args):
     for e in probe_envs:
         mi = batch.mesh_index(e)
         if mi not in meshes:
-            meshes[mi] = oracle.Mesh(*batch.meshes[mi])
+            meshes[mi] = batch.oracle_mesh(mi)
         oe = oracle.Env(meshes[mi], batch.env_params(e))
         oe.reset(args.seed, e)
         probes.append(oe)
@@ -737,17 +758,19 @@ def run_ours(args):
     if rank == 0:
         peaks, peak_src = load_peaks()
         counts = []   # (V, E, T) per env from the library's own tables
-        mesh_counts = []
+        mesh_counts, mesh_cf = [], []   # (V, E, T) and (connections, surface faces) per mesh
         for mi in range(len(batch.meshes)):
             mesh_counts.append((len(batch.meshes[mi][0]), len(sim.mesh_table("edges", mi)) // 2,
                                 len(sim.mesh_table("tets", mi)) // 4))
+            mesh_cf.append((len(sim.mesh_table("conns", mi)) // 4, len(sim.mesh_table("faces", mi)) // 3))
         counts = [mesh_counts[batch.mesh_index(e)] for e in range(n_env)]
+        cf = [mesh_cf[batch.mesh_index(e)] for e in range(n_env)]
         ms_step = t_ms / args.steps
         clock_mhz = float(peaks.get("sm_max_mhz", FALLBACK_PEAKS["sm_max_mhz"]))
         sec = ms_step / 1e3
-        smem_bytes = sum(smem_bytes_per_env_step(V, E, T, params) for V, E, T in counts)
+        smem_bytes = sum(smem_bytes_per_env_step(V, E, T, params, C, F) for (V, E, T), (C, F) in zip(counts, cf))
         smem_peak = SMEM_BYTES_PER_CLK_SM * N_SM * clock_mhz * 1e6 / 1e9
-        flops = sum(flops_per_env_step(V, E, T, params) for V, E, T in counts)
+        flops = sum(flops_per_env_step(V, E, T, params, C, F) for (V, E, T), (C, F) in zip(counts, cf))
         alu_peak = 2 * FP32_LANES * N_SM * clock_mhz * 1e6 / 1e12
         hbm_bytes = sum(BYTES_VERT * V + 4 * sim.obs_dim + 16 for V, _, _ in counts)
         hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
@@ -808,7 +831,7 @@ def run_ours(args):
                 ox, _, _ = oe.state()
                 errs.append(float(np.max(np.abs(x[off[e]:off[e + 1]] - ox)) / oe.mesh.extent))
                 # the oracle's own float32 build over the same steps: the rounding floor
-                o32 = oracle.Env(oracle.Mesh(*batch.meshes[batch.mesh_index(e)], precision="f32"),
+                o32 = oracle.Env(batch.oracle_mesh(batch.mesh_index(e), precision="f32"),
                                  batch.env_params(e))
                 o32.reset(seed, e)
                 o32.run(n_steps, want_obs=False)

@@ -203,6 +203,12 @@ WORKLOADS = {
     # + 1 iteration, fallback to the 10-iteration solve), even envs the plain step
     "block17x17x9_16384env_2000steps": {"shape": (17, 17, 9), "n_env": 16384, "steps": 2000, "mixed": True,
                                         "train_envs": 512, "train_env_substeps": 200_000, "n_full": 10},
+    # the paper's tissue-retraction scene: a 17x17x5 tissue block connected (6 mm) to a
+    # 17x17x5 base block 1 mm below it, the three-capsule grasper with closed clamps
+    # (1 degree) dragging the tissue along the device-drawn random walk
+    "retraction_stacked17x17x5x5_4096env": {"stacked": (17, 17, 5, 5), "gap": 1e-3, "n_env": 4096, "steps": 1000,
+                                            "params": {"tool_model": 1, "conn_radius": 6e-3,
+                                                       "clamp_angle": math.radians(1.0)}},
     # learned warm-start: trained on 200k full-solve (10 iteration) env-substeps,
     # then network + 1 iteration with residual fallback, compared with plain k
     "warmstart_block17x17x9_4096env": {"shape": (17, 17, 9), "n_env": 4096, "steps": 200, "warmstart": True,
