@@ -197,7 +197,8 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("xpbd_step.cu", "xpbd_device.cuh", "xpbd_project.cuh", "mesh_setup.cpp"):
+    for f in ("xpbd_step.cu", "xpbd_device.cuh", "xpbd_project.cuh", "xpbd_grasper.cuh", "xpbd_launch.h",
+              "mesh_setup.cpp"):
         with open(os.path.join(ROOT, "paper_2503_18616_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
