@@ -34,3 +34,16 @@ def test_units_scale_linearly_with_the_mesh():
     assert b == 2 * a
     fa = bench.flops_per_env_step(V, E, T, p)
     assert bench.flops_per_env_step(2 * V, 2 * E, 2 * T, p) == 2 * fa
+
+
+def test_every_workload_builds_its_batch_and_oracle_meshes():
+    """Every named workload yields meshes, parameters and oracle meshes (with
+    the connection radius the workload sets), without a GPU."""
+    for name in inputs.WORKLOADS:
+        b = bench.Batch(name, n_env_override=8)
+        assert b.n_env == 8 and len(b.meshes) >= 1
+        assert b.describe()
+        om = b.oracle_mesh(b.mesh_index(0))
+        assert om.V == b.verts(0)
+        if b.params.get("conn_radius", 0.0) > 0:
+            assert om.C > 0 and b.params["tool_model"] == 1
