@@ -51,6 +51,14 @@ SMEM_EDGE, SMEM_TET, SMEM_VERT = 64, 128, 32
 SMEM_CONN, SMEM_FACE = 128, 48
 FLOP_CONN, FLOP_FACE = 45, 450
 SMEM_BYTES_PER_CLK_SM = 128   # 32 banks x 4 B per clock
+# Algorithmic on-chip bytes of the resident design (the method's own
+# traffic): per projection, the 12-byte position of every vertex it touches,
+# read and written once: 2 x 2 x 12 per edge, 2 x 4 x 12 per tet, 2 x 4 x 12
+# per connection; per grasper face and substep its three positions read.
+ALG_EDGE, ALG_TET, ALG_CONN, ALG_FACE = 48, 96, 96, 36
+# Tensor work of the warm-start network per vertex row and substep:
+# 2 x (15 x 64 + 64 x 64 + 64 x 3) multiply-adds as FLOPs (unpadded).
+NET_FLOP_ROW = 2 * (15 * 64 + 64 * 64 + 64 * 3)
 
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
 N_SM, FP32_LANES = 152, 128
@@ -68,12 +76,16 @@ def load_peaks():
 class Batch:
     """A workload: meshes, the env -> mesh map, per-env edge compliance and the parameters."""
 
-    def __init__(self, name: str, n_env_override: int = 0):
+    def __init__(self, name: str, n_env_override: int = 0, env_ids=None):
+        """env_ids (optional): the global ids of the envs to hold, a subset of
+        the workload's 0 .. n_env - 1 (one rank's shard)."""
         from paper_2503_18616_gb300 import inputs
         w = inputs.WORKLOADS[name]
         self.name = name
         self.params = inputs.default_params(**w.get("params", {}))
-        self.n_env = n_env_override or w["n_env"]
+        n_all = n_env_override or w["n_env"]
+        self.env_ids = np.arange(n_all) if env_ids is None else np.asarray(env_ids, dtype=np.int64)
+        self.n_env = len(self.env_ids)
         self.steps = w["steps"]
         if "stacked" in w:   # base block and connected tissue block in one mesh
             self.shapes = [w["stacked"]]
@@ -85,11 +97,11 @@ class Batch:
             self.env_alpha = None
         else:
             self.shapes, env_mesh = inputs.uneven_batch(w["n_env"], *w["v_range"], seed=12345)
-            env_mesh = env_mesh[:self.n_env]
+            env_mesh = env_mesh[self.env_ids]
             used = sorted(set(int(m) for m in env_mesh))   # keep only meshes still referenced
             self.shapes = [self.shapes[m] for m in used]
             self.env_mesh = np.array([used.index(int(m)) for m in env_mesh], dtype=np.int32)
-            self.env_alpha = inputs.compliance_draws(w["n_env"], *w["alpha_range"], seed=12345)[:self.n_env]
+            self.env_alpha = inputs.compliance_draws(w["n_env"], *w["alpha_range"], seed=12345)[self.env_ids]
         if "stacked" in w:
             self.meshes = [inputs.stacked_blocks(*w["stacked"], gap=w["gap"])]
         else:
@@ -112,6 +124,17 @@ class Batch:
     def verts(self, e: int) -> int:
         return len(self.meshes[self.mesh_index(e)][0])
 
+    def env_work(self):
+        """V + E + T of every env (the work the bin-packing balances)."""
+        from paper_2503_18616_gb300 import sharding
+        per_mesh = []
+        for rest, _, tets in self.meshes:
+            t = np.asarray(tets)
+            pairs = np.concatenate([t[:, [a, b]] for a, b in ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))])
+            n_edges = len(np.unique(np.sort(pairs, axis=1), axis=0))
+            per_mesh.append(sharding.env_work(len(rest), n_edges, len(t)))
+        return [per_mesh[self.mesh_index(e)] for e in range(self.n_env)]
+
     def describe(self) -> str:
         if len(self.shapes) == 1:
             return f"{self.n_env} envs of the {self.verts(0)}-vertex block"
@@ -123,6 +146,13 @@ def flops_per_env_step(V, E, T, params, C=0, F=0):
     s, it = params["substeps"], params["iterations"]
     faces = F if params.get("tool_model", 0) == 1 else 0
     return s * (it * (E * FLOP_EDGE + T * FLOP_TET + C * FLOP_CONN) + V * FLOP_VERT + faces * FLOP_FACE)
+
+
+def smem_alg_bytes_per_env_step(V, E, T, params, C=0, F=0):
+    """Algorithmic on-chip bytes per env-step (the roofline's numerator)."""
+    s, it = params["substeps"], params["iterations"]
+    faces = F if params.get("tool_model", 0) == 1 else 0
+    return s * (it * (E * ALG_EDGE + T * ALG_TET + C * ALG_CONN) + faces * ALG_FACE)
 
 
 def smem_bytes_per_env_step(V, E, T, params, C=0, F=0):
@@ -233,7 +263,7 @@ def oracle_rate(batch, seconds: float, seed: int, envs, max_steps=None):
         if mi not in meshes:
             meshes[mi] = batch.oracle_mesh(mi)
         oe = oracle.Env(meshes[mi], batch.env_params(e))
-        oe.reset(seed, e)
+        oe.reset(seed, int(batch.env_ids[e]))
         oes.append(oe)
     t0 = time.perf_counter()
     for oe in oes:
@@ -243,7 +273,7 @@ def oracle_rate(batch, seconds: float, seed: int, envs, max_steps=None):
     if max_steps is not None:
         n = min(n, max_steps)
     for e, oe in zip(envs, oes):   # restart from reset so all envs run exactly n steps
-        oe.reset(seed, e)
+        oe.reset(seed, int(batch.env_ids[e]))
     t0 = time.perf_counter()
     for oe in oes:
         oe.run(n, want_obs=False)
@@ -263,7 +293,7 @@ def _ref_worker(workload, n_envs_flag, env_ids, seed, steps, warmup, barrier, ou
         if mi not in meshes:
             meshes[mi] = batch.oracle_mesh(mi)
         oe = oracle.Env(meshes[mi], batch.env_params(e))
-        oe.reset(seed, e)
+        oe.reset(seed, int(batch.env_ids[e]))
         envs.append(oe)
     for _ in range(warmup):
         for oe in envs:
@@ -341,7 +371,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_e2e(args, sim, n_env, world, rank, seed, barrier, dist):
+def run_e2e(args, sim, n_env, n_total, rank, seed, barrier, dist):
     import numpy as np
     import torch
     from paper_2503_18616_gb300 import inputs
@@ -362,7 +392,7 @@ def run_e2e(args, sim, n_env, world, rank, seed, barrier, dist):
     t_e2e = time.perf_counter() - t0
     from paper_2503_18616_gb300 import sharding
     t_e2e = sharding.max_over_ranks(t_e2e, dist, "cuda")
-    return {"value": sharding.throughput(n_env, world, args.steps, t_e2e), "unit": UNIT,
+    return {"value": n_total * args.steps / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": int(pool[0].nbytes),
            "d2h_bytes_per_step": int(h_obs.nbytes + h_rew.nbytes + h_done.nbytes)}
 
@@ -612,7 +642,7 @@ def mixed_accuracy(batch, sim, mixed, seed, seconds, max_steps):
     oes = []
     for e in (0, 1):
         oe = oracle.Env(om, batch.env_params(e))
-        oe.reset(seed, e)
+        oe.reset(seed, int(batch.env_ids[e]))
         oes.append(oe)
 
     def advance(n):
@@ -627,7 +657,7 @@ def mixed_accuracy(batch, sim, mixed, seed, seconds, max_steps):
     per = time.perf_counter() - t0
     n = max(5, min(max_steps, int(seconds / per)))
     for e, oe in zip((0, 1), oes):
-        oe.reset(seed, e)
+        oe.reset(seed, int(batch.env_ids[e]))
     t0 = time.perf_counter()
     ofb = advance(n)
     dt = time.perf_counter() - t0
@@ -645,6 +675,138 @@ def mixed_accuracy(batch, sim, mixed, seed, seconds, max_steps):
     cpu = {"value": 2 * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
            "sample": f"env 0 (plain) and env 1 (warm-start) x {n} steps, FP64 oracle, 1 host thread, {dt:.1f} s"}
     return acc, cpu
+
+
+def measure_onchip_peaks():
+    """The library's probe kernels on this device: FP32 FMA TFLOP/s and
+    shared-memory GB/s (best of five launches each), or None if they fail."""
+    from paper_2503_18616_gb300 import ffsrl
+    try:
+        fp32, fp32_ms = ffsrl.probe_fp32(5)
+        smem, smem_ms = ffsrl.probe_smem(5)
+    except Exception as exc:   # reported, and the nominal peaks are used instead
+        return {"error": str(exc)}
+    return {"fp32_tflops": fp32, "fp32_probe_ms": fp32_ms, "smem_gbs": smem, "smem_probe_ms": smem_ms}
+
+
+def full_solve_reference(batch, seed, envs, n_steps, n_full):
+    """FP64 oracle positions of `envs` after n_steps of the n_full-iteration
+    solve from reset(seed), and the host seconds it took."""
+    import oracle
+    om = batch.oracle_mesh(0)
+    ref = {}
+    t0 = time.perf_counter()
+    for e in envs:
+        oe = oracle.Env(om, dict(batch.env_params(e), iterations=n_full))
+        oe.reset(seed, int(batch.env_ids[e]))
+        oe.run(n_steps, want_obs=False)
+        ref[e] = oe.state()[0]
+    return ref, om, time.perf_counter() - t0
+
+
+def warm_start_comparison(args, sim, batch, seed, plain_rate, peaks):
+    """Learned warm-start against plain XPBD at equal error, on the benchmark's
+    own batch: the network is trained on the device (untimed, reported), then
+    the fused warm-start step (network + 1 iteration per substep) is timed
+    with CUDA events over K steps without fallback and with the residual
+    fallback at twice the full solve's median residual; its largest vertex
+    error after N steps from reset is measured against the FP64 oracle's
+    10-iteration full solve on the first and last env, as is the plain step's
+    with 1, 2, 3, 5, 7, 10 iterations (ascending, stopping at the first that
+    is at least as accurate as the warm-start: the cheapest plain setting at
+    equal error)."""
+    import torch
+    from paper_2503_18616_gb300 import ffsrl, surrogate
+    n_env, params, n_full = batch.n_env, batch.params, 10
+    tsim = ffsrl.Sim(batch.meshes, params, 512)
+    tr = surrogate.train(tsim, batch.meshes, n_full=n_full, env_substeps=200_000, lr=1e-3, epochs=2, seed=seed)
+    tsim.close()
+    sim.set_network(tr["params"], *tr["norm"])
+    sim.reset(seed + 1)
+    rf = torch.zeros(n_env, device="cuda")
+    for _ in range(10):
+        sim.record_step(n_full, residual=rf, want=False)
+    full_resid = float(np.median(rf.cpu().numpy()))
+    thr = 2.0 * full_resid
+    N = args.acc_steps
+    envs = (0, n_env - 1)
+    ref, om, t_oracle = full_solve_reference(batch, seed, envs, N, n_full)
+    V = om.V
+
+    def error(s):
+        x, _, _ = s.get_state()
+        x = x.cpu().numpy().astype(np.float64)
+        return float(max(np.abs(x[e * V:(e + 1) * V] - ref[e]).max() for e in envs) / om.extent)
+
+    def timed(step, s):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(s.stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(s.stream)
+        torch.cuda.synchronize()
+        return n_env * args.steps / (ev0.elapsed_time(ev1) / 1e3)
+
+    obs = torch.empty((n_env, sim.obs_dim), dtype=torch.float32, device="cuda")
+    rew = torch.empty(n_env, dtype=torch.float32, device="cuda")
+    done = torch.empty(n_env, dtype=torch.uint8, device="cuda")
+    fb = torch.zeros(n_env, dtype=torch.int32, device="cuda")
+    warm = {}
+    for label, t in (("no_fallback", 1e30), ("fallback", thr)):
+        sim.reset(seed)
+        fb.zero_()
+        for _ in range(N):
+            sim.step_surrogate(t, n_full, fallbacks=fb)
+        err = error(sim)
+        frate = float(fb.sum().item()) / (n_env * N * params["substeps"])
+        sim.reset(seed)
+        rate = timed(lambda: sim.step_surrogate(t, n_full, obs=obs, reward=rew, done=done), sim)
+        warm[label] = {"value": rate, "max_pos_err_over_extent": err, "fallback_rate": frate}
+    sim.sync()
+    err_w = warm["no_fallback"]["max_pos_err_over_extent"]
+    plain = {}
+    k_eq = None
+    for k in (1, 2, 3, 5, 7, 10):
+        ps = sim if k == params["iterations"] else ffsrl.Sim(batch.meshes, dict(params, iterations=k), n_env)
+        ps.reset(seed)
+        for _ in range(N):
+            ps.step_into(None, None, None, None)
+        err = error(ps)
+        rate = plain_rate if ps is sim else timed(lambda: ps.step_into(None, obs, rew, done), ps)
+        plain[str(k)] = {"value": rate, "max_pos_err_over_extent": err}
+        if ps is not sim:
+            ps.close()
+        if err <= err_w:
+            k_eq = k
+            break
+    V_, E_, T_ = V, len(sim.mesh_table("edges")) // 2, len(sim.mesh_table("tets")) // 4
+    w_rate = warm["no_fallback"]["value"]
+    net_flops = NET_FLOP_ROW * V_ * params["substeps"]   # per env-step
+    tc_peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    return {
+        "value": w_rate, "unit": UNIT, "ms_per_step": 1e3 * n_env / w_rate, "steps": args.steps,
+        "path": "fused warm-start kernel: network (BF16 tcgen05, FP32 accumulate) + 1 iteration per substep",
+        "max_pos_err_over_extent": err_w, "error_reference": f"FP64 oracle, {n_full} iterations",
+        "accuracy_steps": N, "accuracy_envs": list(envs),
+        "fallback": {"threshold_rule": "2 x median residual the full solve leaves", "threshold": thr,
+                     "full_solve_residual_median": full_resid, **warm["fallback"]},
+        "plain": plain,
+        "plain_equal_error": ({"iterations": k_eq, "value": plain[str(k_eq)]["value"],
+                               "ratio": w_rate / plain[str(k_eq)]["value"]} if k_eq else None),
+        "within_tolerance": err_w <= POS_TOL,
+        "training": {"seconds": tr["seconds"], "env_substeps": tr["env_substeps"], "adam_steps": tr["adam_steps"],
+                     "loss_first": tr["losses"][0], "loss_last": tr["losses"][-1],
+                     "loss_unit": "mean squared error of normalised corrections"},
+        "tensor_roofline": {"bound": "tensor", "achieved": net_flops * w_rate / 1e12, "peak": tc_peak,
+                            "unit": "TFLOP/s", "frac": net_flops * w_rate / 1e12 / tc_peak,
+                            "algorithmic_flops_per_env_step": net_flops,
+                            "peak_source": "bf16_tflops_sustained of MEASURED_PEAKS.json"},
+        "oracle_seconds": t_oracle,
+        "counts": {"V": V_, "E": E_, "T": T_},
+    }
 
 
 def run_ours(args):
@@ -666,7 +828,22 @@ def run_ours(args):
     if rank == 0 or world > 1:
         __graft_entry__.build()
 
-    batch = Batch(args.workload, args.envs)
+    # The env shard of this rank, by global env ids: weak scaling gives every
+    # rank a workload's worth of envs of its own; --fixed-total splits the
+    # workload's envs (contiguous shares, or bin-packed by V + E + T when the
+    # meshes are uneven). The draws follow the global ids, so every env draws
+    # what it draws in a one-GPU run.
+    if args.fixed_total:
+        full = Batch(args.workload, args.envs)
+        work = full.env_work() if len(full.meshes) > 1 else None
+        ids = sharding.shard_envs(full.n_env, world, rank, work)
+        batch = Batch(args.workload, args.envs, env_ids=ids)
+        shard_rule = ("fixed env set split over the ranks, " +
+                      ("bin-packed by V + E + T" if work is not None else "contiguous shares"))
+    else:
+        batch = Batch(args.workload, args.envs)
+        ids = sharding.weak_shard(batch.n_env, rank)
+        shard_rule = "weak: every rank its own envs, global ids rank x n_env + e"
     params = batch.params
     n_env = batch.n_env
     block, flags = 0, 0
@@ -680,7 +857,9 @@ def run_ours(args):
             flags |= ffsrl.SCHED_FOUR_CTAS
     sim = ffsrl.Sim(batch.meshes, params, n_env, env_mesh=batch.env_mesh, env_compliance=batch.env_alpha,
                     block_threads=block, schedule_flags=flags)
-    seed = sharding.rank_seed(args.seed, rank)   # each rank owns its own env shard
+    sim.set_env_ids(ids)
+    seed = args.seed
+    n_total = int(round(sharding.sum_over_ranks(float(n_env), dist, "cuda")))
     mixed = setup_mixed(args, sim, batch, seed) if inputs.WORKLOADS[args.workload].get("mixed") else None
     sim.reset(seed)
     stream = sim.stream
@@ -702,6 +881,8 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
+    onchip = measure_onchip_peaks() if rank == 0 else None   # probe kernels, same clock window
+    torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
     # one event between consecutive steps: per-step latency without any sync
@@ -724,7 +905,7 @@ def run_ours(args):
         n_warm = int(mixed["mask"].sum())
         fallback_rate = float(mixed["fallbacks"].sum().item()) / (n_warm * args.steps * params["substeps"])
     t_ms = sharding.max_over_ranks(t_ms, dist, "cuda")
-    value = sharding.throughput(n_env, world, args.steps, t_ms / 1e3)
+    value = n_total * args.steps / (t_ms / 1e3)
 
     # Spread over seeds: the same measurement from other resets (shorter runs).
     seed_stats = None
@@ -745,7 +926,7 @@ def run_ours(args):
                 e1.record(stream)
             torch.cuda.synchronize()
             ms = sharding.max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
-            vals.append(sharding.throughput(n_env, world, n_s, ms / 1e3))
+            vals.append(n_total * n_s / (ms / 1e3))
         seed_stats = {"seeds": args.seeds, "steps_each": n_s, "mean": float(np.mean(vals)),
                       "std": float(np.std(vals)), "values": vals, "unit": UNIT}
 
@@ -753,7 +934,7 @@ def run_ours(args):
     # observation, reward and done copied out, every step.
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, sim, n_env, world, rank, seed, barrier, dist)
+        e2e = run_e2e(args, sim, n_env, n_total, rank, seed, barrier, dist)
 
     line = None
     if rank == 0:
@@ -769,10 +950,19 @@ def run_ours(args):
         ms_step = t_ms / args.steps
         clock_mhz = float(peaks.get("sm_max_mhz", FALLBACK_PEAKS["sm_max_mhz"]))
         sec = ms_step / 1e3
-        smem_bytes = sum(smem_bytes_per_env_step(V, E, T, params, C, F) for (V, E, T), (C, F) in zip(counts, cf))
-        smem_peak = SMEM_BYTES_PER_CLK_SM * N_SM * clock_mhz * 1e6 / 1e9
+        smem_bytes = sum(smem_alg_bytes_per_env_step(V, E, T, params, C, F) for (V, E, T), (C, F) in zip(counts, cf))
+        kernel_bytes = sum(smem_bytes_per_env_step(V, E, T, params, C, F) for (V, E, T), (C, F) in zip(counts, cf))
         flops = sum(flops_per_env_step(V, E, T, params, C, F) for (V, E, T), (C, F) in zip(counts, cf))
-        alu_peak = 2 * FP32_LANES * N_SM * clock_mhz * 1e6 / 1e12
+        if onchip and "smem_gbs" in onchip:
+            smem_peak, alu_peak = onchip["smem_gbs"], onchip["fp32_tflops"]
+            smem_src = ("measured in this run: ffsrl_probe_smem (conflict-free 16-byte shared-memory loads, "
+                        "2 x 1024-thread CTAs per SM, best of 5)")
+            alu_src = "measured in this run: ffsrl_probe_fp32 (8 independent FMA chains per thread, best of 5)"
+        else:
+            smem_peak = SMEM_BYTES_PER_CLK_SM * N_SM * clock_mhz * 1e6 / 1e9
+            alu_peak = 2 * FP32_LANES * N_SM * clock_mhz * 1e6 / 1e12
+            smem_src = f"nominal: {SMEM_BYTES_PER_CLK_SM} B/clk/SM x {N_SM} SMs x {clock_mhz:.0f} MHz (probe failed)"
+            alu_src = f"nominal: {N_SM} SMs x {FP32_LANES} FP32 lanes x 2 x {clock_mhz:.0f} MHz (probe failed)"
         hbm_bytes = sum(BYTES_VERT * V + 4 * sim.obs_dim + 16 for V, _, _ in counts)
         hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
         single = len(batch.meshes) == 1
@@ -783,12 +973,18 @@ def run_ours(args):
                   f"xpbd_step_kernel, {sim.n_groups} size classes launched concurrently")
         roofline = {"bound": "smem", "achieved": smem_bytes / sec / 1e9, "peak": smem_peak, "unit": "GB/s",
                     "frac": smem_bytes / sec / 1e9 / smem_peak, "traffic": traffic, "kernel": kernel,
-                    "peak_source": f"shared memory: {SMEM_BYTES_PER_CLK_SM} B/clk/SM x {N_SM} SMs x "
-                                   f"{clock_mhz:.0f} MHz max SM clock ({peak_src})",
+                    "peak_source": smem_src,
                     "algorithmic_bytes_per_launch": smem_bytes,
+                    "algorithmic_bytes_rule": "per projection the 12-byte positions of its vertices read and "
+                                              "written: 48 B per edge, 96 B per tet (and connection), 36 B per "
+                                              "grasper face read per substep",
+                    "kernel_bytes_per_launch": kernel_bytes,
+                    "kernel_bytes_frac": kernel_bytes / sec / 1e9 / smem_peak,
+                    "kernel_bytes_rule": "the kernel's float4 (x, y, z, 1/m) loads and stores: 64 B per edge, "
+                                         "128 B per tet, 32 B per vertex per substep",
                     "alu": {"achieved_tflops": flops / sec / 1e12, "peak_tflops": alu_peak,
                             "frac": flops / sec / 1e12 / alu_peak, "algorithmic_flops_per_launch": flops,
-                            "peak_source": f"{N_SM} SMs x {FP32_LANES} FP32 lanes x 2 x {clock_mhz:.0f} MHz"},
+                            "peak_source": alu_src},
                     "hbm": {"achieved_gbs": hbm_bytes / sec / 1e9, "peak_gbs": hbm_peak,
                             "frac": hbm_bytes / sec / 1e9 / hbm_peak, "algorithmic_bytes_per_launch": hbm_bytes,
                             "peak_source": peak_src}}
@@ -796,12 +992,14 @@ def run_ours(args):
         if mixed is not None:
             V, E, T = counts[0]
             n_warm = int(mixed["mask"].sum())
-            b_mix = (n_env - n_warm) * smem_bytes_per_env_step(V, E, T, params) + \
-                n_warm * smem_bytes_per_warm_env_step(V, E, T, params)
+            b_mix = (n_env - n_warm) * smem_alg_bytes_per_env_step(V, E, T, params) + \
+                n_warm * smem_alg_bytes_per_env_step(V, E, T, params)
             roofline = {"bound": "smem", "achieved": b_mix / sec / 1e9, "peak": smem_peak, "unit": "GB/s",
                         "frac": b_mix / sec / 1e9 / smem_peak, "traffic": None,
                         "kernel": "xpbd_step_kernel (even envs) and warm_step_kernel (odd envs) on two streams",
                         "peak_source": roofline["peak_source"], "algorithmic_bytes_per_launch": b_mix,
+                        "algorithmic_bytes_rule": "the constraint projections of both kinds of env (the "
+                                                  "network's operand traffic not counted)",
                         "hbm": roofline["hbm"]}
 
         # Accuracy and CPU baseline: the FP64 oracle advances two sampled envs
@@ -810,7 +1008,7 @@ def run_ours(args):
         cpu = None
         acc = None
         if world == 1 and not args.no_cpu_baseline and mixed is not None:
-            acc, cpu = mixed_accuracy(batch, sim, mixed, seed, args.cpu_seconds, max(args.steps, 50))
+            acc, cpu = mixed_accuracy(batch, sim, mixed, seed, args.cpu_seconds, batch.steps)
         elif world == 1 and not args.no_cpu_baseline:
             # the first and last env, or the smallest and the largest of an uneven batch
             if single:
@@ -819,7 +1017,7 @@ def run_ours(args):
                 vs = [c[0] for c in counts]
                 sample_envs = (int(np.argmin(vs)), int(np.argmax(vs)))
             rate, n_steps, dt, oes = oracle_rate(batch, args.cpu_seconds, seed, sample_envs,
-                                                 max_steps=max(args.steps, 50))
+                                                 max_steps=batch.steps)
             sim.reset(seed)
             for _ in range(n_steps):
                 sim.step_into(None, None, None, None)
@@ -834,25 +1032,30 @@ def run_ours(args):
                 # the oracle's own float32 build over the same steps: the rounding floor
                 o32 = oracle.Env(batch.oracle_mesh(batch.mesh_index(e), precision="f32"),
                                  batch.env_params(e))
-                o32.reset(seed, e)
+                o32.reset(seed, int(batch.env_ids[e]))
                 o32.run(n_steps, want_obs=False)
                 floors.append(float(np.max(np.abs(o32.state()[0] - ox)) / oe.mesh.extent))
             acc = {"max_pos_err_over_extent": max(errs), "per_env": errs, "tolerance": POS_TOL,
                    "fp32_oracle_err_over_extent": floors, "envs": list(sample_envs),
                    "verts": [counts[e][0] for e in sample_envs], "steps": n_steps,
                    "within_tolerance": max(errs) <= POS_TOL,
-                   "within_fp32_floor": all(g <= max(POS_TOL, 10 * f) for g, f in zip(errs, floors))}
+                   "workload_steps": batch.steps,
+                   "within_fp32_floor": all(g <= max(POS_TOL, 2 * f) for g, f in zip(errs, floors)),
+                   "fp32_floor_rule": "error <= max(tolerance, 2 x the oracle's own float32 build's error)"}
             cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"envs {list(sample_envs)} ({[counts[e][0] for e in sample_envs]} vertices) x "
                              f"{n_steps} steps, FP64 oracle, 1 host thread, {dt:.1f} s"}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": args.workload, "n_env_per_gpu": n_env, "envs": batch.describe(),
+                "scaling": "strong" if args.fixed_total else "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "n_env_per_gpu": n_env, "n_env_total": n_total,
+                           "envs": batch.describe(),
                            "verts_total": V_total, "substeps": params["substeps"],
                            "iterations": params["iterations"], "actions": "device counter-based draws",
                            "l2": f"state {24 * V_total / 1e6:.0f} MB > 129 MB L2, no flush",
                            "parallelism": f"env-sharded x{world}",
+                           "sharding": shard_rule,
                            "schedule": {"threads_per_env": sim.block_threads, "envs_per_cta": sim.envs_per_cta,
                                         "ctas_per_sm": sim.ctas_per_sm,
                                         "tma_ring_envs": sim.ring_envs,
@@ -860,6 +1063,12 @@ def run_ours(args):
                 "roofline": roofline, "cpu_baseline": cpu, "accuracy": acc, "e2e": e2e, "latency": latency,
                 "seed_spread": seed_stats,
                 "gpu_launches": args.steps * (sim.n_groups + (1 if mixed is not None else 0)), "clocks": clk}
+        if onchip is not None:
+            line["onchip_peaks"] = dict(onchip, clocks_during_probe="the clocks field (same sampling window)")
+        wspec = inputs.WORKLOADS[args.workload]
+        if (world == 1 and mixed is None and not args.no_warm_start and single and "shape" in wspec
+                and params.get("tool_model", 0) == 0 and params.get("solver", 0) == 0):
+            line["warm_start"] = warm_start_comparison(args, sim, batch, seed, value, load_peaks()[0])
         if mixed is not None:
             line["dtype"] = "f32+bf16"
             line["mixed"] = {"warm_start_envs": "odd env ids", "n_warm_start": int(mixed["mask"].sum()),
@@ -890,6 +1099,11 @@ def main():
     ap.add_argument("--schedule", default="", help="force threads_per_env:envs_per_cta:ring:permute[:ctas_per_sm]")
     ap.add_argument("--acc-steps", type=int, default=50, help="steps of the warm-start accuracy comparison")
     ap.add_argument("--seeds", type=int, default=5, help="extra resets timed for the spread over seeds")
+    ap.add_argument("--fixed-total", action="store_true",
+                    help="split the workload's envs over the ranks (strong scaling) instead of giving every "
+                         "rank its own (weak scaling)")
+    ap.add_argument("--no-warm-start", action="store_true",
+                    help="skip the learned warm-start comparison at equal error")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -188,6 +188,17 @@ int ffsrl_get_info(const ffsrl_sim* sim, ffsrl_info* out);
 /* Thread-local message of the last failed call on this thread. */
 const char* ffsrl_last_error(void);
 
+/* Global env ids of the counter-based draws (Sec. III-B: envs are independent
+ * slices of one batch, so a batch split across processes or GPUs is the same
+ * set of envs): every draw of env e (actions when the step is given none,
+ * observed vertices, target vertex, auto-reset episodes) is made for id
+ * ids_host[e] instead of e. ids_host [n_env] int64 host array, each in
+ * [0, 2^40) (NULL restores the default ids 0 .. n_env-1); ids need not be
+ * distinct or sorted. A shard that holds envs 10..19 of a 1-process run with
+ * ids 10..19 then draws exactly what that run draws for them. Takes effect for
+ * draws made after the call: call it before ffsrl_reset. Synchronises. */
+int ffsrl_set_env_ids(ffsrl_sim* sim, const int64_t* ids_host);
+
 /* --- state access (checkpoint / resume, tests) ----------------------------- */
 
 /* Packed state: x_dev, v_dev [total_verts][3]; tool_dev [n_env][3] float64.
@@ -248,6 +259,27 @@ int ffsrl_network_gradient(ffsrl_sim* sim, const float* features_dev, const floa
  * copies the network runs with. loss_dev as above. Asynchronous. */
 int ffsrl_train_network(ffsrl_sim* sim, const float* features_dev, const float* targets_dev,
                         const float* row_weight_dev, int64_t rows, float weight_sum, float lr, float* loss_dev);
+
+/* One Adam step (as in ffsrl_train_network) on a caller-given gradient:
+ * grad_dev [FFSRL_NET_PARAMS] float32 device array in the layout of the
+ * parameters (for example the sum over data-parallel ranks of their
+ * ffsrl_network_gradient results, divided by the rank count), then re-rounds
+ * the BF16 copies. The step count t of the bias correction is the number of
+ * Adam steps since ffsrl_set_network. Asynchronous; grad_dev must stay valid
+ * until the stream has passed the call. */
+int ffsrl_network_adam_step(ffsrl_sim* sim, const float* grad_dev, float lr);
+
+/* Frozen normalisation of a training batch, computed on the device in
+ * double: over the rows r < rows with row_weight_dev[r] > 0, per feature
+ * column (features_dev [rows][16], the 16th ignored) and per target column
+ * (targets_dev [rows][4], the 4th ignored) the mean and the population
+ * standard deviation (divisor = number of such rows; 1 where a column has no
+ * spread). norm_host [FFSRL_NET_NORM] float32 receives in_mean[15],
+ * in_std[15], out_mean[3], out_std[3], the layout ffsrl_set_network takes.
+ * Synchronises. FFSRL_E_INVAL if no row has a positive weight, FFSRL_E_NAN
+ * if a selected value is not finite. No network needs to be installed. */
+int ffsrl_network_normalisation(ffsrl_sim* sim, const float* features_dev, const float* targets_dev,
+                                const float* row_weight_dev, int64_t rows, float* norm_host);
 
 /* out_dev[r] = (network output of features_dev[r], 0) for r < rows:
  * features_dev [rows][16] float32 raw features (the 16th is ignored), output
@@ -334,14 +366,18 @@ int ffsrl_get_rows(const ffsrl_sim* sim, int64_t* n_rows, int32_t* row_off_host)
  * actions_dev [n_env][3] is required (caller-owned state has no step counter
  * for device-drawn actions). No observation, reward or done flags are
  * produced. The sim's own state is neither read nor changed; only its
- * constraint tables, parameters and schedule are used. Asynchronous on the
- * sim's stream.
+ * constraint tables, parameters and schedule are used. A device error of the
+ * call (non-finite positions, a bounded wait that gave up) is recorded in the
+ * sim's error flags, so the next ffsrl_sync reports it. Sims with the grasper
+ * tool (whose grasp is per-sim state), auto-reset or a mixed rollout are
+ * refused with FFSRL_E_INVAL. Asynchronous on the sim's stream.
  *
  * Scratch: the working copies of the state, the substep-start positions, the
- * per-env counters and (with iterations > 1) the Lagrange multipliers live in
+ * per-env counters and done flags and (with iterations > 1) the Lagrange
+ * multipliers live in
  * one file-scope static device array of FFSRL_NOALLOC_SCRATCH_BYTES (32 MiB),
  * which every GPU that loads the library holds until the process exits. A sim
- * whose scratch would exceed it (about 36 B per padded vertex row plus 16 B per
+ * whose scratch would exceed it (about 36 B per padded vertex row plus 13 B per
  * env, more with iterations > 1 or meshes too large for shared memory) is
  * rejected with FFSRL_E_INVAL and a message giving both sizes; for the
  * 2601-vertex block that is about 340 envs. The first call on a device looks up

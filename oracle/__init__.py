@@ -106,7 +106,7 @@ def _lib(precision: str = "f64") -> ctypes.CDLL:
             L.orc_env_residual.argtypes = [P]
             L.orc_env_features.argtypes = [P, P, P]
             L.orc_env_step_surrogate.restype = I
-            L.orc_env_step_surrogate.argtypes = [P, P, P, D, P, D, I, P, P, P, P, P, P]
+            L.orc_env_step_surrogate.argtypes = [P, P, P, D, P, D, I, P, P, P, P, P, P, P]
             _LIBS[precision] = L
         return _LIBS[precision]
 
@@ -437,16 +437,22 @@ class Env:
     def residual(self) -> float:
         return float(self._L.orc_env_residual(self._h))
 
-    def step_surrogate(self, net, threshold: float, n_full: int, action=None, alpha_d: float = -1.0):
-        """Surrogate-assisted step; returns (obs, reward, done, fallbacks)."""
+    def step_surrogate(self, net, threshold: float, n_full: int, action=None, alpha_d: float = -1.0,
+                       residuals=None):
+        """Surrogate-assisted step; returns (obs, reward, done, fallbacks).
+        `residuals` (a float64 array [substeps], optional) receives the
+        residual each substep checked against the threshold."""
         obs = np.zeros(self.obs_dim)
         rew = np.zeros(1)
         done = np.zeros(1, dtype=np.uint8)
         fb = np.zeros(1, dtype=np.int32)
         a = None if action is None else np.ascontiguousarray(action, dtype=np.float64).reshape(3)
+        if residuals is not None:
+            assert residuals.dtype == np.float64 and residuals.size >= self.params["substeps"]
         rc = self._L.orc_env_step_surrogate(self._h, ctypes.byref(self._p), _ptr(a) if a is not None else None,
                                             float(alpha_d), ctypes.byref(net), float(threshold), int(n_full),
-                                            _ptr(obs), _ptr(rew), _ptr(done), _ptr(fb), None, None)
+                                            _ptr(obs), _ptr(rew), _ptr(done), _ptr(fb), None, None,
+                                            _ptr(residuals) if residuals is not None else None)
         if rc != 0:
             raise ValueError(f"orc_env_step_surrogate rc={rc}")
         return obs, float(rew[0]), int(done[0]), int(fb[0])
@@ -460,7 +466,7 @@ class Env:
         a = None if action is None else np.ascontiguousarray(action, dtype=np.float64).reshape(3)
         rc = self._L.orc_env_step_surrogate(self._h, ctypes.byref(self._p), _ptr(a) if a is not None else None,
                                             float(alpha_d), None, 0.0, int(n_full), None, None, None, None,
-                                            _ptr(F), _ptr(T))
+                                            _ptr(F), _ptr(T), None)
         if rc != 0:
             raise ValueError(f"orc_env_step_surrogate rc={rc}")
         return F, T

@@ -17,7 +17,7 @@ import numpy as np
 N_IN, N_HID, N_OUT = 15, 64, 3
 
 __all__ = ["N_IN", "N_HID", "N_OUT", "mlp_init", "mlp_forward", "mlp_loss", "mlp_backward",
-           "adam_step", "bf16_round"]
+           "adam_step", "bf16_round", "normalisation"]
 
 
 def mlp_init(seed: int, scale: float = 1.0) -> dict:
@@ -75,6 +75,24 @@ def adam_step(p: dict, g: dict, m: dict, v: dict, t: int, lr: float = 1e-3,
         mhat = m[k] / (1 - beta1 ** t)
         vhat = v[k] / (1 - beta2 ** t)
         p[k] = p[k] - lr * mhat / (np.sqrt(vhat) + eps)
+
+
+def normalisation(F: np.ndarray, T: np.ndarray, w: np.ndarray):
+    """Frozen normalisation of the network's inputs and outputs: per column,
+    the mean and the population standard deviation (divisor n) over the rows
+    whose weight is positive; a column with zero spread gets std 1. F holds
+    at least 15 feature columns, T at least 3 target columns.
+
+    Returns (in_mean[15], in_std[15], out_mean[3], out_std[3])."""
+    sel = np.asarray(w).reshape(-1) > 0
+    f = np.asarray(F, dtype=np.float64)[sel][:, :N_IN]
+    t = np.asarray(T, dtype=np.float64)[sel][:, :N_OUT]
+    out = []
+    for a in (f, t):
+        mean = a.sum(axis=0) / len(a)
+        std = np.sqrt(((a - mean) ** 2).sum(axis=0) / len(a))
+        out += [mean, np.where(std > 0, std, 1.0)]
+    return out[0], out[1], out[2], out[3]
 
 
 def bf16_round(a: np.ndarray) -> np.ndarray:

@@ -1459,15 +1459,21 @@ static void sweep(orc_env* s, const orc_params* p, REAL h, REAL alpha_d) {
  * to free vertices, one constraint iteration, residual check; above
  * `threshold` the prediction is restored and `n_full` iterations run instead.
  * Then collision and velocity update as in the plain substep. `fallbacks`
- * (may be NULL) receives the number of substeps that fell back. When
- * `record_F`/`record_T` are given (and `net` is NULL) the step is the plain
- * full solve and records, per substep, the features [substeps][V][15] and the
- * targets [substeps][V][3] = positions after the full solve minus prediction. */
+ * (may be NULL) receives the number of substeps that fell back; `record_R`
+ * (may be NULL) the residual each substep checked [substeps] (with `net`) or
+ * the residual the full solve left (without). When `record_F`/`record_T` are
+ * given (and `net` is NULL) the step is the plain full solve and records, per
+ * substep, the features [substeps][V][15] and the targets [substeps][V][3] =
+ * positions after the full solve minus prediction. The warm-start is defined
+ * with the sphere tool and the distance and volume constraints only: meshes
+ * with connections (R16) and the grasper (R12-R15) are refused. */
 int orc_env_step_surrogate(orc_env* s, const orc_params* p, const double* action, double alpha_d,
                            const orc_mlp* net, double threshold, int n_full, double* obs, double* reward,
-                           unsigned char* done, int* fallbacks, double* record_F, double* record_T) {
+                           unsigned char* done, int* fallbacks, double* record_F, double* record_T,
+                           double* record_R) {
     const orc_mesh* m = s->m;
     if (m->C > 0) return ORC_E_INVAL;   /* the warm-start network sees no connections */
+    if (p->tool_model != 0) return ORC_E_INVAL;   /* nor the grasper's faces and grasp */
     double a[3];
     for (int k = 0; k < 3; ++k)
         a[k] = action ? action[k] : orc_action(s->seed, s->env, (uint64_t)s->t, k);
@@ -1497,7 +1503,9 @@ int orc_env_step_surrogate(orc_env* s, const orc_params* p, const double* action
                 for (int k = 0; k < 3; ++k) s->x[3 * i + k] += (REAL)dx[k];
             }
             sweep(s, p, h, ad);
-            if (orc_env_residual(s) > threshold) {
+            const double r = orc_env_residual(s);
+            if (record_R) record_R[sub] = r;
+            if (r > threshold) {
                 ++nfb;
                 for (int i = 0; i < 3 * m->V; ++i) s->x[i] = xh[i];
                 for (int e = 0; e < m->E; ++e) s->lam_e[e] = 0;
@@ -1507,12 +1515,12 @@ int orc_env_step_surrogate(orc_env* s, const orc_params* p, const double* action
         } else {
             if (record_F) features(s, xh, vh, &record_F[(size_t)sub * ORC_NN_IN * m->V]);
             for (int it = 0; it < n_full; ++it) sweep(s, p, h, ad);
+            if (record_R) record_R[sub] = orc_env_residual(s);
             if (record_T)
                 for (int i = 0; i < 3 * m->V; ++i)
                     record_T[(size_t)sub * 3 * m->V + i] = (double)(s->x[i] - xh[i]);
         }
-        if (p->tool_model == 1) collide_grasper(s, p, sub == p->substeps - 1);
-        else collide_sphere(s, (REAL)p->radius, sub == p->substeps - 1);
+        collide_sphere(s, (REAL)p->radius, sub == p->substeps - 1);
         for (int i = 0; i < 3 * m->V; ++i) s->v[i] = (s->x[i] - s->xprev[i]) / h;
     }
     free(xh);

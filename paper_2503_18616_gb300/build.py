@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libffsrl.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["ffsrl_api.cu", "xpbd_step.cu", "xpbd_cluster.cu", "xpbd_jacobi.cu", "xpbd_surrogate.cu", "mlp_tc.cu", "mesh_setup.cpp"]
+SOURCES = ["ffsrl_api.cu", "xpbd_step.cu", "xpbd_cluster.cu", "xpbd_jacobi.cu", "xpbd_surrogate.cu", "mlp_tc.cu",
+           "mesh_setup.cpp", "peak_probe.cu"]
 
 
 def nvcc() -> str:
@@ -38,7 +39,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
-    headers.append(os.path.join(os.path.dirname(HERE), "include", "ffsrl.h"))
+    inc = os.path.join(os.path.dirname(HERE), "include")
+    headers += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3", "-Xcompiler", "-pthread",
              "-Xcompiler", "-ffp-contract=off",   # host arithmetic (tool start, bounds) rounded as written
              "--expt-relaxed-constexpr", "-I", os.path.join(os.path.dirname(HERE), "include")] + ARCH

@@ -88,6 +88,11 @@ const int kEnvsPerCta[] = {1, 2, 4};
 
 }  // namespace
 
+namespace ffsrl {
+// Message of the last failed call on this thread, for the other translation units.
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace ffsrl
+
 struct ffsrl_sim {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -96,6 +101,7 @@ struct ffsrl_sim {
     size_t max_smem = 0;
     std::vector<HostMesh> meshes;
     std::vector<int> env_mesh, voff, pstart;
+    std::vector<EnvDev> h_envs;     // per-env descriptors (host copy of S.envs)
     long long stride = 0, total_verts = 0;
     std::vector<void*> dev_allocs;
     float* h_pinned = nullptr;  // staging for ffsrl_step_host
@@ -122,6 +128,8 @@ struct ffsrl_sim {
     float* d_adam_v = nullptr;
     float* d_grad = nullptr;
     float* d_loss = nullptr;
+    double* d_norm_acc = nullptr;   // normalisation statistics (38 doubles) and their float32 result (36)
+    float* d_norm_out = nullptr;
     int adam_t = 0;
     float norm[FFSRL_NET_NORM] = {};
     // surrogate-assisted substeps (allocated on first use)
@@ -611,6 +619,7 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
         ev[e].loff = int(loff);
         const double a = env_alpha ? env_alpha[e] : p.compliance_dist;
         ev[e].alpha_d = float(a / (h * h));
+        ev[e].gid = (unsigned long long)e;
         s->voff[e] = int(voff);
         s->pstart[e] = int(pst);
         voff += d.Vp;
@@ -623,6 +632,7 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
     s->total_verts = pst;
     EnvDev* d_ev;
     FFSRL_CUDA(s->upload(&d_ev, ev.data(), ev.size()));
+    s->h_envs = ev;
     FFSRL_CUDA(s->upload(&s->d_pstart, s->pstart.data(), s->pstart.size()));
 
     SimDev& S = s->S;
@@ -1192,6 +1202,47 @@ int ffsrl_train_network(ffsrl_sim* sim, const float* features_dev, const float* 
     return FFSRL_OK;
 }
 
+int ffsrl_network_adam_step(ffsrl_sim* sim, const float* grad_dev, float lr) {
+    if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
+    if (!sim->has_net) return fail(FFSRL_E_INVAL, "no network installed (ffsrl_set_network)");
+    if (!grad_dev) return fail(FFSRL_E_INVAL, "grad_dev must be non-NULL");
+    if (!(lr > 0)) return fail(FFSRL_E_INVAL, "lr must be > 0");
+    FFSRL_CUDA(cudaSetDevice(sim->device));
+    FFSRL_CUDA(cudaMemcpyAsync(sim->d_grad, grad_dev, FFSRL_NET_PARAMS * sizeof(float), cudaMemcpyDeviceToDevice,
+                               sim->stream));
+    sim->adam_t += 1;
+    FFSRL_CUDA(launch_adam(sim->d_master, sim->d_adam_m, sim->d_adam_v, sim->d_grad, FFSRL_NET_PARAMS, lr,
+                           sim->adam_t, sim->stream));
+    FFSRL_CUDA(launch_mlp_pack(sim->d_master, sim->d_wtiles, sim->d_btiles, sim->d_bias, sim->stream));
+    return FFSRL_OK;
+}
+
+int ffsrl_network_normalisation(ffsrl_sim* sim, const float* features_dev, const float* targets_dev,
+                                const float* row_weight_dev, int64_t rows, float* norm_host) {
+    if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
+    if (rows < 1 || !features_dev || !targets_dev || !row_weight_dev || !norm_host)
+        return fail(FFSRL_E_INVAL, "need rows >= 1 and features, targets, weights and norm_host");
+    if ((reinterpret_cast<uintptr_t>(features_dev) | reinterpret_cast<uintptr_t>(targets_dev)) & 15)
+        return fail(FFSRL_E_INVAL, "features and targets must be 16-byte aligned");
+    FFSRL_CUDA(cudaSetDevice(sim->device));
+    if (!sim->d_norm_acc) {
+        FFSRL_CUDA(sim->alloc(&sim->d_norm_acc, 38));
+        FFSRL_CUDA(sim->alloc(&sim->d_norm_out, FFSRL_NET_NORM));
+    }
+    FFSRL_CUDA(launch_norm_stats(reinterpret_cast<const float4*>(features_dev),
+                                 reinterpret_cast<const float4*>(targets_dev), row_weight_dev, rows, sim->d_norm_acc,
+                                 sim->d_norm_out, sim->n_sm, sim->stream));
+    double count = 0;
+    FFSRL_CUDA(cudaMemcpyAsync(&count, sim->d_norm_acc + 18, sizeof(double), cudaMemcpyDeviceToHost, sim->stream));
+    FFSRL_CUDA(cudaMemcpyAsync(norm_host, sim->d_norm_out, FFSRL_NET_NORM * sizeof(float), cudaMemcpyDeviceToHost,
+                               sim->stream));
+    FFSRL_CUDA(cudaStreamSynchronize(sim->stream));
+    if (!(count > 0)) return fail(FFSRL_E_INVAL, "no row has a positive weight");
+    for (int i = 0; i < FFSRL_NET_NORM; ++i)
+        if (!std::isfinite(norm_host[i])) return fail(FFSRL_E_NAN, "non-finite feature or target in the batch");
+    return FFSRL_OK;
+}
+
 int ffsrl_network_forward(ffsrl_sim* sim, const float* features_dev, float* out_dev, int64_t rows) {
     if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
     if (!sim->has_net) return fail(FFSRL_E_INVAL, "no network installed (ffsrl_set_network)");
@@ -1388,6 +1439,23 @@ int ffsrl_set_surrogate_envs(ffsrl_sim* sim, const uint8_t* mask_host, double th
     return FFSRL_OK;
 }
 
+int ffsrl_set_env_ids(ffsrl_sim* sim, const int64_t* ids_host) {
+    if (!sim) return fail(FFSRL_E_INVAL, "sim is NULL");
+    std::vector<EnvDev> ev = sim->h_envs;
+    for (int e = 0; e < sim->n_env; ++e) {
+        const int64_t id = ids_host ? ids_host[e] : int64_t(e);
+        if (id < 0 || id >= (int64_t(1) << 40))
+            return fail(FFSRL_E_INVAL, "env ids must lie in [0, 2^40)");
+        ev[e].gid = (unsigned long long)id;
+    }
+    FFSRL_CUDA(cudaSetDevice(sim->device));
+    FFSRL_CUDA(cudaStreamSynchronize(sim->stream));
+    FFSRL_CUDA(cudaMemcpy(const_cast<EnvDev*>(sim->S.envs), ev.data(), ev.size() * sizeof(EnvDev),
+                          cudaMemcpyHostToDevice));
+    sim->h_envs = ev;
+    return FFSRL_OK;
+}
+
 int ffsrl_set_clamp_angles(ffsrl_sim* sim, const float* angles_dev) {
     if (!sim || !angles_dev) return fail(FFSRL_E_INVAL, "sim and angles_dev must be non-NULL");
     if (sim->params.tool_model != FFSRL_TOOL_GRASPER) return fail(FFSRL_E_INVAL, "the sim has no grasper tool");
@@ -1556,6 +1624,9 @@ extern "C" int ffsrl_step_noalloc(ffsrl_sim* sim, const float* actions_dev, floa
         return fail(FFSRL_E_INVAL, "ffsrl_step_noalloc needs actions_dev, x_dev, v_dev and tool_dev");
     if (sim->mixed) return fail(FFSRL_E_INVAL, "ffsrl_step_noalloc does not step warm-start envs (mixed rollout)");
     if (sim->params.auto_reset) return fail(FFSRL_E_INVAL, "ffsrl_step_noalloc does not auto-reset");
+    if (sim->params.tool_model != FFSRL_TOOL_SPHERE)
+        return fail(FFSRL_E_INVAL, "ffsrl_step_noalloc steps sims with the sphere tool only (the grasper's grasp "
+                                   "state is per-sim state, not caller state)");
     const size_t rows = size_t(sim->stride), n = size_t(sim->n_env);
     bool any_streaming = false;
     for (const LaunchGroup& g : sim->groups) any_streaming |= !g.cfg.resident;
@@ -1567,14 +1638,16 @@ extern "C" int ffsrl_step_noalloc(ffsrl_sim* sim, const float* actions_dev, floa
         }
     // Scratch layout: x, v and x_prev ([3][rows] float each), the working
     // positions of non-resident envs ([rows] float4), contacts ([rows] int),
-    // per-env counters (4 x [n] int32/float), multipliers.
+    // per-env counters (step count, contact count, last distance: 3 x [n]
+    // int32/float; done flags [n] bytes), multipliers. Error flags are not
+    // scratch: they go to the sim's own flags, which ffsrl_sync reports.
     size_t off = 0;
     const size_t o_x = off; off = align256(off + 3 * rows * sizeof(float));
     const size_t o_v = off; off = align256(off + 3 * rows * sizeof(float));
     const size_t o_p = off; off = align256(off + 3 * rows * sizeof(float));
     const size_t o_xg = off; off = align256(off + (any_streaming ? rows * sizeof(float4) : 0));
     const size_t o_c = off; off = align256(off + rows * sizeof(int));
-    const size_t o_env = off; off = align256(off + 4 * n * sizeof(int));
+    const size_t o_env = off; off = align256(off + 3 * n * sizeof(int) + n);
     const size_t o_lam = off; off = align256(off + lam_slots * sizeof(float));
     if (off > size_t(FFSRL_NOALLOC_SCRATCH_BYTES))
         return fail(FFSRL_E_INVAL, "ffsrl_step_noalloc: this sim needs " + std::to_string(off) +
@@ -1595,12 +1668,12 @@ extern "C" int ffsrl_step_noalloc(ffsrl_sim* sim, const float* actions_dev, floa
     int* env_ints = reinterpret_cast<int*>(base + o_env);
     S.t_step = env_ints;
     S.n_contacts = env_ints + n;
-    S.err = env_ints + 2 * n;
-    S.l_prev = reinterpret_cast<float*>(env_ints + 3 * n);
+    S.l_prev = reinterpret_cast<float*>(env_ints + 2 * n);
+    S.done_flag = reinterpret_cast<uint8_t*>(env_ints + 3 * n);
     S.lambda = lam_slots ? reinterpret_cast<float*>(base + o_lam) : nullptr;
     S.tool = tool_dev;
-    // Step counters, contact counts, error flags and last distances start at zero.
-    FFSRL_CUDA(cudaMemsetAsync(env_ints, 0, 4 * n * sizeof(int), sim->stream));
+    // Step counters, contact counts, last distances and done flags start at zero.
+    FFSRL_CUDA(cudaMemsetAsync(env_ints, 0, 3 * n * sizeof(int) + n, sim->stream));
     FFSRL_CUDA(launch_unpack(S, sim->d_pstart, x_dev, v_dev, sim->stream));
     FFSRL_CUDA(launch_all(sim, &S, actions_dev, nullptr, nullptr, nullptr, sim->stream));
     FFSRL_CUDA(launch_pack(S, sim->d_pstart, x_dev, v_dev, sim->stream));

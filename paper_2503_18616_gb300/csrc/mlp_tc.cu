@@ -602,6 +602,86 @@ __global__ void adam_kernel(float* __restrict__ master, float* __restrict__ m, f
     }
 }
 
+// Frozen normalisation of the network's inputs and outputs (the warm-start's
+// training data): column sums over the rows of positive weight, in double.
+// Pass 0 sums the 15 features, the 3 targets and the row count into
+// acc[0..18]; pass 1 sums the squared deviations from mean[0..17] into
+// acc[19..36]. One atomic add per column and block.
+constexpr int kNormCols = 18;
+
+__global__ void __launch_bounds__(256) norm_stats_kernel(const float4* __restrict__ feat,
+                                                         const float4* __restrict__ targ,
+                                                         const float* __restrict__ wrow, long long rows, int pass,
+                                                         double* __restrict__ acc) {
+    __shared__ double s_part[8][kNormCols + 1];
+    double sum[kNormCols + 1];
+#pragma unroll
+    for (int c = 0; c <= kNormCols; ++c) sum[c] = 0.0;
+    double mean[kNormCols];
+#pragma unroll
+    for (int c = 0; c < kNormCols; ++c) mean[c] = pass ? acc[c] / acc[kNormCols] : 0.0;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows;
+         r += (long long)gridDim.x * blockDim.x) {
+        if (!(wrow[r] > 0.f)) continue;
+        const float4* f = feat + 4 * r;
+        const float4 a = f[0], b = f[1], c = f[2], d = f[3], t = targ[r];
+        const float v[kNormCols] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w, d.x, d.y, d.z,
+                                    t.x, t.y, t.z};
+#pragma unroll
+        for (int q = 0; q < kNormCols; ++q) {
+            const double x = double(v[q]) - mean[q];
+            sum[q] += pass ? x * x : x;
+        }
+        sum[kNormCols] += 1.0;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q <= kNormCols; ++q) {
+        double x = sum[q];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) s_part[warp][q] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x <= kNormCols && (pass == 0 || threadIdx.x < kNormCols)) {
+        double x = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) x += s_part[w][threadIdx.x];
+        if (x != 0.0) atomicAdd(&acc[(pass ? kNormCols + 1 : 0) + threadIdx.x], x);
+    }
+}
+
+// norm[0..35] = in_mean[15], in_std[15], out_mean[3], out_std[3] (float32),
+// population standard deviations, 1 for a column without spread.
+__global__ void norm_finish_kernel(const double* __restrict__ acc, float* __restrict__ norm) {
+    const int q = threadIdx.x;
+    if (q >= kNormCols) return;
+    const double n = acc[kNormCols];
+    const double mean = acc[q] / n;
+    const double sd = sqrt(acc[kNormCols + 1 + q] / n);
+    const float s = sd > 0.0 ? float(sd) : 1.f;
+    if (q < 15) {
+        norm[q] = float(mean);
+        norm[15 + q] = s;
+    } else {
+        norm[30 + q - 15] = float(mean);
+        norm[33 + q - 15] = s;
+    }
+}
+
+cudaError_t launch_norm_stats(const float4* feat, const float4* targ, const float* wrow, long long rows, double* acc,
+                              float* norm, int n_sm, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(acc, 0, 2 * (kNormCols + 1) * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const long long want = (rows + 255) / 256;
+    const int grid = int(want < 4ll * n_sm ? (want > 0 ? want : 1) : 4ll * n_sm);
+    for (int pass = 0; pass < 2; ++pass) {
+        norm_stats_kernel<<<grid, 256, 0, st>>>(feat, targ, wrow, rows, pass, acc);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    norm_finish_kernel<<<1, 32, 0, st>>>(acc, norm);
+    return cudaGetLastError();
+}
+
 size_t mlp_train_smem_bytes() { return size_t(kTrSmem); }
 
 cudaError_t launch_mlp_train(const TrainDev& P, const float4* feat, const float4* targ, const float* wrow,

@@ -53,6 +53,12 @@ cudaError_t launch_mlp_train(const TrainDev& P, const float4* feat, const float4
 cudaError_t launch_mlp_pack(const float* master, uint16_t* wtiles, uint16_t* btiles, float* bias, cudaStream_t st);
 cudaError_t launch_adam(float* master, float* m, float* v, float* grad, int n, float lr, int t, cudaStream_t st);
 
+// Frozen normalisation of a training batch (rows of positive weight):
+// norm[36] float32 = in_mean[15], in_std[15], out_mean[3], out_std[3]; acc is
+// device scratch of 38 doubles; acc[18] holds the row count afterwards.
+cudaError_t launch_norm_stats(const float4* feat, const float4* targ, const float* wrow, long long rows, double* acc,
+                              float* norm, int n_sm, cudaStream_t st);
+
 // out[r] = (de-normalised network output of feat[r], 0); feat is [rows][16]
 // raw features (the 16th ignored); err gets bit 0 on an MMA timeout.
 cudaError_t launch_mlp_forward(const MlpDev& net, const float4* feat, float4* out, long long rows, int* err,

@@ -66,6 +66,7 @@ struct EnvDev {
     int voff;       // first padded vertex row of this env
     float alpha_d;  // edge compliance / h^2 (alpha tilde of XPBD)
     int loff;       // first lambda slot of this env (iterations > 1)
+    unsigned long long gid;  // global env id of the counter-based draws (the env index by default)
 };
 
 // Error bits in SimDev::err.

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kJacobiThreads, 3)
     if (st == 0) {
         // Tool update once per step (Algorithm 1), rounded product then sum.
         const unsigned long long t = (unsigned long long)S.t_step[env];
-        const unsigned long long rs = env_stream(S.seed[env], (unsigned long long)env, 0u);
+        const unsigned long long rs = env_stream(S.seed[env], ed.gid, 0u);
         for (int k = 0; k < 3; ++k) {
             const double a = actions ? (double)actions[3 * env + k] : to_unit_pm1(splitmix64_nth(rs, 3ull * t + k));
             double c = __dadd_rn(S.tool[3 * env + k], __dmul_rn(S.action_scale, a));

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(SUB * ENVS, OCC ? OCC : min_ctas_per_sm(SUB * 
         // env's counter-based stream at its step count. Rounded product then
         // rounded sum, so the float64 tool position is reproducible.
         const unsigned long long t = (unsigned long long)S.t_step[env];
-        const unsigned long long rs = env_stream(S.seed[env], (unsigned long long)env, 0u);
+        const unsigned long long rs = env_stream(S.seed[env], ed.gid, 0u);
         for (int k = 0; k < 3; ++k) {
             const double a = actions ? (double)actions[3 * env + k] : to_unit_pm1(splitmix64_nth(rs, 3ull * t + k));
             double c = __dadd_rn(S.tool[3 * env + k], __dmul_rn(S.action_scale, a));
@@ -477,7 +477,7 @@ __device__ void reset_env(const SimDev& S, int env, unsigned long long seed) {
     }
     if (threadIdx.x == 0) {
         int* ids = S.obs_ids + (long long)env * S.n_obs;
-        const unsigned long long st = env_stream(seed, (unsigned long long)env, 1u);
+        const unsigned long long st = env_stream(seed, ed.gid, 1u);
         const int n = M.n_top, k = S.n_obs;
         int m = 0;
         for (int j = n - k; j < n; ++j) {
@@ -493,7 +493,7 @@ __device__ void reset_env(const SimDev& S, int env, unsigned long long seed) {
             ids[b + 1] = key;
         }
         for (int q = 0; q < m; ++q) ids[q] = M.top[ids[q]];
-        const int tgt = M.top[splitmix64_nth(env_stream(seed, (unsigned long long)env, 2u), 0ull) %
+        const int tgt = M.top[splitmix64_nth(env_stream(seed, ed.gid, 2u), 0ull) %
                               (unsigned long long)n];
         S.target[env] = tgt;
         const float4 rt = M.rest_w[tgt];

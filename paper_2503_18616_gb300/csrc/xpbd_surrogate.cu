@@ -30,7 +30,7 @@ namespace {
 // the plain step kernel: rounded float64 product and sum, clamped to the box.
 __device__ void update_tool(const SimDev& S, const MeshDev& M, int env, const float* actions, double* c_out) {
     const unsigned long long t = (unsigned long long)S.t_step[env];
-    const unsigned long long rs = env_stream(S.seed[env], (unsigned long long)env, 0u);
+    const unsigned long long rs = env_stream(S.seed[env], S.envs[env].gid, 0u);
     for (int k = 0; k < 3; ++k) {
         const double a = actions ? (double)actions[3 * env + k] : to_unit_pm1(splitmix64_nth(rs, 3ull * t + k));
         double c = __dadd_rn(S.tool[3 * env + k], __dmul_rn(S.action_scale, a));

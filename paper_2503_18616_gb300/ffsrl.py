@@ -25,13 +25,14 @@ TABLES = {"tets": 0, "flipped": 1, "edges": 2, "ecolor": 3, "tcolor": 4, "eorder
           "torder": 6, "ecol_off": 7, "tcol_off": 8, "top": 9, "faces": 10, "face_opposite": 11,
           "forder": 12, "fcol_off": 13, "conns": 14, "corder": 15, "ccol_off": 16, "objects": 17}
 
-# every symbol include/ffsrl.h declares
+# every symbol include/ffsrl.h and include/ffsrl_probe.h declare
 EXPORTS = ["ffsrl_create", "ffsrl_reset", "ffsrl_step", "ffsrl_step_host", "ffsrl_sync",
            "ffsrl_destroy", "ffsrl_get_info", "ffsrl_last_error", "ffsrl_get_state",
            "ffsrl_set_state", "ffsrl_get_mesh_table", "ffsrl_get_env_ints", "ffsrl_step_noalloc",
            "ffsrl_set_network", "ffsrl_network_forward", "ffsrl_step_surrogate", "ffsrl_record_step",
            "ffsrl_get_rows", "ffsrl_get_network", "ffsrl_network_gradient", "ffsrl_train_network",
-           "ffsrl_set_surrogate_envs", "ffsrl_set_clamp_angles", "ffsrl_get_grasp"]
+           "ffsrl_set_surrogate_envs", "ffsrl_set_clamp_angles", "ffsrl_get_grasp", "ffsrl_network_adam_step",
+           "ffsrl_network_normalisation", "ffsrl_probe_fp32", "ffsrl_probe_smem", "ffsrl_set_env_ids"]
 
 NOALLOC_SCRATCH_BYTES = 32 << 20
 NET_PARAMS = 64 * 15 + 64 + 64 * 64 + 64 + 3 * 64 + 3   # FFSRL_NET_PARAMS
@@ -131,6 +132,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.ffsrl_network_gradient.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_float, P, P]
     L.ffsrl_train_network.restype = ctypes.c_int
     L.ffsrl_train_network.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_float, ctypes.c_float, P]
+    L.ffsrl_network_adam_step.restype = ctypes.c_int
+    L.ffsrl_network_adam_step.argtypes = [P, P, ctypes.c_float]
+    L.ffsrl_network_normalisation.restype = ctypes.c_int
+    L.ffsrl_network_normalisation.argtypes = [P, P, P, P, ctypes.c_int64, P]
+    L.ffsrl_set_env_ids.restype = ctypes.c_int
+    L.ffsrl_set_env_ids.argtypes = [P, P]
+    L.ffsrl_probe_fp32.restype = ctypes.c_int
+    L.ffsrl_probe_fp32.argtypes = [I32, P, P]
+    L.ffsrl_probe_smem.restype = ctypes.c_int
+    L.ffsrl_probe_smem.argtypes = [I32, P, P]
     L.ffsrl_set_clamp_angles.restype = ctypes.c_int
     L.ffsrl_set_clamp_angles.argtypes = [P, P]
     L.ffsrl_get_grasp.restype = ctypes.c_int
@@ -157,6 +168,22 @@ def _dptr(t) -> ctypes.c_void_p | None:
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError("expected a contiguous CUDA tensor")
     return ctypes.c_void_p(t.data_ptr())
+
+
+def probe_fp32(repeats: int = 5) -> tuple[float, float]:
+    """ffsrl_probe_fp32 on the current device: (TFLOP/s, ms of the best launch)."""
+    L = load_library()
+    r, ms = ctypes.c_double(0), ctypes.c_double(0)
+    _check(L.ffsrl_probe_fp32(int(repeats), ctypes.byref(r), ctypes.byref(ms)))
+    return r.value, ms.value
+
+
+def probe_smem(repeats: int = 5) -> tuple[float, float]:
+    """ffsrl_probe_smem on the current device: (GB/s, ms of the best launch)."""
+    L = load_library()
+    r, ms = ctypes.c_double(0), ctypes.c_double(0)
+    _check(L.ffsrl_probe_smem(int(repeats), ctypes.byref(r), ctypes.byref(ms)))
+    return r.value, ms.value
 
 
 def make_params(d: dict, block_threads: int = 0, schedule_flags: int = 0) -> ffsrl_params:
@@ -338,6 +365,25 @@ class Sim:
         _check(self._L.ffsrl_train_network(self._h, _dptr(features), _dptr(targets), _dptr(row_weight),
                                            int(features.shape[0]), float(weight_sum), float(lr), _dptr(loss)))
 
+    def network_adam_step(self, grad, lr: float) -> None:
+        """One Adam step of the master parameters on a device gradient
+        (float32 tensor [NET_PARAMS] in the parameter layout)."""
+        _check(self._L.ffsrl_network_adam_step(self._h, _dptr(grad), float(lr)))
+
+    def network_normalisation(self, features, targets, row_weight):
+        """Frozen normalisation of a batch computed on the device:
+        (in_mean[15], in_std[15], out_mean[3], out_std[3]) as float64 arrays."""
+        out = np.zeros(NET_NORM, np.float32)
+        f = features.reshape(-1, 16)
+        t = targets.reshape(-1, 4)
+        w = row_weight.reshape(-1)
+        if not (f.shape[0] == t.shape[0] == w.shape[0]):
+            raise ValueError("features, targets and row weights need the same number of rows")
+        _check(self._L.ffsrl_network_normalisation(self._h, _dptr(f), _dptr(t), _dptr(w), int(f.shape[0]),
+                                                   _np_ptr(out)))
+        o = out.astype(np.float64)
+        return o[0:15], o[15:30], o[30:33], o[33:36]
+
     def network_forward(self, features, out=None):
         """features: CUDA tensor [rows][16] float32 -> output [rows][4]."""
         torch = self._torch
@@ -378,6 +424,17 @@ class Sim:
         self._mix_keep = fallbacks
         _check(self._L.ffsrl_set_surrogate_envs(self._h, _np_ptr(m), float(threshold), int(n_full),
                                                 _dptr(fallbacks)))
+
+    def set_env_ids(self, ids) -> None:
+        """Global ids of the envs' counter-based draws (None: 0 .. n_env-1);
+        call before reset."""
+        if ids is None:
+            _check(self._L.ffsrl_set_env_ids(self._h, None))
+            return
+        a = np.ascontiguousarray(np.asarray(ids).reshape(-1), dtype=np.int64)
+        if a.size != self.n_env:
+            raise ValueError("need one id per env")
+        _check(self._L.ffsrl_set_env_ids(self._h, _np_ptr(a)))
 
     def set_clamp_angles(self, angles) -> None:
         """Grasper clamp openings (radians, float32 device tensor [n_env])."""

@@ -6,9 +6,9 @@ the position correction of the full constraint solve from features of the
 predicted state, so that one iteration can replace several. Training data come
 from the simulator itself: ffsrl_record_step runs the plain full solve and
 writes, for every vertex row and substep, the features and the target
-correction. Every arithmetic step (recording, forward, backward, Adam) runs in
-the library's CUDA kernels; this module only schedules them and computes the
-frozen normalisation from a recorded sample on the host.
+correction. Every arithmetic step (recording, normalisation, forward,
+backward, Adam) runs in the library's CUDA kernels; this module only
+schedules them.
 """
 from __future__ import annotations
 
@@ -47,22 +47,6 @@ def row_weights(sim, meshes, env_mesh=None):
     return torch.from_numpy(w).to(sim.device)
 
 
-def normalisation(F, T, w, max_rows: int = 2_000_000, seed: int = 0):
-    """Per-feature and per-output mean and standard deviation over weighted
-    rows of a recorded sample (host computation on at most max_rows rows)."""
-    F = F.reshape(-1, 16)
-    T = T.reshape(-1, 4)
-    w = w.reshape(-1)
-    idx = np.nonzero(w.cpu().numpy() > 0)[0]
-    if len(idx) > max_rows:
-        idx = np.sort(np.random.default_rng(seed).choice(idx, max_rows, replace=False))
-    f = F[idx].cpu().numpy().astype(np.float64)[:, :N_IN]
-    t = T[idx].cpu().numpy().astype(np.float64)[:, :N_OUT]
-    in_mean, in_std = f.mean(0), f.std(0)
-    out_mean, out_std = t.mean(0), t.std(0)
-    in_std = np.where(in_std > 0, in_std, 1.0)
-    out_std = np.where(out_std > 0, out_std, 1.0)
-    return in_mean, in_std, out_mean, out_std
 
 
 def train(sim, meshes, n_full: int = 10, env_substeps: int = 200_000, lr: float = 1e-3, epochs: int = 2,
@@ -81,7 +65,8 @@ def train(sim, meshes, n_full: int = 10, env_substeps: int = 200_000, lr: float 
     S = sim.params["substeps"]
     sim.reset(seed)
     F, T = sim.record_step(n_full)
-    norm = normalisation(F, T, w.expand(S, -1), seed=seed)
+    # the frozen normalisation of the first recorded step's rows (device kernel)
+    norm = sim.network_normalisation(F, T, w.expand(S, -1).contiguous())
     sim.set_network(init_network(seed), *norm)
     loss = torch.zeros(1, dtype=torch.float32, device=sim.device)
     losses = []

@@ -1,7 +1,7 @@
 """Host-side checks of the C ABI (no GPU needed).
 
 The library must build for sm_103a, load, and export every entry point that
-include/ffsrl.h declares; without a GPU, creating a simulator must fail
+include/*.h declare; without a GPU, creating a simulator must fail
 cleanly with FFSRL_E_CUDA (no CPU fallback), and bad arguments must be
 rejected before any device work.
 """
@@ -25,9 +25,13 @@ def lib():
 
 
 def _declared_functions():
-    text = open(os.path.join(ROOT, "include", "ffsrl.h")).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(ffsrl_[a-z_]+)\s*\(", text)))
+    inc = os.path.join(ROOT, "include")
+    names = set()
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            text = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, f)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(ffsrl_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -35,7 +39,7 @@ def test_every_declared_symbol_is_exported(lib):
     assert len(declared) >= 12
     assert sorted(ffsrl.EXPORTS) == declared
     out = subprocess.run(["nm", "-D", "--defined-only", ffsrl.LIB_PATH], capture_output=True, text=True).stdout
-    exported = set(re.findall(r"\bT (ffsrl_[a-z_]+)", out))
+    exported = set(re.findall(r"\bT (ffsrl_[a-z_0-9]+)", out))
     for name in declared:
         assert name in exported, name
         getattr(lib, name)

@@ -47,3 +47,18 @@ def test_every_workload_builds_its_batch_and_oracle_meshes():
         assert om.V == b.verts(0)
         if b.params.get("conn_radius", 0.0) > 0:
             assert om.C > 0 and b.params["tool_model"] == 1
+
+
+def test_algorithmic_shared_memory_bytes_follow_the_method():
+    """The roofline's numerator: per projection the 12-byte positions of the
+    touched vertices read and written (48 B per edge, 96 B per tet), so the
+    4096-env launch of the 17x17x9 block moves 67.5 GB; the kernel's float4
+    traffic (w in the fourth lane) is reported beside it, not instead."""
+    p = inputs.default_params()
+    per = bench.smem_alg_bytes_per_env_step(V, E, T, p)
+    assert per == 10 * (E * 48 + T * 96)
+    assert abs(per * 4096 / 1e9 - 67.52) < 0.01
+    assert bench.smem_alg_bytes_per_env_step(V, E, T, dict(p, iterations=3)) == 3 * per
+    pg = inputs.default_params(tool_model=1)
+    assert bench.smem_alg_bytes_per_env_step(V, E, T, pg, C=7, F=11) == 10 * (E * 48 + T * 96 + 7 * 96 + 11 * 36)
+    assert bench.NET_FLOP_ROW == 10496   # 2 x (960 + 4096 + 192)

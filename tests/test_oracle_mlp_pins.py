@@ -83,3 +83,69 @@ def test_bf16_rounding_cases():
     }
     for x, want in cases.items():
         assert oracle.bf16_round(np.array([x]))[0] == want, x
+
+
+def test_adam_constant_gradient_closed_form():
+    """For a constant gradient g the moments are m_t = g (1 - b1^t) and
+    v_t = g^2 (1 - b2^t), so the bias-corrected step is lr g / (|g| + eps) at
+    every t; a swapped b1/b2 or a wrong bias-correction power fails at t = 2, 3."""
+    g0 = np.array([0.3, -4.0, 1e-3, 2.5e-6])
+    p0 = np.array([1.0, -2.0, 3.0, 0.5])
+    lr, eps = 0.01, 1e-8
+    p = {"a": p0.copy()}
+    m = {"a": np.zeros(4)}
+    v = {"a": np.zeros(4)}
+    for t in (1, 2, 3):
+        oracle.adam_step(p, {"a": g0.copy()}, m, v, t, lr=lr, eps=eps)
+        want = p0 - t * lr * g0 / (np.abs(g0) + eps)
+        assert np.allclose(p["a"], want, rtol=1e-13, atol=1e-15), t
+        assert np.allclose(m["a"], g0 * (1 - 0.9 ** t), rtol=1e-13)
+        assert np.allclose(v["a"], g0 ** 2 * (1 - 0.999 ** t), rtol=1e-13)
+
+
+def test_adam_two_steps_by_hand():
+    """Gradients g1 = 1 then g2 = -1 (b1 0.9, b2 0.999): m1 = 0.1, v1 = 0.001,
+    so the first step is lr; m2 = 0.09 - 0.1 = -0.01 and v2 = 0.000999 + 0.001
+    = 0.001999 = 1 - 0.999^2, so m2_hat = -0.01 / 0.19 = -1/19 and v2_hat = 1:
+    the second step is -lr/19. With g2 = 3 instead: m2 = 0.39, m2_hat = 39/19,
+    v2 = 0.009999, v2_hat = 9999/1999."""
+    lr = 0.01
+    for g2, step2 in ((-1.0, -lr / 19.0), (3.0, lr * (39.0 / 19.0) / np.sqrt(9999.0 / 1999.0))):
+        p = {"a": np.array([0.25])}
+        m = {"a": np.zeros(1)}
+        v = {"a": np.zeros(1)}
+        oracle.adam_step(p, {"a": np.array([1.0])}, m, v, 1, lr=lr, eps=0.0)
+        assert np.isclose(p["a"][0], 0.25 - lr, rtol=1e-14)
+        oracle.adam_step(p, {"a": np.array([g2])}, m, v, 2, lr=lr, eps=0.0)
+        assert np.isclose(p["a"][0], 0.25 - lr - step2, rtol=1e-13), g2
+
+
+def test_normalisation_closed_forms():
+    """Columns taking two values a and b equally often have mean (a + b)/2
+    and standard deviation |a - b|/2; a constant column gets std 1; rows of
+    zero weight do not count; scaling a column by s scales its mean by s and
+    its std by |s|."""
+    n = 64
+    a = np.linspace(-1, 2, 15)
+    b = a + np.arange(1, 16)
+    F = np.zeros((2 * n + 3, 16))
+    F[:n, :15] = a
+    F[n:2 * n, :15] = b
+    F[2 * n:, :15] = 1e6            # zero-weight rows
+    F[:, 7] = 3.0                   # constant column
+    T = np.zeros((2 * n + 3, 4))
+    T[:n, :3] = [1.0, -2.0, 5.0]
+    T[n:2 * n, :3] = [3.0, -2.0, -5.0]
+    w = np.ones(2 * n + 3)
+    w[2 * n:] = 0.0
+    im, isd, om, osd = oracle.normalisation(F, T, w)
+    want_m = (a + b) / 2
+    want_s = np.abs(b - a) / 2
+    want_m[7], want_s[7] = 3.0, 1.0
+    assert np.allclose(im, want_m, rtol=1e-14) and np.allclose(isd, want_s, rtol=1e-14)
+    assert np.allclose(om, [2.0, -2.0, 0.0]) and np.allclose(osd, [1.0, 1.0, 5.0])
+    s = -2.5
+    F2 = F.copy()
+    F2[:, 3] *= s
+    im2, isd2, _, _ = oracle.normalisation(F2, T, w)
+    assert np.isclose(im2[3], s * im[3]) and np.isclose(isd2[3], abs(s) * isd[3])

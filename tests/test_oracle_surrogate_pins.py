@@ -134,3 +134,71 @@ def test_more_iterations_leave_a_smaller_residual():
     _, _, e_ref = _env(iterations=10)
     e_ref.step()
     assert e_ref.residual() < e_one.residual()
+
+
+def test_one_ring_features_closed_form_on_the_top_face():
+    """F[:, 6:9] (and 9:12) against the grid geometry. The five-tet split puts
+    an edge on every axis-aligned grid segment and on the one face diagonal of
+    each cell face that joins its two corners with an odd coordinate sum. On
+    the top face of a 5x5x3 block (spacing D, gravity off) that gives:
+      - vertex (2,2,2), even: neighbours +-x, +-y and -z: offset (0, 0, -D/5);
+      - vertex (1,2,2), odd: five axis neighbours, four diagonals in the top
+        face and four going down: offset (0, 0, -5D/13);
+      - corner (0,0,2), even: +x, +y, -z: offset (D, D, -D)/3.
+    A 1-ring mean that counted the vertex itself would give -D/6, -5D/14 and
+    D/4. With velocities v_z = k z (k a constant) the velocity offsets are k
+    times the z position offsets, and the predicted positions move by h v."""
+    D = inputs.CELL
+    m = oracle.Mesh(*inputs.grid_block(5, 5, 3))
+    p = inputs.default_params(n_obs=4, gravity=(0.0, 0.0, 0.0))
+    e = oracle.Env(m, p)
+    e.reset(1)
+    F = e.features()
+    vid = lambda i, j, k: (k * 5 + j) * 5 + i  # noqa: E731
+    cases = {vid(2, 2, 2): (0.0, 0.0, -D / 5), vid(1, 2, 2): (0.0, 0.0, -5 * D / 13),
+             vid(0, 0, 2): (D / 3, D / 3, -D / 3)}
+    for i, want in cases.items():
+        assert np.allclose(F[i, 6:9], want, rtol=1e-12, atol=1e-18), i
+    # velocity field v = (0, 0, k z) on the free vertices
+    kz = 2.0
+    x, _, _ = e.state()
+    v = np.zeros_like(x)
+    v[:, 2] = kz * x[:, 2] * (m.inv_mass > 0)
+    e.set_state(v=v)
+    G = e.features()
+    h = p["dt"] / p["substeps"]
+    for i, want in cases.items():
+        # z offsets scale by (1 + h k) for positions and by k for velocities
+        # (every neighbour here is free: the bottom layer is two cells below)
+        assert np.allclose(G[i, 6:9], np.array(want) * [1, 1, 1 + h * kz], rtol=1e-12, atol=1e-18), i
+        assert np.allclose(G[i, 9:12], [0.0, 0.0, kz * want[2]], rtol=1e-12, atol=1e-18), i
+
+
+def test_surrogate_step_refuses_the_grasper():
+    """The warm-start is defined with the sphere tool (the network's features
+    have no grasp or face terms), as on the GPU, which refuses it too."""
+    m = oracle.Mesh(*inputs.grid_block(5, 4, 3))
+    p = inputs.default_params(n_obs=4, tool_model=1)
+    e = oracle.Env(m, p)
+    e.reset(0)
+    with pytest.raises(ValueError):
+        e.step_surrogate(_zero_net(), threshold=np.inf, n_full=10)
+    with pytest.raises(ValueError):
+        e.step_record(n_full=10)
+
+
+def test_recorded_residuals_are_the_checked_ones():
+    """The per-substep residuals the surrogate step reports are those the
+    threshold decision saw: with the threshold between two of them, exactly
+    the substeps above it fall back."""
+    m, p, e1 = _env(iterations=1)
+    net = oracle.Net.from_params(oracle.mlp_init(2), out_std=np.full(3, 1e-6))
+    r = np.zeros(p["substeps"])
+    e1.step_surrogate(net, threshold=np.inf, n_full=5, residuals=r)
+    assert np.all(r > 0)
+    thr = float(np.median(r))
+    _, _, e2 = _env(iterations=1)
+    r2 = np.zeros(p["substeps"])
+    _, _, _, fb = e2.step_surrogate(net, threshold=thr, n_full=5, residuals=r2)
+    assert r2[0] == r[0]                        # the same first substep
+    assert fb == int(np.sum(r2 > thr)) and 0 < fb < p["substeps"]
