@@ -17,6 +17,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -481,7 +482,7 @@ def run_warmstart(args):
     obs = torch.empty((n_env, sim.obs_dim), dtype=torch.float32, device="cuda")
     rew = torch.empty(n_env, dtype=torch.float32, device="cuda")
     done = torch.empty(n_env, dtype=torch.uint8, device="cuda")
-    for label, thr in (("no_fallback", 1e30), ("threshold_configured", w["threshold"]),
+    for label, thr in (("no_fallback", math.inf), ("threshold_configured", w["threshold"]),
                        ("threshold_5x_full_solve_residual", 5 * full_resid),
                        ("threshold_2x_full_solve_residual", 2 * full_resid)):
         sim.reset(args.seed)
@@ -499,7 +500,7 @@ def run_warmstart(args):
     pipe.set_network(tr["params"], *tr["norm"])
     pipe.reset(args.seed)
     warm["no_fallback_per_substep_launches"] = {
-        "threshold": None, "env_steps_per_s": timed(lambda: pipe.step_surrogate(1e30, n_full, obs=obs, reward=rew,
+        "threshold": None, "env_steps_per_s": timed(lambda: pipe.step_surrogate(math.inf, n_full, obs=obs, reward=rew,
                                                                                done=done), pipe)}
     pipe.close()
     sim.sync()
@@ -755,7 +756,7 @@ def warm_start_comparison(args, sim, batch, seed, plain_rate, peaks):
     done = torch.empty(n_env, dtype=torch.uint8, device="cuda")
     fb = torch.zeros(n_env, dtype=torch.int32, device="cuda")
     warm = {}
-    for label, t in (("no_fallback", 1e30), ("fallback", thr)):
+    for label, t in (("no_fallback", math.inf), ("fallback", thr)):
         sim.reset(seed)
         fb.zero_()
         for _ in range(N):

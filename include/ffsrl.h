@@ -129,6 +129,10 @@ typedef struct {
 #define FFSRL_SCHED_FOUR_CTAS 128  /* with FFSRL_SCHED_FORCE: the 256-thread, one-env, resident, ring
                                       kernel with registers budgeted for four CTAs per SM (64 per
                                       thread); FFSRL_E_INVAL where four CTAs do not fit an SM */
+#define FFSRL_SCHED_WARM_STAGED 256  /* fused warm-start step: the kernel that stages the network's
+                                        input tiles and corrections in global memory, instead of the
+                                        one that builds each tile's input just in time (the default
+                                        where a mesh's 1-ring spans at most four 128-row tiles) */
 
 /* Sizes of a created simulator. */
 typedef struct {
@@ -296,7 +300,10 @@ int ffsrl_network_forward(ffsrl_sim* sim, const float* features_dev, float* out_
  * then collision and velocity update. Outputs as ffsrl_step; fallbacks_dev
  * [n_env] int32 (may be NULL) is incremented once per fallen-back substep;
  * residual_dev [n_env] float32 (may be NULL) is raised to the largest checked
- * residual (the caller initialises it, e.g. to zero). Asynchronous. */
+ * residual (the caller initialises it, e.g. to zero). A threshold of +inf
+ * never falls back (the residual is then evaluated only for residual_dev);
+ * any other threshold falls back unless the residual is at most the
+ * threshold, so a NaN residual falls back. Asynchronous. */
 int ffsrl_step_surrogate(ffsrl_sim* sim, const float* actions_dev, float* obs_dev, float* reward_dev,
                          uint8_t* done_dev, double threshold, int32_t n_full, int32_t* fallbacks_dev,
                          float* residual_dev);

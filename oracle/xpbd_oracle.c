@@ -1390,7 +1390,7 @@ static void features(const orc_env* s, const REAL* xh, const REAL* vh, double* F
 }
 
 /* Largest relative constraint violation at the current positions:
- * |C| / d for edges, |C| / |V0| for tets. */
+ * |C| / d for edges, |C| / |V0| for tets; NaN if any of them is NaN (W5). */
 double orc_env_residual(const orc_env* s) {
     const orc_mesh* m = s->m;
     double r = 0;
@@ -1398,12 +1398,14 @@ double orc_env_residual(const orc_env* s) {
         REAL ab[3];
         vsub(&s->x[3 * m->edge[2 * e]], &s->x[3 * m->edge[2 * e + 1]], ab);
         double c = fabs((double)(vnorm(ab) - m->d[e])) / (double)m->d[e];
+        if (isnan(c)) return c;
         if (c > r) r = c;
     }
     for (int t = 0; t < m->T; ++t) {
         const int* q = &m->tet[4 * t];
         double c = fabs((double)(tet_volume(&s->x[3 * q[0]], &s->x[3 * q[1]], &s->x[3 * q[2]], &s->x[3 * q[3]]) -
                                  m->V0[t])) / fabs((double)m->V0[t]);
+        if (isnan(c)) return c;
         if (c > r) r = c;
     }
     return r;
@@ -1458,6 +1460,8 @@ static void sweep(orc_env* s, const orc_params* p, REAL h, REAL alpha_d) {
 /* Surrogate-assisted step: per substep predict, add the network's correction
  * to free vertices, one constraint iteration, residual check; above
  * `threshold` the prediction is restored and `n_full` iterations run instead.
+ * A threshold of +inf never falls back; any other falls back unless the
+ * residual is at most the threshold (so a NaN residual falls back).
  * Then collision and velocity update as in the plain substep. `fallbacks`
  * (may be NULL) receives the number of substeps that fell back; `record_R`
  * (may be NULL) the residual each substep checked [substeps] (with `net`) or
@@ -1503,9 +1507,12 @@ int orc_env_step_surrogate(orc_env* s, const orc_params* p, const double* action
                 for (int k = 0; k < 3; ++k) s->x[3 * i + k] += (REAL)dx[k];
             }
             sweep(s, p, h, ad);
-            const double r = orc_env_residual(s);
+            /* W5: a threshold of +inf never falls back; any other threshold
+             * falls back unless the residual is at most it (NaN falls back) */
+            const int decide = !(isinf(threshold) && threshold > 0);
+            const double r = (decide || record_R) ? orc_env_residual(s) : 0.0;
             if (record_R) record_R[sub] = r;
-            if (r > threshold) {
+            if (decide && !(r <= threshold)) {
                 ++nfb;
                 for (int i = 0; i < 3 * m->V; ++i) s->x[i] = xh[i];
                 for (int e = 0; e < m->E; ++e) s->lam_e[e] = 0;

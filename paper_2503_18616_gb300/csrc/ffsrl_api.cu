@@ -213,7 +213,7 @@ int check_params(const ffsrl_params& p) {
         return fail(FFSRL_E_INVAL, "block_threads must be 0, 128, 256, 384, 512 or 1024");
     if (p.schedule_flags & ~(FFSRL_SCHED_FORCE | FFSRL_SCHED_NO_PERMUTE | FFSRL_SCHED_NO_RING |
                              FFSRL_SCHED_ENVS2 | FFSRL_SCHED_ENVS4 | FFSRL_SCHED_SURROGATE_PIPELINE |
-                             FFSRL_SCHED_NO_CLUSTER | FFSRL_SCHED_FOUR_CTAS))
+                             FFSRL_SCHED_NO_CLUSTER | FFSRL_SCHED_FOUR_CTAS | FFSRL_SCHED_WARM_STAGED))
         return fail(FFSRL_E_INVAL, "unknown schedule_flags bits");
     if ((p.schedule_flags & FFSRL_SCHED_ENVS2) && (p.schedule_flags & FFSRL_SCHED_ENVS4))
         return fail(FFSRL_E_INVAL, "FFSRL_SCHED_ENVS2 and FFSRL_SCHED_ENVS4 are exclusive");
@@ -302,6 +302,13 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, const Schedule& sc, MeshDev& d)
             rs[q] = rw[i];
         }
         if (chunks.empty()) chunks.resize(8, 0);
+        // how many 128-row network tiles apart a slot and its 1-ring neighbours lie
+        int reach = 0;
+        for (int q = 0; q < m.V; ++q) {
+            const int i = sc.vert_of[q];
+            for (int k = off[i]; k < off[i + 1]; ++k)
+                reach = std::max(reach, std::abs(q / 128 - int(sc.slot_of[nb[k]]) / 128));
+        }
         int* d_hdr;
         uint4* d_ch;
         float4* d_rs;
@@ -348,6 +355,7 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, const Schedule& sc, MeshDev& d)
         d.snbr_hdr = d_hdr;
         d.snbr_ch = d_ch;
         d.max_deg = max_deg;
+        d.tile_reach = reach;
         d.rest_s = d_rs;
     }
     // Tool box around the rest bounding box and tool start above the top face.
@@ -920,7 +928,7 @@ int ffsrl_reset(ffsrl_sim* sim, const uint8_t* env_mask_dev, uint64_t seed) {
 namespace {
 int launch_warm_groups(ffsrl_sim* sim, cudaStream_t st, bool sublists, const float* actions, float* obs,
                        float* reward, uint8_t* done, float threshold, int n_full, int* fallbacks, float* residual);
-size_t warm_smem(const ffsrl_sim* s, const LaunchGroup& g);
+size_t warm_smem(const ffsrl_sim* s, const LaunchGroup& g, bool* jit = nullptr);
 }  // namespace
 
 namespace {
@@ -967,7 +975,11 @@ int ffsrl_step(ffsrl_sim* sim, const float* actions_dev, float* obs_dev, float* 
         for (const LaunchGroup& g : sim->groups) {
             if (g.jacobi) FFSRL_CUDA(configure_jacobi_step(g.smem));
             else if (g.cluster <= 1) FFSRL_CUDA(configure_step(g.cfg, g.smem));
-            if (sim->mixed && g.n_warm) FFSRL_CUDA(configure_warm_step(warm_smem(sim, g)));
+            if (sim->mixed && g.n_warm) {
+                bool jit = false;
+                const size_t ws = warm_smem(sim, g, &jit);
+                FFSRL_CUDA(configure_warm_step(ws, jit));
+            }
         }
         FFSRL_CUDA(cudaStreamBeginCapture(sim->graph_stream, cudaStreamCaptureModeThreadLocal));
         const int rc = step_body(sim, sim->graph_stream, actions_dev, obs_dev, reward_dev, done_dev);
@@ -1284,15 +1296,34 @@ size_t substep_smem(const ffsrl_sim* s, const LaunchGroup& g, bool& resident) {
     return resident ? res : substep_smem_bytes(vp, false);
 }
 
-// Shared memory of the fused warm-start step for a group (0: does not fit).
-size_t warm_smem(const ffsrl_sim* s, const LaunchGroup& g) {
-    size_t b = 0;
+// Shared memory of the fused warm-start step for a group (0: does not fit),
+// and in *jit which of its two kernels runs: the just-in-time one where every
+// mesh's 1-ring spans at most kWarmJitMaxReach tiles and it fits (unless
+// FFSRL_SCHED_WARM_STAGED), else the staged one.
+size_t warm_smem(const ffsrl_sim* s, const LaunchGroup& g, bool* jit) {
+    size_t b_jit = 0, b_st = 0;
+    bool can_jit = !(s->params.schedule_flags & FFSRL_SCHED_WARM_STAGED);
     for (int mi : g.meshes) {
         const MeshDev& d = s->h_meshes[g.permute ? 1 : 0][mi];
         if (d.max_deg > kWarmMaxDegree) return 0;
-        b = std::max(b, warm_smem_bytes(d.Vp, d.ring_bytes, d.n_seg));
+        can_jit &= d.tile_reach <= kWarmJitMaxReach;
+        b_jit = std::max(b_jit, warm_smem_bytes(d.Vp, d.ring_bytes, d.n_seg, true));
+        b_st = std::max(b_st, warm_smem_bytes(d.Vp, d.ring_bytes, d.n_seg, false));
     }
-    return b + 1024 + 256 <= s->max_smem ? b : 0;   // room for the kernel's static shared memory
+    const size_t room = 1024 + 256;   // the kernels' static shared memory
+    const bool use_jit = can_jit && b_jit + room <= s->max_smem;
+    if (jit) *jit = use_jit;
+    if (use_jit) return b_jit;
+    return b_st + room <= s->max_smem ? b_st : 0;
+}
+
+// Residual evaluation and fallback decision of a warm-start substep: a
+// threshold of +inf never falls back (and the residual is evaluated only if
+// it is requested); any other threshold falls back unless the residual is at
+// most the threshold (a NaN residual falls back).
+void set_residual_flags(SubstepCtl& C, float threshold, const float* residual) {
+    C.decide = !(std::isinf(threshold) && threshold > 0) ? 1 : 0;
+    C.check = (C.decide || residual) ? 1 : 0;
 }
 
 // Fused warm-start steps of the groups that fit (all envs of each group, or
@@ -1302,6 +1333,7 @@ int launch_warm_groups(ffsrl_sim* sim, cudaStream_t st, bool sublists, const flo
     SubstepCtl C{};
     C.mode = kSubstepSurrogate;
     C.threshold = threshold;
+    set_residual_flags(C, threshold, residual);
     C.n_full = n_full;
     C.lambda = sim->d_lambda_full;
     C.fallbacks = fallbacks;
@@ -1311,12 +1343,13 @@ int launch_warm_groups(ffsrl_sim* sim, cudaStream_t st, bool sublists, const flo
     C.arows = sim->d_arows;
     for (const LaunchGroup& g : sim->groups) {
         const int n = sublists ? g.n_warm : g.n;
-        const size_t smem = warm_smem(sim, g);
+        bool jit = false;
+        const size_t smem = warm_smem(sim, g, &jit);
         if (!n || !smem) continue;
         SimDev S = sim->S;
         S.meshes = sim->d_meshes[g.permute ? 1 : 0];
-        FFSRL_CUDA(launch_warm_step(S, sim->net, C, sublists ? g.d_warm : g.d_list, n, smem, actions, obs, reward,
-                                    done, st));
+        FFSRL_CUDA(launch_warm_step(S, sim->net, C, sublists ? g.d_warm : g.d_list, n, smem, jit, actions, obs,
+                                    reward, done, st));
     }
     return FFSRL_OK;
 }
@@ -1363,6 +1396,7 @@ int run_substeps(ffsrl_sim* sim, int mode, const float* actions, float* obs, flo
         C.dx = sim->d_dx;
         C.target = target_out ? reinterpret_cast<float4*>(target_out) + size_t(sub) * rows : nullptr;
         C.threshold = threshold;
+        set_residual_flags(C, threshold, residual);
         C.n_full = n_full;
         C.lambda = sim->d_lambda_full;
         C.fallbacks = fallbacks;

@@ -46,10 +46,12 @@ __global__ void __launch_bounds__(kThreads) smem_probe_kernel(unsigned* out, int
     const int t = int(threadIdx.x);
     for (int it = 0; it < iters; ++it) {
         // a quarter warp reads 8 consecutive words from a multiple of 8: one
-        // whole 128-byte line, every bank once; the start moves every trip
+        // whole 128-byte line, every bank once. The kLoads words of a thread
+        // are distinct (offsets u x 256 below the 2048-word buffer), so none
+        // of the loads repeats another, and the start moves every trip.
 #pragma unroll
         for (int u = 0; u < kLoads; ++u) {
-            const uint4 v = buf[(t + u * kThreads + it * 32) & (kWords - 1)];
+            const uint4 v = buf[(t + u * (kWords / kLoads) + it * 32) & (kWords - 1)];
             a0 ^= v.x ^ v.y;
             a1 ^= v.z ^ v.w;
         }

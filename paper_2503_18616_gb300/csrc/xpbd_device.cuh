@@ -43,7 +43,7 @@ struct MeshDev {
     const uint4* snbr_ch;
     const float4* rest_s;             // [V] rest position and inverse mass (slot order)
     int max_deg;                      // largest vertex degree
-    int pad2;
+    int tile_reach;                   // largest |s / 128 - j / 128| over slots s and their 1-ring slots j
     int parts;                        // segments per colour (CTAs of a cluster holding one env)
     int part_slots;                   // slots per part, a multiple of 32 (parts > 1)
     const float* inv_ncons;           // [V] 1 / (constraints containing the slot's vertex), slot order

@@ -26,6 +26,10 @@ namespace ffsrl {
 
 namespace {
 
+// Maximum that keeps a NaN (fmaxf drops it): a NaN violation makes the
+// residual NaN, which then falls back (the warm-start's residual reading).
+__device__ __forceinline__ float nan_max(float r, float c) { return (isnan(c) || c > r) ? c : r; }
+
 // Tool update once per step (Algorithm 1, "evaluate instrument state"), as in
 // the plain step kernel: rounded float64 product and sum, clamped to the box.
 __device__ void update_tool(const SimDev& S, const MeshDev& M, int env, const float* actions, double* c_out) {
@@ -148,10 +152,10 @@ __device__ float env_residual(const float4* X, const MeshDev& M, int* s_max) {
         const unsigned char* base = M.recs + sg.x;
         if (c < M.n_ecol) {
             for (int q = st; q < sg.z; q += SUB)
-                r = fmaxf(r, edge_violation(X, __ldg(reinterpret_cast<const uint2*>(base) + q)));
+                r = nan_max(r, edge_violation(X, __ldg(reinterpret_cast<const uint2*>(base) + q)));
         } else {
             for (int q = st; q < sg.z; q += SUB)
-                r = fmaxf(r, tet_violation(X, __ldg(reinterpret_cast<const uint4*>(base) + q)));
+                r = nan_max(r, tet_violation(X, __ldg(reinterpret_cast<const uint4*>(base) + q)));
         }
     }
     // non-negative floats order like their bit patterns; NaN maps above +inf
@@ -213,9 +217,11 @@ __global__ void __launch_bounds__(SUB) substep_kernel(SimDev S, SubstepCtl C, co
     float* lam = C.lambda ? C.lambda + ed.loff : nullptr;
     if (C.mode == kSubstepSurrogate) {
         iterate<SUB>(X, M, 1, ed.alpha_d, S.alpha_v, nullptr);
-        const float r = env_residual<SUB>(X, M, &s_resid);
-        if (st == 0 && C.residual) C.residual[env] = fmaxf(C.residual[env], r);
-        if (!(r <= C.threshold)) atomicMax(&s_red, 1);   // a NaN residual also falls back
+        if (C.check) {
+            const float r = env_residual<SUB>(X, M, &s_resid);
+            if (st == 0 && C.residual) C.residual[env] = fmaxf(C.residual[env], r);
+            if (C.decide && !(r <= C.threshold)) atomicMax(&s_red, 1);   // a NaN residual also falls back
+        }
         __syncthreads();
         if (s_red) {
             // Fallback: back to the bare prediction, then the full solve.
@@ -374,29 +380,38 @@ cudaError_t launch_substep(const SimDev& S, const SubstepCtl& C, const int* env_
 // One CTA of 256 threads advances one env through all substeps of a step with
 // its positions resident in shared memory, as the plain step kernel does, and
 // runs the warm-start network inside the same CTA on the tensor cores. Per
-// substep:
-//   1. features of every row (shared-memory slot) at the predicted state, one
-//      row per thread, normalised, rounded to BF16 and written to global
-//      scratch already in the tensor-core operand layout (4 KB per 128 rows);
-//   2. the network tile by tile: the tile's input copied to shared memory
-//      (fetched into registers during the previous tile), three tcgen05.mma
-//      chains into TMEM with the bias/ReLU/BF16 epilogues in between, the
-//      corrections to global scratch;
-//   3. the corrections added to the free vertices (every tile's features saw
-//      the uncorrected prediction), one constraint iteration with the records
-//      streamed through a TMA double buffer, the residual sweep (order-free,
-//      records from L2), the fallback to the full solve if the residual
-//      exceeds the threshold;
-//   4. collision, the velocity update and the next prediction.
+// substep: the features of every row (shared-memory slot) at the predicted
+// state, the network tile by tile (128 rows: three tcgen05.mma chains into
+// TMEM with the bias / ReLU / BF16 epilogues in between), the corrections
+// added to the free vertices (every tile's features see the uncorrected
+// prediction, as the method defines), one constraint iteration with the
+// records streamed through a TMA double buffer, the residual sweep (order-free,
+// records from L2) and the fallback to the full solve above the threshold,
+// then collision, the velocity update and the next prediction.
+//
+// Two kernels implement it:
+//   - warm_step_jit_kernel (meshes whose 1-ring spans at most four 128-row
+//     tiles of slots): warps 4-7 build each tile's input just in time, while
+//     warps 0-3 run the previous tile's tensor-core chain and epilogues; a
+//     tile's network output stays in TMEM (four 16-column slots) until no
+//     later tile's features read its rows, and is then added to the
+//     positions. No global scratch but the predicted velocities and the
+//     substep-start positions.
+//   - warm_step_kernel (any mesh that fits): the features of every row first,
+//     written to global scratch in the operand layout, then the network tile
+//     by tile with the corrections staged in global scratch.
 // Shared memory holds the positions and one region used in turn by the record
-// ring (constraint phases) and by the weight and hidden tiles (network phase),
-// so three CTAs fit on an SM. Predicted velocities and substep-start
+// ring (constraint phases) and by the weight, hidden and input tiles (network
+// phase), so three CTAs fit on an SM. Predicted velocities and substep-start
 // positions live in global memory in slot order (L1/L2-resident while the CTA
 // runs). The fallback rebuilds the prediction exactly: x~ = fma(h, v~, x_prev)
-// is the same rounded operation that made it.
+// is the same rounded operation that made it. The two kernels give the same
+// bits.
 namespace {
 
 constexpr int kNetBytes = kMlpWeightBytes + 16384;   // weight tiles + one hidden tile
+constexpr int kJitNetBytes = kNetBytes + 4096;        // + one input tile
+constexpr int kJitSlots = 4;                          // TMEM slots of pending network outputs
 
 struct WarmLayout {
     size_t x, u, bias, segs, bits, total;
@@ -407,6 +422,21 @@ struct WarmLayout {
         bias = u + (un + 127) / 128 * 128;
         segs = bias + 144 * 4;
         bits = segs + size_t(n_seg) * 16;
+        total = bits + size_t(Vp / 32) * 4;
+    }
+};
+
+// The just-in-time kernel reads the segment table from L2 instead of shared
+// memory (the room goes to the input tile).
+struct JitLayout {
+    size_t x, u, bias, bits, total;
+    __host__ __device__ JitLayout(int Vp, int ring_bytes) {
+        x = 0;
+        u = size_t(Vp) * 16;
+        const size_t un =
+            2 * size_t(ring_bytes) > size_t(kJitNetBytes) ? 2 * size_t(ring_bytes) : size_t(kJitNetBytes);
+        bias = u + (un + 127) / 128 * 128;
+        bits = bias + 144 * 4;
         total = bits + size_t(Vp / 32) * 4;
     }
 };
@@ -472,387 +502,242 @@ __device__ bool ring_sweep(float4* X, const MeshDev& M, const int4* segs, unsign
     return true;
 }
 
-}  // namespace
-
-size_t warm_smem_bytes(int Vp, int ring_bytes, int n_seg) { return WarmLayout(Vp, ring_bytes, n_seg).total; }
-
-__global__ void __launch_bounds__(kWarmThreads, 3)
-    warm_step_kernel(SimDev S, MlpDev net, SubstepCtl C, const int* __restrict__ env_list, int n_list,
-                     const float* __restrict__ actions, float* __restrict__ obs, float* __restrict__ reward,
-                     uint8_t* __restrict__ done) {
-    using namespace tc;
-    constexpr int SUB = kWarmThreads;
-    extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ __align__(8) uint64_t mbar[3];   // [0], [1] record ring; [2] tensor-core completion
-    __shared__ uint32_t tmem_slot;
-    __shared__ double s_tool[3];
-    __shared__ int s_resid;
-    if (int(blockIdx.x) >= n_list) return;
-    const int env = env_list[blockIdx.x];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const EnvDev ed = S.envs[env];
-    const MeshDev& M = S.meshes[ed.mesh];
-    const int V = M.V, Vp = M.Vp;
+// Loads the env's state (vertex order in, slot order out), keeps the
+// substep-start positions and predicts the first substep (Algorithm 1).
+__device__ void warm_load_predict(const SimDev& S, const MeshDev& M, const EnvDev& ed, float4* X, float* Px,
+                                  float* Py, float* Pz, float4* VH) {
     const long long stride = S.stride;
-    const WarmLayout L(Vp, M.ring_bytes, M.n_seg);
-    float4* X = reinterpret_cast<float4*>(sm + L.x);
-    unsigned char* U = sm + L.u;            // record ring, or weight tiles + hidden tile
-    unsigned char* Wt = U;
-    unsigned char* Ht = U + kMlpWeightBytes;
-    unsigned char* At = Ht;                 // the input tile is dead once layer 1 has read it
-    float* bias = reinterpret_cast<float*>(sm + L.bias);
-    int4* segs = reinterpret_cast<int4*>(sm + L.segs);
-    unsigned* bits = reinterpret_cast<unsigned*>(sm + L.bits);
-    float* Px = S.pg + ed.voff;
-    float* Py = Px + stride;
-    float* Pz = Py + stride;
-    float4* DX = C.scratch + ed.voff;       // corrections, slot order
-    float4* VH = C.vpred + ed.voff;         // predicted velocities, slot order
-    uint4* AR = C.arows + 2 * (ed.voff + 128ll * env);   // network input tiles, 4 KB each
+    const float h = S.h;
+    const float hgx = h * S.gx, hgy = h * S.gy, hgz = h * S.gz;
+    const float* gx = S.x + ed.voff;
+    const float* gv = S.v + ed.voff;
+    for (int i = threadIdx.x; i < M.V; i += kWarmThreads) {
+        const int s = M.slot_of[i];
+        const float w = M.rest_w[i].w;
+        const float x0 = gx[i], x1 = gx[stride + i], x2 = gx[2 * stride + i];
+        float v0 = gv[i], v1 = gv[stride + i], v2 = gv[2 * stride + i];
+        Px[s] = x0;
+        Py[s] = x1;
+        Pz[s] = x2;
+        if (w > 0.f) {
+            v0 += hgx;
+            v1 += hgy;
+            v2 += hgz;
+            X[s] = make_float4(__fmaf_rn(h, v0, x0), __fmaf_rn(h, v1, x1), __fmaf_rn(h, v2, x2), w);
+        } else {
+            X[s] = make_float4(x0, x1, x2, w);
+        }
+        VH[s] = make_float4(v0, v1, v2, 0.f);
+    }
+}
 
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
-                     "r"(kWarmTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+// Features of slot s (15 values, normalised, the 16th zero) packed as BF16
+// pairs; rows s >= V give zeros.
+__device__ __forceinline__ void warm_features(const MeshDev& M, const MlpDev& net, const float4* X, const float4* VH,
+                                              int s, float cx, float cy, float cz, uint32_t* pk) {
+    using namespace tc;
+    float f[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) f[q] = 0.f;
+    if (s < M.V) {
+        const float4 xs = X[s];
+        const float4 vs = VH[s];
+        const int hd = M.snbr_hdr[s], deg = hd & 31;
+        const uint4* ch = M.snbr_ch + (hd >> 5);
+        const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+        const uint4 c0 = ch[0], c1 = deg > 8 ? ch[1] : zero, c2 = deg > 16 ? ch[2] : zero;
+        const uint32_t w[12] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y, c2.z, c2.w};
+        float m0 = 0.f, m1 = 0.f, m2 = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f;
+#pragma unroll
+        for (int q = 0; q < kWarmMaxDegree; ++q) {
+            if (q < deg) {
+                const int j = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFF;
+                const float4 xj = X[j];
+                const float4 vj = VH[j];
+                m0 += xj.x; m1 += xj.y; m2 += xj.z;
+                n0 += vj.x; n1 += vj.y; n2 += vj.z;
+            }
+        }
+        const float4 rs = M.rest_s[s];
+        f[0] = xs.x - rs.x; f[1] = xs.y - rs.y; f[2] = xs.z - rs.z;
+        f[3] = vs.x; f[4] = vs.y; f[5] = vs.z;
+        if (deg > 0) {
+            const float inv = 1.0f / float(deg);
+            f[6] = m0 * inv - xs.x; f[7] = m1 * inv - xs.y; f[8] = m2 * inv - xs.z;
+            f[9] = n0 * inv - vs.x; f[10] = n1 * inv - vs.y; f[11] = n2 * inv - vs.z;
+        }
+        f[12] = xs.x - cx; f[13] = xs.y - cy; f[14] = xs.z - cz;
+#pragma unroll
+        for (int q = 0; q < 15; ++q) f[q] = (f[q] - net.in_mean[q]) * net.in_inv_std[q];
     }
-    for (int i = tid; i < 144; i += SUB) bias[i] = net.bias[i];
-    for (int c = tid; c < M.n_seg; c += SUB) segs[c] = M.segs[c];
-    for (int w = tid; w < Vp / 32; w += SUB) bits[w] = 0u;
-    if (tid == 0) {
-        mbar_init(&mbar[0]);
-        mbar_init(&mbar[1]);
-        mbar_init(&mbar[2]);
-        update_tool(S, M, env, actions, s_tool);
-    }
-    // Load the state (vertex order in, slot order out) and predict the first substep.
+#pragma unroll
+    for (int q = 0; q < 8; ++q) pk[q] = bf16_bits(f[2 * q]) | (bf16_bits(f[2 * q + 1]) << 16);
+}
+
+// Bias, ReLU and BF16 rounding of 16 accumulator columns c0 .. c0+15 of this
+// thread's row into the hidden tile (K-major, 64 columns).
+__device__ __forceinline__ void warm_hidden16(uint32_t taddr, const float* bias, int c0, unsigned char* Ht,
+                                              int erow) {
+    using namespace tc;
+    float v[16];
+    tmem_ld16(taddr, v);
+    uint32_t pk[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        pk[q] = bf16_bits(fmaxf(v[2 * q] + bias[c0 + 2 * q], 0.f)) |
+                (bf16_bits(fmaxf(v[2 * q + 1] + bias[c0 + 2 * q + 1], 0.f)) << 16);
+    *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8, 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8 + 1, 8)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+}
+
+// The de-normalised network output (3 accumulator columns from v) of slot s
+// added to a free vertex.
+__device__ __forceinline__ void warm_correct(float4* X, const MlpDev& net, const float* bias, int s, int V,
+                                             const float* v) {
+    if (s >= V) return;
+    float4 xi = X[s];
+    if (!(xi.w > 0.f)) return;
+    const float y0 = (v[0] + bias[128]) * net.out_std[0] + net.out_mean[0];
+    const float y1 = (v[1] + bias[129]) * net.out_std[1] + net.out_mean[1];
+    const float y2 = (v[2] + bias[130]) * net.out_std[2] + net.out_mean[2];
+    xi.x += y0;
+    xi.y += y1;
+    xi.z += y2;
+    X[s] = xi;
+}
+
+// Sphere collision (Sec. III-A "Collisions"), the velocity update and the
+// next substep's prediction (Algorithm 1), two vertices per thread and trip
+// with their global loads issued together; on the last substep only the
+// collision, with the contact bits.
+__device__ void warm_collide_advance(const SimDev& S, const MeshDev& M, float4* X, float* Px, float* Py, float* Pz,
+                                     float4* VH, unsigned* bits, float cx, float cy, float cz, bool last) {
+    constexpr int SUB = kWarmThreads;
+    const int V = M.V;
     const float h = S.h, inv_h = S.inv_h;
     const float hgx = h * S.gx, hgy = h * S.gy, hgz = h * S.gz;
-    {
-        const float* gx = S.x + ed.voff;
-        const float* gv = S.v + ed.voff;
-        for (int i = tid; i < V; i += SUB) {
-            const int s = M.slot_of[i];
-            const float w = M.rest_w[i].w;
-            const float x0 = gx[i], x1 = gx[stride + i], x2 = gx[2 * stride + i];
-            float v0 = gv[i], v1 = gv[stride + i], v2 = gv[2 * stride + i];
-            Px[s] = x0;
-            Py[s] = x1;
-            Pz[s] = x2;
+    const float rad = S.radius, rad2 = rad * rad;
+    for (int s0 = threadIdx.x; s0 < V; s0 += 2 * SUB) {
+        float4 xv[2];
+        float p0[2], p1[2], p2[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int s = s0 + u * SUB;
+            if (s < V) {
+                xv[u] = X[s];
+                p0[u] = Px[s];
+                p1[u] = Py[s];
+                p2[u] = Pz[s];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int s = s0 + u * SUB;
+            if (s >= V) continue;
+            float4 xi = xv[u];
+            const float w = xi.w;
+            if (w > 0.f) {
+                const float dx = xi.x - cx, dy = xi.y - cy, dz = xi.z - cz;
+                const float l2 = dx * dx + dy * dy + dz * dz;
+                if (l2 < rad2) {
+                    const float len = sqrtf(l2);
+                    if (len > 0.f) {
+                        const float f = __fdividef(rad, len);
+                        xi.x = cx + f * dx;
+                        xi.y = cy + f * dy;
+                        xi.z = cz + f * dz;
+                    } else {
+                        xi.x = cx;
+                        xi.y = cy;
+                        xi.z = cz + rad;
+                    }
+                    if (last) {
+                        const int i = M.vert_of[s];
+                        atomicOr(&bits[i >> 5], 1u << (i & 31));
+                    }
+                }
+            }
+            if (last) {
+                X[s] = xi;
+                continue;
+            }
+            float v0 = (xi.x - p0[u]) * inv_h, v1 = (xi.y - p1[u]) * inv_h, v2 = (xi.z - p2[u]) * inv_h;
+            Px[s] = xi.x;
+            Py[s] = xi.y;
+            Pz[s] = xi.z;
             if (w > 0.f) {
                 v0 += hgx;
                 v1 += hgy;
                 v2 += hgz;
-                X[s] = make_float4(__fmaf_rn(h, v0, x0), __fmaf_rn(h, v1, x1), __fmaf_rn(h, v2, x2), w);
-            } else {
-                X[s] = make_float4(x0, x1, x2, w);
+                xi.x = __fmaf_rn(h, v0, xi.x);
+                xi.y = __fmaf_rn(h, v1, xi.y);
+                xi.z = __fmaf_rn(h, v2, xi.z);
             }
             VH[s] = make_float4(v0, v1, v2, 0.f);
+            X[s] = xi;
         }
     }
-    fence_before_sync();
-    __syncthreads();
-    fence_after_sync();
-    const uint32_t tmem = tmem_slot;
-    const uint32_t idesc64 = umma_idesc_bf16(128, 64), idesc16 = umma_idesc_bf16(128, 16);
-    const uint32_t aW1 = saddr(Wt), aW2 = aW1 + 2048, aW3 = aW1 + 10240, aA = saddr(At), aH = saddr(Ht);
-    const float cx = float(s_tool[0]), cy = float(s_tool[1]), cz = float(s_tool[2]);
-    const int n_tiles = (V + 127) / 128;
-    // TMEM lanes of this warp (a warp reaches the 32 lanes of its quarter) and
-    // the column half it reads back in the hidden-layer epilogues.
-    const int q4 = warp & 3, chalf = warp >> 2;
-    const uint32_t tlane = uint32_t(32 * q4) << 16;
-    const int erow = 32 * q4 + lane;
-    uint32_t phase = 0;   // tensor-core completions so far
-    uint32_t k = 0;       // record copies so far
-    bool failed = false;
-    int n_fallback = 0;
+}
 
-    for (int sub = 0; sub < S.substeps && !failed; ++sub) {
-        const bool last = sub == S.substeps - 1;
-        if (tid == 0) s_resid = 0;
-        // -- the weight tiles into the shared region (the ring used it last)
-        for (int i = tid; i < kMlpWeightBytes / 16; i += SUB)
-            reinterpret_cast<uint4*>(Wt)[i] = reinterpret_cast<const uint4*>(net.wtiles)[i];
-        // -- features of every row at the predicted state, normalised and
-        //    rounded to BF16, written as the network's input tiles (the
-        //    tensor-core operand layout) to global scratch: one row per thread
-        for (int s = tid; s < n_tiles * 128; s += SUB) {
-            float f[16];
-#pragma unroll
-            for (int q = 0; q < 16; ++q) f[q] = 0.f;
-            if (s < V) {
-                const float4 xs = X[s];
-                const float4 vs = VH[s];
-                const int hd = M.snbr_hdr[s], deg = hd & 31;
-                const uint4* ch = M.snbr_ch + (hd >> 5);
-                const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
-                const uint4 c0 = ch[0], c1 = deg > 8 ? ch[1] : zero, c2 = deg > 16 ? ch[2] : zero;
-                const uint32_t w[12] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y, c2.z, c2.w};
-                float m0 = 0.f, m1 = 0.f, m2 = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f;
-#pragma unroll
-                for (int q = 0; q < kWarmMaxDegree; ++q) {
-                    if (q < deg) {
-                        const int j = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFF;
-                        const float4 xj = X[j];
-                        const float4 vj = VH[j];
-                        m0 += xj.x; m1 += xj.y; m2 += xj.z;
-                        n0 += vj.x; n1 += vj.y; n2 += vj.z;
-                    }
-                }
-                const float4 rs = M.rest_s[s];
-                f[0] = xs.x - rs.x; f[1] = xs.y - rs.y; f[2] = xs.z - rs.z;
-                f[3] = vs.x; f[4] = vs.y; f[5] = vs.z;
-                if (deg > 0) {
-                    const float inv = 1.0f / float(deg);
-                    f[6] = m0 * inv - xs.x; f[7] = m1 * inv - xs.y; f[8] = m2 * inv - xs.z;
-                    f[9] = n0 * inv - vs.x; f[10] = n1 * inv - vs.y; f[11] = n2 * inv - vs.z;
-                }
-                f[12] = xs.x - cx; f[13] = xs.y - cy; f[14] = xs.z - cz;
-#pragma unroll
-                for (int q = 0; q < 15; ++q) f[q] = (f[q] - net.in_mean[q]) * net.in_inv_std[q];
-            }
-            uint32_t pk[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) pk[q] = bf16_bits(f[2 * q]) | (bf16_bits(f[2 * q + 1]) << 16);
-            unsigned char* tile = reinterpret_cast<unsigned char*>(AR) + size_t(s >> 7) * 4096;
-            *reinterpret_cast<uint4*>(tile + tile_off(s & 127, 0, 2)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-            *reinterpret_cast<uint4*>(tile + tile_off(s & 127, 1, 2)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-        }
-        __syncthreads();
-        // -- the network, one 128-row tile at a time (the next tile's input
-        //    is fetched into registers while the current tile runs)
-        uint4 a_next = AR[tid];
-        for (int t = 0; t < n_tiles; ++t) {
-            reinterpret_cast<uint4*>(At)[tid] = a_next;
-            if (t + 1 < n_tiles) a_next = AR[(t + 1) * 256 + tid];
-            fence_async_smem();
-            fence_before_sync();
-            __syncthreads();
-            fence_after_sync();
-            // Layer 1: D[0:64) = A (128 x 16) W1^T.
-            if (tid == 0) {
-                umma_bf16(tmem, umma_desc(aA, 128, 256), umma_desc(aW1, 128, 256), idesc64, 0);
-                umma_commit(&mbar[2]);
-            }
-            if (__syncthreads_or(!mbar_wait(&mbar[2], phase & 1))) {
-                failed = true;
-                break;
-            }
-            ++phase;
-            fence_after_sync();
-            // Epilogue 1: bias, ReLU, BF16 -> hidden tile (each warp: 32 rows x 32 columns).
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int c0 = 32 * chalf + 16 * c;
-                float v[16];
-                tmem_ld16(tmem + tlane + c0, v);
-                uint32_t pk[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    pk[q] = bf16_bits(fmaxf(v[2 * q] + bias[c0 + 2 * q], 0.f)) |
-                            (bf16_bits(fmaxf(v[2 * q + 1] + bias[c0 + 2 * q + 1], 0.f)) << 16);
-                *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8, 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8 + 1, 8)) =
-                    make_uint4(pk[4], pk[5], pk[6], pk[7]);
-            }
-            fence_async_smem();
-            fence_before_sync();
-            __syncthreads();
-            fence_after_sync();
-            // Layer 2: D[64:128) = H1 (128 x 64) W2^T, four K = 16 steps.
-            if (tid == 0) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    umma_bf16(tmem + 64, umma_desc(aH + 256 * j, 128, 1024), umma_desc(aW2 + 256 * j, 128, 1024),
-                              idesc64, j);
-                umma_commit(&mbar[2]);
-            }
-            if (__syncthreads_or(!mbar_wait(&mbar[2], phase & 1))) {
-                failed = true;
-                break;
-            }
-            ++phase;
-            fence_after_sync();
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const int c0 = 32 * chalf + 16 * c;
-                float v[16];
-                tmem_ld16(tmem + tlane + 64 + c0, v);
-                uint32_t pk[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    pk[q] = bf16_bits(fmaxf(v[2 * q] + bias[64 + c0 + 2 * q], 0.f)) |
-                            (bf16_bits(fmaxf(v[2 * q + 1] + bias[64 + c0 + 2 * q + 1], 0.f)) << 16);
-                *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8, 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8 + 1, 8)) =
-                    make_uint4(pk[4], pk[5], pk[6], pk[7]);
-            }
-            fence_async_smem();
-            fence_before_sync();
-            __syncthreads();
-            fence_after_sync();
-            // Layer 3: D[0:16) = H2 (128 x 64) W3^T (rows 3..15 of W3 are zero).
-            if (tid == 0) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    umma_bf16(tmem, umma_desc(aH + 256 * j, 128, 1024), umma_desc(aW3 + 256 * j, 128, 1024), idesc16,
-                              j);
-                umma_commit(&mbar[2]);
-            }
-            if (__syncthreads_or(!mbar_wait(&mbar[2], phase & 1))) {
-                failed = true;
-                break;
-            }
-            ++phase;
-            fence_after_sync();
-            if (warp < 4) {
-                float v[16];
-                tmem_ld16(tmem + tlane, v);
-                const int s = t * 128 + erow;
-                if (s < V) {
-                    const float y0 = (v[0] + bias[128]) * net.out_std[0] + net.out_mean[0];
-                    const float y1 = (v[1] + bias[129]) * net.out_std[1] + net.out_mean[1];
-                    const float y2 = (v[2] + bias[130]) * net.out_std[2] + net.out_mean[2];
-                    DX[s] = make_float4(y0, y1, y2, 0.f);
-                }
-            }
-            fence_before_sync();
-            __syncthreads();   // the next tile overwrites the input tile and TMEM columns 0..63
-            fence_after_sync();
-        }
-        if (failed) break;
-        // -- corrections of the free vertices (the features above saw none of them)
-        for (int s = tid; s < V; s += SUB) {
-            float4 xi = X[s];
-            if (xi.w > 0.f) {
-                const float4 d = DX[s];
-                xi.x += d.x;
-                xi.y += d.y;
-                xi.z += d.z;
-                X[s] = xi;
-            }
-        }
-        // -- one iteration and the residual sweep, then the fallback to the full solve
+// One constraint iteration, the residual sweep (when C.check) and the
+// fallback to the full solve (when C.decide and the residual is not at most
+// the threshold, NaN included). Returns false (uniformly) if a bounded wait
+// gave up.
+__device__ bool warm_iterate(const SimDev& S, const MeshDev& M, const EnvDev& ed, int env, const SubstepCtl& C,
+                             float4* X, const float* Px, const float* Py, const float* Pz, const float4* VH,
+                             const int4* segs, unsigned char* U, uint64_t* mbar, uint32_t& k, int* s_resid,
+                             int& n_fallback) {
+    constexpr int SUB = kWarmThreads;
+    const int tid = threadIdx.x;
+    const float h = S.h;
+    if (!ring_sweep(X, M, segs, U, mbar, k, 1, ed.alpha_d, S.alpha_v, nullptr)) return false;
+    float res = 0.f;
+    if (C.check) {
+        // it only reads positions, so it needs neither the colour order nor
+        // barriers; the unpadded record lists come from L2
         float rmax = 0.f;
-        if (!ring_sweep(X, M, segs, U, mbar, k, 1, ed.alpha_d, S.alpha_v, nullptr)) {
-            failed = true;
-            break;
-        }
-        // residual sweep: it only reads positions, so it needs neither the
-        // colour order nor barriers; the unpadded record lists come from L2
-        {
-            const uint2* er = M.erec;
-            const uint4* tr = M.trec;
+        const uint2* er = M.erec;
+        const uint4* tr = M.trec;
 #pragma unroll 4
-            for (int q = tid; q < M.E; q += SUB) rmax = fmaxf(rmax, edge_violation(X, __ldg(er + q)));
+        for (int q = tid; q < M.E; q += SUB) rmax = nan_max(rmax, edge_violation(X, __ldg(er + q)));
 #pragma unroll 4
-            for (int q = tid; q < M.T; q += SUB) rmax = fmaxf(rmax, tet_violation(X, __ldg(tr + q)));
-        }
+        for (int q = tid; q < M.T; q += SUB) rmax = nan_max(rmax, tet_violation(X, __ldg(tr + q)));
         // non-negative floats order like their bit patterns; NaN maps above +inf
-        atomicMax(&s_resid, isnan(rmax) ? 0x7f800001 : __float_as_int(rmax));
+        atomicMax(s_resid, isnan(rmax) ? 0x7f800001 : __float_as_int(rmax));
         __syncthreads();
-        const float res = __int_as_float(s_resid);
+        res = __int_as_float(*s_resid);
         if (tid == 0 && C.residual) C.residual[env] = fmaxf(C.residual[env], res);
-        if (!(res <= C.threshold)) {   // a NaN residual also falls back (uniform over the CTA)
-            for (int s = tid; s < V; s += SUB) {
-                const float w = X[s].w;
-                const float4 vh = VH[s];
-                const float p0 = Px[s], p1 = Py[s], p2 = Pz[s];
-                X[s] = w > 0.f ? make_float4(__fmaf_rn(h, vh.x, p0), __fmaf_rn(h, vh.y, p1), __fmaf_rn(h, vh.z, p2), w)
-                               : make_float4(p0, p1, p2, w);
-            }
-            if (!ring_sweep(X, M, segs, U, mbar, k, C.n_full, ed.alpha_d, S.alpha_v,
-                            C.lambda ? C.lambda + ed.loff : nullptr)) {
-                failed = true;
-                break;
-            }
-            ++n_fallback;
-        }
-        // -- collision, velocity update and the next prediction (two vertices
-        //    per thread and trip, their global loads issued together)
-        const float rad = S.radius, rad2 = rad * rad;
-        for (int s0 = tid; s0 < V; s0 += 2 * SUB) {
-            float4 xv[2];
-            float p0[2], p1[2], p2[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int s = s0 + u * SUB;
-                if (s < V) {
-                    xv[u] = X[s];
-                    p0[u] = Px[s];
-                    p1[u] = Py[s];
-                    p2[u] = Pz[s];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int s = s0 + u * SUB;
-                if (s >= V) continue;
-                float4 xi = xv[u];
-                const float w = xi.w;
-                if (w > 0.f) {
-                    const float dx = xi.x - cx, dy = xi.y - cy, dz = xi.z - cz;
-                    const float l2 = dx * dx + dy * dy + dz * dz;
-                    if (l2 < rad2) {
-                        const float len = sqrtf(l2);
-                        if (len > 0.f) {
-                            const float f = __fdividef(rad, len);
-                            xi.x = cx + f * dx;
-                            xi.y = cy + f * dy;
-                            xi.z = cz + f * dz;
-                        } else {
-                            xi.x = cx;
-                            xi.y = cy;
-                            xi.z = cz + rad;
-                        }
-                        if (last) {
-                            const int i = M.vert_of[s];
-                            atomicOr(&bits[i >> 5], 1u << (i & 31));
-                        }
-                    }
-                }
-                if (last) {
-                    X[s] = xi;
-                    continue;
-                }
-                float v0 = (xi.x - p0[u]) * inv_h, v1 = (xi.y - p1[u]) * inv_h, v2 = (xi.z - p2[u]) * inv_h;
-                Px[s] = xi.x;
-                Py[s] = xi.y;
-                Pz[s] = xi.z;
-                if (w > 0.f) {
-                    v0 += hgx;
-                    v1 += hgy;
-                    v2 += hgz;
-                    xi.x = __fmaf_rn(h, v0, xi.x);
-                    xi.y = __fmaf_rn(h, v1, xi.y);
-                    xi.z = __fmaf_rn(h, v2, xi.z);
-                }
-                VH[s] = make_float4(v0, v1, v2, 0.f);
-                X[s] = xi;
-            }
-        }
-        __syncthreads();
     }
-    if (failed) {
-        // A bounded wait gave up: let the tensor-core commit in flight land
-        // (bounded), free TMEM, flag the env and leave its state.
-        mbar_wait(&mbar[2], phase & 1);
-        if (tid == 0) atomicOr(&S.err[env], kErrTimeout);
+    if (C.decide && !(res <= C.threshold)) {   // uniform over the CTA
+        for (int s = tid; s < M.V; s += SUB) {
+            const float w = X[s].w;
+            const float4 vh = VH[s];
+            const float p0 = Px[s], p1 = Py[s], p2 = Pz[s];
+            X[s] = w > 0.f ? make_float4(__fmaf_rn(h, vh.x, p0), __fmaf_rn(h, vh.y, p1), __fmaf_rn(h, vh.z, p2), w)
+                           : make_float4(p0, p1, p2, w);
+        }
+        if (!ring_sweep(X, M, segs, U, mbar, k, C.n_full, ed.alpha_d, S.alpha_v,
+                        C.lambda ? C.lambda + ed.loff : nullptr))
+            return false;
+        ++n_fallback;
     }
-    fence_before_sync();
-    __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWarmTmemCols)
-                     : "memory");
-    if (failed) return;
-    if (tid == 0 && C.fallbacks && n_fallback) C.fallbacks[env] += n_fallback;
+    return true;
+}
 
-    // Write back x and v = (x - x_prev) / h in vertex order; flag non-finite positions.
+// Writes x and v = (x - x_prev) / h back in vertex order (flagging non-finite
+// positions), then the contacts of the last substep (ascending vertex ids),
+// the observation, the reward and termination (Sec. III-B, Sec. IV).
+__device__ void warm_write_outputs(const SimDev& S, const MeshDev& M, const EnvDev& ed, int env, const float4* X,
+                                   const float* Px, const float* Py, const float* Pz, const unsigned* bits,
+                                   const double* s_tool, float* obs, float* reward, uint8_t* done) {
+    constexpr int SUB = kWarmThreads;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long stride = S.stride;
+    const float inv_h = S.inv_h;
     float* ox = S.x + ed.voff;
     float* ov = S.v + ed.voff;
     bool bad = false;
-    for (int i = tid; i < V; i += SUB) {
+    for (int i = tid; i < M.V; i += SUB) {
         const int s = M.slot_of[i];
         const float4 xi = X[s];
         ox[i] = xi.x;
@@ -864,9 +749,8 @@ __global__ void __launch_bounds__(kWarmThreads, 3)
         bad |= !(isfinite(xi.x) && isfinite(xi.y) && isfinite(xi.z));
     }
     if (bad) atomicOr(&S.err[env], kErrNonFinite);
-    // Contacts of the last substep (ascending vertex ids), observation, reward, termination.
     if (warp == 0) {
-        const int nwords = Vp / 32;
+        const int nwords = M.Vp / 32;
         int base = 0;
         for (int w0 = 0; w0 < nwords; w0 += 32) {
             unsigned word = (w0 + lane < nwords) ? bits[w0 + lane] : 0u;
@@ -917,23 +801,448 @@ __global__ void __launch_bounds__(kWarmThreads, 3)
     }
 }
 
-cudaError_t configure_warm_step(size_t smem) {
-    static size_t configured = 48 * 1024;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(warm_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+}  // namespace
+
+size_t warm_smem_bytes(int Vp, int ring_bytes, int n_seg, bool jit) {
+    return jit ? JitLayout(Vp, ring_bytes).total : WarmLayout(Vp, ring_bytes, n_seg).total;
+}
+
+__global__ void __launch_bounds__(kWarmThreads, 3)
+    warm_step_kernel(SimDev S, MlpDev net, SubstepCtl C, const int* __restrict__ env_list, int n_list,
+                     const float* __restrict__ actions, float* __restrict__ obs, float* __restrict__ reward,
+                     uint8_t* __restrict__ done) {
+    using namespace tc;
+    constexpr int SUB = kWarmThreads;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) uint64_t mbar[3];   // [0], [1] record ring; [2] tensor-core completion
+    __shared__ uint32_t tmem_slot;
+    __shared__ double s_tool[3];
+    __shared__ int s_resid;
+    if (int(blockIdx.x) >= n_list) return;
+    const int env = env_list[blockIdx.x];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const EnvDev ed = S.envs[env];
+    const MeshDev& M = S.meshes[ed.mesh];
+    const int V = M.V, Vp = M.Vp;
+    const long long stride = S.stride;
+    const WarmLayout L(Vp, M.ring_bytes, M.n_seg);
+    float4* X = reinterpret_cast<float4*>(sm + L.x);
+    unsigned char* U = sm + L.u;            // record ring, or weight tiles + hidden tile
+    unsigned char* Wt = U;
+    unsigned char* Ht = U + kMlpWeightBytes;
+    unsigned char* At = Ht;                 // the input tile is dead once layer 1 has read it
+    float* bias = reinterpret_cast<float*>(sm + L.bias);
+    int4* segs = reinterpret_cast<int4*>(sm + L.segs);
+    unsigned* bits = reinterpret_cast<unsigned*>(sm + L.bits);
+    float* Px = S.pg + ed.voff;
+    float* Py = Px + stride;
+    float* Pz = Py + stride;
+    float4* DX = C.scratch + ed.voff;       // corrections, slot order
+    float4* VH = C.vpred + ed.voff;         // predicted velocities, slot order
+    uint4* AR = C.arows + 2 * (ed.voff + 128ll * env);   // network input tiles, 4 KB each
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                     "r"(kWarmTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int i = tid; i < 144; i += SUB) bias[i] = net.bias[i];
+    for (int c = tid; c < M.n_seg; c += SUB) segs[c] = M.segs[c];
+    for (int w = tid; w < Vp / 32; w += SUB) bits[w] = 0u;
+    if (tid == 0) {
+        mbar_init(&mbar[0]);
+        mbar_init(&mbar[1]);
+        mbar_init(&mbar[2]);
+        update_tool(S, M, env, actions, s_tool);
+    }
+    warm_load_predict(S, M, ed, X, Px, Py, Pz, VH);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc64 = umma_idesc_bf16(128, 64), idesc16 = umma_idesc_bf16(128, 16);
+    const uint32_t aW1 = saddr(Wt), aW2 = aW1 + 2048, aW3 = aW1 + 10240, aA = saddr(At), aH = saddr(Ht);
+    const float cx = float(s_tool[0]), cy = float(s_tool[1]), cz = float(s_tool[2]);
+    const int n_tiles = (V + 127) / 128;
+    // TMEM lanes of this warp (a warp reaches the 32 lanes of its quarter) and
+    // the column half it reads back in the hidden-layer epilogues.
+    const int q4 = warp & 3, chalf = warp >> 2;
+    const uint32_t tlane = uint32_t(32 * q4) << 16;
+    const int erow = 32 * q4 + lane;
+    uint32_t phase = 0;   // tensor-core completions so far
+    uint32_t k = 0;       // record copies so far
+    bool failed = false;
+    int n_fallback = 0;
+
+    for (int sub = 0; sub < S.substeps && !failed; ++sub) {
+        const bool last = sub == S.substeps - 1;
+        if (tid == 0) s_resid = 0;
+        // -- the weight tiles into the shared region (the ring used it last)
+        for (int i = tid; i < kMlpWeightBytes / 16; i += SUB)
+            reinterpret_cast<uint4*>(Wt)[i] = reinterpret_cast<const uint4*>(net.wtiles)[i];
+        // -- features of every row at the predicted state, normalised and
+        //    rounded to BF16, written as the network's input tiles (the
+        //    tensor-core operand layout) to global scratch: one row per thread
+        for (int s = tid; s < n_tiles * 128; s += SUB) {
+            uint32_t pk[8];
+            warm_features(M, net, X, VH, s, cx, cy, cz, pk);
+            unsigned char* tile = reinterpret_cast<unsigned char*>(AR) + size_t(s >> 7) * 4096;
+            *reinterpret_cast<uint4*>(tile + tile_off(s & 127, 0, 2)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            *reinterpret_cast<uint4*>(tile + tile_off(s & 127, 1, 2)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+        __syncthreads();
+        // -- the network, one 128-row tile at a time (the next tile's input
+        //    is fetched into registers while the current tile runs)
+        uint4 a_next = AR[tid];
+        for (int t = 0; t < n_tiles; ++t) {
+            reinterpret_cast<uint4*>(At)[tid] = a_next;
+            if (t + 1 < n_tiles) a_next = AR[(t + 1) * 256 + tid];
+            fence_async_smem();
+            fence_before_sync();
+            __syncthreads();
+            fence_after_sync();
+            // Layer 1: D[0:64) = A (128 x 16) W1^T.
+            if (tid == 0) {
+                umma_bf16(tmem, umma_desc(aA, 128, 256), umma_desc(aW1, 128, 256), idesc64, 0);
+                umma_commit(&mbar[2]);
+            }
+            if (__syncthreads_or(!mbar_wait(&mbar[2], phase & 1))) {
+                failed = true;
+                break;
+            }
+            ++phase;
+            fence_after_sync();
+            // Epilogue 1: bias, ReLU, BF16 -> hidden tile (each warp: 32 rows x 32 columns).
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int c0 = 32 * chalf + 16 * c;
+                warm_hidden16(tmem + tlane + c0, bias, c0, Ht, erow);
+            }
+            fence_async_smem();
+            fence_before_sync();
+            __syncthreads();
+            fence_after_sync();
+            // Layer 2: D[64:128) = H1 (128 x 64) W2^T, four K = 16 steps.
+            if (tid == 0) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    umma_bf16(tmem + 64, umma_desc(aH + 256 * j, 128, 1024), umma_desc(aW2 + 256 * j, 128, 1024),
+                              idesc64, j);
+                umma_commit(&mbar[2]);
+            }
+            if (__syncthreads_or(!mbar_wait(&mbar[2], phase & 1))) {
+                failed = true;
+                break;
+            }
+            ++phase;
+            fence_after_sync();
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const int c0 = 32 * chalf + 16 * c;
+                warm_hidden16(tmem + tlane + 64 + c0, bias + 64, c0, Ht, erow);
+            }
+            fence_async_smem();
+            fence_before_sync();
+            __syncthreads();
+            fence_after_sync();
+            // Layer 3: D[0:16) = H2 (128 x 64) W3^T (rows 3..15 of W3 are zero).
+            if (tid == 0) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    umma_bf16(tmem, umma_desc(aH + 256 * j, 128, 1024), umma_desc(aW3 + 256 * j, 128, 1024), idesc16,
+                              j);
+                umma_commit(&mbar[2]);
+            }
+            if (__syncthreads_or(!mbar_wait(&mbar[2], phase & 1))) {
+                failed = true;
+                break;
+            }
+            ++phase;
+            fence_after_sync();
+            if (warp < 4) {
+                float v[16];
+                tmem_ld16(tmem + tlane, v);
+                const int s = t * 128 + erow;
+                if (s < V) {
+                    const float y0 = (v[0] + bias[128]) * net.out_std[0] + net.out_mean[0];
+                    const float y1 = (v[1] + bias[129]) * net.out_std[1] + net.out_mean[1];
+                    const float y2 = (v[2] + bias[130]) * net.out_std[2] + net.out_mean[2];
+                    DX[s] = make_float4(y0, y1, y2, 0.f);
+                }
+            }
+            fence_before_sync();
+            __syncthreads();   // the next tile overwrites the input tile and TMEM columns 0..63
+            fence_after_sync();
+        }
+        if (failed) break;
+        // -- corrections of the free vertices (the features above saw none of them)
+        for (int s = tid; s < V; s += SUB) {
+            float4 xi = X[s];
+            if (xi.w > 0.f) {
+                const float4 d = DX[s];
+                xi.x += d.x;
+                xi.y += d.y;
+                xi.z += d.z;
+                X[s] = xi;
+            }
+        }
+        // -- one iteration, the residual and the fallback to the full solve
+        if (!warm_iterate(S, M, ed, env, C, X, Px, Py, Pz, VH, segs, U, mbar, k, &s_resid, n_fallback)) {
+            failed = true;
+            break;
+        }
+        // -- collision, velocity update and the next prediction
+        warm_collide_advance(S, M, X, Px, Py, Pz, VH, bits, cx, cy, cz, last);
+        __syncthreads();
+    }
+    if (failed) {
+        // A bounded wait gave up: let the tensor-core commit in flight land
+        // (bounded), free TMEM, flag the env and leave its state.
+        mbar_wait(&mbar[2], phase & 1);
+        if (tid == 0) atomicOr(&S.err[env], kErrTimeout);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWarmTmemCols)
+                     : "memory");
+    if (failed) return;
+    if (tid == 0 && C.fallbacks && n_fallback) C.fallbacks[env] += n_fallback;
+    warm_write_outputs(S, M, ed, env, X, Px, Py, Pz, bits, s_tool, obs, reward, done);
+}
+
+// The just-in-time kernel. Warps 0-3 ("epilogue warps", one TMEM lane quarter
+// each) run the tensor-core chain of tile t: layer 1 into TMEM columns 0..63,
+// its epilogue into the hidden tile, layer 2 into columns 0..63 again, its
+// epilogue, layer 3 into the pending slot 64 + 16 (t mod 4). Warps 4-7
+// ("feature warps", one row each) meanwhile gather the features of tile t + 1
+// and write them into the input tile once layer 1 of tile t has read it.
+// The features of a tile read rows at most R = M.tile_reach tiles away, so the
+// output of tile p is added to the positions at the start of tile p + r with
+// r = max(R, 2) (every feature that reads its rows is built by then, and the
+// commit waited on in tile p + r - 1 covers layer 3 of tile p); r <= 4 slots.
+__global__ void __launch_bounds__(kWarmThreads, 3)
+    warm_step_jit_kernel(SimDev S, MlpDev net, SubstepCtl C, const int* __restrict__ env_list, int n_list,
+                         const float* __restrict__ actions, float* __restrict__ obs, float* __restrict__ reward,
+                         uint8_t* __restrict__ done) {
+    using namespace tc;
+    constexpr int SUB = kWarmThreads;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    // [0], [1] record ring; [2] tensor-core completions for the epilogue
+    // warps; [3] layer-1 completions for the feature warps (input tile free)
+    __shared__ __align__(8) uint64_t mbar[4];
+    __shared__ uint32_t tmem_slot;
+    __shared__ double s_tool[3];
+    __shared__ int s_resid;
+    if (int(blockIdx.x) >= n_list) return;
+    const int env = env_list[blockIdx.x];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const EnvDev ed = S.envs[env];
+    const MeshDev& M = S.meshes[ed.mesh];
+    const int V = M.V, Vp = M.Vp;
+    const long long stride = S.stride;
+    const JitLayout L(Vp, M.ring_bytes);
+    float4* X = reinterpret_cast<float4*>(sm + L.x);
+    unsigned char* U = sm + L.u;            // record ring, or weight, hidden and input tiles
+    unsigned char* Wt = U;
+    unsigned char* Ht = U + kMlpWeightBytes;
+    unsigned char* At = Ht + 16384;
+    float* bias = reinterpret_cast<float*>(sm + L.bias);
+    unsigned* bits = reinterpret_cast<unsigned*>(sm + L.bits);
+    float* Px = S.pg + ed.voff;
+    float* Py = Px + stride;
+    float* Pz = Py + stride;
+    float4* VH = C.vpred + ed.voff;         // predicted velocities, slot order
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                     "r"(kWarmTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int i = tid; i < 144; i += SUB) bias[i] = net.bias[i];
+    for (int w = tid; w < Vp / 32; w += SUB) bits[w] = 0u;
+    if (tid == 0) {
+        for (int b = 0; b < 4; ++b) mbar_init(&mbar[b]);
+        update_tool(S, M, env, actions, s_tool);
+    }
+    warm_load_predict(S, M, ed, X, Px, Py, Pz, VH);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t idesc64 = umma_idesc_bf16(128, 64), idesc16 = umma_idesc_bf16(128, 16);
+    const uint32_t aW1 = saddr(Wt), aW2 = aW1 + 2048, aW3 = aW1 + 10240, aA = saddr(At), aH = saddr(Ht);
+    const float cx = float(s_tool[0]), cy = float(s_tool[1]), cz = float(s_tool[2]);
+    const int n_tiles = (V + 127) / 128;
+    const int reach = M.tile_reach > 2 ? M.tile_reach : 2;
+    const bool epi = warp < 4;
+    const uint32_t tlane = uint32_t(32 * (warp & 3)) << 16;
+    const int erow = 32 * (warp & 3) + lane;   // epilogue warps: the tile row of this lane
+    const int frow = tid - 128;                // feature warps: the tile row of this thread
+    uint32_t ph_e = 0;    // completions of mbar[2] seen by the epilogue warps
+    uint32_t ph_a = 0;    // completions of mbar[3] seen by the feature warps
+    uint32_t k = 0;       // record copies so far
+    bool failed = false;
+    int n_fallback = 0;
+    const int4* segs = M.segs;
+
+    // network output of tile p (pending in its TMEM slot) added to the free vertices of its rows
+    auto apply_tile = [&](int p) {
+        float v[4];
+        tmem_ld4(tmem + tlane + 64 + 16 * (p & (kJitSlots - 1)), v);
+        warm_correct(X, net, bias, p * 128 + erow, V, v);
+    };
+
+    for (int sub = 0; sub < S.substeps && !failed; ++sub) {
+        const bool last = sub == S.substeps - 1;
+        if (tid == 0) s_resid = 0;
+        // -- the weight tiles into the shared region (the ring used it last),
+        //    and the input tile of tile 0
+        for (int i = tid; i < kMlpWeightBytes / 16; i += SUB)
+            reinterpret_cast<uint4*>(Wt)[i] = reinterpret_cast<const uint4*>(net.wtiles)[i];
+        if (!epi) {
+            uint32_t pk[8];
+            warm_features(M, net, X, VH, frow, cx, cy, cz, pk);
+            *reinterpret_cast<uint4*>(At + tile_off(frow, 0, 2)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            *reinterpret_cast<uint4*>(At + tile_off(frow, 1, 2)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+        fence_async_smem();
+        fence_before_sync();
+        __syncthreads();
+        fence_after_sync();
+        bool bad = false;
+        for (int t = 0; t < n_tiles; ++t) {
+            // Layer 1: D[0:64) = A (128 x 16) W1^T; its completion is signalled
+            // to both warp groups.
+            if (tid == 0) {
+                umma_bf16(tmem, umma_desc(aA, 128, 256), umma_desc(aW1, 128, 256), idesc64, 0);
+                umma_commit(&mbar[2]);
+                umma_commit(&mbar[3]);
+            }
+            if (epi) {
+                if (t >= reach) apply_tile(t - reach);
+                bad |= !mbar_wait(&mbar[2], ph_e & 1);
+                ++ph_e;
+                fence_after_sync();
+#pragma unroll
+                for (int c = 0; c < 4; ++c) warm_hidden16(tmem + tlane + 16 * c, bias, 16 * c, Ht, erow);
+                fence_async_smem();
+                fence_before_sync();
+                named_bar_sync(1, 128);
+                fence_after_sync();
+                // Layer 2: D[0:64) = H1 (128 x 64) W2^T, four K = 16 steps (layer 1's
+                // columns, read back above).
+                if (tid == 0) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        umma_bf16(tmem, umma_desc(aH + 256 * j, 128, 1024), umma_desc(aW2 + 256 * j, 128, 1024),
+                                  idesc64, j);
+                    umma_commit(&mbar[2]);
+                }
+                bad |= !mbar_wait(&mbar[2], ph_e & 1);
+                ++ph_e;
+                fence_after_sync();
+#pragma unroll
+                for (int c = 0; c < 4; ++c) warm_hidden16(tmem + tlane + 16 * c, bias + 64, 16 * c, Ht, erow);
+                fence_async_smem();
+                fence_before_sync();
+                named_bar_sync(1, 128);
+                fence_after_sync();
+                // Layer 3: the pending slot of tile t = H2 (128 x 64) W3^T (rows
+                // 3..15 of W3 are zero); read back r tiles later.
+                if (tid == 0) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        umma_bf16(tmem + 64 + 16 * (t & (kJitSlots - 1)), umma_desc(aH + 256 * j, 128, 1024),
+                                  umma_desc(aW3 + 256 * j, 128, 1024), idesc16, j);
+                }
+            } else {
+                uint32_t pk[8];
+                if (t + 1 < n_tiles) warm_features(M, net, X, VH, (t + 1) * 128 + frow, cx, cy, cz, pk);
+                // layer 1 of tile t has read the input tile once this completes
+                bad |= !mbar_wait(&mbar[3], ph_a & 1);
+                ++ph_a;
+                if (t + 1 < n_tiles) {
+                    *reinterpret_cast<uint4*>(At + tile_off(frow, 0, 2)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                    *reinterpret_cast<uint4*>(At + tile_off(frow, 1, 2)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+                    fence_async_smem();
+                }
+            }
+            fence_before_sync();
+            if (__syncthreads_or(bad)) {
+                failed = true;
+                break;
+            }
+            fence_after_sync();
+        }
+        if (failed) break;
+        // -- the outputs of the last tiles, once layer 3 of the last tile is done
+        if (tid == 0) umma_commit(&mbar[2]);
+        if (epi) {
+            bad |= !mbar_wait(&mbar[2], ph_e & 1);
+            ++ph_e;
+            fence_after_sync();
+            for (int p = n_tiles > reach ? n_tiles - reach : 0; p < n_tiles; ++p) apply_tile(p);
+        }
+        fence_before_sync();
+        if (__syncthreads_or(bad)) {
+            failed = true;
+            break;
+        }
+        fence_after_sync();
+        // -- one iteration, the residual and the fallback to the full solve
+        if (!warm_iterate(S, M, ed, env, C, X, Px, Py, Pz, VH, segs, U, mbar, k, &s_resid, n_fallback)) {
+            failed = true;
+            break;
+        }
+        // -- collision, velocity update and the next prediction
+        warm_collide_advance(S, M, X, Px, Py, Pz, VH, bits, cx, cy, cz, last);
+        __syncthreads();
+    }
+    if (failed) {
+        // A bounded wait gave up: one more commit covers every tensor-core
+        // operation issued so far; let it land (bounded), free TMEM, flag the
+        // env and leave its state.
+        if (tid == 0) umma_commit(&mbar[2]);
+        if (epi) mbar_wait(&mbar[2], ph_e & 1);
+        if (tid == 0) atomicOr(&S.err[env], kErrTimeout);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWarmTmemCols)
+                     : "memory");
+    if (failed) return;
+    if (tid == 0 && C.fallbacks && n_fallback) C.fallbacks[env] += n_fallback;
+    warm_write_outputs(S, M, ed, env, X, Px, Py, Pz, bits, s_tool, obs, reward, done);
+}
+
+cudaError_t configure_warm_step(size_t smem, bool jit) {
+    static size_t configured[2] = {48 * 1024, 48 * 1024};
+    if (smem > configured[jit]) {
+        cudaError_t e = jit ? cudaFuncSetAttribute(warm_step_jit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   int(smem))
+                            : cudaFuncSetAttribute(warm_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   int(smem));
         if (e != cudaSuccess) return e;
-        configured = smem;
+        configured[jit] = smem;
     }
     return cudaSuccess;
 }
 
 cudaError_t launch_warm_step(const SimDev& S, const MlpDev& net, const SubstepCtl& C, const int* env_list,
-                             int n_list, size_t smem, const float* actions, float* obs, float* reward, uint8_t* done,
-                             cudaStream_t st) {
+                             int n_list, size_t smem, bool jit, const float* actions, float* obs, float* reward,
+                             uint8_t* done, cudaStream_t st) {
     if (n_list <= 0) return cudaSuccess;
-    const cudaError_t ce = configure_warm_step(smem);
+    const cudaError_t ce = configure_warm_step(smem, jit);
     if (ce != cudaSuccess) return ce;
-    warm_step_kernel<<<n_list, kWarmThreads, smem, st>>>(S, net, C, env_list, n_list, actions, obs, reward, done);
+    if (jit)
+        warm_step_jit_kernel<<<n_list, kWarmThreads, smem, st>>>(S, net, C, env_list, n_list, actions, obs, reward,
+                                                                 done);
+    else
+        warm_step_kernel<<<n_list, kWarmThreads, smem, st>>>(S, net, C, env_list, n_list, actions, obs, reward, done);
     return cudaGetLastError();
 }
 

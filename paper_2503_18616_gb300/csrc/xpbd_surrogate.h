@@ -19,6 +19,8 @@ struct SubstepCtl {
     const float4* dx;       // [stride] network corrections (surrogate mode)
     float4* target;         // [stride] solve minus prediction (record mode; may be null)
     float threshold;        // residual above which the surrogate substep falls back
+    int check;              // evaluate the residual (a finite threshold, or a residual output)
+    int decide;             // fall back unless residual <= threshold (a finite threshold; +inf never falls back)
     int n_full;             // iterations of the full solve
     float* lambda;          // multipliers of the full solve (per env at EnvDev::loff)
     int* fallbacks;         // [n_env] counters (may be null)
@@ -43,10 +45,15 @@ cudaError_t launch_substep(const SimDev& S, const SubstepCtl& C, const int* env_
 // ignored.
 constexpr int kWarmThreads = 256;
 constexpr int kWarmMaxDegree = 24;   // 1-ring size the fused kernel gathers (three index chunks)
-size_t warm_smem_bytes(int Vp, int ring_bytes, int n_seg);
-cudaError_t configure_warm_step(size_t smem);   // shared-memory limit, ahead of stream capture
+// jit: the kernel that builds each tile's input just in time and keeps the
+// network outputs in TMEM until applied (meshes with tile_reach <= 4; it does
+// not use C.scratch or C.arows); else the kernel that stages both in global
+// memory.
+constexpr int kWarmJitMaxReach = 4;
+size_t warm_smem_bytes(int Vp, int ring_bytes, int n_seg, bool jit);
+cudaError_t configure_warm_step(size_t smem, bool jit);   // shared-memory limit, ahead of stream capture
 cudaError_t launch_warm_step(const SimDev& S, const MlpDev& net, const SubstepCtl& C, const int* env_list,
-                             int n_list, size_t smem, const float* actions, float* obs, float* reward, uint8_t* done,
-                             cudaStream_t st);
+                             int n_list, size_t smem, bool jit, const float* actions, float* obs, float* reward,
+                             uint8_t* done, cudaStream_t st);
 
 }  // namespace ffsrl

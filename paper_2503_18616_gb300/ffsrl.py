@@ -70,6 +70,7 @@ SCHED_FORCE, SCHED_NO_PERMUTE, SCHED_NO_RING, SCHED_ENVS2, SCHED_ENVS4 = 1, 2, 4
 SCHED_SURROGATE_PIPELINE = 32
 SCHED_NO_CLUSTER = 64
 SCHED_FOUR_CTAS = 128
+SCHED_WARM_STAGED = 256
 
 
 class ffsrl_info(ctypes.Structure):
@@ -412,7 +413,7 @@ class Sim:
                                             float(threshold), int(n_full), _dptr(fallbacks), _dptr(residual)))
         return obs, reward, done
 
-    def set_surrogate_envs(self, mask, threshold: float = 1e30, n_full: int = 10, fallbacks=None) -> None:
+    def set_surrogate_envs(self, mask, threshold: float = float("inf"), n_full: int = 10, fallbacks=None) -> None:
         """Mixed rollout: envs with a non-zero mask byte take the warm-start
         step inside step()/step_host(); mask None switches back to plain."""
         if mask is None:

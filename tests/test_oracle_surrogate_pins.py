@@ -202,3 +202,22 @@ def test_recorded_residuals_are_the_checked_ones():
     _, _, _, fb = e2.step_surrogate(net, threshold=thr, n_full=5, residuals=r2)
     assert r2[0] == r[0]                        # the same first substep
     assert fb == int(np.sum(r2 > thr)) and 0 < fb < p["substeps"]
+
+
+def test_threshold_reading_for_nan_and_infinity():
+    """A threshold of +inf never falls back; a finite one falls back unless the
+    residual is at most it, so a network that returns NaN makes every substep
+    fall back to the full solve (which is then the plain full-solve step)."""
+    p = oracle.mlp_init(0)
+    p["b3"] = np.array([np.nan, 0.0, 0.0])
+    net = oracle.Net.from_params(p)
+    m, prm, e1 = _env(iterations=10)
+    _, _, e2 = _env(iterations=1)
+    for _ in range(2):
+        e1.step()
+        _, _, _, fb = e2.step_surrogate(net, threshold=1e9, n_full=10)
+        assert fb == prm["substeps"]
+    assert np.array_equal(e1.state()[0], e2.state()[0])
+    _, _, e3 = _env(iterations=1)
+    _, _, _, fb = e3.step_surrogate(net, threshold=np.inf, n_full=10)
+    assert fb == 0 and np.isnan(e3.state()[0]).any()

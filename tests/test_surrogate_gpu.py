@@ -233,3 +233,34 @@ def test_fallback_decided_per_env_and_substep():
         assert int(fb[e]) == fbs[e], (e, int(fb[e]), fbs[e])
         assert np.max(np.abs(x[e * V:(e + 1) * V] - oe.state()[0])) <= POS_TOL * ext, e
         assert np.array_equal(tool[e], oe.state()[2])
+
+
+@pytest.mark.parametrize("shape", [(9, 9, 5), (17, 17, 9)])
+def test_just_in_time_and_staged_kernels_give_the_same_bits(shape):
+    """The fused warm-start step has two kernels: one builds each tile's input
+    just in time and keeps the network outputs in TMEM until no later tile's
+    features read their rows, the other stages inputs and corrections in
+    global memory. Same operations, same rounding: equal bits, with and
+    without fallbacks (threshold between the substeps' residuals)."""
+    from paper_2503_18616_gb300 import ffsrl
+    m = grid(shape)
+    p = inputs.default_params(radius=4e-3)
+    n_env, steps = 3, 4
+    params, norm, _ = _case_network("random_network")
+    out = {}
+    for name, flags in (("jit", 0), ("staged", ffsrl.SCHED_WARM_STAGED)):
+        sim = make_sim([m], p, n_env, seed=14, schedule_flags=flags)
+        _install(sim, params, norm)
+        fb = torch.zeros(n_env, dtype=torch.int32, device="cuda")
+        res = torch.zeros(n_env, dtype=torch.float32, device="cuda")
+        for k in range(steps):
+            # the first steps without fallback, then a threshold that some substeps exceed
+            thr = float("inf") if k < 2 else 8e-3
+            obs, rew, _ = sim.step_surrogate(thr, 10, fallbacks=fb, residual=res)
+        sim.sync()
+        x, v, tool = sim.get_state()
+        out[name] = (x.cpu().numpy(), v.cpu().numpy(), obs.cpu().numpy(), rew.cpu().numpy(), fb.cpu().numpy(),
+                     res.cpu().numpy())
+        sim.close()
+    for a, b in zip(out["jit"], out["staged"]):
+        assert np.array_equal(a, b)

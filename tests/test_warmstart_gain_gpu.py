@@ -51,7 +51,7 @@ def test_trained_warm_start_beats_the_plain_step_at_one_iteration():
     ws = make_sim([m], p, n_env, seed=seed)
     ws.set_network(tr["params"], *tr["norm"])
     for _ in range(N):
-        ws.step_surrogate(1e30, 10)
+        ws.step_surrogate(float("inf"), 10)
     ws.sync()
     xw, _, _ = gpu_positions(ws)
     ps = make_sim([m], p, n_env, seed=seed)
