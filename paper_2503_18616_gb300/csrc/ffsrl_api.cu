@@ -286,22 +286,25 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, const Schedule& sc, MeshDev& d)
         FFSRL_CUDA(s->upload(&d_nb, nb.data(), nb.size()));
         d.nbr_off = d_off;
         d.nbr = d_nb;
-        // the same adjacency indexed by shared-memory slot, in 16-byte chunks
-        // of 8 neighbour slots (fused warm-start step)
-        std::vector<int> hdr(m.V);
-        std::vector<uint16_t> chunks;
+        // the same adjacency indexed by shared-memory slot (fused warm-start
+        // step): one 48-byte record per slot, its degree and neighbour slots
         std::vector<float4> rs(m.V);
         int max_deg = 0;
         for (int q = 0; q < m.V; ++q) {
             const int i = sc.vert_of[q];
-            const int deg = off[i + 1] - off[i];
-            max_deg = std::max(max_deg, deg);
-            hdr[q] = int(chunks.size() / 8) << 5 | std::min(deg, 31);
-            for (int k = off[i]; k < off[i + 1]; ++k) chunks.push_back(sc.slot_of[nb[k]]);
-            while (chunks.size() % 8) chunks.push_back(0);
+            max_deg = std::max(max_deg, off[i + 1] - off[i]);
             rs[q] = rw[i];
         }
-        if (chunks.empty()) chunks.resize(8, 0);
+        std::vector<uint16_t> recs;
+        if (max_deg <= kWarmMaxDegree) {
+            recs.assign(24 * size_t(m.V), 0);
+            for (int q = 0; q < m.V; ++q) {
+                const int i = sc.vert_of[q];
+                uint16_t* r = &recs[24 * size_t(q)];
+                r[0] = uint16_t(off[i + 1] - off[i]);
+                for (int k = off[i]; k < off[i + 1]; ++k) r[1 + k - off[i]] = sc.slot_of[nb[k]];
+            }
+        }
         // how many 128-row network tiles apart a slot and its 1-ring neighbours lie
         int reach = 0;
         for (int q = 0; q < m.V; ++q) {
@@ -309,11 +312,10 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, const Schedule& sc, MeshDev& d)
             for (int k = off[i]; k < off[i + 1]; ++k)
                 reach = std::max(reach, std::abs(q / 128 - int(sc.slot_of[nb[k]]) / 128));
         }
-        int* d_hdr;
-        uint4* d_ch;
+        uint4* d_nr = nullptr;
         float4* d_rs;
-        FFSRL_CUDA(s->upload(&d_hdr, hdr.data(), hdr.size()));
-        FFSRL_CUDA(s->upload(&d_ch, reinterpret_cast<const uint4*>(chunks.data()), chunks.size() / 8));
+        if (!recs.empty())
+            FFSRL_CUDA(s->upload(&d_nr, reinterpret_cast<const uint4*>(recs.data()), recs.size() / 8));
         FFSRL_CUDA(s->upload(&d_rs, rs.data(), rs.size()));
         // the records without segment padding (order-free residual sweeps)
         std::vector<uint2> er;
@@ -352,8 +354,7 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, const Schedule& sc, MeshDev& d)
         float* d_invn;
         FFSRL_CUDA(s->upload(&d_invn, inv_n.data(), inv_n.size()));
         d.inv_ncons = d_invn;
-        d.snbr_hdr = d_hdr;
-        d.snbr_ch = d_ch;
+        d.snbr = d_nr;
         d.max_deg = max_deg;
         d.tile_reach = reach;
         d.rest_s = d_rs;

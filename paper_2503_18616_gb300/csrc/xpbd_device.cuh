@@ -36,11 +36,11 @@ struct MeshDev {
     const int* top;                   // [n_top] top-face vertex ids
     const int* nbr_off;               // [V + 1] 1-ring of each vertex (vertex order, CSR)
     const int* nbr;                   // [2E]
-    // 1-ring of each slot in slot terms (same neighbour order as nbr): slot s
-    // owns 16-byte chunks of 8 neighbour slots (uint16) from chunk
-    // snbr_hdr[s] >> 5 on; its degree is snbr_hdr[s] & 31 (at most 24).
-    const int* snbr_hdr;              // [V]
-    const uint4* snbr_ch;
+    // 1-ring of each slot in slot terms (same neighbour order as nbr): the
+    // 48-byte record of slot s, snbr[3 s .. 3 s + 2], holds 24 uint16 fields:
+    // its degree, then its neighbour slots (at most 23; a mesh with a larger
+    // 1-ring has no records: snbr is null).
+    const uint4* snbr;
     const float4* rest_s;             // [V] rest position and inverse mass (slot order)
     int max_deg;                      // largest vertex degree
     int tile_reach;                   // largest |s / 128 - j / 128| over slots s and their 1-ring slots j

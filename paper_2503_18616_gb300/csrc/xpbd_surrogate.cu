@@ -531,10 +531,33 @@ __device__ void warm_load_predict(const SimDev& S, const MeshDev& M, const EnvDe
     }
 }
 
+// The per-row tables the features of slot s read from global memory (its
+// 1-ring header and neighbour slots, its rest position), loaded ahead of use.
+struct FeatRow {
+    uint4 c0, c1, c2;   // the slot's 1-ring record: degree, then neighbour slots (uint16 fields)
+    float4 rest;
+};
+
+__device__ __forceinline__ FeatRow warm_feat_fetch(const MeshDev& M, int s) {
+    FeatRow r;
+    const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
+    r.c0 = r.c1 = r.c2 = zero;
+    r.rest = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (s < M.V) {
+        const uint4* rec = M.snbr + 3 * s;
+        r.c0 = __ldg(rec);
+        r.c1 = __ldg(rec + 1);
+        r.c2 = __ldg(rec + 2);
+        r.rest = __ldg(M.rest_s + s);
+    }
+    return r;
+}
+
 // Features of slot s (15 values, normalised, the 16th zero) packed as BF16
-// pairs; rows s >= V give zeros.
-__device__ __forceinline__ void warm_features(const MeshDev& M, const MlpDev& net, const float4* X, const float4* VH,
-                                              int s, float cx, float cy, float cz, uint32_t* pk) {
+// pairs from its tables; rows s >= V give zeros.
+__device__ __forceinline__ void warm_features_row(const MeshDev& M, const MlpDev& net, const float4* X,
+                                                  const float4* VH, int s, const FeatRow& r, float cx, float cy,
+                                                  float cz, uint32_t* pk) {
     using namespace tc;
     float f[16];
 #pragma unroll
@@ -542,23 +565,21 @@ __device__ __forceinline__ void warm_features(const MeshDev& M, const MlpDev& ne
     if (s < M.V) {
         const float4 xs = X[s];
         const float4 vs = VH[s];
-        const int hd = M.snbr_hdr[s], deg = hd & 31;
-        const uint4* ch = M.snbr_ch + (hd >> 5);
-        const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
-        const uint4 c0 = ch[0], c1 = deg > 8 ? ch[1] : zero, c2 = deg > 16 ? ch[2] : zero;
-        const uint32_t w[12] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w, c2.x, c2.y, c2.z, c2.w};
+        const uint32_t w[12] = {r.c0.x, r.c0.y, r.c0.z, r.c0.w, r.c1.x, r.c1.y,
+                                r.c1.z, r.c1.w, r.c2.x, r.c2.y, r.c2.z, r.c2.w};
+        const int deg = int(w[0] & 0xFFFF);
         float m0 = 0.f, m1 = 0.f, m2 = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f;
 #pragma unroll
         for (int q = 0; q < kWarmMaxDegree; ++q) {
             if (q < deg) {
-                const int j = (w[q >> 1] >> (16 * (q & 1))) & 0xFFFF;
+                const int j = (w[(q + 1) >> 1] >> (16 * ((q + 1) & 1))) & 0xFFFF;
                 const float4 xj = X[j];
                 const float4 vj = VH[j];
                 m0 += xj.x; m1 += xj.y; m2 += xj.z;
                 n0 += vj.x; n1 += vj.y; n2 += vj.z;
             }
         }
-        const float4 rs = M.rest_s[s];
+        const float4 rs = r.rest;
         f[0] = xs.x - rs.x; f[1] = xs.y - rs.y; f[2] = xs.z - rs.z;
         f[3] = vs.x; f[4] = vs.y; f[5] = vs.z;
         if (deg > 0) {
@@ -571,7 +592,12 @@ __device__ __forceinline__ void warm_features(const MeshDev& M, const MlpDev& ne
         for (int q = 0; q < 15; ++q) f[q] = (f[q] - net.in_mean[q]) * net.in_inv_std[q];
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) pk[q] = bf16_bits(f[2 * q]) | (bf16_bits(f[2 * q + 1]) << 16);
+    for (int q = 0; q < 8; ++q) pk[q] = pack_bf16x2(f[2 * q], f[2 * q + 1]);
+}
+
+__device__ __forceinline__ void warm_features(const MeshDev& M, const MlpDev& net, const float4* X, const float4* VH,
+                                              int s, float cx, float cy, float cz, uint32_t* pk) {
+    warm_features_row(M, net, X, VH, s, warm_feat_fetch(M, s), cx, cy, cz, pk);
 }
 
 // Bias, ReLU and BF16 rounding of 16 accumulator columns c0 .. c0+15 of this
@@ -584,10 +610,29 @@ __device__ __forceinline__ void warm_hidden16(uint32_t taddr, const float* bias,
     uint32_t pk[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-        pk[q] = bf16_bits(fmaxf(v[2 * q] + bias[c0 + 2 * q], 0.f)) |
-                (bf16_bits(fmaxf(v[2 * q + 1] + bias[c0 + 2 * q + 1], 0.f)) << 16);
+        pk[q] = pack_bf16x2(fmaxf(v[2 * q] + bias[c0 + 2 * q], 0.f), fmaxf(v[2 * q + 1] + bias[c0 + 2 * q + 1], 0.f));
     *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8, 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
     *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8 + 1, 8)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+}
+
+// The same for 32 columns c0 .. c0+31 (one TMEM load).
+__device__ __forceinline__ void warm_hidden32(uint32_t taddr, const float* bias, int c0, unsigned char* Ht,
+                                              int erow) {
+    using namespace tc;
+    float v[32];
+    tmem_ld32(taddr, v);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t pk[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int c = 16 * h + 2 * q;
+            pk[q] = pack_bf16x2(fmaxf(v[c] + bias[c0 + c], 0.f), fmaxf(v[c + 1] + bias[c0 + c + 1], 0.f));
+        }
+        *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8 + 2 * h, 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8 + 2 * h + 1, 8)) =
+            make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    }
 }
 
 // The de-normalised network output (3 accumulator columns from v) of slot s
@@ -1102,11 +1147,13 @@ __global__ void __launch_bounds__(kWarmThreads, 3)
         //    and the input tile of tile 0
         for (int i = tid; i < kMlpWeightBytes / 16; i += SUB)
             reinterpret_cast<uint4*>(Wt)[i] = reinterpret_cast<const uint4*>(net.wtiles)[i];
+        FeatRow fr{};   // feature warps: the tables of their row of the next tile, fetched a tile ahead
         if (!epi) {
             uint32_t pk[8];
             warm_features(M, net, X, VH, frow, cx, cy, cz, pk);
             *reinterpret_cast<uint4*>(At + tile_off(frow, 0, 2)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             *reinterpret_cast<uint4*>(At + tile_off(frow, 1, 2)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            fr = warm_feat_fetch(M, 128 + frow);
         }
         fence_async_smem();
         fence_before_sync();
@@ -1127,7 +1174,7 @@ __global__ void __launch_bounds__(kWarmThreads, 3)
                 ++ph_e;
                 fence_after_sync();
 #pragma unroll
-                for (int c = 0; c < 4; ++c) warm_hidden16(tmem + tlane + 16 * c, bias, 16 * c, Ht, erow);
+                for (int c = 0; c < 2; ++c) warm_hidden32(tmem + tlane + 32 * c, bias, 32 * c, Ht, erow);
                 fence_async_smem();
                 fence_before_sync();
                 named_bar_sync(1, 128);
@@ -1145,7 +1192,7 @@ __global__ void __launch_bounds__(kWarmThreads, 3)
                 ++ph_e;
                 fence_after_sync();
 #pragma unroll
-                for (int c = 0; c < 4; ++c) warm_hidden16(tmem + tlane + 16 * c, bias + 64, 16 * c, Ht, erow);
+                for (int c = 0; c < 2; ++c) warm_hidden32(tmem + tlane + 32 * c, bias + 64, 32 * c, Ht, erow);
                 fence_async_smem();
                 fence_before_sync();
                 named_bar_sync(1, 128);
@@ -1160,7 +1207,10 @@ __global__ void __launch_bounds__(kWarmThreads, 3)
                 }
             } else {
                 uint32_t pk[8];
-                if (t + 1 < n_tiles) warm_features(M, net, X, VH, (t + 1) * 128 + frow, cx, cy, cz, pk);
+                if (t + 1 < n_tiles) {
+                    warm_features_row(M, net, X, VH, (t + 1) * 128 + frow, fr, cx, cy, cz, pk);
+                    fr = warm_feat_fetch(M, (t + 2) * 128 + frow);
+                }
                 // layer 1 of tile t has read the input tile once this completes
                 bad |= !mbar_wait(&mbar[3], ph_a & 1);
                 ++ph_a;

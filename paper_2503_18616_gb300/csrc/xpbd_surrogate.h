@@ -44,7 +44,7 @@ cudaError_t launch_substep(const SimDev& S, const SubstepCtl& C, const int* env_
 // tiles start at row voff_e + 128 e); C.mode, C.last, C.dx and C.target are
 // ignored.
 constexpr int kWarmThreads = 256;
-constexpr int kWarmMaxDegree = 24;   // 1-ring size the fused kernel gathers (three index chunks)
+constexpr int kWarmMaxDegree = 23;   // 1-ring size the fused kernel gathers (a 48-byte record per slot)
 // jit: the kernel that builds each tile's input just in time and keeps the
 // network outputs in TMEM until applied (meshes with tile_reach <= 4; it does
 // not use C.scratch or C.arows); else the kernel that stages both in global
