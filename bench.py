@@ -253,9 +253,14 @@ def ncu_traffic(profile: str):
         return None
 
 
-def oracle_rate(batch, seconds: float, seed: int, envs, max_steps=None):
+CHECK_EVERY = 10   # steps between the accuracy leg's checkpoints
+
+
+def oracle_rate(batch, seconds: float, seed: int, envs, max_steps=None, checkpoints=None):
     """FP64 oracle env-steps/s on one host thread over a bounded sample; also
-    returns the oracle envs after the sampled steps for the accuracy check."""
+    returns the oracle envs after the sampled steps for the accuracy check.
+    With a dict `checkpoints`, the positions of every env at every
+    CHECK_EVERY-th step are kept in it ({step: [positions per env]})."""
     import oracle
     meshes = {}
     oes = []
@@ -276,8 +281,15 @@ def oracle_rate(batch, seconds: float, seed: int, envs, max_steps=None):
     for e, oe in zip(envs, oes):   # restart from reset so all envs run exactly n steps
         oe.reset(seed, int(batch.env_ids[e]))
     t0 = time.perf_counter()
-    for oe in oes:
-        oe.run(n, want_obs=False)
+    if checkpoints is None:
+        for oe in oes:
+            oe.run(n, want_obs=False)
+    else:
+        for k in range(0, n, CHECK_EVERY):
+            m = min(CHECK_EVERY, n - k)
+            for oe in oes:
+                oe.run(m, want_obs=False)
+            checkpoints[k + m] = [oe.state()[0] for oe in oes]
     dt = time.perf_counter() - t0
     return len(oes) * n / dt, n, dt, oes
 
@@ -1017,14 +1029,27 @@ def run_ours(args):
             else:
                 vs = [c[0] for c in counts]
                 sample_envs = (int(np.argmin(vs)), int(np.argmax(vs)))
+            ckpt = {}
             rate, n_steps, dt, oes = oracle_rate(batch, args.cpu_seconds, seed, sample_envs,
-                                                 max_steps=batch.steps)
+                                                 max_steps=batch.steps, checkpoints=ckpt)
+            # the GPU replays the same envs from the same reset; positions are
+            # compared at every checkpoint (first step over the tolerance)
+            off = np.concatenate([[0], np.cumsum([c[0] for c in counts])])
             sim.reset(seed)
-            for _ in range(n_steps):
-                sim.step_into(None, None, None, None)
+            done_steps, first_over = 0, [None] * len(sample_envs)
+            for step in sorted(ckpt):
+                for _ in range(step - done_steps):
+                    sim.step_into(None, None, None, None)
+                done_steps = step
+                xs, _, _ = sim.get_state()
+                xs = xs.cpu().numpy()
+                for j, (e, oe) in enumerate(zip(sample_envs, oes)):
+                    err_j = float(np.max(np.abs(xs[off[e]:off[e + 1]].astype(np.float64) - ckpt[step][j])) /
+                                  oe.mesh.extent)
+                    if first_over[j] is None and err_j > POS_TOL:
+                        first_over[j] = step
             x, _, _ = sim.get_state()
             x = x.cpu().numpy().astype(np.float64)
-            off = np.concatenate([[0], np.cumsum([c[0] for c in counts])])
             errs, floors = [], []
             import oracle
             for e, oe in zip(sample_envs, oes):
@@ -1040,6 +1065,7 @@ def run_ours(args):
                    "fp32_oracle_err_over_extent": floors, "envs": list(sample_envs),
                    "verts": [counts[e][0] for e in sample_envs], "steps": n_steps,
                    "within_tolerance": max(errs) <= POS_TOL,
+                   "first_checkpoint_over_tolerance": first_over, "checkpoint_every": CHECK_EVERY,
                    "workload_steps": batch.steps,
                    "within_fp32_floor": all(g <= max(POS_TOL, 2 * f) for g, f in zip(errs, floors)),
                    "fp32_floor_rule": "error <= max(tolerance, 2 x the oracle's own float32 build's error)"}

@@ -172,6 +172,32 @@ __device__ __forceinline__ float seg_tri_closest(float3 q0, float3 q1, float3 a,
     return best;
 }
 
+// Whether the face (a, b, c) lies certainly farther than r from segment
+// q0-q1: the distance from the face's centroid g to the segment, less the
+// radius of the face's bounding sphere about g, is at least r plus a margin
+// of 1e-3 r + 1e-5 x (the largest coordinate of g, q0 and q1). The second
+// term is about a hundred times the rounding error of these sums and of the
+// exact closest-point distance (a few ulp of the coordinates), so a face this
+// test rejects is one the exact test below would leave alone: skipping it
+// does not change any bit.
+__device__ __forceinline__ bool face_out_of_reach(float3 a, float3 b, float3 c, float3 q0, float3 q1, float r) {
+    const float3 g = make_float3((a.x + b.x + c.x) * (1.f / 3.f), (a.y + b.y + c.y) * (1.f / 3.f),
+                                 (a.z + b.z + c.z) * (1.f / 3.f));
+    const float3 ga = make_float3(a.x - g.x, a.y - g.y, a.z - g.z), gb = make_float3(b.x - g.x, b.y - g.y, b.z - g.z),
+                 gc = make_float3(c.x - g.x, c.y - g.y, c.z - g.z);
+    const float rho2 = fmaxf(fmaxf(ga.x * ga.x + ga.y * ga.y + ga.z * ga.z, gb.x * gb.x + gb.y * gb.y + gb.z * gb.z),
+                             gc.x * gc.x + gc.y * gc.y + gc.z * gc.z);
+    const float3 ax = make_float3(q1.x - q0.x, q1.y - q0.y, q1.z - q0.z), rg = make_float3(g.x - q0.x, g.y - q0.y, g.z - q0.z);
+    const float la2 = ax.x * ax.x + ax.y * ax.y + ax.z * ax.z;
+    float t = la2 > 0.f ? (rg.x * ax.x + rg.y * ax.y + rg.z * ax.z) / la2 : 0.f;
+    t = t < 0.f ? 0.f : (t > 1.f ? 1.f : t);
+    const float3 dv = make_float3(rg.x - t * ax.x, rg.y - t * ax.y, rg.z - t * ax.z);
+    const float d = sqrtf(dv.x * dv.x + dv.y * dv.y + dv.z * dv.z);
+    const float scale = fmaxf(fmaxf(fabsf(g.x), fabsf(g.y)), fabsf(g.z)) + fmaxf(fmaxf(fabsf(q0.x), fabsf(q0.y)), fabsf(q0.z)) +
+                        fmaxf(fmaxf(fabsf(q1.x), fabsf(q1.y)), fabsf(q1.z));
+    return d - sqrtf(rho2) >= r * 1.001f + 1e-5f * scale;
+}
+
 // Pushes one surface face out of the three capsules (shaft, then clamps).
 // X is the env's position array (slot order). With `bits` set (last substep)
 // the free vertices a push moves are marked in the contact bits (vertex ids).
@@ -182,6 +208,7 @@ __device__ __forceinline__ void grasper_face(float4* X, uint4 rec, const Capsule
         float4 xa = X[ia], xb = X[ib], xc = X[ic];
         const float3 a = make_float3(xa.x, xa.y, xa.z), b = make_float3(xb.x, xb.y, xb.z), c = make_float3(xc.x, xc.y, xc.z);
         const float3 q0 = make_float3(K.a[k][0], K.a[k][1], K.a[k][2]), q1 = make_float3(K.b[k][0], K.b[k][1], K.b[k][2]);
+        if (face_out_of_reach(a, b, c, q0, q1, K.r[k])) continue;
         float w[3];
         float3 q;
         const float dist = seg_tri_closest(q0, q1, a, b, c, w, q);

@@ -463,12 +463,18 @@ def test_uneven_1024_env_batch_sampled():
     """The uneven-batching configuration: 1024 envs, vertex counts log-uniform in
     [500, 20000] (37 block sizes), per-env edge compliance, all size classes
     launched concurrently (the largest meshes on 2-CTA clusters); the
-    smallest, a middle and the largest env are checked against the oracle."""
+    smallest, a middle and the largest env are checked against the FP64
+    oracle after 100 steps. An env whose error exceeds the 1e-5 x extent
+    tolerance must stay within twice what the oracle's own float32 build
+    deviates from its float64 build over the same steps (the float32 rounding
+    floor of a trajectory that buckles under the tool); the smallest and the
+    middle env must meet the tolerance outright."""
+    import oracle
     shapes, env_mesh = inputs.uneven_batch(1024, 500, 20000, seed=12345)
     meshes = [grid(s) for s in shapes]
     alpha = inputs.compliance_draws(1024, 1e-7, 1e-5, seed=12345)
     p = P()
-    steps = 30
+    steps = 100
     sim = make_sim(meshes, p, 1024, env_mesh=env_mesh, env_compliance=alpha, seed=8)
     assert sim.n_groups >= 2 and sim.resident_envs == 1024   # every env on chip
     vs = np.array([len(meshes[m][0]) for m in env_mesh])
@@ -478,7 +484,21 @@ def test_uneven_1024_env_batch_sampled():
         sim.step()
     for oe in oenvs.values():
         oe.run(steps, want_obs=False)
-    compare_states(sim, oenvs, meshes, 1024, env_mesh=env_mesh, label="uneven 1024")
+    x, _, _ = gpu_positions(sim)
+    off = packed_offsets(meshes, 1024, env_mesh)
+    for rank, e in enumerate(sample):
+        oe = oenvs[e]
+        ox = oe.state()[0]
+        ext = oe.mesh.extent
+        err = float(np.max(np.abs(x[off[e]:off[e + 1]] - ox)) / ext)
+        if err <= POS_TOL:
+            continue
+        assert rank == 2, f"env {e} ({vs[e]} vertices): {err:.3e} x extent"
+        o32 = oracle.Env(oracle.Mesh(*meshes[env_mesh[e]], precision="f32"), dict(p, alpha_d=float(alpha[e])))
+        o32.reset(8, e)
+        o32.run(steps, want_obs=False)
+        floor = float(np.max(np.abs(o32.state()[0] - ox)) / ext)
+        assert err <= 2 * floor, f"env {e} ({vs[e]} vertices): {err:.3e} vs float32 floor {floor:.3e}"
 
 
 def test_largest_supported_mesh_and_the_size_limit():
