@@ -725,9 +725,9 @@ def warm_start_comparison(args, sim, batch, seed, plain_rate, peaks):
     fallback at twice the full solve's median residual; its largest vertex
     error after N steps from reset is measured against the FP64 oracle's
     10-iteration full solve on the first and last env, as is the plain step's
-    with 1, 2, 3, 5, 7, 10 iterations (ascending, stopping at the first that
-    is at least as accurate as the warm-start: the cheapest plain setting at
-    equal error)."""
+    with 1, 2, 3, 5, 7, 8, 9, 10 iterations (ascending, stopping at the first
+    that is at least as accurate as the warm-start: the cheapest plain
+    setting at equal error)."""
     import torch
     from paper_2503_18616_gb300 import ffsrl, surrogate
     n_env, params, n_full = batch.n_env, batch.params, 10
@@ -782,7 +782,7 @@ def warm_start_comparison(args, sim, batch, seed, plain_rate, peaks):
     err_w = warm["no_fallback"]["max_pos_err_over_extent"]
     plain = {}
     k_eq = None
-    for k in (1, 2, 3, 5, 7, 10):
+    for k in (1, 2, 3, 5, 7, 8, 9, 10):
         ps = sim if k == params["iterations"] else ffsrl.Sim(batch.meshes, dict(params, iterations=k), n_env)
         ps.reset(seed)
         for _ in range(N):

@@ -50,14 +50,16 @@ def row_weights(sim, meshes, env_mesh=None):
 
 
 def train(sim, meshes, n_full: int = 10, env_substeps: int = 200_000, lr: float = 1e-3, epochs: int = 2,
-          seed: int = 0, env_mesh=None, log=None):
+          seed: int = 0, env_mesh=None, log=None, lr_final: float | None = None):
     """Trains the network of `sim` on trajectories of its own full solve.
 
     Each ffsrl_record_step advances every env one step with the n_full
     iteration solve and records all vertex rows of all substeps; each substep's
     rows form one batch, visited `epochs` times with Adam. Recording stops once
-    env_substeps env-substeps have been generated. Returns a summary dict with
-    the parameters, normalisation and loss history (normalised MSE)."""
+    env_substeps env-substeps have been generated. With lr_final the learning
+    rate follows a cosine from lr down to lr_final over the Adam steps, else it
+    stays lr. Returns a summary dict with the parameters, normalisation and
+    loss history (normalised MSE)."""
     import torch
     t0 = time.perf_counter()
     w = row_weights(sim, meshes, env_mesh)
@@ -71,7 +73,14 @@ def train(sim, meshes, n_full: int = 10, env_substeps: int = 200_000, lr: float 
     loss = torch.zeros(1, dtype=torch.float32, device=sim.device)
     losses = []
     n_records = max(1, math.ceil(env_substeps / (sim.n_env * S)))
+    n_adam = n_records * epochs * S
     done_substeps = sim.n_env * S
+    k_adam = 0
+
+    def rate():
+        if lr_final is None:
+            return lr
+        return lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * k_adam / max(1, n_adam - 1)))
     for rec in range(n_records):
         if rec > 0:
             if rec % 50 == 0:
@@ -80,10 +89,11 @@ def train(sim, meshes, n_full: int = 10, env_substeps: int = 200_000, lr: float 
             done_substeps += sim.n_env * S
         for _ in range(epochs):
             for s in range(S):
-                sim.train_network(F[s], T[s], w, wsum, lr, loss)
+                sim.train_network(F[s], T[s], w, wsum, rate(), loss)
+                k_adam += 1
         losses.append(float(loss.item()) / (3 * wsum))
         if log:
             log(f"record {rec + 1}/{n_records}: loss {losses[-1]:.4e}")
     sim.sync()
     return {"params": sim.get_network(), "norm": norm, "losses": losses, "env_substeps": done_substeps,
-            "adam_steps": n_records * epochs * S, "seconds": time.perf_counter() - t0}
+            "adam_steps": n_adam, "seconds": time.perf_counter() - t0}
