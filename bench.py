@@ -418,12 +418,12 @@ def run_warmstart(args):
     (untimed, reported). Then, on the 4096-env workload, each path runs K
     timed steps (CUDA events) and, separately, N steps from the same reset
     whose positions are compared with the FP64 oracle running the full solve:
-    plain XPBD with k = 1, 2, 3, 5, 7, 10 iterations, and the warm-start
+    plain XPBD with k = 1, 2, 3, 5, 7, 8, 9, 10 iterations, and the warm-start
     (network + 1 iteration) with the residual-triggered fallback at the
     configured threshold and at multiples of the full solve's own median
     residual. `value` is the warm-start's env-steps/s without fallback; the
-    comparison at equal error picks the cheapest plain k whose error is not
-    larger than the warm-start's."""
+    comparison at equal error picks the cheapest plain k (1, 2, 3, 5, 7, 8, 9,
+    10) whose error is not larger than the warm-start's."""
     import torch
     import __graft_entry__
     import oracle
@@ -479,7 +479,7 @@ def run_warmstart(args):
         return n_env * args.steps / (ev0.elapsed_time(ev1) / 1e3)
 
     plain = {}
-    for k in (1, 2, 3, 5, 7, 10):
+    for k in (1, 2, 3, 5, 7, 8, 9, 10):
         ps = ffsrl.Sim([mesh], inputs.default_params(iterations=k), n_env)
         ps.reset(args.seed)
         for _ in range(N):
