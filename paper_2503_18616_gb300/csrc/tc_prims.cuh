@@ -134,6 +134,14 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     return r;
 }
 
+// pack_bf16x2(max(lo, 0), max(hi, 0)): the ReLU folded into the conversion
+// (negative inputs give +0 or -0, which the tensor cores treat alike).
+__device__ __forceinline__ uint32_t pack_bf16x2_relu(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
 // Byte offset of the 16-byte chunk (row r, k-chunk kc) in a K-major tile with kcs chunks per row.
 __device__ __forceinline__ uint32_t tile_off(int r, int kc, int kcs) {
     return uint32_t(((r >> 3) * kcs + kc) * 128 + (r & 7) * 16);

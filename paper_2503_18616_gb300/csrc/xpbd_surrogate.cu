@@ -610,7 +610,7 @@ __device__ __forceinline__ void warm_hidden16(uint32_t taddr, const float* bias,
     uint32_t pk[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-        pk[q] = pack_bf16x2(fmaxf(v[2 * q] + bias[c0 + 2 * q], 0.f), fmaxf(v[2 * q + 1] + bias[c0 + 2 * q + 1], 0.f));
+        pk[q] = pack_bf16x2_relu(v[2 * q] + bias[c0 + 2 * q], v[2 * q + 1] + bias[c0 + 2 * q + 1]);
     *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8, 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
     *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8 + 1, 8)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
 }
@@ -627,7 +627,7 @@ __device__ __forceinline__ void warm_hidden32(uint32_t taddr, const float* bias,
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int c = 16 * h + 2 * q;
-            pk[q] = pack_bf16x2(fmaxf(v[c] + bias[c0 + c], 0.f), fmaxf(v[c + 1] + bias[c0 + c + 1], 0.f));
+            pk[q] = pack_bf16x2_relu(v[c] + bias[c0 + c], v[c + 1] + bias[c0 + c + 1]);
         }
         *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8 + 2 * h, 8)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         *reinterpret_cast<uint4*>(Ht + tile_off(erow, c0 / 8 + 2 * h + 1, 8)) =
