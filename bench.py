@@ -646,23 +646,37 @@ def setup_mixed(args, sim, batch, seed):
 
 def mixed_accuracy(batch, sim, mixed, seed, seconds, max_steps):
     """FP64 oracle on env 0 (plain step) and env 1 (warm-start step with the
-    same BF16 network and threshold) from the same reset; returns the CPU rate
-    and the position errors of the GPU replay."""
+    same BF16 network and threshold) from the same reset, compared with the
+    GPU step by step. The fallback decision is a threshold test on a residual,
+    so a substep whose residual lies near the threshold can fall back on one
+    side only, after which the two trajectories part; the first step whose
+    fallback counts differ is reported with the oracle's residuals there, and
+    the warm env's error up to the step before it. The oracle's own float32
+    build runs the warm env too: its distance from the FP64 run is the
+    rounding floor of that trajectory (BF16 rounding of features computed in
+    float32 rather than float64 can round the other way). Returns the
+    accuracy object and the CPU rate."""
     import numpy as np
+    import torch
     import oracle
     om = oracle.Mesh(*batch.meshes[0])
     net = oracle.Net.from_params(mixed["params"], *mixed["norm"], bf16=True)
+    S = batch.params["substeps"]
     oes = []
     for e in (0, 1):
         oe = oracle.Env(om, batch.env_params(e))
         oe.reset(seed, int(batch.env_ids[e]))
         oes.append(oe)
 
-    def advance(n):
+    def advance(n, keep=None):
         fb1 = 0
         for _ in range(n):
+            res = np.zeros(S)
             oes[0].step()
-            fb1 += oes[1].step_surrogate(net, mixed["threshold"], mixed["n_full"])[3]
+            f = oes[1].step_surrogate(net, mixed["threshold"], mixed["n_full"], residuals=res)[3]
+            fb1 += f
+            if keep is not None:
+                keep.append((oes[0].state()[0].copy(), oes[1].state()[0].copy(), f, res))
         return fb1
 
     t0 = time.perf_counter()
@@ -671,20 +685,54 @@ def mixed_accuracy(batch, sim, mixed, seed, seconds, max_steps):
     n = max(5, min(max_steps, int(seconds / per)))
     for e, oe in zip((0, 1), oes):
         oe.reset(seed, int(batch.env_ids[e]))
+    ref = []
     t0 = time.perf_counter()
-    ofb = advance(n)
+    ofb = advance(n, ref)
     dt = time.perf_counter() - t0
     sim.reset(seed)
     mixed["fallbacks"].zero_()
-    for _ in range(n):
-        sim.step_into(None, None, None, None)
-    x, _, _ = sim.get_state()
-    x = x.cpu().numpy().astype(np.float64)
     V = om.V
-    errs = [float(np.max(np.abs(x[e * V:(e + 1) * V] - oes[e].state()[0])) / om.extent) for e in (0, 1)]
-    acc = {"max_pos_err_over_extent": max(errs), "per_env": errs, "envs": [0, 1], "steps": n,
-           "kinds": ["plain", "warm-start"], "tolerance": POS_TOL, "within_tolerance": max(errs) <= POS_TOL,
-           "warm_env_fallbacks": {"gpu": int(mixed["fallbacks"][1].item()), "oracle": int(ofb)}}
+    errs = np.zeros((n, 2))
+    gfb = np.zeros(n, dtype=np.int64)
+    prev = 0
+    for k in range(n):
+        sim.step_into(None, None, None, None)
+        x, _, _ = sim.get_state()
+        x01 = x[:2 * V].cpu().numpy().astype(np.float64)
+        c = int(mixed["fallbacks"][1].item())
+        gfb[k], prev = c - prev, c
+        for e in (0, 1):
+            errs[k, e] = float(np.max(np.abs(x01[e * V:(e + 1) * V] - ref[k][e]))) / om.extent
+    ofb_steps = np.array([r[2] for r in ref])
+    o32 = oracle.Env(oracle.Mesh(*batch.meshes[0], precision="f32"), batch.env_params(1))
+    o32.reset(seed, int(batch.env_ids[1]))
+    floor = np.zeros(n)
+    for k in range(n):
+        o32.step_surrogate(net, mixed["threshold"], mixed["n_full"])
+        floor[k] = float(np.max(np.abs(o32.state()[0] - ref[k][1]))) / om.extent
+    diff = np.nonzero(gfb != ofb_steps)[0]
+    first = int(diff[0]) if len(diff) else None
+    agree = {"first_step_fallbacks_differ": None if first is None else first + 1,
+             "warm_env_err_before_it": float(errs[:first, 1].max()) if first else (
+                 float(errs[:, 1].max()) if first is None else None)}
+    if first is not None:
+        r = ref[first][3] / mixed["threshold"]
+        agree["oracle_residual_over_threshold_that_step"] = [float(v) for v in r]
+        agree["fallbacks_that_step"] = {"gpu": int(gfb[first]), "oracle": int(ofb_steps[first])}
+    final = [float(errs[-1, 0]), float(errs[-1, 1])]
+    acc = {"max_pos_err_over_extent": max(final), "per_env": final, "envs": [0, 1], "steps": n,
+           "kinds": ["plain", "warm-start"], "tolerance": POS_TOL, "within_tolerance": max(final) <= POS_TOL,
+           "checkpoints": {"every": CHECK_EVERY,
+                           "plain": [float(v) for v in errs[CHECK_EVERY - 1::CHECK_EVERY, 0]],
+                           "warm_start": [float(v) for v in errs[CHECK_EVERY - 1::CHECK_EVERY, 1]],
+                           "warm_start_fp32_oracle": [float(v) for v in floor[CHECK_EVERY - 1::CHECK_EVERY]]},
+           "warm_env_max_over_steps": float(errs[:, 1].max()),
+           "warm_env_fp32_oracle_max_over_steps": float(floor.max()),
+           "within_fp32_floor": bool(errs[:, 1].max() <= max(POS_TOL, 2 * floor.max())),
+           "fp32_floor_rule": "warm env's largest error over the steps <= max(tolerance, 2 x the oracle's own "
+                              "float32 build's largest error over the same steps)",
+           "warm_env_fallbacks": {"gpu": int(gfb.sum()), "oracle": int(ofb)},
+           "fallback_agreement": agree}
     cpu = {"value": 2 * n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
            "sample": f"env 0 (plain) and env 1 (warm-start) x {n} steps, FP64 oracle, 1 host thread, {dt:.1f} s"}
     return acc, cpu
@@ -797,6 +845,7 @@ def warm_start_comparison(args, sim, batch, seed, plain_rate, peaks):
             break
     V_, E_, T_ = V, len(sim.mesh_table("edges")) // 2, len(sim.mesh_table("tets")) // 4
     w_rate = warm["no_fallback"]["value"]
+    trained = {"params": tr["params"], "norm": tr["norm"], "threshold": thr, "n_full": n_full}
     net_flops = NET_FLOP_ROW * V_ * params["substeps"]   # per env-step
     tc_peak = float(peaks.get("bf16_tflops_sustained", 1700.0))
     return {
@@ -819,7 +868,72 @@ def warm_start_comparison(args, sim, batch, seed, plain_rate, peaks):
                             "peak_source": "bf16_tflops_sustained of MEASURED_PEAKS.json"},
         "oracle_seconds": t_oracle,
         "counts": {"V": V_, "E": E_, "T": T_},
-    }
+    }, trained
+
+
+MIXED_WORKLOAD = "block17x17x9_16384env_2000steps"
+
+
+def mixed_rollout_leg(args, seed, trained, peaks):
+    """The full device-resident rollout on 16384 envs of the same block: odd
+    envs take the warm-start step with the network the warm-start comparison
+    trained (and its threshold, twice the full solve's median residual), even
+    envs the plain step, both in one captured graph. Timed with one CUDA event
+    per step over the workload's 2000 steps (p50 / p99 from those), clocks
+    sampled meanwhile; the FP64 oracle replays env 0 (plain) and env 1
+    (warm-start) for a bounded number of steps."""
+    import torch
+    from paper_2503_18616_gb300 import ffsrl
+    batch = Batch(MIXED_WORKLOAD)
+    params, n_env = batch.params, batch.n_env
+    steps = args.mixed_steps or batch.steps
+    sim = ffsrl.Sim(batch.meshes, params, n_env)
+    sim.set_network(trained["params"], *trained["norm"])
+    mask = (np.arange(n_env) % 2).astype(np.uint8)
+    fb = torch.zeros(n_env, dtype=torch.int32, device="cuda")
+    sim.set_surrogate_envs(mask, trained["threshold"], trained["n_full"], fb)
+    obs = torch.empty((n_env, sim.obs_dim), dtype=torch.float32, device="cuda")
+    rew = torch.empty(n_env, dtype=torch.float32, device="cuda")
+    done = torch.empty(n_env, dtype=torch.uint8, device="cuda")
+    sim.reset(seed)
+    for _ in range(args.warmup):
+        sim.step_into(None, obs, rew, done)
+    torch.cuda.synchronize()
+    sim.sync()
+    fb.zero_()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    stream = sim.stream
+    with torch.cuda.stream(stream):
+        evs[0].record(stream)
+        for k in range(steps):
+            sim.step_into(None, obs, rew, done)
+            evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sim.sync()
+    t_ms = evs[0].elapsed_time(evs[-1])
+    lat = np.array([evs[k].elapsed_time(evs[k + 1]) for k in range(steps)])
+    n_warm = int(mask.sum())
+    frate = float(fb.sum().item()) / (n_warm * steps * params["substeps"])
+    out = {"workload": MIXED_WORKLOAD, "value": n_env * steps / (t_ms / 1e3), "unit": UNIT,
+           "ms_per_step": t_ms / steps, "steps": steps, "warmup": args.warmup,
+           "latency": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                       "max_ms": float(lat.max()), "unit": "ms per step (all envs)"},
+           "n_env": n_env, "warm_start_envs": "odd env ids", "n_warm_start": n_warm,
+           "threshold": trained["threshold"],
+           "threshold_rule": "2 x median residual the full solve leaves (the warm_start object's)",
+           "n_full": trained["n_full"], "fallback_rate": frate,
+           "network": "the warm_start object's, trained once", "dtype": "f32+bf16",
+           "gpu_launches": steps * (sim.n_groups + 1), "clocks": clk}
+    if not args.no_cpu_baseline:
+        mixed = {"params": trained["params"], "norm": trained["norm"], "threshold": trained["threshold"],
+                 "n_full": trained["n_full"], "fallbacks": fb}
+        out["accuracy"], out["cpu_baseline"] = mixed_accuracy(batch, sim, mixed, seed, args.cpu_seconds, steps)
+    sim.close()
+    return out
 
 
 def run_ours(args):
@@ -1095,7 +1209,11 @@ def run_ours(args):
         wspec = inputs.WORKLOADS[args.workload]
         if (world == 1 and mixed is None and not args.no_warm_start and single and "shape" in wspec
                 and params.get("tool_model", 0) == 0 and params.get("solver", 0) == 0):
-            line["warm_start"] = warm_start_comparison(args, sim, batch, seed, value, load_peaks()[0])
+            line["warm_start"], trained = warm_start_comparison(args, sim, batch, seed, value, load_peaks()[0])
+            if not args.no_mixed:
+                sim.close()
+                sim = None
+                line["mixed_rollout"] = mixed_rollout_leg(args, seed, trained, load_peaks()[0])
         if mixed is not None:
             line["dtype"] = "f32+bf16"
             line["mixed"] = {"warm_start_envs": "odd env ids", "n_warm_start": int(mixed["mask"].sum()),
@@ -1103,7 +1221,8 @@ def run_ours(args):
                              "n_full": mixed["n_full"], "fallback_rate": fallback_rate,
                              "training": mixed["training"]}
         print(json.dumps(line), flush=True)
-    sim.close()
+    if sim is not None:
+        sim.close()
     if dist is not None:
         dist.destroy_process_group()
     return line
@@ -1125,6 +1244,10 @@ def main():
     ap.add_argument("--envs", type=int, default=0, help="override the workload's env count")
     ap.add_argument("--schedule", default="", help="force threads_per_env:envs_per_cta:ring:permute[:ctas_per_sm]")
     ap.add_argument("--acc-steps", type=int, default=50, help="steps of the warm-start accuracy comparison")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed plain / warm-start rollout on 16384 envs after the warm-start comparison")
+    ap.add_argument("--mixed-steps", type=int, default=0,
+                    help="timed steps of the mixed rollout (0: the workload's 2000)")
     ap.add_argument("--seeds", type=int, default=5, help="extra resets timed for the spread over seeds")
     ap.add_argument("--fixed-total", action="store_true",
                     help="split the workload's envs over the ranks (strong scaling) instead of giving every "
