@@ -982,6 +982,8 @@ def run_ours(args):
         flags |= {1: 0, 2: ffsrl.SCHED_ENVS2, 4: ffsrl.SCHED_ENVS4}[envs]
         if len(fields) > 4 and fields[4] == 4:
             flags |= ffsrl.SCHED_FOUR_CTAS
+    if args.global_memory:   # the streaming design point: positions in a global working copy
+        flags |= ffsrl.SCHED_GLOBAL_MEMORY
     sim = ffsrl.Sim(batch.meshes, params, n_env, env_mesh=batch.env_mesh, env_compliance=batch.env_alpha,
                     block_threads=block, schedule_flags=flags)
     sim.set_env_ids(ids)
@@ -1094,8 +1096,9 @@ def run_ours(args):
         hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_PEAKS["hbm_gbs"]))
         single = len(batch.meshes) == 1
         traffic = ncu_traffic("xpbd_step_block17x17x9_4096env.txt") if (
-            single and n_env == 4096 and counts[0][0] == 2601) else None
-        kernel = (f"xpbd_step_kernel<{sim.block_threads},{sim.envs_per_cta},resident,"
+            single and n_env == 4096 and counts[0][0] == 2601 and not args.global_memory) else None
+        kernel = (f"xpbd_step_kernel<{sim.block_threads},{sim.envs_per_cta},"
+                  f"{'resident' if sim.resident_envs else 'global working copy'},"
                   f"{'ring' if sim.ring_envs else 'l2'}> ({sim.ctas_per_sm} CTAs/SM)" if single else
                   f"xpbd_step_kernel, {sim.n_groups} size classes launched concurrently")
         roofline = {"bound": "smem", "achieved": smem_bytes / sec / 1e9, "peak": smem_peak, "unit": "GB/s",
@@ -1243,6 +1246,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--envs", type=int, default=0, help="override the workload's env count")
     ap.add_argument("--schedule", default="", help="force threads_per_env:envs_per_cta:ring:permute[:ctas_per_sm]")
+    ap.add_argument("--global-memory", action="store_true",
+                    help="every env on the global-memory working copy (the streaming design point)")
     ap.add_argument("--acc-steps", type=int, default=50, help="steps of the warm-start accuracy comparison")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed plain / warm-start rollout on 16384 envs after the warm-start comparison")

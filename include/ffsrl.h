@@ -133,6 +133,9 @@ typedef struct {
                                         input tiles and corrections in global memory, instead of the
                                         one that builds each tile's input just in time (the default
                                         where a mesh's 1-ring spans at most four 128-row tiles) */
+#define FFSRL_SCHED_GLOBAL_MEMORY 512  /* every env of the plain step on the global-memory working copy
+                                          (the variant of meshes above the shared memory), even where
+                                          its positions fit on chip: the streaming design point */
 
 /* Sizes of a created simulator. */
 typedef struct {

@@ -213,7 +213,8 @@ int check_params(const ffsrl_params& p) {
         return fail(FFSRL_E_INVAL, "block_threads must be 0, 128, 256, 384, 512 or 1024");
     if (p.schedule_flags & ~(FFSRL_SCHED_FORCE | FFSRL_SCHED_NO_PERMUTE | FFSRL_SCHED_NO_RING |
                              FFSRL_SCHED_ENVS2 | FFSRL_SCHED_ENVS4 | FFSRL_SCHED_SURROGATE_PIPELINE |
-                             FFSRL_SCHED_NO_CLUSTER | FFSRL_SCHED_FOUR_CTAS | FFSRL_SCHED_WARM_STAGED))
+                             FFSRL_SCHED_NO_CLUSTER | FFSRL_SCHED_FOUR_CTAS | FFSRL_SCHED_WARM_STAGED |
+                             FFSRL_SCHED_GLOBAL_MEMORY))
         return fail(FFSRL_E_INVAL, "unknown schedule_flags bits");
     if ((p.schedule_flags & FFSRL_SCHED_ENVS2) && (p.schedule_flags & FFSRL_SCHED_ENVS4))
         return fail(FFSRL_E_INVAL, "FFSRL_SCHED_ENVS2 and FFSRL_SCHED_ENVS4 are exclusive");
@@ -712,13 +713,15 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
         const size_t b = group_smem(s, md[mi], probe);   // 256 threads, resident, ring
         mesh_class[mi] = b ? std::min<int>(3, int(size_t(smem_sm) / (b + 1024))) : 0;
         if (b && mesh_class[mi] == 0) mesh_class[mi] = 1;
+        if (p.schedule_flags & FFSRL_SCHED_GLOBAL_MEMORY) mesh_class[mi] = 0;
     }
     // Meshes above one CTA's shared memory: a cluster of 2 or 4 CTAs holds
     // the env on chip (class -CL) when it fits and can be scheduled; else the
     // global-memory variant (class 0).
     std::vector<int> part_slots(md.size(), 0);
     std::vector<size_t> cl_smem(md.size(), 0);
-    if (!(p.schedule_flags & FFSRL_SCHED_NO_CLUSTER) && p.tool_model == FFSRL_TOOL_SPHERE) {
+    if (!(p.schedule_flags & (FFSRL_SCHED_NO_CLUSTER | FFSRL_SCHED_GLOBAL_MEMORY)) &&
+        p.tool_model == FFSRL_TOOL_SPHERE) {
         for (size_t mi = 0; mi < md.size(); ++mi) {
             if (mesh_class[mi] != 0 || s->meshes[mi].C > 0) continue;
             for (int cl : {2, 4}) {

@@ -71,6 +71,7 @@ SCHED_SURROGATE_PIPELINE = 32
 SCHED_NO_CLUSTER = 64
 SCHED_FOUR_CTAS = 128
 SCHED_WARM_STAGED = 256
+SCHED_GLOBAL_MEMORY = 512
 
 
 class ffsrl_info(ctypes.Structure):

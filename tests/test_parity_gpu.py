@@ -430,6 +430,18 @@ def test_every_schedule_gives_bit_identical_results():
             for a, b in zip(ref, out):
                 assert np.array_equal(a, b), (flags, block)
         sim.close()
+    # the global-memory working copy, autotuned and forced
+    for flags in (ffsrl.SCHED_GLOBAL_MEMORY, ffsrl.SCHED_GLOBAL_MEMORY | ffsrl.SCHED_FORCE):
+        sim = make_sim([m], p, n_env, block_threads=256 if flags & ffsrl.SCHED_FORCE else 0,
+                       schedule_flags=flags, seed=3)
+        assert sim.resident_envs == 0
+        for _ in range(steps):
+            obs, rew, done = sim.step()
+        x, v, _ = sim.get_state()
+        out = (x.cpu().numpy(), v.cpu().numpy(), obs.cpu().numpy(), rew.cpu().numpy())
+        for a, b in zip(ref, out):
+            assert np.array_equal(a, b), flags
+        sim.close()
 
 
 def test_refined_phases_and_four_cta_kernel_give_the_colour_schedule_bits():
