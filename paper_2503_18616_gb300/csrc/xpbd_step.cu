@@ -271,19 +271,36 @@ __global__ void __launch_bounds__(SUB * ENVS, OCC ? OCC : min_ctas_per_sm(SUB * 
                 const bool carry = lam != nullptr;
                 if (ok && active) {
                     const bool lin = carry && it > 0;
+                    // one iteration (no multipliers kept): loops without the
+                    // multiplier loads and stores, with lambda = 0 as the
+                    // carried loops start from
                     if (c < n_ecol) {
                         const uint2* rec = reinterpret_cast<const uint2*>(base);
-                        for (int q = st; q < sg.z; q += SUB) {
-                            float l = lin ? lam[sg.w + q] : 0.f;
-                            project_edge(X, rec[q], at_d, M.min_len2, l);
-                            if (carry) lam[sg.w + q] = l;
+                        if (!carry) {
+                            for (int q = st; q < sg.z; q += SUB) {
+                                float l = 0.f;
+                                project_edge(X, rec[q], at_d, M.min_len2, l);
+                            }
+                        } else {
+                            for (int q = st; q < sg.z; q += SUB) {
+                                float l = lin ? lam[sg.w + q] : 0.f;
+                                project_edge(X, rec[q], at_d, M.min_len2, l);
+                                lam[sg.w + q] = l;
+                            }
                         }
                     } else if (c < M.n_dseg) {
                         const uint4* rec = reinterpret_cast<const uint4*>(base);
-                        for (int q = st; q < sg.z; q += SUB) {
-                            float l = lin ? lam[sg.w + q] : 0.f;
-                            project_tet(X, rec[q], at_v, l);
-                            if (carry) lam[sg.w + q] = l;
+                        if (!carry) {
+                            for (int q = st; q < sg.z; q += SUB) {
+                                float l = 0.f;
+                                project_tet(X, rec[q], at_v, l);
+                            }
+                        } else {
+                            for (int q = st; q < sg.z; q += SUB) {
+                                float l = lin ? lam[sg.w + q] : 0.f;
+                                project_tet(X, rec[q], at_v, l);
+                                lam[sg.w + q] = l;
+                            }
                         }
                     } else {
                         // tissue connections, after the volume colours
