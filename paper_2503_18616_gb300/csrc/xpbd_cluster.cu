@@ -171,6 +171,7 @@ __global__ void __launch_bounds__(SUB, 1)
                 const unsigned char* base = M.recs + sg.x;
                 const bool carry = lam != nullptr;
                 uint4 cur = first_rec(c);
+                // one iteration keeps no multipliers: loops without their loads and stores
                 if (c < M.n_ecol) {
                     const uint2* rec = reinterpret_cast<const uint2*>(base);
                     for (int q = tid; q < sg.z; q += SUB) {
@@ -179,18 +180,28 @@ __global__ void __launch_bounds__(SUB, 1)
                             const uint2 e = __ldg(rec + q + SUB);
                             nxt = make_uint4(e.x, e.y, 0u, 0u);
                         }
-                        float l = (carry && it > 0) ? lam[sg.w + q] : 0.f;
-                        project_edge(X, make_uint2(cur.x, cur.y), at_d, M.min_len2, l);
-                        if (carry) lam[sg.w + q] = l;
+                        if (!carry) {
+                            float l = 0.f;
+                            project_edge(X, make_uint2(cur.x, cur.y), at_d, M.min_len2, l);
+                        } else {
+                            float l = it > 0 ? lam[sg.w + q] : 0.f;
+                            project_edge(X, make_uint2(cur.x, cur.y), at_d, M.min_len2, l);
+                            lam[sg.w + q] = l;
+                        }
                         cur = nxt;
                     }
                 } else {
                     const uint4* rec = reinterpret_cast<const uint4*>(base);
                     for (int q = tid; q < sg.z; q += SUB) {
                         const uint4 nxt = (q + SUB < sg.z) ? __ldg(rec + q + SUB) : cur;
-                        float l = (carry && it > 0) ? lam[sg.w + q] : 0.f;
-                        project_tet(X, cur, at_v, l);
-                        if (carry) lam[sg.w + q] = l;
+                        if (!carry) {
+                            float l = 0.f;
+                            project_tet(X, cur, at_v, l);
+                        } else {
+                            float l = it > 0 ? lam[sg.w + q] : 0.f;
+                            project_tet(X, cur, at_v, l);
+                            lam[sg.w + q] = l;
+                        }
                         cur = nxt;
                     }
                 }

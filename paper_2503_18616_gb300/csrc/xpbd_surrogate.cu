@@ -476,19 +476,34 @@ __device__ bool ring_sweep(float4* X, const MeshDev& M, const int4* segs, unsign
             const int4 sg = segs[c];
             const unsigned char* base = ring + (k & 1) * M.ring_bytes;
             const bool carry = lam != nullptr && n_proj > 1;
+            // one pass keeps no multipliers: loops without their loads and stores
             if (c < n_ecol) {
                 const uint2* rec = reinterpret_cast<const uint2*>(base);
-                for (int q = st; q < sg.z; q += kWarmThreads) {
-                    float l = (carry && pass > 0) ? lam[sg.w + q] : 0.f;
-                    project_edge(X, rec[q], at_d, M.min_len2, l);
-                    if (carry) lam[sg.w + q] = l;
+                if (!carry) {
+                    for (int q = st; q < sg.z; q += kWarmThreads) {
+                        float l = 0.f;
+                        project_edge(X, rec[q], at_d, M.min_len2, l);
+                    }
+                } else {
+                    for (int q = st; q < sg.z; q += kWarmThreads) {
+                        float l = pass > 0 ? lam[sg.w + q] : 0.f;
+                        project_edge(X, rec[q], at_d, M.min_len2, l);
+                        lam[sg.w + q] = l;
+                    }
                 }
             } else {
                 const uint4* rec = reinterpret_cast<const uint4*>(base);
-                for (int q = st; q < sg.z; q += kWarmThreads) {
-                    float l = (carry && pass > 0) ? lam[sg.w + q] : 0.f;
-                    project_tet(X, rec[q], at_v, l);
-                    if (carry) lam[sg.w + q] = l;
+                if (!carry) {
+                    for (int q = st; q < sg.z; q += kWarmThreads) {
+                        float l = 0.f;
+                        project_tet(X, rec[q], at_v, l);
+                    }
+                } else {
+                    for (int q = st; q < sg.z; q += kWarmThreads) {
+                        float l = pass > 0 ? lam[sg.w + q] : 0.f;
+                        project_tet(X, rec[q], at_v, l);
+                        lam[sg.w + q] = l;
+                    }
                 }
             }
         }
