@@ -339,51 +339,70 @@ __global__ void __launch_bounds__(SUB * ENVS, OCC ? OCC : min_ctas_per_sm(SUB * 
         // centre-to-vertex direction (straight up if it sits on the centre).
         // Except after the last substep, the same pass performs the velocity
         // update v = (x - x_prev) / h and the next substep's prediction.
-        if (active) {
-            for (int s = st; s < V; s += SUB) {
-                float4 xi = X[s];
-                if (!(xi.w > 0.f)) {
-                    if (!last) {
-                        Px[s] = xi.x;
-                        Py[s] = xi.y;
-                        Pz[s] = xi.z;
-                    }
-                    continue;
-                }
-                const float dx = __fsub_rn(xi.x, cx), dy = __fsub_rn(xi.y, cy), dz = __fsub_rn(xi.z, cz);
-                const float l2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-                bool moved = false;
-                if (l2 < r2) {
-                    const float len = sqrtf(l2);
-                    if (len > 0.f) {
-                        const float f = __fdividef(r, len);
-                        xi.x = __fmaf_rn(f, dx, cx);
-                        xi.y = __fmaf_rn(f, dy, cy);
-                        xi.z = __fmaf_rn(f, dz, cz);
-                    } else {
-                        xi.x = cx;
-                        xi.y = cy;
-                        xi.z = __fadd_rn(cz, r);
-                    }
-                    moved = true;
-                    if (last) {
-                        const int i = M.vert_of[s];
-                        atomicOr(&bits[i >> 5], 1u << (i & 31));
-                    }
-                }
+        // Two slots per loop trip, both slots' substep-start positions loaded
+        // before either is used (the global loads of one trip overlap).
+        auto vertex_pass = [&](int s, float4 xi, float px, float py, float pz) {
+            if (!(xi.w > 0.f)) {
                 if (!last) {
-                    const float vx = __fmul_rn(__fsub_rn(xi.x, Px[s]), inv_h),
-                                vy = __fmul_rn(__fsub_rn(xi.y, Py[s]), inv_h),
-                                vz = __fmul_rn(__fsub_rn(xi.z, Pz[s]), inv_h);
                     Px[s] = xi.x;
                     Py[s] = xi.y;
                     Pz[s] = xi.z;
-                    xi.x = __fmaf_rn(h, __fadd_rn(vx, hgx), xi.x);
-                    xi.y = __fmaf_rn(h, __fadd_rn(vy, hgy), xi.y);
-                    xi.z = __fmaf_rn(h, __fadd_rn(vz, hgz), xi.z);
-                    moved = true;
                 }
-                if (moved) X[s] = xi;
+                return;
+            }
+            const float dx = __fsub_rn(xi.x, cx), dy = __fsub_rn(xi.y, cy), dz = __fsub_rn(xi.z, cz);
+            const float l2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+            bool moved = false;
+            if (l2 < r2) {
+                const float len = sqrtf(l2);
+                if (len > 0.f) {
+                    const float f = __fdividef(r, len);
+                    xi.x = __fmaf_rn(f, dx, cx);
+                    xi.y = __fmaf_rn(f, dy, cy);
+                    xi.z = __fmaf_rn(f, dz, cz);
+                } else {
+                    xi.x = cx;
+                    xi.y = cy;
+                    xi.z = __fadd_rn(cz, r);
+                }
+                moved = true;
+                if (last) {
+                    const int i = M.vert_of[s];
+                    atomicOr(&bits[i >> 5], 1u << (i & 31));
+                }
+            }
+            if (!last) {
+                const float vx = __fmul_rn(__fsub_rn(xi.x, px), inv_h), vy = __fmul_rn(__fsub_rn(xi.y, py), inv_h),
+                            vz = __fmul_rn(__fsub_rn(xi.z, pz), inv_h);
+                Px[s] = xi.x;
+                Py[s] = xi.y;
+                Pz[s] = xi.z;
+                xi.x = __fmaf_rn(h, __fadd_rn(vx, hgx), xi.x);
+                xi.y = __fmaf_rn(h, __fadd_rn(vy, hgy), xi.y);
+                xi.z = __fmaf_rn(h, __fadd_rn(vz, hgz), xi.z);
+                moved = true;
+            }
+            if (moved) X[s] = xi;
+        };
+        if (active) {
+            for (int s = st; s < V; s += 2 * SUB) {
+                const int s2 = s + SUB;
+                const bool two = s2 < V;
+                const float4 x1 = X[s];
+                const float4 x2 = two ? X[s2] : x1;
+                float p1x = 0.f, p1y = 0.f, p1z = 0.f, p2x = 0.f, p2y = 0.f, p2z = 0.f;
+                if (!last) {
+                    p1x = Px[s];
+                    p1y = Py[s];
+                    p1z = Pz[s];
+                    if (two) {
+                        p2x = Px[s2];
+                        p2y = Py[s2];
+                        p2z = Pz[s2];
+                    }
+                }
+                vertex_pass(s, x1, p1x, p1y, p1z);
+                if (two) vertex_pass(s2, x2, p2x, p2y, p2z);
             }
         }
         __syncthreads();
