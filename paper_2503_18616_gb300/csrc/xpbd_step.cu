@@ -175,18 +175,35 @@ __global__ void __launch_bounds__(SUB * ENVS, OCC ? OCC : min_ctas_per_sm(SUB * 
         // for the first substep (Algorithm 1: v~ = v + h g, x~ = x + h v~).
         const float* gx = S.x + ed.voff;
         const float* gv = S.v + ed.voff;
-        for (int i = st; i < V; i += SUB) {
-            const int s = M.slot_of[i];
-            float4 xi = make_float4(gx[i], gx[stride + i], gx[2 * stride + i], M.rest_w[i].w);
-            Px[s] = xi.x;
-            Py[s] = xi.y;
-            Pz[s] = xi.z;
-            if (xi.w > 0.f) {   // rounding spelled out: the same bits in every kernel instantiation
-                xi.x = __fmaf_rn(h, __fadd_rn(gv[i], hgx), xi.x);
-                xi.y = __fmaf_rn(h, __fadd_rn(gv[stride + i], hgy), xi.y);
-                xi.z = __fmaf_rn(h, __fadd_rn(gv[2 * stride + i], hgz), xi.z);
+        constexpr int NL = 4;   // vertices per loop trip, their loads issued together
+        for (int i0 = st; i0 < V; i0 += NL * SUB) {
+            int sl[NL];
+            float4 xs[NL];
+            float vx[NL], vy[NL], vz[NL];
+#pragma unroll
+            for (int u = 0; u < NL; ++u) {
+                const int i = i0 + u * SUB < V ? i0 + u * SUB : i0;
+                sl[u] = M.slot_of[i];
+                xs[u] = make_float4(gx[i], gx[stride + i], gx[2 * stride + i], M.rest_w[i].w);
+                vx[u] = gv[i];
+                vy[u] = gv[stride + i];
+                vz[u] = gv[2 * stride + i];
             }
-            X[s] = xi;
+#pragma unroll
+            for (int u = 0; u < NL; ++u) {
+                if (i0 + u * SUB >= V) break;
+                const int s = sl[u];
+                float4 xi = xs[u];
+                Px[s] = xi.x;
+                Py[s] = xi.y;
+                Pz[s] = xi.z;
+                if (xi.w > 0.f) {   // rounding spelled out: the same bits in every kernel instantiation
+                    xi.x = __fmaf_rn(h, __fadd_rn(vx[u], hgx), xi.x);
+                    xi.y = __fmaf_rn(h, __fadd_rn(vy[u], hgy), xi.y);
+                    xi.z = __fmaf_rn(h, __fadd_rn(vz[u], hgz), xi.z);
+                }
+                X[s] = xi;
+            }
         }
     }
     __syncthreads();
@@ -339,8 +356,8 @@ __global__ void __launch_bounds__(SUB * ENVS, OCC ? OCC : min_ctas_per_sm(SUB * 
         // centre-to-vertex direction (straight up if it sits on the centre).
         // Except after the last substep, the same pass performs the velocity
         // update v = (x - x_prev) / h and the next substep's prediction.
-        // Two slots per loop trip, both slots' substep-start positions loaded
-        // before either is used (the global loads of one trip overlap).
+        // Several slots per loop trip, all their substep-start positions
+        // loaded before any is used (the global loads of one trip overlap).
         auto vertex_pass = [&](int s, float4 xi, float px, float py, float pz) {
             if (!(xi.w > 0.f)) {
                 if (!last) {
@@ -385,24 +402,24 @@ __global__ void __launch_bounds__(SUB * ENVS, OCC ? OCC : min_ctas_per_sm(SUB * 
             if (moved) X[s] = xi;
         };
         if (active) {
-            for (int s = st; s < V; s += 2 * SUB) {
-                const int s2 = s + SUB;
-                const bool two = s2 < V;
-                const float4 x1 = X[s];
-                const float4 x2 = two ? X[s2] : x1;
-                float p1x = 0.f, p1y = 0.f, p1z = 0.f, p2x = 0.f, p2y = 0.f, p2z = 0.f;
-                if (!last) {
-                    p1x = Px[s];
-                    p1y = Py[s];
-                    p1z = Pz[s];
-                    if (two) {
-                        p2x = Px[s2];
-                        p2y = Py[s2];
-                        p2z = Pz[s2];
+            constexpr int NV = 4;   // slots per loop trip
+            for (int s0 = st; s0 < V; s0 += NV * SUB) {
+                float4 xs[NV];
+                float px[NV], py[NV], pz[NV];
+#pragma unroll
+                for (int u = 0; u < NV; ++u) {
+                    const int s = s0 + u * SUB;
+                    xs[u] = s < V ? X[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    px[u] = py[u] = pz[u] = 0.f;
+                    if (!last && s < V) {
+                        px[u] = Px[s];
+                        py[u] = Py[s];
+                        pz[u] = Pz[s];
                     }
                 }
-                vertex_pass(s, x1, p1x, p1y, p1z);
-                if (two) vertex_pass(s2, x2, p2x, p2y, p2z);
+#pragma unroll
+                for (int u = 0; u < NV; ++u)
+                    if (s0 + u * SUB < V) vertex_pass(s0 + u * SUB, xs[u], px[u], py[u], pz[u]);
             }
         }
         __syncthreads();
@@ -420,16 +437,33 @@ __global__ void __launch_bounds__(SUB * ENVS, OCC ? OCC : min_ctas_per_sm(SUB * 
     float* ox = S.x + ed.voff;
     float* ov = S.v + ed.voff;
     bool bad = false;
-    for (int i = st; i < V; i += SUB) {
-        const int s = M.slot_of[i];
-        const float4 xi = X[s];
-        ox[i] = xi.x;
-        ox[stride + i] = xi.y;
-        ox[2 * stride + i] = xi.z;
-        ov[i] = __fmul_rn(__fsub_rn(xi.x, Px[s]), inv_h);
-        ov[stride + i] = __fmul_rn(__fsub_rn(xi.y, Py[s]), inv_h);
-        ov[2 * stride + i] = __fmul_rn(__fsub_rn(xi.z, Pz[s]), inv_h);
-        bad |= !(isfinite(xi.x) && isfinite(xi.y) && isfinite(xi.z));
+    constexpr int NW = 4;   // vertices per loop trip, their loads issued together
+    for (int i0 = st; i0 < V; i0 += NW * SUB) {
+        int sl[NW];
+#pragma unroll
+        for (int u = 0; u < NW; ++u) sl[u] = i0 + u * SUB < V ? int(M.slot_of[i0 + u * SUB]) : 0;
+        float4 xs[NW];
+        float px[NW], py[NW], pz[NW];
+#pragma unroll
+        for (int u = 0; u < NW; ++u) {
+            xs[u] = X[sl[u]];
+            px[u] = Px[sl[u]];
+            py[u] = Py[sl[u]];
+            pz[u] = Pz[sl[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < NW; ++u) {
+            const int i = i0 + u * SUB;
+            if (i >= V) break;
+            const float4 xi = xs[u];
+            ox[i] = xi.x;
+            ox[stride + i] = xi.y;
+            ox[2 * stride + i] = xi.z;
+            ov[i] = __fmul_rn(__fsub_rn(xi.x, px[u]), inv_h);
+            ov[stride + i] = __fmul_rn(__fsub_rn(xi.y, py[u]), inv_h);
+            ov[2 * stride + i] = __fmul_rn(__fsub_rn(xi.z, pz[u]), inv_h);
+            bad |= !(isfinite(xi.x) && isfinite(xi.y) && isfinite(xi.z));
+        }
     }
     if (bad) atomicOr(&S.err[env], kErrNonFinite);
 
