@@ -121,18 +121,36 @@ __global__ void __launch_bounds__(SUB, 1)
         // Load the own slot range (its vertices are the same aligned blocks) and predict.
         const float* gx = S.x + ed.voff;
         const float* gv = S.v + ed.voff;
-        for (int s = lo + tid; s < hi; s += SUB) {
-            const int i = M.vert_of[s];
-            float4 xi = make_float4(gx[i], gx[stride + i], gx[2 * stride + i], M.rest_w[i].w);
-            Px[s] = xi.x;
-            Py[s] = xi.y;
-            Pz[s] = xi.z;
-            if (xi.w > 0.f) {   // rounding spelled out, as in the single-CTA kernel
-                xi.x = __fmaf_rn(h, __fadd_rn(gv[i], hgx), xi.x);
-                xi.y = __fmaf_rn(h, __fadd_rn(gv[stride + i], hgy), xi.y);
-                xi.z = __fmaf_rn(h, __fadd_rn(gv[2 * stride + i], hgz), xi.z);
+        // two slots per loop trip, their loads issued together
+        for (int s0 = lo + tid; s0 < hi; s0 += 2 * SUB) {
+            int iv[2];
+            float4 xs[2];
+            float vx[2], vy[2], vz[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) iv[u] = M.vert_of[s0 + u * SUB < hi ? s0 + u * SUB : s0];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int i = iv[u];
+                xs[u] = make_float4(gx[i], gx[stride + i], gx[2 * stride + i], M.rest_w[i].w);
+                vx[u] = gv[i];
+                vy[u] = gv[stride + i];
+                vz[u] = gv[2 * stride + i];
             }
-            Xl[s - lo] = xi;
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int s = s0 + u * SUB;
+                if (s >= hi) break;
+                float4 xi = xs[u];
+                Px[s] = xi.x;
+                Py[s] = xi.y;
+                Pz[s] = xi.z;
+                if (xi.w > 0.f) {   // rounding spelled out, as in the single-CTA kernel
+                    xi.x = __fmaf_rn(h, __fadd_rn(vx[u], hgx), xi.x);
+                    xi.y = __fmaf_rn(h, __fadd_rn(vy[u], hgy), xi.y);
+                    xi.z = __fmaf_rn(h, __fadd_rn(vz[u], hgz), xi.z);
+                }
+                Xl[s - lo] = xi;
+            }
         }
     }
     cl_sync();   // every range loaded, the tool centre published by CTA 0
@@ -211,15 +229,14 @@ __global__ void __launch_bounds__(SUB, 1)
         // Collision, and except after the last substep the velocity update and
         // the next prediction, on the own range (as the single-CTA kernel).
         const bool last = sub == S.substeps - 1;
-        for (int s = lo + tid; s < hi; s += SUB) {
-            float4 xi = Xl[s - lo];
+        auto vertex_pass = [&](int s, float4 xi, float px, float py, float pz) {
             if (!(xi.w > 0.f)) {
                 if (!last) {
                     Px[s] = xi.x;
                     Py[s] = xi.y;
                     Pz[s] = xi.z;
                 }
-                continue;
+                return;
             }
             const float dx = __fsub_rn(xi.x, cx), dy = __fsub_rn(xi.y, cy), dz = __fsub_rn(xi.z, cz);
             const float l2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
@@ -243,9 +260,8 @@ __global__ void __launch_bounds__(SUB, 1)
                 }
             }
             if (!last) {
-                const float vx = __fmul_rn(__fsub_rn(xi.x, Px[s]), inv_h),
-                            vy = __fmul_rn(__fsub_rn(xi.y, Py[s]), inv_h),
-                            vz = __fmul_rn(__fsub_rn(xi.z, Pz[s]), inv_h);
+                const float vx = __fmul_rn(__fsub_rn(xi.x, px), inv_h), vy = __fmul_rn(__fsub_rn(xi.y, py), inv_h),
+                            vz = __fmul_rn(__fsub_rn(xi.z, pz), inv_h);
                 Px[s] = xi.x;
                 Py[s] = xi.y;
                 Pz[s] = xi.z;
@@ -255,6 +271,26 @@ __global__ void __launch_bounds__(SUB, 1)
                 moved = true;
             }
             if (moved) Xl[s - lo] = xi;
+        };
+        // two slots per loop trip, both slots' substep-start positions loaded first
+        for (int s = lo + tid; s < hi; s += 2 * SUB) {
+            const int s2 = s + SUB;
+            const bool two = s2 < hi;
+            const float4 x1 = Xl[s - lo];
+            const float4 x2 = two ? Xl[s2 - lo] : x1;
+            float p1x = 0.f, p1y = 0.f, p1z = 0.f, p2x = 0.f, p2y = 0.f, p2z = 0.f;
+            if (!last) {
+                p1x = Px[s];
+                p1y = Py[s];
+                p1z = Pz[s];
+                if (two) {
+                    p2x = Px[s2];
+                    p2y = Py[s2];
+                    p2z = Pz[s2];
+                }
+            }
+            vertex_pass(s, x1, p1x, p1y, p1z);
+            if (two) vertex_pass(s2, x2, p2x, p2y, p2z);
         }
         cl_sync();
     }
@@ -262,16 +298,31 @@ __global__ void __launch_bounds__(SUB, 1)
     float* ox = S.x + ed.voff;
     float* ov = S.v + ed.voff;
     bool bad = false;
-    for (int s = lo + tid; s < hi; s += SUB) {
-        const int i = M.vert_of[s];
-        const float4 xi = Xl[s - lo];
-        ox[i] = xi.x;
-        ox[stride + i] = xi.y;
-        ox[2 * stride + i] = xi.z;
-        ov[i] = __fmul_rn(__fsub_rn(xi.x, Px[s]), inv_h);
-        ov[stride + i] = __fmul_rn(__fsub_rn(xi.y, Py[s]), inv_h);
-        ov[2 * stride + i] = __fmul_rn(__fsub_rn(xi.z, Pz[s]), inv_h);
-        bad |= !(isfinite(xi.x) && isfinite(xi.y) && isfinite(xi.z));
+    for (int s0 = lo + tid; s0 < hi; s0 += 2 * SUB) {   // two slots per trip, loads first
+        int iv[2];
+        float px[2], py[2], pz[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int s = s0 + u * SUB < hi ? s0 + u * SUB : s0;
+            iv[u] = M.vert_of[s];
+            px[u] = Px[s];
+            py[u] = Py[s];
+            pz[u] = Pz[s];
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int s = s0 + u * SUB;
+            if (s >= hi) break;
+            const int i = iv[u];
+            const float4 xi = Xl[s - lo];
+            ox[i] = xi.x;
+            ox[stride + i] = xi.y;
+            ox[2 * stride + i] = xi.z;
+            ov[i] = __fmul_rn(__fsub_rn(xi.x, px[u]), inv_h);
+            ov[stride + i] = __fmul_rn(__fsub_rn(xi.y, py[u]), inv_h);
+            ov[2 * stride + i] = __fmul_rn(__fsub_rn(xi.z, pz[u]), inv_h);
+            bad |= !(isfinite(xi.x) && isfinite(xi.y) && isfinite(xi.z));
+        }
     }
     if (bad) atomicOr(&S.err[env], kErrNonFinite);
     if (rank == 0) {
