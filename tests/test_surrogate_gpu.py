@@ -264,3 +264,31 @@ def test_just_in_time_and_staged_kernels_give_the_same_bits(shape):
         sim.close()
     for a, b in zip(out["jit"], out["staged"]):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("shape", [(9, 9, 5), (17, 17, 9)])
+def test_step_residual_matches_oracle(shape):
+    """The residual the fallback decision reads (largest relative violation
+    after the one iteration, W5), asked for at an infinite threshold so that
+    nothing falls back: per env and step, the GPU's maximum over the step's
+    substeps equals the oracle's within 1% (both read states that agree to
+    the position tolerance; a relative violation moves by about the position
+    error over the rest length)."""
+    m = grid(shape)
+    p = inputs.default_params(radius=4e-3)
+    n_env, steps, S = 3, 8, p["substeps"]
+    params, norm, _ = _case_network("random_network")
+    net = oracle.Net.from_params(params, *norm, bf16=True)
+    oenvs, _ = oracle_envs([m], p, n_env, seed=21)
+    sim = make_sim([m], p, n_env, seed=21)
+    _install(sim, params, norm)
+    res = torch.zeros(n_env, dtype=torch.float32, device="cuda")
+    for k in range(steps):
+        res.zero_()
+        sim.step_surrogate(float("inf"), 10, residual=res)
+        g = res.cpu().numpy()
+        for e, oe in oenvs.items():
+            r = np.zeros(S)
+            oe.step_surrogate(net, float("inf"), 10, residuals=r)
+            assert r.max() > 0
+            assert abs(g[e] - r.max()) <= 1e-2 * r.max(), (k, e, float(g[e]), float(r.max()))
