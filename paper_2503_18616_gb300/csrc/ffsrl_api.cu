@@ -268,6 +268,28 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, const Schedule& sc, MeshDev& d)
     FFSRL_CUDA(s->upload(&d_top, m.top.data(), m.top.size()));
     d.recs = d_recs;
     d.segs = d_segs;
+    if (sc.parts == 1 && d.Vp <= 4096) {
+        // the stream again with every slot field x 16 (a byte offset): edge
+        // records hold two slots in their first word, tet and connection
+        // records in their first two
+        std::vector<unsigned char> b16(sc.stream);
+        for (int c = 0; c < d.n_seg; ++c) {
+            const int32_t* sg = &sc.segs[4 * c];
+            const bool edge = c < sc.n_ephase;
+            const int rb = edge ? 8 : 16, words = edge ? 1 : 2;
+            for (int q = 0; q < sg[2]; ++q)
+                for (int w = 0; w < words; ++w) {
+                    uint32_t v;
+                    unsigned char* at = b16.data() + sg[0] + size_t(q) * rb + 4 * w;
+                    std::memcpy(&v, at, 4);
+                    v = ((v & 0xFFFFu) << 4) | (((v >> 16) << 4) << 16);
+                    std::memcpy(at, &v, 4);
+                }
+        }
+        unsigned char* d_b16;
+        FFSRL_CUDA(s->upload(&d_b16, b16.data(), b16.size()));
+        d.recs16 = d_b16;
+    }
     d.slot_of = d_slot;
     d.vert_of = d_vert;
     d.rest_w = d_rw;
@@ -403,8 +425,9 @@ size_t group_smem(const ffsrl_sim* s, const MeshDev& d, const StepConfig& c) {
     if (!step_config_supported(c.sub, c.envs, c.resident, c.ring, c.occ)) return 0;
     const size_t b = step_smem_bytes(d.Vp, c.resident, c.ring, d.ring_bytes, d.n_seg, c.envs);
     if (b + 256 > s->max_smem) return 0;  // room for the kernel's static shared memory
-    // the 4-CTA register budget only pays when four CTAs fit an SM's shared memory
-    if (c.occ && step_max_active(c, b) < c.occ) return 0;
+    // the 4-CTA register budget only pays when four CTAs fit an SM's shared
+    // memory; that build reads the byte-offset record stream
+    if (c.occ && (step_max_active(c, b) < c.occ || !d.recs16)) return 0;
     return b;
 }
 

@@ -29,6 +29,10 @@ struct MeshDev {
     int ring_bytes;                   // largest segment in bytes (one ring stage)
     int n_dseg;                       // edge and tet segments (the rest are tissue connections)
     const unsigned char* recs;        // constraint stream
+    // the same stream with every slot field holding the slot's byte offset
+    // (slot x 16), for meshes of at most 4096 slots in one part (else null):
+    // a record then addresses shared memory without a shift
+    const unsigned char* recs16;
     const int4* segs;                 // [n_seg] {byte offset, bytes, count, first constraint}
     const uint16_t* slot_of;          // [V] shared-memory slot of each vertex
     const uint16_t* vert_of;          // [V] vertex of each slot

@@ -15,6 +15,13 @@ struct SmemX {
     __device__ __forceinline__ float4 ld(int s) const { return p[s]; }
     __device__ __forceinline__ void st(int s, float4 v) const { p[s] = v; }
 };
+// The same positions reached by byte offset (slot x 16) instead of slot: for
+// the record stream whose slot fields hold byte offsets (MeshDev::recs16).
+struct SmemXB {
+    unsigned char* p;
+    __device__ __forceinline__ float4 ld(int off) const { return *reinterpret_cast<const float4*>(p + off); }
+    __device__ __forceinline__ void st(int off, float4 v) const { *reinterpret_cast<float4*>(p + off) = v; }
+};
 
 // Edge-distance constraint C = |x_a - x_b| - d in XPBD form (Eq. 1 with
 // compliance): dlambda = (-C - at lambda) / (w_a + w_b + at), x_a += w_a dlambda n,

@@ -23,6 +23,7 @@
 // project one colour in parallel and a barrier separates colours; the result
 // equals the sequential colour-by-colour Gauss-Seidel order.
 #include <cstdint>
+#include <type_traits>
 
 #include "xpbd_device.cuh"
 #include "xpbd_grasper.cuh"
@@ -129,6 +130,12 @@ __global__ void __launch_bounds__(SUB * ENVS, OCC ? OCC : min_ctas_per_sm(SUB * 
     const SmemLayout L(Vp, RES, RING, M.ring_bytes, n_seg, ENVS);
 
     float4* X = RES ? reinterpret_cast<float4*>(smem_raw + L.x_off) + size_t(el) * Vp : S.xg + ed.voff;
+    // The four-CTA build reads the record stream whose slot fields are byte
+    // offsets (its meshes have at most 4096 slots): no shift per vertex access.
+    constexpr bool BYTES = OCC == 4 && RES;
+    using Acc = typename std::conditional<BYTES, SmemXB, SmemX>::type;
+    const Acc XA{reinterpret_cast<decltype(Acc::p)>(X)};
+    const unsigned char* recs = BYTES ? M.recs16 : M.recs;
     unsigned char* ring = smem_raw + L.ring_off;
     int4* segs = reinterpret_cast<int4*>(smem_raw + L.seg_off);
     unsigned* bits = reinterpret_cast<unsigned*>(smem_raw + L.bits_off) + size_t(el) * (Vp / 32);
@@ -165,7 +172,7 @@ __global__ void __launch_bounds__(SUB * ENVS, OCC ? OCC : min_ctas_per_sm(SUB * 
     if (RING && tid == 0 && K > 0) {
         const int4 sg = segs[0];
         mbar_expect_tx(&mbar[0], uint32_t(sg.y));
-        bulk_copy_g2s(ring, M.recs + sg.x, uint32_t(sg.y), &mbar[0]);
+        bulk_copy_g2s(ring, recs + sg.x, uint32_t(sg.y), &mbar[0]);
     }
 
     const float h = S.h, inv_h = S.inv_h;
@@ -271,7 +278,7 @@ __global__ void __launch_bounds__(SUB * ENVS, OCC ? OCC : min_ctas_per_sm(SUB * 
         for (int it = 0; it < S.iterations && !failed; ++it) {
             for (int c = 0; c < n_seg; ++c, ++k) {
                 const int4 sg = segs[c];
-                const unsigned char* base = M.recs + sg.x;
+                const unsigned char* base = recs + sg.x;
                 bool ok = true;
                 if (RING) {
                     if (tid == 0 && k + 1 < K) {
@@ -280,7 +287,7 @@ __global__ void __launch_bounds__(SUB * ENVS, OCC ? OCC : min_ctas_per_sm(SUB * 
                         const int4 nx = segs[(c + 1 == n_seg) ? 0 : c + 1];
                         uint64_t* b = &mbar[(k + 1) & 1];
                         mbar_expect_tx(b, uint32_t(nx.y));
-                        bulk_copy_g2s(ring + ((k + 1) & 1) * M.ring_bytes, M.recs + nx.x, uint32_t(nx.y), b);
+                        bulk_copy_g2s(ring + ((k + 1) & 1) * M.ring_bytes, recs + nx.x, uint32_t(nx.y), b);
                     }
                     ok = mbar_wait_bounded(&mbar[k & 1], uint32_t((k >> 1) & 1));
                     base = ring + (k & 1) * M.ring_bytes;
@@ -296,12 +303,12 @@ __global__ void __launch_bounds__(SUB * ENVS, OCC ? OCC : min_ctas_per_sm(SUB * 
                         if (!carry) {
                             for (int q = st; q < sg.z; q += SUB) {
                                 float l = 0.f;
-                                project_edge(X, rec[q], at_d, M.min_len2, l);
+                                project_edge(XA, rec[q], at_d, M.min_len2, l);
                             }
                         } else {
                             for (int q = st; q < sg.z; q += SUB) {
                                 float l = lin ? lam[sg.w + q] : 0.f;
-                                project_edge(X, rec[q], at_d, M.min_len2, l);
+                                project_edge(XA, rec[q], at_d, M.min_len2, l);
                                 lam[sg.w + q] = l;
                             }
                         }
@@ -310,12 +317,12 @@ __global__ void __launch_bounds__(SUB * ENVS, OCC ? OCC : min_ctas_per_sm(SUB * 
                         if (!carry) {
                             for (int q = st; q < sg.z; q += SUB) {
                                 float l = 0.f;
-                                project_tet(X, rec[q], at_v, l);
+                                project_tet(XA, rec[q], at_v, l);
                             }
                         } else {
                             for (int q = st; q < sg.z; q += SUB) {
                                 float l = lin ? lam[sg.w + q] : 0.f;
-                                project_tet(X, rec[q], at_v, l);
+                                project_tet(XA, rec[q], at_v, l);
                                 lam[sg.w + q] = l;
                             }
                         }
@@ -324,7 +331,7 @@ __global__ void __launch_bounds__(SUB * ENVS, OCC ? OCC : min_ctas_per_sm(SUB * 
                         const uint4* rec = reinterpret_cast<const uint4*>(base);
                         for (int q = st; q < sg.z; q += SUB) {
                             float l = (carry && it > 0) ? lam[sg.w + q] : 0.f;
-                            project_conn(X, rec[q], at_d, M.min_len2, l);
+                            project_conn(XA, rec[q], at_d, M.min_len2, l);
                             if (carry) lam[sg.w + q] = l;
                         }
                     }
