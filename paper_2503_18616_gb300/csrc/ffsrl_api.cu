@@ -606,29 +606,32 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
     FFSRL_CUDA(cudaMemset(s->d_net_err, 0, sizeof(int)));
 
     // Schedules of every mesh in both variants, built on host threads
-    // (largest meshes first; the bank-aware variant searches for a while).
+    // (largest meshes first). The bank-aware variant searches for a while and
+    // chooses each tet's vertex order; the mesh keeps those orders, so the
+    // plain-order variant, built second, and the cluster variant use them too
+    // and every schedule gives the same bits.
     const int n_mesh = int(s->meshes.size());
     std::vector<Schedule> sched(2 * size_t(n_mesh));
-    {
-        std::vector<int> jobs(2 * n_mesh);
-        for (int j = 0; j < 2 * n_mesh; ++j) jobs[j] = j;
-        std::stable_sort(jobs.begin(), jobs.end(), [&](int a, int b) {
-            return s->meshes[a / 2].V + (a & 1) * (1 << 30) > s->meshes[b / 2].V + (b & 1) * (1 << 30);
-        });
+    for (int v = 1; v >= 0; --v) {
+        std::vector<int> jobs(n_mesh);
+        for (int mi = 0; mi < n_mesh; ++mi) jobs[mi] = mi;
+        std::stable_sort(jobs.begin(), jobs.end(),
+                         [&](int a, int b) { return s->meshes[a].V > s->meshes[b].V; });
         std::atomic<int> next{0};
         auto work = [&]() {
-            for (int q; (q = next.fetch_add(1)) < 2 * n_mesh;) {
-                const int j = jobs[q];
-                const HostMesh& m = s->meshes[j / 2];
-                build_schedule(m, 0x5EEDull + uint64_t(m.V), (j & 1) == 1, sched[j]);
+            for (int q; (q = next.fetch_add(1)) < n_mesh;) {
+                const HostMesh& m = s->meshes[jobs[q]];
+                build_schedule(m, 0x5EEDull + uint64_t(m.V), v == 1, sched[2 * jobs[q] + v]);
             }
         };
         const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-        const int n_thr = int(std::min<unsigned>(hw, unsigned(2 * n_mesh)));
+        const int n_thr = int(std::min<unsigned>(hw, unsigned(n_mesh)));
         std::vector<std::thread> pool;
         for (int t = 1; t < n_thr; ++t) pool.emplace_back(work);
         work();
         for (std::thread& t : pool) t.join();
+        if (v == 1)
+            for (int mi = 0; mi < n_mesh; ++mi) s->meshes[mi].tet_rot = sched[2 * mi + 1].tet_rot;
     }
     for (int v = 0; v < 2; ++v) {
         s->h_meshes[v].resize(s->meshes.size());

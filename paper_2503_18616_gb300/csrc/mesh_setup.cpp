@@ -12,6 +12,9 @@
 #include "../../include/ffsrl.h"
 
 namespace ffsrl {
+
+const int kEvenPerm[12][4] = {{0, 1, 2, 3}, {1, 0, 3, 2}, {2, 3, 0, 1}, {3, 2, 1, 0}, {0, 2, 3, 1}, {0, 3, 1, 2},
+                              {1, 2, 0, 3}, {2, 0, 1, 3}, {1, 3, 2, 0}, {3, 0, 2, 1}, {2, 1, 3, 0}, {3, 1, 0, 2}};
 namespace {
 
 constexpr int kColourWords = 4;  // up to 256 colours per constraint family
@@ -297,8 +300,9 @@ namespace {
 // changes results: a colour's constraints touch disjoint vertices.
 
 // A record while it is being placed: the slots of its vertices in positions
-// 0 .. ARITY-1 and the constraint index in position 4.
-using Rec = std::array<int, 5>;
+// 0 .. ARITY-1, the constraint index in position 4 and (tets) the index of
+// its vertex order in kEvenPerm in position 5.
+using Rec = std::array<int, 6>;
 
 // Cost of one group of records: for each vertex position, the largest number
 // of records sharing a bank group (1 = conflict-free).
@@ -362,8 +366,20 @@ std::vector<Rec> group_greedy(const std::vector<Rec>& recs, bool flip) {
 // Local search: move a conflicting record of a conflicted group into a random
 // other group (swapping with one of its records, an edge record flipped if
 // that helps) whenever the two groups' cost does not rise.
+// Index in kEvenPerm of the permutation q[k] = p[e[k]] (p = kEvenPerm[a], e = kEvenPerm[b]).
+int compose_even(int a, int b) {
+    int q[4];
+    for (int k = 0; k < 4; ++k) q[k] = kEvenPerm[a][kEvenPerm[b][k]];
+    for (int r = 0; r < 12; ++r)
+        if (std::equal(q, q + 4, kEvenPerm[r])) return r;
+    return 0;   // not reached: even permutations compose to an even permutation
+}
+
+// With `rot` (tets), half of the moves instead apply an even permutation to
+// the vertex order of a record of a conflicted group, kept when the group's
+// cost does not rise.
 template <int ARITY>
-void group_improve(std::vector<Rec>& g, std::mt19937_64& rng, long long iters, bool flip) {
+void group_improve(std::vector<Rec>& g, std::mt19937_64& rng, long long iters, bool flip, bool rot = false) {
     const int n = int(g.size()), G = (n + 7) / 8;
     if (G < 2) return;
     auto size_of = [&](int a) { return std::min(8, n - 8 * a); };
@@ -377,6 +393,16 @@ void group_improve(std::vector<Rec>& g, std::mt19937_64& rng, long long iters, b
             if (bad.empty()) return;
         }
         const int a = bad[rng() % bad.size()], b = int(rng() % G);
+        if (ARITY == 4 && rot && (rng() & 1)) {
+            const int i = 8 * a + int(rng() % size_of(a)), e = 1 + int(rng() % 11);
+            const Rec old = g[i];
+            for (int k = 0; k < 4; ++k) g[i][k] = old[kEvenPerm[e][k]];
+            g[i][5] = compose_even(old[5], e);
+            const int c = group_cost<ARITY>(&g[8 * a], size_of(a));
+            if (c <= cost[a]) cost[a] = c;
+            else g[i] = old;
+            continue;
+        }
         if (a == b) continue;
         // a record of group a that shares its bank group with another record
         // of the group in some position (scanning from random ones)
@@ -623,12 +649,16 @@ void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& ou
         out.slot_of[i] = uint16_t(slot[i]);
         out.vert_of[slot[i]] = uint16_t(i);
     }
+    // the mesh's tet vertex orders (identity unless a refined schedule chose
+    // them); a refined schedule may change them below
+    out.tet_rot.assign(size_t(m.T), 0);
+    if (m.tet_rot.size() == size_t(m.T)) out.tet_rot = m.tet_rot;
     const int P = out.part_slots;
     int first = 0;   // multiplier slot of the next record
     for (const std::vector<int>& phase : eph) {
         std::vector<std::vector<Rec>> part(parts);
         for (int e : phase) {
-            const Rec r = {out.slot_of[m.edge[2 * e]], out.slot_of[m.edge[2 * e + 1]], 0, 0, e};
+            const Rec r = {out.slot_of[m.edge[2 * e]], out.slot_of[m.edge[2 * e + 1]], 0, 0, e, 0};
             part[r[0] / P].push_back(r);
         }
         for (std::vector<Rec>& r : part) {
@@ -652,8 +682,11 @@ void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& ou
     for (const std::vector<int>& phase : tph) {
         std::vector<std::vector<Rec>> part(parts);
         for (int t : phase) {
-            const Rec r = {out.slot_of[m.tet[4 * t]], out.slot_of[m.tet[4 * t + 1]], out.slot_of[m.tet[4 * t + 2]],
-                           out.slot_of[m.tet[4 * t + 3]], t};
+            const int rt = out.tet_rot[t];
+            Rec r{};
+            for (int k = 0; k < 4; ++k) r[k] = out.slot_of[m.tet[4 * t + kEvenPerm[rt][k]]];
+            r[4] = t;
+            r[5] = rt;
             part[r[0] / P].push_back(r);
         }
         for (std::vector<Rec>& r : part) {
@@ -661,7 +694,10 @@ void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& ou
             if (permute) {
                 r = group_greedy<4>(r, false);
                 group_improve<4>(r, rng, search * n, false);
+                // the refined schedule also chooses each tet's vertex order
+                if (unit > 0) group_improve<4>(r, rng, search * n, false, true);
             }
+            for (const Rec& q : r) out.tet_rot[q[4]] = uint8_t(q[5]);
             std::vector<uint32_t> buf(4 * size_t(n));
             for (int j = 0; j < n; ++j) {
                 float v0 = m.V0[r[j][4]];
@@ -681,7 +717,7 @@ void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& ou
         std::vector<std::vector<Rec>> part(parts);
         for (int k : phase) {
             const Rec r = {out.slot_of[m.conn[4 * k]], out.slot_of[m.conn[4 * k + 1]], out.slot_of[m.conn[4 * k + 2]],
-                           out.slot_of[m.conn[4 * k + 3]], k};
+                           out.slot_of[m.conn[4 * k + 3]], k, 0};
             part[r[0] / P].push_back(r);
         }
         for (std::vector<Rec>& r : part) {

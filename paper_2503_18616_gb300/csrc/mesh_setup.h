@@ -43,7 +43,16 @@ struct HostMesh {
     std::vector<int32_t> ccolor, corder, ccol_off;
     double bbmin[3] = {0, 0, 0}, bbmax[3] = {0, 0, 0};
     double extent = 0;
+    // Order of each tet's vertices in the GPU's records: an even permutation
+    // of tet[4t .. 4t+3] (index into kEvenPerm; empty = all identity). The
+    // signed volume, hence V0, is unchanged; the bank-aware schedule chooses
+    // them and every schedule of the mesh then uses the same order.
+    std::vector<uint8_t> tet_rot;
 };
+
+// The 12 even permutations of four positions (row 0 the identity): record
+// position k holds tet vertex kEvenPerm[r][k].
+extern const int kEvenPerm[12][4];
 
 // Returns 0 or a negative FFSRL_E_* code with a message in err.
 // conn_radius > 0 adds tissue connections between the mesh's objects.
@@ -69,6 +78,7 @@ struct Schedule {
     int parts = 1;                           // segments per colour (one per cluster CTA)
     int part_slots = 0;                      // slots per part (multiple of 32)
     int n_ephase = 0, n_tphase = 0, n_cphase = 0;   // phases per family
+    std::vector<uint8_t> tet_rot;            // [T] the vertex orders the tet records use
 };
 
 constexpr int kPhaseUnit = 256;              // threads per env of the common step configuration

@@ -64,14 +64,16 @@ int main(int argc, char** argv) {
         return 0;
     }
     // constraint lookup by sorted vertex tuple -> (family, colour)
-    std::map<std::array<int, 4>, int> ecol, tcol, ccol;
+    std::map<std::array<int, 4>, int> ecol, tcol, ccol, tidx;
     for (int e = 0; e < m.E; ++e) ecol[{m.edge[2 * e], m.edge[2 * e + 1], -1, -1}] = m.ecolor[e];
     for (int t = 0; t < m.T; ++t) {
         std::array<int, 4> k = {m.tet[4 * t], m.tet[4 * t + 1], m.tet[4 * t + 2], m.tet[4 * t + 3]};
         std::sort(k.begin(), k.end());
         tcol[k] = m.tcolor[t];
+        tidx[k] = t;
     }
     for (int c = 0; c < m.C; ++c) ccol[{m.conn[4 * c], m.conn[4 * c + 1], m.conn[4 * c + 2], m.conn[4 * c + 3]}] = m.ccolor[c];
+    long long rotated[2] = {0, 0};   // tets of the bank-aware schedule in their own / another order
     for (int perm = 0; perm < 2; ++perm) {
         Schedule sc;
         build_schedule(m, 0x5EEDull + uint64_t(m.V), perm == 1, sc);
@@ -105,7 +107,24 @@ int main(int argc, char** argv) {
                 } else if (fam == 1) {
                     std::sort(key.begin(), key.end());
                     auto it = tcol.find(key);
-                    if (it != tcol.end()) col = it->second;
+                    if (it != tcol.end()) {
+                        col = it->second;
+                        // the record's vertex order: the tet's under the schedule's
+                        // even permutation (same signed volume)
+                        const int t = tidx[key];
+                        if (sc.tet_rot.size() != size_t(m.T) || sc.tet_rot[t] >= 12) {
+                            ok = false;
+                        } else {
+                            int inv = 0;
+                            for (int a = 0; a < 4; ++a) {
+                                if (v[a] != m.tet[4 * t + kEvenPerm[sc.tet_rot[t]][a]]) ok = false;
+                                for (int b = a + 1; b < 4; ++b)
+                                    inv += kEvenPerm[sc.tet_rot[t]][a] > kEvenPerm[sc.tet_rot[t]][b];
+                            }
+                            if (inv % 2) ok = false;
+                            if (perm == 1) ++rotated[sc.tet_rot[t] != 0];
+                        }
+                    }
                 } else {
                     auto it = ccol.find(key);
                     if (it != ccol.end()) col = it->second;
@@ -128,5 +147,6 @@ int main(int argc, char** argv) {
         std::printf("permute %d phases %d %d %d colours %d %d %d rounds %lld ok %d\n", perm, sc.n_ephase, sc.n_tphase,
                     sc.n_cphase, m.n_ecol, m.n_tcol, m.n_ccol, rounds, int(ok));
     }
+    std::printf("rotated %lld %lld\n", rotated[0], rotated[1]);
     return 0;
 }

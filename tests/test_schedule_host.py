@@ -7,7 +7,10 @@ checked on grid blocks and a connected two-object scene.
 For both slot orders every constraint lies in exactly one record, every phase
 is vertex-disjoint, and every vertex meets its constraints in colour order,
 so the GPU's phases give the bits of the colour-by-colour Gauss-Seidel sweep.
-On the 17x17x9 block the refined phases cut the thread rounds of 256."""
+On the 17x17x9 block the refined phases cut the thread rounds of 256.
+Every tet record lists its tet's vertices in an even permutation of the
+mesh's order (the signed volume and V0 unchanged): the one the schedule
+reports, which the bank-aware schedule chooses."""
 import os
 import re
 import shutil
@@ -45,6 +48,10 @@ def _run(exe, mesh, conn_radius=0.0):
                          check=True).stdout
     rows = {}
     for line in out.splitlines():
+        r = re.match(r"rotated (\d+) (\d+)", line)
+        if r:   # bank-aware schedule's tets in their own vertex order / in another even order
+            rows["rotated"] = (int(r.group(1)), int(r.group(2)))
+            continue
         m = re.match(r"permute (\d) phases (\d+) (\d+) (\d+) colours (\d+) (\d+) (\d+) rounds (\d+) ok (\d)", line)
         assert m, line
         g = [int(x) for x in m.groups()]
@@ -60,6 +67,9 @@ def test_phases_keep_colour_order_on_grid_blocks(checker, shape):
     if shape == (17, 17, 9):
         assert rows[1]["phases"][:2] == [31, 43]              # 512-edge / 256-tet phases
         assert rows[1]["rounds"] == 98 and rows[0]["rounds"] == 130
+        # the refined schedule reorders some tets' vertices (even permutations,
+        # checked record by record above) to spread bank groups
+        assert rows["rotated"][1] > 0
 
 
 def test_phases_keep_colour_order_with_connections(checker):
