@@ -83,6 +83,42 @@ struct TuneChoice {
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneChoice> g_tune_cache;
 
+// Schedules built in this process, keyed by everything build_schedule reads
+// (the mesh's positions, masses, tets, connections and tet vertex orders,
+// the seed, the variant and the parts): the bank-aware search takes seconds
+// on larger meshes, and a process often creates several simulators of one mesh.
+std::mutex g_sched_mu;
+std::map<std::string, Schedule> g_sched_cache;
+
+template <class T>
+void key_append(std::string& k, const std::vector<T>& v) {
+    const size_t n = v.size();
+    k.append(reinterpret_cast<const char*>(&n), sizeof n);
+    k.append(reinterpret_cast<const char*>(v.data()), v.size() * sizeof(T));
+}
+
+void cached_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& out, int parts = 1) {
+    std::string key;
+    const long long head[8] = {m.V, m.T, m.E, m.C, (long long)seed, permute, parts, 0};
+    key.append(reinterpret_cast<const char*>(head), sizeof head);
+    key_append(key, m.rest);
+    key_append(key, m.inv_mass);
+    key_append(key, m.tet);
+    key_append(key, m.conn);
+    key_append(key, m.tet_rot);
+    {
+        std::lock_guard<std::mutex> lk(g_sched_mu);
+        auto it = g_sched_cache.find(key);
+        if (it != g_sched_cache.end()) {
+            out = it->second;
+            return;
+        }
+    }
+    build_schedule(m, seed, permute, out, parts);
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    g_sched_cache.emplace(std::move(key), out);
+}
+
 const int kSubs[] = {128, 256, 384, 512};
 const int kEnvsPerCta[] = {1, 2, 4};
 
@@ -621,7 +657,7 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
         auto work = [&]() {
             for (int q; (q = next.fetch_add(1)) < n_mesh;) {
                 const HostMesh& m = s->meshes[jobs[q]];
-                build_schedule(m, 0x5EEDull + uint64_t(m.V), v == 1, sched[2 * jobs[q] + v]);
+                cached_schedule(m, 0x5EEDull + uint64_t(m.V), v == 1, sched[2 * jobs[q] + v]);
             }
         };
         const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
@@ -771,7 +807,7 @@ int build_device(ffsrl_sim* s, const double* env_alpha) {
         auto work = [&]() {
             for (int q; (q = next.fetch_add(1)) < int(todo.size());) {
                 const HostMesh& m = s->meshes[todo[q]];
-                build_schedule(m, 0x5EEDull + uint64_t(m.V), true, sc[q], -mesh_class[todo[q]]);
+                cached_schedule(m, 0x5EEDull + uint64_t(m.V), true, sc[q], -mesh_class[todo[q]]);
             }
         };
         const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
