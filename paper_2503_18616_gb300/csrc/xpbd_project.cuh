@@ -23,6 +23,21 @@ struct SmemXB {
     __device__ __forceinline__ void st(int off, float4 v) const { *reinterpret_cast<float4*>(p + off) = v; }
 };
 
+// The hardware's reciprocal and reciprocal-square-root estimates (PTX
+// rcp.approx.ftz / rsqrt.approx.ftz, flushing subnormals): the projections'
+// operands are normal numbers (|x_ab|^2 is at least min_len2, denominators
+// are sums of inverse masses and compliances).
+__device__ __forceinline__ float rcp_est(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_est(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Edge-distance constraint C = |x_a - x_b| - d in XPBD form (Eq. 1 with
 // compliance): dlambda = (-C - at lambda) / (w_a + w_b + at), x_a += w_a dlambda n,
 // x_b -= w_b dlambda n, n = (x_a - x_b) / |x_a - x_b|. Applied to register
@@ -34,10 +49,10 @@ __device__ __forceinline__ bool edge_update(float4& xa, float4& xb, float d, flo
     const float l2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
     const float denom = __fadd_rn(__fadd_rn(xa.w, xb.w), at);
     if (l2 < min_len2 || denom == 0.f) return false;
-    const float il = rsqrtf(l2);               // 1/|x_ab| (hardware estimate, within 2 ulp)
+    const float il = rsqrt_est(l2);            // 1/|x_ab| (hardware estimate)
     const float len = __fmul_rn(l2, il);
     const float C = __fsub_rn(len, d);
-    const float dl = __fdividef(__fmaf_rn(-at, lam, -C), denom);
+    const float dl = __fmul_rn(__fmaf_rn(-at, lam, -C), rcp_est(denom));
     const float s = __fmul_rn(dl, il);
     const float sa = __fmul_rn(xa.w, s), sb = __fmul_rn(xb.w, s);
     xa.x = __fmaf_rn(sa, dx, xa.x); xa.y = __fmaf_rn(sa, dy, xa.y); xa.z = __fmaf_rn(sa, dz, xa.z);
@@ -95,7 +110,7 @@ __device__ __forceinline__ bool tet_update(float4& xa, float4& xb, float4& xc, f
                                                                           __fmul_rn(xa.w, dot3_rn(g0, g0)))));
     const float denom = __fmaf_rn(sw, 1.0f / 36.0f, at);
     if (denom == 0.f) return false;
-    const float dl = __fdividef(__fmaf_rn(-at, lam, -C), denom);
+    const float dl = __fmul_rn(__fmaf_rn(-at, lam, -C), rcp_est(denom));
     const float s = __fmul_rn(dl, 1.0f / 6.0f);
     const float sa = __fmul_rn(xa.w, s), sb = __fmul_rn(xb.w, s), sc = __fmul_rn(xc.w, s), sd = __fmul_rn(xd.w, s);
     xa.x = __fmaf_rn(sa, g0.x, xa.x); xa.y = __fmaf_rn(sa, g0.y, xa.y); xa.z = __fmaf_rn(sa, g0.z, xa.z);
