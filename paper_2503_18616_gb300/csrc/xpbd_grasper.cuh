@@ -204,8 +204,11 @@ __device__ __forceinline__ bool face_out_of_reach(float3 a, float3 b, float3 c, 
 __device__ __forceinline__ void grasper_face(float4* X, uint4 rec, const Capsules& K, float tiny_len, unsigned* bits,
                                           const uint16_t* vert_of) {
     const int ia = int(rec.x & 0xffffu), ib = int(rec.x >> 16), ic = int(rec.y & 0xffffu), io = int(rec.y >> 16);
+    // loaded once: only this thread moves the face's vertices while it
+    // processes the face (faces of one colour share no vertex), so after a push
+    // the registers hold what the next capsule would read back
+    float4 xa = X[ia], xb = X[ib], xc = X[ic];
     for (int k = 0; k < 3; ++k) {
-        float4 xa = X[ia], xb = X[ib], xc = X[ic];
         const float3 a = make_float3(xa.x, xa.y, xa.z), b = make_float3(xb.x, xb.y, xb.z), c = make_float3(xc.x, xc.y, xc.z);
         const float3 q0 = make_float3(K.a[k][0], K.a[k][1], K.a[k][2]), q1 = make_float3(K.b[k][0], K.b[k][1], K.b[k][2]);
         if (face_out_of_reach(a, b, c, q0, q1, K.r[k])) continue;
