@@ -434,14 +434,10 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, const Schedule& sc, MeshDev& d)
     d.rcm[1] = float((m.bbmin[1] + m.bbmax[1]) / 2);
     d.rcm[2] = float(m.bbmax[2] + p.rcm_height);
     {
-        // surface faces in colour-major order, as slots
+        // surface faces in colour-major order, as slots (the schedule's records)
         std::vector<uint4> fr(std::max(1, m.F));
-        for (int q = 0; q < m.F; ++q) {
-            const int f = m.forder[q];
-            const int a = sc.slot_of[m.face[3 * f]], b = sc.slot_of[m.face[3 * f + 1]];
-            const int c = sc.slot_of[m.face[3 * f + 2]], o = sc.slot_of[m.fopp[f]];
-            fr[q] = make_uint4(uint32_t(a) | (uint32_t(b) << 16), uint32_t(c) | (uint32_t(o) << 16), 0u, 0u);
-        }
+        for (int q = 0; q < m.F; ++q)
+            fr[q] = make_uint4(sc.frec[4 * size_t(q)], sc.frec[4 * size_t(q) + 1], 0u, 0u);
         uint4* d_fr;
         int* d_fo;
         FFSRL_CUDA(s->upload(&d_fr, fr.data(), fr.size()));

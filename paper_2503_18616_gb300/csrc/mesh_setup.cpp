@@ -742,6 +742,26 @@ void build_schedule(const HostMesh& m, uint64_t seed, bool permute, Schedule& ou
             first += n;
         }
     }
+    // Surface faces for the grasper, colour by colour (faces of one colour
+    // share no vertex, so their order inside a colour is free).
+    out.frec.assign(4 * size_t(m.F), 0u);
+    for (int fc = 0; fc < m.n_fcol; ++fc) {
+        std::vector<Rec> r;
+        for (int q = m.fcol_off[fc]; q < m.fcol_off[fc + 1]; ++q) {
+            const int f = m.forder[q];
+            r.push_back({out.slot_of[m.face[3 * f]], out.slot_of[m.face[3 * f + 1]], out.slot_of[m.face[3 * f + 2]],
+                         out.slot_of[m.fopp[f]], f, 0});
+        }
+        if (permute && r.size() > 8) {
+            r = group_greedy<3>(r, false);
+            group_improve<3>(r, rng, search * static_cast<long long>(r.size()), false);
+        }
+        for (size_t j = 0; j < r.size(); ++j) {
+            uint32_t* o = &out.frec[4 * (size_t(m.fcol_off[fc]) + j)];
+            o[0] = uint32_t(r[j][0]) | (uint32_t(r[j][1]) << 16);
+            o[1] = uint32_t(r[j][2]) | (uint32_t(r[j][3]) << 16);
+        }
+    }
 }
 
 }  // namespace ffsrl

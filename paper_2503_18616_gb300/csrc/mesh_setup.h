@@ -79,6 +79,11 @@ struct Schedule {
     int part_slots = 0;                      // slots per part (multiple of 32)
     int n_ephase = 0, n_tphase = 0, n_cphase = 0;   // phases per family
     std::vector<uint8_t> tet_rot;            // [T] the vertex orders the tet records use
+    // [F][4] surface-face records for the grasper, colour-major like
+    // HostMesh::forder (same colour sizes): slot(a) | slot(b) << 16,
+    // slot(c) | slot(opposite vertex) << 16, 0, 0; with the permutation each
+    // colour's faces are grouped in 8s by bank groups of a, b and c
+    std::vector<uint32_t> frec;
 };
 
 constexpr int kPhaseUnit = 256;              // threads per env of the common step configuration

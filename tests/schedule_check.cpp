@@ -144,6 +144,34 @@ int main(int argc, char** argv) {
                     if (pr.first[k] >= 0) last[pr.first[k]] = pr.second;
         }
         if (records != m.E + m.T + m.C) ok = false;
+        // grasper face records: colour by colour, every face of the colour
+        // once (with its opposite vertex), no vertex twice in a colour
+        if (sc.frec.size() != 4 * size_t(m.F)) ok = false;
+        std::map<std::array<int, 3>, int> face_of;
+        for (int f = 0; f < m.F; ++f) {
+            std::array<int, 3> k = {m.face[3 * f], m.face[3 * f + 1], m.face[3 * f + 2]};
+            std::sort(k.begin(), k.end());
+            face_of[k] = f;
+        }
+        std::vector<int> face_seen(m.F, 0), fcol(m.F, -1);
+        for (int fc = 0; fc < m.n_fcol; ++fc)
+            for (int q = m.fcol_off[fc]; q < m.fcol_off[fc + 1]; ++q) fcol[m.forder[q]] = fc;
+        for (int fc = 0; fc < m.n_fcol && sc.frec.size() == 4 * size_t(m.F); ++fc) {
+            std::vector<char> used(V, 0);
+            for (int q = m.fcol_off[fc]; q < m.fcol_off[fc + 1]; ++q) {
+                const uint32_t* r = &sc.frec[4 * size_t(q)];
+                std::array<int, 3> k = {sc.vert_of[r[0] & 0xffffu], sc.vert_of[r[0] >> 16], sc.vert_of[r[1] & 0xffffu]};
+                for (int v : k) {
+                    if (used[v]) ok = false;
+                    used[v] = 1;
+                }
+                std::sort(k.begin(), k.end());
+                auto it = face_of.find(k);
+                if (it == face_of.end() || fcol[it->second] != fc || ++face_seen[it->second] != 1 ||
+                    sc.vert_of[r[1] >> 16] != m.fopp[it->second])
+                    ok = false;
+            }
+        }
         std::printf("permute %d phases %d %d %d colours %d %d %d rounds %lld ok %d\n", perm, sc.n_ephase, sc.n_tphase,
                     sc.n_cphase, m.n_ecol, m.n_tcol, m.n_ccol, rounds, int(ok));
     }
