@@ -23,6 +23,9 @@ namespace ffsrl {
 struct Capsules {
     float a[3][3], b[3][3];   // segment ends of shaft, clamp +, clamp -
     float r[3];
+    // for the faces' reach test: axis b - a, 1 / |b - a|^2 (0 for a point),
+    // and the largest coordinate magnitude of a plus that of b
+    float ax[3][3], inv_la2[3], qscale[3];
 };
 
 // Every product and sum below is rounded on its own (no fused multiply-add),
@@ -81,6 +84,14 @@ __device__ __forceinline__ void grasper_capsules(const SimDev& S, const MeshDev&
     }
     K.r[0] = S.shaft_radius;
     K.r[1] = K.r[2] = S.clamp_radius;
+    for (int k = 0; k < 3; ++k) {
+        const float3 ax = make_float3(B[k].x - A[k].x, B[k].y - A[k].y, B[k].z - A[k].z);
+        const float la2 = ax.x * ax.x + ax.y * ax.y + ax.z * ax.z;
+        K.ax[k][0] = ax.x; K.ax[k][1] = ax.y; K.ax[k][2] = ax.z;
+        K.inv_la2[k] = la2 > 0.f ? 1.f / la2 : 0.f;
+        K.qscale[k] = fmaxf(fmaxf(fabsf(A[k].x), fabsf(A[k].y)), fabsf(A[k].z)) +
+                      fmaxf(fmaxf(fabsf(B[k].x), fabsf(B[k].y)), fabsf(B[k].z));
+    }
 }
 
 // Closest point of triangle (a, b, c) to x: barycentric weights w.
@@ -172,30 +183,40 @@ __device__ __forceinline__ float seg_tri_closest(float3 q0, float3 q1, float3 a,
     return best;
 }
 
-// Whether the face (a, b, c) lies certainly farther than r from segment
-// q0-q1: the distance from the face's centroid g to the segment, less the
-// radius of the face's bounding sphere about g, is at least r plus a margin
-// of 1e-3 r + 1e-5 x (the largest coordinate of g, q0 and q1). The second
-// term is about a hundred times the rounding error of these sums and of the
-// exact closest-point distance (a few ulp of the coordinates), so a face this
-// test rejects is one the exact test below would leave alone: skipping it
-// does not change any bit.
-__device__ __forceinline__ bool face_out_of_reach(float3 a, float3 b, float3 c, float3 q0, float3 q1, float r) {
-    const float3 g = make_float3((a.x + b.x + c.x) * (1.f / 3.f), (a.y + b.y + c.y) * (1.f / 3.f),
-                                 (a.z + b.z + c.z) * (1.f / 3.f));
-    const float3 ga = make_float3(a.x - g.x, a.y - g.y, a.z - g.z), gb = make_float3(b.x - g.x, b.y - g.y, b.z - g.z),
-                 gc = make_float3(c.x - g.x, c.y - g.y, c.z - g.z);
-    const float rho2 = fmaxf(fmaxf(ga.x * ga.x + ga.y * ga.y + ga.z * ga.z, gb.x * gb.x + gb.y * gb.y + gb.z * gb.z),
-                             gc.x * gc.x + gc.y * gc.y + gc.z * gc.z);
-    const float3 ax = make_float3(q1.x - q0.x, q1.y - q0.y, q1.z - q0.z), rg = make_float3(g.x - q0.x, g.y - q0.y, g.z - q0.z);
-    const float la2 = ax.x * ax.x + ax.y * ax.y + ax.z * ax.z;
-    float t = la2 > 0.f ? (rg.x * ax.x + rg.y * ax.y + rg.z * ax.z) / la2 : 0.f;
+// Bounding sphere of face (a, b, c) about its centroid g, with the largest
+// coordinate magnitude of g (for the reach test's margin).
+struct FaceSphere {
+    float3 g;
+    float rho, gmax;
+};
+__device__ __forceinline__ FaceSphere face_sphere(float3 a, float3 b, float3 c) {
+    FaceSphere F;
+    F.g = make_float3((a.x + b.x + c.x) * (1.f / 3.f), (a.y + b.y + c.y) * (1.f / 3.f), (a.z + b.z + c.z) * (1.f / 3.f));
+    const float3 ga = make_float3(a.x - F.g.x, a.y - F.g.y, a.z - F.g.z),
+                 gb = make_float3(b.x - F.g.x, b.y - F.g.y, b.z - F.g.z),
+                 gc = make_float3(c.x - F.g.x, c.y - F.g.y, c.z - F.g.z);
+    F.rho = sqrtf(fmaxf(fmaxf(ga.x * ga.x + ga.y * ga.y + ga.z * ga.z, gb.x * gb.x + gb.y * gb.y + gb.z * gb.z),
+                        gc.x * gc.x + gc.y * gc.y + gc.z * gc.z));
+    F.gmax = fmaxf(fmaxf(fabsf(F.g.x), fabsf(F.g.y)), fabsf(F.g.z));
+    return F;
+}
+
+// Whether the face lies certainly farther than r_k from capsule k's axis
+// segment: the distance from the face's centroid to the segment, less the
+// radius of the face's bounding sphere, is at least r_k plus a margin of
+// 1e-3 r_k + 1e-5 x (the largest coordinate of g, plus those of the segment's
+// ends). The second term is about a hundred times the rounding error of these
+// sums and of the exact closest-point distance (a few ulp of the
+// coordinates), so a face this test rejects is one the exact test below
+// would leave alone: skipping it does not change any bit.
+__device__ __forceinline__ bool face_out_of_reach(const FaceSphere& F, const Capsules& K, int k) {
+    const float3 ax = make_float3(K.ax[k][0], K.ax[k][1], K.ax[k][2]);
+    const float3 rg = make_float3(F.g.x - K.a[k][0], F.g.y - K.a[k][1], F.g.z - K.a[k][2]);
+    float t = (rg.x * ax.x + rg.y * ax.y + rg.z * ax.z) * K.inv_la2[k];
     t = t < 0.f ? 0.f : (t > 1.f ? 1.f : t);
     const float3 dv = make_float3(rg.x - t * ax.x, rg.y - t * ax.y, rg.z - t * ax.z);
     const float d = sqrtf(dv.x * dv.x + dv.y * dv.y + dv.z * dv.z);
-    const float scale = fmaxf(fmaxf(fabsf(g.x), fabsf(g.y)), fabsf(g.z)) + fmaxf(fmaxf(fabsf(q0.x), fabsf(q0.y)), fabsf(q0.z)) +
-                        fmaxf(fmaxf(fabsf(q1.x), fabsf(q1.y)), fabsf(q1.z));
-    return d - sqrtf(rho2) >= r * 1.001f + 1e-5f * scale;
+    return d - F.rho >= K.r[k] * 1.001f + 1e-5f * (F.gmax + K.qscale[k]);
 }
 
 // Pushes one surface face out of the three capsules (shaft, then clamps).
@@ -208,10 +229,12 @@ __device__ __forceinline__ void grasper_face(float4* X, uint4 rec, const Capsule
     // processes the face (faces of one colour share no vertex), so after a push
     // the registers hold what the next capsule would read back
     float4 xa = X[ia], xb = X[ib], xc = X[ic];
+    // the face's bounding sphere, computed again after a push moves the face
+    FaceSphere F = face_sphere(make_float3(xa.x, xa.y, xa.z), make_float3(xb.x, xb.y, xb.z), make_float3(xc.x, xc.y, xc.z));
     for (int k = 0; k < 3; ++k) {
+        if (face_out_of_reach(F, K, k)) continue;
         const float3 a = make_float3(xa.x, xa.y, xa.z), b = make_float3(xb.x, xb.y, xb.z), c = make_float3(xc.x, xc.y, xc.z);
         const float3 q0 = make_float3(K.a[k][0], K.a[k][1], K.a[k][2]), q1 = make_float3(K.b[k][0], K.b[k][1], K.b[k][2]);
-        if (face_out_of_reach(a, b, c, q0, q1, K.r[k])) continue;
         float w[3];
         float3 q;
         const float dist = seg_tri_closest(q0, q1, a, b, c, w, q);
@@ -250,6 +273,7 @@ __device__ __forceinline__ void grasper_face(float4* X, uint4 rec, const Capsule
         X[ia] = xa;
         X[ib] = xb;
         X[ic] = xc;
+        F = face_sphere(make_float3(xa.x, xa.y, xa.z), make_float3(xb.x, xb.y, xb.z), make_float3(xc.x, xc.y, xc.z));
         if (bits) {
             const int sl[3] = {ia, ib, ic};
             const float wv[3] = {xa.w, xb.w, xc.w};
