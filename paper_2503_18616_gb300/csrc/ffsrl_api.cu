@@ -327,6 +327,13 @@ int upload_mesh(ffsrl_sim* s, const HostMesh& m, const Schedule& sc, MeshDev& d)
         d.recs16 = d_b16;
     }
     d.slot_of = d_slot;
+    {
+        // the warm-start network skips leading 128-slot tiles of pinned vertices
+        // (their corrections are never applied)
+        int q = 0;
+        while (q < m.V && !(m.inv_mass[sc.vert_of[q]] > 0.f)) ++q;
+        d.first_free_tile = q / 128;
+    }
     d.vert_of = d_vert;
     d.rest_w = d_rw;
     d.top = d_top;

@@ -57,7 +57,7 @@ struct MeshDev {
     const uint4* frec;
     const int* fcol_off;              // [n_fcol + 1]
     float rcm[3];                     // remote centre of motion of the grasper
-    int pad3;
+    int first_free_tile;              // 128-slot tiles before it hold pinned vertices only
     const uint2* erec;                // [E] edge records of the stream, unpadded, stream order
     const uint4* trec;                // [T] tet records of the stream, unpadded, stream order
     double box_lo[3], box_hi[3], tool_start[3];

@@ -1136,6 +1136,9 @@ __global__ void __launch_bounds__(kWarmThreads, 3)
     const uint32_t aW1 = saddr(Wt), aW2 = aW1 + 2048, aW3 = aW1 + 10240, aA = saddr(At), aH = saddr(Ht);
     const float cx = float(s_tool[0]), cy = float(s_tool[1]), cz = float(s_tool[2]);
     const int n_tiles = (V + 127) / 128;
+    // tiles of pinned vertices only come first in slot order on meshes pinned
+    // at their lowest vertex ids; their outputs would never be applied
+    const int t0 = M.first_free_tile < n_tiles ? M.first_free_tile : n_tiles;
     const int reach = M.tile_reach > 2 ? M.tile_reach : 2;
     const bool epi = warp < 4;
     const uint32_t tlane = uint32_t(32 * (warp & 3)) << 16;
@@ -1165,17 +1168,17 @@ __global__ void __launch_bounds__(kWarmThreads, 3)
         FeatRow fr{};   // feature warps: the tables of their row of the next tile, fetched a tile ahead
         if (!epi) {
             uint32_t pk[8];
-            warm_features(M, net, X, VH, frow, cx, cy, cz, pk);
+            warm_features(M, net, X, VH, t0 * 128 + frow, cx, cy, cz, pk);
             *reinterpret_cast<uint4*>(At + tile_off(frow, 0, 2)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
             *reinterpret_cast<uint4*>(At + tile_off(frow, 1, 2)) = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-            fr = warm_feat_fetch(M, 128 + frow);
+            fr = warm_feat_fetch(M, (t0 + 1) * 128 + frow);
         }
         fence_async_smem();
         fence_before_sync();
         __syncthreads();
         fence_after_sync();
         bool bad = false;
-        for (int t = 0; t < n_tiles; ++t) {
+        for (int t = t0; t < n_tiles; ++t) {
             // Layer 1: D[0:64) = A (128 x 16) W1^T; its completion is signalled
             // to both warp groups.
             if (tid == 0) {
@@ -1184,7 +1187,7 @@ __global__ void __launch_bounds__(kWarmThreads, 3)
                 umma_commit(&mbar[3]);
             }
             if (epi) {
-                if (t >= reach) apply_tile(t - reach);
+                if (t - reach >= t0) apply_tile(t - reach);
                 bad |= !mbar_wait(&mbar[2], ph_e & 1);
                 ++ph_e;
                 fence_after_sync();
@@ -1249,7 +1252,7 @@ __global__ void __launch_bounds__(kWarmThreads, 3)
             bad |= !mbar_wait(&mbar[2], ph_e & 1);
             ++ph_e;
             fence_after_sync();
-            for (int p = n_tiles > reach ? n_tiles - reach : 0; p < n_tiles; ++p) apply_tile(p);
+            for (int p = n_tiles - reach > t0 ? n_tiles - reach : t0; p < n_tiles; ++p) apply_tile(p);
         }
         fence_before_sync();
         if (__syncthreads_or(bad)) {
