@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(SUB, 1)
                         }
                         if (!carry) {
                             float l = 0.f;
-                            project_edge(X, make_uint2(cur.x, cur.y), at_d, M.min_len2, l);
+                            project_edge<false>(X, make_uint2(cur.x, cur.y), at_d, M.min_len2, l);
                         } else {
                             float l = it > 0 ? lam[sg.w + q] : 0.f;
                             project_edge(X, make_uint2(cur.x, cur.y), at_d, M.min_len2, l);
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(SUB, 1)
                         const uint4 nxt = (q + SUB < sg.z) ? __ldg(rec + q + SUB) : cur;
                         if (!carry) {
                             float l = 0.f;
-                            project_tet(X, cur, at_v, l);
+                            project_tet<false>(X, cur, at_v, l);
                         } else {
                             float l = it > 0 ? lam[sg.w + q] : 0.f;
                             project_tet(X, cur, at_v, l);

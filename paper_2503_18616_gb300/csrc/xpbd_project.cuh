@@ -44,6 +44,9 @@ __device__ __forceinline__ float rsqrt_est(float x) {
 // copies; false (nothing changed) for a skipped constraint. Every rounding
 // step is spelled out (fused multiply-adds where written), so all kernels
 // that call this give the same bits whatever their register budget.
+// LAM = false: lambda is 0 and not kept (one iteration); fma(-at, 0, -C) is
+// -C exactly for a finite at >= 0, so -C is used directly (same bits).
+template <bool LAM = true>
 __device__ __forceinline__ bool edge_update(float4& xa, float4& xb, float d, float at, float min_len2, float& lam) {
     const float dx = __fsub_rn(xa.x, xb.x), dy = __fsub_rn(xa.y, xb.y), dz = __fsub_rn(xa.z, xb.z);
     const float l2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
@@ -52,26 +55,27 @@ __device__ __forceinline__ bool edge_update(float4& xa, float4& xb, float d, flo
     const float il = rsqrt_est(l2);            // 1/|x_ab| (hardware estimate)
     const float len = __fmul_rn(l2, il);
     const float C = __fsub_rn(len, d);
-    const float dl = __fmul_rn(__fmaf_rn(-at, lam, -C), rcp_est(denom));
+    const float dl = __fmul_rn(LAM ? __fmaf_rn(-at, lam, -C) : -C, rcp_est(denom));
     const float s = __fmul_rn(dl, il);
     const float sa = __fmul_rn(xa.w, s), sb = __fmul_rn(xb.w, s);
     xa.x = __fmaf_rn(sa, dx, xa.x); xa.y = __fmaf_rn(sa, dy, xa.y); xa.z = __fmaf_rn(sa, dz, xa.z);
     xb.x = __fmaf_rn(-sb, dx, xb.x); xb.y = __fmaf_rn(-sb, dy, xb.y); xb.z = __fmaf_rn(-sb, dz, xb.z);
-    lam = __fadd_rn(lam, dl);
+    if (LAM) lam = __fadd_rn(lam, dl);
     return true;
 }
 
-template <class Acc>
+template <bool LAM = true, class Acc>
 __device__ __forceinline__ void project_edge(const Acc& X, uint2 rec, float at, float min_len2, float& lam) {
     const int a = int(rec.x & 0xffffu), b = int(rec.x >> 16);
     float4 xa = X.ld(a), xb = X.ld(b);
-    if (edge_update(xa, xb, __uint_as_float(rec.y), at, min_len2, lam)) {
+    if (edge_update<LAM>(xa, xb, __uint_as_float(rec.y), at, min_len2, lam)) {
         X.st(a, xa);
         X.st(b, xb);
     }
 }
+template <bool LAM = true>
 __device__ __forceinline__ void project_edge(float4* X, uint2 rec, float at, float min_len2, float& lam) {
-    project_edge(SmemX{X}, rec, at, min_len2, lam);
+    project_edge<LAM>(SmemX{X}, rec, at, min_len2, lam);
 }
 
 __device__ __forceinline__ float3 sub3(float4 a, float4 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
@@ -97,7 +101,8 @@ __device__ __forceinline__ float dot3_rn(float3 a, float3 b) {
 // g_a = -(g_b + g_c + g_d) (the consistent reading of Eq. 2), scaled as in
 // Eq. 3 with inverse masses and compliance: dlambda = (-C - at lambda) /
 // (sum w_i |g_i|^2 + at), x_i += w_i dlambda g_i. Register copies, rounding
-// spelled out as for edges.
+// spelled out as for edges; LAM as for edges.
+template <bool LAM = true>
 __device__ __forceinline__ bool tet_update(float4& xa, float4& xb, float4& xc, float4& xd, float V0, float at,
                                            float& lam) {
     const float3 ba = sub3_rn(xb, xa), ca = sub3_rn(xc, xa), da = sub3_rn(xd, xa);
@@ -110,31 +115,32 @@ __device__ __forceinline__ bool tet_update(float4& xa, float4& xb, float4& xc, f
                                                                           __fmul_rn(xa.w, dot3_rn(g0, g0)))));
     const float denom = __fmaf_rn(sw, 1.0f / 36.0f, at);
     if (denom == 0.f) return false;
-    const float dl = __fmul_rn(__fmaf_rn(-at, lam, -C), rcp_est(denom));
+    const float dl = __fmul_rn(LAM ? __fmaf_rn(-at, lam, -C) : -C, rcp_est(denom));
     const float s = __fmul_rn(dl, 1.0f / 6.0f);
     const float sa = __fmul_rn(xa.w, s), sb = __fmul_rn(xb.w, s), sc = __fmul_rn(xc.w, s), sd = __fmul_rn(xd.w, s);
     xa.x = __fmaf_rn(sa, g0.x, xa.x); xa.y = __fmaf_rn(sa, g0.y, xa.y); xa.z = __fmaf_rn(sa, g0.z, xa.z);
     xb.x = __fmaf_rn(sb, g1.x, xb.x); xb.y = __fmaf_rn(sb, g1.y, xb.y); xb.z = __fmaf_rn(sb, g1.z, xb.z);
     xc.x = __fmaf_rn(sc, g2.x, xc.x); xc.y = __fmaf_rn(sc, g2.y, xc.y); xc.z = __fmaf_rn(sc, g2.z, xc.z);
     xd.x = __fmaf_rn(sd, g3.x, xd.x); xd.y = __fmaf_rn(sd, g3.y, xd.y); xd.z = __fmaf_rn(sd, g3.z, xd.z);
-    lam = __fadd_rn(lam, dl);
+    if (LAM) lam = __fadd_rn(lam, dl);
     return true;
 }
 
-template <class Acc>
+template <bool LAM = true, class Acc>
 __device__ __forceinline__ void project_tet(const Acc& X, uint4 rec, float at, float& lam) {
     const int a = int(rec.x & 0xffffu), b = int(rec.x >> 16);
     const int c = int(rec.y & 0xffffu), d = int(rec.y >> 16);
     float4 xa = X.ld(a), xb = X.ld(b), xc = X.ld(c), xd = X.ld(d);
-    if (tet_update(xa, xb, xc, xd, __uint_as_float(rec.z), at, lam)) {
+    if (tet_update<LAM>(xa, xb, xc, xd, __uint_as_float(rec.z), at, lam)) {
         X.st(a, xa);
         X.st(b, xb);
         X.st(c, xc);
         X.st(d, xd);
     }
 }
+template <bool LAM = true>
 __device__ __forceinline__ void project_tet(float4* X, uint4 rec, float at, float& lam) {
-    project_tet(SmemX{X}, rec, at, lam);
+    project_tet<LAM>(SmemX{X}, rec, at, lam);
 }
 
 // Tissue connection (Sec. III-A): C = |x_v - p| - d0 with p the centroid of

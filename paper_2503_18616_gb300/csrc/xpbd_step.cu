@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(SUB * ENVS, OCC ? OCC : min_ctas_per_sm(SUB * 
                         if (!carry) {
                             for (int q = st; q < sg.z; q += SUB) {
                                 float l = 0.f;
-                                project_edge(XA, rec[q], at_d, M.min_len2, l);
+                                project_edge<false>(XA, rec[q], at_d, M.min_len2, l);
                             }
                         } else {
                             for (int q = st; q < sg.z; q += SUB) {
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(SUB * ENVS, OCC ? OCC : min_ctas_per_sm(SUB * 
                         if (!carry) {
                             for (int q = st; q < sg.z; q += SUB) {
                                 float l = 0.f;
-                                project_tet(XA, rec[q], at_v, l);
+                                project_tet<false>(XA, rec[q], at_v, l);
                             }
                         } else {
                             for (int q = st; q < sg.z; q += SUB) {
