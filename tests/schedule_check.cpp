@@ -74,6 +74,10 @@ int main(int argc, char** argv) {
     }
     for (int c = 0; c < m.C; ++c) ccol[{m.conn[4 * c], m.conn[4 * c + 1], m.conn[4 * c + 2], m.conn[4 * c + 3]}] = m.ccolor[c];
     long long rotated[2] = {0, 0};   // tets of the bank-aware schedule in their own / another order
+    // modelled shared-memory wavefronts of the bank-aware schedule's tet records: per group of 8
+    // consecutive records (one quarter-warp) and vertex position, the largest number of records
+    // whose slots share a bank group (slot mod 8); and the conflict-free count (one per position)
+    long long tet_wave = 0, tet_ideal = 0;
     for (int perm = 0; perm < 2; ++perm) {
         Schedule sc;
         build_schedule(m, 0x5EEDull + uint64_t(m.V), perm == 1, sc);
@@ -144,6 +148,21 @@ int main(int argc, char** argv) {
                     if (pr.first[k] >= 0) last[pr.first[k]] = pr.second;
         }
         if (records != m.E + m.T + m.C) ok = false;
+        if (perm == 1)
+            for (int c = sc.n_ephase; c < sc.n_ephase + sc.n_tphase; ++c) {
+                const int32_t* sg = &sc.segs[4 * c];
+                for (int g = 0; 8 * g < sg[2]; ++g)
+                    for (int k = 0; k < 4; ++k) {
+                        int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0}, mx = 0;
+                        for (int l = 8 * g; l < sg[2] && l < 8 * g + 8; ++l) {
+                            const uint32_t* r = reinterpret_cast<const uint32_t*>(sc.stream.data() + sg[0] + 16 * size_t(l));
+                            const int slot = (k & 1) ? int(r[k / 2] >> 16) : int(r[k / 2] & 0xffffu);
+                            mx = std::max(mx, ++cnt[slot & 7]);
+                        }
+                        tet_wave += mx;
+                        ++tet_ideal;
+                    }
+            }
         // grasper face records: colour by colour, every face of the colour
         // once (with its opposite vertex), no vertex twice in a colour
         if (sc.frec.size() != 4 * size_t(m.F)) ok = false;
@@ -176,5 +195,6 @@ int main(int argc, char** argv) {
                     sc.n_cphase, m.n_ecol, m.n_tcol, m.n_ccol, rounds, int(ok));
     }
     std::printf("rotated %lld %lld\n", rotated[0], rotated[1]);
+    std::printf("tetwaves %lld %lld\n", tet_wave, tet_ideal);
     return 0;
 }
